@@ -1,0 +1,265 @@
+"""FP64 CPU oracle of the hybrid FNO-LBM hot path (arXiv 2604.27158).
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, `__graft_entry__.smoke()` and
+the CPU-baseline / reference legs of `bench.py` may import this package.  The
+product path (package `paper_2604_27158_gb300`) never imports it and has no CPU
+fallback.
+
+Contents:
+  * `lbm_oracle.c` (built to `liblbm_oracle.so` with gcc): D2Q9 SRT LBM,
+    Sec. 2.1 — equilibrium, collision, streaming with halfway bounce-back,
+    Zou-He inlet/outlet completion, moments, Guo body force, and the
+    re-initialisation from macroscopic fields of the hybrid framework (Sec. 2.3).
+  * `fno_oracle.py`: the FNO forward pass of Sec. 2.2 with a naive truncated DFT.
+  * this module: ctypes bindings, the steady-state residual and the two hybrid
+    drivers of Sec. 2.3 (FNO initialisation for steady flows, FNO/LBM
+    super-time-stepping for unsteady flows).
+
+Every function here is pinned by the `-m "not gpu"` tests in
+`tests/test_oracle_*.py` (conservation, fixed point, Poiseuille, Taylor-Green,
+bounce-back permutation, brute-force DFT, library FFT, parameter counts).
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import subprocess
+from typing import Optional
+
+import numpy as np
+
+from . import fno_oracle  # noqa: F401  (re-exported)
+from .fno_oracle import fno_forward, param_count  # noqa: F401
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lbm_oracle.c")
+_LIB = os.path.join(_HERE, "liblbm_oracle.so")
+
+BC_PERIODIC, BC_PRESSURE, BC_VELOCITY = 0, 1, 2
+Q = 9
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle (plain -O2, single thread) if it is missing or stale."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _OlGrid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("tau", ctypes.c_double),
+                ("fx", ctypes.c_double), ("fy", ctypes.c_double),
+                ("bc_west", ctypes.c_int), ("bc_east", ctypes.c_int),
+                ("west_value", ctypes.c_double), ("east_value", ctypes.c_double)]
+
+
+@dataclasses.dataclass
+class Grid:
+    """One lattice: size, relaxation time, body force and x-end boundary kinds."""
+    nx: int
+    ny: int
+    tau: float
+    fx: float = 0.0
+    fy: float = 0.0
+    bc_west: int = BC_PERIODIC
+    bc_east: int = BC_PERIODIC
+    west_value: float = 1.0
+    east_value: float = 1.0
+
+    def c(self) -> _OlGrid:
+        return _OlGrid(self.nx, self.ny, self.tau, self.fx, self.fy, self.bc_west,
+                       self.bc_east, self.west_value, self.east_value)
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        P = ctypes.POINTER
+        d, u8 = P(ctypes.c_double), P(ctypes.c_uint8)
+        g = P(_OlGrid)
+        for name, args in [
+            ("ol_equilibrium", [ctypes.c_double, ctypes.c_double, ctypes.c_double, d]),
+            ("ol_collide", [g, u8, d, d]),
+            ("ol_stream", [g, u8, d, d]),
+            ("ol_boundary", [g, u8, d]),
+            ("ol_run", [g, u8, d, ctypes.c_int]),
+            ("ol_macro", [g, u8, d, d, d, d]),
+            ("ol_reinit", [g, u8, d, d, d, ctypes.c_int, d]),
+            ("ol_lattice", [P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int), d]),
+        ]:
+            fn = getattr(_lib, name)
+            fn.argtypes = args
+            fn.restype = None
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _mask(solid: np.ndarray, grid: Grid) -> np.ndarray:
+    m = np.ascontiguousarray(solid, dtype=np.uint8)
+    assert m.shape == (grid.ny, grid.nx)
+    return m
+
+
+def _u8(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+
+
+def lattice():
+    """(cx, cy, w, opp) of the D2Q9 lattice as the C oracle defines it."""
+    cx = (ctypes.c_int * Q)()
+    cy = (ctypes.c_int * Q)()
+    opp = (ctypes.c_int * Q)()
+    w = (ctypes.c_double * Q)()
+    lib().ol_lattice(cx, cy, opp, w)
+    return (np.array(cx[:]), np.array(cy[:]), np.array(w[:]), np.array(opp[:]))
+
+
+def equilibrium(rho: float, ux: float, uy: float) -> np.ndarray:
+    out = np.zeros(Q)
+    lib().ol_equilibrium(rho, ux, uy, _dp(out))
+    return out
+
+
+def collide(grid: Grid, solid: np.ndarray, f: np.ndarray) -> np.ndarray:
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.empty_like(f)
+    m = _mask(solid, grid)
+    gc = grid.c()
+    lib().ol_collide(ctypes.byref(gc), _u8(m), _dp(f), _dp(out))
+    return out
+
+
+def stream(grid: Grid, solid: np.ndarray, fstar: np.ndarray) -> np.ndarray:
+    """Streaming with halfway bounce-back, then Zou-He completion."""
+    fstar = np.ascontiguousarray(fstar, dtype=np.float64)
+    out = np.empty_like(fstar)
+    m = _mask(solid, grid)
+    gc = grid.c()
+    lib().ol_stream(ctypes.byref(gc), _u8(m), _dp(fstar), _dp(out))
+    return out
+
+
+def boundary(grid: Grid, solid: np.ndarray, f: np.ndarray) -> np.ndarray:
+    f = np.array(f, dtype=np.float64, order="C")
+    m = _mask(solid, grid)
+    gc = grid.c()
+    lib().ol_boundary(ctypes.byref(gc), _u8(m), _dp(f))
+    return f
+
+
+def run(grid: Grid, solid: np.ndarray, f: np.ndarray, nsteps: int) -> np.ndarray:
+    """nsteps of collide + stream; returns the post-stream populations."""
+    f = np.array(f, dtype=np.float64, order="C")
+    m = _mask(solid, grid)
+    gc = grid.c()
+    lib().ol_run(ctypes.byref(gc), _u8(m), _dp(f), int(nsteps))
+    return f
+
+
+def macro(grid: Grid, solid: np.ndarray, f: np.ndarray):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    rho = np.empty((grid.ny, grid.nx))
+    ux = np.empty_like(rho)
+    uy = np.empty_like(rho)
+    m = _mask(solid, grid)
+    gc = grid.c()
+    lib().ol_macro(ctypes.byref(gc), _u8(m), _dp(f), _dp(rho), _dp(ux), _dp(uy))
+    return rho, ux, uy
+
+
+def reinit(grid: Grid, solid: np.ndarray, rho, ux, uy, neq_mode: int = 1) -> np.ndarray:
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    ux = np.ascontiguousarray(ux, dtype=np.float64)
+    uy = np.ascontiguousarray(uy, dtype=np.float64)
+    f = np.empty((Q, grid.ny, grid.nx))
+    m = _mask(solid, grid)
+    gc = grid.c()
+    lib().ol_reinit(ctypes.byref(gc), _u8(m), _dp(rho), _dp(ux), _dp(uy), int(neq_mode), _dp(f))
+    return f
+
+
+def rest_state(grid: Grid, solid: np.ndarray) -> np.ndarray:
+    """Default initialisation of Fig. 1: rho = 1, u = 0, f = f^eq (Zou-He completed)."""
+    one = np.ones((grid.ny, grid.nx))
+    zero = np.zeros_like(one)
+    return reinit(grid, solid, one, zero, zero, neq_mode=0)
+
+
+def steady_residual(solid: np.ndarray, ux_now, uy_now, ux_prev, uy_prev) -> float:
+    """r = ||u^n - u^(n-K)||_2 / ||u^n||_2 over fluid cells (steady-state criterion)."""
+    fl = ~np.asarray(solid, dtype=bool)
+    num = np.sum((ux_now - ux_prev)[fl] ** 2 + (uy_now - uy_prev)[fl] ** 2)
+    den = np.sum(ux_now[fl] ** 2 + uy_now[fl] ** 2)
+    return float(np.sqrt(num / den)) if den > 0 else float("inf")
+
+
+def clamp_macro(rho, ux, uy, rho_lo=0.9, rho_hi=1.1, u_max=0.2):
+    """Clamp predicted fields before re-initialisation: rho into [rho_lo, rho_hi], |u| <= u_max."""
+    rho = np.clip(rho, rho_lo, rho_hi)
+    sp = np.sqrt(ux * ux + uy * uy)
+    scale = np.where(sp > u_max, u_max / np.maximum(sp, 1e-300), 1.0)
+    return rho, ux * scale, uy * scale
+
+
+def fno_input(solid: np.ndarray, rho, ux, uy) -> np.ndarray:
+    """FNO input channels (rho - 1, u_x, u_y, mask) as [4, ny, nx] float64."""
+    return np.stack([rho - 1.0, ux, uy, np.asarray(solid, dtype=np.float64)])
+
+
+def hybrid_steady(grid: Grid, solid: np.ndarray, shape, params, nsteps: int,
+                  check_every: int = 100, neq_mode: int = 1, use_fno: bool = True,
+                  activation: str = "gelu", clamp=(0.9, 1.1, 0.2)):
+    """Steady framework (Fig. 3a): FNO prediction -> re-initialisation -> LBM.
+
+    The FNO sees the default fields (rho = 1, u = 0) and the mask; its output
+    (delta rho, u_x, u_y) is clamped and turned into populations.  Returns
+    (f, residual history [(step, r)]).
+    """
+    one = np.ones((grid.ny, grid.nx))
+    zero = np.zeros_like(one)
+    if use_fno:
+        x = fno_input(solid, one, zero, zero)[None]
+        y = fno_forward(shape, params, x, activation=activation)[0]
+        rho, ux, uy = clamp_macro(1.0 + y[0], y[1], y[2], *clamp)
+        f = reinit(grid, solid, rho, ux, uy, neq_mode)
+    else:
+        f = rest_state(grid, solid)
+    hist = []
+    _, ux_p, uy_p = macro(grid, solid, f)
+    done = 0
+    while done < nsteps:
+        k = min(check_every, nsteps - done)
+        f = run(grid, solid, f, k)
+        done += k
+        _, ux_n, uy_n = macro(grid, solid, f)
+        hist.append((done, steady_residual(solid, ux_n, uy_n, ux_p, uy_p)))
+        ux_p, uy_p = ux_n, uy_n
+    return f, hist
+
+
+def hybrid_unsteady(grid: Grid, solid: np.ndarray, shape, params, f0: np.ndarray,
+                    k_lbm: int, m_fno: int, cycles: int, neq_mode: int = 1,
+                    activation: str = "gelu", clamp=(0.9, 1.1, 0.2)):
+    """Super-time-stepping (Fig. 3b): per cycle k_lbm LBM steps, then m_fno FNO
+    steps on the macroscopic fields, then re-initialisation of f.  Returns f."""
+    f = np.array(f0, dtype=np.float64)
+    for _ in range(cycles):
+        f = run(grid, solid, f, k_lbm)
+        rho, ux, uy = macro(grid, solid, f)
+        for _ in range(m_fno):
+            y = fno_forward(shape, params, fno_input(solid, rho, ux, uy)[None],
+                            activation=activation)[0]
+            rho, ux, uy = clamp_macro(1.0 + y[0], y[1], y[2], *clamp)
+        f = reinit(grid, solid, rho, ux, uy, neq_mode)
+    return f

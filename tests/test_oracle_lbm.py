@@ -1,0 +1,322 @@
+"""Pins of the FP64 LBM oracle against what the method and the mathematics fix.
+
+Each test names the property it checks and where the paper states the
+underlying equation (Sec. 2.1 equilibrium / SRT collision / streaming /
+moments).  None of them re-types an oracle formula: they check conservation
+laws, fixed points, analytic flows, permutation structure and library routines.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+CX, CY, W, OPP = oracle.lattice()
+CS2 = 1.0 / 3.0
+
+
+def test_lattice_isotropy():
+    # D2Q9 moment identities (any valid weight/velocity set must satisfy them)
+    assert np.isclose(W.sum(), 1.0)
+    assert np.isclose((W * CX).sum(), 0.0) and np.isclose((W * CY).sum(), 0.0)
+    assert np.isclose((W * CX * CX).sum(), CS2) and np.isclose((W * CY * CY).sum(), CS2)
+    assert np.isclose((W * CX * CY).sum(), 0.0)
+    assert np.isclose((W * CX ** 4).sum(), 3 * CS2 ** 2)
+    assert np.isclose((W * CX ** 2 * CY ** 2).sum(), CS2 ** 2)
+    for i in range(9):
+        assert CX[OPP[i]] == -CX[i] and CY[OPP[i]] == -CY[i]
+
+
+@pytest.mark.parametrize("rho,ux,uy", [(1.0, 0.0, 0.0), (1.02, 0.05, -0.03), (0.97, -0.1, 0.08)])
+def test_equilibrium_moments(rho, ux, uy):
+    # zeroth, first and second moments of f^eq: rho, rho u, rho (cs2 I + u u)
+    feq = oracle.equilibrium(rho, ux, uy)
+    assert np.isclose(feq.sum(), rho, rtol=0, atol=1e-15)
+    assert np.isclose((CX * feq).sum(), rho * ux, atol=1e-15)
+    assert np.isclose((CY * feq).sum(), rho * uy, atol=1e-15)
+    assert np.isclose((CX * CX * feq).sum(), rho * (CS2 + ux * ux), atol=1e-15)
+    assert np.isclose((CY * CY * feq).sum(), rho * (CS2 + uy * uy), atol=1e-15)
+    assert np.isclose((CX * CY * feq).sum(), rho * ux * uy, atol=1e-15)
+
+
+def _periodic(nx, ny, tau, **kw):
+    return oracle.Grid(nx=nx, ny=ny, tau=tau, **kw)
+
+
+def test_collision_conserves_mass_and_momentum():
+    g = _periodic(16, 12, 0.8)
+    solid = np.zeros((12, 16), bool)
+    rng = np.random.default_rng(1)
+    f = W[:, None, None] * (1.0 + 0.05 * rng.standard_normal((9, 12, 16)))
+    fs = oracle.collide(g, solid, f)
+    d = fs - f
+    assert np.abs(d.sum(axis=0)).max() < 1e-15
+    assert np.abs((CX[:, None, None] * d).sum(axis=0)).max() < 1e-15
+    assert np.abs((CY[:, None, None] * d).sum(axis=0)).max() < 1e-15
+    # and it does relax: the non-conserved moments change
+    assert np.abs(d).max() > 1e-4
+
+
+def test_equilibrium_is_fixed_point_of_collision():
+    g = _periodic(8, 8, 0.63)
+    solid = np.zeros((8, 8), bool)
+    rho, ux, uy = synth.smooth_macro_fields(8, 8, seed=3)
+    f = oracle.reinit(g, solid, rho, ux, uy, neq_mode=0)
+    fs = oracle.collide(g, solid, f)
+    assert np.abs(fs - f).max() < 1e-16 * 10
+
+
+def test_collision_relaxation_rate():
+    # the non-equilibrium part decays by exactly (1 - 1/tau) per collision
+    tau = 0.7
+    g = _periodic(4, 4, tau)
+    solid = np.zeros((4, 4), bool)
+    rng = np.random.default_rng(2)
+    f = W[:, None, None] * (1.0 + 0.02 * rng.standard_normal((9, 4, 4)))
+    rho, ux, uy = oracle.macro(g, solid, f)
+    feq = np.stack([oracle.equilibrium(rho[y, x], ux[y, x], uy[y, x])
+                    for y in range(4) for x in range(4)], axis=1).reshape(9, 4, 4)
+    fs = oracle.collide(g, solid, f)
+    np.testing.assert_allclose(fs - feq, (1 - 1 / tau) * (f - feq), atol=1e-15)
+
+
+def _probe_state(ny, nx):
+    # f*_i(x) = 9 * cell + i : distinct integers, exact in float32 and float64
+    cell = np.arange(ny * nx).reshape(ny, nx)
+    return (9 * cell[None] + np.arange(9)[:, None, None]).astype(np.float64)
+
+
+def test_streaming_is_translation_on_empty_periodic_domain():
+    ny, nx = 7, 10
+    g = _periodic(nx, ny, 0.8)
+    solid = np.zeros((ny, nx), bool)
+    fs = _probe_state(ny, nx)
+    f = fs.copy()
+    for n in range(1, 4):
+        f = oracle.stream(g, solid, f)
+        for i in range(9):
+            # a library routine: np.roll moves population i by n * c_i
+            np.testing.assert_array_equal(f[i], np.roll(fs[i], (n * CY[i], n * CX[i]), axis=(0, 1)))
+
+
+def test_bounce_back_reflects_single_particle():
+    ny, nx = 9, 9
+    g = _periodic(nx, ny, 0.8)
+    solid = np.zeros((ny, nx), bool)
+    solid[4, 5] = True  # obstacle east of the centre cell (4, 4)
+    fs = np.zeros((9, ny, nx))
+    fs[1, 4, 4] = 1.0   # moving east, towards the obstacle
+    fs[3, 4, 4] = 2.0   # moving west, free
+    f = oracle.stream(g, solid, fs)
+    assert f[3, 4, 4] == 1.0          # reflected into the opposite direction, same cell
+    assert f[3, 4, 3] == 2.0          # free particle moved one cell west
+    assert np.count_nonzero(f[:, ~solid]) == 2
+
+
+def test_streaming_with_walls_is_permutation_and_conserves_mass():
+    solid, _ = synth.channel_with_disks(nx=40, ny=24, ndisks=3, rmin=3, rmax=5, seed=4)
+    g = _periodic(40, 24, 0.8)
+    fs = _probe_state(24, 40)
+    f = oracle.stream(g, solid, fs)
+    fl = ~solid
+    a = np.sort(fs[:, fl].ravel())
+    b = np.sort(f[:, fl].ravel())
+    np.testing.assert_array_equal(a, b)  # bijection on fluid populations
+
+
+def test_mass_conservation_2000_steps_config1_geometry():
+    solid, _ = synth.channel_with_disks(seed=0)  # 128 x 64, 6 disks, wall rows
+    g = _periodic(128, 64, 0.8)
+    rng = np.random.default_rng(0)
+    rho = 1.0 + 0.01 * rng.standard_normal((64, 128))
+    ux = 0.02 * rng.standard_normal((64, 128))
+    uy = 0.02 * rng.standard_normal((64, 128))
+    f = oracle.reinit(g, solid, rho, ux, uy, neq_mode=0)
+    m0 = f[:, ~solid].sum()
+    f = oracle.run(g, solid, f, 2000)
+    m1 = f[:, ~solid].sum()
+    assert abs(m1 - m0) / m0 < 1e-12
+
+
+def test_momentum_conservation_periodic_no_force():
+    g = _periodic(24, 16, 0.9)
+    solid = np.zeros((16, 24), bool)
+    rho, ux, uy = synth.smooth_macro_fields(24, 16, seed=5)
+    f = oracle.reinit(g, solid, rho, ux, uy, neq_mode=1)
+    p0 = np.array([(CX[:, None, None] * f).sum(), (CY[:, None, None] * f).sum()])
+    f = oracle.run(g, solid, f, 300)
+    p1 = np.array([(CX[:, None, None] * f).sum(), (CY[:, None, None] * f).sum()])
+    assert np.abs(p1 - p0).max() < 1e-12
+
+
+def test_uniform_force_adds_momentum_linearly():
+    # Guo forcing: total momentum grows by F per cell per step (periodic, no walls)
+    g = _periodic(12, 10, 0.75, fx=1e-5, fy=-2e-5)
+    solid = np.zeros((10, 12), bool)
+    f = oracle.rest_state(g, solid)
+    steps = 50
+    f = oracle.run(g, solid, f, steps)
+    px = (CX[:, None, None] * f).sum()
+    py = (CY[:, None, None] * f).sum()
+    assert np.isclose(px, steps * 1e-5 * 120, rtol=1e-10)
+    assert np.isclose(py, steps * -2e-5 * 120, rtol=1e-10)
+
+
+def _poiseuille_error(nfluid, tau, gx=1e-6, nx=4, time_constants=6.0):
+    ny = nfluid + 2
+    g = _periodic(nx, ny, tau, fx=gx)
+    solid = np.zeros((ny, nx), bool)
+    solid[0, :] = True
+    solid[-1, :] = True
+    nu = CS2 * (tau - 0.5)
+    y = np.arange(ny, dtype=np.float64)
+    y0, y1 = 0.5, ny - 1.5           # halfway walls
+    exact = gx / (2 * nu) * (y - y0) * (y1 - y)
+    # start from the analytic profile to shorten the transient
+    rho = np.ones((ny, nx))
+    ux = np.repeat(exact[:, None], nx, axis=1)
+    ux[solid] = 0.0
+    uy = np.zeros_like(ux)
+    f = oracle.reinit(g, solid, rho, ux, uy, neq_mode=1)
+    steps = int(time_constants * nfluid ** 2 / nu / math.pi ** 2) + 200
+    f = oracle.run(g, solid, f, steps)
+    _, uxn, _ = oracle.macro(g, solid, f)
+    prof = uxn[1:-1, 0]
+    ex = exact[1:-1]
+    return np.sqrt(np.sum((prof - ex) ** 2) / np.sum(ex ** 2))
+
+
+def test_poiseuille_second_order_convergence():
+    tau = 0.8
+    errs = [_poiseuille_error(h, tau) for h in (8, 16, 32)]
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(1.8 < o < 2.2 for o in orders), (errs, orders)
+
+
+def test_poiseuille_exact_at_magic_tau():
+    # BGK with halfway bounce-back places the wall exactly when (tau - 1/2)^2 = 3/16
+    tau = 0.5 + math.sqrt(3.0 / 16.0)
+    assert _poiseuille_error(10, tau, time_constants=25.0) < 1e-9
+
+
+def _taylor_green(n, tau, steps, u0=1e-3):
+    g = _periodic(n, n, tau)
+    solid = np.zeros((n, n), bool)
+    k = 2 * math.pi / n
+    x = np.arange(n)[None, :]
+    y = np.arange(n)[:, None]
+    ux = -u0 * np.cos(k * x) * np.sin(k * y)
+    uy = u0 * np.sin(k * x) * np.cos(k * y)
+    p = -0.25 * u0 ** 2 * (np.cos(2 * k * x) + np.cos(2 * k * y))
+    rho = 1.0 + p / CS2
+    f = oracle.reinit(g, solid, rho, ux, uy, neq_mode=1)
+    f = oracle.run(g, solid, f, steps)
+    _, uxn, uyn = oracle.macro(g, solid, f)
+    amp = np.sum(uxn * ux + uyn * uy) / np.sum(ux * ux + uy * uy)
+    nu = CS2 * (tau - 0.5)
+    return amp, math.exp(-2 * nu * k * k * steps)
+
+
+def test_taylor_green_decay_rate():
+    tau = 0.8
+    errs = []
+    for n in (16, 32):
+        nu = CS2 * (tau - 0.5)
+        k = 2 * math.pi / n
+        steps = int(round(0.5 / (2 * nu * k * k)))  # amplitude decays to ~e^-0.5
+        amp, exact = _taylor_green(n, tau, steps)
+        errs.append(abs(amp - exact) / exact)
+    assert errs[1] < 2e-3
+    assert errs[0] / errs[1] > 3.0, errs  # second-order in k
+
+
+def test_zou_he_imposes_density_and_normal_velocity():
+    solid, _, _ = synth.porous_media(nx=96, ny=48, rmin=3, rmax=5, seed=1)
+    g = oracle.Grid(nx=96, ny=48, tau=0.7, bc_west=oracle.BC_PRESSURE,
+                    bc_east=oracle.BC_PRESSURE, west_value=1.001, east_value=1.0)
+    f = oracle.rest_state(g, solid)
+    f = oracle.run(g, solid, f, 300)
+    rho, ux, uy = oracle.macro(g, solid, f)
+    west, east = ~solid[:, 0], ~solid[:, -1]
+    np.testing.assert_allclose(rho[west, 0], 1.001, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(rho[east, -1], 1.0, rtol=0, atol=1e-14)
+    assert np.abs(uy[west, 0]).max() < 1e-15 and np.abs(uy[east, -1]).max() < 1e-15
+    assert ux[west, 0].mean() > 0  # flow from high to low pressure
+
+
+def test_zou_he_velocity_inlet():
+    ny, nx = 20, 40
+    solid = np.zeros((ny, nx), bool)
+    g = oracle.Grid(nx=nx, ny=ny, tau=0.8, bc_west=oracle.BC_VELOCITY,
+                    bc_east=oracle.BC_PRESSURE, west_value=0.02, east_value=1.0)
+    f = oracle.rest_state(g, solid)
+    f = oracle.run(g, solid, f, 200)
+    rho, ux, uy = oracle.macro(g, solid, f)
+    np.testing.assert_allclose(ux[:, 0], 0.02, atol=1e-15)
+    np.testing.assert_allclose(uy[:, 0], 0.0, atol=1e-15)
+    np.testing.assert_allclose(rho[:, -1], 1.0, atol=1e-14)
+
+
+def test_reinit_equilibrium_roundtrip():
+    solid, _ = synth.channel_with_disks(nx=32, ny=20, ndisks=2, rmin=3, rmax=4, seed=2)
+    g = _periodic(32, 20, 0.8)
+    rho, ux, uy = synth.smooth_macro_fields(32, 20, seed=7)
+    f = oracle.reinit(g, solid, rho, ux, uy, neq_mode=0)
+    r2, ux2, uy2 = oracle.macro(g, solid, f)
+    fl = ~solid
+    np.testing.assert_allclose(r2[fl], rho[fl], atol=1e-14)
+    np.testing.assert_allclose(ux2[fl], ux[fl], atol=1e-14)
+    np.testing.assert_allclose(uy2[fl], uy[fl], atol=1e-14)
+    assert np.all(f[:, solid] == W[:, None])
+
+
+def test_reinit_nonequilibrium_reproduces_viscous_stress():
+    # Chapman-Enskog: Pi^neq_ab = sum_i c_ia c_ib f^neq_i = -rho cs2 tau (d_a u_b + d_b u_a)
+    ny, nx, tau = 16, 12, 0.9
+    g = _periodic(nx, ny, tau)
+    solid = np.zeros((ny, nx), bool)
+    a, b, c = 2e-3, -1e-3, 5e-4   # linear field, exact central differences away from wrap
+    xg = np.arange(nx)[None, :] * np.ones((ny, 1))
+    yg = np.arange(ny)[:, None] * np.ones((1, nx))
+    ux = a * yg + c * xg
+    uy = b * xg - c * yg
+    rho = np.full((ny, nx), 1.01)
+    f1 = oracle.reinit(g, solid, rho, ux, uy, neq_mode=1)
+    f0 = oracle.reinit(g, solid, rho, ux, uy, neq_mode=0)
+    fneq = (f1 - f0)[:, 1:-1, 1:-1]
+    dxux, dyux, dxuy, dyuy = c, a, b, -c
+    pxx = (CX[:, None, None] ** 2 * fneq).sum(0)
+    pyy = (CY[:, None, None] ** 2 * fneq).sum(0)
+    pxy = (CX[:, None, None] * CY[:, None, None] * fneq).sum(0)
+    k = -1.01 * CS2 * tau
+    np.testing.assert_allclose(pxx, k * 2 * dxux, atol=1e-15)
+    np.testing.assert_allclose(pyy, k * 2 * dyuy, atol=1e-15)
+    np.testing.assert_allclose(pxy, k * (dxuy + dyux), atol=1e-15)
+    # f^neq carries no mass and no momentum
+    assert np.abs(fneq.sum(0)).max() < 1e-16 * 100
+    assert np.abs((CX[:, None, None] * fneq).sum(0)).max() < 1e-16 * 100
+
+
+def test_steady_residual_definition():
+    solid = np.zeros((2, 2), bool)
+    solid[0, 0] = True
+    ux = np.array([[9.0, 3.0], [0.0, 4.0]])
+    uy = np.zeros((2, 2))
+    r = oracle.steady_residual(solid, ux, uy, ux * 0.5, uy)
+    assert np.isclose(r, 0.5)  # ||u - u/2|| / ||u|| over the three fluid cells
+
+
+def test_hybrid_steady_driver_runs_and_converges_toward_steady_state():
+    import synth as s
+    solid, _, _ = s.porous_media(nx=64, ny=32, rmin=3, rmax=4, seed=3)
+    g = oracle.Grid(nx=64, ny=32, tau=0.7, bc_west=oracle.BC_PRESSURE,
+                    bc_east=oracle.BC_PRESSURE, west_value=1.001, east_value=1.0)
+    shape = s.FnoShape(width=8, layers=1, modes=3, dec_size=8)
+    params = s.fno_random_params(shape, seed=0)
+    _, hist_fno = oracle.hybrid_steady(g, solid, shape, params, nsteps=3000, check_every=500)
+    _, hist_rest = oracle.hybrid_steady(g, solid, shape, params, nsteps=3000, check_every=500,
+                                        use_fno=False)
+    for hist in (hist_fno, hist_rest):
+        assert hist[-1][1] < hist[1][1] < 1.0
