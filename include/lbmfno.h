@@ -1,0 +1,155 @@
+/*
+ * lbmfno — GB300 (sm_103a) hot path of the hybrid Fourier Neural Operator -
+ * Lattice Boltzmann Method (arXiv 2604.27158).  Plain C ABI.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every call returns an int status (enum lbm_status).  Nothing throws.  On
+ *    failure lbm_last_error() returns a message (thread-local, valid until the
+ *    next failing call on the same thread).
+ *  - Pointers with a `_d` suffix are device pointers (cudaMalloc / torch CUDA
+ *    memory) owned by the caller; `_h` pointers are host memory owned by the
+ *    caller.  The library owns only its opaque handles and small tables.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are asynchronous on that stream unless stated otherwise.
+ *  - Lattice: D2Q9, i = 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1)
+ *    6:(-1,1) 7:(-1,-1) 8:(1,-1); weights 4/9, 1/9 (i=1..4), 1/36 (i=5..8);
+ *    c_s^2 = 1/3; lattice units dx = dt = 1.
+ *  - Canonical population layout ("canonical" below): for grid g with
+ *    cells_before(g) = sum of nx*ny of the grids before it, population i of
+ *    cell (x, y) sits at 9 * cells_before(g) + (i * ny + y) * nx + x.  Values
+ *    are *shifted*: g_i = f_i - w_i (FP32), the quantity the kernels carry.
+ *  - Dense field layout ("dense"): value of cell (x, y) of grid g at
+ *    cells_before(g) + y * nx + x.
+ *  - Packed mask: for grid g, words_before(g) = sum of ny * ceil(nx/32) of the
+ *    grids before it; bit (x % 32) of word words_before(g) + y*ceil(nx/32) + x/32
+ *    is 1 iff cell (x, y) is solid.
+ */
+#ifndef LBMFNO_H
+#define LBMFNO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum lbm_status {
+  LBM_OK = 0,
+  LBM_ERR_INVALID_ARG = 1, /* bad size, pointer, alignment or configuration */
+  LBM_ERR_CUDA = 2,        /* a CUDA runtime / driver call failed */
+  LBM_ERR_UNSTABLE = 3,    /* NaN/Inf or |u| > u_max detected in a reduction */
+  LBM_ERR_TIMEOUT = 4,     /* a bounded device-side wait expired */
+  LBM_ERR_UNSUPPORTED = 5  /* valid request this build does not implement */
+};
+
+/* x-end boundary kinds.  y is always periodic; walls are solid mask rows. */
+enum lbm_bc {
+  LBM_BC_PERIODIC = 0, /* both x ends periodic */
+  LBM_BC_PRESSURE = 1, /* Zou-He, prescribed density (value = rho) */
+  LBM_BC_VELOCITY = 2  /* Zou-He, prescribed normal velocity (value = u_x), u_y = 0 */
+};
+
+/* One lattice of a batch.  Sec. 2.1 (D2Q9 SRT); porous-media boundary set-up of
+ * the appendix table (fixed inflow, periodic sides, fixed outlet pressure). */
+typedef struct lbm_grid {
+  int32_t nx, ny;     /* lattice size, nx >= 2, ny >= 2 */
+  double tau;         /* BGK relaxation time, > 0.5 */
+  double fx, fy;      /* constant body-force density (Guo forcing), lattice units */
+  int32_t bc_west;    /* enum lbm_bc at x = 0 */
+  int32_t bc_east;    /* enum lbm_bc at x = nx-1 (periodic iff bc_west periodic) */
+  double west_value;  /* rho or u_x imposed at x = 0 */
+  double east_value;  /* rho or u_x imposed at x = nx-1 */
+} lbm_grid;
+
+/* Sizes a caller allocates for a batch of grids (lbm_query_layout). */
+typedef struct lbm_layout {
+  size_t f_elems;    /* floats in EACH of the two population buffers */
+  size_t mask_words; /* uint32 words of the packed mask */
+  size_t cells;      /* total cells: length of a dense field */
+  size_t ws_bytes;   /* device workspace bytes for lbm_init */
+} lbm_layout;
+
+/* Per-grid statistics returned by lbm_residual, LBM_NSTAT doubles per grid. */
+#define LBM_NSTAT 8
+enum lbm_stat_index {
+  LBM_STAT_RESIDUAL = 0, /* ||u^n - u^prev||_2 / ||u^n||_2 over fluid cells */
+  LBM_STAT_UNORM = 1,    /* ||u^n||_2 over fluid cells */
+  LBM_STAT_DP = 2,       /* c_s^2 (mean rho at x=0 - mean rho at x=nx-1), fluid cells */
+  LBM_STAT_MASS = 3,     /* sum of rho over fluid cells */
+  LBM_STAT_MOMX = 4,     /* sum of rho u_x over fluid cells */
+  LBM_STAT_MOMY = 5,     /* sum of rho u_y over fluid cells */
+  LBM_STAT_BAD = 6,      /* cells with non-finite values or |u| > u_max */
+  LBM_STAT_FLUID = 7     /* fluid cells */
+};
+
+typedef struct lbm_handle lbm_handle;
+
+const char* lbm_last_error(void);
+
+/* Layout of a batch of `ngrids` grids (host only, no GPU work). */
+int lbm_query_layout(const lbm_grid* grids_h, int ngrids, lbm_layout* out_h);
+
+/*
+ * Create a solver for a batch of grids and set the rest state rho = 1, u = 0
+ * (the default initialisation of Fig. 1).  mask_d: packed mask (read, must
+ * stay valid and unchanged for the handle's life).  f_a_d, f_b_d: two
+ * population buffers of layout.f_elems floats, 16-byte aligned, owned by the
+ * caller, used as ping-pong state.  ws_d: layout.ws_bytes of workspace.
+ * u_max: |u| above which reductions flag a cell as unstable.
+ */
+int lbm_init(const lbm_grid* grids_h, int ngrids, const uint32_t* mask_d, float* f_a_d,
+             float* f_b_d, void* ws_d, double u_max, void* stream, lbm_handle** out);
+
+/* Advance every grid by nsteps fused collide+stream steps (Sec. 2.1 loop:
+ * equilibrium, SRT collision, streaming with halfway bounce-back, moments).
+ * One kernel launch per step. */
+int lbm_step(lbm_handle* h, int nsteps, void* stream);
+
+/* Macroscopic fields (Sec. 2.1 moments) of the current state, dense layout.
+ * Solid cells report rho = 1, u = 0.  Any output pointer may be NULL. */
+int lbm_macro(lbm_handle* h, float* rho_d, float* ux_d, float* uy_d, void* stream);
+
+/*
+ * Steady-state statistics of the current state (FP64 reductions on the GPU,
+ * deterministic order): LBM_NSTAT doubles per grid into out_h.  The residual
+ * compares u with the velocity stored by the previous lbm_residual call with
+ * update_prev != 0 (or by lbm_init / lbm_reinit_from_macro); with
+ * update_prev != 0 the current velocity is stored for the next call.
+ * Synchronises `stream`.  Returns LBM_ERR_UNSTABLE if any grid has BAD > 0.
+ */
+int lbm_residual(lbm_handle* h, double* out_h, int update_prev, void* stream);
+
+/*
+ * Re-initialise the populations from macroscopic fields (hybrid framework,
+ * Sec. 2.3): fluid cells get f^eq(rho, u) (Sec. 2.1) plus, if neq_mode != 0,
+ * the first-order non-equilibrium estimate
+ *   f_i^neq = -(tau w_i rho / c_s^2) Q_iab d_a u_b,  Q_iab = c_ia c_ib - c_s^2 d_ab,
+ * with central differences (one-sided next to solid cells and open ends).
+ * Inputs are dense fields.  The stored velocity used by lbm_residual is reset
+ * to the given u.
+ */
+int lbm_reinit_from_macro(lbm_handle* h, const float* rho_d, const float* ux_d,
+                          const float* uy_d, int neq_mode, void* stream);
+
+/* Post-stream shifted populations g_i = f_i - w_i of the current time level
+ * (after bounce-back and Zou-He completion), canonical layout, 9*cells floats.
+ * Solid cells export 0. */
+int lbm_export_f(lbm_handle* h, float* g_d, void* stream);
+
+/* Overwrite / read the raw stored state: the shifted post-collision
+ * populations of the previous time level, canonical layout.  Streaming them
+ * (lbm_export_f) gives the current time level. */
+int lbm_set_state(lbm_handle* h, const float* gstar_d, void* stream);
+int lbm_get_state(lbm_handle* h, float* gstar_d, void* stream);
+
+/* Number of lbm_step time steps taken since lbm_init / the last reinit. */
+int lbm_steps_done(const lbm_handle* h, long long* out_h);
+
+int lbm_destroy(lbm_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBMFNO_H */

@@ -1,0 +1,883 @@
+// D2Q9 BGK lattice Boltzmann kernels for GB300 (sm_103a) and their C ABI.
+//
+// Method: Sec. 2.1 of arXiv 2604.27158 (equilibrium, SRT collision, streaming,
+// moments) with halfway bounce-back on a bit-packed solid mask, Zou-He
+// inlet/outlet columns, Guo body force, and the re-initialisation of the
+// populations from macroscopic fields used by the hybrid framework (Sec. 2.3).
+//
+// State and data layout (all FP32, HBM resident, caller-owned):
+//   * Two state buffers A/B (ping-pong).  The current buffer holds the
+//     *post-collision* populations of the previous time level, shifted by the
+//     lattice weights (g*_i = f*_i - w_i), structure of arrays per grid:
+//     plane i of grid g at f_off + i * ny * pitch, rows `pitch` floats apart
+//     (pitch = nx rounded up to 32 so each warp's 32 lanes read one aligned
+//     128-byte line per population).
+//   * One step is a *pull*: cell x gathers g*_i(x - c_i) (bounce-back
+//     g*_opp(i)(x) when x - c_i is solid), completes the Zou-He unknowns on the
+//     open end columns, takes moments, relaxes, and stores its own nine g*
+//     at aligned addresses of the other buffer.  72 B of HBM traffic per fluid
+//     cell and step, plus the 1-bit mask.
+//   * Solid cells are never read or written by the step.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace lbmfno {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+
+// raw per-block reduction slots of the residual kernel
+enum {
+  R_DU2 = 0,
+  R_U2,
+  R_RHO_W,
+  R_N_W,
+  R_RHO_E,
+  R_N_E,
+  R_DRHO,  // sum of (rho - 1) over fluid cells
+  R_MOMX,
+  R_MOMY,
+  R_BAD,
+  R_FLUID,
+  R_COUNT
+};
+
+// ------------------------------------------------------------ cell pull ---
+// Gather the post-stream shifted populations of fluid cell (x, y) from the
+// post-collision state `src` (streaming with halfway bounce-back), then apply
+// the Zou-He completion on open end columns.  Returns false for solid cells.
+__device__ __forceinline__ bool pull_cell(const GridDev& G, const uint32_t* __restrict__ mask,
+                                          const float* __restrict__ src, int x, int y,
+                                          float g[kQ]) {
+  const uint32_t* m = mask + G.mask_off;
+  if (mask_bit(m, G.wpr, x, y)) return false;
+  const float* b = src + G.f_off;
+  const long long P = G.plane;
+  const int pitch = G.pitch;
+  const int ym = (y == 0) ? G.ny - 1 : y - 1;
+  const int yp = (y == G.ny - 1) ? 0 : y + 1;
+  int xm = x - 1, xp = x + 1;
+  bool xm_out = false, xp_out = false;
+  if (xm < 0) {
+    if (G.periodic_x) xm = G.nx - 1; else xm_out = true;
+  }
+  if (xp >= G.nx) {
+    if (G.periodic_x) xp = 0; else xp_out = true;
+  }
+  const long long here = (long long)y * pitch + x;
+  g[0] = __ldg(b + here);
+#define LBM_PULL(i, XS, YS, OUT)                                              \
+  if (OUT) {                                                                  \
+    g[i] = 0.0f;                                                              \
+  } else if (mask_bit(m, G.wpr, XS, YS)) {                                    \
+    g[i] = __ldg(b + (long long)opp_of(i) * P + here);                        \
+  } else {                                                                    \
+    g[i] = __ldg(b + (long long)(i) * P + (long long)(YS) * pitch + (XS));    \
+  }
+  LBM_PULL(1, xm, y, xm_out)
+  LBM_PULL(2, x, ym, false)
+  LBM_PULL(3, xp, y, xp_out)
+  LBM_PULL(4, x, yp, false)
+  LBM_PULL(5, xm, ym, xm_out)
+  LBM_PULL(6, xp, ym, xp_out)
+  LBM_PULL(7, xp, yp, xp_out)
+  LBM_PULL(8, xm, yp, xm_out)
+#undef LBM_PULL
+  if (xm_out) {  // west column, unknown i = 1, 5, 8 (Zou-He, shifted form)
+    const float G0 = g[0] + g[2] + g[4] + 2.0f * (g[3] + g[6] + g[7]);
+    float ru;  // rho * u_x
+    if (G.bc_west == LBM_BC_PRESSURE) {
+      ru = G.west_d - G0;  // rho_in u_x = (rho_in - 1) - G0
+    } else {
+      const float U = G.west_d;
+      ru = (1.0f + G0) / (1.0f - U) * U;
+    }
+    const float t = 0.5f * (g[2] - g[4]);
+    g[1] = g[3] + (2.0f / 3.0f) * ru;
+    g[5] = g[7] - t + (1.0f / 6.0f) * ru;
+    g[8] = g[6] + t + (1.0f / 6.0f) * ru;
+  }
+  if (xp_out) {  // east column, unknown i = 3, 6, 7
+    const float G0 = g[0] + g[2] + g[4] + 2.0f * (g[1] + g[5] + g[8]);
+    float ru;
+    if (G.bc_east == LBM_BC_PRESSURE) {
+      ru = G0 - G.east_d;  // rho_out u_x = G0 - (rho_out - 1)
+    } else {
+      const float U = G.east_d;
+      ru = (1.0f + G0) / (1.0f + U) * U;
+    }
+    const float t = 0.5f * (g[2] - g[4]);
+    g[3] = g[1] - (2.0f / 3.0f) * ru;
+    g[7] = g[5] + t - (1.0f / 6.0f) * ru;
+    g[6] = g[8] - t - (1.0f / 6.0f) * ru;
+  }
+  return true;
+}
+
+// Moments of shifted populations: drho = rho - 1, u with the Guo half-force shift.
+__device__ __forceinline__ void moments(const GridDev& G, const float g[kQ], float& drho,
+                                        float& rho, float& ux, float& uy) {
+  drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+  rho = 1.0f + drho;
+  const float jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]) + 0.5f * G.fx;
+  const float jy = (g[2] - g[4]) + (g[5] - g[8]) + (g[6] - g[7]) + 0.5f * G.fy;
+  const float inv = 1.0f / rho;
+  ux = jx * inv;
+  uy = jy * inv;
+}
+
+// BGK relaxation towards the shifted equilibrium, plus the Guo source.  Opposite
+// directions (i, opp(i)) share the even part of f^eq and of the source and differ
+// in the sign of the odd part, so the nine updates are written per pair.
+__device__ __forceinline__ void collide_pair(float& gi, float& go, float w, float cu, float cf,
+                                             float drho, float rho, float usq, float om,
+                                             float sym_f, float guo) {
+  // shifted equilibrium: w (drho + rho (3 cu + 4.5 cu^2 - 1.5 u^2))
+  const float even = w * (drho + rho * (4.5f * cu * cu - usq));
+  const float odd = w * rho * 3.0f * cu;
+  // Guo source: guo w [3 (c - u).F + 9 (c.u)(c.F)]; even part -3 u.F + 9 cu cF, odd 3 cF
+  const float s_even = guo * w * (sym_f + 9.0f * cu * cf);
+  const float s_odd = guo * w * 3.0f * cf;
+  gi = gi + om * (even + odd - gi) + (s_even + s_odd);
+  go = go + om * (even - odd - go) + (s_even - s_odd);
+}
+
+__device__ __forceinline__ void collide(const GridDev& G, float g[kQ]) {
+  float drho, rho, ux, uy;
+  moments(G, g, drho, rho, ux, uy);
+  const float usq = 1.5f * (ux * ux + uy * uy);
+  const float om = G.omega, guo = G.guo, fx = G.fx, fy = G.fy;
+  const float sym_f = -3.0f * (ux * fx + uy * fy);
+  g[0] = g[0] + om * (kW0 * (drho - rho * usq) - g[0]) + guo * kW0 * sym_f;
+  collide_pair(g[1], g[3], kW1, ux, fx, drho, rho, usq, om, sym_f, guo);
+  collide_pair(g[2], g[4], kW1, uy, fy, drho, rho, usq, om, sym_f, guo);
+  collide_pair(g[5], g[7], kW2, ux + uy, fx + fy, drho, rho, usq, om, sym_f, guo);
+  collide_pair(g[6], g[8], kW2, uy - ux, fy - fx, drho, rho, usq, om, sym_f, guo);
+}
+
+__device__ __forceinline__ bool cell_of_thread(const GridDev* __restrict__ grids, int ngrids,
+                                               int& gi, int& x, int& y) {
+  gi = grid_of_block(grids, ngrids, blockIdx.x);
+  const GridDev& G = grids[gi];
+  const int p = (blockIdx.x - G.blk_start) * kBlock + threadIdx.x;
+  y = p / G.pitch;
+  x = p - y * G.pitch;
+  return y < G.ny && x < G.nx;
+}
+
+// --------------------------------------------------------------- kernels ---
+// The fused step.  One warp owns a 128-cell row segment; each lane owns four
+// consecutive cells x..x+3 (x = x0 + 4 lane).  Per population plane the lane
+// issues one aligned 16-byte load at its source row; the +-1 x-shift of the
+// pull comes from the neighbouring lane's register (warp shuffle), and the
+// segment edges take one scalar load.  The nine solid bits around each cell come
+// from 18 mask words loaded once per warp and funnel-shifted per lane.  Results
+// are stored as aligned float4 (per-cell stores where a lane has solid or
+// out-of-range cells).
+#ifndef LBM_STEP_VEC
+#define LBM_STEP_VEC 4  // cells per lane (2 or 4)
+#endif
+#ifndef LBM_STEP_MINB
+#define LBM_STEP_MINB 2  // minimum resident blocks per SM requested from ptxas
+#endif
+constexpr int kVec = LBM_STEP_VEC;
+constexpr int kSeg = 32 * kVec;
+constexpr int kStepWarps = 8;
+static_assert(kVec == 2 || kVec == 4, "LBM_STEP_VEC must be 2 or 4");
+
+template <int V>
+struct VecT;
+template <>
+struct VecT<4> {
+  using T = float4;
+  static __device__ __forceinline__ void load(const float* p, float o[4]) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  }
+  static __device__ __forceinline__ void store(float* p, const float o[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+  }
+};
+template <>
+struct VecT<2> {
+  static __device__ __forceinline__ void load(const float* p, float o[2]) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    o[0] = v.x; o[1] = v.y;
+  }
+  static __device__ __forceinline__ void store(float* p, const float o[2]) {
+    *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
+  }
+};
+
+__global__ void __launch_bounds__(kStepWarps * 32, LBM_STEP_MINB)
+    k_step(const GridDev* __restrict__ grids, int ngrids, const uint32_t* __restrict__ mask,
+           const float* __restrict__ src, float* __restrict__ dst) {
+  using V = VecT<kVec>;
+  constexpr int kWords = kVec + 2;  // mask words per row around a segment
+  const int gidx = grid_of<&GridDev::sblk_start>(grids, ngrids, blockIdx.x);
+  const GridDev& G = grids[gidx];
+  const int lane = threadIdx.x & 31;
+  const int task = (blockIdx.x - G.sblk_start) * kStepWarps + (threadIdx.x >> 5);
+  const int nx = G.nx, ny = G.ny;
+  const int y = task / G.nseg;
+  if (y >= ny) return;  // warp-uniform
+  const int x0 = (task - y * G.nseg) * kSeg;
+  const int x = x0 + kVec * lane;
+  const bool active = x < nx;
+  const bool periodic = G.periodic_x != 0;
+  const int ym = (y == 0) ? ny - 1 : y - 1;
+  const int yp = (y == ny - 1) ? 0 : y + 1;
+  const int pitch = G.pitch;
+  const unsigned P = (unsigned)G.plane;  // plane offsets fit in 32 bits (checked on the host)
+  const float* b = src + G.f_off;
+  const unsigned rowM = (unsigned)(ym * pitch), rowY = (unsigned)(y * pitch),
+                 rowP = (unsigned)(yp * pitch);
+
+  // ---- solid bits: lanes 0..3*kWords-1 fetch the mask words around the segment
+  const uint32_t* m = mask + G.mask_off;
+  uint32_t word = 0;
+  if (lane < 3 * kWords) {
+    const int r = lane / kWords;
+    const int wi = (x0 >> 5) - 1 + (lane - r * kWords);
+    const int yy = r == 0 ? ym : (r == 1 ? y : yp);
+    if (wi >= 0 && wi < G.wpr) word = __ldg(&m[yy * G.wpr + wi]);
+  }
+  // window bit b of row r <-> cell (x - 1 + b), b = 0 .. kVec+1
+  constexpr uint32_t kWin = (1u << (kVec + 2)) - 1u;
+  const int bitpos = 31 + kVec * lane;
+  const int k0 = bitpos >> 5, sh = bitpos & 31;
+  uint32_t win[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const uint32_t lo = __shfl_sync(0xffffffffu, word, r * kWords + k0);
+    const uint32_t hi = __shfl_sync(0xffffffffu, word, r * kWords + k0 + 1);
+    win[r] = __funnelshift_r(lo, hi, sh) & kWin;
+  }
+  // x-edge neighbours: the west neighbour of x = 0 and the east one of x = nx-1
+  const int jw = nx - 1 - x;  // lane-local index of the cell x = nx-1, if 0..kVec-1
+  if (active) {
+    if (x == 0) {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        win[r] &= ~1u;
+        if (periodic) win[r] |= (uint32_t)mask_bit(m, G.wpr, nx - 1, r == 0 ? ym : (r == 1 ? y : yp));
+      }
+    }
+    if (jw >= 0 && jw < kVec) {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        win[r] &= ~(1u << (jw + 2));
+        if (periodic)
+          win[r] |= (uint32_t)mask_bit(m, G.wpr, 0, r == 0 ? ym : (r == 1 ? y : yp)) << (jw + 2);
+      }
+    }
+  }
+  const uint32_t own_solid = (win[1] >> 1) & ((1u << kVec) - 1u);
+
+  // ---- pull: aligned vector loads at the source rows, shuffled by +-1 cell
+  float g[kQ][kVec];
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    const unsigned row = cy_of(i) == 0 ? rowY : (cy_of(i) > 0 ? rowM : rowP);
+    float v[kVec];
+    if (active) {
+      V::load(b + i * P + row + x, v);
+    } else {
+#pragma unroll
+      for (int j = 0; j < kVec; ++j) v[j] = 0.0f;
+    }
+    if (cx_of(i) == 0) {
+#pragma unroll
+      for (int j = 0; j < kVec; ++j) g[i][j] = v[j];
+    } else if (cx_of(i) > 0) {  // source x - 1
+      float pw = __shfl_up_sync(0xffffffffu, v[kVec - 1], 1);
+      if (lane == 0) {
+        if (x0 > 0)
+          pw = __ldg(b + i * P + row + x0 - 1);
+        else
+          pw = periodic ? __ldg(b + i * P + row + nx - 1) : 0.0f;
+      }
+      g[i][0] = pw;
+#pragma unroll
+      for (int j = 1; j < kVec; ++j) g[i][j] = v[j - 1];
+    } else {  // source x + 1
+      float nv = __shfl_down_sync(0xffffffffu, v[0], 1);
+      if (lane == 31) nv = (x0 + kSeg < nx) ? __ldg(b + i * P + row + x0 + kSeg) : 0.0f;
+#pragma unroll
+      for (int j = 0; j < kVec - 1; ++j) g[i][j] = v[j + 1];
+      g[i][kVec - 1] = nv;
+      if (active && jw >= 0 && jw < kVec) {
+        const float wrap = periodic ? __ldg(b + i * P + row) : 0.0f;
+#pragma unroll
+        for (int j = 0; j < kVec; ++j)
+          if (j == jw) g[i][j] = wrap;
+      }
+    }
+  }
+  // ---- halfway bounce-back where the source cell is solid
+#pragma unroll
+  for (int i = 1; i < kQ; ++i) {
+    const int r = cy_of(i) > 0 ? 0 : (cy_of(i) == 0 ? 1 : 2);
+    const uint32_t bb = ((win[r] >> (1 - cx_of(i))) & ((1u << kVec) - 1u)) & ~own_solid;
+    if (active && bb) {
+      float o[kVec];
+      V::load(b + opp_of(i) * P + rowY + x, o);
+#pragma unroll
+      for (int j = 0; j < kVec; ++j)
+        if (bb & (1u << j)) g[i][j] = o[j];
+    }
+  }
+  if (!active) return;
+  // ---- per cell: Zou-He completion, moments, collision
+#pragma unroll
+  for (int j = 0; j < kVec; ++j) {
+    float c[kQ];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) c[i] = g[i][j];
+    if (!periodic) {
+      if (x + j == 0) {
+        const float G0 = c[0] + c[2] + c[4] + 2.0f * (c[3] + c[6] + c[7]);
+        const float ru = (G.bc_west == LBM_BC_PRESSURE)
+                             ? G.west_d - G0
+                             : (1.0f + G0) / (1.0f - G.west_d) * G.west_d;
+        const float t = 0.5f * (c[2] - c[4]);
+        c[1] = c[3] + (2.0f / 3.0f) * ru;
+        c[5] = c[7] - t + (1.0f / 6.0f) * ru;
+        c[8] = c[6] + t + (1.0f / 6.0f) * ru;
+      }
+      if (x + j == nx - 1) {
+        const float G0 = c[0] + c[2] + c[4] + 2.0f * (c[1] + c[5] + c[8]);
+        const float ru = (G.bc_east == LBM_BC_PRESSURE)
+                             ? G0 - G.east_d
+                             : (1.0f + G0) / (1.0f + G.east_d) * G.east_d;
+        const float t = 0.5f * (c[2] - c[4]);
+        c[3] = c[1] - (2.0f / 3.0f) * ru;
+        c[7] = c[5] + t - (1.0f / 6.0f) * ru;
+        c[6] = c[8] - t - (1.0f / 6.0f) * ru;
+      }
+    }
+    collide(G, c);
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) g[i][j] = c[i];
+  }
+  // ---- store the post-collision populations of this lane's cells
+  float* o = dst + G.f_off + rowY + x;
+  const bool full = (own_solid == 0) && (x + kVec <= nx);
+  if (full) {
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) V::store(o + i * P, g[i]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < kVec; ++j) {
+      if (x + j < nx && !((own_solid >> j) & 1u)) {
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) o[i * P + j] = g[i][j];
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_export(const GridDev* __restrict__ grids, int ngrids,
+                                                   const uint32_t* __restrict__ mask,
+                                                   const float* __restrict__ src,
+                                                   float* __restrict__ out) {
+  int gidx, x, y;
+  if (!cell_of_thread(grids, ngrids, gidx, x, y)) return;
+  const GridDev& G = grids[gidx];
+  float g[kQ];
+  if (!pull_cell(G, mask, src, x, y, g)) {
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) g[i] = 0.0f;
+  }
+  const long long cells = (long long)G.nx * G.ny;
+  float* o = out + 9 * G.cell_off + (long long)y * G.nx + x;
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) o[i * cells] = g[i];
+}
+
+// copy canonical <-> pitched state (dir 0: canonical -> state, 1: state -> canonical)
+__global__ void __launch_bounds__(kBlock) k_copy_state(const GridDev* __restrict__ grids,
+                                                       int ngrids, float* state,
+                                                       float* canon, int dir) {
+  int gidx, x, y;
+  if (!cell_of_thread(grids, ngrids, gidx, x, y)) return;
+  const GridDev& G = grids[gidx];
+  const long long cells = (long long)G.nx * G.ny;
+  float* s = state + G.f_off + (long long)y * G.pitch + x;
+  float* c = canon + 9 * G.cell_off + (long long)y * G.nx + x;
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    if (dir == 0)
+      s[i * G.plane] = c[i * cells];
+    else
+      c[i * cells] = s[i * G.plane];
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_macro(const GridDev* __restrict__ grids, int ngrids,
+                                                  const uint32_t* __restrict__ mask,
+                                                  const float* __restrict__ src, float* rho_o,
+                                                  float* ux_o, float* uy_o) {
+  int gidx, x, y;
+  if (!cell_of_thread(grids, ngrids, gidx, x, y)) return;
+  const GridDev& G = grids[gidx];
+  float g[kQ];
+  float rho = 1.0f, ux = 0.0f, uy = 0.0f, drho;
+  if (pull_cell(G, mask, src, x, y, g)) moments(G, g, drho, rho, ux, uy);
+  const long long c = G.cell_off + (long long)y * G.nx + x;
+  if (rho_o) rho_o[c] = rho;
+  if (ux_o) ux_o[c] = ux;
+  if (uy_o) uy_o[c] = uy;
+}
+
+// Deterministic FP64 block reduction of R_COUNT values; thread 0 writes the result.
+__device__ __forceinline__ void block_reduce_store(double v[R_COUNT], double* out) {
+  __shared__ double red[kBlock / 32][R_COUNT];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < R_COUNT; ++k) {
+    double a = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if (lane == 0) red[warp][k] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < R_COUNT) {
+    double a = 0.0;
+    for (int w = 0; w < kBlock / 32; ++w) a += red[w][threadIdx.x];
+    out[threadIdx.x] = a;
+  }
+}
+
+// Macroscopic fields + steady-state statistics of the current time level.
+__global__ void __launch_bounds__(kBlock) k_residual(const GridDev* __restrict__ grids,
+                                                     int ngrids,
+                                                     const uint32_t* __restrict__ mask,
+                                                     const float* __restrict__ src,
+                                                     float* ux_prev, float* uy_prev,
+                                                     int update_prev, float u_max2,
+                                                     double* __restrict__ partial) {
+  double v[R_COUNT];
+#pragma unroll
+  for (int k = 0; k < R_COUNT; ++k) v[k] = 0.0;
+  const int gidx = grid_of_block(grids, ngrids, blockIdx.x);
+  const GridDev& G = grids[gidx];
+  const int p = (blockIdx.x - G.blk_start) * kBlock + threadIdx.x;
+  const int y = p / G.pitch, x = p - y * G.pitch;
+  if (y < G.ny && x < G.nx) {
+    float g[kQ];
+    if (pull_cell(G, mask, src, x, y, g)) {
+      float drho, rho, ux, uy;
+      moments(G, g, drho, rho, ux, uy);
+      const long long c = G.cell_off + (long long)y * G.nx + x;
+      const float pux = ux_prev[c], puy = uy_prev[c];
+      if (update_prev) {
+        ux_prev[c] = ux;
+        uy_prev[c] = uy;
+      }
+      const double dux = (double)ux - (double)pux, duy = (double)uy - (double)puy;
+      v[R_DU2] = dux * dux + duy * duy;
+      const float u2 = ux * ux + uy * uy;
+      v[R_U2] = (double)ux * ux + (double)uy * uy;
+      if (!G.periodic_x && x == 0) {
+        v[R_RHO_W] = drho;
+        v[R_N_W] = 1.0;
+      }
+      if (!G.periodic_x && x == G.nx - 1) {
+        v[R_RHO_E] = drho;
+        v[R_N_E] = 1.0;
+      }
+      v[R_DRHO] = drho;
+      v[R_MOMX] = (double)rho * ux;
+      v[R_MOMY] = (double)rho * uy;
+      v[R_BAD] = (!isfinite(drho) || !isfinite(u2) || u2 > u_max2) ? 1.0 : 0.0;
+      v[R_FLUID] = 1.0;
+    }
+  }
+  block_reduce_store(v, partial + (size_t)blockIdx.x * R_COUNT);
+}
+
+__global__ void __launch_bounds__(kBlock) k_residual_final(const GridDev* __restrict__ grids,
+                                                           const double* __restrict__ partial,
+                                                           double* __restrict__ stats) {
+  const GridDev& G = grids[blockIdx.x];
+  double v[R_COUNT];
+#pragma unroll
+  for (int k = 0; k < R_COUNT; ++k) v[k] = 0.0;
+  for (int b = threadIdx.x; b < G.nblk; b += kBlock) {
+    const double* s = partial + (size_t)(G.blk_start + b) * R_COUNT;
+#pragma unroll
+    for (int k = 0; k < R_COUNT; ++k) v[k] += s[k];
+  }
+  block_reduce_store(v, stats + (size_t)blockIdx.x * R_COUNT);
+}
+
+// Re-initialisation: f = f^eq(rho, u) (+ f^neq), written *inverse-streamed*
+// into the post-collision buffer so that the next pull reproduces it.
+__device__ __forceinline__ float dfield(const GridDev& G, const uint32_t* __restrict__ m,
+                                        const float* __restrict__ v, int x, int y, int axis) {
+  int xp = x, xm = x, yp = y, ym = y;
+  bool okp = true, okm = true;
+  if (axis == 0) {
+    xp = x + 1;
+    xm = x - 1;
+    if (G.periodic_x) {
+      if (xp >= G.nx) xp = 0;
+      if (xm < 0) xm = G.nx - 1;
+    } else {
+      okp = xp < G.nx;
+      okm = xm >= 0;
+    }
+  } else {
+    yp = (y == G.ny - 1) ? 0 : y + 1;
+    ym = (y == 0) ? G.ny - 1 : y - 1;
+  }
+  if (okp && mask_bit(m, G.wpr, xp, yp)) okp = false;
+  if (okm && mask_bit(m, G.wpr, xm, ym)) okm = false;
+  const float vc = v[(long long)y * G.nx + x];
+  if (okp && okm) return 0.5f * (v[(long long)yp * G.nx + xp] - v[(long long)ym * G.nx + xm]);
+  if (okp) return v[(long long)yp * G.nx + xp] - vc;
+  if (okm) return vc - v[(long long)ym * G.nx + xm];
+  return 0.0f;
+}
+
+__global__ void __launch_bounds__(kBlock) k_reinit(const GridDev* __restrict__ grids, int ngrids,
+                                                   const uint32_t* __restrict__ mask,
+                                                   const float* __restrict__ rho_i,
+                                                   const float* __restrict__ ux_i,
+                                                   const float* __restrict__ uy_i, int neq_mode,
+                                                   float* __restrict__ state, float* ux_prev,
+                                                   float* uy_prev) {
+  int gidx, x, y;
+  if (!cell_of_thread(grids, ngrids, gidx, x, y)) return;
+  const GridDev& G = grids[gidx];
+  const uint32_t* m = mask + G.mask_off;
+  const long long c = (long long)y * G.nx + x;
+  const float* R = rho_i + G.cell_off;
+  const float* UX = ux_i + G.cell_off;
+  const float* UY = uy_i + G.cell_off;
+  const bool solid = mask_bit(m, G.wpr, x, y);
+  ux_prev[G.cell_off + c] = solid ? 0.0f : UX[c];
+  uy_prev[G.cell_off + c] = solid ? 0.0f : UY[c];
+  if (solid) return;
+  const float rho = R[c], ux = UX[c], uy = UY[c];
+  const float drho = rho - 1.0f;
+  float dxux = 0.f, dxuy = 0.f, dyux = 0.f, dyuy = 0.f;
+  if (neq_mode) {
+    dxux = dfield(G, m, UX, x, y, 0);
+    dxuy = dfield(G, m, UY, x, y, 0);
+    dyux = dfield(G, m, UX, x, y, 1);
+    dyuy = dfield(G, m, UY, x, y, 1);
+  }
+  const float usq = 1.5f * (ux * ux + uy * uy);
+  const float div = dxux + dyuy;
+  const float kneq = -3.0f * G.tau * rho;  // -(tau rho / c_s^2)
+  float* b = state + G.f_off;
+  const int ym = (y == 0) ? G.ny - 1 : y - 1;
+  const int yp = (y == G.ny - 1) ? 0 : y + 1;
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    const int cx = cx_of(i), cy = cy_of(i);
+    const float cu = cx * ux + cy * uy;
+    // Q_iab d_a u_b = c_ia c_ib d_a u_b - c_s^2 div u
+    const float qd = (float)(cx * cx) * dxux + (float)(cx * cy) * (dxuy + dyux) +
+                     (float)(cy * cy) * dyuy - (1.0f / 3.0f) * div;
+    const float gi = w_of(i) * (drho + rho * (3.0f * cu + 4.5f * cu * cu - usq)) +
+                     w_of(i) * kneq * qd;
+    // pull source of population i at (x, y) is (x - c_i, y - c_i)
+    int xs = x - cx;
+    const int ys = cy == 0 ? y : (cy > 0 ? ym : yp);
+    bool out = false;
+    if (xs < 0 || xs >= G.nx) {
+      if (G.periodic_x)
+        xs = xs < 0 ? G.nx - 1 : 0;
+      else
+        out = true;
+    }
+    if (out) continue;  // a Zou-He unknown: completed at the next pull
+    if (mask_bit(m, G.wpr, xs, ys))
+      b[(long long)opp_of(i) * G.plane + (long long)y * G.pitch + x] = gi;
+    else
+      b[(long long)i * G.plane + (long long)ys * G.pitch + xs] = gi;
+  }
+}
+
+// ------------------------------------------------------------ host side ---
+struct Handle {
+  std::vector<lbm_grid> grids;
+  std::vector<GridDev> gd;
+  GridDev* gd_d = nullptr;  // in the caller's workspace
+  int ngrids = 0;
+  int nblk_total = 0;
+  int nsblk_total = 0;
+  const uint32_t* mask = nullptr;
+  float* f[2] = {nullptr, nullptr};
+  int cur = 0;  // buffer holding the current state
+  float* ux_prev = nullptr;
+  float* uy_prev = nullptr;
+  double* partial = nullptr;
+  double* stats_d = nullptr;
+  std::vector<double> stats_h;
+  lbm_layout layout{};
+  float u_max2 = 0.04f;
+  long long steps = 0;
+};
+
+struct WsPlan {
+  size_t grids_off, uprev_off, partial_off, stats_off, total;
+};
+
+static int plan_layout(const lbm_grid* grids, int ngrids, lbm_layout* lay,
+                       std::vector<GridDev>* gd, WsPlan* wp) {
+  LBM_REQUIRE(grids != nullptr && ngrids > 0, "lbm: need at least one grid");
+  size_t f = 0, words = 0, cells = 0;
+  long long blk = 0, sblk = 0;
+  if (gd) gd->clear();
+  for (int k = 0; k < ngrids; ++k) {
+    const lbm_grid& g = grids[k];
+    LBM_REQUIRE(g.nx >= 2 && g.ny >= 2 && g.nx <= (1 << 20) && g.ny <= (1 << 20),
+                "lbm: grid %d has invalid size %d x %d", k, g.nx, g.ny);
+    LBM_REQUIRE(g.tau > 0.5 && g.tau < 100.0, "lbm: grid %d tau %g not in (0.5, 100)", k,
+                g.tau);
+    const bool pw = g.bc_west == LBM_BC_PERIODIC, pe = g.bc_east == LBM_BC_PERIODIC;
+    LBM_REQUIRE(pw == pe, "lbm: grid %d: periodic x needs both ends periodic", k);
+    LBM_REQUIRE(g.bc_west >= 0 && g.bc_west <= 2 && g.bc_east >= 0 && g.bc_east <= 2,
+                "lbm: grid %d: unknown boundary kind", k);
+    if (g.bc_west == LBM_BC_VELOCITY)
+      LBM_REQUIRE(fabs(g.west_value) < 0.5, "lbm: grid %d: |inlet velocity| >= 0.5", k);
+    if (g.bc_east == LBM_BC_VELOCITY)
+      LBM_REQUIRE(fabs(g.east_value) < 0.5, "lbm: grid %d: |outlet velocity| >= 0.5", k);
+    if (g.bc_west == LBM_BC_PRESSURE)
+      LBM_REQUIRE(g.west_value > 0.5 && g.west_value < 2.0, "lbm: grid %d: inlet rho", k);
+    if (g.bc_east == LBM_BC_PRESSURE)
+      LBM_REQUIRE(g.east_value > 0.5 && g.east_value < 2.0, "lbm: grid %d: outlet rho", k);
+    GridDev d{};
+    d.nx = g.nx;
+    d.ny = g.ny;
+    d.pitch = (int)align_up((size_t)g.nx, 32);
+    d.wpr = (g.nx + 31) / 32;
+    d.f_off = (long long)f;
+    d.plane = (long long)g.ny * d.pitch;
+    d.mask_off = (long long)words;
+    d.cell_off = (long long)cells;
+    d.nblk = (int)((d.plane + kBlock - 1) / kBlock);
+    d.blk_start = (int)blk;
+    d.nseg = (g.nx + kSeg - 1) / kSeg;
+    d.nsblk = (int)(((long long)d.nseg * g.ny + kStepWarps - 1) / kStepWarps);
+    d.sblk_start = (int)sblk;
+    d.tau = (float)g.tau;
+    d.omega = (float)(1.0 / g.tau);
+    d.guo = (float)(1.0 - 0.5 / g.tau);
+    d.fx = (float)g.fx;
+    d.fy = (float)g.fy;
+    d.periodic_x = pw ? 1 : 0;
+    d.bc_west = g.bc_west;
+    d.bc_east = g.bc_east;
+    d.west_d = (float)(g.bc_west == LBM_BC_PRESSURE ? g.west_value - 1.0 : g.west_value);
+    d.east_d = (float)(g.bc_east == LBM_BC_PRESSURE ? g.east_value - 1.0 : g.east_value);
+    LBM_REQUIRE((size_t)kQ * d.plane < (1ull << 31),
+                "lbm: grid %d too large for one batch entry (9*ny*pitch >= 2^31)", k);
+    f += (size_t)kQ * d.plane;
+    words += (size_t)d.wpr * g.ny;
+    cells += (size_t)g.nx * g.ny;
+    blk += d.nblk;
+    sblk += d.nsblk;
+    LBM_REQUIRE(blk < (1LL << 30) && sblk < (1LL << 30), "lbm: batch too large");
+    if (gd) gd->push_back(d);
+  }
+  WsPlan w{};
+  w.grids_off = 0;
+  w.uprev_off = align_up(sizeof(GridDev) * ngrids, 256);
+  w.partial_off = align_up(w.uprev_off + 2 * cells * sizeof(float), 256);
+  w.stats_off = align_up(w.partial_off + (size_t)blk * R_COUNT * sizeof(double), 256);
+  w.total = align_up(w.stats_off + (size_t)ngrids * R_COUNT * sizeof(double), 256);
+  lay->f_elems = f;
+  lay->mask_words = words;
+  lay->cells = cells;
+  lay->ws_bytes = w.total;
+  if (wp) *wp = w;
+  return LBM_OK;
+}
+
+static inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace lbmfno
+
+using namespace lbmfno;
+
+struct lbm_handle : Handle {};
+
+extern "C" {
+
+const char* lbm_last_error(void) { return lbmfno::g_err; }
+
+int lbm_query_layout(const lbm_grid* grids_h, int ngrids, lbm_layout* out_h) {
+  LBM_REQUIRE(out_h != nullptr, "lbm_query_layout: null output");
+  return plan_layout(grids_h, ngrids, out_h, nullptr, nullptr);
+}
+
+int lbm_init(const lbm_grid* grids_h, int ngrids, const uint32_t* mask_d, float* f_a_d,
+             float* f_b_d, void* ws_d, double u_max, void* stream, lbm_handle** out) {
+  LBM_REQUIRE(out != nullptr, "lbm_init: null handle output");
+  *out = nullptr;
+  LBM_REQUIRE(mask_d && f_a_d && f_b_d && ws_d, "lbm_init: null device pointer");
+  LBM_REQUIRE(((uintptr_t)f_a_d % 16) == 0 && ((uintptr_t)f_b_d % 16) == 0 &&
+                  ((uintptr_t)ws_d % 256) == 0,
+              "lbm_init: f buffers need 16-byte and workspace 256-byte alignment");
+  LBM_REQUIRE(u_max > 0.0 && u_max < 1.0, "lbm_init: u_max must be in (0, 1)");
+  lbm_handle* h = new lbm_handle();
+  WsPlan wp;
+  int st = plan_layout(grids_h, ngrids, &h->layout, &h->gd, &wp);
+  if (st != LBM_OK) {
+    delete h;
+    return st;
+  }
+  h->grids.assign(grids_h, grids_h + ngrids);
+  h->ngrids = ngrids;
+  h->nblk_total = h->gd.back().blk_start + h->gd.back().nblk;
+  h->nsblk_total = h->gd.back().sblk_start + h->gd.back().nsblk;
+  h->mask = mask_d;
+  h->f[0] = f_a_d;
+  h->f[1] = f_b_d;
+  char* ws = static_cast<char*>(ws_d);
+  h->gd_d = reinterpret_cast<GridDev*>(ws + wp.grids_off);
+  h->ux_prev = reinterpret_cast<float*>(ws + wp.uprev_off);
+  h->uy_prev = h->ux_prev + h->layout.cells;
+  h->partial = reinterpret_cast<double*>(ws + wp.partial_off);
+  h->stats_d = reinterpret_cast<double*>(ws + wp.stats_off);
+  h->stats_h.assign((size_t)ngrids * R_COUNT, 0.0);
+  h->u_max2 = (float)(u_max * u_max);
+  cudaStream_t s = S(stream);
+  auto fail = [&](int code) {
+    delete h;
+    return code;
+  };
+  if (cudaMemcpyAsync(h->gd_d, h->gd.data(), sizeof(GridDev) * ngrids, cudaMemcpyHostToDevice,
+                      s) != cudaSuccess ||
+      cudaMemsetAsync(f_a_d, 0, h->layout.f_elems * sizeof(float), s) != cudaSuccess ||
+      cudaMemsetAsync(f_b_d, 0, h->layout.f_elems * sizeof(float), s) != cudaSuccess ||
+      cudaMemsetAsync(h->ux_prev, 0, 2 * h->layout.cells * sizeof(float), s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    set_error("lbm_init: %s", cudaGetErrorString(cudaGetLastError()));
+    return fail(LBM_ERR_CUDA);
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+int lbm_step(lbm_handle* h, int nsteps, void* stream) {
+  LBM_REQUIRE(h != nullptr && nsteps >= 0, "lbm_step: bad arguments");
+  cudaStream_t s = S(stream);
+  for (int k = 0; k < nsteps; ++k) {
+    k_step<<<h->nsblk_total, kStepWarps * 32, 0, s>>>(h->gd_d, h->ngrids, h->mask,
+                                                      h->f[h->cur], h->f[h->cur ^ 1]);
+    LBM_CHECK_LAUNCH();
+    h->cur ^= 1;
+  }
+  h->steps += nsteps;
+  return LBM_OK;
+}
+
+int lbm_macro(lbm_handle* h, float* rho_d, float* ux_d, float* uy_d, void* stream) {
+  LBM_REQUIRE(h != nullptr, "lbm_macro: null handle");
+  k_macro<<<h->nblk_total, kBlock, 0, S(stream)>>>(h->gd_d, h->ngrids, h->mask, h->f[h->cur],
+                                                   rho_d, ux_d, uy_d);
+  LBM_CHECK_LAUNCH();
+  return LBM_OK;
+}
+
+int lbm_residual(lbm_handle* h, double* out_h, int update_prev, void* stream) {
+  LBM_REQUIRE(h != nullptr && out_h != nullptr, "lbm_residual: bad arguments");
+  cudaStream_t s = S(stream);
+  k_residual<<<h->nblk_total, kBlock, 0, s>>>(h->gd_d, h->ngrids, h->mask, h->f[h->cur],
+                                              h->ux_prev, h->uy_prev, update_prev, h->u_max2,
+                                              h->partial);
+  LBM_CHECK_LAUNCH();
+  k_residual_final<<<h->ngrids, kBlock, 0, s>>>(h->gd_d, h->partial, h->stats_d);
+  LBM_CHECK_LAUNCH();
+  LBM_CHECK_CUDA(cudaMemcpyAsync(h->stats_h.data(), h->stats_d,
+                                 sizeof(double) * R_COUNT * h->ngrids, cudaMemcpyDeviceToHost,
+                                 s));
+  LBM_CHECK_CUDA(cudaStreamSynchronize(s));
+  bool bad = false;
+  for (int g = 0; g < h->ngrids; ++g) {
+    const double* r = &h->stats_h[(size_t)g * R_COUNT];
+    double* o = out_h + (size_t)g * LBM_NSTAT;
+    o[LBM_STAT_RESIDUAL] = r[R_U2] > 0 ? sqrt(r[R_DU2] / r[R_U2]) : INFINITY;
+    o[LBM_STAT_UNORM] = sqrt(r[R_U2]);
+    const double rw = r[R_N_W] > 0 ? r[R_RHO_W] / r[R_N_W] : 0.0;
+    const double re = r[R_N_E] > 0 ? r[R_RHO_E] / r[R_N_E] : 0.0;
+    o[LBM_STAT_DP] = (rw - re) / 3.0;
+    o[LBM_STAT_MASS] = r[R_FLUID] + r[R_DRHO];
+    o[LBM_STAT_MOMX] = r[R_MOMX];
+    o[LBM_STAT_MOMY] = r[R_MOMY];
+    o[LBM_STAT_BAD] = r[R_BAD];
+    o[LBM_STAT_FLUID] = r[R_FLUID];
+    if (r[R_BAD] > 0 || !std::isfinite(r[R_DU2]) || !std::isfinite(r[R_U2])) bad = true;
+  }
+  if (bad) {
+    set_error("lbm_residual: non-finite values or |u| > u_max detected");
+    return LBM_ERR_UNSTABLE;
+  }
+  return LBM_OK;
+}
+
+int lbm_reinit_from_macro(lbm_handle* h, const float* rho_d, const float* ux_d,
+                          const float* uy_d, int neq_mode, void* stream) {
+  LBM_REQUIRE(h != nullptr && rho_d && ux_d && uy_d, "lbm_reinit_from_macro: bad arguments");
+  k_reinit<<<h->nblk_total, kBlock, 0, S(stream)>>>(h->gd_d, h->ngrids, h->mask, rho_d, ux_d,
+                                                    uy_d, neq_mode, h->f[h->cur], h->ux_prev,
+                                                    h->uy_prev);
+  LBM_CHECK_LAUNCH();
+  h->steps = 0;
+  return LBM_OK;
+}
+
+int lbm_export_f(lbm_handle* h, float* g_d, void* stream) {
+  LBM_REQUIRE(h != nullptr && g_d != nullptr, "lbm_export_f: bad arguments");
+  k_export<<<h->nblk_total, kBlock, 0, S(stream)>>>(h->gd_d, h->ngrids, h->mask, h->f[h->cur],
+                                                    g_d);
+  LBM_CHECK_LAUNCH();
+  return LBM_OK;
+}
+
+int lbm_set_state(lbm_handle* h, const float* gstar_d, void* stream) {
+  LBM_REQUIRE(h != nullptr && gstar_d != nullptr, "lbm_set_state: bad arguments");
+  k_copy_state<<<h->nblk_total, kBlock, 0, S(stream)>>>(h->gd_d, h->ngrids, h->f[h->cur],
+                                                        const_cast<float*>(gstar_d), 0);
+  LBM_CHECK_LAUNCH();
+  return LBM_OK;
+}
+
+int lbm_get_state(lbm_handle* h, float* gstar_d, void* stream) {
+  LBM_REQUIRE(h != nullptr && gstar_d != nullptr, "lbm_get_state: bad arguments");
+  k_copy_state<<<h->nblk_total, kBlock, 0, S(stream)>>>(h->gd_d, h->ngrids, h->f[h->cur],
+                                                        gstar_d, 1);
+  LBM_CHECK_LAUNCH();
+  return LBM_OK;
+}
+
+int lbm_steps_done(const lbm_handle* h, long long* out_h) {
+  LBM_REQUIRE(h != nullptr && out_h != nullptr, "lbm_steps_done: bad arguments");
+  *out_h = h->steps;
+  return LBM_OK;
+}
+
+int lbm_destroy(lbm_handle* h) {
+  delete h;
+  return LBM_OK;
+}
+
+}  // extern "C"

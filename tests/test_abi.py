@@ -1,0 +1,60 @@
+"""CPU-side checks of the C ABI: the library builds, loads, exports every declared
+symbol, and validates arguments on the host (no GPU work is issued)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import paper_2604_27158_gb300 as P
+from paper_2604_27158_gb300 import _abi
+from paper_2604_27158_gb300.lbm import GridSpec, query_layout
+
+
+def test_library_exports_every_declared_symbol():
+    lib = P.lib()
+    names = _abi.declared_symbols()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_query_layout_sizes():
+    grids = [GridSpec(128, 64, 0.8), GridSpec(37, 20, 0.6, bc_west=P.BC_PRESSURE,
+                                                bc_east=P.BC_PRESSURE, west_value=1.001)]
+    lay = query_layout(grids)
+    assert lay.cells == 128 * 64 + 37 * 20
+    assert lay.f_elems == 9 * (64 * 128 + 20 * 64)       # pitch = nx rounded up to 32
+    assert lay.mask_words == 64 * 4 + 20 * 2
+    assert lay.ws_bytes > 0 and lay.ws_bytes % 256 == 0
+
+
+@pytest.mark.parametrize("bad", [
+    GridSpec(1, 8, 0.8),                                   # too small
+    GridSpec(8, 8, 0.5),                                   # tau must exceed 1/2
+    GridSpec(8, 8, 0.8, bc_west=P.BC_PRESSURE),            # periodic on one end only
+    GridSpec(8, 8, 0.8, bc_west=P.BC_VELOCITY, bc_east=P.BC_PRESSURE, west_value=0.7),
+    GridSpec(8, 8, 0.8, bc_west=7, bc_east=7),
+])
+def test_query_layout_rejects_invalid_grids(bad):
+    with pytest.raises(P.LbmError) as e:
+        query_layout([bad])
+    assert e.value.code == _abi.LBM_ERR_INVALID_ARG
+    assert "lbm" in str(e.value)
+
+
+def test_null_arguments_rejected_without_gpu():
+    lib = P.lib()
+    assert lib.lbm_query_layout(None, 0, None) == _abi.LBM_ERR_INVALID_ARG
+    h = ctypes.c_void_p()
+    assert lib.lbm_init(None, 0, None, None, None, None, 0.2, None, ctypes.byref(h)) == _abi.LBM_ERR_INVALID_ARG
+    assert lib.lbm_step(None, 1, None) == _abi.LBM_ERR_INVALID_ARG
+    assert h.value is None
+
+
+def test_mask_packing_layout():
+    solid = np.zeros((3, 40), bool)
+    solid[1, 33] = True
+    solid[2, 0] = True
+    w = P.pack_mask(solid)
+    assert w.shape == (6,)
+    assert w[1 * 2 + 1] == (1 << 1) and w[2 * 2] == 1 and w.sum() == 3
