@@ -82,8 +82,8 @@ struct GridDev {
   int blk_start;       // first block of the grid in flat 256-cell block launches
   int nblk;            // blocks of the grid
   int nseg;            // 128-cell row segments per row (step kernel)
-  int sblk_start;      // first block of the grid in step-kernel launches
-  int nsblk;           // step-kernel blocks of the grid (8 row segments each)
+  int tile_start;      // first tile of the grid in the step kernel
+  int ntiles;          // step-kernel tiles of the grid
   float omega;         // 1 / tau
   float tau;
   float guo;           // 1 - 1/(2 tau)

@@ -23,6 +23,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "common.cuh"
@@ -154,17 +156,47 @@ __device__ __forceinline__ void collide_pair(float& gi, float& go, float w, floa
   go = go + om * (even - odd - go) + (s_even - s_odd);
 }
 
+// Unforced pair update (no source term).
+__device__ __forceinline__ void relax_pair(float& gi, float& go, float wr3, float wcu, float cu,
+                                           float base, float rho, float om) {
+  // even part w (drho + rho (4.5 cu^2 - 1.5 u^2)) = w drho - w rho usq + 4.5 w rho cu^2
+  const float even = fmaf(4.5f * wcu * cu, cu, base);
+  const float odd = wr3 * cu;
+  gi = fmaf(om, (even + odd) - gi, gi);
+  go = fmaf(om, (even - odd) - go, go);
+}
+
+// One BGK collision of a cell's nine shifted populations (Sec. 2.1), with the Guo
+// source when the grid carries a body force.
 __device__ __forceinline__ void collide(const GridDev& G, float g[kQ]) {
-  float drho, rho, ux, uy;
-  moments(G, g, drho, rho, ux, uy);
-  const float usq = 1.5f * (ux * ux + uy * uy);
-  const float om = G.omega, guo = G.guo, fx = G.fx, fy = G.fy;
-  const float sym_f = -3.0f * (ux * fx + uy * fy);
-  g[0] = g[0] + om * (kW0 * (drho - rho * usq) - g[0]) + guo * kW0 * sym_f;
-  collide_pair(g[1], g[3], kW1, ux, fx, drho, rho, usq, om, sym_f, guo);
-  collide_pair(g[2], g[4], kW1, uy, fy, drho, rho, usq, om, sym_f, guo);
-  collide_pair(g[5], g[7], kW2, ux + uy, fx + fy, drho, rho, usq, om, sym_f, guo);
-  collide_pair(g[6], g[8], kW2, uy - ux, fy - fx, drho, rho, usq, om, sym_f, guo);
+  if (G.fx != 0.0f || G.fy != 0.0f) {
+    float drho, rho, ux, uy;
+    moments(G, g, drho, rho, ux, uy);
+    const float usq = 1.5f * (ux * ux + uy * uy);
+    const float om = G.omega, guo = G.guo, fx = G.fx, fy = G.fy;
+    const float sym_f = -3.0f * (ux * fx + uy * fy);
+    g[0] = g[0] + om * (kW0 * (drho - rho * usq) - g[0]) + guo * kW0 * sym_f;
+    collide_pair(g[1], g[3], kW1, ux, fx, drho, rho, usq, om, sym_f, guo);
+    collide_pair(g[2], g[4], kW1, uy, fy, drho, rho, usq, om, sym_f, guo);
+    collide_pair(g[5], g[7], kW2, ux + uy, fx + fy, drho, rho, usq, om, sym_f, guo);
+    collide_pair(g[6], g[8], kW2, uy - ux, fy - fx, drho, rho, usq, om, sym_f, guo);
+    return;
+  }
+  const float drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+  const float rho = 1.0f + drho;
+  const float jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
+  const float jy = (g[2] - g[4]) + (g[5] - g[8]) + (g[6] - g[7]);
+  const float inv = __frcp_rn(rho);
+  const float ux = jx * inv, uy = jy * inv;
+  const float om = G.omega;
+  const float rusq = rho * 1.5f * fmaf(ux, ux, uy * uy);   // rho * 1.5 u^2
+  const float e1 = kW1 * (drho - rusq), e2 = kW2 * (drho - rusq);
+  const float r1 = kW1 * rho, r2 = kW2 * rho;
+  g[0] = fmaf(om, kW0 * (drho - rusq) - g[0], g[0]);
+  relax_pair(g[1], g[3], 3.0f * r1, r1, ux, e1, rho, om);
+  relax_pair(g[2], g[4], 3.0f * r1, r1, uy, e1, rho, om);
+  relax_pair(g[5], g[7], 3.0f * r2, r2, ux + uy, e2, rho, om);
+  relax_pair(g[6], g[8], 3.0f * r2, r2, uy - ux, e2, rho, om);
 }
 
 __device__ __forceinline__ bool cell_of_thread(const GridDev* __restrict__ grids, int ngrids,
@@ -186,205 +218,320 @@ __device__ __forceinline__ bool cell_of_thread(const GridDev* __restrict__ grids
 // from 18 mask words loaded once per warp and funnel-shifted per lane.  Results
 // are stored as aligned float4 (per-cell stores where a lane has solid or
 // out-of-range cells).
-#ifndef LBM_STEP_VEC
-#define LBM_STEP_VEC 4  // cells per lane (2 or 4)
-#endif
-#ifndef LBM_STEP_MINB
-#define LBM_STEP_MINB 2  // minimum resident blocks per SM requested from ptxas
-#endif
-constexpr int kVec = LBM_STEP_VEC;
+// ------------------------------------------------------ the fused step ---
+// One time step of every grid of the batch in one launch: pull streaming with
+// halfway bounce-back, Zou-He completion, moments, BGK collision (Sec. 2.1).
+//
+// Work decomposition: tiles of kTY rows x 128 cells.  A persistent grid of CTAs
+// (several per SM) walks the tiles.  Each CTA has one producer warp and kTY
+// consumer warps sharing a kStages-deep ring of shared-memory stages:
+//  * the producer issues one cp.async.bulk per (population i, tile row r): the
+//    row segment x0-4 .. x0+131 of population i's *source* row y0 + r - c_iy.
+//    Because every population is fetched at its own source row, a tile needs
+//    no y-halo and every source row is read once.  It also stages the tile's
+//    metadata (the grid descriptor) and the packed mask words of rows
+//    y0-1 .. y0+kTY, then arrives on the stage's mbarrier;
+//  * consumer warp w owns tile row y0 + w; lane l owns cells x0+4l .. x0+4l+3.
+//    The nine pulled values are aligned 16-byte shared loads (the +-1 x-shift is
+//    a neighbouring 16-byte chunk), bounce-back takes the own cell's opposite
+//    population from the stage, Zou-He completes open ends, and the collision
+//    result is stored as float4 rows straight to global memory (solid cells
+//    store 0, so every 32-byte sector is written whole).
+// DRAM traffic: 36 B read + 36 B written per cell; the 8-float x-halo only costs
+// shared-memory bandwidth.  Every mbarrier wait is bounded: on expiry the kernel
+// records LBM_ERR_TIMEOUT in `status` and stops.
+constexpr int kVec = 4;
 constexpr int kSeg = 32 * kVec;
-constexpr int kStepWarps = 8;
-static_assert(kVec == 2 || kVec == 4, "LBM_STEP_VEC must be 2 or 4");
-
-template <int V>
-struct VecT;
-template <>
-struct VecT<4> {
-  using T = float4;
-  static __device__ __forceinline__ void load(const float* p, float o[4]) {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
-  }
-  static __device__ __forceinline__ void store(float* p, const float o[4]) {
-    *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
-  }
+#ifndef LBM_TMA_TY
+#define LBM_TMA_TY 4  // rows per tile = consumer warps per CTA
+#endif
+#ifndef LBM_TMA_STAGES
+#define LBM_TMA_STAGES 2  // shared-memory ring depth
+#endif
+#ifndef LBM_TMA_MINB
+#define LBM_TMA_MINB 4  // resident CTAs per SM
+#endif
+constexpr int kTY = LBM_TMA_TY;
+constexpr int kRowF = kSeg + 8;  // floats per staged row segment
+constexpr int kStages = LBM_TMA_STAGES;
+constexpr int kStageFloats = kQ * kTY * kRowF;
+constexpr int kWords = kVec + 2;               // mask words per row around a segment
+constexpr int kMaskWords = (kTY + 2) * kWords;  // rows y0-1 .. y0+kTY
+struct __align__(16) TileMeta {
+  GridDev g;
+  int x0, y0, rows, pad;
+  uint32_t mask[kMaskWords];
 };
-template <>
-struct VecT<2> {
-  static __device__ __forceinline__ void load(const float* p, float o[2]) {
-    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
-    o[0] = v.x; o[1] = v.y;
-  }
-  static __device__ __forceinline__ void store(float* p, const float o[2]) {
-    *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
-  }
-};
+constexpr size_t kTmaSmem =
+    (size_t)kStages * kStageFloats * sizeof(float) + (size_t)kStages * sizeof(TileMeta);
+constexpr long long kWaitLimit = 4000000000LL;  // ~2 s of SM clocks
+constexpr unsigned kStatusTimeout = 1u;
 
-__global__ void __launch_bounds__(kStepWarps * 32, LBM_STEP_MINB)
-    k_step(const GridDev* __restrict__ grids, int ngrids, const uint32_t* __restrict__ mask,
-           const float* __restrict__ src, float* __restrict__ dst) {
-  using V = VecT<kVec>;
-  constexpr int kWords = kVec + 2;  // mask words per row around a segment
-  const int gidx = grid_of<&GridDev::sblk_start>(grids, ngrids, blockIdx.x);
-  const GridDev& G = grids[gidx];
-  const int lane = threadIdx.x & 31;
-  const int task = (blockIdx.x - G.sblk_start) * kStepWarps + (threadIdx.x >> 5);
-  const int nx = G.nx, ny = G.ny;
-  const int y = task / G.nseg;
-  if (y >= ny) return;  // warp-uniform
-  const int x0 = (task - y * G.nseg) * kSeg;
-  const int x = x0 + kVec * lane;
-  const bool active = x < nx;
-  const bool periodic = G.periodic_x != 0;
-  const int ym = (y == 0) ? ny - 1 : y - 1;
-  const int yp = (y == ny - 1) ? 0 : y + 1;
-  const int pitch = G.pitch;
-  const unsigned P = (unsigned)G.plane;  // plane offsets fit in 32 bits (checked on the host)
-  const float* b = src + G.f_off;
-  const unsigned rowM = (unsigned)(ym * pitch), rowY = (unsigned)(y * pitch),
-                 rowP = (unsigned)(yp * pitch);
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait; returns false (and flags the status word) when the limit expires
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > kWaitLimit) {
+      atomicOr(status, kStatusTimeout);
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
 
-  // ---- solid bits: lanes 0..3*kWords-1 fetch the mask words around the segment
-  const uint32_t* m = mask + G.mask_off;
-  uint32_t word = 0;
-  if (lane < 3 * kWords) {
-    const int r = lane / kWords;
-    const int wi = (x0 >> 5) - 1 + (lane - r * kWords);
-    const int yy = r == 0 ? ym : (r == 1 ? y : yp);
-    if (wi >= 0 && wi < G.wpr) word = __ldg(&m[yy * G.wpr + wi]);
+__global__ void __launch_bounds__((kTY + 1) * 32, LBM_TMA_MINB)
+    k_step_tma(const GridDev* __restrict__ grids, int ngrids, int ntiles,
+               const uint32_t* __restrict__ mask, const float* __restrict__ src,
+               float* __restrict__ dst, unsigned* __restrict__ status) {
+  extern __shared__ __align__(128) float stage_mem[];
+  TileMeta* metas = reinterpret_cast<TileMeta*>(stage_mem + (size_t)kStages * kStageFloats);
+  __shared__ __align__(8) uint64_t full_bar[kStages];
+  __shared__ __align__(8) uint64_t empty_bar[kStages];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], kTY);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // window bit b of row r <-> cell (x - 1 + b), b = 0 .. kVec+1
-  constexpr uint32_t kWin = (1u << (kVec + 2)) - 1u;
-  const int bitpos = 31 + kVec * lane;
-  const int k0 = bitpos >> 5, sh = bitpos & 31;
-  uint32_t win[3];
-#pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    const uint32_t lo = __shfl_sync(0xffffffffu, word, r * kWords + k0);
-    const uint32_t hi = __shfl_sync(0xffffffffu, word, r * kWords + k0 + 1);
-    win[r] = __funnelshift_r(lo, hi, sh) & kWin;
-  }
-  // x-edge neighbours: the west neighbour of x = 0 and the east one of x = nx-1
-  const int jw = nx - 1 - x;  // lane-local index of the cell x = nx-1, if 0..kVec-1
-  if (active) {
-    if (x == 0) {
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        win[r] &= ~1u;
-        if (periodic) win[r] |= (uint32_t)mask_bit(m, G.wpr, nx - 1, r == 0 ? ym : (r == 1 ? y : yp));
+  __syncthreads();
+
+  if (warp == kTY) {
+    // ------------------------------------------------------------ producer
+    int k = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+      const int s = k % kStages;
+      if (k >= kStages) ok = mbar_wait(&empty_bar[s], ((k / kStages) - 1) & 1, status);
+      if (!ok) break;
+      const int gi = grid_of<&GridDev::tile_start>(grids, ngrids, t);
+      const GridDev* Gp = grids + gi;
+      const int lt = t - __ldg(&Gp->tile_start);
+      const int nseg = __ldg(&Gp->nseg), ny = __ldg(&Gp->ny), pitch = __ldg(&Gp->pitch);
+      const int yt = lt / nseg;
+      const int x0 = (lt - yt * nseg) * kSeg, y0 = yt * kTY;
+      const float* b = src + __ldg(&Gp->f_off);
+      const long long plane = __ldg(&Gp->plane);
+      const int xs = max(x0 - 4, 0);
+      const int xe = min(x0 + kSeg + 4, pitch);
+      const unsigned seg_bytes = (unsigned)(xe - xs) * 4u;
+      const int rows = min(kTY, ny - y0);
+      float* st = stage_mem + (size_t)s * kStageFloats;
+      if (lane == 0) mbar_expect_tx(&full_bar[s], seg_bytes * (unsigned)(kQ * rows));
+      __syncwarp();
+      for (int c = lane; c < kQ * kTY; c += 32) {
+        const int i = c / kTY, r = c - i * kTY;
+        if (r >= rows) continue;
+        int ys = y0 + r - cy_of(i);
+        ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
+        bulk_g2s(st + (i * kTY + r) * kRowF + (xs - (x0 - 4)),
+                 b + (size_t)i * plane + (size_t)ys * pitch + xs, seg_bytes, &full_bar[s]);
       }
-    }
-    if (jw >= 0 && jw < kVec) {
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        win[r] &= ~(1u << (jw + 2));
-        if (periodic)
-          win[r] |= (uint32_t)mask_bit(m, G.wpr, 0, r == 0 ? ym : (r == 1 ? y : yp)) << (jw + 2);
+      // tile metadata and mask words (generic-proxy stores, released by the arrive)
+      TileMeta* tm = metas + s;
+      const uint32_t* gw = reinterpret_cast<const uint32_t*>(Gp);
+      uint32_t* sw = reinterpret_cast<uint32_t*>(&tm->g);
+      for (int w = lane; w < (int)(sizeof(GridDev) / 4); w += 32) sw[w] = __ldg(gw + w);
+      const uint32_t* m = mask + __ldg(&Gp->mask_off);
+      const int wpr = __ldg(&Gp->wpr);
+      for (int w = lane; w < kMaskWords; w += 32) {
+        const int r = w / kWords;
+        int yy = y0 - 1 + r;
+        yy = yy < 0 ? yy + ny : (yy >= ny ? yy % ny : yy);
+        const int wi = (x0 >> 5) - 1 + (w - r * kWords);
+        tm->mask[w] = (wi >= 0 && wi < wpr) ? __ldg(&m[yy * wpr + wi]) : 0u;
       }
-    }
-  }
-  const uint32_t own_solid = (win[1] >> 1) & ((1u << kVec) - 1u);
-
-  // ---- pull: aligned vector loads at the source rows, shuffled by +-1 cell
-  float g[kQ][kVec];
-#pragma unroll
-  for (int i = 0; i < kQ; ++i) {
-    const unsigned row = cy_of(i) == 0 ? rowY : (cy_of(i) > 0 ? rowM : rowP);
-    float v[kVec];
-    if (active) {
-      V::load(b + i * P + row + x, v);
-    } else {
-#pragma unroll
-      for (int j = 0; j < kVec; ++j) v[j] = 0.0f;
-    }
-    if (cx_of(i) == 0) {
-#pragma unroll
-      for (int j = 0; j < kVec; ++j) g[i][j] = v[j];
-    } else if (cx_of(i) > 0) {  // source x - 1
-      float pw = __shfl_up_sync(0xffffffffu, v[kVec - 1], 1);
       if (lane == 0) {
-        if (x0 > 0)
-          pw = __ldg(b + i * P + row + x0 - 1);
-        else
-          pw = periodic ? __ldg(b + i * P + row + nx - 1) : 0.0f;
+        tm->x0 = x0;
+        tm->y0 = y0;
+        tm->rows = rows;
       }
-      g[i][0] = pw;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&full_bar[s]);
+    }
+    // never leave with bulk copies in flight: wait (bounded) for the issued stages
+    const int issued = k;
+    for (int q = max(0, issued - kStages); q < issued; ++q)
+      mbar_wait(&full_bar[q % kStages], (q / kStages) & 1, status);
+    return;
+  }
+
+  // -------------------------------------------------------------- consumers
+  int k = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+    const int s = k % kStages;
+    if (!mbar_wait(&full_bar[s], (k / kStages) & 1, status)) return;
+    const TileMeta* tm = metas + s;
+    const GridDev G = tm->g;
+    const int x0 = tm->x0, y0 = tm->y0;
+    const bool row_ok = warp < tm->rows;  // warp-uniform
+    if (!row_ok) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty_bar[s]);
+      continue;
+    }
+    const int nx = G.nx, ny = G.ny;
+    const int y = y0 + warp;
+    const int x = x0 + kVec * lane;
+    const bool active = x < nx;
+    const bool periodic = G.periodic_x != 0;
+    const int ym = (y == 0) ? ny - 1 : y - 1;
+    const int yp = (y == ny - 1) ? 0 : y + 1;
+    const float* b = src + G.f_off;
+    const unsigned P = (unsigned)G.plane;
+    // solid bits: window bit b of row r (r = 0: y-1, 1: y, 2: y+1) <-> cell x - 1 + b
+    const int bitpos = 31 + kVec * lane;
+    const int k0 = bitpos >> 5, sh = bitpos & 31;
+    uint32_t win[3];
 #pragma unroll
-      for (int j = 1; j < kVec; ++j) g[i][j] = v[j - 1];
-    } else {  // source x + 1
-      float nv = __shfl_down_sync(0xffffffffu, v[0], 1);
-      if (lane == 31) nv = (x0 + kSeg < nx) ? __ldg(b + i * P + row + x0 + kSeg) : 0.0f;
+    for (int r = 0; r < 3; ++r) {
+      const uint32_t* mw = tm->mask + (warp + r) * kWords;
+      win[r] = __funnelshift_r(mw[k0], mw[k0 + 1], sh) & ((1u << (kVec + 2)) - 1u);
+    }
+    const int jw = nx - 1 - x;  // lane-local index of the cell x = nx-1, if 0..3
+    const float* st = stage_mem + (size_t)s * kStageFloats;
+    float g[kQ][kVec];
+    uint32_t own_solid = 0;
+    if (active) {
+      const uint32_t* m = mask + G.mask_off;
+      if (x == 0) {  // west neighbour of the first column
 #pragma unroll
-      for (int j = 0; j < kVec - 1; ++j) g[i][j] = v[j + 1];
-      g[i][kVec - 1] = nv;
-      if (active && jw >= 0 && jw < kVec) {
-        const float wrap = periodic ? __ldg(b + i * P + row) : 0.0f;
+        for (int r = 0; r < 3; ++r) {
+          win[r] &= ~1u;
+          if (periodic) win[r] |= (uint32_t)mask_bit(m, G.wpr, nx - 1, r == 0 ? ym : (r == 1 ? y : yp));
+        }
+      }
+      if (jw >= 0 && jw < kVec) {  // east neighbour of the last column
 #pragma unroll
-        for (int j = 0; j < kVec; ++j)
-          if (j == jw) g[i][j] = wrap;
+        for (int r = 0; r < 3; ++r) {
+          win[r] &= ~(1u << (jw + 2));
+          if (periodic)
+            win[r] |= (uint32_t)mask_bit(m, G.wpr, 0, r == 0 ? ym : (r == 1 ? y : yp)) << (jw + 2);
+        }
+      }
+      own_solid = (win[1] >> 1) & 0xFu;
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) {
+        const float* rowp = st + (i * kTY + warp) * kRowF + 4 + kVec * lane;
+        const float4 c0 = *reinterpret_cast<const float4*>(rowp);
+        const int ys = cy_of(i) > 0 ? ym : (cy_of(i) == 0 ? y : yp);
+        if (cx_of(i) == 0) {
+          g[i][0] = c0.x; g[i][1] = c0.y; g[i][2] = c0.z; g[i][3] = c0.w;
+        } else if (cx_of(i) > 0) {  // source x - 1
+          const float4 cm = *reinterpret_cast<const float4*>(rowp - 4);
+          g[i][0] = cm.w; g[i][1] = c0.x; g[i][2] = c0.y; g[i][3] = c0.z;
+          if (x == 0) g[i][0] = periodic ? __ldg(b + i * P + ys * G.pitch + nx - 1) : 0.0f;
+        } else {  // source x + 1
+          const float4 cp = *reinterpret_cast<const float4*>(rowp + 4);
+          g[i][0] = c0.y; g[i][1] = c0.z; g[i][2] = c0.w; g[i][3] = cp.x;
+          if (jw >= 0 && jw < kVec) {
+            const float wrap = periodic ? __ldg(b + i * P + ys * G.pitch) : 0.0f;
+#pragma unroll
+            for (int j = 0; j < kVec; ++j)
+              if (j == jw) g[i][j] = wrap;
+          }
+        }
+      }
+      // halfway bounce-back: own-cell opposite population, from the stage when staged
+#pragma unroll
+      for (int i = 1; i < kQ; ++i) {
+        const int r = cy_of(i) > 0 ? 0 : (cy_of(i) == 0 ? 1 : 2);
+        const uint32_t bb = ((win[r] >> (1 - cx_of(i))) & 0xFu) & ~own_solid;
+        if (bb) {
+          const int o = opp_of(i);
+          const int ro = warp + cy_of(o);  // stage row of population o that holds row y
+          float4 v;
+          if (ro >= 0 && ro < kTY && y0 + ro < ny)
+            v = *reinterpret_cast<const float4*>(st + (o * kTY + ro) * kRowF + 4 + kVec * lane);
+          else
+            v = __ldg(reinterpret_cast<const float4*>(b + o * P + y * G.pitch + x));
+          if (bb & 1u) g[i][0] = v.x;
+          if (bb & 2u) g[i][1] = v.y;
+          if (bb & 4u) g[i][2] = v.z;
+          if (bb & 8u) g[i][3] = v.w;
+        }
       }
     }
-  }
-  // ---- halfway bounce-back where the source cell is solid
-#pragma unroll
-  for (int i = 1; i < kQ; ++i) {
-    const int r = cy_of(i) > 0 ? 0 : (cy_of(i) == 0 ? 1 : 2);
-    const uint32_t bb = ((win[r] >> (1 - cx_of(i))) & ((1u << kVec) - 1u)) & ~own_solid;
-    if (active && bb) {
-      float o[kVec];
-      V::load(b + opp_of(i) * P + rowY + x, o);
-#pragma unroll
-      for (int j = 0; j < kVec; ++j)
-        if (bb & (1u << j)) g[i][j] = o[j];
-    }
-  }
-  if (!active) return;
-  // ---- per cell: Zou-He completion, moments, collision
-#pragma unroll
-  for (int j = 0; j < kVec; ++j) {
-    float c[kQ];
-#pragma unroll
-    for (int i = 0; i < kQ; ++i) c[i] = g[i][j];
-    if (!periodic) {
-      if (x + j == 0) {
-        const float G0 = c[0] + c[2] + c[4] + 2.0f * (c[3] + c[6] + c[7]);
-        const float ru = (G.bc_west == LBM_BC_PRESSURE)
-                             ? G.west_d - G0
-                             : (1.0f + G0) / (1.0f - G.west_d) * G.west_d;
-        const float t = 0.5f * (c[2] - c[4]);
-        c[1] = c[3] + (2.0f / 3.0f) * ru;
-        c[5] = c[7] - t + (1.0f / 6.0f) * ru;
-        c[8] = c[6] + t + (1.0f / 6.0f) * ru;
-      }
-      if (x + j == nx - 1) {
-        const float G0 = c[0] + c[2] + c[4] + 2.0f * (c[1] + c[5] + c[8]);
-        const float ru = (G.bc_east == LBM_BC_PRESSURE)
-                             ? G0 - G.east_d
-                             : (1.0f + G0) / (1.0f + G.east_d) * G.east_d;
-        const float t = 0.5f * (c[2] - c[4]);
-        c[3] = c[1] - (2.0f / 3.0f) * ru;
-        c[7] = c[5] + t - (1.0f / 6.0f) * ru;
-        c[6] = c[8] - t - (1.0f / 6.0f) * ru;
-      }
-    }
-    collide(G, c);
-#pragma unroll
-    for (int i = 0; i < kQ; ++i) g[i][j] = c[i];
-  }
-  // ---- store the post-collision populations of this lane's cells
-  float* o = dst + G.f_off + rowY + x;
-  const bool full = (own_solid == 0) && (x + kVec <= nx);
-  if (full) {
-#pragma unroll
-    for (int i = 0; i < kQ; ++i) V::store(o + i * P, g[i]);
-  } else {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty_bar[s]);  // this warp no longer reads the stage
+    if (!active) continue;
 #pragma unroll
     for (int j = 0; j < kVec; ++j) {
-      if (x + j < nx && !((own_solid >> j) & 1u)) {
+      float c[kQ];
 #pragma unroll
-        for (int i = 0; i < kQ; ++i) o[i * P + j] = g[i][j];
+      for (int i = 0; i < kQ; ++i) c[i] = g[i][j];
+      if (!periodic) {
+        if (x + j == 0) {
+          const float G0 = c[0] + c[2] + c[4] + 2.0f * (c[3] + c[6] + c[7]);
+          const float ru = (G.bc_west == LBM_BC_PRESSURE)
+                               ? G.west_d - G0
+                               : (1.0f + G0) / (1.0f - G.west_d) * G.west_d;
+          const float tt = 0.5f * (c[2] - c[4]);
+          c[1] = c[3] + (2.0f / 3.0f) * ru;
+          c[5] = c[7] - tt + (1.0f / 6.0f) * ru;
+          c[8] = c[6] + tt + (1.0f / 6.0f) * ru;
+        }
+        if (x + j == nx - 1) {
+          const float G0 = c[0] + c[2] + c[4] + 2.0f * (c[1] + c[5] + c[8]);
+          const float ru = (G.bc_east == LBM_BC_PRESSURE)
+                               ? G0 - G.east_d
+                               : (1.0f + G0) / (1.0f + G.east_d) * G.east_d;
+          const float tt = 0.5f * (c[2] - c[4]);
+          c[3] = c[1] - (2.0f / 3.0f) * ru;
+          c[7] = c[5] + tt - (1.0f / 6.0f) * ru;
+          c[6] = c[8] - tt - (1.0f / 6.0f) * ru;
+        }
       }
+      collide(G, c);
+      const bool keep = !((own_solid >> j) & 1u);  // solid cells store 0
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) g[i][j] = keep ? c[i] : 0.0f;
+    }
+    float* o = dst + G.f_off + (size_t)y * G.pitch + x;
+    if (x + kVec <= nx) {
+#pragma unroll
+      for (int i = 0; i < kQ; ++i)
+        *reinterpret_cast<float4*>(o + i * P) = make_float4(g[i][0], g[i][1], g[i][2], g[i][3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < kVec; ++j)
+        if (x + j < nx) {
+#pragma unroll
+          for (int i = 0; i < kQ; ++i) o[i * P + j] = g[i][j];
+        }
     }
   }
 }
@@ -621,7 +768,11 @@ struct Handle {
   GridDev* gd_d = nullptr;  // in the caller's workspace
   int ngrids = 0;
   int nblk_total = 0;
-  int nsblk_total = 0;
+  int ntiles_total = 0;
+  int nsm = 0;
+  int tma_blocks_per_sm = 1;
+  unsigned* status_d = nullptr;
+  unsigned status_h = 0;
   const uint32_t* mask = nullptr;
   float* f[2] = {nullptr, nullptr};
   int cur = 0;  // buffer holding the current state
@@ -636,14 +787,14 @@ struct Handle {
 };
 
 struct WsPlan {
-  size_t grids_off, uprev_off, partial_off, stats_off, total;
+  size_t grids_off, uprev_off, partial_off, stats_off, status_off, total;
 };
 
 static int plan_layout(const lbm_grid* grids, int ngrids, lbm_layout* lay,
                        std::vector<GridDev>* gd, WsPlan* wp) {
   LBM_REQUIRE(grids != nullptr && ngrids > 0, "lbm: need at least one grid");
   size_t f = 0, words = 0, cells = 0;
-  long long blk = 0, sblk = 0;
+  long long blk = 0, tiles = 0;
   if (gd) gd->clear();
   for (int k = 0; k < ngrids; ++k) {
     const lbm_grid& g = grids[k];
@@ -675,8 +826,9 @@ static int plan_layout(const lbm_grid* grids, int ngrids, lbm_layout* lay,
     d.nblk = (int)((d.plane + kBlock - 1) / kBlock);
     d.blk_start = (int)blk;
     d.nseg = (g.nx + kSeg - 1) / kSeg;
-    d.nsblk = (int)(((long long)d.nseg * g.ny + kStepWarps - 1) / kStepWarps);
-    d.sblk_start = (int)sblk;
+
+    d.ntiles = d.nseg * ((g.ny + kTY - 1) / kTY);
+    d.tile_start = (int)tiles;
     d.tau = (float)g.tau;
     d.omega = (float)(1.0 / g.tau);
     d.guo = (float)(1.0 - 0.5 / g.tau);
@@ -693,8 +845,9 @@ static int plan_layout(const lbm_grid* grids, int ngrids, lbm_layout* lay,
     words += (size_t)d.wpr * g.ny;
     cells += (size_t)g.nx * g.ny;
     blk += d.nblk;
-    sblk += d.nsblk;
-    LBM_REQUIRE(blk < (1LL << 30) && sblk < (1LL << 30), "lbm: batch too large");
+    tiles += d.ntiles;
+    LBM_REQUIRE(blk < (1LL << 30) && tiles < (1LL << 30),
+                "lbm: batch too large");
     if (gd) gd->push_back(d);
   }
   WsPlan w{};
@@ -702,7 +855,8 @@ static int plan_layout(const lbm_grid* grids, int ngrids, lbm_layout* lay,
   w.uprev_off = align_up(sizeof(GridDev) * ngrids, 256);
   w.partial_off = align_up(w.uprev_off + 2 * cells * sizeof(float), 256);
   w.stats_off = align_up(w.partial_off + (size_t)blk * R_COUNT * sizeof(double), 256);
-  w.total = align_up(w.stats_off + (size_t)ngrids * R_COUNT * sizeof(double), 256);
+  w.status_off = align_up(w.stats_off + (size_t)ngrids * R_COUNT * sizeof(double), 256);
+  w.total = align_up(w.status_off + sizeof(unsigned), 256);
   lay->f_elems = f;
   lay->mask_words = words;
   lay->cells = cells;
@@ -747,7 +901,7 @@ int lbm_init(const lbm_grid* grids_h, int ngrids, const uint32_t* mask_d, float*
   h->grids.assign(grids_h, grids_h + ngrids);
   h->ngrids = ngrids;
   h->nblk_total = h->gd.back().blk_start + h->gd.back().nblk;
-  h->nsblk_total = h->gd.back().sblk_start + h->gd.back().nsblk;
+  h->ntiles_total = h->gd.back().tile_start + h->gd.back().ntiles;
   h->mask = mask_d;
   h->f[0] = f_a_d;
   h->f[1] = f_b_d;
@@ -757,9 +911,24 @@ int lbm_init(const lbm_grid* grids_h, int ngrids, const uint32_t* mask_d, float*
   h->uy_prev = h->ux_prev + h->layout.cells;
   h->partial = reinterpret_cast<double*>(ws + wp.partial_off);
   h->stats_d = reinterpret_cast<double*>(ws + wp.stats_off);
+  h->status_d = reinterpret_cast<unsigned*>(ws + wp.status_off);
   h->stats_h.assign((size_t)ngrids * R_COUNT, 0.0);
   h->u_max2 = (float)(u_max * u_max);
   cudaStream_t s = S(stream);
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaFuncSetAttribute(k_step_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kTmaSmem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->tma_blocks_per_sm, k_step_tma,
+                                                      (kTY + 1) * 32, kTmaSmem) != cudaSuccess) {
+      set_error("lbm_init: %s", cudaGetErrorString(cudaGetLastError()));
+      delete h;
+      return LBM_ERR_CUDA;
+    }
+  }
+  h->tma_blocks_per_sm = std::max(1, h->tma_blocks_per_sm);
   auto fail = [&](int code) {
     delete h;
     return code;
@@ -769,6 +938,7 @@ int lbm_init(const lbm_grid* grids_h, int ngrids, const uint32_t* mask_d, float*
       cudaMemsetAsync(f_a_d, 0, h->layout.f_elems * sizeof(float), s) != cudaSuccess ||
       cudaMemsetAsync(f_b_d, 0, h->layout.f_elems * sizeof(float), s) != cudaSuccess ||
       cudaMemsetAsync(h->ux_prev, 0, 2 * h->layout.cells * sizeof(float), s) != cudaSuccess ||
+      cudaMemsetAsync(h->status_d, 0, sizeof(unsigned), s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {
     set_error("lbm_init: %s", cudaGetErrorString(cudaGetLastError()));
     return fail(LBM_ERR_CUDA);
@@ -780,9 +950,11 @@ int lbm_init(const lbm_grid* grids_h, int ngrids, const uint32_t* mask_d, float*
 int lbm_step(lbm_handle* h, int nsteps, void* stream) {
   LBM_REQUIRE(h != nullptr && nsteps >= 0, "lbm_step: bad arguments");
   cudaStream_t s = S(stream);
+  const int ctas = std::min(h->ntiles_total, h->nsm * h->tma_blocks_per_sm);
   for (int k = 0; k < nsteps; ++k) {
-    k_step<<<h->nsblk_total, kStepWarps * 32, 0, s>>>(h->gd_d, h->ngrids, h->mask,
-                                                      h->f[h->cur], h->f[h->cur ^ 1]);
+    k_step_tma<<<ctas, (kTY + 1) * 32, kTmaSmem, s>>>(h->gd_d, h->ngrids, h->ntiles_total,
+                                                      h->mask, h->f[h->cur], h->f[h->cur ^ 1],
+                                                      h->status_d);
     LBM_CHECK_LAUNCH();
     h->cur ^= 1;
   }
@@ -810,7 +982,13 @@ int lbm_residual(lbm_handle* h, double* out_h, int update_prev, void* stream) {
   LBM_CHECK_CUDA(cudaMemcpyAsync(h->stats_h.data(), h->stats_d,
                                  sizeof(double) * R_COUNT * h->ngrids, cudaMemcpyDeviceToHost,
                                  s));
+  LBM_CHECK_CUDA(cudaMemcpyAsync(&h->status_h, h->status_d, sizeof(unsigned),
+                                 cudaMemcpyDeviceToHost, s));
   LBM_CHECK_CUDA(cudaStreamSynchronize(s));
+  if (h->status_h & kStatusTimeout) {
+    set_error("lbm: a device-side wait expired (status 0x%x)", h->status_h);
+    return LBM_ERR_TIMEOUT;
+  }
   bool bad = false;
   for (int g = 0; g < h->ngrids; ++g) {
     const double* r = &h->stats_h[(size_t)g * R_COUNT];
