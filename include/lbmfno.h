@@ -149,6 +149,120 @@ int lbm_steps_done(const lbm_handle* h, long long* out_h);
 
 int lbm_destroy(lbm_handle* h);
 
+
+/* ======================================================================
+ * Fourier Neural Operator (Sec. 2.2, Fig. 2):
+ *   theta_0 = P(phi);  theta_{n+1} = sigma(W theta_n + F^-1(R . F(theta_n))), n < N;
+ *   out = Q(theta_N).
+ * P: 1x1 network (c_in + 2 coordinate channels x/(W-1), y/(H-1)) -> C/2 -> sigma
+ *    -> C.  F keeps ky in [0, m) U [H-m, H), kx in [0, m) (unnormalised forward
+ *    DFT); R: per kept mode a complex C x C matrix (one [C, C, m, m] block per
+ *    ky half); F^-1 is the real-input inverse (1/(H W), kx > 0 counted twice).
+ *    W: 1x1 convolution with bias.  sigma: GELU (exact erf form) or ReLU.
+ *    Q: dec_layers hidden 1x1 layers of dec_size with sigma, then a linear
+ *    output layer.
+ * Precision: parameters and inputs are bfloat16 values, activations are stored
+ * as bfloat16 between layers, every sum accumulates in FP32.
+ * Parameter pack (bfloat16 bits, this order, row-major shapes):
+ *   lift0.w [C/2][c_in+2], lift0.b [C/2], lift1.w [C][C/2], lift1.b [C],
+ *   per layer n: r1.re, r1.im, r2.re, r2.im [C_in][C_out][m][m], w [C][C], b [C],
+ *   per decoder layer l: w [S][fan_in], b [S];  out.w [c_out][S], out.b [c_out].
+ * ====================================================================== */
+enum fno_activation { FNO_ACT_GELU = 0, FNO_ACT_RELU = 1 };
+
+typedef struct fno_config {
+  int32_t c_in;       /* physical input channels */
+  int32_t c_out;      /* output channels */
+  int32_t width;      /* latent channels C (even, <= 64) */
+  int32_t layers;     /* Fourier layers N */
+  int32_t modes;      /* kept modes m per corner block */
+  int32_t dec_layers; /* hidden decoder layers (>= 1) */
+  int32_t dec_size;   /* decoder width S (<= 64) */
+  int32_t activation; /* enum fno_activation */
+} fno_config;
+
+typedef struct fno_sizes {
+  size_t n_params;     /* parameters in the bfloat16 pack */
+  size_t packed_bytes; /* device bytes of the repacked parameters (fno_create) */
+  size_t ws_bytes;     /* device workspace bytes of fno_forward for (B, H, W) */
+} fno_sizes;
+
+typedef struct fno_handle fno_handle;
+
+/* Sizes for a configuration and a forward shape B x H x W (host only).
+ * Requires 2m <= H and m < W/2. */
+int fno_query(const fno_config* cfg_h, int B, int H, int W, fno_sizes* out_h);
+
+/* Repack the bfloat16 parameter pack params_d (n_params values, device) into
+ * packed_d (packed_bytes, caller-owned, 256-byte aligned).  The handle keeps
+ * pointers to packed_d only. */
+int fno_create(const fno_config* cfg_h, const uint16_t* params_d, void* packed_d, void* stream,
+               fno_handle** out);
+
+/* Forward pass.  in_d: [B][c_in][H][W] FP32 (rounded to bfloat16 on entry);
+ * out_d: [B][c_out][H][W] FP32; ws_d: ws_bytes from fno_query(B, H, W). */
+int fno_forward(fno_handle* h, const float* in_d, float* out_d, int B, int H, int W, void* ws_d,
+                size_t ws_bytes, void* stream);
+
+/* Configuration the handle was created with. */
+int fno_get_config(const fno_handle* h, fno_config* out_h);
+
+int fno_destroy(fno_handle* h);
+
+/* ======================================================================
+ * Hybrid FNO-LBM framework (Sec. 2.3, Fig. 3)
+ *   steady   (Fig. 3a): FNO prediction of (rho - 1, u) from the mask and the
+ *            default fields -> clamp -> re-initialisation of f -> LBM until the
+ *            residual of every grid is below tol (checked every check_every
+ *            steps) or max_steps.  use_fno = 0 runs the plain rest-state start.
+ *   unsteady (Fig. 3b): per cycle k_lbm LBM steps, then m_fno FNO steps on the
+ *            macroscopic fields, then re-initialisation of f.
+ * FNO inputs are (rho - 1, u_x, u_y, mask) per cell, outputs (rho - 1, u_x, u_y).
+ * Grids of equal size share one FNO call.
+ * ====================================================================== */
+enum hybrid_mode { HYBRID_STEADY = 0, HYBRID_UNSTEADY = 1 };
+
+typedef struct hybrid_config {
+  int32_t mode;        /* enum hybrid_mode */
+  int32_t use_fno;     /* steady: 1 = FNO initialisation, 0 = rest state */
+  int32_t neq_mode;    /* re-initialisation: 1 = f^eq + f^neq, 0 = f^eq */
+  int32_t check_every; /* steady: residual interval (steps) */
+  double tol;          /* steady: residual tolerance */
+  int64_t max_steps;   /* steady: step cap */
+  int32_t k_lbm;       /* unsteady: LBM steps per cycle */
+  int32_t m_fno;       /* unsteady: FNO steps per cycle */
+  double rho_lo, rho_hi; /* clamp of the predicted density before re-initialisation */
+  double u_clamp;        /* clamp of the predicted speed */
+} hybrid_config;
+
+typedef struct hybrid_stats {
+  int64_t steps;       /* LBM steps taken by this call */
+  int32_t converged;   /* steady: all grids below tol */
+  int32_t fno_calls;   /* fno_forward calls made */
+  double max_residual; /* steady: largest final residual over grids */
+} hybrid_stats;
+
+typedef struct hybrid_handle hybrid_handle;
+
+/* Device workspace bytes of a hybrid over the LBM batch `grids_h` with FNO `cfg_h`. */
+int hybrid_query_ws(const lbm_grid* grids_h, int ngrids, const fno_config* cfg_h, size_t* ws_h);
+
+/* Couple an LBM handle and an FNO handle (both stay owned by the caller). */
+int hybrid_create(lbm_handle* lbm, fno_handle* fno, const hybrid_config* cfg_h, void* ws_d,
+                  size_t ws_bytes, hybrid_handle** out);
+
+/*
+ * Steady mode: cycles is ignored; runs to convergence or max_steps.
+ * grid_steps_h (ngrids, may be NULL): step count at which each grid first met
+ * tol (-1 if never); grid_residual_h (ngrids, may be NULL): final residuals.
+ * Unsteady mode: runs `cycles` cycles, enqueued on `stream` without host
+ * synchronisation (replayed from a CUDA graph after the first cycle).
+ */
+int hybrid_advance(hybrid_handle* h, int cycles, hybrid_stats* out_h, int64_t* grid_steps_h,
+                   double* grid_residual_h, void* stream);
+
+int hybrid_destroy(hybrid_handle* h);
+
 #ifdef __cplusplus
 }
 #endif

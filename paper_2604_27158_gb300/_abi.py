@@ -42,6 +42,34 @@ class lbm_layout(ctypes.Structure):
                 ("cells", ctypes.c_size_t), ("ws_bytes", ctypes.c_size_t)]
 
 
+class fno_config(ctypes.Structure):
+    _fields_ = [("c_in", ctypes.c_int32), ("c_out", ctypes.c_int32), ("width", ctypes.c_int32),
+                ("layers", ctypes.c_int32), ("modes", ctypes.c_int32),
+                ("dec_layers", ctypes.c_int32), ("dec_size", ctypes.c_int32),
+                ("activation", ctypes.c_int32)]
+
+
+class fno_sizes(ctypes.Structure):
+    _fields_ = [("n_params", ctypes.c_size_t), ("packed_bytes", ctypes.c_size_t),
+                ("ws_bytes", ctypes.c_size_t)]
+
+
+class hybrid_config(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("use_fno", ctypes.c_int32), ("neq_mode", ctypes.c_int32),
+                ("check_every", ctypes.c_int32), ("tol", ctypes.c_double),
+                ("max_steps", ctypes.c_int64), ("k_lbm", ctypes.c_int32), ("m_fno", ctypes.c_int32),
+                ("rho_lo", ctypes.c_double), ("rho_hi", ctypes.c_double),
+                ("u_clamp", ctypes.c_double)]
+
+
+class hybrid_stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("converged", ctypes.c_int32),
+                ("fno_calls", ctypes.c_int32), ("max_residual", ctypes.c_double)]
+
+
+FNO_ACT_GELU, FNO_ACT_RELU = 0, 1
+HYBRID_STEADY, HYBRID_UNSTEADY = 0, 1
+
 VP = ctypes.c_void_p
 I = ctypes.c_int
 _PROTOS = {
@@ -58,6 +86,18 @@ _PROTOS = {
     "lbm_get_state": ([VP, VP, VP], I),
     "lbm_steps_done": ([VP, ctypes.POINTER(ctypes.c_longlong)], I),
     "lbm_destroy": ([VP], I),
+    "fno_query": ([ctypes.POINTER(fno_config), I, I, I, ctypes.POINTER(fno_sizes)], I),
+    "fno_create": ([ctypes.POINTER(fno_config), VP, VP, VP, ctypes.POINTER(VP)], I),
+    "fno_forward": ([VP, VP, VP, I, I, I, VP, ctypes.c_size_t, VP], I),
+    "fno_get_config": ([VP, ctypes.POINTER(fno_config)], I),
+    "fno_destroy": ([VP], I),
+    "hybrid_query_ws": ([ctypes.POINTER(lbm_grid), I, ctypes.POINTER(fno_config),
+                         ctypes.POINTER(ctypes.c_size_t)], I),
+    "hybrid_create": ([VP, VP, ctypes.POINTER(hybrid_config), VP, ctypes.c_size_t,
+                       ctypes.POINTER(VP)], I),
+    "hybrid_advance": ([VP, I, ctypes.POINTER(hybrid_stats), ctypes.POINTER(ctypes.c_int64),
+                        ctypes.POINTER(ctypes.c_double), VP], I),
+    "hybrid_destroy": ([VP], I),
 }
 
 

@@ -2,6 +2,7 @@
 // constants, per-grid metadata).  Used only by the CUDA path.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 

@@ -1,0 +1,505 @@
+// Fourier Neural Operator forward pass (Sec. 2.2, Fig. 2 of arXiv 2604.27158)
+// for GB300 (sm_103a) and its C ABI.
+//
+// Data layout (caller-owned workspace, HBM resident):
+//   theta   [B][H][W][C]  bfloat16 latent field (channels innermost)
+//   X1      [B][H][m][C]  float2  forward x-DFT of each row (kx < m)
+//   Xh, Yh  [B][2m][m][C] float2  kept spectral coefficients before / after mixing
+//   Z       [B][H][m][C]  float2  inverse y-DFT of the mixed coefficients
+// The spectral convolution is separable: forward x-DFT per row, forward y-DFT per
+// column over the kept kx, per-mode complex channel mixing, inverse y-DFT, and a
+// fused "inverse x-DFT + W theta + bias + activation" row kernel that writes the
+// next latent field.  All sums accumulate in FP32; twiddles e^{+-2 pi i k n / N}
+// come from FP32 tables indexed by (k n mod N).
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace lbmfno {
+
+struct FnoOffsets {
+  size_t lift0_w, lift0_b, lift1_w, lift1_b;
+  std::vector<size_t> r1re, r1im, r2re, r2im, w, b;
+  std::vector<size_t> dec_w, dec_b;
+  size_t out_w, out_b;
+  size_t n_params;
+  size_t rt_off;     // float offset of the transposed spectral filters
+  size_t rt_layer;   // floats per layer of transposed filters
+  size_t total_floats;
+};
+
+static int fno_offsets(const fno_config& c, FnoOffsets* o) {
+  LBM_REQUIRE(c.c_in >= 1 && c.c_in <= 16 && c.c_out >= 1 && c.c_out <= 16,
+              "fno: channel counts out of range");
+  LBM_REQUIRE(c.width >= 2 && c.width <= 64 && c.width % 2 == 0, "fno: width must be even, <= 64");
+  LBM_REQUIRE(c.layers >= 1 && c.layers <= 16 && c.modes >= 1 && c.modes <= 64,
+              "fno: layers / modes out of range");
+  LBM_REQUIRE(c.dec_layers >= 1 && c.dec_layers <= 8 && c.dec_size >= 1 && c.dec_size <= 64,
+              "fno: decoder shape out of range");
+  LBM_REQUIRE(c.activation == FNO_ACT_GELU || c.activation == FNO_ACT_RELU,
+              "fno: unknown activation");
+  const size_t C = c.width, h = C / 2, m = c.modes, cin2 = c.c_in + 2;
+  size_t p = 0;
+  auto take = [&](size_t n) {
+    const size_t at = p;
+    p += n;
+    return at;
+  };
+  o->lift0_w = take(h * cin2);
+  o->lift0_b = take(h);
+  o->lift1_w = take(C * h);
+  o->lift1_b = take(C);
+  o->r1re.clear(); o->r1im.clear(); o->r2re.clear(); o->r2im.clear(); o->w.clear(); o->b.clear();
+  for (int n = 0; n < c.layers; ++n) {
+    o->r1re.push_back(take(C * C * m * m));
+    o->r1im.push_back(take(C * C * m * m));
+    o->r2re.push_back(take(C * C * m * m));
+    o->r2im.push_back(take(C * C * m * m));
+    o->w.push_back(take(C * C));
+    o->b.push_back(take(C));
+  }
+  o->dec_w.clear(); o->dec_b.clear();
+  size_t fan = C;
+  for (int l = 0; l < c.dec_layers; ++l) {
+    o->dec_w.push_back(take((size_t)c.dec_size * fan));
+    o->dec_b.push_back(take(c.dec_size));
+    fan = c.dec_size;
+  }
+  o->out_w = take((size_t)c.c_out * fan);
+  o->out_b = take(c.c_out);
+  o->n_params = p;
+  o->rt_off = align_up(p, 64);
+  o->rt_layer = 2 * m * m * C * C * 2;  // float2 per (mode, i, o)
+  o->total_floats = o->rt_off + o->rt_layer * c.layers;
+  return LBM_OK;
+}
+
+struct FnoWs {
+  size_t theta0, theta1, x1, xh, yh, z, twx, twy, total;
+};
+static FnoWs fno_ws_plan(const fno_config& c, int B, int H, int W) {
+  FnoWs w{};
+  const size_t C = c.width, m = c.modes;
+  size_t p = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = p;
+    p = align_up(p + bytes, 256);
+    return at;
+  };
+  const size_t pix = (size_t)B * H * W;
+  w.theta0 = take(pix * C * 2);
+  w.theta1 = take(pix * C * 2);
+  w.x1 = take((size_t)B * H * m * C * sizeof(float2));
+  w.xh = take((size_t)B * 2 * m * m * C * sizeof(float2));
+  w.yh = take((size_t)B * 2 * m * m * C * sizeof(float2));
+  w.z = take((size_t)B * H * m * C * sizeof(float2));
+  w.twx = take((size_t)W * sizeof(float2));
+  w.twy = take((size_t)H * sizeof(float2));
+  w.total = p;
+  return w;
+}
+
+// ---------------------------------------------------------------- kernels ---
+__device__ __forceinline__ float act_fn(float v, int act) {
+  return act == FNO_ACT_GELU ? 0.5f * v * (1.0f + erff(v * 0.70710678118654752f)) : fmaxf(v, 0.0f);
+}
+__device__ __forceinline__ float bf16r(float v) {  // round to the nearest bfloat16 value
+  return __bfloat162float(__float2bfloat16_rn(v));
+}
+
+__global__ void k_bf16_to_f32(const uint16_t* __restrict__ in, float* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t u = (uint32_t)in[i] << 16;
+    out[i] = __uint_as_float(u);
+  }
+}
+
+// Rt[(mode * C + i) * C + o] = (re, im) with mode = a * m + kx, a < m from r1, a >= m from r2
+__global__ void k_transpose_r(const float* __restrict__ r1re, const float* __restrict__ r1im,
+                              const float* __restrict__ r2re, const float* __restrict__ r2im,
+                              float2* __restrict__ rt, int C, int m) {
+  const size_t n = (size_t)2 * m * m * C * C;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int o = (int)(t % C);
+    const int i = (int)((t / C) % C);
+    const int mode = (int)(t / ((size_t)C * C));
+    const int a = mode / m, kx = mode % m;
+    const bool lo = a < m;
+    const int ky = lo ? a : a - m;
+    const size_t src = (((size_t)i * C + o) * m + ky) * m + kx;
+    rt[t] = lo ? make_float2(r1re[src], r1im[src]) : make_float2(r2re[src], r2im[src]);
+  }
+}
+
+// tw[t] = (cos(2 pi t / N), sin(2 pi t / N))
+__global__ void k_twiddle(float2* __restrict__ tw, int N) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < N) {
+    double s, c;
+    sincospi(2.0 * (double)t / (double)N, &s, &c);
+    tw[t] = make_float2((float)c, (float)s);
+  }
+}
+
+// Lifting network P with the two coordinate channels; one thread per pixel.
+__global__ void k_lift(const float* __restrict__ in, __nv_bfloat16* __restrict__ theta,
+                       const float* __restrict__ w0, const float* __restrict__ b0,
+                       const float* __restrict__ w1, const float* __restrict__ b1, int B, int H,
+                       int W, int cin, int C, int act) {
+  const size_t pix = (size_t)B * H * W;
+  const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (p >= pix) return;
+  const int x = (int)(p % W);
+  const int y = (int)((p / W) % H);
+  const int b = (int)(p / ((size_t)W * H));
+  float xin[18];
+  for (int c = 0; c < cin; ++c) xin[c] = bf16r(in[(((size_t)b * cin + c) * H + y) * W + x]);
+  xin[cin] = bf16r((float)x / (float)max(W - 1, 1));
+  xin[cin + 1] = bf16r((float)y / (float)max(H - 1, 1));
+  const int h = C / 2, cin2 = cin + 2;
+  float hid[32];
+  for (int j = 0; j < h; ++j) {
+    float a = b0[j];
+    for (int c = 0; c < cin2; ++c) a = fmaf(w0[j * cin2 + c], xin[c], a);
+    hid[j] = act_fn(a, act);
+  }
+  __nv_bfloat16* out = theta + p * C;
+  for (int o = 0; o < C; ++o) {
+    float a = b1[o];
+    for (int j = 0; j < h; ++j) a = fmaf(w1[o * h + j], hid[j], a);
+    out[o] = __float2bfloat16_rn(a);
+  }
+}
+
+// Forward x-DFT of one row (b, y): X1[kx][c] = sum_x theta[x][c] e^{-2 pi i kx x / W}.
+// Threads: c = tid % C, kx group = tid / C (kx = group, group + G, ...).
+__global__ void k_fwd_x(const __nv_bfloat16* __restrict__ theta, float2* __restrict__ x1,
+                        const float2* __restrict__ twx, int H, int W, int C, int m) {
+  extern __shared__ float smem_f[];
+  float* row = smem_f;                                  // W * C
+  float2* tw = reinterpret_cast<float2*>(row + (size_t)W * C);  // W
+  const size_t r = blockIdx.x;  // row index b * H + y
+  const __nv_bfloat16* src = theta + r * (size_t)W * C;
+  for (int t = threadIdx.x; t < W * C; t += blockDim.x) row[t] = __bfloat162float(src[t]);
+  for (int t = threadIdx.x; t < W; t += blockDim.x) tw[t] = twx[t];
+  __syncthreads();
+  const int groups = blockDim.x / C;
+  const int c = threadIdx.x % C, g0 = threadIdx.x / C;
+  if (g0 >= groups) return;
+  for (int kx = g0; kx < m; kx += groups) {
+    float re = 0.f, im = 0.f;
+    int idx = 0;
+    for (int x = 0; x < W; ++x) {
+      const float v = row[x * C + c];
+      const float2 e = tw[idx];
+      re = fmaf(v, e.x, re);
+      im = fmaf(-v, e.y, im);
+      idx += kx;
+      if (idx >= W) idx -= W;
+    }
+    x1[(r * m + kx) * C + c] = make_float2(re, im);
+  }
+}
+
+__device__ __forceinline__ int kept_ky(int a, int H, int m) { return a < m ? a : H - 2 * m + a; }
+
+// Forward y-DFT over the kept ky for one (b, kx): Xh[b][a][kx][c].
+__global__ void k_fwd_y(const float2* __restrict__ x1, float2* __restrict__ xh,
+                        const float2* __restrict__ twy, int H, int C, int m) {
+  const int b = blockIdx.x / m, kx = blockIdx.x % m;
+  const int c = threadIdx.x % C, g0 = threadIdx.x / C, groups = blockDim.x / C;
+  if (g0 >= groups) return;
+  for (int a = g0; a < 2 * m; a += groups) {
+    const int ky = kept_ky(a, H, m);
+    float re = 0.f, im = 0.f;
+    int idx = 0;
+    for (int y = 0; y < H; ++y) {
+      const float2 v = x1[(((size_t)b * H + y) * m + kx) * C + c];
+      const float2 e = twy[idx];  // e^{-i phi} = cos - i sin
+      re += v.x * e.x + v.y * e.y;
+      im += v.y * e.x - v.x * e.y;
+      idx += ky;
+      if (idx >= H) idx -= H;
+    }
+    xh[(((size_t)b * 2 * m + a) * m + kx) * C + c] = make_float2(re, im);
+  }
+}
+
+// Per-mode complex channel mixing: Yh[b][mode][o] = sum_i Xh[b][mode][i] R[mode][i][o].
+__global__ void k_mix(const float2* __restrict__ xh, float2* __restrict__ yh,
+                      const float2* __restrict__ rt, int B, int C, int modes) {
+  extern __shared__ float2 rs[];  // C * C
+  const int mode = blockIdx.x;
+  for (int t = threadIdx.x; t < C * C; t += blockDim.x) rs[t] = rt[(size_t)mode * C * C + t];
+  __syncthreads();
+  const int o = threadIdx.x % C, bg = threadIdx.x / C, groups = blockDim.x / C;
+  if (bg >= groups) return;
+  for (int b = bg; b < B; b += groups) {
+    const float2* xv = xh + ((size_t)b * modes + mode) * C;
+    float re = 0.f, im = 0.f;
+    for (int i = 0; i < C; ++i) {
+      const float2 a = xv[i], r = rs[i * C + o];
+      re += a.x * r.x - a.y * r.y;
+      im += a.x * r.y + a.y * r.x;
+    }
+    yh[((size_t)b * modes + mode) * C + o] = make_float2(re, im);
+  }
+}
+
+// Inverse y-DFT over the kept ky for one (b, kx): Z[b][y][kx][o].
+__global__ void k_inv_y(const float2* __restrict__ yh, float2* __restrict__ z,
+                        const float2* __restrict__ twy, int H, int C, int m) {
+  extern __shared__ float2 ys[];  // 2m * C
+  const int b = blockIdx.x / m, kx = blockIdx.x % m;
+  for (int t = threadIdx.x; t < 2 * m * C; t += blockDim.x) {
+    const int a = t / C, o = t % C;
+    ys[t] = yh[(((size_t)b * 2 * m + a) * m + kx) * C + o];
+  }
+  __syncthreads();
+  const int o = threadIdx.x % C, g0 = threadIdx.x / C, groups = blockDim.x / C;
+  if (g0 >= groups) return;
+  for (int y = g0; y < H; y += groups) {
+    float re = 0.f, im = 0.f;
+    for (int a = 0; a < 2 * m; ++a) {
+      const int ky = kept_ky(a, H, m);
+      const float2 e = twy[(int)(((long long)ky * y) % H)];  // e^{+i phi} = cos + i sin
+      const float2 v = ys[a * C + o];
+      re += v.x * e.x - v.y * e.y;
+      im += v.x * e.y + v.y * e.x;
+    }
+    z[(((size_t)b * H + y) * m + kx) * C + o] = make_float2(re, im);
+  }
+}
+
+// Row kernel: theta'[x][o] = act( (1/HW) sum_kx c_kx Re(Z[kx][o] e^{+2 pi i kx x/W})
+//                                 + sum_i Wt[o][i] theta[x][i] + bias[o] ).
+__global__ void k_inv_x_w(const __nv_bfloat16* __restrict__ theta, const float2* __restrict__ z,
+                          const float* __restrict__ wmat, const float* __restrict__ bias,
+                          __nv_bfloat16* __restrict__ out, const float2* __restrict__ twx, int H,
+                          int W, int C, int m, int act) {
+  extern __shared__ float smem_f[];
+  float* wt = smem_f;                                      // C * C, [i][o]
+  float2* zs = reinterpret_cast<float2*>(wt + C * C);      // m * C
+  float2* tw = zs + m * C;                                 // W
+  const size_t r = blockIdx.x;
+  for (int t = threadIdx.x; t < C * C; t += blockDim.x) {
+    const int i = t / C, o = t % C;
+    wt[t] = wmat[o * C + i];
+  }
+  for (int t = threadIdx.x; t < m * C; t += blockDim.x) zs[t] = z[r * m * C + t];
+  for (int t = threadIdx.x; t < W; t += blockDim.x) tw[t] = twx[t];
+  __syncthreads();
+  const float inv_hw = 1.0f / ((float)H * (float)W);
+  const __nv_bfloat16* src = theta + r * (size_t)W * C;
+  __nv_bfloat16* dst = out + r * (size_t)W * C;
+  const int o = threadIdx.x % C, xg = threadIdx.x / C, groups = blockDim.x / C;
+  if (xg >= groups) return;
+  const float bo = bias[o];
+  for (int x = xg; x < W; x += groups) {
+    float s = 0.f;
+    int idx = 0;
+    for (int kx = 0; kx < m; ++kx) {
+      const float2 e = tw[idx];
+      const float2 v = zs[kx * C + o];
+      const float t = v.x * e.x - v.y * e.y;
+      s += (kx == 0 ? 1.0f : 2.0f) * t;
+      idx += x;
+      while (idx >= W) idx -= W;
+    }
+    float a = fmaf(s, inv_hw, bo);
+    const __nv_bfloat16* tv = src + (size_t)x * C;
+    for (int i = 0; i < C; ++i) a = fmaf(wt[i * C + o], __bfloat162float(tv[i]), a);
+    dst[(size_t)x * C + o] = __float2bfloat16_rn(act_fn(a, act));
+  }
+}
+
+// Projection Q: hidden layers with the activation, then the linear output layer.
+__global__ void k_decoder(const __nv_bfloat16* __restrict__ theta, float* __restrict__ out,
+                          const float* __restrict__ params, const unsigned* __restrict__ offs,
+                          int nlayers, int B, int H, int W, int C, int S, int cout, int act) {
+  const size_t pix = (size_t)B * H * W;
+  const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (p >= pix) return;
+  float a[64], t[64];
+  for (int c = 0; c < C; ++c) a[c] = __bfloat162float(theta[p * C + c]);
+  int fan = C;
+  for (int l = 0; l < nlayers; ++l) {
+    const float* w = params + offs[2 * l];
+    const float* bb = params + offs[2 * l + 1];
+    for (int j = 0; j < S; ++j) {
+      float v = bb[j];
+      for (int c = 0; c < fan; ++c) v = fmaf(w[j * fan + c], a[c], v);
+      t[j] = act_fn(v, act);
+    }
+    for (int j = 0; j < S; ++j) a[j] = t[j];
+    fan = S;
+  }
+  const float* w = params + offs[2 * nlayers];
+  const float* bb = params + offs[2 * nlayers + 1];
+  const int x = (int)(p % W);
+  const int y = (int)((p / W) % H);
+  const int b = (int)(p / ((size_t)W * H));
+  for (int o = 0; o < cout; ++o) {
+    float v = bb[o];
+    for (int c = 0; c < fan; ++c) v = fmaf(w[o * fan + c], a[c], v);
+    out[(((size_t)b * cout + o) * H + y) * W + x] = v;
+  }
+}
+
+}  // namespace lbmfno
+
+using namespace lbmfno;
+
+static constexpr size_t kRowSmemMax = 200 * 1024;
+
+struct fno_handle {
+  fno_config cfg;
+  FnoOffsets off;
+  float* packed = nullptr;  // caller-owned
+  unsigned* dec_offs = nullptr;  // inside packed: decoder offsets table (as floats' bits)
+};
+
+static inline cudaStream_t SS(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+extern "C" {
+
+int fno_query(const fno_config* cfg_h, int B, int H, int W, fno_sizes* out_h) {
+  LBM_REQUIRE(cfg_h && out_h, "fno_query: null argument");
+  FnoOffsets o;
+  LBM_TRY(fno_offsets(*cfg_h, &o));
+  LBM_REQUIRE(B >= 0 && H >= 1 && W >= 1, "fno_query: bad shape");
+  LBM_REQUIRE(2 * cfg_h->modes <= H && 2 * cfg_h->modes < W,
+              "fno_query: need 2m <= H and m < W/2 (m=%d, H=%d, W=%d)", cfg_h->modes, H, W);
+  out_h->n_params = o.n_params;
+  out_h->packed_bytes = align_up((o.total_floats + 64) * sizeof(float), 256);
+  out_h->ws_bytes = fno_ws_plan(*cfg_h, std::max(B, 1), H, W).total;
+  return LBM_OK;
+}
+
+int fno_create(const fno_config* cfg_h, const uint16_t* params_d, void* packed_d, void* stream,
+               fno_handle** out) {
+  LBM_REQUIRE(out != nullptr, "fno_create: null handle output");
+  *out = nullptr;
+  LBM_REQUIRE(cfg_h && params_d && packed_d, "fno_create: null argument");
+  LBM_REQUIRE(((uintptr_t)packed_d % 256) == 0, "fno_create: packed buffer must be 256-byte aligned");
+  fno_handle* h = new fno_handle();
+  h->cfg = *cfg_h;
+  int st = fno_offsets(*cfg_h, &h->off);
+  if (st != LBM_OK) {
+    delete h;
+    return st;
+  }
+  h->packed = static_cast<float*>(packed_d);
+  cudaStream_t s = SS(stream);
+  // row kernels size their shared memory by W; opt in once (not allowed inside graph capture)
+  if (cudaFuncSetAttribute(k_fwd_x, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kRowSmemMax) != cudaSuccess ||
+      cudaFuncSetAttribute(k_inv_x_w, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kRowSmemMax) != cudaSuccess) {
+    set_error("fno_create: %s", cudaGetErrorString(cudaGetLastError()));
+    delete h;
+    return LBM_ERR_CUDA;
+  }
+  const FnoOffsets& o = h->off;
+  k_bf16_to_f32<<<1024, 256, 0, s>>>(params_d, h->packed, o.n_params);
+  for (int n = 0; n < cfg_h->layers; ++n) {
+    k_transpose_r<<<512, 256, 0, s>>>(h->packed + o.r1re[n], h->packed + o.r1im[n],
+                                      h->packed + o.r2re[n], h->packed + o.r2im[n],
+                                      reinterpret_cast<float2*>(h->packed + o.rt_off + o.rt_layer * n),
+                                      cfg_h->width, cfg_h->modes);
+  }
+  // decoder offset table after the transposed filters
+  std::vector<unsigned> offs;
+  for (int l = 0; l < cfg_h->dec_layers; ++l) {
+    offs.push_back((unsigned)o.dec_w[l]);
+    offs.push_back((unsigned)o.dec_b[l]);
+  }
+  offs.push_back((unsigned)o.out_w);
+  offs.push_back((unsigned)o.out_b);
+  h->dec_offs = reinterpret_cast<unsigned*>(h->packed + o.total_floats);
+  if (cudaMemcpyAsync(h->dec_offs, offs.data(), offs.size() * sizeof(unsigned),
+                      cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+    set_error("fno_create: %s", cudaGetErrorString(cudaGetLastError()));
+    delete h;
+    return LBM_ERR_CUDA;
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+int fno_forward(fno_handle* h, const float* in_d, float* out_d, int B, int H, int W, void* ws_d,
+                size_t ws_bytes, void* stream) {
+  LBM_REQUIRE(h && in_d && out_d && ws_d, "fno_forward: null argument");
+  const fno_config& c = h->cfg;
+  LBM_REQUIRE(B >= 1 && 2 * c.modes <= H && 2 * c.modes < W,
+              "fno_forward: need B >= 1, 2m <= H, m < W/2");
+  const FnoWs wp = fno_ws_plan(c, B, H, W);
+  LBM_REQUIRE(ws_bytes >= wp.total, "fno_forward: workspace too small (%zu < %zu)", ws_bytes,
+              wp.total);
+  LBM_REQUIRE(((uintptr_t)ws_d % 256) == 0, "fno_forward: workspace must be 256-byte aligned");
+  char* ws = static_cast<char*>(ws_d);
+  __nv_bfloat16* th[2] = {reinterpret_cast<__nv_bfloat16*>(ws + wp.theta0),
+                          reinterpret_cast<__nv_bfloat16*>(ws + wp.theta1)};
+  float2* x1 = reinterpret_cast<float2*>(ws + wp.x1);
+  float2* xh = reinterpret_cast<float2*>(ws + wp.xh);
+  float2* yh = reinterpret_cast<float2*>(ws + wp.yh);
+  float2* z = reinterpret_cast<float2*>(ws + wp.z);
+  float2* twx = reinterpret_cast<float2*>(ws + wp.twx);
+  float2* twy = reinterpret_cast<float2*>(ws + wp.twy);
+  cudaStream_t s = SS(stream);
+  const int C = c.width, m = c.modes;
+  const float* P = h->packed;
+  const FnoOffsets& o = h->off;
+  k_twiddle<<<(W + 255) / 256, 256, 0, s>>>(twx, W);
+  k_twiddle<<<(H + 255) / 256, 256, 0, s>>>(twy, H);
+  const size_t pix = (size_t)B * H * W;
+  k_lift<<<(unsigned)((pix + 127) / 128), 128, 0, s>>>(in_d, th[0], P + o.lift0_w, P + o.lift0_b,
+                                                       P + o.lift1_w, P + o.lift1_b, B, H, W,
+                                                       c.c_in, C, c.activation);
+  LBM_CHECK_LAUNCH();
+  const int rows = B * H;
+  const size_t smem_fx = (size_t)W * C * sizeof(float) + (size_t)W * sizeof(float2);
+  const size_t smem_ix = (size_t)C * C * sizeof(float) + (size_t)m * C * sizeof(float2) +
+                         (size_t)W * sizeof(float2);
+  LBM_REQUIRE(smem_fx <= kRowSmemMax && smem_ix <= kRowSmemMax,
+              "fno_forward: W * C too large for the row kernels");
+  const int cur_threads = 256;
+  int cur = 0;
+  for (int n = 0; n < c.layers; ++n) {
+    k_fwd_x<<<rows, cur_threads, smem_fx, s>>>(th[cur], x1, twx, H, W, C, m);
+    k_fwd_y<<<B * m, cur_threads, 0, s>>>(x1, xh, twy, H, C, m);
+    k_mix<<<2 * m * m, cur_threads, (size_t)C * C * sizeof(float2), s>>>(
+        xh, yh, reinterpret_cast<const float2*>(P + o.rt_off + o.rt_layer * n), B, C, 2 * m * m);
+    k_inv_y<<<B * m, cur_threads, (size_t)2 * m * C * sizeof(float2), s>>>(yh, z, twy, H, C, m);
+    k_inv_x_w<<<rows, cur_threads, smem_ix, s>>>(th[cur], z, P + o.w[n], P + o.b[n],
+                                                 th[cur ^ 1], twx, H, W, C, m, c.activation);
+    LBM_CHECK_LAUNCH();
+    cur ^= 1;
+  }
+  k_decoder<<<(unsigned)((pix + 127) / 128), 128, 0, s>>>(th[cur], out_d, P, h->dec_offs,
+                                                          c.dec_layers, B, H, W, C, c.dec_size,
+                                                          c.c_out, c.activation);
+  LBM_CHECK_LAUNCH();
+  return LBM_OK;
+}
+
+int fno_get_config(const fno_handle* h, fno_config* out_h) {
+  LBM_REQUIRE(h && out_h, "fno_get_config: null argument");
+  *out_h = h->cfg;
+  return LBM_OK;
+}
+
+int fno_destroy(fno_handle* h) {
+  delete h;
+  return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,363 @@
+// Hybrid FNO-LBM driver (Sec. 2.3, Fig. 3 of arXiv 2604.27158) and its C ABI.
+//
+//  steady   (Fig. 3a): FNO prediction of (rho - 1, u) from the mask and the
+//           default fields -> clamp -> re-initialisation of f -> LBM time
+//           marching until every grid's residual is below tol.
+//  unsteady (Fig. 3b): super-time-stepping cycles of k LBM steps, m FNO steps
+//           on the macroscopic fields and re-initialisation of f.  One cycle is
+//           captured as a CUDA graph (one per starting buffer parity) and
+//           replayed, so a cycle costs one graph launch on the host.
+// Grids of equal size form one FNO batch.  All buffers live in the caller's
+// workspace; the only host synchronisation is the steady residual check.
+#include <math.h>
+
+#include <algorithm>
+#include <map>
+#include <vector>
+
+#include "common.cuh"
+#include "lbm_internal.cuh"
+
+namespace lbmfno {
+
+struct Group {
+  int H, W;                 // ny, nx of its grids
+  std::vector<int> grids;   // grid indices
+  int* grids_d = nullptr;   // device copy (workspace)
+};
+
+struct HybWs {
+  size_t rho, ux, uy, fin, fout, fws, tables, total;
+  size_t fws_bytes;
+};
+
+static void make_groups(const lbm_grid* grids, int ngrids, std::vector<Group>* groups) {
+  std::map<std::pair<int, int>, int> at;
+  groups->clear();
+  for (int g = 0; g < ngrids; ++g) {
+    const auto key = std::make_pair(grids[g].ny, grids[g].nx);
+    auto it = at.find(key);
+    if (it == at.end()) {
+      at[key] = (int)groups->size();
+      Group gr;
+      gr.H = grids[g].ny;
+      gr.W = grids[g].nx;
+      groups->push_back(gr);
+      it = at.find(key);
+    }
+    (*groups)[it->second].grids.push_back(g);
+  }
+}
+
+static int plan_ws(const lbm_grid* grids, int ngrids, const fno_config* cfg, HybWs* w,
+                   std::vector<Group>* groups) {
+  LBM_REQUIRE(grids && ngrids > 0 && cfg, "hybrid: bad arguments");
+  make_groups(grids, ngrids, groups);
+  size_t cells = 0;
+  for (int g = 0; g < ngrids; ++g) cells += (size_t)grids[g].nx * grids[g].ny;
+  size_t max_cells = 0, max_ws = 0;
+  for (const Group& gr : *groups) {
+    fno_sizes fs;
+    LBM_TRY(fno_query(cfg, (int)gr.grids.size(), gr.H, gr.W, &fs));
+    max_ws = std::max(max_ws, fs.ws_bytes);
+    max_cells = std::max(max_cells, gr.grids.size() * (size_t)gr.H * gr.W);
+  }
+  LBM_REQUIRE(cfg->c_in == 4 && cfg->c_out == 3,
+              "hybrid: the FNO must map (rho-1, ux, uy, mask) to (rho-1, ux, uy)");
+  size_t p = 0;
+  auto take = [&](size_t bytes) {
+    const size_t a = p;
+    p = align_up(p + bytes, 256);
+    return a;
+  };
+  w->rho = take(cells * sizeof(float));
+  w->ux = take(cells * sizeof(float));
+  w->uy = take(cells * sizeof(float));
+  w->fin = take(max_cells * 4 * sizeof(float));
+  w->fout = take(max_cells * 3 * sizeof(float));
+  w->fws = take(max_ws);
+  w->fws_bytes = max_ws;
+  w->tables = take((size_t)ngrids * (sizeof(int) + sizeof(long long)) + 256);
+  w->total = p;
+  return LBM_OK;
+}
+
+// FNO input of a size group: (rho - 1, u_x, u_y, mask) planes per grid.
+__global__ void k_pack(const GridDev* __restrict__ gd, const int* __restrict__ gids, int B, int H,
+                       int W, const uint32_t* __restrict__ mask, const float* __restrict__ rho,
+                       const float* __restrict__ ux, const float* __restrict__ uy,
+                       float* __restrict__ in) {
+  const size_t n = (size_t)B * H * W;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(t / ((size_t)H * W));
+    const int c = (int)(t % ((size_t)H * W));
+    const int y = c / W, x = c % W;
+    const GridDev& G = gd[gids[b]];
+    const long long k = G.cell_off + c;
+    const float s = (float)mask_bit(mask + G.mask_off, G.wpr, x, y);
+    const size_t plane = (size_t)H * W;
+    float* o = in + (size_t)b * 4 * plane + c;
+    o[0] = rho[k] - 1.0f;
+    o[plane] = ux[k];
+    o[2 * plane] = uy[k];
+    o[3 * plane] = s;
+  }
+}
+
+// FNO output -> clamped dense fields: rho = clamp(1 + out0), |u| <= u_clamp.
+__global__ void k_unpack(const GridDev* __restrict__ gd, const int* __restrict__ gids, int B,
+                         int H, int W, const float* __restrict__ out, float rho_lo, float rho_hi,
+                         float u_clamp, float* __restrict__ rho, float* __restrict__ ux,
+                         float* __restrict__ uy) {
+  const size_t n = (size_t)B * H * W;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(t / ((size_t)H * W));
+    const int c = (int)(t % ((size_t)H * W));
+    const GridDev& G = gd[gids[b]];
+    const long long k = G.cell_off + c;
+    const size_t plane = (size_t)H * W;
+    const float* o = out + (size_t)b * 3 * plane + c;
+    const float r = fminf(fmaxf(1.0f + o[0], rho_lo), rho_hi);
+    float vx = o[plane], vy = o[2 * plane];
+    const float sp = sqrtf(vx * vx + vy * vy);
+    if (sp > u_clamp) {
+      const float sc = u_clamp / sp;
+      vx *= sc;
+      vy *= sc;
+    }
+    rho[k] = r;
+    ux[k] = vx;
+    uy[k] = vy;
+  }
+}
+
+__global__ void k_fill_rest(float* __restrict__ rho, float* __restrict__ ux, float* __restrict__ uy,
+                            size_t n) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
+       t += (size_t)gridDim.x * blockDim.x) {
+    rho[t] = 1.0f;
+    ux[t] = 0.0f;
+    uy[t] = 0.0f;
+  }
+}
+
+}  // namespace lbmfno
+
+using namespace lbmfno;
+
+struct hybrid_handle {
+  lbm_handle* lbm = nullptr;
+  fno_handle* fno = nullptr;
+  hybrid_config cfg{};
+  fno_config fcfg{};
+  std::vector<Group> groups;
+  HybWs w{};
+  char* ws = nullptr;
+  float *rho = nullptr, *ux = nullptr, *uy = nullptr, *fin = nullptr, *fout = nullptr;
+  void* fws = nullptr;
+  cudaStream_t cap = nullptr;     // private stream used for graph capture and replay
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t cycle[2] = {nullptr, nullptr};  // by starting buffer parity
+};
+
+static inline cudaStream_t HS(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// FNO prediction for every size group from the dense fields, clamped into the same fields.
+static int hyb_predict(hybrid_handle* h, cudaStream_t s) {
+  lbm_handle* L = h->lbm;
+  for (Group& gr : h->groups) {
+    const int B = (int)gr.grids.size();
+    const size_t n = (size_t)B * gr.H * gr.W;
+    const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 65535);
+    k_pack<<<blocks, 256, 0, s>>>(L->gd_d, gr.grids_d, B, gr.H, gr.W, L->mask, h->rho, h->ux,
+                                  h->uy, h->fin);
+    LBM_CHECK_LAUNCH();
+    LBM_TRY(fno_forward(h->fno, h->fin, h->fout, B, gr.H, gr.W, h->fws, h->w.fws_bytes, s));
+    k_unpack<<<blocks, 256, 0, s>>>(L->gd_d, gr.grids_d, B, gr.H, gr.W, h->fout,
+                                    (float)h->cfg.rho_lo, (float)h->cfg.rho_hi,
+                                    (float)h->cfg.u_clamp, h->rho, h->ux, h->uy);
+    LBM_CHECK_LAUNCH();
+  }
+  return LBM_OK;
+}
+
+// One unsteady cycle: k LBM steps, m FNO steps, re-initialisation.
+static int hyb_cycle(hybrid_handle* h, cudaStream_t s) {
+  LBM_TRY(lbm_step(h->lbm, h->cfg.k_lbm, s));
+  LBM_TRY(lbm_macro(h->lbm, h->rho, h->ux, h->uy, s));
+  for (int j = 0; j < h->cfg.m_fno; ++j) LBM_TRY(hyb_predict(h, s));
+  return lbm_reinit_from_macro(h->lbm, h->rho, h->ux, h->uy, h->cfg.neq_mode, s);
+}
+
+extern "C" {
+
+int hybrid_query_ws(const lbm_grid* grids_h, int ngrids, const fno_config* cfg_h, size_t* ws_h) {
+  LBM_REQUIRE(ws_h != nullptr, "hybrid_query_ws: null output");
+  HybWs w;
+  std::vector<Group> groups;
+  LBM_TRY(plan_ws(grids_h, ngrids, cfg_h, &w, &groups));
+  *ws_h = w.total;
+  return LBM_OK;
+}
+
+int hybrid_create(lbm_handle* lbm, fno_handle* fno, const hybrid_config* cfg_h, void* ws_d,
+                  size_t ws_bytes, hybrid_handle** out) {
+  LBM_REQUIRE(out != nullptr, "hybrid_create: null handle output");
+  *out = nullptr;
+  LBM_REQUIRE(lbm && cfg_h && ws_d, "hybrid_create: null argument");
+  LBM_REQUIRE(((uintptr_t)ws_d % 256) == 0, "hybrid_create: workspace must be 256-byte aligned");
+  const hybrid_config& c = *cfg_h;
+  LBM_REQUIRE(c.mode == HYBRID_STEADY || c.mode == HYBRID_UNSTEADY, "hybrid_create: bad mode");
+  if (c.mode == HYBRID_STEADY)
+    LBM_REQUIRE(c.check_every >= 1 && c.tol > 0 && c.max_steps >= 1,
+                "hybrid_create: steady mode needs check_every >= 1, tol > 0, max_steps >= 1");
+  else
+    LBM_REQUIRE(c.k_lbm >= 0 && c.m_fno >= 0 && fno, "hybrid_create: unsteady mode needs an FNO");
+  const bool needs_fno = (c.mode == HYBRID_UNSTEADY && c.m_fno > 0) ||
+                         (c.mode == HYBRID_STEADY && c.use_fno);
+  LBM_REQUIRE(!needs_fno || fno, "hybrid_create: this configuration needs an FNO handle");
+  LBM_REQUIRE(c.rho_lo > 0.0 && c.rho_hi > c.rho_lo && c.u_clamp > 0.0,
+              "hybrid_create: bad clamp bounds");
+  hybrid_handle* h = new hybrid_handle();
+  h->lbm = lbm;
+  h->fno = fno;
+  h->cfg = c;
+  fno_config fc{};
+  if (fno) {
+    const int sc = fno_get_config(fno, &fc);
+    if (sc != LBM_OK) {
+      delete h;
+      return sc;
+    }
+  } else {
+    fc = fno_config{4, 3, 2, 1, 1, 1, 1, FNO_ACT_GELU};
+  }
+  h->fcfg = fc;
+  int st = plan_ws(lbm->grids.data(), lbm->ngrids, &fc, &h->w, &h->groups);
+  if (st == LBM_OK && ws_bytes < h->w.total) {
+    set_error("hybrid_create: workspace too small (%zu < %zu)", ws_bytes, h->w.total);
+    st = LBM_ERR_INVALID_ARG;
+  }
+  if (st != LBM_OK) {
+    delete h;
+    return st;
+  }
+  h->ws = static_cast<char*>(ws_d);
+  h->rho = reinterpret_cast<float*>(h->ws + h->w.rho);
+  h->ux = reinterpret_cast<float*>(h->ws + h->w.ux);
+  h->uy = reinterpret_cast<float*>(h->ws + h->w.uy);
+  h->fin = reinterpret_cast<float*>(h->ws + h->w.fin);
+  h->fout = reinterpret_cast<float*>(h->ws + h->w.fout);
+  h->fws = h->ws + h->w.fws;
+  // per-group index / offset tables
+  std::vector<int> ids;
+  int* ids_d = reinterpret_cast<int*>(h->ws + h->w.tables);
+  for (Group& gr : h->groups) {
+    gr.grids_d = ids_d + ids.size();
+    for (int g : gr.grids) ids.push_back(g);
+  }
+  if (cudaMemcpy(ids_d, ids.data(), ids.size() * sizeof(int), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    set_error("hybrid_create: %s", cudaGetErrorString(cudaGetLastError()));
+    if (h->cap) cudaStreamDestroy(h->cap);
+    delete h;
+    return LBM_ERR_CUDA;
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+int hybrid_advance(hybrid_handle* h, int cycles, hybrid_stats* out_h, int64_t* grid_steps_h,
+                   double* grid_residual_h, void* stream) {
+  LBM_REQUIRE(h != nullptr, "hybrid_advance: null handle");
+  cudaStream_t s = HS(stream);
+  lbm_handle* L = h->lbm;
+  hybrid_stats stats{};
+  const hybrid_config& c = h->cfg;
+  if (c.mode == HYBRID_STEADY) {
+    const size_t cells = L->layout.cells;
+    const unsigned blocks = (unsigned)std::min<size_t>((cells + 255) / 256, 65535);
+    k_fill_rest<<<blocks, 256, 0, s>>>(h->rho, h->ux, h->uy, cells);
+    LBM_CHECK_LAUNCH();
+    if (c.use_fno) {
+      LBM_TRY(hyb_predict(h, s));
+      stats.fno_calls = (int)h->groups.size();
+    }
+    LBM_TRY(lbm_reinit_from_macro(L, h->rho, h->ux, h->uy, c.use_fno ? c.neq_mode : 0, s));
+    const int ng = L->ngrids;
+    std::vector<int64_t> first(ng, -1);
+    std::vector<double> st((size_t)ng * LBM_NSTAT);
+    long long steps = 0;
+    bool all = false;
+    while (steps < c.max_steps) {
+      const int k = (int)std::min<long long>(c.check_every, c.max_steps - steps);
+      LBM_TRY(lbm_step(L, k, s));
+      steps += k;
+      LBM_TRY(lbm_residual(L, st.data(), 1, s));
+      all = true;
+      double mx = 0.0;
+      for (int g = 0; g < ng; ++g) {
+        const double r = st[(size_t)g * LBM_NSTAT + LBM_STAT_RESIDUAL];
+        if (first[g] < 0 && r < c.tol) first[g] = steps;
+        if (first[g] < 0) all = false;
+        mx = std::max(mx, r);
+      }
+      stats.max_residual = mx;
+      if (all) break;
+    }
+    stats.steps = steps;
+    stats.converged = all ? 1 : 0;
+    for (int g = 0; g < ng; ++g) {
+      if (grid_steps_h) grid_steps_h[g] = first[g];
+      if (grid_residual_h) grid_residual_h[g] = st[(size_t)g * LBM_NSTAT + LBM_STAT_RESIDUAL];
+    }
+  } else {
+    LBM_REQUIRE(cycles >= 0, "hybrid_advance: cycles must be >= 0");
+    // order the private stream after the caller's work
+    LBM_CHECK_CUDA(cudaEventRecord(h->ev_in, s));
+    LBM_CHECK_CUDA(cudaStreamWaitEvent(h->cap, h->ev_in, 0));
+    for (int k = 0; k < cycles; ++k) {
+      const int parity = L->cur;
+      if (!h->cycle[parity]) {
+        cudaGraph_t g = nullptr;
+        LBM_CHECK_CUDA(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+        const long long steps_before = L->steps;
+        const int rc = hyb_cycle(h, h->cap);
+        const cudaError_t ec = cudaStreamEndCapture(h->cap, &g);
+        if (rc != LBM_OK) return rc;
+        LBM_CHECK_CUDA(ec);
+        LBM_CHECK_CUDA(cudaGraphInstantiate(&h->cycle[parity], g, 0));
+        cudaGraphDestroy(g);
+        L->cur = parity;  // capture recorded the launches without running them
+        L->steps = steps_before;
+      }
+      LBM_CHECK_CUDA(cudaGraphLaunch(h->cycle[parity], h->cap));
+      if (c.k_lbm % 2) L->cur ^= 1;
+      L->steps = 0;  // the cycle ends with a re-initialisation
+      stats.steps += c.k_lbm;
+      stats.fno_calls += c.m_fno * (int)h->groups.size();
+    }
+    LBM_CHECK_CUDA(cudaEventRecord(h->ev_out, h->cap));
+    LBM_CHECK_CUDA(cudaStreamWaitEvent(s, h->ev_out, 0));
+  }
+  if (out_h) *out_h = stats;
+  return LBM_OK;
+}
+
+int hybrid_destroy(hybrid_handle* h) {
+  if (!h) return LBM_OK;
+  for (int p = 0; p < 2; ++p)
+    if (h->cycle[p]) cudaGraphExecDestroy(h->cycle[p]);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  delete h;
+  return LBM_OK;
+}
+
+}  // extern "C"

@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "lbm_internal.cuh"
 
 namespace lbmfno {
 
@@ -762,30 +763,6 @@ __global__ void __launch_bounds__(kBlock) k_reinit(const GridDev* __restrict__ g
 }
 
 // ------------------------------------------------------------ host side ---
-struct Handle {
-  std::vector<lbm_grid> grids;
-  std::vector<GridDev> gd;
-  GridDev* gd_d = nullptr;  // in the caller's workspace
-  int ngrids = 0;
-  int nblk_total = 0;
-  int ntiles_total = 0;
-  int nsm = 0;
-  int tma_blocks_per_sm = 1;
-  unsigned* status_d = nullptr;
-  unsigned status_h = 0;
-  const uint32_t* mask = nullptr;
-  float* f[2] = {nullptr, nullptr};
-  int cur = 0;  // buffer holding the current state
-  float* ux_prev = nullptr;
-  float* uy_prev = nullptr;
-  double* partial = nullptr;
-  double* stats_d = nullptr;
-  std::vector<double> stats_h;
-  lbm_layout layout{};
-  float u_max2 = 0.04f;
-  long long steps = 0;
-};
-
 struct WsPlan {
   size_t grids_off, uprev_off, partial_off, stats_off, status_off, total;
 };
@@ -871,7 +848,6 @@ static inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s)
 
 using namespace lbmfno;
 
-struct lbm_handle : Handle {};
 
 extern "C" {
 

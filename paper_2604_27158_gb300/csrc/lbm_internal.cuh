@@ -1,0 +1,36 @@
+// Internal definition of the LBM handle, shared by the LBM and hybrid units.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace lbmfno {
+
+struct Handle {
+  std::vector<lbm_grid> grids;
+  std::vector<GridDev> gd;
+  GridDev* gd_d = nullptr;  // in the caller's workspace
+  int ngrids = 0;
+  int nblk_total = 0;
+  int ntiles_total = 0;
+  int nsm = 0;
+  int tma_blocks_per_sm = 1;
+  unsigned* status_d = nullptr;
+  unsigned status_h = 0;
+  const uint32_t* mask = nullptr;
+  float* f[2] = {nullptr, nullptr};
+  int cur = 0;  // buffer holding the current state
+  float* ux_prev = nullptr;
+  float* uy_prev = nullptr;
+  double* partial = nullptr;
+  double* stats_d = nullptr;
+  std::vector<double> stats_h;
+  lbm_layout layout{};
+  float u_max2 = 0.04f;
+  long long steps = 0;
+};
+
+}  // namespace lbmfno
+
+struct lbm_handle : lbmfno::Handle {};

@@ -1,0 +1,109 @@
+"""GPU parity of the FNO forward pass (Sec. 2.2) against the FP64 oracle, through the C ABI.
+
+Bar: BF16 FNO outputs within 2e-2 relative L2 of the FP64 oracle, which sees the
+same bfloat16-rounded parameters and inputs.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import fno_oracle as fo
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_2604_27158_gb300")
+from paper_2604_27158_gb300.fno import Fno, FnoShape  # noqa: E402
+
+REL_L2_FNO = 2e-2
+
+
+def _requires_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def _pair(c_in=4, c_out=3, width=8, layers=2, modes=3, dec_layers=1, dec_size=8, act=0, seed=1,
+          out_scale=1.0):
+    s = synth.FnoShape(c_in=c_in, c_out=c_out, width=width, layers=layers, modes=modes,
+                       dec_layers=dec_layers, dec_size=dec_size)
+    g = FnoShape(c_in=c_in, c_out=c_out, width=width, layers=layers, modes=modes,
+                 dec_layers=dec_layers, dec_size=dec_size, activation=act)
+    params = synth.fno_random_params(s, seed=seed, out_scale=out_scale)
+    return s, g, params
+
+
+def _inputs(B, c_in, H, W, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((B, c_in, H, W)).astype(np.float32)
+
+
+@pytest.mark.parametrize("B,H,W,act", [(2, 12, 16, 0), (1, 6, 7, 1), (3, 20, 33, 0)])
+def test_small_fno_matches_oracle(B, H, W, act):
+    _requires_gpu()
+    s, g, params = _pair(act=act)
+    net = Fno(g, synth.fno_flatten_params(s, params))
+    x = _inputs(B, 4, H, W, seed=B + H)
+    y = net(torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = fo.fno_forward(s, params, x, activation="gelu" if act == 0 else "relu")
+    e = rel_l2(y, ref)
+    print(f"FNO {B}x{H}x{W} act={act}: rel L2 {e:.3e}")
+    assert e < REL_L2_FNO
+
+
+@pytest.mark.parametrize("H,W", [(32, 48), (64, 64)])
+def test_hot_path_architecture_matches_oracle(H, W):
+    """4 layers, 32 latent channels, 12x12 modes, decoder 32 -> 3 (2,365,331 parameters)."""
+    _requires_gpu()
+    s, g, params = _pair(width=32, layers=4, modes=12, dec_size=32, seed=5)
+    assert fo.param_count(s) == 2365331
+    net = Fno(g, synth.fno_flatten_params(s, params))
+    x = _inputs(2, 4, H, W, seed=7)
+    y = net(torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = fo.fno_forward(s, params, x)
+    e = rel_l2(y, ref)
+    print(f"FNO C=32 m=12 {H}x{W}: rel L2 {e:.3e}")
+    assert e < REL_L2_FNO
+
+
+def _flow_inputs(B, H, W, seed0=0):
+    """(rho-1, ux, uy, mask) shaped like snapshots of the 128x64 channel workload, at H x W."""
+    xs = []
+    for b in range(B):
+        solid, _ = synth.channel_with_disks(W, H, 6, 4 * W // 128, 8 * W // 128, seed=seed0 + b)
+        rho, ux, uy = synth.smooth_macro_fields(W, H, seed=seed0 + b, drho=1e-3, umax=0.05)
+        f = np.stack([rho - 1.0, ux, uy, solid.astype(np.float32)]).astype(np.float32)
+        f[:3, solid] = 0.0
+        xs.append(f)
+    return np.stack(xs)
+
+
+def test_fno_throughput_workload_sampled_against_oracle():
+    """Batch 32 at 256x256 (the FNO throughput workload); the oracle checks two sampled items."""
+    _requires_gpu()
+    s, g, params = _pair(width=32, layers=4, modes=12, dec_size=32, seed=0, out_scale=1e-2)
+    net = Fno(g, synth.fno_flatten_params(s, params))
+    x = _flow_inputs(32, 256, 256)
+    y = net(torch.from_numpy(x).cuda()).cpu().numpy()
+    for b in (0, 31):
+        ref = fo.fno_forward(s, params, x[b:b + 1])[0]
+        e = rel_l2(y[b], ref)
+        print(f"FNO 32x256x256 item {b}: rel L2 {e:.3e}")
+        assert e < REL_L2_FNO
+    # items are independent: a batch of one gives the same result
+    y1 = net(torch.from_numpy(x[5:6].copy()).cuda()).cpu().numpy()
+    np.testing.assert_array_equal(y1[0], y[5])
+
+
+def test_invalid_fno_shapes_rejected():
+    _requires_gpu()
+    s, g, params = _pair(modes=4)
+    net = Fno(g, synth.fno_flatten_params(s, params))
+    with pytest.raises(P.LbmError):
+        net(torch.zeros((1, 4, 7, 16), device="cuda"))  # 2m > H
+    with pytest.raises(P.LbmError):
+        net(torch.zeros((1, 4, 16, 8), device="cuda"))  # m >= W/2

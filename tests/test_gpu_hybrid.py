@@ -1,0 +1,105 @@
+"""GPU parity of the hybrid FNO-LBM driver (Sec. 2.3, Fig. 3) against the oracle drivers."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_2604_27158_gb300")
+from paper_2604_27158_gb300.fno import Fno, FnoShape, Hybrid, HybridConfig  # noqa: E402
+from paper_2604_27158_gb300.lbm import GridSpec, Lattice  # noqa: E402
+
+_, _, W, _ = oracle.lattice()
+
+
+def _requires_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def to_oracle(g):
+    return oracle.Grid(nx=g.nx, ny=g.ny, tau=g.tau, fx=g.fx, fy=g.fy, bc_west=g.bc_west,
+                       bc_east=g.bc_east, west_value=g.west_value, east_value=g.east_value)
+
+
+def _net(width=8, layers=1, modes=3, seed=0, out_scale=1e-2):
+    s = synth.FnoShape(width=width, layers=layers, modes=modes, dec_size=width)
+    g = FnoShape(width=width, layers=layers, modes=modes, dec_size=width)
+    params = synth.fno_random_params(s, seed=seed, out_scale=out_scale)
+    return s, params, Fno(g, synth.fno_flatten_params(s, params))
+
+
+def _porous(n, nx=64, ny=32):
+    specs = []
+    for k in range(n):
+        solid, _, _ = synth.porous_media(nx, ny, 3, 4, seed=10 + k)
+        specs.append((GridSpec(nx, ny, 0.7, bc_west=P.BC_PRESSURE, bc_east=P.BC_PRESSURE,
+                               west_value=1.001, east_value=1.0), solid))
+    return specs
+
+
+@pytest.mark.parametrize("use_fno", [0, 1])
+def test_steady_driver_matches_oracle(use_fno):
+    _requires_gpu()
+    specs = _porous(3)
+    s, params, net = _net(out_scale=1.0)
+    lat = Lattice([a for a, _ in specs], [b for _, b in specs])
+    hyb = Hybrid(lat, net, HybridConfig(use_fno=use_fno, neq_mode=1, check_every=100, tol=1e-30,
+                                        max_steps=300))
+    st, first, res = hyb.advance()
+    assert st.steps == 300 and st.converged == 0 and np.all(first == -1)
+    parts = lat.split(lat.export_f().cpu(), per_cell=9)
+    for k, (g, solid) in enumerate(specs):
+        f, hist = oracle.hybrid_steady(to_oracle(g), solid, s, params, nsteps=300,
+                                       check_every=100, use_fno=bool(use_fno))
+        fl = ~solid
+        e = rel_l2(parts[k].numpy()[:, fl], (f - W[:, None, None])[:, fl])
+        print(f"steady use_fno={use_fno} grid {k}: rel L2 g {e:.3e}, residual gpu {res[k]:.4e} "
+              f"oracle {hist[-1][1]:.4e}")
+        assert e < (1e-5 if not use_fno else 2e-2)
+        assert abs(res[k] - hist[-1][1]) / hist[-1][1] < (1e-3 if not use_fno else 5e-2)
+
+
+def test_steady_driver_reports_convergence():
+    _requires_gpu()
+    specs = _porous(2, nx=48, ny=24)
+    lat = Lattice([a for a, _ in specs], [b for _, b in specs])
+    hyb = Hybrid(lat, None, HybridConfig(use_fno=0, check_every=100, tol=1e-3, max_steps=20000))
+    st, first, res = hyb.advance()
+    assert st.converged == 1 and np.all(first > 0) and np.all(res < 1e-3)
+    assert st.steps == first.max() and st.steps % 100 == 0
+
+
+@pytest.mark.parametrize("k_lbm", [10, 7])
+def test_unsteady_cycles_match_oracle(k_lbm):
+    """Super-time-stepping over a batch of two grid sizes (one FNO call per size)."""
+    _requires_gpu()
+    specs = []
+    for k, (nx, ny) in enumerate([(48, 24), (64, 32), (48, 24)]):
+        solid, _ = synth.flow_past_disks(nx, ny, seed=k, rmax=4)
+        specs.append((GridSpec(nx, ny, 0.6 + 0.05 * k, bc_west=P.BC_VELOCITY, bc_east=P.BC_PRESSURE,
+                               west_value=0.03, east_value=1.0), solid))
+    s, params, net = _net(out_scale=1e-1)
+    lat = Lattice([a for a, _ in specs], [b for _, b in specs])
+    hyb = Hybrid(lat, net, HybridConfig(mode=P._abi.HYBRID_UNSTEADY, k_lbm=k_lbm, m_fno=2,
+                                        neq_mode=1))
+    st, _, _ = hyb.advance(cycles=3)
+    torch.cuda.synchronize()
+    assert st.steps == 3 * k_lbm and st.fno_calls == 3 * 2 * 2
+    rho, ux, uy = (lat.split(t.cpu()) for t in lat.macro())
+    for k, (g, solid) in enumerate(specs):
+        f0 = oracle.rest_state(to_oracle(g), solid)
+        f = oracle.hybrid_unsteady(to_oracle(g), solid, s, params, f0, k_lbm=k_lbm, m_fno=2,
+                                   cycles=3)
+        orho, oux, ouy = oracle.macro(to_oracle(g), solid, f)
+        fl = ~solid
+        e = rel_l2(np.stack([ux[k].numpy()[fl], uy[k].numpy()[fl]]), np.stack([oux[fl], ouy[fl]]))
+        print(f"unsteady k={k_lbm} grid {k}: rel L2 u {e:.3e}")
+        assert e < 2e-2
