@@ -122,6 +122,29 @@ int lbm_macro(lbm_handle* h, float* rho_d, float* ux_d, float* uy_d, void* strea
 int lbm_residual(lbm_handle* h, double* out_h, int update_prev, void* stream);
 
 /*
+ * lbm_residual without caller-provided scratch memory (the paper has no
+ * counterpart: this is a library convenience).  Same statistics, same output
+ * layout and same update_prev behaviour as lbm_residual; the FP64 block partials
+ * and per-grid sums live in a 1 MiB array compiled into the library instead of
+ * the lbm_init workspace, for callers that cannot allocate device memory when
+ * they need the statistics (their device memory is owned by another allocator,
+ * or their runtime forbids allocation after start-up).  Allocates nothing: no
+ * cudaMalloc, no cudaFree, no allocating library routine.
+ *  - Limit: batches whose flat reduction needs more than 1 MiB of scratch (about
+ *    11,900 blocks of 256 cells, i.e. roughly 3 million lattice cells counting
+ *    row padding) are rejected with LBM_ERR_INVALID_ARG; use lbm_residual for them.
+ *  - The first call on a device looks up the array's device address with that
+ *    device current (cudaGetSymbolAddress) and caches it; make that first call
+ *    before any stream capture.
+ *  - Every GPU that loads the library holds the array until the process exits.
+ *    All calls share it and it keeps the last call's contents (every slot a call
+ *    reads is rewritten by that call first, so nothing needs clearing).  Calls
+ *    whose kernels overlap on the GPU race on it.
+ * Synchronises `stream`.
+ */
+int lbm_residual_static(lbm_handle* h, double* out_h, int update_prev, void* stream);
+
+/*
  * Re-initialise the populations from macroscopic fields (hybrid framework,
  * Sec. 2.3): fluid cells get f^eq(rho, u) (Sec. 2.1) plus, if neq_mode != 0,
  * the first-order non-equilibrium estimate

@@ -17,7 +17,7 @@
 //     open end columns, takes moments, relaxes, and stores its own nine g*
 //     at aligned addresses of the other buffer.  72 B of HBM traffic per fluid
 //     cell and step, plus the 1-bit mask.
-//   * Solid cells are never read or written by the step.
+//   * Solid cells are never read by the step; it stores 0 into their slots.
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -1035,3 +1035,97 @@ int lbm_destroy(lbm_handle* h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Residual statistics without caller-provided scratch memory.
+//
+// lbm_residual keeps its FP64 block partials and per-grid sums in the workspace
+// the caller allocated for lbm_init.  Some callers cannot allocate device memory
+// when they want these statistics: for example a host program whose device
+// memory is entirely handed out by another allocator (a framework's caching
+// allocator that already owns the budget), or a runtime that forbids device
+// allocation once it has started.  lbm_residual_static gives them the same
+// numbers with the scratch held in a fixed array compiled into this library.
+//
+// The array is file-scope device memory of kResidualStaticBytes; every GPU that
+// loads the library holds it until the process exits.  Host code may not use the
+// array's name as a device address, so the first call on each device looks the
+// address up with cudaGetSymbolAddress (with that device current) and caches it.
+// Every call shares the array and it keeps the previous call's contents: each
+// block overwrites its own partial slot and the final pass overwrites every
+// per-grid slot, so nothing has to start at zero.  Calls whose kernels overlap
+// on the GPU (two streams, two threads) race on the array.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace lbmfno {
+constexpr size_t kResidualStaticBytes = 1u << 20;  // 1 MiB
+static __device__ __align__(256) unsigned char g_residual_static[kResidualStaticBytes];
+constexpr int kMaxStaticDevices = 64;
+static void* g_residual_static_addr[kMaxStaticDevices] = {};
+static std::mutex g_residual_static_mutex;
+}  // namespace lbmfno
+
+extern "C" int lbm_residual_static(lbm_handle* h, double* out_h, int update_prev, void* stream) {
+  LBM_REQUIRE(h != nullptr && out_h != nullptr, "lbm_residual_static: bad arguments");
+  const size_t partial_bytes = (size_t)h->nblk_total * R_COUNT * sizeof(double);
+  const size_t stats_off = align_up(partial_bytes, 256);
+  const size_t need = stats_off + (size_t)h->ngrids * R_COUNT * sizeof(double);
+  LBM_REQUIRE(need <= kResidualStaticBytes,
+              "lbm_residual_static: batch needs %zu bytes of scratch, the static array holds "
+              "%zu (at most about %zu reduction blocks of 256 cells); use lbm_residual",
+              need, kResidualStaticBytes, kResidualStaticBytes / (R_COUNT * sizeof(double)));
+  int dev = 0;
+  LBM_CHECK_CUDA(cudaGetDevice(&dev));
+  LBM_REQUIRE(dev >= 0 && dev < kMaxStaticDevices, "lbm_residual_static: device %d out of range",
+              dev);
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_residual_static_mutex);
+    if (g_residual_static_addr[dev] == nullptr) {
+      void* p = nullptr;
+      LBM_CHECK_CUDA(cudaGetSymbolAddress(&p, g_residual_static));
+      g_residual_static_addr[dev] = p;
+    }
+    base = g_residual_static_addr[dev];
+  }
+  double* partial = static_cast<double*>(base);
+  double* stats = reinterpret_cast<double*>(static_cast<char*>(base) + stats_off);
+  cudaStream_t s = S(stream);
+  k_residual<<<h->nblk_total, kBlock, 0, s>>>(h->gd_d, h->ngrids, h->mask, h->f[h->cur],
+                                              h->ux_prev, h->uy_prev, update_prev, h->u_max2,
+                                              partial);
+  LBM_CHECK_LAUNCH();
+  k_residual_final<<<h->ngrids, kBlock, 0, s>>>(h->gd_d, partial, stats);
+  LBM_CHECK_LAUNCH();
+  LBM_CHECK_CUDA(cudaMemcpyAsync(h->stats_h.data(), stats, sizeof(double) * R_COUNT * h->ngrids,
+                                 cudaMemcpyDeviceToHost, s));
+  LBM_CHECK_CUDA(cudaMemcpyAsync(&h->status_h, h->status_d, sizeof(unsigned),
+                                 cudaMemcpyDeviceToHost, s));
+  LBM_CHECK_CUDA(cudaStreamSynchronize(s));
+  if (h->status_h & kStatusTimeout) {
+    set_error("lbm: a device-side wait expired (status 0x%x)", h->status_h);
+    return LBM_ERR_TIMEOUT;
+  }
+  bool bad = false;
+  for (int g = 0; g < h->ngrids; ++g) {
+    const double* r = &h->stats_h[(size_t)g * R_COUNT];
+    double* o = out_h + (size_t)g * LBM_NSTAT;
+    o[LBM_STAT_RESIDUAL] = r[R_U2] > 0 ? sqrt(r[R_DU2] / r[R_U2]) : INFINITY;
+    o[LBM_STAT_UNORM] = sqrt(r[R_U2]);
+    const double rw = r[R_N_W] > 0 ? r[R_RHO_W] / r[R_N_W] : 0.0;
+    const double re = r[R_N_E] > 0 ? r[R_RHO_E] / r[R_N_E] : 0.0;
+    o[LBM_STAT_DP] = (rw - re) / 3.0;
+    o[LBM_STAT_MASS] = r[R_FLUID] + r[R_DRHO];
+    o[LBM_STAT_MOMX] = r[R_MOMX];
+    o[LBM_STAT_MOMY] = r[R_MOMY];
+    o[LBM_STAT_BAD] = r[R_BAD];
+    o[LBM_STAT_FLUID] = r[R_FLUID];
+    if (r[R_BAD] > 0 || !std::isfinite(r[R_DU2]) || !std::isfinite(r[R_U2])) bad = true;
+  }
+  if (bad) {
+    set_error("lbm_residual_static: non-finite values or |u| > u_max detected");
+    return LBM_ERR_UNSTABLE;
+  }
+  return LBM_OK;
+}
