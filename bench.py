@@ -74,6 +74,22 @@ def read_peaks():
         return 6800.0, "fallback"
 
 
+def step_kernel_traffic(cells):
+    """DRAM bytes per step-kernel launch from the committed ncu record, scaled to `cells`;
+    None when the step kernel's source changed since the counters were taken."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "k_step_tma_traffic.json")))
+        src = open(os.path.join(ROOT, "paper_2604_27158_gb300", "csrc", "lbm.cu")).read()
+        a = src.index("// ------------------------------------------------------ the fused step ---")
+        b = src.index("__global__ void __launch_bounds__(kBlock) k_export(")
+        if hashlib.sha256(src[a:b].encode()).hexdigest()[:16] != rec["source_section_sha256_16"]:
+            return None
+        return rec["traffic_bytes_per_launch"] * cells / rec["cells"]
+    except Exception:
+        return None
+
+
 def workload(T, seed0):
     import synth
     masks, phis = [], []
@@ -327,7 +343,8 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "kernel": "k_step_tma", "bytes_per_launch": BYTES_PER_CELL * cells,
-                         "launch_ms": kms, "traffic": None},
+                         "launch_ms": kms, "traffic": step_kernel_traffic(cells),
+                         "traffic_unit": "bytes per launch (ncu dram read + write)"},
             "solve": {"lbm_steps": steps_per_solve, "converged": bool(st.converged),
                       "max_residual": float(st.max_residual)},
             "time_to_steady": tts,

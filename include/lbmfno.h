@@ -130,9 +130,9 @@ int lbm_residual(lbm_handle* h, double* out_h, int update_prev, void* stream);
  * they need the statistics (their device memory is owned by another allocator,
  * or their runtime forbids allocation after start-up).  Allocates nothing: no
  * cudaMalloc, no cudaFree, no allocating library routine.
- *  - Limit: batches whose flat reduction needs more than 1 MiB of scratch (about
- *    11,900 blocks of 256 cells, i.e. roughly 3 million lattice cells counting
- *    row padding) are rejected with LBM_ERR_INVALID_ARG; use lbm_residual for them.
+ *  - Limit: batches whose reduction needs more than 1 MiB of scratch (about 11,900
+ *    blocks of 2048 cells, i.e. roughly 24 million lattice cells counting row
+ *    padding) are rejected with LBM_ERR_INVALID_ARG; use lbm_residual for them.
  *  - The first call on a device looks up the array's device address with that
  *    device current (cudaGetSymbolAddress) and caches it; make that first call
  *    before any stream capture.

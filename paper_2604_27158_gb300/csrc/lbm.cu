@@ -41,6 +41,9 @@ void set_error(const char* fmt, ...) {
   va_end(ap);
 }
 
+// cells per thread of the residual kernel
+constexpr int kResCells = 8;
+
 // raw per-block reduction slots of the residual kernel
 enum {
   R_DU2 = 0,
@@ -226,11 +229,12 @@ __device__ __forceinline__ bool cell_of_thread(const GridDev* __restrict__ grids
 // Work decomposition: tiles of kTY rows x 128 cells.  A persistent grid of CTAs
 // (several per SM) walks the tiles.  Each CTA has one producer warp and kTY
 // consumer warps sharing a kStages-deep ring of shared-memory stages:
-//  * the producer issues one cp.async.bulk per (population i, tile row r): the
-//    row segment x0-4 .. x0+131 of population i's *source* row y0 + r - c_iy.
-//    Because every population is fetched at its own source row, a tile needs
-//    no y-halo and every source row is read once.  It also stages the tile's
-//    metadata (the grid descriptor) and the packed mask words of rows
+//  * the producer issues one cp.async.bulk per (population i, staged row): the
+//    row segment x0-4 .. x0+131 of population i's *source* rows y0 + r - c_iy,
+//    plus one own row for the six populations with c_iy != 0 (bounce-back reads
+//    the own cell's opposite population).  Every population is fetched at its
+//    own source rows, so a tile needs no y-halo.  The producer also stages the
+//    tile's metadata (the grid descriptor) and the packed mask words of rows
 //    y0-1 .. y0+kTY, then arrives on the stage's mbarrier;
 //  * consumer warp w owns tile row y0 + w; lane l owns cells x0+4l .. x0+4l+3.
 //    The nine pulled values are aligned 16-byte shared loads (the +-1 x-shift is
@@ -244,18 +248,33 @@ __device__ __forceinline__ bool cell_of_thread(const GridDev* __restrict__ grids
 constexpr int kVec = 4;
 constexpr int kSeg = 32 * kVec;
 #ifndef LBM_TMA_TY
-#define LBM_TMA_TY 4  // rows per tile = consumer warps per CTA
+#define LBM_TMA_TY 3  // rows per tile = consumer warps per CTA
 #endif
 #ifndef LBM_TMA_STAGES
 #define LBM_TMA_STAGES 2  // shared-memory ring depth
 #endif
 #ifndef LBM_TMA_MINB
-#define LBM_TMA_MINB 4  // resident CTAs per SM
+#define LBM_TMA_MINB 5  // resident CTAs per SM
 #endif
 constexpr int kTY = LBM_TMA_TY;
 constexpr int kRowF = kSeg + 8;  // floats per staged row segment
 constexpr int kStages = LBM_TMA_STAGES;
-constexpr int kStageFloats = kQ * kTY * kRowF;
+// Staged rows of population i: the kTY rows it is pulled from plus, for c_iy != 0,
+// the tile's own last (c_iy = +1) or first (c_iy = -1) row, so that bounce-back always
+// finds the own cell's opposite population in the stage.  Stage row 0 of population i
+// holds source row y0 + stage_first(i).
+__host__ __device__ constexpr int stage_rows(int i) { return kTY + (cy_of(i) != 0 ? 1 : 0); }
+// first stage row of population i = sum of stage_rows(j) for j < i (closed form:
+// the populations with c_jy != 0 are j = 2, 4, 5, 6, 7, 8)
+__host__ __device__ constexpr int stage_row0(int i) {
+  return i * kTY + (i > 2 ? 1 : 0) + (i > 4 ? 1 : 0) + (i > 5 ? i - 5 : 0);
+}
+static_assert(stage_row0(3) == 3 * kTY + 1 && stage_row0(kQ) == 9 * kTY + 6 &&
+                  stage_row0(8) + stage_rows(8) == stage_row0(kQ),
+              "stage row offsets");
+__host__ __device__ constexpr int stage_first(int i) { return cy_of(i) > 0 ? -1 : 0; }
+constexpr int kStageRows = stage_row0(kQ);  // 9 kTY + 6
+constexpr int kStageFloats = kStageRows * kRowF;
 constexpr int kWords = kVec + 2;               // mask words per row around a segment
 constexpr int kMaskWords = (kTY + 2) * kWords;  // rows y0-1 .. y0+kTY
 struct __align__(16) TileMeta {
@@ -351,15 +370,17 @@ __global__ void __launch_bounds__((kTY + 1) * 32, LBM_TMA_MINB)
       const unsigned seg_bytes = (unsigned)(xe - xs) * 4u;
       const int rows = min(kTY, ny - y0);
       float* st = stage_mem + (size_t)s * kStageFloats;
-      if (lane == 0) mbar_expect_tx(&full_bar[s], seg_bytes * (unsigned)(kQ * rows));
+      if (lane == 0) mbar_expect_tx(&full_bar[s], seg_bytes * (unsigned)(kQ * rows + 6));
       __syncwarp();
-      for (int c = lane; c < kQ * kTY; c += 32) {
-        const int i = c / kTY, r = c - i * kTY;
-        if (r >= rows) continue;
-        int ys = y0 + r - cy_of(i);
-        ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
-        bulk_g2s(st + (i * kTY + r) * kRowF + (xs - (x0 - 4)),
-                 b + (size_t)i * plane + (size_t)ys * pitch + xs, seg_bytes, &full_bar[s]);
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) {  // compile-time population index
+        const int nr = rows + (cy_of(i) != 0 ? 1 : 0);  // rows past the last grid row skipped
+        for (int r = lane; r < nr; r += 32) {
+          int ys = y0 + stage_first(i) + r;
+          ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
+          bulk_g2s(st + (stage_row0(i) + r) * kRowF + (xs - (x0 - 4)),
+                   b + (size_t)i * plane + (size_t)ys * pitch + xs, seg_bytes, &full_bar[s]);
+        }
       }
       // tile metadata and mask words (generic-proxy stores, released by the arrive)
       TileMeta* tm = metas + s;
@@ -446,7 +467,8 @@ __global__ void __launch_bounds__((kTY + 1) * 32, LBM_TMA_MINB)
       own_solid = (win[1] >> 1) & 0xFu;
 #pragma unroll
       for (int i = 0; i < kQ; ++i) {
-        const float* rowp = st + (i * kTY + warp) * kRowF + 4 + kVec * lane;
+        const float* rowp =
+            st + (stage_row0(i) + warp - cy_of(i) - stage_first(i)) * kRowF + 4 + kVec * lane;
         const float4 c0 = *reinterpret_cast<const float4*>(rowp);
         const int ys = cy_of(i) > 0 ? ym : (cy_of(i) == 0 ? y : yp);
         if (cx_of(i) == 0) {
@@ -466,19 +488,15 @@ __global__ void __launch_bounds__((kTY + 1) * 32, LBM_TMA_MINB)
           }
         }
       }
-      // halfway bounce-back: own-cell opposite population, from the stage when staged
+      // halfway bounce-back: the own cell's opposite population, from the stage
 #pragma unroll
       for (int i = 1; i < kQ; ++i) {
         const int r = cy_of(i) > 0 ? 0 : (cy_of(i) == 0 ? 1 : 2);
         const uint32_t bb = ((win[r] >> (1 - cx_of(i))) & 0xFu) & ~own_solid;
         if (bb) {
           const int o = opp_of(i);
-          const int ro = warp + cy_of(o);  // stage row of population o that holds row y
-          float4 v;
-          if (ro >= 0 && ro < kTY && y0 + ro < ny)
-            v = *reinterpret_cast<const float4*>(st + (o * kTY + ro) * kRowF + 4 + kVec * lane);
-          else
-            v = __ldg(reinterpret_cast<const float4*>(b + o * P + y * G.pitch + x));
+          const float4 v = *reinterpret_cast<const float4*>(
+              st + (stage_row0(o) + warp - stage_first(o)) * kRowF + 4 + kVec * lane);
           if (bb & 1u) g[i][0] = v.x;
           if (bb & 2u) g[i][1] = v.y;
           if (bb & 4u) g[i][2] = v.z;
@@ -609,7 +627,11 @@ __device__ __forceinline__ void block_reduce_store(double v[R_COUNT], double* ou
   }
 }
 
-// Macroscopic fields + steady-state statistics of the current time level.
+// Macroscopic fields + steady-state statistics of the current time level.  Each
+// block owns kResCells x 256 consecutive (pitched) cells of one grid; a thread
+// accumulates its cells in FP64 registers (squares and products formed in FP32),
+// so the FP64 block reduction - costly on this part's FP64 units - runs once per
+// kResCells x 256 cells.  Deterministic: fixed cell-to-thread map, fixed tree.
 __global__ void __launch_bounds__(kBlock) k_residual(const GridDev* __restrict__ grids,
                                                      int ngrids,
                                                      const uint32_t* __restrict__ mask,
@@ -620,40 +642,47 @@ __global__ void __launch_bounds__(kBlock) k_residual(const GridDev* __restrict__
   double v[R_COUNT];
 #pragma unroll
   for (int k = 0; k < R_COUNT; ++k) v[k] = 0.0;
-  const int gidx = grid_of_block(grids, ngrids, blockIdx.x);
+  int n_w = 0, n_e = 0, bad = 0, fluid = 0;
+  const int gidx = grid_of<&GridDev::rblk_start>(grids, ngrids, blockIdx.x);
   const GridDev& G = grids[gidx];
-  const int p = (blockIdx.x - G.blk_start) * kBlock + threadIdx.x;
-  const int y = p / G.pitch, x = p - y * G.pitch;
-  if (y < G.ny && x < G.nx) {
+  const int base = (blockIdx.x - G.rblk_start) * (kBlock * kResCells) + threadIdx.x;
+#pragma unroll 2
+  for (int j = 0; j < kResCells; ++j) {
+    const int p = base + j * kBlock;
+    const int y = p / G.pitch, x = p - y * G.pitch;
+    if (y >= G.ny || x >= G.nx) continue;
     float g[kQ];
-    if (pull_cell(G, mask, src, x, y, g)) {
-      float drho, rho, ux, uy;
-      moments(G, g, drho, rho, ux, uy);
-      const long long c = G.cell_off + (long long)y * G.nx + x;
-      const float pux = ux_prev[c], puy = uy_prev[c];
-      if (update_prev) {
-        ux_prev[c] = ux;
-        uy_prev[c] = uy;
-      }
-      const double dux = (double)ux - (double)pux, duy = (double)uy - (double)puy;
-      v[R_DU2] = dux * dux + duy * duy;
-      const float u2 = ux * ux + uy * uy;
-      v[R_U2] = (double)ux * ux + (double)uy * uy;
-      if (!G.periodic_x && x == 0) {
-        v[R_RHO_W] = drho;
-        v[R_N_W] = 1.0;
-      }
-      if (!G.periodic_x && x == G.nx - 1) {
-        v[R_RHO_E] = drho;
-        v[R_N_E] = 1.0;
-      }
-      v[R_DRHO] = drho;
-      v[R_MOMX] = (double)rho * ux;
-      v[R_MOMY] = (double)rho * uy;
-      v[R_BAD] = (!isfinite(drho) || !isfinite(u2) || u2 > u_max2) ? 1.0 : 0.0;
-      v[R_FLUID] = 1.0;
+    if (!pull_cell(G, mask, src, x, y, g)) continue;
+    float drho, rho, ux, uy;
+    moments(G, g, drho, rho, ux, uy);
+    const long long c = G.cell_off + (long long)y * G.nx + x;
+    const float pux = ux_prev[c], puy = uy_prev[c];
+    if (update_prev) {
+      ux_prev[c] = ux;
+      uy_prev[c] = uy;
     }
+    const float dux = ux - pux, duy = uy - puy;
+    const float u2 = ux * ux + uy * uy;
+    v[R_DU2] += (double)(dux * dux + duy * duy);
+    v[R_U2] += (double)u2;
+    if (!G.periodic_x && x == 0) {
+      v[R_RHO_W] += drho;
+      ++n_w;
+    }
+    if (!G.periodic_x && x == G.nx - 1) {
+      v[R_RHO_E] += drho;
+      ++n_e;
+    }
+    v[R_DRHO] += drho;
+    v[R_MOMX] += (double)(rho * ux);
+    v[R_MOMY] += (double)(rho * uy);
+    bad += (!isfinite(drho) || !isfinite(u2) || u2 > u_max2) ? 1 : 0;
+    ++fluid;
   }
+  v[R_N_W] = n_w;
+  v[R_N_E] = n_e;
+  v[R_BAD] = bad;
+  v[R_FLUID] = fluid;
   block_reduce_store(v, partial + (size_t)blockIdx.x * R_COUNT);
 }
 
@@ -664,8 +693,8 @@ __global__ void __launch_bounds__(kBlock) k_residual_final(const GridDev* __rest
   double v[R_COUNT];
 #pragma unroll
   for (int k = 0; k < R_COUNT; ++k) v[k] = 0.0;
-  for (int b = threadIdx.x; b < G.nblk; b += kBlock) {
-    const double* s = partial + (size_t)(G.blk_start + b) * R_COUNT;
+  for (int b = threadIdx.x; b < G.nrblk; b += kBlock) {
+    const double* s = partial + (size_t)(G.rblk_start + b) * R_COUNT;
 #pragma unroll
     for (int k = 0; k < R_COUNT; ++k) v[k] += s[k];
   }
@@ -771,7 +800,7 @@ static int plan_layout(const lbm_grid* grids, int ngrids, lbm_layout* lay,
                        std::vector<GridDev>* gd, WsPlan* wp) {
   LBM_REQUIRE(grids != nullptr && ngrids > 0, "lbm: need at least one grid");
   size_t f = 0, words = 0, cells = 0;
-  long long blk = 0, tiles = 0;
+  long long blk = 0, tiles = 0, rblk = 0;
   if (gd) gd->clear();
   for (int k = 0; k < ngrids; ++k) {
     const lbm_grid& g = grids[k];
@@ -803,6 +832,8 @@ static int plan_layout(const lbm_grid* grids, int ngrids, lbm_layout* lay,
     d.nblk = (int)((d.plane + kBlock - 1) / kBlock);
     d.blk_start = (int)blk;
     d.nseg = (g.nx + kSeg - 1) / kSeg;
+    d.nrblk = (int)((d.plane + kBlock * kResCells - 1) / (kBlock * kResCells));
+    d.rblk_start = (int)rblk;
 
     d.ntiles = d.nseg * ((g.ny + kTY - 1) / kTY);
     d.tile_start = (int)tiles;
@@ -823,6 +854,7 @@ static int plan_layout(const lbm_grid* grids, int ngrids, lbm_layout* lay,
     cells += (size_t)g.nx * g.ny;
     blk += d.nblk;
     tiles += d.ntiles;
+    rblk += d.nrblk;
     LBM_REQUIRE(blk < (1LL << 30) && tiles < (1LL << 30),
                 "lbm: batch too large");
     if (gd) gd->push_back(d);
@@ -831,7 +863,7 @@ static int plan_layout(const lbm_grid* grids, int ngrids, lbm_layout* lay,
   w.grids_off = 0;
   w.uprev_off = align_up(sizeof(GridDev) * ngrids, 256);
   w.partial_off = align_up(w.uprev_off + 2 * cells * sizeof(float), 256);
-  w.stats_off = align_up(w.partial_off + (size_t)blk * R_COUNT * sizeof(double), 256);
+  w.stats_off = align_up(w.partial_off + (size_t)rblk * R_COUNT * sizeof(double), 256);
   w.status_off = align_up(w.stats_off + (size_t)ngrids * R_COUNT * sizeof(double), 256);
   w.total = align_up(w.status_off + sizeof(unsigned), 256);
   lay->f_elems = f;
@@ -878,6 +910,7 @@ int lbm_init(const lbm_grid* grids_h, int ngrids, const uint32_t* mask_d, float*
   h->ngrids = ngrids;
   h->nblk_total = h->gd.back().blk_start + h->gd.back().nblk;
   h->ntiles_total = h->gd.back().tile_start + h->gd.back().ntiles;
+  h->nrblk_total = h->gd.back().rblk_start + h->gd.back().nrblk;
   h->mask = mask_d;
   h->f[0] = f_a_d;
   h->f[1] = f_b_d;
@@ -949,7 +982,7 @@ int lbm_macro(lbm_handle* h, float* rho_d, float* ux_d, float* uy_d, void* strea
 int lbm_residual(lbm_handle* h, double* out_h, int update_prev, void* stream) {
   LBM_REQUIRE(h != nullptr && out_h != nullptr, "lbm_residual: bad arguments");
   cudaStream_t s = S(stream);
-  k_residual<<<h->nblk_total, kBlock, 0, s>>>(h->gd_d, h->ngrids, h->mask, h->f[h->cur],
+  k_residual<<<h->nrblk_total, kBlock, 0, s>>>(h->gd_d, h->ngrids, h->mask, h->f[h->cur],
                                               h->ux_prev, h->uy_prev, update_prev, h->u_max2,
                                               h->partial);
   LBM_CHECK_LAUNCH();
@@ -1068,12 +1101,12 @@ static std::mutex g_residual_static_mutex;
 
 extern "C" int lbm_residual_static(lbm_handle* h, double* out_h, int update_prev, void* stream) {
   LBM_REQUIRE(h != nullptr && out_h != nullptr, "lbm_residual_static: bad arguments");
-  const size_t partial_bytes = (size_t)h->nblk_total * R_COUNT * sizeof(double);
+  const size_t partial_bytes = (size_t)h->nrblk_total * R_COUNT * sizeof(double);
   const size_t stats_off = align_up(partial_bytes, 256);
   const size_t need = stats_off + (size_t)h->ngrids * R_COUNT * sizeof(double);
   LBM_REQUIRE(need <= kResidualStaticBytes,
               "lbm_residual_static: batch needs %zu bytes of scratch, the static array holds "
-              "%zu (at most about %zu reduction blocks of 256 cells); use lbm_residual",
+              "%zu (at most about %zu reduction blocks of 2048 cells); use lbm_residual",
               need, kResidualStaticBytes, kResidualStaticBytes / (R_COUNT * sizeof(double)));
   int dev = 0;
   LBM_CHECK_CUDA(cudaGetDevice(&dev));
@@ -1092,7 +1125,7 @@ extern "C" int lbm_residual_static(lbm_handle* h, double* out_h, int update_prev
   double* partial = static_cast<double*>(base);
   double* stats = reinterpret_cast<double*>(static_cast<char*>(base) + stats_off);
   cudaStream_t s = S(stream);
-  k_residual<<<h->nblk_total, kBlock, 0, s>>>(h->gd_d, h->ngrids, h->mask, h->f[h->cur],
+  k_residual<<<h->nrblk_total, kBlock, 0, s>>>(h->gd_d, h->ngrids, h->mask, h->f[h->cur],
                                               h->ux_prev, h->uy_prev, update_prev, h->u_max2,
                                               partial);
   LBM_CHECK_LAUNCH();

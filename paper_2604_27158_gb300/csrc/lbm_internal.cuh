@@ -14,6 +14,7 @@ struct Handle {
   int ngrids = 0;
   int nblk_total = 0;
   int ntiles_total = 0;
+  int nrblk_total = 0;  // blocks of the residual kernel
   int nsm = 0;
   int tma_blocks_per_sm = 1;
   unsigned* status_d = nullptr;

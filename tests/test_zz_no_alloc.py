@@ -75,8 +75,8 @@ def test_static_scratch_residual_matches_workspace_residual():
 
 def test_static_scratch_rejects_batches_beyond_its_size():
     _requires_gpu()
-    # 1800 x 1800 cells need ~12,800 reduction blocks of 256 cells: more than 1 MiB of partials
-    lat = Lattice([GridSpec(1800, 1800, 0.8)], [np.zeros((1800, 1800), bool)])
+    # 5000 x 5000 cells need ~12,300 reduction blocks of 2048 cells: more than 1 MiB of partials
+    lat = Lattice([GridSpec(5000, 5000, 0.8)], [np.zeros((5000, 5000), bool)])
     code, _ = _static_call(lat, update_prev=0)
     assert code == _abi.LBM_ERR_INVALID_ARG
     assert "static array" in _abi.last_error()
