@@ -131,8 +131,9 @@ int lbm_residual(lbm_handle* h, double* out_h, int update_prev, void* stream);
  * or their runtime forbids allocation after start-up).  Allocates nothing: no
  * cudaMalloc, no cudaFree, no allocating library routine.
  *  - Limit: batches whose reduction needs more than 1 MiB of scratch (about 11,900
- *    blocks of 2048 cells, i.e. roughly 24 million lattice cells counting row
- *    padding) are rejected with LBM_ERR_INVALID_ARG; use lbm_residual for them.
+ *    blocks of 8 row segments of 128 cells, i.e. roughly 12 million lattice cells
+ *    counting row padding) are rejected with LBM_ERR_INVALID_ARG; use lbm_residual
+ *    for them.
  *  - The first call on a device looks up the array's device address with that
  *    device current (cudaGetSymbolAddress) and caches it; make that first call
  *    before any stream capture.

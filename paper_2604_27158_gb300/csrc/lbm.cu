@@ -41,9 +41,6 @@ void set_error(const char* fmt, ...) {
   va_end(ap);
 }
 
-// cells per thread of the residual kernel
-constexpr int kResCells = 8;
-
 // raw per-block reduction slots of the residual kernel
 enum {
   R_DU2 = 0,
@@ -561,7 +558,7 @@ __global__ void __launch_bounds__(kBlock) k_export(const GridDev* __restrict__ g
                                                    float* __restrict__ out) {
   int gidx, x, y;
   if (!cell_of_thread(grids, ngrids, gidx, x, y)) return;
-  const GridDev& G = grids[gidx];
+  const GridDev G = grids[gidx];  // registers: stores below cannot alias it
   float g[kQ];
   if (!pull_cell(G, mask, src, x, y, g)) {
 #pragma unroll
@@ -579,7 +576,7 @@ __global__ void __launch_bounds__(kBlock) k_copy_state(const GridDev* __restrict
                                                        float* canon, int dir) {
   int gidx, x, y;
   if (!cell_of_thread(grids, ngrids, gidx, x, y)) return;
-  const GridDev& G = grids[gidx];
+  const GridDev G = grids[gidx];  // registers: stores below cannot alias it
   const long long cells = (long long)G.nx * G.ny;
   float* s = state + G.f_off + (long long)y * G.pitch + x;
   float* c = canon + 9 * G.cell_off + (long long)y * G.nx + x;
@@ -594,11 +591,13 @@ __global__ void __launch_bounds__(kBlock) k_copy_state(const GridDev* __restrict
 
 __global__ void __launch_bounds__(kBlock) k_macro(const GridDev* __restrict__ grids, int ngrids,
                                                   const uint32_t* __restrict__ mask,
-                                                  const float* __restrict__ src, float* rho_o,
-                                                  float* ux_o, float* uy_o) {
+                                                  const float* __restrict__ src,
+                                                  float* __restrict__ rho_o,
+                                                  float* __restrict__ ux_o,
+                                                  float* __restrict__ uy_o) {
   int gidx, x, y;
   if (!cell_of_thread(grids, ngrids, gidx, x, y)) return;
-  const GridDev& G = grids[gidx];
+  const GridDev G = grids[gidx];  // registers: stores below cannot alias it
   float g[kQ];
   float rho = 1.0f, ux = 0.0f, uy = 0.0f, drho;
   if (pull_cell(G, mask, src, x, y, g)) moments(G, g, drho, rho, ux, uy);
@@ -627,63 +626,222 @@ __device__ __forceinline__ void block_reduce_store(double v[R_COUNT], double* ou
   }
 }
 
-// Macroscopic fields + steady-state statistics of the current time level.  Each
-// block owns kResCells x 256 consecutive (pitched) cells of one grid; a thread
-// accumulates its cells in FP64 registers (squares and products formed in FP32),
-// so the FP64 block reduction - costly on this part's FP64 units - runs once per
-// kResCells x 256 cells.  Deterministic: fixed cell-to-thread map, fixed tree.
+// Macroscopic fields + steady-state statistics of the current time level.  One
+// warp owns a 128-cell row segment, each lane four cells: the nine pulled values
+// are aligned 16-byte loads at the source rows (the +-1 x-shift from the
+// neighbouring lane by shuffle), the solid bits come from the segment's mask words
+// (loaded once per warp), and Zou-He completes open columns - the same pull as the
+// step.  Each lane sums its four cells in FP32, the warp reduces in FP32 (a tree
+// over 128 cells, relative error ~ 1e-6 at worst), and the eight warps of a block
+// are combined in FP64; blocks are combined in FP64 by k_residual_final.  Fixed
+// cell-to-lane map and fixed trees: deterministic.
+__device__ __forceinline__ float f4get(const float4& v, int j) {
+  return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 __global__ void __launch_bounds__(kBlock) k_residual(const GridDev* __restrict__ grids,
                                                      int ngrids,
                                                      const uint32_t* __restrict__ mask,
                                                      const float* __restrict__ src,
-                                                     float* ux_prev, float* uy_prev,
+                                                     float* __restrict__ ux_prev,
+                                                     float* __restrict__ uy_prev,
                                                      int update_prev, float u_max2,
                                                      double* __restrict__ partial) {
-  double v[R_COUNT];
-#pragma unroll
-  for (int k = 0; k < R_COUNT; ++k) v[k] = 0.0;
-  int n_w = 0, n_e = 0, bad = 0, fluid = 0;
+  constexpr int kWarps = kBlock / 32;
+  __shared__ double red[kWarps][R_COUNT];
   const int gidx = grid_of<&GridDev::rblk_start>(grids, ngrids, blockIdx.x);
-  const GridDev& G = grids[gidx];
-  const int base = (blockIdx.x - G.rblk_start) * (kBlock * kResCells) + threadIdx.x;
-#pragma unroll 2
-  for (int j = 0; j < kResCells; ++j) {
-    const int p = base + j * kBlock;
-    const int y = p / G.pitch, x = p - y * G.pitch;
-    if (y >= G.ny || x >= G.nx) continue;
-    float g[kQ];
-    if (!pull_cell(G, mask, src, x, y, g)) continue;
-    float drho, rho, ux, uy;
-    moments(G, g, drho, rho, ux, uy);
-    const long long c = G.cell_off + (long long)y * G.nx + x;
-    const float pux = ux_prev[c], puy = uy_prev[c];
-    if (update_prev) {
-      ux_prev[c] = ux;
-      uy_prev[c] = uy;
+  const GridDev G = grids[gidx];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int task = (blockIdx.x - G.rblk_start) * kWarps + warp;
+  float acc[R_COUNT];
+#pragma unroll
+  for (int k = 0; k < R_COUNT; ++k) acc[k] = 0.0f;
+  const int nx = G.nx, ny = G.ny;
+  const int y = task / G.nseg;
+  if (y < ny) {  // warp-uniform
+    const int x0 = (task - y * G.nseg) * kSeg;
+    const int x = x0 + kVec * lane;
+    const bool active = x < nx;
+    const bool periodic = G.periodic_x != 0;
+    const int ym = (y == 0) ? ny - 1 : y - 1;
+    const int yp = (y == ny - 1) ? 0 : y + 1;
+    const float* b = src + G.f_off;
+    const unsigned P = (unsigned)G.plane;
+    const int pitch = G.pitch;
+    const uint32_t* m = mask + G.mask_off;
+    // solid bits around the segment: lanes 0..17 fetch the 6 words of rows y-1, y, y+1
+    uint32_t word = 0;
+    if (lane < 18) {
+      const int r = lane / 6;
+      const int wi = (x0 >> 5) - 1 + (lane - r * 6);
+      const int yy = r == 0 ? ym : (r == 1 ? y : yp);
+      if (wi >= 0 && wi < G.wpr) word = __ldg(&m[yy * G.wpr + wi]);
     }
-    const float dux = ux - pux, duy = uy - puy;
-    const float u2 = ux * ux + uy * uy;
-    v[R_DU2] += (double)(dux * dux + duy * duy);
-    v[R_U2] += (double)u2;
-    if (!G.periodic_x && x == 0) {
-      v[R_RHO_W] += drho;
-      ++n_w;
+    const int bitpos = 31 + kVec * lane;
+    const int k0 = bitpos >> 5, sh = bitpos & 31;
+    uint32_t win[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const uint32_t lo = __shfl_sync(0xffffffffu, word, r * 6 + k0);
+      const uint32_t hi = __shfl_sync(0xffffffffu, word, r * 6 + k0 + 1);
+      win[r] = __funnelshift_r(lo, hi, sh) & 0x3Fu;
     }
-    if (!G.periodic_x && x == G.nx - 1) {
-      v[R_RHO_E] += drho;
-      ++n_e;
+    const int jw = nx - 1 - x;
+    if (active) {
+      if (x == 0) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          win[r] &= ~1u;
+          if (periodic) win[r] |= (uint32_t)mask_bit(m, G.wpr, nx - 1, r == 0 ? ym : (r == 1 ? y : yp));
+        }
+      }
+      if (jw >= 0 && jw < kVec) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          win[r] &= ~(1u << (jw + 2));
+          if (periodic)
+            win[r] |= (uint32_t)mask_bit(m, G.wpr, 0, r == 0 ? ym : (r == 1 ? y : yp)) << (jw + 2);
+        }
+      }
     }
-    v[R_DRHO] += drho;
-    v[R_MOMX] += (double)(rho * ux);
-    v[R_MOMY] += (double)(rho * uy);
-    bad += (!isfinite(drho) || !isfinite(u2) || u2 > u_max2) ? 1 : 0;
-    ++fluid;
+    const uint32_t own_solid = (win[1] >> 1) & 0xFu;
+    float g[kQ][kVec];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      const unsigned row = (unsigned)((cy_of(i) == 0 ? y : (cy_of(i) > 0 ? ym : yp)) * pitch);
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (active) v = __ldg(reinterpret_cast<const float4*>(b + i * P + row + x));
+      if (cx_of(i) == 0) {
+        g[i][0] = v.x; g[i][1] = v.y; g[i][2] = v.z; g[i][3] = v.w;
+      } else if (cx_of(i) > 0) {  // source x - 1
+        float pw = __shfl_up_sync(0xffffffffu, v.w, 1);
+        if (lane == 0)
+          pw = x0 > 0 ? __ldg(b + i * P + row + x0 - 1)
+                      : (periodic ? __ldg(b + i * P + row + nx - 1) : 0.0f);
+        g[i][0] = pw; g[i][1] = v.x; g[i][2] = v.y; g[i][3] = v.z;
+      } else {  // source x + 1
+        float nv = __shfl_down_sync(0xffffffffu, v.x, 1);
+        if (lane == 31) nv = (x0 + kSeg < nx) ? __ldg(b + i * P + row + x0 + kSeg) : 0.0f;
+        g[i][0] = v.y; g[i][1] = v.z; g[i][2] = v.w; g[i][3] = nv;
+        if (active && jw >= 0 && jw < kVec) {
+          const float wrap = periodic ? __ldg(b + i * P + row) : 0.0f;
+#pragma unroll
+          for (int j = 0; j < kVec; ++j)
+            if (j == jw) g[i][j] = wrap;
+        }
+      }
+    }
+    if (active) {
+#pragma unroll
+      for (int i = 1; i < kQ; ++i) {  // halfway bounce-back
+        const int r = cy_of(i) > 0 ? 0 : (cy_of(i) == 0 ? 1 : 2);
+        const uint32_t bb = ((win[r] >> (1 - cx_of(i))) & 0xFu) & ~own_solid;
+        if (bb) {
+          const float4 o = __ldg(reinterpret_cast<const float4*>(b + opp_of(i) * P + y * pitch + x));
+          if (bb & 1u) g[i][0] = o.x;
+          if (bb & 2u) g[i][1] = o.y;
+          if (bb & 4u) g[i][2] = o.z;
+          if (bb & 8u) g[i][3] = o.w;
+        }
+      }
+      float ux4[kVec], uy4[kVec];
+      const long long c0 = G.cell_off + (long long)y * nx + x;
+      float4 pu = make_float4(0.f, 0.f, 0.f, 0.f), pv = pu;
+      // vector access only where both fields are 16-byte aligned at this cell
+      const bool vec = (x + kVec <= nx) && ((reinterpret_cast<uintptr_t>(ux_prev + c0) & 15) == 0) &&
+                       ((reinterpret_cast<uintptr_t>(uy_prev + c0) & 15) == 0);
+      if (vec) {
+        pu = *reinterpret_cast<const float4*>(ux_prev + c0);
+        pv = *reinterpret_cast<const float4*>(uy_prev + c0);
+      }
+#pragma unroll
+      for (int j = 0; j < kVec; ++j) {
+        ux4[j] = 0.0f;
+        uy4[j] = 0.0f;
+        if (x + j >= nx || ((own_solid >> j) & 1u)) continue;
+        float c[kQ];
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) c[i] = g[i][j];
+        if (!periodic) {
+          if (x + j == 0) {
+            const float G0 = c[0] + c[2] + c[4] + 2.0f * (c[3] + c[6] + c[7]);
+            const float ru = (G.bc_west == LBM_BC_PRESSURE)
+                                 ? G.west_d - G0
+                                 : (1.0f + G0) / (1.0f - G.west_d) * G.west_d;
+            const float t = 0.5f * (c[2] - c[4]);
+            c[1] = c[3] + (2.0f / 3.0f) * ru;
+            c[5] = c[7] - t + (1.0f / 6.0f) * ru;
+            c[8] = c[6] + t + (1.0f / 6.0f) * ru;
+          }
+          if (x + j == nx - 1) {
+            const float G0 = c[0] + c[2] + c[4] + 2.0f * (c[1] + c[5] + c[8]);
+            const float ru = (G.bc_east == LBM_BC_PRESSURE)
+                                 ? G0 - G.east_d
+                                 : (1.0f + G0) / (1.0f + G.east_d) * G.east_d;
+            const float t = 0.5f * (c[2] - c[4]);
+            c[3] = c[1] - (2.0f / 3.0f) * ru;
+            c[7] = c[5] + t - (1.0f / 6.0f) * ru;
+            c[6] = c[8] - t - (1.0f / 6.0f) * ru;
+          }
+        }
+        float drho, rho, ux, uy;
+        moments(G, c, drho, rho, ux, uy);
+        const float pux = vec ? f4get(pu, j) : ux_prev[c0 + j];
+        const float puy = vec ? f4get(pv, j) : uy_prev[c0 + j];
+        const float dux = ux - pux, duy = uy - puy;
+        const float u2 = ux * ux + uy * uy;
+        acc[R_DU2] += dux * dux + duy * duy;
+        acc[R_U2] += u2;
+        if (!periodic && x + j == 0) {
+          acc[R_RHO_W] += drho;
+          acc[R_N_W] += 1.0f;
+        }
+        if (!periodic && x + j == nx - 1) {
+          acc[R_RHO_E] += drho;
+          acc[R_N_E] += 1.0f;
+        }
+        acc[R_DRHO] += drho;
+        acc[R_MOMX] += rho * ux;
+        acc[R_MOMY] += rho * uy;
+        acc[R_BAD] += (!isfinite(drho) || !isfinite(u2) || u2 > u_max2) ? 1.0f : 0.0f;
+        acc[R_FLUID] += 1.0f;
+        ux4[j] = ux;
+        uy4[j] = uy;
+      }
+      if (update_prev) {
+        if (vec) {
+          // solid cells keep u_prev = 0, as set by the re-initialisation
+          *reinterpret_cast<float4*>(ux_prev + c0) = make_float4(ux4[0], ux4[1], ux4[2], ux4[3]);
+          *reinterpret_cast<float4*>(uy_prev + c0) = make_float4(uy4[0], uy4[1], uy4[2], uy4[3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < kVec; ++j)
+            if (x + j < nx) {
+              ux_prev[c0 + j] = ux4[j];
+              uy_prev[c0 + j] = uy4[j];
+            }
+        }
+      }
+    }
   }
-  v[R_N_W] = n_w;
-  v[R_N_E] = n_e;
-  v[R_BAD] = bad;
-  v[R_FLUID] = fluid;
-  block_reduce_store(v, partial + (size_t)blockIdx.x * R_COUNT);
+  // warp tree in FP32, then the block's warps in FP64
+#pragma unroll
+  for (int k = 0; k < R_COUNT; ++k) {
+    const float w = warp_sum(acc[k]);
+    if (lane == 0) red[warp][k] = (double)w;
+  }
+  __syncthreads();
+  if (threadIdx.x < R_COUNT) {
+    double a = 0.0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) a += red[w][threadIdx.x];
+    partial[(size_t)blockIdx.x * R_COUNT + threadIdx.x] = a;
+  }
 }
 
 __global__ void __launch_bounds__(kBlock) k_residual_final(const GridDev* __restrict__ grids,
@@ -735,11 +893,12 @@ __global__ void __launch_bounds__(kBlock) k_reinit(const GridDev* __restrict__ g
                                                    const float* __restrict__ rho_i,
                                                    const float* __restrict__ ux_i,
                                                    const float* __restrict__ uy_i, int neq_mode,
-                                                   float* __restrict__ state, float* ux_prev,
-                                                   float* uy_prev) {
+                                                   float* __restrict__ state,
+                                                   float* __restrict__ ux_prev,
+                                                   float* __restrict__ uy_prev) {
   int gidx, x, y;
   if (!cell_of_thread(grids, ngrids, gidx, x, y)) return;
-  const GridDev& G = grids[gidx];
+  const GridDev G = grids[gidx];  // registers: stores below cannot alias it
   const uint32_t* m = mask + G.mask_off;
   const long long c = (long long)y * G.nx + x;
   const float* R = rho_i + G.cell_off;
@@ -832,7 +991,7 @@ static int plan_layout(const lbm_grid* grids, int ngrids, lbm_layout* lay,
     d.nblk = (int)((d.plane + kBlock - 1) / kBlock);
     d.blk_start = (int)blk;
     d.nseg = (g.nx + kSeg - 1) / kSeg;
-    d.nrblk = (int)((d.plane + kBlock * kResCells - 1) / (kBlock * kResCells));
+    d.nrblk = (int)(((long long)d.nseg * g.ny + kBlock / 32 - 1) / (kBlock / 32));
     d.rblk_start = (int)rblk;
 
     d.ntiles = d.nseg * ((g.ny + kTY - 1) / kTY);
@@ -1106,7 +1265,7 @@ extern "C" int lbm_residual_static(lbm_handle* h, double* out_h, int update_prev
   const size_t need = stats_off + (size_t)h->ngrids * R_COUNT * sizeof(double);
   LBM_REQUIRE(need <= kResidualStaticBytes,
               "lbm_residual_static: batch needs %zu bytes of scratch, the static array holds "
-              "%zu (at most about %zu reduction blocks of 2048 cells); use lbm_residual",
+              "%zu (at most about %zu reduction blocks of 8 x 128 cells); use lbm_residual",
               need, kResidualStaticBytes, kResidualStaticBytes / (R_COUNT * sizeof(double)));
   int dev = 0;
   LBM_CHECK_CUDA(cudaGetDevice(&dev));

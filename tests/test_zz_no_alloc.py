@@ -75,7 +75,7 @@ def test_static_scratch_residual_matches_workspace_residual():
 
 def test_static_scratch_rejects_batches_beyond_its_size():
     _requires_gpu()
-    # 5000 x 5000 cells need ~12,300 reduction blocks of 2048 cells: more than 1 MiB of partials
+    # 5000 x 5000 cells need ~25,000 reduction blocks of 8 x 128 cells: more than 1 MiB of partials
     lat = Lattice([GridSpec(5000, 5000, 0.8)], [np.zeros((5000, 5000), bool)])
     code, _ = _static_call(lat, update_prev=0)
     assert code == _abi.LBM_ERR_INVALID_ARG
