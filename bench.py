@@ -90,6 +90,20 @@ def step_kernel_traffic(cells):
         return None
 
 
+def fno_flops(B, H, W, C=32, m=12, layers=4, cin=4, S=32, cout=3):
+    """Algorithmic FLOPs of one FNO forward (separable truncated DFTs, Sec. 2.2 layer equation)."""
+    px = B * H * W
+    layer = (2 * 2 * m * W * B * H * C          # forward x-DFT over the kept kx
+             + 8 * 2 * m * H * m * B * C        # forward y-DFT over the kept ky (complex)
+             + 8 * C * C * 2 * m * m * B        # per-mode complex channel mixing
+             + 8 * 2 * m * H * m * B * C        # inverse y-DFT
+             + 2 * 2 * m * W * B * H * C        # inverse x-DFT (real output)
+             + 2 * C * C * px)                  # 1x1 convolution W
+    lift = 2 * ((cin + 2) * C // 2 + C // 2 * C) * px
+    dec = 2 * (C * S + S * cout) * px
+    return layers * layer + lift + dec
+
+
 def workload(T, seed0):
     import synth
     masks, phis = [], []
@@ -299,6 +313,36 @@ def main():
                "plain_init": arms["plain"],
                "fno": "seeded random weights (no trained weights exist here)"}
 
+    # FNO throughput alone (B=32, 256x256, 4 channels -> 32 latent, 4 layers, 12x12 modes)
+    fno_tp = None
+    if rank == 0:
+        Bf, Hf, Wf = 32, 256, 256
+        xin = torch.randn((Bf, 4, Hf, Wf), device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+        yout = torch.empty((Bf, 3, Hf, Wf), device="cuda")
+        for _ in range(3):
+            net(xin, yout)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nf = 20
+        f0.record(stream)
+        for _ in range(nf):
+            net(xin, yout)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        net.check(Bf, Hf, Wf)
+        fms = f0.elapsed_time(f1) / nf
+        flops = fno_flops(Bf, Hf, Wf)
+        tf = flops / (fms * 1e-3) / 1e12
+        try:
+            pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+            tpeak, tkind = float(pk["bf16_tflops"]), "measured burst"
+        except Exception:
+            tpeak, tkind = 1900.0, "fallback"
+        fno_tp = {"workload": "FNO forward, batch 32 x 256 x 256, (rho-1, ux, uy, mask), 32 latent "
+                              "channels, 4 layers, 12x12 modes, decoder 32 -> 3, BF16 / FP32 accumulate",
+                  "ms_per_forward": fms, "gflop_per_forward": flops / 1e9, "tflops": tf,
+                  "tensor_peak_tflops": tpeak, "peak_kind": tkind, "frac_of_tensor_peak": tf / tpeak,
+                  "tensor_cores": bool(net.uses_tensor_cores(Hf, Wf))}
+
     # end to end through the public API with host buffers (pinned): masks in, fields out
     e2e = None
     if args.steps > 0:
@@ -348,6 +392,7 @@ def main():
             "solve": {"lbm_steps": steps_per_solve, "converged": bool(st.converged),
                       "max_residual": float(st.max_residual)},
             "time_to_steady": tts,
+            "fno_throughput": fno_tp,
             "gpu_launches": None,
             "clocks": clk.summary(),
             "e2e": e2e,

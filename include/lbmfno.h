@@ -231,6 +231,18 @@ int fno_forward(fno_handle* h, const float* in_d, float* out_d, int B, int H, in
 /* Configuration the handle was created with. */
 int fno_get_config(const fno_handle* h, fno_config* out_h);
 
+/* Kernel path.  FNO_PATH_AUTO (default): tcgen05 tensor-core kernels where the
+ * shape allows (C in {16, 32, 64}, m <= 16, W a multiple of 128, W <= 2048),
+ * CUDA-core kernels otherwise.  FNO_PATH_CUDA_CORES: always the CUDA-core
+ * kernels (same results up to rounding). */
+enum fno_path { FNO_PATH_AUTO = 0, FNO_PATH_CUDA_CORES = 1 };
+int fno_set_path(fno_handle* h, int path);
+/* *out_h = 1 when fno_forward(B, H, W) runs the tensor-core kernels. */
+int fno_uses_tensor_cores(const fno_handle* h, int H, int W, int* out_h);
+/* Synchronise `stream` and report a device-side wait that expired during the
+ * last fno_forward(B, H, W) on workspace ws_d (LBM_ERR_TIMEOUT), else LBM_OK. */
+int fno_check(const fno_handle* h, const void* ws_d, int B, int H, int W, void* stream);
+
 int fno_destroy(fno_handle* h);
 
 /* ======================================================================

@@ -68,6 +68,7 @@ class hybrid_stats(ctypes.Structure):
 
 
 FNO_ACT_GELU, FNO_ACT_RELU = 0, 1
+FNO_PATH_AUTO, FNO_PATH_CUDA_CORES = 0, 1
 HYBRID_STEADY, HYBRID_UNSTEADY = 0, 1
 
 VP = ctypes.c_void_p
@@ -90,6 +91,9 @@ _PROTOS = {
     "fno_create": ([ctypes.POINTER(fno_config), VP, VP, VP, ctypes.POINTER(VP)], I),
     "fno_forward": ([VP, VP, VP, I, I, I, VP, ctypes.c_size_t, VP], I),
     "fno_get_config": ([VP, ctypes.POINTER(fno_config)], I),
+    "fno_set_path": ([VP, I], I),
+    "fno_uses_tensor_cores": ([VP, I, I, ctypes.POINTER(I)], I),
+    "fno_check": ([VP, VP, I, I, I, VP], I),
     "fno_destroy": ([VP], I),
     "hybrid_query_ws": ([ctypes.POINTER(lbm_grid), I, ctypes.POINTER(fno_config),
                          ctypes.POINTER(ctypes.c_size_t)], I),

@@ -19,6 +19,8 @@
 #include <vector>
 
 #include "common.cuh"
+#include "fno_tc.cuh"
+#include "sm100.cuh"
 
 namespace lbmfno {
 
@@ -364,6 +366,7 @@ struct fno_handle {
   FnoOffsets off;
   float* packed = nullptr;  // caller-owned
   unsigned* dec_offs = nullptr;  // inside packed: decoder offsets table (as floats' bits)
+  bool force_cuda_cores = false;  // use the CUDA-core kernels even where tensor cores apply
 };
 
 static inline cudaStream_t SS(void* s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -379,7 +382,10 @@ int fno_query(const fno_config* cfg_h, int B, int H, int W, fno_sizes* out_h) {
               "fno_query: need 2m <= H and m < W/2 (m=%d, H=%d, W=%d)", cfg_h->modes, H, W);
   out_h->n_params = o.n_params;
   out_h->packed_bytes = align_up((o.total_floats + 64) * sizeof(float), 256);
-  out_h->ws_bytes = fno_ws_plan(*cfg_h, std::max(B, 1), H, W).total;
+  out_h->ws_bytes = std::max(fno_ws_plan(*cfg_h, std::max(B, 1), H, W).total,
+                             fno_tc_supported(*cfg_h, H, W)
+                                 ? fno_tc_ws_plan(*cfg_h, std::max(B, 1), H, W).total
+                                 : (size_t)0);
   return LBM_OK;
 }
 
@@ -402,7 +408,8 @@ int fno_create(const fno_config* cfg_h, const uint16_t* params_d, void* packed_d
   if (cudaFuncSetAttribute(k_fwd_x, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kRowSmemMax) != cudaSuccess ||
       cudaFuncSetAttribute(k_inv_x_w, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kRowSmemMax) != cudaSuccess) {
+                           (int)kRowSmemMax) != cudaSuccess ||
+      fno_tc_prepare(*cfg_h) != LBM_OK) {
     set_error("fno_create: %s", cudaGetErrorString(cudaGetLastError()));
     delete h;
     return LBM_ERR_CUDA;
@@ -445,6 +452,24 @@ int fno_forward(fno_handle* h, const float* in_d, float* out_d, int B, int H, in
   LBM_REQUIRE(ws_bytes >= wp.total, "fno_forward: workspace too small (%zu < %zu)", ws_bytes,
               wp.total);
   LBM_REQUIRE(((uintptr_t)ws_d % 256) == 0, "fno_forward: workspace must be 256-byte aligned");
+  if (fno_tc_supported(c, H, W) && !h->force_cuda_cores) {
+    LBM_REQUIRE(ws_bytes >= fno_tc_ws_plan(c, B, H, W).total, "fno_forward: workspace too small");
+    FnoTcParams tp{};
+    const float* P0 = h->packed;
+    const FnoOffsets& o0 = h->off;
+    tp.lift0_w = P0 + o0.lift0_w;
+    tp.lift0_b = P0 + o0.lift0_b;
+    tp.lift1_w = P0 + o0.lift1_w;
+    tp.lift1_b = P0 + o0.lift1_b;
+    for (int n = 0; n < c.layers; ++n) {
+      tp.rt[n] = reinterpret_cast<const float2*>(P0 + o0.rt_off + o0.rt_layer * n);
+      tp.w[n] = P0 + o0.w[n];
+      tp.b[n] = P0 + o0.b[n];
+    }
+    tp.params = P0;
+    tp.dec_offs = h->dec_offs;
+    return fno_forward_tc(c, tp, in_d, out_d, B, H, W, static_cast<char*>(ws_d), SS(stream));
+  }
   char* ws = static_cast<char*>(ws_d);
   __nv_bfloat16* th[2] = {reinterpret_cast<__nv_bfloat16*>(ws + wp.theta0),
                           reinterpret_cast<__nv_bfloat16*>(ws + wp.theta1)};
@@ -488,6 +513,36 @@ int fno_forward(fno_handle* h, const float* in_d, float* out_d, int B, int H, in
                                                           c.dec_layers, B, H, W, C, c.dec_size,
                                                           c.c_out, c.activation);
   LBM_CHECK_LAUNCH();
+  return LBM_OK;
+}
+
+int fno_set_path(fno_handle* h, int path) {
+  LBM_REQUIRE(h != nullptr && (path == FNO_PATH_AUTO || path == FNO_PATH_CUDA_CORES),
+              "fno_set_path: bad arguments");
+  h->force_cuda_cores = path == FNO_PATH_CUDA_CORES;
+  return LBM_OK;
+}
+
+int fno_uses_tensor_cores(const fno_handle* h, int H, int W, int* out_h) {
+  LBM_REQUIRE(h != nullptr && out_h != nullptr, "fno_uses_tensor_cores: bad arguments");
+  *out_h = (!h->force_cuda_cores && fno_tc_supported(h->cfg, H, W)) ? 1 : 0;
+  return LBM_OK;
+}
+
+int fno_check(const fno_handle* h, const void* ws_d, int B, int H, int W, void* stream) {
+  LBM_REQUIRE(h != nullptr && ws_d != nullptr, "fno_check: bad arguments");
+  cudaStream_t s = SS(stream);
+  LBM_CHECK_CUDA(cudaStreamSynchronize(s));
+  if (!h->force_cuda_cores && fno_tc_supported(h->cfg, H, W)) {
+    const FnoTcWs wp = fno_tc_ws_plan(h->cfg, B, H, W);
+    unsigned st = 0;
+    LBM_CHECK_CUDA(cudaMemcpy(&st, static_cast<const char*>(ws_d) + wp.status, sizeof(unsigned),
+                              cudaMemcpyDeviceToHost));
+    if (st & kStatusTimeout) {
+      set_error("fno: a device-side wait expired (status 0x%x)", st);
+      return LBM_ERR_TIMEOUT;
+    }
+  }
   return LBM_OK;
 }
 

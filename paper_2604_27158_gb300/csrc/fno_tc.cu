@@ -1,0 +1,751 @@
+// Tensor-core (tcgen05) path of the FNO forward pass (Sec. 2.2 of arXiv 2604.27158).
+//
+// Latent field layout ("channel-blocked"): theta[b][y][c/8][x][c%8] bfloat16, so a
+// run of x positions of one 8-channel group is contiguous and every operand tile
+// is a set of contiguous 128-byte core matrices (no swizzle).
+//
+// One Fourier layer  theta' = act(W theta + F^-1(R . F(theta)) + bias):
+//  1. k_fwd_x_tc   X1[b][y][kx][c] = sum_x theta[x][c] e^{-2 pi i kx x / W}
+//                  tcgen05: D[(row, c)][kx re|im] = A[(row, c)][x] * Fw[x][kx re|im]
+//                  (M = 128 = 128/C rows x C channels, N = 32, K = W; A MN-major)
+//  2. k_spec_fwd   per (b, kx): y-DFT over the kept ky, then the per-mode complex
+//                  channel mixing -> Yh[b][a][kx][o]            (CUDA cores)
+//  3. k_spec_inv   per (b, row block): inverse y-DFT -> Zt[b][y][k'/8][o][k'%8]
+//                  (bfloat16, k' < m real parts, m <= k' < 2m imaginary parts)
+//  4. k_inv_x_tc   theta'[x][o] = act( sum_k' T[x][k'] Zt[k'][o] + sum_i theta[x][i] W[o][i] + b[o] )
+//                  tcgen05: D[x][o] = [T | theta][x][k] * [Zt ; W^T][k][o]
+//                  (M = 128 x positions, N = C, K = 32 + C; both operands K-major)
+// T folds 1/(H W) and the real-input inverse weights (1 for kx = 0, 2 otherwise).
+//
+// The tcgen05 kernels are persistent and warp-specialised: warps 0-3 drain the
+// TMEM accumulator (epilogue), warp 4 streams operand tiles with cp.async.bulk
+// into a ring of shared-memory stages, warp 5 issues the MMAs.  Two TMEM
+// accumulators let the epilogue of one tile overlap the MMAs of the next.  Every
+// wait is bounded and records a timeout in the status word.
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "fno_tc.cuh"
+#include "sm100.cuh"
+
+namespace lbmfno {
+
+__device__ __forceinline__ float act_tc(float v, int act) {
+  return act == FNO_ACT_GELU ? 0.5f * v * (1.0f + erff(v * 0.70710678118654752f)) : fmaxf(v, 0.0f);
+}
+__device__ __forceinline__ int kept_ky_tc(int a, int H, int m) { return a < m ? a : H - 2 * m + a; }
+
+// ------------------------------------------------------------------ tables
+// Fw[x/8][n][x%8]: n < m: cos(2 pi n x / W); m <= n < 2m: -sin(2 pi (n-m) x / W); else 0.
+__global__ void k_table_fwd(__nv_bfloat16* __restrict__ fw, int W, int m) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= W * 32) return;
+  const int xl = t & 7, n = (t >> 3) & 31, xh = t >> 8;
+  const int x = xh * 8 + xl;
+  float v = 0.0f;
+  if (n < 2 * m) {
+    const int k = n < m ? n : n - m;
+    double s, c;
+    sincospi(2.0 * (double)((long long)k * x % W) / (double)W, &s, &c);
+    v = n < m ? (float)c : (float)(-s);
+  }
+  fw[t] = __float2bfloat16_rn(v);
+}
+// Ti[k'/8][x][k'%8]: k' < m: c_k cos(2 pi k' x / W) / (H W); m <= k' < 2m:
+// -c_k sin(2 pi (k'-m) x / W) / (H W); else 0; c_0 = 1, c_k = 2 (k > 0).
+__global__ void k_table_inv(__nv_bfloat16* __restrict__ ti, int H, int W, int m) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= W * 32) return;
+  const int kl = t & 7, x = (t >> 3) % W, kh = (t >> 3) / W;
+  const int kp = kh * 8 + kl;
+  float v = 0.0f;
+  if (kp < 2 * m) {
+    const int k = kp < m ? kp : kp - m;
+    double s, c;
+    sincospi(2.0 * (double)((long long)k * x % W) / (double)W, &s, &c);
+    const double w = (k == 0 ? 1.0 : 2.0) / ((double)H * (double)W);
+    v = kp < m ? (float)(w * c) : (float)(-w * s);
+  }
+  ti[t] = __float2bfloat16_rn(v);
+}
+// tw[t] = (cos, sin)(2 pi t / N)
+__global__ void k_twiddle_tc(float2* __restrict__ tw, int N) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < N) {
+    double s, c;
+    sincospi(2.0 * (double)t / (double)N, &s, &c);
+    tw[t] = make_float2((float)c, (float)s);
+  }
+}
+
+// ---------------------------------------------------- lifting / projection
+// Lifting network P (1x1, (c_in + 2) -> C/2 -> act -> C); one thread per pixel,
+// weights staged in shared memory (broadcast reads).
+template <int kC, int kCin>
+__global__ void __launch_bounds__(128)
+    k_lift_blk(const float* __restrict__ in, __nv_bfloat16* __restrict__ theta,
+               const float* __restrict__ w0, const float* __restrict__ b0,
+               const float* __restrict__ w1, const float* __restrict__ b1, int B, int H, int W,
+               int cin_rt, int act) {
+  // kCin > 0: compile-time input channel count (registers); 0: runtime count
+  const int cin = kCin > 0 ? kCin : cin_rt;
+  __shared__ float s_w0[(kC / 2) * 18], s_b0[kC / 2], s_w1[kC * (kC / 2)], s_b1[kC];
+  const int cin2 = cin + 2;
+  for (int t = threadIdx.x; t < (kC / 2) * cin2; t += blockDim.x) s_w0[t] = w0[t];
+  for (int t = threadIdx.x; t < kC / 2; t += blockDim.x) s_b0[t] = b0[t];
+  for (int t = threadIdx.x; t < kC * (kC / 2); t += blockDim.x) s_w1[t] = w1[t];
+  for (int t = threadIdx.x; t < kC; t += blockDim.x) s_b1[t] = b1[t];
+  __syncthreads();
+  const size_t pix = (size_t)B * H * W;
+  const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (p >= pix) return;
+  const int x = (int)(p % W);
+  const size_t row = p / W;  // b * H + y
+  const int y = (int)(row % H);
+  const int b = (int)(row / H);
+  float xin[kCin > 0 ? kCin + 2 : 18];
+#pragma unroll
+  for (int c = 0; c < (kCin > 0 ? kCin : 16); ++c)
+    if (c < cin)
+      xin[c] = __bfloat162float(__float2bfloat16_rn(in[(((size_t)b * cin + c) * H + y) * W + x]));
+  xin[cin] = __bfloat162float(__float2bfloat16_rn((float)x / (float)max(W - 1, 1)));
+  xin[cin + 1] = __bfloat162float(__float2bfloat16_rn((float)y / (float)max(H - 1, 1)));
+  float hid[kC / 2];
+#pragma unroll
+  for (int j = 0; j < kC / 2; ++j) {
+    float a = s_b0[j];
+#pragma unroll
+    for (int c = 0; c < (kCin > 0 ? kCin + 2 : 18); ++c)
+      if (c < cin2) a = fmaf(s_w0[j * cin2 + c], xin[c], a);
+    hid[j] = act_tc(a, act);
+  }
+#pragma unroll
+  for (int g = 0; g < kC / 8; ++g) {
+    __align__(16) __nv_bfloat16 o8[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int o = g * 8 + q;
+      float a = s_b1[o];
+#pragma unroll
+      for (int j = 0; j < kC / 2; ++j) a = fmaf(s_w1[o * (kC / 2) + j], hid[j], a);
+      o8[q] = __float2bfloat16_rn(a);
+    }
+    *reinterpret_cast<uint4*>(theta + ((row * (kC / 8) + g) * W + x) * 8) =
+        *reinterpret_cast<const uint4*>(o8);
+  }
+}
+
+// Projection Q from the channel-blocked field; one thread per pixel, decoder
+// weights staged in shared memory.  kS > 0: one hidden layer of width kS and
+// kOut outputs, fully unrolled (registers); kS == 0: any decoder shape.
+template <int kC, int kS, int kOut>
+__global__ void __launch_bounds__(128)
+    k_decoder_blk(const __nv_bfloat16* __restrict__ theta, float* __restrict__ out,
+                  const float* __restrict__ params, const unsigned* __restrict__ offs,
+                  int nlayers, int B, int H, int W, int S, int cout, int act) {
+  extern __shared__ float dec_s[];
+  // layout: for each layer l: w [S][fan] then b [S]; then out.w [cout][fan], out.b [cout]
+  int at = 0, fan = kC;
+  for (int l = 0; l <= nlayers; ++l) {
+    const int rows = l < nlayers ? S : cout;
+    const float* w = params + offs[2 * l];
+    const float* bb = params + offs[2 * l + 1];
+    for (int t = threadIdx.x; t < rows * fan; t += blockDim.x) dec_s[at + t] = w[t];
+    for (int t = threadIdx.x; t < rows; t += blockDim.x) dec_s[at + rows * fan + t] = bb[t];
+    at += rows * fan + rows;
+    fan = S;
+  }
+  __syncthreads();
+  const size_t pix = (size_t)B * H * W;
+  const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (p >= pix) return;
+  const int x = (int)(p % W);
+  const size_t row = p / W;
+  const int y = (int)(row % H);
+  const int b = (int)(row / H);
+  float a[kC];
+#pragma unroll
+  for (int g = 0; g < kC / 8; ++g) {
+    const uint4 v = *reinterpret_cast<const uint4*>(theta + ((row * (kC / 8) + g) * W + x) * 8);
+    const __nv_bfloat16* hv = reinterpret_cast<const __nv_bfloat16*>(&v);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a[g * 8 + q] = __bfloat162float(hv[q]);
+  }
+  if constexpr (kS > 0) {
+    const float* w1 = dec_s;
+    const float* b1 = w1 + kS * kC;
+    const float* w2 = b1 + kS;
+    const float* b2 = w2 + kOut * kS;
+    float o[kOut];
+#pragma unroll
+    for (int q = 0; q < kOut; ++q) o[q] = b2[q];
+#pragma unroll 4
+    for (int j = 0; j < kS; ++j) {
+      float v = b1[j];
+#pragma unroll
+      for (int c = 0; c < kC; ++c) v = fmaf(w1[j * kC + c], a[c], v);
+      v = act_tc(v, act);
+#pragma unroll
+      for (int q = 0; q < kOut; ++q) o[q] = fmaf(w2[q * kS + j], v, o[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < kOut; ++q) out[(((size_t)b * kOut + q) * H + y) * W + x] = o[q];
+  } else {
+    float h[64], t[64];
+#pragma unroll
+    for (int c = 0; c < kC; ++c) h[c] = a[c];
+    at = 0;
+    fan = kC;
+    for (int l = 0; l < nlayers; ++l) {
+      const float* w = dec_s + at;
+      const float* bb = w + S * fan;
+      for (int j = 0; j < S; ++j) {
+        float v = bb[j];
+        for (int c = 0; c < fan; ++c) v = fmaf(w[j * fan + c], h[c], v);
+        t[j] = act_tc(v, act);
+      }
+      for (int j = 0; j < S; ++j) h[j] = t[j];
+      at += S * fan + S;
+      fan = S;
+    }
+    const float* w = dec_s + at;
+    const float* bb = w + cout * fan;
+    for (int q = 0; q < cout; ++q) {
+      float v = bb[q];
+      for (int c = 0; c < fan; ++c) v = fmaf(w[q * fan + c], h[c], v);
+      out[(((size_t)b * cout + q) * H + y) * W + x] = v;
+    }
+  }
+}
+
+// --------------------------------------------------- 1. forward x-DFT (tcgen05)
+constexpr int kTcThreads = 192;  // warps 0-3 epilogue, 4 producer, 5 MMA
+constexpr int kFwdChunk = 64;    // x positions per stage
+constexpr int kFwdStages = 3;
+constexpr int kFwdStageBytes = 128 * kFwdChunk * 2;  // 16 KB: 128 (row, channel) x 64 x
+
+template <int kC>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_fwd_x_tc(const __nv_bfloat16* __restrict__ theta, const __nv_bfloat16* __restrict__ fw,
+               float2* __restrict__ x1, int B, int H, int W, int m,
+               unsigned* __restrict__ status) {
+  constexpr int kRows = 128 / kC;  // image rows per tile
+  constexpr int kG = kC / 8;       // 8-channel groups
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* fw_s = smem;                                // W * 64 bytes
+  unsigned char* stages = smem + (size_t)W * 64;             // kFwdStages * 16 KB
+  __shared__ __align__(8) uint64_t full_bar[kFwdStages], empty_bar[kFwdStages];
+  __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], fw_bar;
+  __shared__ uint32_t tmem_base;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ytiles = (H + kRows - 1) / kRows;
+  const int ntiles = B * ytiles;
+  const int nchunks = W / kFwdChunk;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kFwdStages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], 4);
+    }
+    mbar_init(&fw_bar, 1);
+    mbar_init_fence();
+  }
+  if (warp == 0) tmem_alloc(&tmem_base, 64);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 4) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      mbar_arrive_expect_tx(&fw_bar, (unsigned)(W * 64));
+      bulk_g2s(fw_s, fw, (unsigned)(W * 64), &fw_bar);
+    }
+    __syncwarp();
+    int k = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const int b = t / ytiles, y0 = (t - b * ytiles) * kRows;
+      const int rows = min(kRows, H - y0);
+      for (int ch = 0; ch < nchunks; ++ch, ++k) {
+        const int s = k % kFwdStages;
+        if (k >= kFwdStages) ok = mbar_wait(&empty_bar[s], ((k / kFwdStages) - 1) & 1, status);
+        if (!ok) break;
+        unsigned char* st = stages + (size_t)s * kFwdStageBytes;
+        if (lane == 0) mbar_arrive_expect_tx(&full_bar[s], (unsigned)(rows * kG * kFwdChunk * 16));
+        __syncwarp();
+        for (int q = lane; q < rows * kG; q += 32) {
+          const int r = q / kG, g = q - r * kG;
+          const __nv_bfloat16* src =
+              theta + ((((size_t)b * H + y0 + r) * kG + g) * W + (size_t)ch * kFwdChunk) * 8;
+          bulk_g2s(st + (size_t)q * kFwdChunk * 16, src, kFwdChunk * 16, &full_bar[s]);
+        }
+      }
+    }
+    // no copy may still be in flight when the CTA exits
+    mbar_wait(&fw_bar, 0, status);
+    for (int q = max(0, k - kFwdStages); q < k; ++q)
+      mbar_wait(&full_bar[q % kFwdStages], (q / kFwdStages) & 1, status);
+  } else if (warp == 5) {
+    // ---------------------------------------------------------------- MMA
+    constexpr uint32_t idesc = idesc_bf16(128, 32, /*a_mn=*/true, /*b_mn=*/false);
+    bool ok = mbar_wait(&fw_bar, 0, status);
+    int k = 0, j = 0;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++j) {
+      const int acc = j & 1;
+      if (j >= 2) ok = mbar_wait(&acc_empty[acc], ((j >> 1) - 1) & 1, status);
+      if (!ok) break;
+      tc_fence_after();
+      for (int ch = 0; ch < nchunks; ++ch, ++k) {
+        const int s = k % kFwdStages;
+        ok = mbar_wait(&full_bar[s], (k / kFwdStages) & 1, status);
+        if (!ok) break;
+        tc_fence_after();
+        if (lane == 0) {
+          const unsigned char* st = stages + (size_t)s * kFwdStageBytes;
+#pragma unroll
+          for (int kk = 0; kk < kFwdChunk / 16; ++kk) {
+            // A: MN-major, K-adjacent core matrices 128 B apart, MN-adjacent 1024 B
+            const uint64_t ad = smem_desc(st + kk * 256, 128, kFwdChunk * 16);
+            // B: K-major, K-adjacent core matrices 512 B apart, N-adjacent 128 B
+            const uint64_t bd = smem_desc(fw_s + (size_t)((ch * kFwdChunk + kk * 16) / 8) * 512, 512, 128);
+            mma_bf16(tmem + acc * 32, ad, bd, idesc, ch > 0 || kk > 0);
+          }
+          mma_commit(&empty_bar[s]);  // stage reusable once these MMAs have read it
+        }
+        __syncwarp();
+      }
+      if (!ok) break;
+      if (lane == 0) mma_commit(&acc_full[acc]);
+      __syncwarp();
+    }
+  } else {
+    // ----------------------------------------------------------- epilogue
+    int j = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+      const int acc = j & 1;
+      if (!mbar_wait(&acc_full[acc], (j >> 1) & 1, status)) break;
+      tc_fence_after();
+      float v[32];
+      tmem_ld32(tmem + acc * 32 + ((uint32_t)(warp * 32) << 16), v);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[acc]);
+      const int b = t / ytiles, y0 = (t - b * ytiles) * kRows;
+      const int mi = warp * 32 + lane;  // accumulator row = r * C + c
+      const int r = mi / kC, c = mi - r * kC;
+      const int y = y0 + r;
+      if (y < H) {
+        float2* o = x1 + (((size_t)b * H + y) * m) * kC + c;
+        for (int kx = 0; kx < m; ++kx) o[(size_t)kx * kC] = make_float2(v[kx], v[m + kx]);
+      }
+    }
+  }
+  // all MMAs of this CTA have completed once the epilogue has drained (or timed out)
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, 64);
+}
+
+// ------------------------------------- 2. y-DFT + per-mode mixing (CUDA cores)
+// One block per (b, kx).  Xh[a][c] = sum_y X1[b][y][kx][c] e^{-2 pi i ky(a) y / H};
+// Yh[b][a][kx][o] = sum_c Xh[a][c] R[a * m + kx][c][o].
+template <int kC>
+__global__ void __launch_bounds__(256)
+    k_spec_fwd(const float2* __restrict__ x1, const float2* __restrict__ rt,
+               float2* __restrict__ yh, const float2* __restrict__ twy, int H, int m) {
+  extern __shared__ float2 sm2[];
+  float2* col = sm2;                  // H * kC
+  float2* tw = col + (size_t)H * kC;  // H
+  float2* xh = tw + H;                // 2m * kC
+  const int b = blockIdx.x / m, kx = blockIdx.x % m;
+  for (int t = threadIdx.x; t < H * kC; t += blockDim.x) {
+    const int y = t / kC, c = t - y * kC;
+    col[t] = x1[(((size_t)b * H + y) * m + kx) * kC + c];
+  }
+  for (int t = threadIdx.x; t < H; t += blockDim.x) tw[t] = twy[t];
+  __syncthreads();
+  constexpr int kGroups = 256 / kC;
+  constexpr int kMaxA = (32 + kGroups - 1) / kGroups;  // kept ky per thread (2m <= 32)
+  const int c = threadIdx.x % kC, g0 = threadIdx.x / kC;
+  float re[kMaxA], im[kMaxA];
+  int idx[kMaxA], step[kMaxA];
+#pragma unroll
+  for (int q = 0; q < kMaxA; ++q) {
+    re[q] = 0.f;
+    im[q] = 0.f;
+    idx[q] = 0;
+    const int a = g0 + q * kGroups;
+    step[q] = a < 2 * m ? kept_ky_tc(a, H, m) : 0;
+  }
+#pragma unroll 2
+  for (int y = 0; y < H; ++y) {
+    const float2 v = col[y * kC + c];
+#pragma unroll
+    for (int q = 0; q < kMaxA; ++q) {
+      const float2 e = tw[idx[q]];  // e^{-i phi} = cos - i sin
+      re[q] = fmaf(v.x, e.x, fmaf(v.y, e.y, re[q]));
+      im[q] = fmaf(v.y, e.x, fmaf(-v.x, e.y, im[q]));
+      idx[q] += step[q];
+      if (idx[q] >= H) idx[q] -= H;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kMaxA; ++q) {
+    const int a = g0 + q * kGroups;
+    if (a < 2 * m) xh[a * kC + c] = make_float2(re[q], im[q]);
+  }
+  __syncthreads();
+  const int o = threadIdx.x % kC;
+  for (int a = g0; a < 2 * m; a += kGroups) {
+    const float2* r = rt + ((size_t)(a * m + kx) * kC) * kC + o;
+    float re = 0.f, im = 0.f;
+#pragma unroll 8
+    for (int i = 0; i < kC; ++i) {
+      const float2 xv = xh[a * kC + i];
+      const float2 w = r[(size_t)i * kC];
+      re = fmaf(xv.x, w.x, fmaf(-xv.y, w.y, re));
+      im = fmaf(xv.x, w.y, fmaf(xv.y, w.x, im));
+    }
+    yh[(((size_t)b * 2 * m + a) * m + kx) * kC + o] = make_float2(re, im);
+  }
+}
+
+// ------------------------------------------------ 3. inverse y-DFT (CUDA cores)
+// One block per (b, block of kSpecRows rows).  Zt[b][y][k'/8][o][k'%8] (bf16):
+// k' < m: Re Z(kx = k'), m <= k' < 2m: Im Z(kx = k' - m), else 0, with
+// Z[kx][o] = sum_a Yh[b][a][kx][o] e^{+2 pi i ky(a) y / H}.  The block stages Yh[b]
+// and the e^{+i phi} factors of its rows in shared memory; each thread forms
+// complete complex sums and writes both halves.
+constexpr int kSpecRows = 16;
+template <int kC>
+__global__ void __launch_bounds__(256)
+    k_spec_inv(const float2* __restrict__ yh, __nv_bfloat16* __restrict__ zt,
+               const float2* __restrict__ twy, int H, int m) {
+  extern __shared__ float2 sm2[];
+  float2* ys = sm2;                              // 2m * m * kC
+  float2* ph = ys + (size_t)2 * m * m * kC;      // kSpecRows * 2m factors
+  const int nblk = (H + kSpecRows - 1) / kSpecRows;
+  const int b = blockIdx.x / nblk, y0 = (blockIdx.x - b * nblk) * kSpecRows;
+  const int n = 2 * m * m * kC;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) ys[t] = yh[(size_t)b * n + t];
+  for (int t = threadIdx.x; t < kSpecRows * 2 * m; t += blockDim.x) {
+    const int rr = t / (2 * m), a = t - rr * 2 * m;
+    const int y = min(y0 + rr, H - 1);
+    ph[t] = twy[(int)(((long long)kept_ky_tc(a, H, m) * y) % H)];
+  }
+  __syncthreads();
+  constexpr int kRow = 32 * kC;  // bf16 entries of one Zt row (k' padded to 32)
+  // zero the padding k' in [2m, 32) of this block's rows
+  for (int e = threadIdx.x; e < kSpecRows * kRow; e += blockDim.x) {
+    const int rr = e / kRow, q = e - rr * kRow;
+    const int kp = (q / (kC * 8)) * 8 + (q % 8);
+    if (y0 + rr < H && kp >= 2 * m) zt[((size_t)b * H + y0 + rr) * kRow + q] = __float2bfloat16_rn(0.0f);
+  }
+  for (int e = threadIdx.x; e < m * kC; e += blockDim.x) {
+    const int kx = e / kC, o = e - kx * kC;
+    float re[kSpecRows], im[kSpecRows];
+#pragma unroll
+    for (int rr = 0; rr < kSpecRows; ++rr) {
+      re[rr] = 0.f;
+      im[rr] = 0.f;
+    }
+    for (int a = 0; a < 2 * m; ++a) {
+      const float2 w = ys[((size_t)a * m + kx) * kC + o];
+#pragma unroll
+      for (int rr = 0; rr < kSpecRows; ++rr) {
+        const float2 e2 = ph[rr * 2 * m + a];  // e^{+i phi}, broadcast
+        re[rr] = fmaf(w.x, e2.x, fmaf(-w.y, e2.y, re[rr]));
+        im[rr] = fmaf(w.x, e2.y, fmaf(w.y, e2.x, im[rr]));
+      }
+    }
+    const int kr = kx, ki = m + kx;
+#pragma unroll
+    for (int rr = 0; rr < kSpecRows; ++rr) {
+      const int y = y0 + rr;
+      if (y >= H) break;
+      __nv_bfloat16* row = zt + ((size_t)b * H + y) * kRow;
+      row[((kr / 8) * kC + o) * 8 + (kr % 8)] = __float2bfloat16_rn(re[rr]);
+      row[((ki / 8) * kC + o) * 8 + (ki % 8)] = __float2bfloat16_rn(im[rr]);
+    }
+  }
+}
+
+// ------------------------ 4. inverse x-DFT + W theta + bias + activation (tcgen05)
+constexpr int kInvStages = 4;
+constexpr int kInvEpiWarps = 8;  // two warps per TMEM lane quadrant, each half of the columns
+constexpr int kInvThreads = (kInvEpiWarps + 2) * 32;
+
+template <int kC>
+__global__ void __launch_bounds__(kInvThreads, 1)
+    k_inv_x_tc(const __nv_bfloat16* __restrict__ theta, const __nv_bfloat16* __restrict__ ti,
+               const __nv_bfloat16* __restrict__ zt, const float* __restrict__ wmat,
+               const float* __restrict__ bias, __nv_bfloat16* __restrict__ out, int B, int H,
+               int W, int act, unsigned* __restrict__ status) {
+  constexpr int kG = kC / 8;
+  constexpr int kKG = 4 + kG;                 // K groups of 8: 4 spectral (k' < 32) + C channels
+  constexpr int kABytes = kKG * 128 * 16;     // A: [k group][x (128)][8]
+  constexpr int kBBytes = kKG * kC * 16;      // B: [k group][o (C)][8]
+  constexpr int kStageBytes = kABytes + kBBytes;
+  constexpr int kAccCols = kC < 32 ? 32 : kC;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full_bar[kInvStages], empty_bar[kInvStages];
+  __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ float bias_s[kC];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int xt = W / 128;
+  const int ntiles = B * H * xt;
+
+  // the W^T half of every stage's B operand is constant: fill it once
+  for (int e = threadIdx.x; e < kInvStages * kG * kC * 8; e += blockDim.x) {
+    const int s = e / (kG * kC * 8), q = e - s * (kG * kC * 8);
+    const int g = q / (kC * 8), o = (q / 8) % kC, il = q % 8;
+    __nv_bfloat16* bq = reinterpret_cast<__nv_bfloat16*>(smem + (size_t)s * kStageBytes + kABytes);
+    bq[(4 + g) * kC * 8 + o * 8 + il] = __float2bfloat16_rn(wmat[o * kC + g * 8 + il]);
+  }
+  for (int o = threadIdx.x; o < kC; o += blockDim.x) bias_s[o] = bias[o];
+  fence_proxy_async_smem();
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kInvStages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], kInvEpiWarps);
+    }
+    mbar_init_fence();
+  }
+  if (warp == 0) tmem_alloc(&tmem_base, 2 * kAccCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == kInvEpiWarps) {
+    // ------------------------------------------------------------ producer
+    int k = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+      const int s = k % kInvStages;
+      if (k >= kInvStages) ok = mbar_wait(&empty_bar[s], ((k / kInvStages) - 1) & 1, status);
+      if (!ok) break;
+      const int row = t / xt;  // b * H + y
+      const int x0 = (t - row * xt) * 128;
+      unsigned char* st = smem + (size_t)s * kStageBytes;
+      if (lane == 0) mbar_arrive_expect_tx(&full_bar[s], (unsigned)(kKG * 128 * 16 + 4 * kC * 16));
+      __syncwarp();
+      if (lane < 4) {  // inverse-DFT table, k group = lane
+        bulk_g2s(st + lane * 2048, ti + ((size_t)lane * W + x0) * 8, 2048, &full_bar[s]);
+      } else if (lane < 4 + kG) {  // latent channels, group lane - 4
+        const int g = lane - 4;
+        bulk_g2s(st + lane * 2048, theta + (((size_t)row * kG + g) * W + x0) * 8, 2048,
+                 &full_bar[s]);
+      } else if (lane == 4 + kG) {  // spectral half of B: Zt row
+        bulk_g2s(st + kABytes, zt + (size_t)row * 32 * kC, 4 * kC * 16, &full_bar[s]);
+      }
+    }
+    for (int q = max(0, k - kInvStages); q < k; ++q)
+      mbar_wait(&full_bar[q % kInvStages], (q / kInvStages) & 1, status);
+  } else if (warp == kInvEpiWarps + 1) {
+    // ---------------------------------------------------------------- MMA
+    constexpr uint32_t idesc = idesc_bf16(128, kC, false, false);
+    int j = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+      const int acc = j & 1;
+      if (j >= 2) ok = mbar_wait(&acc_empty[acc], ((j >> 1) - 1) & 1, status);
+      if (ok) ok = mbar_wait(&full_bar[j % kInvStages], (j / kInvStages) & 1, status);
+      if (!ok) break;
+      tc_fence_after();
+      if (lane == 0) {
+        const unsigned char* st = smem + (size_t)(j % kInvStages) * kStageBytes;
+#pragma unroll
+        for (int kk = 0; kk < kKG / 2; ++kk) {
+          const uint64_t ad = smem_desc(st + kk * 2 * 2048, 2048, 128);
+          const uint64_t bd = smem_desc(st + kABytes + kk * 2 * kC * 16, kC * 16, 128);
+          mma_bf16(tmem + acc * kAccCols, ad, bd, idesc, kk > 0);
+        }
+        mma_commit(&empty_bar[j % kInvStages]);
+        mma_commit(&acc_full[acc]);
+      }
+      __syncwarp();
+    }
+  } else {
+    // ----------------------------------------------------------- epilogue
+    // warp w drains TMEM lanes 32 (w % 4) .. +31 (x positions) and the column half w / 4
+    constexpr int kHalf = kC / 2;  // output channels per epilogue warp (8, 16 or 32)
+    const int quad = warp & 3, half = warp >> 2;
+    int j = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+      const int acc = j & 1;
+      if (!mbar_wait(&acc_full[acc], (j >> 1) & 1, status)) break;
+      tc_fence_after();
+      float v[32];
+      const uint32_t ta = tmem + acc * kAccCols + half * kHalf + ((uint32_t)(quad * 32) << 16);
+      if (kHalf >= 32) tmem_ld32(ta, v);
+      else tmem_ld16(ta, v);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[acc]);
+      const int row = t / xt;
+      const int x = (t - row * xt) * 128 + quad * 32 + lane;
+#pragma unroll
+      for (int g = 0; g < kHalf / 8; ++g) {
+        const int o0 = half * kHalf + g * 8;
+        __align__(16) __nv_bfloat16 o8[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          o8[q] = __float2bfloat16_rn(act_tc(v[g * 8 + q] + bias_s[o0 + q], act));
+        *reinterpret_cast<uint4*>(out + (((size_t)row * kG + o0 / 8) * W + x) * 8) =
+            *reinterpret_cast<const uint4*>(o8);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, 2 * kAccCols);
+}
+
+// ------------------------------------------------------------------- host
+bool fno_tc_supported(const fno_config& c, int H, int W) {
+  const size_t C = c.width, m = c.modes;
+  const size_t spec_fwd = ((size_t)H * C + H + 2 * m * C) * sizeof(float2);
+  const size_t spec_inv = ((size_t)2 * m * m * C + 16 * 2 * m) * sizeof(float2);
+  return (C == 16 || C == 32 || C == 64) && m <= 16 && 2 * m <= (size_t)H && W % 128 == 0 &&
+         W <= 2048 && c.c_in <= 16 && spec_fwd <= 200 * 1024 && spec_inv <= 200 * 1024;
+}
+
+FnoTcWs fno_tc_ws_plan(const fno_config& c, int B, int H, int W) {
+  FnoTcWs w{};
+  const size_t C = c.width, m = c.modes;
+  size_t p = 0;
+  auto take = [&](size_t bytes) {
+    const size_t a = p;
+    p = align_up(p + bytes, 256);
+    return a;
+  };
+  const size_t pix = (size_t)B * H * W;
+  w.theta0 = take(pix * C * 2);
+  w.theta1 = take(pix * C * 2);
+  w.x1 = take((size_t)B * H * m * C * sizeof(float2));
+  w.yh = take((size_t)B * 2 * m * m * C * sizeof(float2));
+  w.zt = take((size_t)B * H * 32 * C * 2);
+  w.fw = take((size_t)W * 64);
+  w.ti = take((size_t)W * 64);
+  w.twy = take((size_t)H * sizeof(float2));
+  w.status = take(sizeof(unsigned));
+  w.total = p;
+  return w;
+}
+
+template <int kC>
+static int fno_forward_tc_impl(const fno_config& c, const FnoTcParams& P, const float* in,
+                               float* out, int B, int H, int W, char* ws, cudaStream_t s) {
+  const FnoTcWs wp = fno_tc_ws_plan(c, B, H, W);
+  __nv_bfloat16* th[2] = {reinterpret_cast<__nv_bfloat16*>(ws + wp.theta0),
+                          reinterpret_cast<__nv_bfloat16*>(ws + wp.theta1)};
+  float2* x1 = reinterpret_cast<float2*>(ws + wp.x1);
+  float2* yh = reinterpret_cast<float2*>(ws + wp.yh);
+  __nv_bfloat16* zt = reinterpret_cast<__nv_bfloat16*>(ws + wp.zt);
+  __nv_bfloat16* fw = reinterpret_cast<__nv_bfloat16*>(ws + wp.fw);
+  __nv_bfloat16* ti = reinterpret_cast<__nv_bfloat16*>(ws + wp.ti);
+  float2* twy = reinterpret_cast<float2*>(ws + wp.twy);
+  unsigned* status = reinterpret_cast<unsigned*>(ws + wp.status);
+  const int m = c.modes;
+  int dev = 0, nsm = 0;
+  LBM_CHECK_CUDA(cudaGetDevice(&dev));
+  LBM_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  LBM_CHECK_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), s));
+  k_table_fwd<<<(W * 32 + 255) / 256, 256, 0, s>>>(fw, W, m);
+  k_table_inv<<<(W * 32 + 255) / 256, 256, 0, s>>>(ti, H, W, m);
+  k_twiddle_tc<<<(H + 255) / 256, 256, 0, s>>>(twy, H);
+  const size_t pix = (size_t)B * H * W;
+  if (c.c_in == 4)
+    k_lift_blk<kC, 4><<<(unsigned)((pix + 127) / 128), 128, 0, s>>>(
+        in, th[0], P.lift0_w, P.lift0_b, P.lift1_w, P.lift1_b, B, H, W, c.c_in, c.activation);
+  else
+    k_lift_blk<kC, 0><<<(unsigned)((pix + 127) / 128), 128, 0, s>>>(
+        in, th[0], P.lift0_w, P.lift0_b, P.lift1_w, P.lift1_b, B, H, W, c.c_in, c.activation);
+  LBM_CHECK_LAUNCH();
+  const size_t fwd_smem = (size_t)W * 64 + (size_t)kFwdStages * kFwdStageBytes;
+  const size_t spec_fwd_smem = ((size_t)H * kC + H + 2 * m * kC) * sizeof(float2);
+  const size_t spec_inv_smem = ((size_t)2 * m * m * kC + kSpecRows * 2 * m) * sizeof(float2);
+  constexpr int kStageBytesInv = (4 + kC / 8) * 128 * 16 + (4 + kC / 8) * kC * 16;
+  const size_t inv_smem = (size_t)kInvStages * kStageBytesInv;
+  LBM_REQUIRE(spec_fwd_smem <= 200 * 1024 && spec_inv_smem <= 200 * 1024,
+              "fno_forward: spectral working set too large for shared memory");
+  const int ytiles = (H + (128 / kC) - 1) / (128 / kC);
+  const int fwd_ctas = std::min(B * ytiles, 2 * nsm);
+  const int inv_ctas = std::min(B * H * (W / 128), 2 * nsm);
+  int cur = 0;
+  for (int n = 0; n < c.layers; ++n) {
+    k_fwd_x_tc<kC><<<fwd_ctas, kTcThreads, fwd_smem, s>>>(th[cur], fw, x1, B, H, W, m, status);
+    LBM_CHECK_LAUNCH();
+    k_spec_fwd<kC><<<B * m, 256, spec_fwd_smem, s>>>(x1, P.rt[n], yh, twy, H, m);
+    LBM_CHECK_LAUNCH();
+    k_spec_inv<kC><<<B * ((H + kSpecRows - 1) / kSpecRows), 256, spec_inv_smem, s>>>(yh, zt, twy,
+                                                                                     H, m);
+    LBM_CHECK_LAUNCH();
+    k_inv_x_tc<kC><<<inv_ctas, kInvThreads, inv_smem, s>>>(th[cur], ti, zt, P.w[n], P.b[n],
+                                                          th[cur ^ 1], B, H, W, c.activation,
+                                                          status);
+    LBM_CHECK_LAUNCH();
+    cur ^= 1;
+  }
+  const size_t dec_smem =
+      ((size_t)c.dec_layers * (c.dec_size * 64 + c.dec_size) + c.c_out * 64 + c.c_out) * sizeof(float);
+  if (c.dec_layers == 1 && c.dec_size == kC && c.c_out == 3)
+    k_decoder_blk<kC, kC, 3><<<(unsigned)((pix + 127) / 128), 128, dec_smem, s>>>(
+        th[cur], out, P.params, P.dec_offs, c.dec_layers, B, H, W, c.dec_size, c.c_out,
+        c.activation);
+  else
+    k_decoder_blk<kC, 0, 1><<<(unsigned)((pix + 127) / 128), 128, dec_smem, s>>>(
+        th[cur], out, P.params, P.dec_offs, c.dec_layers, B, H, W, c.dec_size, c.c_out,
+        c.activation);
+  LBM_CHECK_LAUNCH();
+  return LBM_OK;
+}
+
+template <int kC>
+static int tc_set_smem_attrs() {
+  const int big = 200 * 1024;
+  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_fwd_x_tc<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_inv_x_tc<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_spec_fwd<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_spec_inv<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  return LBM_OK;
+}
+
+int fno_tc_prepare(const fno_config& c) {
+  switch (c.width) {
+    case 16: return tc_set_smem_attrs<16>();
+    case 32: return tc_set_smem_attrs<32>();
+    case 64: return tc_set_smem_attrs<64>();
+    default: return LBM_OK;
+  }
+}
+
+int fno_forward_tc(const fno_config& c, const FnoTcParams& P, const float* in, float* out, int B,
+                   int H, int W, char* ws, cudaStream_t s) {
+  switch (c.width) {
+    case 16: return fno_forward_tc_impl<16>(c, P, in, out, B, H, W, ws, s);
+    case 32: return fno_forward_tc_impl<32>(c, P, in, out, B, H, W, ws, s);
+    case 64: return fno_forward_tc_impl<64>(c, P, in, out, B, H, W, ws, s);
+    default:
+      set_error("fno_forward: no tensor-core kernels for width %d", c.width);
+      return LBM_ERR_UNSUPPORTED;
+  }
+}
+
+}  // namespace lbmfno

@@ -29,6 +29,7 @@
 
 #include "common.cuh"
 #include "lbm_internal.cuh"
+#include "sm100.cuh"
 
 namespace lbmfno {
 
@@ -281,53 +282,6 @@ struct __align__(16) TileMeta {
 };
 constexpr size_t kTmaSmem =
     (size_t)kStages * kStageFloats * sizeof(float) + (size_t)kStages * sizeof(TileMeta);
-constexpr long long kWaitLimit = 4000000000LL;  // ~2 s of SM clocks
-constexpr unsigned kStatusTimeout = 1u;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait; returns false (and flags the status word) when the limit expires
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned* status) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > kWaitLimit) {
-      atomicOr(status, kStatusTimeout);
-      return false;
-    }
-  }
-  return true;
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
-                                         uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-      ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
 __global__ void __launch_bounds__((kTY + 1) * 32, LBM_TMA_MINB)
     k_step_tma(const GridDev* __restrict__ grids, int ngrids, int ntiles,
                const uint32_t* __restrict__ mask, const float* __restrict__ src,
@@ -342,7 +296,7 @@ __global__ void __launch_bounds__((kTY + 1) * 32, LBM_TMA_MINB)
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], kTY);
     }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_init_fence();
   }
   __syncthreads();
 

@@ -83,6 +83,20 @@ class Fno:
 
     __call__ = forward
 
+    def set_path(self, path: int) -> None:
+        """FNO_PATH_AUTO (tensor cores where the shape allows) or FNO_PATH_CUDA_CORES."""
+        call("fno_set_path", self._h, int(path))
+
+    def uses_tensor_cores(self, H: int, W: int) -> bool:
+        v = ctypes.c_int()
+        call("fno_uses_tensor_cores", self._h, int(H), int(W), ctypes.byref(v))
+        return bool(v.value)
+
+    def check(self, B: int, H: int, W: int, stream=None) -> None:
+        """Synchronise and raise if a device-side wait expired in the last forward."""
+        ws = self.workspace(B, H, W)
+        call("fno_check", self._h, ws.data_ptr(), int(B), int(H), int(W), _stream_ptr(stream))
+
     def close(self) -> None:
         if self._h:
             _abi.lib().fno_destroy(self._h)

@@ -87,8 +87,10 @@ def test_fno_throughput_workload_sampled_against_oracle():
     _requires_gpu()
     s, g, params = _pair(width=32, layers=4, modes=12, dec_size=32, seed=0, out_scale=1e-2)
     net = Fno(g, synth.fno_flatten_params(s, params))
+    assert net.uses_tensor_cores(256, 256)
     x = _flow_inputs(32, 256, 256)
     y = net(torch.from_numpy(x).cuda()).cpu().numpy()
+    net.check(32, 256, 256)
     for b in (0, 31):
         ref = fo.fno_forward(s, params, x[b:b + 1])[0]
         e = rel_l2(y[b], ref)
@@ -107,3 +109,35 @@ def test_invalid_fno_shapes_rejected():
         net(torch.zeros((1, 4, 7, 16), device="cuda"))  # 2m > H
     with pytest.raises(P.LbmError):
         net(torch.zeros((1, 4, 16, 8), device="cuda"))  # m >= W/2
+
+
+@pytest.mark.parametrize("H,W,width", [(32, 128, 32), (64, 256, 32), (40, 128, 16), (32, 128, 64)])
+def test_tensor_core_path_matches_oracle(H, W, width):
+    """tcgen05 path (channel-blocked latents, DFT and 1x1 layers as MMAs) vs the FP64 oracle."""
+    _requires_gpu()
+    s, g, params = _pair(width=width, layers=3, modes=12 if width != 16 else 6,
+                         dec_size=width, seed=11)
+    net = Fno(g, synth.fno_flatten_params(s, params))
+    assert net.uses_tensor_cores(H, W)
+    x = _inputs(2, 4, H, W, seed=13)
+    y = net(torch.from_numpy(x).cuda()).cpu().numpy()
+    net.check(2, H, W)
+    ref = fo.fno_forward(s, params, x)
+    e = rel_l2(y, ref)
+    print(f"FNO tensor cores C={width} {H}x{W}: rel L2 {e:.3e}")
+    assert e < REL_L2_FNO
+
+
+def test_tensor_core_and_cuda_core_paths_agree():
+    _requires_gpu()
+    s, g, params = _pair(width=32, layers=4, modes=12, dec_size=32, seed=3)
+    net = Fno(g, synth.fno_flatten_params(s, params))
+    x = torch.from_numpy(_inputs(3, 4, 64, 128, seed=4)).cuda()
+    y_tc = net(x).cpu().numpy()
+    net.check(3, 64, 128)
+    net.set_path(P._abi.FNO_PATH_CUDA_CORES)
+    assert not net.uses_tensor_cores(64, 128)
+    y_cc = net(x).cpu().numpy()
+    e = rel_l2(y_tc, y_cc)
+    print(f"tensor-core vs CUDA-core path: rel L2 {e:.3e}")
+    assert e < REL_L2_FNO
