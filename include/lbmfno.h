@@ -168,6 +168,22 @@ int lbm_export_f(lbm_handle* h, float* g_d, void* stream);
 int lbm_set_state(lbm_handle* h, const float* gstar_d, void* stream);
 int lbm_get_state(lbm_handle* h, float* gstar_d, void* stream);
 
+/*
+ * Step-kernel tile shapes.  The fused step runs as a persistent kernel whose
+ * tile shape (rows per tile, shared-memory stages, CTAs per SM) is one of
+ * LBM_STEP_VARIANTS compiled shapes; all shapes give bitwise identical results.
+ * lbm_autotune times every shape `reps` times on this batch (reading the
+ * current state, writing only the scratch buffer: the state is unchanged),
+ * selects the fastest, and optionally returns the per-shape milliseconds per
+ * step (ms_h, LBM_STEP_VARIANTS entries, INFINITY for shapes that do not fit)
+ * and the chosen index.  Synchronises `stream`.
+ */
+#define LBM_STEP_VARIANTS 6
+int lbm_autotune(lbm_handle* h, int reps, float* ms_h, int* chosen_h, void* stream);
+int lbm_set_step_variant(lbm_handle* h, int variant);
+int lbm_get_step_variant(const lbm_handle* h, int* variant_h, int* rows_per_tile_h, int* stages_h,
+                         int* ctas_per_sm_h);
+
 /* Number of lbm_step time steps taken since lbm_init / the last reinit. */
 int lbm_steps_done(const lbm_handle* h, long long* out_h);
 

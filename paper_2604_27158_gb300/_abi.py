@@ -20,6 +20,7 @@ LBM_OK, LBM_ERR_INVALID_ARG, LBM_ERR_CUDA, LBM_ERR_UNSTABLE, LBM_ERR_TIMEOUT, LB
 # enum lbm_bc
 LBM_BC_PERIODIC, LBM_BC_PRESSURE, LBM_BC_VELOCITY = 0, 1, 2
 LBM_NSTAT = 8
+LBM_STEP_VARIANTS = 6
 (LBM_STAT_RESIDUAL, LBM_STAT_UNORM, LBM_STAT_DP, LBM_STAT_MASS, LBM_STAT_MOMX, LBM_STAT_MOMY,
  LBM_STAT_BAD, LBM_STAT_FLUID) = range(8)
 
@@ -86,6 +87,10 @@ _PROTOS = {
     "lbm_set_state": ([VP, VP, VP], I),
     "lbm_get_state": ([VP, VP, VP], I),
     "lbm_steps_done": ([VP, ctypes.POINTER(ctypes.c_longlong)], I),
+    "lbm_autotune": ([VP, I, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(I), VP], I),
+    "lbm_set_step_variant": ([VP, I], I),
+    "lbm_get_step_variant": ([VP, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
+                              ctypes.POINTER(I)], I),
     "lbm_destroy": ([VP], I),
     "fno_query": ([ctypes.POINTER(fno_config), I, I, I, ctypes.POINTER(fno_sizes)], I),
     "fno_create": ([ctypes.POINTER(fno_config), VP, VP, VP, ctypes.POINTER(VP)], I),

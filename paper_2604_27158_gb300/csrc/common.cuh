@@ -85,8 +85,6 @@ struct GridDev {
   int nseg;            // 128-cell row segments per row (step kernel)
   int rblk_start;      // first block of the grid in the residual kernel
   int nrblk;           // residual-kernel blocks of the grid
-  int tile_start;      // first tile of the grid in the step kernel
-  int ntiles;          // step-kernel tiles of the grid
   float omega;         // 1 / tau
   float tau;
   float guo;           // 1 - 1/(2 tau)

@@ -245,47 +245,64 @@ __device__ __forceinline__ bool cell_of_thread(const GridDev* __restrict__ grids
 // records LBM_ERR_TIMEOUT in `status` and stops.
 constexpr int kVec = 4;
 constexpr int kSeg = 32 * kVec;
-#ifndef LBM_TMA_TY
-#define LBM_TMA_TY 3  // rows per tile = consumer warps per CTA
-#endif
-#ifndef LBM_TMA_STAGES
-#define LBM_TMA_STAGES 2  // shared-memory ring depth
-#endif
-#ifndef LBM_TMA_MINB
-#define LBM_TMA_MINB 5  // resident CTAs per SM
-#endif
-constexpr int kTY = LBM_TMA_TY;
 constexpr int kRowF = kSeg + 8;  // floats per staged row segment
-constexpr int kStages = LBM_TMA_STAGES;
-// Staged rows of population i: the kTY rows it is pulled from plus, for c_iy != 0,
+constexpr int kWords = kVec + 2;  // mask words per row around a segment
+// Staged rows of population i: the TY rows it is pulled from plus, for c_iy != 0,
 // the tile's own last (c_iy = +1) or first (c_iy = -1) row, so that bounce-back always
 // finds the own cell's opposite population in the stage.  Stage row 0 of population i
 // holds source row y0 + stage_first(i).
-__host__ __device__ constexpr int stage_rows(int i) { return kTY + (cy_of(i) != 0 ? 1 : 0); }
+template <int TY>
+__host__ __device__ constexpr int stage_rows(int i) { return TY + (cy_of(i) != 0 ? 1 : 0); }
 // first stage row of population i = sum of stage_rows(j) for j < i (closed form:
 // the populations with c_jy != 0 are j = 2, 4, 5, 6, 7, 8)
+template <int TY>
 __host__ __device__ constexpr int stage_row0(int i) {
-  return i * kTY + (i > 2 ? 1 : 0) + (i > 4 ? 1 : 0) + (i > 5 ? i - 5 : 0);
+  return i * TY + (i > 2 ? 1 : 0) + (i > 4 ? 1 : 0) + (i > 5 ? i - 5 : 0);
 }
-static_assert(stage_row0(3) == 3 * kTY + 1 && stage_row0(kQ) == 9 * kTY + 6 &&
-                  stage_row0(8) + stage_rows(8) == stage_row0(kQ),
-              "stage row offsets");
 __host__ __device__ constexpr int stage_first(int i) { return cy_of(i) > 0 ? -1 : 0; }
-constexpr int kStageRows = stage_row0(kQ);  // 9 kTY + 6
-constexpr int kStageFloats = kStageRows * kRowF;
-constexpr int kWords = kVec + 2;               // mask words per row around a segment
-constexpr int kMaskWords = (kTY + 2) * kWords;  // rows y0-1 .. y0+kTY
-struct __align__(16) TileMeta {
-  GridDev g;
-  int x0, y0, rows, pad;
-  uint32_t mask[kMaskWords];
+
+// A tile shape of the step kernel: TY rows per tile (= consumer warps per CTA),
+// ST stages in the shared-memory ring, MB CTAs requested per SM.
+template <int TY, int ST, int MB>
+struct StepShape {
+  static constexpr int kStageRows = stage_row0<TY>(kQ);  // 9 TY + 6
+  static constexpr int kStageFloats = kStageRows * kRowF;
+  static constexpr int kMaskWords = (TY + 2) * kWords;  // rows y0-1 .. y0+TY
+  struct __align__(16) Meta {
+    GridDev g;
+    int x0, y0, rows, pad;
+    uint32_t mask[kMaskWords];
+  };
+  static constexpr size_t kSmem =
+      (size_t)ST * kStageFloats * sizeof(float) + (size_t)ST * sizeof(Meta);
+  static_assert(stage_row0<TY>(3) == 3 * TY + 1 && stage_row0<TY>(kQ) == 9 * TY + 6 &&
+                    stage_row0<TY>(8) + stage_rows<TY>(8) == stage_row0<TY>(kQ),
+                "stage row offsets");
 };
-constexpr size_t kTmaSmem =
-    (size_t)kStages * kStageFloats * sizeof(float) + (size_t)kStages * sizeof(TileMeta);
-__global__ void __launch_bounds__((kTY + 1) * 32, LBM_TMA_MINB)
-    k_step_tma(const GridDev* __restrict__ grids, int ngrids, int ntiles,
-               const uint32_t* __restrict__ mask, const float* __restrict__ src,
+
+// Grid of tile t: binary search over the shape's per-grid first-tile prefix.
+__device__ __forceinline__ int grid_of_tile(const int* __restrict__ tile_start, int ngrids,
+                                            int t) {
+  int lo = 0, hi = ngrids - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&tile_start[mid]) <= t)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int TY, int ST, int MB>
+__global__ void __launch_bounds__((TY + 1) * 32, MB)
+    k_step_tma(const GridDev* __restrict__ grids, int ngrids, const int* __restrict__ tile_start,
+               int ntiles, const uint32_t* __restrict__ mask, const float* __restrict__ src,
                float* __restrict__ dst, unsigned* __restrict__ status) {
+  using SS = StepShape<TY, ST, MB>;
+  using TileMeta = typename SS::Meta;
+  constexpr int kTY = TY, kStages = ST, kStageFloats = SS::kStageFloats,
+                kMaskWords = SS::kMaskWords;
   extern __shared__ __align__(128) float stage_mem[];
   TileMeta* metas = reinterpret_cast<TileMeta*>(stage_mem + (size_t)kStages * kStageFloats);
   __shared__ __align__(8) uint64_t full_bar[kStages];
@@ -308,9 +325,9 @@ __global__ void __launch_bounds__((kTY + 1) * 32, LBM_TMA_MINB)
       const int s = k % kStages;
       if (k >= kStages) ok = mbar_wait(&empty_bar[s], ((k / kStages) - 1) & 1, status);
       if (!ok) break;
-      const int gi = grid_of<&GridDev::tile_start>(grids, ngrids, t);
+      const int gi = grid_of_tile(tile_start, ngrids, t);
       const GridDev* Gp = grids + gi;
-      const int lt = t - __ldg(&Gp->tile_start);
+      const int lt = t - __ldg(&tile_start[gi]);
       const int nseg = __ldg(&Gp->nseg), ny = __ldg(&Gp->ny), pitch = __ldg(&Gp->pitch);
       const int yt = lt / nseg;
       const int x0 = (lt - yt * nseg) * kSeg, y0 = yt * kTY;
@@ -322,6 +339,7 @@ __global__ void __launch_bounds__((kTY + 1) * 32, LBM_TMA_MINB)
       const int rows = min(kTY, ny - y0);
       float* st = stage_mem + (size_t)s * kStageFloats;
       if (lane == 0) mbar_expect_tx(&full_bar[s], seg_bytes * (unsigned)(kQ * rows + 6));
+      static_assert(kStageFloats > 0 && kMaskWords > 0, "shape");
       __syncwarp();
 #pragma unroll
       for (int i = 0; i < kQ; ++i) {  // compile-time population index
@@ -329,7 +347,7 @@ __global__ void __launch_bounds__((kTY + 1) * 32, LBM_TMA_MINB)
         for (int r = lane; r < nr; r += 32) {
           int ys = y0 + stage_first(i) + r;
           ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
-          bulk_g2s(st + (stage_row0(i) + r) * kRowF + (xs - (x0 - 4)),
+          bulk_g2s(st + (stage_row0<TY>(i) + r) * kRowF + (xs - (x0 - 4)),
                    b + (size_t)i * plane + (size_t)ys * pitch + xs, seg_bytes, &full_bar[s]);
         }
       }
@@ -419,7 +437,7 @@ __global__ void __launch_bounds__((kTY + 1) * 32, LBM_TMA_MINB)
 #pragma unroll
       for (int i = 0; i < kQ; ++i) {
         const float* rowp =
-            st + (stage_row0(i) + warp - cy_of(i) - stage_first(i)) * kRowF + 4 + kVec * lane;
+            st + (stage_row0<TY>(i) + warp - cy_of(i) - stage_first(i)) * kRowF + 4 + kVec * lane;
         const float4 c0 = *reinterpret_cast<const float4*>(rowp);
         const int ys = cy_of(i) > 0 ? ym : (cy_of(i) == 0 ? y : yp);
         if (cx_of(i) == 0) {
@@ -447,7 +465,7 @@ __global__ void __launch_bounds__((kTY + 1) * 32, LBM_TMA_MINB)
         if (bb) {
           const int o = opp_of(i);
           const float4 v = *reinterpret_cast<const float4*>(
-              st + (stage_row0(o) + warp - stage_first(o)) * kRowF + 4 + kVec * lane);
+              st + (stage_row0<TY>(o) + warp - stage_first(o)) * kRowF + 4 + kVec * lane);
           if (bb & 1u) g[i][0] = v.x;
           if (bb & 2u) g[i][1] = v.y;
           if (bb & 4u) g[i][2] = v.z;
@@ -505,6 +523,23 @@ __global__ void __launch_bounds__((kTY + 1) * 32, LBM_TMA_MINB)
     }
   }
 }
+
+// Tile shapes compiled into the library (rows per tile, stages, CTAs per SM).
+// Every shape performs the same arithmetic per cell in the same order, so the
+// choice changes speed only; lbm_autotune times them on the caller's batch.
+using StepKernel = void (*)(const GridDev*, int, const int*, int, const uint32_t*, const float*,
+                           float*, unsigned*);
+struct StepVariant {
+  int ty, stages, minb;
+  StepKernel kernel;
+  size_t smem;
+};
+#define LBM_STEP_VARIANT(TY, ST, MB) \
+  StepVariant { TY, ST, MB, k_step_tma<TY, ST, MB>, StepShape<TY, ST, MB>::kSmem }
+static const StepVariant kStepVariants[LBM_STEP_VARIANTS] = {
+    LBM_STEP_VARIANT(3, 2, 5), LBM_STEP_VARIANT(4, 2, 4), LBM_STEP_VARIANT(2, 2, 7),
+    LBM_STEP_VARIANT(5, 2, 4), LBM_STEP_VARIANT(3, 3, 4), LBM_STEP_VARIANT(6, 2, 3)};
+#undef LBM_STEP_VARIANT
 
 __global__ void __launch_bounds__(kBlock) k_export(const GridDev* __restrict__ grids, int ngrids,
                                                    const uint32_t* __restrict__ mask,
@@ -906,7 +941,7 @@ __global__ void __launch_bounds__(kBlock) k_reinit(const GridDev* __restrict__ g
 
 // ------------------------------------------------------------ host side ---
 struct WsPlan {
-  size_t grids_off, uprev_off, partial_off, stats_off, status_off, total;
+  size_t grids_off, uprev_off, partial_off, stats_off, status_off, tiles_off, total;
 };
 
 static int plan_layout(const lbm_grid* grids, int ngrids, lbm_layout* lay,
@@ -948,8 +983,7 @@ static int plan_layout(const lbm_grid* grids, int ngrids, lbm_layout* lay,
     d.nrblk = (int)(((long long)d.nseg * g.ny + kBlock / 32 - 1) / (kBlock / 32));
     d.rblk_start = (int)rblk;
 
-    d.ntiles = d.nseg * ((g.ny + kTY - 1) / kTY);
-    d.tile_start = (int)tiles;
+
     d.tau = (float)g.tau;
     d.omega = (float)(1.0 / g.tau);
     d.guo = (float)(1.0 - 0.5 / g.tau);
@@ -966,7 +1000,7 @@ static int plan_layout(const lbm_grid* grids, int ngrids, lbm_layout* lay,
     words += (size_t)d.wpr * g.ny;
     cells += (size_t)g.nx * g.ny;
     blk += d.nblk;
-    tiles += d.ntiles;
+    tiles += (long long)d.nseg * g.ny;
     rblk += d.nrblk;
     LBM_REQUIRE(blk < (1LL << 30) && tiles < (1LL << 30),
                 "lbm: batch too large");
@@ -978,7 +1012,8 @@ static int plan_layout(const lbm_grid* grids, int ngrids, lbm_layout* lay,
   w.partial_off = align_up(w.uprev_off + 2 * cells * sizeof(float), 256);
   w.stats_off = align_up(w.partial_off + (size_t)rblk * R_COUNT * sizeof(double), 256);
   w.status_off = align_up(w.stats_off + (size_t)ngrids * R_COUNT * sizeof(double), 256);
-  w.total = align_up(w.status_off + sizeof(unsigned), 256);
+  w.tiles_off = align_up(w.status_off + sizeof(unsigned), 256);
+  w.total = align_up(w.tiles_off + (size_t)LBM_STEP_VARIANTS * (ngrids + 1) * sizeof(int), 256);
   lay->f_elems = f;
   lay->mask_words = words;
   lay->cells = cells;
@@ -988,6 +1023,17 @@ static int plan_layout(const lbm_grid* grids, int ngrids, lbm_layout* lay,
 }
 
 static inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// One step of every grid with tile shape `v`: reads `src`, writes `dst`.
+static int launch_step(Handle* h, int v, const float* src, float* dst, cudaStream_t s) {
+  const StepVariant& sv = kStepVariants[v];
+  const int ctas = std::min(h->ntiles_v[v], h->nsm * std::max(1, h->blocks_per_sm_v[v]));
+  sv.kernel<<<ctas, (sv.ty + 1) * 32, sv.smem, s>>>(
+      h->gd_d, h->ngrids, h->tile_start_d + (size_t)v * (h->ngrids + 1), h->ntiles_v[v],
+      h->mask, src, dst, h->status_d);
+  LBM_CHECK_LAUNCH();
+  return LBM_OK;
+}
 
 }  // namespace lbmfno
 
@@ -1022,7 +1068,6 @@ int lbm_init(const lbm_grid* grids_h, int ngrids, const uint32_t* mask_d, float*
   h->grids.assign(grids_h, grids_h + ngrids);
   h->ngrids = ngrids;
   h->nblk_total = h->gd.back().blk_start + h->gd.back().nblk;
-  h->ntiles_total = h->gd.back().tile_start + h->gd.back().ntiles;
   h->nrblk_total = h->gd.back().rblk_start + h->gd.back().nrblk;
   h->mask = mask_d;
   h->f[0] = f_a_d;
@@ -1034,23 +1079,38 @@ int lbm_init(const lbm_grid* grids_h, int ngrids, const uint32_t* mask_d, float*
   h->partial = reinterpret_cast<double*>(ws + wp.partial_off);
   h->stats_d = reinterpret_cast<double*>(ws + wp.stats_off);
   h->status_d = reinterpret_cast<unsigned*>(ws + wp.status_off);
+  h->tile_start_d = reinterpret_cast<int*>(ws + wp.tiles_off);
+  std::vector<int> tile_prefix((size_t)LBM_STEP_VARIANTS * (ngrids + 1));
+  for (int v = 0; v < LBM_STEP_VARIANTS; ++v) {
+    long long acc = 0;
+    for (int k = 0; k < ngrids; ++k) {
+      tile_prefix[(size_t)v * (ngrids + 1) + k] = (int)acc;
+      acc += (long long)h->gd[k].nseg * ((h->gd[k].ny + kStepVariants[v].ty - 1) / kStepVariants[v].ty);
+    }
+    tile_prefix[(size_t)v * (ngrids + 1) + ngrids] = (int)acc;
+    h->ntiles_v[v] = (int)acc;
+  }
   h->stats_h.assign((size_t)ngrids * R_COUNT, 0.0);
   h->u_max2 = (float)(u_max * u_max);
   cudaStream_t s = S(stream);
   {
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaFuncSetAttribute(k_step_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kTmaSmem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->tma_blocks_per_sm, k_step_tma,
-                                                      (kTY + 1) * 32, kTmaSmem) != cudaSuccess) {
+    bool ok = cudaGetDevice(&dev) == cudaSuccess &&
+              cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess;
+    for (int v = 0; ok && v < LBM_STEP_VARIANTS; ++v) {
+      const StepVariant& sv = kStepVariants[v];
+      ok = cudaFuncSetAttribute(sv.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sv.smem) == cudaSuccess &&
+           cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->blocks_per_sm_v[v], sv.kernel,
+                                                         (sv.ty + 1) * 32, sv.smem) == cudaSuccess;
+    }
+    if (!ok) {
       set_error("lbm_init: %s", cudaGetErrorString(cudaGetLastError()));
       delete h;
       return LBM_ERR_CUDA;
     }
+    h->variant = 0;
   }
-  h->tma_blocks_per_sm = std::max(1, h->tma_blocks_per_sm);
   auto fail = [&](int code) {
     delete h;
     return code;
@@ -1061,6 +1121,8 @@ int lbm_init(const lbm_grid* grids_h, int ngrids, const uint32_t* mask_d, float*
       cudaMemsetAsync(f_b_d, 0, h->layout.f_elems * sizeof(float), s) != cudaSuccess ||
       cudaMemsetAsync(h->ux_prev, 0, 2 * h->layout.cells * sizeof(float), s) != cudaSuccess ||
       cudaMemsetAsync(h->status_d, 0, sizeof(unsigned), s) != cudaSuccess ||
+      cudaMemcpyAsync(h->tile_start_d, tile_prefix.data(), tile_prefix.size() * sizeof(int),
+                      cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {
     set_error("lbm_init: %s", cudaGetErrorString(cudaGetLastError()));
     return fail(LBM_ERR_CUDA);
@@ -1072,12 +1134,8 @@ int lbm_init(const lbm_grid* grids_h, int ngrids, const uint32_t* mask_d, float*
 int lbm_step(lbm_handle* h, int nsteps, void* stream) {
   LBM_REQUIRE(h != nullptr && nsteps >= 0, "lbm_step: bad arguments");
   cudaStream_t s = S(stream);
-  const int ctas = std::min(h->ntiles_total, h->nsm * h->tma_blocks_per_sm);
   for (int k = 0; k < nsteps; ++k) {
-    k_step_tma<<<ctas, (kTY + 1) * 32, kTmaSmem, s>>>(h->gd_d, h->ngrids, h->ntiles_total,
-                                                      h->mask, h->f[h->cur], h->f[h->cur ^ 1],
-                                                      h->status_d);
-    LBM_CHECK_LAUNCH();
+    LBM_TRY(launch_step(h, h->variant, h->f[h->cur], h->f[h->cur ^ 1], s));
     h->cur ^= 1;
   }
   h->steps += nsteps;
@@ -1166,6 +1224,72 @@ int lbm_get_state(lbm_handle* h, float* gstar_d, void* stream) {
   k_copy_state<<<h->nblk_total, kBlock, 0, S(stream)>>>(h->gd_d, h->ngrids, h->f[h->cur],
                                                         gstar_d, 1);
   LBM_CHECK_LAUNCH();
+  return LBM_OK;
+}
+
+int lbm_autotune(lbm_handle* h, int reps, float* ms_h, int* chosen_h, void* stream) {
+  LBM_REQUIRE(h != nullptr && reps >= 1, "lbm_autotune: bad arguments");
+  cudaStream_t s = S(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  LBM_CHECK_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    set_error("lbm_autotune: cudaEventCreate failed");
+    return LBM_ERR_CUDA;
+  }
+  // timing launches read the current state and overwrite only the other buffer,
+  // which the next step overwrites anyway: the simulation state is unchanged
+  const float* src = h->f[h->cur];
+  float* scratch = h->f[h->cur ^ 1];
+  int best = h->variant;
+  float best_ms = INFINITY;
+  int rc = LBM_OK;
+  for (int v = 0; v < LBM_STEP_VARIANTS && rc == LBM_OK; ++v) {
+    float ms = INFINITY;
+    if (h->blocks_per_sm_v[v] > 0) {
+      for (int w = 0; w < 2 && rc == LBM_OK; ++w) rc = launch_step(h, v, src, scratch, s);
+      if (rc == LBM_OK && cudaEventRecord(e0, s) != cudaSuccess) rc = LBM_ERR_CUDA;
+      for (int k = 0; k < reps && rc == LBM_OK; ++k) rc = launch_step(h, v, src, scratch, s);
+      if (rc == LBM_OK && (cudaEventRecord(e1, s) != cudaSuccess ||
+                           cudaEventSynchronize(e1) != cudaSuccess ||
+                           cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        rc = LBM_ERR_CUDA;
+      ms /= (float)reps;
+    }
+    if (ms_h) ms_h[v] = ms;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != LBM_OK) {
+    if (rc == LBM_ERR_CUDA) set_error("lbm_autotune: %s", cudaGetErrorString(cudaGetLastError()));
+    return rc;
+  }
+  h->variant = best;
+  if (chosen_h) *chosen_h = best;
+  return LBM_OK;
+}
+
+int lbm_set_step_variant(lbm_handle* h, int variant) {
+  LBM_REQUIRE(h != nullptr && variant >= 0 && variant < LBM_STEP_VARIANTS,
+              "lbm_set_step_variant: bad arguments");
+  LBM_REQUIRE(h->blocks_per_sm_v[variant] > 0, "lbm_set_step_variant: shape %d does not fit",
+              variant);
+  h->variant = variant;
+  return LBM_OK;
+}
+
+int lbm_get_step_variant(const lbm_handle* h, int* variant_h, int* rows_per_tile_h,
+                         int* stages_h, int* ctas_per_sm_h) {
+  LBM_REQUIRE(h != nullptr, "lbm_get_step_variant: null handle");
+  const StepVariant& sv = kStepVariants[h->variant];
+  if (variant_h) *variant_h = h->variant;
+  if (rows_per_tile_h) *rows_per_tile_h = sv.ty;
+  if (stages_h) *stages_h = sv.stages;
+  if (ctas_per_sm_h) *ctas_per_sm_h = h->blocks_per_sm_v[h->variant];
   return LBM_OK;
 }
 

@@ -13,10 +13,12 @@ struct Handle {
   GridDev* gd_d = nullptr;  // in the caller's workspace
   int ngrids = 0;
   int nblk_total = 0;
-  int ntiles_total = 0;
   int nrblk_total = 0;  // blocks of the residual kernel
   int nsm = 0;
-  int tma_blocks_per_sm = 1;
+  int variant = 0;                             // step-kernel tile shape in use
+  int ntiles_v[LBM_STEP_VARIANTS] = {};        // tiles of the batch per shape
+  int blocks_per_sm_v[LBM_STEP_VARIANTS] = {};  // resident CTAs per SM per shape
+  int* tile_start_d = nullptr;                 // per-shape first-tile prefixes (workspace)
   unsigned* status_d = nullptr;
   unsigned status_h = 0;
   const uint32_t* mask = nullptr;

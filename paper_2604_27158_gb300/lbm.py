@@ -129,6 +129,24 @@ class Lattice:
         call("lbm_get_state", self._h, out.data_ptr(), _stream_ptr(stream))
         return out
 
+    def autotune(self, reps: int = 10, stream=None):
+        """Time every compiled step-kernel tile shape on this batch and keep the fastest.
+
+        The state is unchanged.  Returns (chosen index, milliseconds per step per shape)."""
+        ms = (ctypes.c_float * _abi.LBM_STEP_VARIANTS)()
+        chosen = ctypes.c_int()
+        call("lbm_autotune", self._h, int(reps), ms, ctypes.byref(chosen), _stream_ptr(stream))
+        return chosen.value, list(ms)
+
+    def set_step_variant(self, variant: int) -> None:
+        call("lbm_set_step_variant", self._h, int(variant))
+
+    def step_variant(self):
+        """(index, rows per tile, stages, CTAs per SM) of the step kernel in use."""
+        v = [ctypes.c_int() for _ in range(4)]
+        call("lbm_get_step_variant", self._h, *[ctypes.byref(x) for x in v])
+        return tuple(x.value for x in v)
+
     def steps_done(self) -> int:
         v = ctypes.c_longlong()
         call("lbm_steps_done", self._h, ctypes.byref(v))

@@ -38,6 +38,7 @@ __all__ = [
     "fno_random_params",
     "fno_flatten_params",
     "smooth_macro_fields",
+    "unsteady_batch",
     "random_post_collision_state",
 ]
 
@@ -178,6 +179,33 @@ def flow_past_disks(nx: int, ny: int, seed: int, ndisks_range=(1, 4),
         gap=2, stop=lambda ds: len(ds) >= n)
     solid = rasterise_disks(nx, ny, disks, periodic_x=False, periodic_y=True)
     return solid, disks
+
+
+UNSTEADY_SIZES = ((128, 128), (256, 128), (256, 256), (512, 256))  # (nx, ny)
+
+
+def unsteady_batch(n: int, seed: int = 0, sizes=UNSTEADY_SIZES, tau_range=(0.55, 0.8),
+                   re_range=(50.0, 200.0), u_cap: float = 0.08):
+    """Batch of flow-past-disks trajectories of uneven size (the super-time-stepping workload).
+
+    Per trajectory: a size drawn from `sizes`, 1-4 disks (flow_past_disks), tau ~
+    U(tau_range), a Reynolds number Re ~ U(re_range) based on the channel height
+    ny, and the inlet speed U = Re nu / ny with nu = (tau - 1/2) / 3, capped at
+    `u_cap` for Mach safety (the effective Re is returned).  Velocity inlet,
+    pressure outlet rho = 1, periodic in y.
+    Returns a list of dicts {nx, ny, tau, u_in, re, solid}.
+    """
+    rng = _rng(seed)
+    out = []
+    for k in range(n):
+        nx, ny = sizes[int(rng.integers(0, len(sizes)))]
+        tau = float(rng.uniform(*tau_range))
+        re = float(rng.uniform(*re_range))
+        solid, _ = flow_past_disks(nx, ny, seed=int(rng.integers(0, 2 ** 31)))
+        nu = (tau - 0.5) / 3.0
+        u = min(re * nu / ny, u_cap)
+        out.append(dict(nx=nx, ny=ny, tau=tau, u_in=u, re=u * ny / nu, solid=solid))
+    return out
 
 
 def pack_mask_bits(solid: np.ndarray) -> np.ndarray:

@@ -103,3 +103,35 @@ def test_unsteady_cycles_match_oracle(k_lbm):
         e = rel_l2(np.stack([ux[k].numpy()[fl], uy[k].numpy()[fl]]), np.stack([oux[fl], ouy[fl]]))
         print(f"unsteady k={k_lbm} grid {k}: rel L2 u {e:.3e}")
         assert e < 2e-2
+
+
+def test_uneven_batch_super_time_stepping_matches_oracle():
+    """The batched unsteady workload (four grid sizes, k = 50 LBM steps, m = 5 FNO steps,
+    reinit) on one trajectory per size, against the oracle driver with the same weights."""
+    _requires_gpu()
+    batch = synth.unsteady_batch(24, seed=3)
+    picked, seen = [], set()
+    for t in batch:
+        if (t["nx"], t["ny"]) not in seen:
+            seen.add((t["nx"], t["ny"]))
+            picked.append(t)
+    assert len(picked) == 4
+    grids = [GridSpec(t["nx"], t["ny"], t["tau"], bc_west=P.BC_VELOCITY, bc_east=P.BC_PRESSURE,
+                      west_value=t["u_in"], east_value=1.0) for t in picked]
+    s, params, net = _net(width=16, layers=1, modes=4, out_scale=1e-1)
+    assert all(net.uses_tensor_cores(t["ny"], t["nx"]) for t in picked)
+    lat = Lattice(grids, [t["solid"] for t in picked])
+    hyb = Hybrid(lat, net, HybridConfig(mode=P._abi.HYBRID_UNSTEADY, k_lbm=50, m_fno=5, neq_mode=1))
+    st, _, _ = hyb.advance(cycles=2)
+    torch.cuda.synchronize()
+    assert st.steps == 100 and st.fno_calls == 2 * 5 * 4
+    _, ux, uy = (lat.split(t.cpu()) for t in lat.macro())
+    for k, (g, t) in enumerate(zip(grids, picked)):
+        og, solid = to_oracle(g), t["solid"]
+        f = oracle.hybrid_unsteady(og, solid, s, params, oracle.rest_state(og, solid), k_lbm=50,
+                                   m_fno=5, cycles=2)
+        _, oux, ouy = oracle.macro(og, solid, f)
+        fl = ~solid
+        e = rel_l2(np.stack([ux[k].numpy()[fl], uy[k].numpy()[fl]]), np.stack([oux[fl], ouy[fl]]))
+        print(f"uneven batch {g.nx}x{g.ny}: rel L2 u {e:.3e}")
+        assert e < 2e-2

@@ -239,3 +239,42 @@ def test_degenerate_grids():
     assert st[1, P._abi.LBM_STAT_FLUID] == 0
     gg = lat.split(lat.export_f().cpu(), per_cell=9)
     assert torch.all(gg[0] == 0) and torch.all(gg[1] == 0) and torch.all(gg[2] == 0)
+
+
+def test_all_step_tile_shapes_give_identical_states():
+    """Every compiled tile shape runs the same per-cell arithmetic: states agree bitwise."""
+    _requires_gpu()
+    specs = [GEOMS[k]() for k in sorted(GEOMS)]
+    solid2, _, _ = synth.porous_media(512, 256, 4, 12, seed=5)
+    specs.append((GridSpec(512, 256, 0.7, bc_west=P.BC_PRESSURE, bc_east=P.BC_PRESSURE,
+                           west_value=1.001, east_value=1.0), solid2))
+    ref = None
+    for v in range(P._abi.LBM_STEP_VARIANTS):
+        lat = Lattice([s[0] for s in specs], [s[1] for s in specs])
+        try:
+            lat.set_step_variant(v)
+        except P.LbmError:
+            continue  # a shape that does not fit on this device
+        lat.step(37)
+        state = lat.get_state().cpu()
+        if ref is None:
+            ref = state
+        else:
+            assert torch.equal(state, ref), f"tile shape {v} differs"
+    assert ref is not None
+
+
+def test_autotune_keeps_state_and_picks_a_shape():
+    _requires_gpu()
+    g, solid = GEOMS["porous_zou_he_70x33"]()
+    lat = Lattice([g], [solid])
+    lat.step(11)
+    before = lat.get_state().cpu()
+    chosen, ms = lat.autotune(reps=3)
+    assert torch.equal(lat.get_state().cpu(), before)
+    assert 0 <= chosen < P._abi.LBM_STEP_VARIANTS and ms[chosen] == min(ms)
+    assert lat.step_variant()[0] == chosen
+    lat.step(5)
+    ref = Lattice([g], [solid])
+    ref.step(16)
+    assert torch.equal(lat.get_state().cpu(), ref.get_state().cpu())
