@@ -57,6 +57,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--unsteady-trajectories", type=int, default=100)
     ap.add_argument("--unsteady-cycles", type=int, default=20)
+    ap.add_argument("--ladder-trajectories", type=int, default=20,
+                    help="trajectories of the tolerance ladder (steps to 1e-4 ... 1e-7, both starts)")
+    ap.add_argument("--ladder-max-steps", type=int, default=100000)
+    ap.add_argument("--no-sweep", action="store_true", help="skip the large-domain LBM sweep")
+    ap.add_argument("--step-variant", type=int, default=-1,
+                    help="step-kernel tile shape index; -1 (default) times all shapes and keeps the fastest")
     return ap.parse_args()
 
 
@@ -94,9 +100,10 @@ def read_peaks():
         return 6800.0, "fallback"
 
 
-def step_kernel_traffic(cells):
-    """DRAM bytes per step-kernel launch from the committed ncu record, scaled to `cells`;
-    None when the step kernel's source changed since the counters were taken."""
+def step_kernel_traffic(cells, shape):
+    """DRAM bytes per step-kernel launch from the committed ncu record of the tile shape in
+    use, scaled to `cells`; None when there is no record for that shape or the step kernel's
+    source changed since the counters were taken."""
     import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "k_step_tma_traffic.json")))
@@ -104,6 +111,8 @@ def step_kernel_traffic(cells):
         a = src.index("// ------------------------------------------------------ the fused step ---")
         b = src.index("__global__ void __launch_bounds__(kBlock) k_export(")
         if hashlib.sha256(src[a:b].encode()).hexdigest()[:16] != rec["source_section_sha256_16"]:
+            return None
+        if rec["variant"] != shape[0]:
             return None
         return rec["traffic_bytes_per_launch"] * cells / rec["cells"]
     except Exception:
@@ -122,6 +131,40 @@ def fno_flops(B, H, W, C=32, m=12, layers=4, cin=4, S=32, cout=3):
     lift = 2 * ((cin + 2) * C // 2 + C // 2 * C) * px
     dec = 2 * (C * S + S * cout) * px
     return layers * layer + lift + dec
+
+
+def fno_bytes(B, H, W, C=32, layers=4, cin=4, cout=3):
+    """Algorithmic HBM bytes of one FNO forward with fused layer boundaries: every layer
+    reads and writes its BF16 latent field once; FP32 input and output fields."""
+    return layers * 2 * B * H * W * C * 2 + B * H * W * (cin + cout) * 4
+
+
+def fno_snapshot_inputs(P, GridSpec, Lattice, B, H, W, steps=2000):
+    """FNO inputs (rho-1, ux, uy, mask) from LBM snapshots: B body-force channels of H x W
+    with walls and 6 seeded disks (radius 4-8 scaled by W/128), tau 0.8, after `steps` steps."""
+    import synth
+    import torch
+    masks = [synth.channel_with_disks(W, H, 6, 4 * W // 128, 8 * W // 128, seed=b)[0]
+             for b in range(B)]
+    lat = Lattice([GridSpec(W, H, 0.8, fx=1e-6) for _ in range(B)], masks)
+    lat.step(steps)
+    rho, ux, uy = lat.macro()
+    m = torch.from_numpy(np.stack(masks).astype(np.float32)).cuda()
+    x = torch.stack([rho.view(B, H, W) - 1.0, ux.view(B, H, W), uy.view(B, H, W), m], dim=1)
+    torch.cuda.synchronize()
+    lat.close()
+    return x.contiguous()
+
+
+def tiled_porous(nx, ny, seed, ntiles=8, porosity=0.7):
+    """A large porous domain built from seeded 512 x 256 tiles of the porous-media generator
+    at a fixed porosity (the tiles keep their disks away from the tile's x edges)."""
+    import synth
+    tiles = [synth.porous_media(NX, NY, 4, 12, porosity_range=(porosity, porosity), seed=seed + k)[0]
+             for k in range(ntiles)]
+    rng = np.random.default_rng(seed)
+    pick = rng.integers(0, ntiles, size=(ny // NY, nx // NX))
+    return np.block([[tiles[k] for k in row] for row in pick])
 
 
 def workload(T, seed0):
@@ -195,43 +238,74 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(masks, budget_s=12.0):
-    """The FP64 C oracle (single thread) on one trajectory, bounded to ~budget_s."""
+def _oracle_glups(g, solid, budget_s, openmp):
+    import oracle
+    f = oracle.rest_state(g, solid)
+    t0 = time.perf_counter()
+    f = oracle.run(g, solid, f, 10, openmp=openmp)
+    dt = time.perf_counter() - t0
+    n = max(10, int(budget_s / max(dt / 10, 1e-9)))
+    t0 = time.perf_counter()
+    oracle.run(g, solid, f, n, openmp=openmp)
+    dt = time.perf_counter() - t0
+    return NX * NY * n / dt / 1e9, n, dt
+
+
+def cpu_baseline(masks, budget_s=8.0):
+    """The FP64 C oracle on one trajectory, bounded to ~budget_s per build: the OpenMP build
+    on all host cores (the reported value) and the single-thread parity build."""
     import oracle
     g = oracle.Grid(nx=NX, ny=NY, tau=TAU, bc_west=oracle.BC_PRESSURE, bc_east=oracle.BC_PRESSURE,
                     west_value=RHO_IN, east_value=RHO_OUT)
-    f = oracle.rest_state(g, masks[0])
-    t0 = time.perf_counter()
-    f = oracle.run(g, masks[0], f, 20)
-    dt = time.perf_counter() - t0
-    n = max(20, int(budget_s / max(dt / 20, 1e-9)))
-    t0 = time.perf_counter()
-    oracle.run(g, masks[0], f, n)
-    dt = time.perf_counter() - t0
-    return {"value": NX * NY * n / dt / 1e9, "unit": "GLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"FP64 C oracle, 1 thread: {n} LBM steps of one 512x256 porous trajectory "
-                      f"(seed 0) in {dt:.1f} s"}
+    cores = os.cpu_count() or 1
+    v1, n1, dt1 = _oracle_glups(g, masks[0], budget_s, openmp=False)
+    try:
+        vm, nm, dtm = _oracle_glups(g, masks[0], budget_s, openmp=True)
+    except Exception as e:  # no OpenMP runtime: report the single-thread build only
+        return {"value": v1, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+                "sample": f"FP64 C oracle, 1 thread ({type(e).__name__} building the OpenMP "
+                          f"oracle): {n1} LBM steps of one 512x256 porous trajectory in {dt1:.1f} s"}
+    return {"value": vm, "unit": "GLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"FP64 C oracle, OpenMP rows on {cores} host threads: {nm} LBM steps of one "
+                      f"512x256 porous trajectory (seed 0) in {dtm:.1f} s",
+            "single_thread": {"value": v1, "unit": "GLUPS", "cores": 1,
+                              "sample": f"{n1} steps in {dt1:.1f} s"}}
+
+
+def bench_config(T, phis, solve_steps, world):
+    cells = T * NX * NY
+    return {"workload": f"porous-media steady state, {T} trajectories of {NX}x{NY} per GPU "
+                        f"(tau {TAU}, rho_in {RHO_IN}, rho_out {RHO_OUT}, disks r 4-12, "
+                        f"porosity {min(phis):.3f}-{max(phis):.3f}); step = FNO init "
+                        f"(4x32ch, 12x12 modes, BF16) + reinit + LBM until residual < {TOL:g} "
+                        f"or {solve_steps} steps",
+            "trajectories_per_gpu": T, "cells_per_gpu": cells,
+            "lbm_steps_per_step": solve_steps, "l2": "working set "
+            f"{2 * 36 * cells / 1e6:.0f} MB of populations per step > 129 MB L2, no flush",
+            "parallelism": f"independent trajectories x{world}"}
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    masks, _ = workload(1, 0)
+    masks, phis = workload(args.trajectories, 0)
     samples = []
     for _ in range(args.warmup):
-        cpu_baseline(masks, budget_s=2.0)
+        cpu_baseline(masks, budget_s=1.0)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        samples.append(cpu_baseline(masks, budget_s=8.0))
+        samples.append(cpu_baseline(masks, budget_s=6.0))
     wall = time.perf_counter() - t0
     v = float(np.mean([s["value"] for s in samples]))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "porous 512x256 steady state, CPU oracle sample"},
-            "cpu_baseline": {"value": v, "unit": "GLUPS", "cores": 1, "kind": "oracle",
-                             "sample": samples[0]["sample"]},
+            "data": "synthetic", "config": bench_config(args.trajectories, phis, args.solve_steps, 1),
+            "cpu_baseline": {"value": v, "unit": "GLUPS", "cores": samples[0]["cores"],
+                             "kind": "oracle",
+                             "sample": "each step: " + samples[0]["sample"] + " (a bounded sample "
+                                       "of the workload; GLUPS is per cell update, as in ours)"},
             "e2e": {"value": v, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -259,7 +333,11 @@ def main():
     net = Fno(FnoShape(), flat)
     lat = Lattice(grids, masks)
     cells = lat.cells
-    tuned, tune_ms = lat.autotune(reps=20)
+    if args.step_variant >= 0:
+        lat.set_step_variant(args.step_variant)
+        tune_ms = None
+    else:
+        _, tune_ms = lat.autotune(reps=20)
     shape = lat.step_variant()
     hyb = Hybrid(lat, net, HybridConfig(use_fno=1, neq_mode=1, check_every=CHECK_EVERY, tol=TOL,
                                         max_steps=args.solve_steps))
@@ -328,11 +406,88 @@ def main():
                "plain_init": arms["plain"],
                "fno": "seeded random weights (no trained weights exist here)"}
 
+    # tolerance ladder (Table 1 of the paper reports outputs to 1e-4 ... 2e-7): per trajectory,
+    # the first check step at which r < eps, FNO-initialised vs rest-state start, on a batch
+    # of --ladder-trajectories trajectories with a step cap; geometric mean over trajectories
+    ladder = None
+    if args.ladder_trajectories > 0:
+        Tl = min(args.ladder_trajectories, T)
+        eps_list = [1e-4, 1e-5, 1e-6, 2e-7, 1e-7]
+        lat_l = Lattice(grids[:Tl], masks[:Tl])
+        lat_l.set_step_variant(shape[0])
+        arms = {}
+        for name, use in (("fno_init", 1), ("plain_init", 0)):
+            h_l = Hybrid(lat_l, net if use else None,
+                         HybridConfig(use_fno=use, neq_mode=1, check_every=CHECK_EVERY, tol=1e-30,
+                                      max_steps=CHECK_EVERY))
+            first = np.full((len(eps_list), Tl), -1, dtype=np.int64)
+            l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            l0.record(stream)
+            _, _, r = h_l.advance()  # init (+ FNO and reinit) and the first CHECK_EVERY steps
+            n = CHECK_EVERY
+            while True:
+                for e, eps in enumerate(eps_list):
+                    hit = (first[e] < 0) & (r < eps)
+                    first[e][hit] = n
+                if (first[-1] >= 0).all() or n >= args.ladder_max_steps:
+                    break
+                lat_l.step(CHECK_EVERY)
+                n += CHECK_EVERY
+                r = lat_l.residual(update_prev=True, raise_unstable=False)[:, 0]
+            l1.record(stream)
+            torch.cuda.synchronize()
+            h_l.close()
+            rows = {}
+            for e, eps in enumerate(eps_list):
+                ok = first[e] > 0
+                rows[f"{eps:g}"] = {
+                    "reached": int(ok.sum()),
+                    "geomean_steps": float(np.exp(np.mean(np.log(first[e][ok])))) if ok.any() else None,
+                    "steps": [int(v) for v in first[e]]}
+            arms[name] = {"per_tol": rows, "steps_run": n, "seconds": l0.elapsed_time(l1) / 1e3}
+        lat_l.close()
+        ladder = {"trajectories": Tl, "step_cap": args.ladder_max_steps, "check_every": CHECK_EVERY,
+                  "residual": "||u^n - u^(n-100)|| / ||u^n|| over fluid cells (FP64 on the GPU)",
+                  **arms,
+                  "fno": "seeded random weights (no trained weights exist here)"}
+
+    # large single domains of the same porous generator at porosity 0.7 (1 GPU, rank 0):
+    # the step kernel alone, 200 warm-up steps then 1000 timed steps
+    sweep = None
+    if rank == 0 and not args.no_sweep:
+        sweep = []
+        for (sx, sy) in ((4096, 4096), (8192, 8192), (16384, 8192)):
+            solid = tiled_porous(sx, sy, seed=77)
+            gs = GridSpec(sx, sy, TAU, bc_west=P.BC_PRESSURE, bc_east=P.BC_PRESSURE,
+                          west_value=RHO_IN, east_value=RHO_OUT)
+            lat_s = Lattice([gs], [solid])
+            _, sw_ms = lat_s.autotune(reps=5)
+            sv = lat_s.step_variant()
+            lat_s.step(200)
+            w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            w0.record(stream)
+            lat_s.step(1000)
+            w1.record(stream)
+            torch.cuda.synchronize()
+            sms = w0.elapsed_time(w1) / 1000
+            cells_s = sx * sy
+            fluid_s = int((~solid).sum())
+            gl = cells_s / (sms * 1e-3) / 1e9
+            sweep.append({"nx": sx, "ny": sy, "cells": cells_s, "porosity": fluid_s / cells_s,
+                          "f_bytes": 2 * 36 * cells_s, "ms_per_step": sms, "glups": gl,
+                          "glups_fluid_only": fluid_s / (sms * 1e-3) / 1e9,
+                          "frac_of_measured_hbm": gl * BYTES_PER_CELL / peak,
+                          "frac_of_8tbs": gl * BYTES_PER_CELL / 8000.0,
+                          "tile_shape": {"rows_per_tile": sv[1], "stages": sv[2],
+                                         "ctas_per_sm": sv[3]}})
+            lat_s.close()
+            del solid
+
     # FNO throughput alone (B=32, 256x256, 4 channels -> 32 latent, 4 layers, 12x12 modes)
     fno_tp = None
     if rank == 0:
         Bf, Hf, Wf = 32, 256, 256
-        xin = torch.randn((Bf, 4, Hf, Wf), device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+        xin = fno_snapshot_inputs(P, GridSpec, Lattice, Bf, Hf, Wf)
         yout = torch.empty((Bf, 3, Hf, Wf), device="cuda")
         for _ in range(3):
             net(xin, yout)
@@ -352,10 +507,22 @@ def main():
             tpeak, tkind = float(pk["bf16_tflops"]), "measured burst"
         except Exception:
             tpeak, tkind = 1900.0, "fallback"
-        fno_tp = {"workload": "FNO forward, batch 32 x 256 x 256, (rho-1, ux, uy, mask), 32 latent "
-                              "channels, 4 layers, 12x12 modes, decoder 32 -> 3, BF16 / FP32 accumulate",
+        try:
+            tpeak_s = float(pk["bf16_tflops_sustained"])
+        except Exception:
+            tpeak_s = 1700.0
+        fbytes = fno_bytes(Bf, Hf, Wf)
+        fno_tp = {"workload": "FNO forward, batch 32 x 256 x 256, (rho-1, ux, uy, mask) snapshots "
+                              "after 2000 LBM steps of 32 body-force channels with 6 disks, 32 "
+                              "latent channels, 4 layers, 12x12 modes, decoder 32 -> 3, BF16 / "
+                              "FP32 accumulate",
                   "ms_per_forward": fms, "gflop_per_forward": flops / 1e9, "tflops": tf,
                   "tensor_peak_tflops": tpeak, "peak_kind": tkind, "frac_of_tensor_peak": tf / tpeak,
+                  "frac_of_sustained_tensor_peak": tf / tpeak_s,
+                  "algorithmic_gb_per_forward": fbytes / 1e9,
+                  "hbm_gbs": fbytes / (fms * 1e-3) / 1e9,
+                  "frac_of_measured_hbm": fbytes / (fms * 1e-3) / 1e9 / peak,
+                  "tensor_ceiling_at_this_intensity": (flops / fbytes) * peak / 1e3 / tpeak,
                   "tensor_cores": bool(net.uses_tensor_cores(Hf, Wf))}
 
     # batched super-time-stepping (Fig. 3b): 100 trajectories of uneven size, cycles of
@@ -443,26 +610,19 @@ def main():
             "warmup": args.warmup, "ms_per_step": t_max / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {
-                "workload": f"porous-media steady state, {T} trajectories of {NX}x{NY} per GPU "
-                            f"(tau {TAU}, rho_in {RHO_IN}, rho_out {RHO_OUT}, disks r 4-12, "
-                            f"porosity {min(phis):.3f}-{max(phis):.3f}); step = FNO init "
-                            f"(4x32ch, 12x12 modes, BF16) + reinit + LBM until residual < {TOL:g} "
-                            f"or {args.solve_steps} steps",
-                "trajectories_per_gpu": T, "cells_per_gpu": cells,
-                "lbm_steps_per_step": steps_per_solve, "l2": "working set "
-                f"{2 * 36 * cells / 1e6:.0f} MB of populations per step > 129 MB L2, no flush",
-                "parallelism": f"independent trajectories x{world}"},
+            "config": bench_config(T, phis, args.solve_steps, world),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "kernel": "k_step_tma", "bytes_per_launch": BYTES_PER_CELL * cells,
                          "tile_shape": {"rows_per_tile": shape[1], "stages": shape[2],
                                         "ctas_per_sm": shape[3], "autotune_ms": tune_ms},
-                         "launch_ms": kms, "traffic": step_kernel_traffic(cells),
+                         "launch_ms": kms, "traffic": step_kernel_traffic(cells, shape),
                          "traffic_unit": "bytes per launch (ncu dram read + write)"},
             "solve": {"lbm_steps": steps_per_solve, "converged": bool(st.converged),
                       "max_residual": float(st.max_residual)},
             "time_to_steady": tts,
+            "tolerance_ladder": ladder,
+            "lbm_sweep": sweep,
             "fno_throughput": fno_tp,
             "unsteady_hybrid": unsteady,
             "gpu_launches": None,
@@ -470,9 +630,11 @@ def main():
             "e2e": e2e,
             "cpu_baseline": cpu,
         }
-        # our kernels per step: FNO (2 twiddle + lift + 5 per layer + decoder), reinit, fill,
+        # our kernels per step: FNO on the tensor-core path (3 table kernels + lift + 4 per
+        # layer + decoder, else 2 twiddle + lift + 5 per layer + decoder), reinit, fill,
         # pack/unpack, one step kernel per LBM step, two reduction kernels per check
-        per_step = (2 + 1 + 5 * 4 + 1) + 1 + 1 + 2 + steps_per_solve + 2 * math.ceil(steps_per_solve / CHECK_EVERY)
+        fno_k = (3 + 1 + 4 * 4 + 1) if net.uses_tensor_cores(NY, NX) else (2 + 1 + 5 * 4 + 1)
+        per_step = fno_k + 1 + 1 + 2 + steps_per_solve + 2 * math.ceil(steps_per_solve / CHECK_EVERY)
         line["gpu_launches"] = per_step * args.steps
         print(json.dumps(line), flush=True)
     hyb.close()

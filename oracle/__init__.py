@@ -40,13 +40,21 @@ BC_PERIODIC, BC_PRESSURE, BC_VELOCITY = 0, 1, 2
 Q = 9
 
 
-def build(force: bool = False) -> str:
-    """Compile the C oracle (plain -O2, single thread) if it is missing or stale."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+_LIB_OMP = os.path.join(_HERE, "liblbm_oracle_omp.so")
+
+
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the C oracle if it is missing or stale: plain -O2, single thread (the parity
+    reference), or with -fopenmp, where the row loops of collision and streaming run on
+    all host cores (every cell is independent, so the results are identical)."""
+    out = _LIB_OMP if openmp else _LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".tmp{os.getpid()}"
+        flags = ["-fopenmp"] if openmp else []
+        subprocess.check_call(["gcc", "-O2", "-std=c99", *flags, "-shared", "-fPIC", "-o", tmp,
+                               _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
 class _OlGrid(ctypes.Structure):
@@ -75,29 +83,39 @@ class Grid:
 
 
 _lib: Optional[ctypes.CDLL] = None
+_lib_omp: Optional[ctypes.CDLL] = None
 
 
-def lib() -> ctypes.CDLL:
-    global _lib
+def lib(openmp: bool = False) -> ctypes.CDLL:
+    """The single-thread oracle library, or its OpenMP build."""
+    global _lib, _lib_omp
+    if openmp:
+        if _lib_omp is None:
+            _lib_omp = _declare(ctypes.CDLL(build(openmp=True)))
+        return _lib_omp
     if _lib is None:
-        _lib = ctypes.CDLL(build())
-        P = ctypes.POINTER
-        d, u8 = P(ctypes.c_double), P(ctypes.c_uint8)
-        g = P(_OlGrid)
-        for name, args in [
-            ("ol_equilibrium", [ctypes.c_double, ctypes.c_double, ctypes.c_double, d]),
-            ("ol_collide", [g, u8, d, d]),
-            ("ol_stream", [g, u8, d, d]),
-            ("ol_boundary", [g, u8, d]),
-            ("ol_run", [g, u8, d, ctypes.c_int]),
-            ("ol_macro", [g, u8, d, d, d, d]),
-            ("ol_reinit", [g, u8, d, d, d, ctypes.c_int, d]),
-            ("ol_lattice", [P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int), d]),
-        ]:
-            fn = getattr(_lib, name)
-            fn.argtypes = args
-            fn.restype = None
+        _lib = _declare(ctypes.CDLL(build()))
     return _lib
+
+
+def _declare(L: ctypes.CDLL) -> ctypes.CDLL:
+    P = ctypes.POINTER
+    d, u8 = P(ctypes.c_double), P(ctypes.c_uint8)
+    g = P(_OlGrid)
+    for name, args in [
+        ("ol_equilibrium", [ctypes.c_double, ctypes.c_double, ctypes.c_double, d]),
+        ("ol_collide", [g, u8, d, d]),
+        ("ol_stream", [g, u8, d, d]),
+        ("ol_boundary", [g, u8, d]),
+        ("ol_run", [g, u8, d, ctypes.c_int]),
+        ("ol_macro", [g, u8, d, d, d, d]),
+        ("ol_reinit", [g, u8, d, d, d, ctypes.c_int, d]),
+        ("ol_lattice", [P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int), d]),
+    ]:
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = None
+    return L
 
 
 def _dp(a: np.ndarray):
@@ -158,12 +176,13 @@ def boundary(grid: Grid, solid: np.ndarray, f: np.ndarray) -> np.ndarray:
     return f
 
 
-def run(grid: Grid, solid: np.ndarray, f: np.ndarray, nsteps: int) -> np.ndarray:
+def run(grid: Grid, solid: np.ndarray, f: np.ndarray, nsteps: int,
+        openmp: bool = False) -> np.ndarray:
     """nsteps of collide + stream; returns the post-stream populations."""
     f = np.array(f, dtype=np.float64, order="C")
     m = _mask(solid, grid)
     gc = grid.c()
-    lib().ol_run(ctypes.byref(gc), _u8(m), _dp(f), int(nsteps))
+    lib(openmp).ol_run(ctypes.byref(gc), _u8(m), _dp(f), int(nsteps))
     return f
 
 

@@ -174,10 +174,11 @@ void ol_boundary(const ol_grid* g, const uint8_t* solid, double* f) {
  * Solid cells are copied unchanged.
  */
 void ol_collide(const ol_grid* g, const uint8_t* solid, const double* f, double* fstar) {
-  double fc[OL_Q], feq[OL_Q];
   const double inv_tau = 1.0 / g->tau;
   const double guo = 1.0 - 0.5 * inv_tau;
+#pragma omp parallel for schedule(static)
   for (int y = 0; y < g->ny; ++y) {
+    double fc[OL_Q], feq[OL_Q];
     for (int x = 0; x < g->nx; ++x) {
       ol_gather(g, f, x, y, fc);
       if (!ol_solid(g, solid, x, y)) {
@@ -206,6 +207,7 @@ void ol_collide(const ol_grid* g, const uint8_t* solid, const double* f, double*
  */
 void ol_stream(const ol_grid* g, const uint8_t* solid, const double* fstar, double* f) {
   const int periodic_x = (g->bc_west == OL_BC_PERIODIC);
+#pragma omp parallel for schedule(static)
   for (int y = 0; y < g->ny; ++y) {
     for (int x = 0; x < g->nx; ++x) {
       if (ol_solid(g, solid, x, y)) {

@@ -140,6 +140,21 @@ def test_mass_conservation_2000_steps_config1_geometry():
     assert abs(m1 - m0) / m0 < 1e-12
 
 
+def test_openmp_build_is_bitwise_identical():
+    """The OpenMP build of the oracle (row loops on all host cores, used only as a timed CPU
+    baseline) gives exactly the single-thread result: every cell update is independent."""
+    solid, _, _ = synth.porous_media(96, 64, 3, 6, seed=4)
+    g = oracle.Grid(nx=96, ny=64, tau=0.7, bc_west=oracle.BC_PRESSURE,
+                    bc_east=oracle.BC_PRESSURE, west_value=1.001, east_value=1.0)
+    f0 = oracle.rest_state(g, solid)
+    try:
+        b = oracle.run(g, solid, f0, 40, openmp=True)
+    except Exception as e:  # no OpenMP runtime on this host
+        pytest.skip(f"OpenMP oracle unavailable: {e}")
+    a = oracle.run(g, solid, f0, 40)
+    np.testing.assert_array_equal(a, b)
+
+
 def test_momentum_conservation_periodic_no_force():
     g = _periodic(24, 16, 0.9)
     solid = np.zeros((16, 24), bool)
