@@ -189,6 +189,58 @@ int lbm_steps_done(const lbm_handle* h, long long* out_h);
 
 int lbm_destroy(lbm_handle* h);
 
+/* ----------------------------------------------------------------------
+ * Adjoint (reverse mode) of the LBM part of the hybrid pipeline, for training
+ * the FNO on a loss taken after LBM steps that follow its prediction (Sec. 2.3).
+ * The paper trains its networks offline on data and differentiates nothing
+ * through the LBM; these calls are this library's extension of its method.
+ *
+ * Let s_n be the stored state at time level n (what lbm_get_state returns),
+ * P the pull (streaming with halfway bounce-back of Sec. 2.1, then the Zou-He
+ * completion of the open end columns), C the BGK collision with the Guo source
+ * and M the moments:  lbm_step: s_{n+1} = C(P(s_n));  lbm_macro: M(P(s_n)).
+ * The adjoint variable mu_n (canonical layout, FP32) is the gradient of the loss
+ * with respect to the populations of level n as the pull gathers them, before
+ * the Zou-He completion: solid cells and the Zou-He unknowns of open end cells
+ * (i = 1, 5, 8 at x = 0; 3, 6, 7 at x = nx-1) hold 0.  A loss on
+ * (rho, u) of level N and initial fields (rho, u)_0 give:
+ *   mu_N = lbm_adjoint_macro(s_N, dL/drho_N, dL/du_N);
+ *   mu_{n-1} = lbm_adjoint_step(s_{n-1}, mu_n), n = N .. 1;
+ *   dL/d(rho, u)_0 = lbm_adjoint_reinit(mu_0, (rho, u)_0).
+ * States s_n come from lbm_get_state (checkpoints, recomputed in between with
+ * lbm_set_state + lbm_step); none of these calls changes the handle's state.
+ * All are asynchronous on `stream`, per-cell, deterministic (no atomics).
+ * ------------------------------------------------------------------- */
+
+/* mu_d (canonical) = adjoint seed of the moments of P(gstar_d): for fluid cells
+ * mu_j = drho + (dux (c_jx - u_x) + duy (c_jy - u_y)) / rho, then the transpose
+ * of the Zou-He completion.  gstar_d: canonical state s_N; drho_d, dux_d, duy_d:
+ * dense gradients of the loss with respect to lbm_macro's outputs (their values
+ * at solid cells are ignored). */
+int lbm_adjoint_macro(lbm_handle* h, const float* gstar_d, const float* drho_d,
+                      const float* dux_d, const float* duy_d, float* mu_d, void* stream);
+
+/* mu_prev_d (canonical) = adjoint of one time step: the transpose of the pull's
+ * gather applied to mu_d (slot (j, x) of s_n is read by cell x + c_j if that is a
+ * fluid cell of the domain, by population opp(j) of x if it is solid),
+ * times the transposed collision Jacobian at P(gstar_prev_d), then the transpose
+ * of the Zou-He completion.  gstar_prev_d: canonical state s_{n-1}.  mu_d and
+ * mu_prev_d must not alias. */
+int lbm_adjoint_step(lbm_handle* h, const float* gstar_prev_d, const float* mu_d,
+                     float* mu_prev_d, void* stream);
+
+/* Gradients with respect to the fields given to lbm_reinit_from_macro: the
+ * populations that the pull gathers after a reinit are f^eq(rho, u) + f^neq
+ * (f^neq = -(tau w_i rho / c_s^2) Q_iab d_a u_b with the library's
+ * central/one-sided differences), so dL/d(rho, u) is the transpose of that map
+ * applied to mu_d = mu_0, including the transposed difference stencils when
+ * neq_mode != 0.  rho_d, ux_d, uy_d: the dense fields the reinit was given.
+ * scratch_d: 3 * cells floats.  Outputs drho_d, dux_d, duy_d: dense (0 at solid
+ * cells).  The outputs must not alias the inputs. */
+int lbm_adjoint_reinit(lbm_handle* h, const float* mu_d, const float* rho_d, const float* ux_d,
+                       const float* uy_d, int neq_mode, float* scratch_d, float* drho_d,
+                       float* dux_d, float* duy_d, void* stream);
+
 
 /* ======================================================================
  * Fourier Neural Operator (Sec. 2.2, Fig. 2):
@@ -260,6 +312,42 @@ int fno_uses_tensor_cores(const fno_handle* h, int H, int W, int* out_h);
 int fno_check(const fno_handle* h, const void* ws_d, int B, int H, int W, void* stream);
 
 int fno_destroy(fno_handle* h);
+
+/* ----------------------------------------------------------------------
+ * FNO training path: forward with saved activations and its exact reverse mode
+ * (Sec. 2.2 network; the training objective itself is the caller's).  FP32 master
+ * parameters in the packing order of the bfloat16 pack (n_params floats), FP32
+ * activations, FP32 accumulation; no handle: every call takes the configuration
+ * and the current parameters.  Spectral-layer adjoint, per layer:
+ *   dz = dtheta' sigma'(z);  dW = sum_pixels dz theta^T;  db = sum_pixels dz;
+ *   dY = (c_kx / (H W)) F(dz);  dR = sum_batch conj(X) dY;  dX = dY conj(R)^T;
+ *   dtheta = W^T dz + Re sum_k dX e^{+i phi_k}
+ * (F the truncated forward DFT, X = F(theta) saved by the forward pass).  Limits:
+ * m <= 32, 2m <= H <= 8192, m <= W/2, W <= 2048.  Deterministic (fixed-order
+ * reductions, no atomics).
+ * ------------------------------------------------------------------- */
+typedef struct fno_train_sizes {
+  size_t n_params;    /* FP32 parameters (same order as the bfloat16 pack) */
+  size_t saved_bytes; /* activations kept from forward to backward */
+  size_t ws_bytes;    /* scratch of either call */
+} fno_train_sizes;
+
+int fno_train_query(const fno_config* cfg_h, int B, int H, int W, fno_train_sizes* out_h);
+
+/* out_d [B][c_out][H][W] = FNO(in_d [B][c_in][H][W]); the input is used as given
+ * (no bfloat16 rounding), the coordinate channels as in fno_forward.  saved_d:
+ * saved_bytes, kept unchanged until the matching backward; ws_d: ws_bytes,
+ * 256-byte aligned.  Parameters are read, not kept. */
+int fno_train_forward(const fno_config* cfg_h, const float* params_d, const float* in_d,
+                      float* out_d, int B, int H, int W, float* saved_d, void* ws_d,
+                      void* stream);
+
+/* Given dout_d = dL/dout, writes dparams_d (n_params, overwritten) = dL/dparams and,
+ * if din_d is not NULL, din_d [B][c_in][H][W] = dL/din.  params_d and saved_d must
+ * be those of the forward call. */
+int fno_train_backward(const fno_config* cfg_h, const float* params_d, const float* dout_d,
+                       const float* saved_d, float* dparams_d, float* din_d, int B, int H, int W,
+                       void* ws_d, void* stream);
 
 /* ======================================================================
  * Hybrid FNO-LBM framework (Sec. 2.3, Fig. 3)

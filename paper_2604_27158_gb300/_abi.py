@@ -55,6 +55,11 @@ class fno_sizes(ctypes.Structure):
                 ("ws_bytes", ctypes.c_size_t)]
 
 
+class fno_train_sizes(ctypes.Structure):
+    _fields_ = [("n_params", ctypes.c_size_t), ("saved_bytes", ctypes.c_size_t),
+                ("ws_bytes", ctypes.c_size_t)]
+
+
 class hybrid_config(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("use_fno", ctypes.c_int32), ("neq_mode", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("tol", ctypes.c_double),
@@ -92,6 +97,9 @@ _PROTOS = {
     "lbm_get_step_variant": ([VP, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                               ctypes.POINTER(I)], I),
     "lbm_destroy": ([VP], I),
+    "lbm_adjoint_macro": ([VP, VP, VP, VP, VP, VP, VP], I),
+    "lbm_adjoint_step": ([VP, VP, VP, VP, VP], I),
+    "lbm_adjoint_reinit": ([VP, VP, VP, VP, VP, I, VP, VP, VP, VP, VP], I),
     "fno_query": ([ctypes.POINTER(fno_config), I, I, I, ctypes.POINTER(fno_sizes)], I),
     "fno_create": ([ctypes.POINTER(fno_config), VP, VP, VP, ctypes.POINTER(VP)], I),
     "fno_forward": ([VP, VP, VP, I, I, I, VP, ctypes.c_size_t, VP], I),
@@ -100,6 +108,9 @@ _PROTOS = {
     "fno_uses_tensor_cores": ([VP, I, I, ctypes.POINTER(I)], I),
     "fno_check": ([VP, VP, I, I, I, VP], I),
     "fno_destroy": ([VP], I),
+    "fno_train_query": ([ctypes.POINTER(fno_config), I, I, I, ctypes.POINTER(fno_train_sizes)], I),
+    "fno_train_forward": ([ctypes.POINTER(fno_config), VP, VP, VP, I, I, I, VP, VP, VP], I),
+    "fno_train_backward": ([ctypes.POINTER(fno_config), VP, VP, VP, VP, VP, I, I, I, VP, VP], I),
     "hybrid_query_ws": ([ctypes.POINTER(lbm_grid), I, ctypes.POINTER(fno_config),
                          ctypes.POINTER(ctypes.c_size_t)], I),
     "hybrid_create": ([VP, VP, ctypes.POINTER(hybrid_config), VP, ctypes.c_size_t,

@@ -152,6 +152,40 @@ class Lattice:
         call("lbm_steps_done", self._h, ctypes.byref(v))
         return v.value
 
+    # ------------------------------------------------------------- adjoint
+    def adjoint_macro(self, gstar: torch.Tensor, drho: torch.Tensor, dux: torch.Tensor,
+                      duy: torch.Tensor, stream=None) -> torch.Tensor:
+        """Adjoint seed mu_N of a loss on lbm_macro's outputs at the state gstar (canonical)."""
+        for t in (drho, dux, duy):
+            assert t.dtype == torch.float32 and t.is_contiguous() and t.numel() == self.cells
+        assert gstar.dtype == torch.float32 and gstar.numel() == 9 * self.cells
+        mu = torch.empty(9 * self.cells, dtype=torch.float32, device=self.device)
+        call("lbm_adjoint_macro", self._h, gstar.data_ptr(), drho.data_ptr(), dux.data_ptr(),
+             duy.data_ptr(), mu.data_ptr(), _stream_ptr(stream))
+        return mu
+
+    def adjoint_step(self, gstar_prev: torch.Tensor, mu: torch.Tensor, out=None,
+                     stream=None) -> torch.Tensor:
+        """mu_{n-1} from mu_n and the stored state s_{n-1} (canonical)."""
+        assert gstar_prev.numel() == 9 * self.cells and mu.numel() == 9 * self.cells
+        if out is None:
+            out = torch.empty_like(mu)
+        call("lbm_adjoint_step", self._h, gstar_prev.data_ptr(), mu.data_ptr(), out.data_ptr(),
+             _stream_ptr(stream))
+        return out
+
+    def adjoint_reinit(self, mu: torch.Tensor, rho: torch.Tensor, ux: torch.Tensor,
+                       uy: torch.Tensor, neq_mode: int = 1, stream=None):
+        """(dL/drho, dL/dux, dL/duy) of the fields given to reinit, from mu_0."""
+        for t in (rho, ux, uy):
+            assert t.dtype == torch.float32 and t.is_contiguous() and t.numel() == self.cells
+        scratch = torch.empty(3 * self.cells, dtype=torch.float32, device=self.device)
+        out = [torch.empty(self.cells, dtype=torch.float32, device=self.device) for _ in range(3)]
+        call("lbm_adjoint_reinit", self._h, mu.data_ptr(), rho.data_ptr(), ux.data_ptr(),
+             uy.data_ptr(), int(neq_mode), scratch.data_ptr(), *[o.data_ptr() for o in out],
+             _stream_ptr(stream))
+        return tuple(out)
+
     def split(self, dense: torch.Tensor, per_cell: int = 1):
         """Split a dense (or canonical, per_cell=9) field into per-grid [.., ny, nx] views."""
         out = []
