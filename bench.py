@@ -61,6 +61,8 @@ def parse():
                     help="trajectories of the tolerance ladder (steps to 1e-4 ... 1e-7, both starts)")
     ap.add_argument("--ladder-max-steps", type=int, default=100000)
     ap.add_argument("--no-sweep", action="store_true", help="skip the large-domain LBM sweep")
+    ap.add_argument("--train-steps", type=int, default=5,
+                    help="timed steps of the differentiable hybrid training workload (0: skip)")
     ap.add_argument("--step-variant", type=int, default=-1,
                     help="step-kernel tile shape index; -1 (default) times all shapes and keeps the fastest")
     return ap.parse_args()
@@ -579,6 +581,64 @@ def main():
         lat_h.close()
         lat_r.close()
 
+    # differentiable hybrid training step (rank 0): batch 8 porous 512 x 512, FNO 4 x 64
+    # channels, 13 x 13 modes (11.1 M parameters, FP32 master weights), loss = MSE of
+    # (rho, u) after 32 LBM steps that follow the FNO-based reinit, backward through the
+    # LBM adjoint with f checkpointed every 8 steps, then an Adam update
+    training = None
+    if rank == 0 and args.train_steps > 0:
+        import synth
+        from paper_2604_27158_gb300.train import hybrid_loss
+        Bt, Nt = 8, 512
+        tshape_s = synth.FnoShape(c_in=4, c_out=3, width=64, layers=4, modes=13, dec_layers=1,
+                                  dec_size=64)
+        tshape = FnoShape(c_in=4, c_out=3, width=64, layers=4, modes=13, dec_layers=1,
+                          dec_size=64)
+        tparams = torch.nn.Parameter(torch.from_numpy(synth.fno_flatten_params(
+            tshape_s, synth.fno_random_params(tshape_s, seed=5, out_scale=1e-2))
+            .astype(np.float32)).cuda())
+        tmasks = [synth.porous_media(Nt, Nt, 4, 12, seed=300 + k)[0] for k in range(Bt)]
+        lat_t = Lattice([GridSpec(Nt, Nt, TAU, bc_west=P.BC_PRESSURE, bc_east=P.BC_PRESSURE,
+                                  west_value=RHO_IN, east_value=RHO_OUT)] * Bt, tmasks)
+        xt = torch.zeros((Bt, 4, Nt, Nt), device="cuda")
+        xt[:, 3] = torch.from_numpy(np.stack(tmasks).astype(np.float32)).cuda()
+        tgt = [torch.from_numpy(np.concatenate([np.asarray(synth.smooth_macro_fields(
+            Nt, Nt, seed=400 + k, drho=1e-3, umax=0.02)[c]).ravel() for k in range(Bt)])).cuda()
+            for c in range(3)]
+        fluid_t = torch.from_numpy(~np.concatenate([m.ravel() for m in tmasks])).cuda()
+        opt = torch.optim.Adam([tparams], lr=1e-4)
+
+        def train_step():
+            opt.zero_grad(set_to_none=True)
+            loss = hybrid_loss(lat_t, tshape, tparams, xt, 32, tgt, every=8, fluid=fluid_t)
+            loss.backward()
+            opt.step()
+            return loss
+
+        for _ in range(2):
+            train_step()
+        torch.cuda.synchronize()
+        t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0e.record(stream)
+        tl = []
+        for _ in range(args.train_steps):
+            tl.append(train_step())
+        t1e.record(stream)
+        torch.cuda.synchronize()
+        tms = t0e.elapsed_time(t1e) / args.train_steps
+        training = {
+            "workload": "differentiable hybrid training step: batch 8 porous 512x512, FNO 4 "
+                        "layers x 64 channels, 13x13 modes, decoder 64 -> 3 (FP32 master "
+                        "weights), reinit, 32 LBM steps, MSE of (rho, u), backward through the "
+                        "LBM adjoint (checkpoints every 8 steps) and the FNO adjoint, Adam",
+            "params": int(tparams.numel()), "ms_per_step": tms,
+            "samples_per_s": Bt / (tms * 1e-3),
+            "loss_first_last": [float(tl[0]), float(tl[-1])],
+            "gradient_check": "tests/test_gpu_train.py, tests/test_gpu_adjoint.py (FP64 "
+                              "autograd references pinned to central differences)"}
+        lat_t.close()
+        del lat_t, tparams, opt
+
     # end to end through the public API with host buffers (pinned): masks in, fields out
     e2e = None
     if args.steps > 0:
@@ -623,6 +683,7 @@ def main():
             "time_to_steady": tts,
             "tolerance_ladder": ladder,
             "lbm_sweep": sweep,
+            "hybrid_training": training,
             "fno_throughput": fno_tp,
             "unsteady_hybrid": unsteady,
             "gpu_launches": None,

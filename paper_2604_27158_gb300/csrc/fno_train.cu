@@ -364,12 +364,14 @@ __global__ void __launch_bounds__(kSpecThreads) k_tr_dft_x(const float* __restri
       for (int k = 0; k < kAccMax; ++k) {
         const int kx = g + k * G;
         if (kx < m) {
+          int idx = (kx * x0) % W;  // phase index (kx x) mod W, advanced by kx per x
           for (int xx = 0; xx < nx; ++xx) {
-            const int x = x0 + xx;
-            const float2 e = tw[(int)(((long long)kx * x) % W)];
+            const float2 e = tw[idx];
             const float v = tile[xx * C + c];
             acc[k].x = fmaf(v, e.x, acc[k].x);
             acc[k].y = fmaf(-v, e.y, acc[k].y);
+            idx += kx;
+            if (idx >= W) idx -= W;
           }
         }
       }
@@ -416,9 +418,11 @@ __global__ void __launch_bounds__(kSpecThreads) k_tr_dft_y(const float2* __restr
         const int a = g + k * G;
         if (a < 2 * m) {
           const int ky = a < m ? a : H - 2 * m + a;
+          int idx = (int)(((long long)ky * y0) % H);  // (ky y) mod H, advanced by ky per y
           for (int yy = 0; yy < ny; ++yy) {
-            const int y = y0 + yy;
-            const float2 e = tw[(int)(((long long)ky * y) % H)];  // e^{+i}: use conj
+            const float2 e = tw[idx];  // e^{+i}: use conj
+            idx += ky;
+            if (idx >= H) idx -= H;
             const float2 v = tile[yy * C + c];
             // v * conj(e)
             acc[k].x = fmaf(v.x, e.x, fmaf(v.y, e.y, acc[k].x));
@@ -522,9 +526,12 @@ __global__ void __launch_bounds__(kSpecThreads) k_tr_inv_y(const float2* __restr
   if (g >= G) return;
   for (int y = g; y < H; y += G) {
     float re = 0.f, im = 0.f;
+    int idx = 0;  // (ky y) mod H for ky = 0 .. m-1, then H-m .. H-1
     for (int a = 0; a < 2 * m; ++a) {
-      const int ky = a < m ? a : H - 2 * m + a;
-      const float2 e = tw[(int)(((long long)ky * y) % H)];
+      if (a == m) idx = (int)(((long long)(H - m) * y) % H);
+      const float2 e = tw[idx];
+      idx += y;
+      if (idx >= H) idx -= H;
       const float2 v = col[a * C + c];
       re = fmaf(v.x, e.x, fmaf(-v.y, e.y, re));
       im = fmaf(v.x, e.y, fmaf(v.y, e.x, im));
@@ -557,8 +564,11 @@ __global__ void __launch_bounds__(kSpecThreads) k_tr_inv_x(const float2* __restr
   if (g >= G) return;
   for (int x = g; x < W; x += G) {
     float acc = 0.f;
+    int idx = 0;  // (kx x) mod W
     for (int kx = 0; kx < m; ++kx) {
-      const float2 e = tw[(int)(((long long)kx * x) % W)];
+      const float2 e = tw[idx];
+      idx += x;
+      if (idx >= W) idx -= W;
       const float2 v = zr[kx * C + c];
       acc = fmaf(v.x, e.x, fmaf(-v.y, e.y, acc));
     }
