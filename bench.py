@@ -61,6 +61,8 @@ def parse():
                     help="trajectories of the tolerance ladder (steps to 1e-4 ... 1e-7, both starts)")
     ap.add_argument("--ladder-max-steps", type=int, default=100000)
     ap.add_argument("--no-sweep", action="store_true", help="skip the large-domain LBM sweep")
+    ap.add_argument("--shear-trajectories", type=int, default=100,
+                    help="double-shear-layer trajectories (0: skip the workload)")
     ap.add_argument("--train-steps", type=int, default=5,
                     help="timed steps of the differentiable hybrid training workload (0: skip)")
     ap.add_argument("--step-variant", type=int, default=-1,
@@ -581,6 +583,94 @@ def main():
         lat_h.close()
         lat_r.close()
 
+    # double shear layer (Sec. 3.2): periodic 128^2, 100 trajectories, the 2.6 M model group
+    # (density net on rho - 1: 14 channels, 3 layers, 8 modes; velocity net on (u, v): 14
+    # channels, 3 layers, 32 modes; decoders 1 x 32; padding 9), random weights.  Hybrids
+    # 1:k = one FNO step of Delta T = 223 LBM steps, then k Delta T of LBM, against pure
+    # LBM over the same physical time; and the pure autoregressive FNO rollout.
+    shear = None
+    if rank == 0 and args.shear_trajectories > 0:
+        import synth
+        setup = synth.DoubleShear()
+        ns, Ts, dT = setup.n, args.shear_trajectories, setup.steps_per_dT
+        ics = synth.double_shear(Ts, seed=2000)
+        s_fields = [torch.from_numpy(np.concatenate([ic[k].ravel() for ic in ics])).cuda()
+                    for k in ("rho", "ux", "uy")]
+        s_grids = [GridSpec(ns, ns, setup.tau)] * Ts
+        s_masks = [np.zeros((ns, ns), bool)] * Ts
+        d_s = synth.FnoShape(c_in=1, c_out=1, width=14, layers=3, modes=8, dec_size=32, padding=9)
+        v_s = synth.FnoShape(c_in=2, c_out=2, width=14, layers=3, modes=32, dec_size=32,
+                             padding=9)
+        nparams = [int(sum(int(np.prod(sh)) for _, sh in synth.fno_param_shapes(x)))
+                   for x in (d_s, v_s)]
+        dnet = Fno(FnoShape(c_in=1, c_out=1, width=14, layers=3, modes=8, dec_size=32, padding=9),
+                   synth.fno_flatten_params(d_s, synth.fno_random_params(d_s, seed=31,
+                                                                         out_scale=1e-2)))
+        vnet = Fno(FnoShape(c_in=2, c_out=2, width=14, layers=3, modes=32, dec_size=32,
+                            padding=9),
+                   synth.fno_flatten_params(v_s, synth.fno_random_params(v_s, seed=32,
+                                                                         out_scale=1e-2)))
+
+        def s_metrics(lat_a, lat_b):
+            ra, ua, va = lat_a.macro()
+            rb, ub, vb = lat_b.macro()
+            mse = float(((ra - rb) ** 2 + (ua - ub) ** 2 + (va - vb) ** 2).mean() / 3.0)
+            wa = lat_a.vorticity(ua, va).view(Ts, -1)
+            wb = lat_b.vorticity(ub, vb).view(Ts, -1)
+            ew = float(((wa - wb).norm(dim=1) / wb.norm(dim=1)).mean())
+            return mse, ew
+
+        arms = {}
+        for label, k in (("1:1", 1), ("1:2", 2), ("1:3", 3), ("fno_only", 0)):
+            cyc = 30 if k == 0 else -(-30 // (k + 1))
+            lat_h = Lattice(s_grids, s_masks, u_max=0.3)
+            lat_r = Lattice(s_grids, s_masks, u_max=0.3)
+            lat_h.reinit(*s_fields, neq_mode=1)
+            lat_r.reinit(*s_fields, neq_mode=1)
+            hyb_s = Hybrid(lat_h, dnet, HybridConfig(mode=1, k_lbm=k * dT, m_fno=1, neq_mode=1,
+                                                     in_channels=1, in_channels_u=6), fno_u=vnet)
+            hms, rms_, mses, ews = [], [], [], []
+            for _ in range(cyc):
+                c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                c0.record(stream)
+                hyb_s.advance(cycles=1)
+                c1.record(stream)
+                r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                r0.record(stream)
+                lat_r.step((k + 1) * dT)
+                r1.record(stream)
+                torch.cuda.synchronize()
+                hms.append(c0.elapsed_time(c1))
+                rms_.append(r0.elapsed_time(r1))
+                m_, w_ = s_metrics(lat_h, lat_r)
+                mses.append(m_)
+                ews.append(w_)
+            steady_h = float(np.mean(hms[1:])) if cyc > 1 else hms[0]
+            arms[label] = {"cycles": cyc, "lbm_steps_per_cycle": k * dT,
+                           "cycle_ms": steady_h, "pure_lbm_ms_same_time": float(np.mean(rms_)),
+                           "eps_T": 1.0 - steady_h / float(np.mean(rms_)),
+                           "eps_N": 1.0 - k / (k + 1.0),
+                           "mse_per_cycle": mses, "vorticity_rel_l2_per_cycle": ews,
+                           "mse_global": float(np.mean(mses)),
+                           "vorticity_global": float(np.mean(ews))}
+            hyb_s.close()
+            lat_h.close()
+            lat_r.close()
+        for label in ("1:1", "1:2", "1:3"):
+            for key in ("mse_global", "vorticity_global"):
+                base = arms["fno_only"][key]
+                arms[label][key.replace("_global", "_reduction_vs_fno")] = (
+                    (base - arms[label][key]) / base if base > 0 else None)
+        shear = {"workload": f"double shear layer, {Ts} trajectories of {ns}x{ns} periodic, "
+                             f"tau {setup.tau:.4f}, U {setup.u_lattice:.4f} (lattice), A1, A2 "
+                             f"U(20, 125), Delta T = {dT} steps, 30 Delta T horizon",
+                 "model_group": {"density_params": nparams[0], "velocity_params": nparams[1],
+                                 "padding": 9, "path": "CUDA cores (14 channels, padded grid)"},
+                 "arms": arms,
+                 "fno": "seeded random weights: errors are not an accuracy claim"}
+        dnet.close()
+        vnet.close()
+
     # differentiable hybrid training step (rank 0): batch 8 porous 512 x 512, FNO 4 x 64
     # channels, 13 x 13 modes (11.1 M parameters, FP32 master weights), loss = MSE of
     # (rho, u) after 32 LBM steps that follow the FNO-based reinit, backward through the
@@ -684,6 +774,7 @@ def main():
             "tolerance_ladder": ladder,
             "lbm_sweep": sweep,
             "hybrid_training": training,
+            "double_shear": shear,
             "fno_throughput": fno_tp,
             "unsteady_hybrid": unsteady,
             "gpu_launches": None,

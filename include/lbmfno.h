@@ -157,6 +157,13 @@ int lbm_residual_static(lbm_handle* h, double* out_h, int update_prev, void* str
 int lbm_reinit_from_macro(lbm_handle* h, const float* rho_d, const float* ux_d,
                           const float* uy_d, int neq_mode, void* stream);
 
+/* Vorticity omega = d_x u_y - d_y u_x of dense velocity fields (the unsteady
+ * accuracy metric, Sec. 3.2.2: normalised vorticity error), with the difference
+ * stencils of lbm_reinit_from_macro (central; one-sided next to solid cells and open
+ * ends; periodic wrap).  Dense layout; solid cells get 0. */
+int lbm_vorticity(lbm_handle* h, const float* ux_d, const float* uy_d, float* omega_d,
+                  void* stream);
+
 /* Post-stream shifted populations g_i = f_i - w_i of the current time level
  * (after bounce-back and Zou-He completion), canonical layout, 9*cells floats.
  * Solid cells export 0. */
@@ -271,6 +278,9 @@ typedef struct fno_config {
   int32_t dec_layers; /* hidden decoder layers (>= 1) */
   int32_t dec_size;   /* decoder width S (<= 64) */
   int32_t activation; /* enum fno_activation */
+  int32_t padding;    /* zero padding of the latent field after lifting, at the high
+                         end of both axes; cropped after the last Fourier layer
+                         (appendix tables: "Padding: 9"); 0 <= padding <= 64 */
 } fno_config;
 
 typedef struct fno_sizes {
@@ -282,7 +292,7 @@ typedef struct fno_sizes {
 typedef struct fno_handle fno_handle;
 
 /* Sizes for a configuration and a forward shape B x H x W (host only).
- * Requires 2m <= H and m < W/2. */
+ * Requires 2m <= H + padding and m < (W + padding)/2. */
 int fno_query(const fno_config* cfg_h, int B, int H, int W, fno_sizes* out_h);
 
 /* Repack the bfloat16 parameter pack params_d (n_params values, device) into
@@ -300,7 +310,7 @@ int fno_forward(fno_handle* h, const float* in_d, float* out_d, int B, int H, in
 int fno_get_config(const fno_handle* h, fno_config* out_h);
 
 /* Kernel path.  FNO_PATH_AUTO (default): tcgen05 tensor-core kernels where the
- * shape allows (C in {16, 32, 64}, m <= 16, W a multiple of 128, W <= 2048),
+ * shape allows (C in {16, 32, 64}, m <= 16, W a multiple of 128, W <= 2048, no padding),
  * CUDA-core kernels otherwise.  FNO_PATH_CUDA_CORES: always the CUDA-core
  * kernels (same results up to rounding). */
 enum fno_path { FNO_PATH_AUTO = 0, FNO_PATH_CUDA_CORES = 1 };
@@ -357,8 +367,12 @@ int fno_train_backward(const fno_config* cfg_h, const float* params_d, const flo
  *            steps) or max_steps.  use_fno = 0 runs the plain rest-state start.
  *   unsteady (Fig. 3b): per cycle k_lbm LBM steps, then m_fno FNO steps on the
  *            macroscopic fields, then re-initialisation of f.
- * FNO inputs are (rho - 1, u_x, u_y, mask) per cell, outputs (rho - 1, u_x, u_y).
- * Grids of equal size share one FNO call.
+ * FNO input planes are chosen from (rho - 1, u_x, u_y, mask) per cell (a bit mask,
+ * bit 0 = rho - 1, bit 1 = u_x, bit 2 = u_y, bit 3 = mask; 0 means all four, in that
+ * order).  One network maps its planes to (rho - 1, u_x, u_y); or, as the paper's
+ * model groups are built (appendix tables), a density network (one output, rho - 1)
+ * and a velocity network (two outputs, u_x and u_y), both reading the fields of the
+ * same time level.  Grids of equal size share one FNO call per network.
  * ====================================================================== */
 enum hybrid_mode { HYBRID_STEADY = 0, HYBRID_UNSTEADY = 1 };
 
@@ -373,23 +387,30 @@ typedef struct hybrid_config {
   int32_t m_fno;       /* unsteady: FNO steps per cycle */
   double rho_lo, rho_hi; /* clamp of the predicted density before re-initialisation */
   double u_clamp;        /* clamp of the predicted speed */
+  int32_t in_channels;   /* input planes of the (density) network, 0 = all four */
+  int32_t in_channels_u; /* input planes of the velocity network, 0 = all four */
 } hybrid_config;
 
 typedef struct hybrid_stats {
   int64_t steps;       /* LBM steps taken by this call */
   int32_t converged;   /* steady: all grids below tol */
-  int32_t fno_calls;   /* fno_forward calls made */
+  int32_t fno_calls;   /* fno_forward calls made (per size group and network) */
   double max_residual; /* steady: largest final residual over grids */
 } hybrid_stats;
 
 typedef struct hybrid_handle hybrid_handle;
 
-/* Device workspace bytes of a hybrid over the LBM batch `grids_h` with FNO `cfg_h`. */
-int hybrid_query_ws(const lbm_grid* grids_h, int ngrids, const fno_config* cfg_h, size_t* ws_h);
+/* Device workspace bytes of a hybrid over the LBM batch `grids_h` with the network
+ * `cfg_h` and, if cfg_u_h is not NULL, the velocity network cfg_u_h. */
+int hybrid_query_ws(const lbm_grid* grids_h, int ngrids, const fno_config* cfg_h,
+                    const fno_config* cfg_u_h, size_t* ws_h);
 
-/* Couple an LBM handle and an FNO handle (both stay owned by the caller). */
-int hybrid_create(lbm_handle* lbm, fno_handle* fno, const hybrid_config* cfg_h, void* ws_d,
-                  size_t ws_bytes, hybrid_handle** out);
+/* Couple an LBM handle with one FNO (fno_u NULL: c_out = 3) or with a density network
+ * `fno` (c_out = 1) and a velocity network `fno_u` (c_out = 2).  Each network's c_in
+ * must equal the number of planes its in_channels selects.  All handles stay owned by
+ * the caller. */
+int hybrid_create(lbm_handle* lbm, fno_handle* fno, fno_handle* fno_u, const hybrid_config* cfg_h,
+                  void* ws_d, size_t ws_bytes, hybrid_handle** out);
 
 /*
  * Steady mode: cycles is ignored; runs to convergence or max_steps.

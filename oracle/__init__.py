@@ -215,6 +215,29 @@ def rest_state(grid: Grid, solid: np.ndarray) -> np.ndarray:
     return reinit(grid, solid, one, zero, zero, neq_mode=0)
 
 
+def derivative(grid: Grid, solid: np.ndarray, v, axis: int) -> np.ndarray:
+    """d v / d x (axis 0) or d v / d y (axis 1) at every fluid cell: central where both
+    neighbours along the axis are fluid cells of the domain, one-sided where only one
+    is, zero where none is (y periodic; x periodic only for periodic grids).  The
+    velocity-gradient estimate of the re-initialisation and of the vorticity."""
+    v = np.asarray(v, dtype=np.float64)
+    fluid = ~np.asarray(solid, dtype=bool)
+    ax = 1 if axis == 0 else 0
+    vp, vm = np.roll(v, -1, axis=ax), np.roll(v, 1, axis=ax)
+    fp, fm = np.roll(fluid, -1, axis=ax), np.roll(fluid, 1, axis=ax)
+    if axis == 0 and grid.bc_west != BC_PERIODIC:
+        fp[:, -1] = False
+        fm[:, 0] = False
+    d = np.where(fp & fm, 0.5 * (vp - vm), np.where(fp, vp - v, np.where(fm, v - vm, 0.0)))
+    return np.where(fluid, d, 0.0)
+
+
+def vorticity(grid: Grid, solid: np.ndarray, ux, uy) -> np.ndarray:
+    """omega = d u_y / d x - d u_x / d y (the vorticity of the unsteady error metric,
+    Sec. 3.2.2); 0 at solid cells."""
+    return derivative(grid, solid, uy, 0) - derivative(grid, solid, ux, 1)
+
+
 def steady_residual(solid: np.ndarray, ux_now, uy_now, ux_prev, uy_prev) -> float:
     """r = ||u^n - u^(n-K)||_2 / ||u^n||_2 over fluid cells (steady-state criterion)."""
     fl = ~np.asarray(solid, dtype=bool)
@@ -236,21 +259,42 @@ def fno_input(solid: np.ndarray, rho, ux, uy) -> np.ndarray:
     return np.stack([rho - 1.0, ux, uy, np.asarray(solid, dtype=np.float64)])
 
 
+ALL_CHANNELS = (0, 1, 2, 3)  # indices into the input planes (rho - 1, u_x, u_y, mask)
+
+
+def fno_predict(solid, rho, ux, uy, nets, activation="gelu", clamp=(0.9, 1.1, 0.2)):
+    """One FNO step on the macroscopic fields (Sec. 2.3), clamped.
+
+    nets: ((shape, params, channels),) for one network mapping the selected input planes
+    to (delta rho, u_x, u_y), or ((shape_rho, params_rho, channels_rho), (shape_u,
+    params_u, channels_u)) for a density network (one output, delta rho) and a velocity
+    network (two outputs, u_x and u_y), as the paper's model groups are built.  Both
+    networks read the fields of the same time level."""
+    planes = fno_input(solid, rho, ux, uy)
+    outs = [fno_forward(sh, pa, planes[list(ch)][None], activation=activation)[0]
+            for sh, pa, ch in nets]
+    if len(nets) == 1:
+        dr, vx, vy = outs[0]
+    else:
+        dr, (vx, vy) = outs[0][0], outs[1]
+    return clamp_macro(1.0 + dr, vx, vy, *clamp)
+
+
 def hybrid_steady(grid: Grid, solid: np.ndarray, shape, params, nsteps: int,
                   check_every: int = 100, neq_mode: int = 1, use_fno: bool = True,
-                  activation: str = "gelu", clamp=(0.9, 1.1, 0.2)):
+                  activation: str = "gelu", clamp=(0.9, 1.1, 0.2), nets=None):
     """Steady framework (Fig. 3a): FNO prediction -> re-initialisation -> LBM.
 
     The FNO sees the default fields (rho = 1, u = 0) and the mask; its output
-    (delta rho, u_x, u_y) is clamped and turned into populations.  Returns
-    (f, residual history [(step, r)]).
+    (delta rho, u_x, u_y) is clamped and turned into populations.  `nets` overrides the
+    single (shape, params) network (see fno_predict).  Returns (f, residual history
+    [(step, r)]).
     """
     one = np.ones((grid.ny, grid.nx))
     zero = np.zeros_like(one)
     if use_fno:
-        x = fno_input(solid, one, zero, zero)[None]
-        y = fno_forward(shape, params, x, activation=activation)[0]
-        rho, ux, uy = clamp_macro(1.0 + y[0], y[1], y[2], *clamp)
+        nets = nets or ((shape, params, ALL_CHANNELS),)
+        rho, ux, uy = fno_predict(solid, one, zero, zero, nets, activation, clamp)
         f = reinit(grid, solid, rho, ux, uy, neq_mode)
     else:
         f = rest_state(grid, solid)
@@ -269,16 +313,16 @@ def hybrid_steady(grid: Grid, solid: np.ndarray, shape, params, nsteps: int,
 
 def hybrid_unsteady(grid: Grid, solid: np.ndarray, shape, params, f0: np.ndarray,
                     k_lbm: int, m_fno: int, cycles: int, neq_mode: int = 1,
-                    activation: str = "gelu", clamp=(0.9, 1.1, 0.2)):
+                    activation: str = "gelu", clamp=(0.9, 1.1, 0.2), nets=None):
     """Super-time-stepping (Fig. 3b): per cycle k_lbm LBM steps, then m_fno FNO
-    steps on the macroscopic fields, then re-initialisation of f.  Returns f."""
+    steps on the macroscopic fields, then re-initialisation of f.  `nets` overrides
+    the single (shape, params) network (see fno_predict).  Returns f."""
+    nets = nets or ((shape, params, ALL_CHANNELS),)
     f = np.array(f0, dtype=np.float64)
     for _ in range(cycles):
         f = run(grid, solid, f, k_lbm)
         rho, ux, uy = macro(grid, solid, f)
         for _ in range(m_fno):
-            y = fno_forward(shape, params, fno_input(solid, rho, ux, uy)[None],
-                            activation=activation)[0]
-            rho, ux, uy = clamp_macro(1.0 + y[0], y[1], y[2], *clamp)
+            rho, ux, uy = fno_predict(solid, rho, ux, uy, nets, activation, clamp)
         f = reinit(grid, solid, rho, ux, uy, neq_mode)
     return f

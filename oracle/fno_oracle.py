@@ -25,6 +25,9 @@ Readings of points the paper leaves open:
     Both are available.
   * Q is `dec_layers` hidden pointwise layers of width `dec_size` with the
     activation, then a linear output layer.
+  * Padding ("Padding: 9" in the appendix tables): the lifted latent field is
+    zero-padded by `padding` cells at the high end of both axes, the Fourier layers
+    run on the padded grid, and the field is cropped back to H x W before Q.
   * Precision: parameters and inputs are rounded to bfloat16 first, then every
     operation runs in float64, so a comparison measures only compute error.
 """
@@ -130,6 +133,10 @@ def fno_forward(shape: FnoShape, params: dict, phi: np.ndarray, activation: str 
     # lifting network P
     h = act(_pointwise(p["lift0.w"], p["lift0.b"], x))
     theta = _pointwise(p["lift1.w"], p["lift1.b"], h)
+    # optional zero padding of the latent field at the high end of both axes
+    pad = getattr(shape, "padding", 0)
+    if pad:
+        theta = np.pad(theta, ((0, 0), (0, 0), (0, pad), (0, pad)))
     latents = [theta]
     # Fourier layers
     for n in range(shape.layers):
@@ -138,8 +145,8 @@ def fno_forward(shape: FnoShape, params: dict, phi: np.ndarray, activation: str 
         s = spectral_conv(theta, r1, r2)
         theta = act(_pointwise(p[f"layer{n}.w"], p[f"layer{n}.b"], theta) + s)
         latents.append(theta)
-    # projection Q
-    h = theta
+    # crop back to the input grid after the last Fourier layer, then projection Q
+    h = theta[:, :, :H, :W]
     for l in range(shape.dec_layers):
         h = act(_pointwise(p[f"dec{l}.w"], p[f"dec{l}.b"], h))
     out = _pointwise(p["out.w"], p["out.b"], h)

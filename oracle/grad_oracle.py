@@ -244,16 +244,20 @@ def fno_forward(shape, params: Dict[str, torch.Tensor], phi: torch.Tensor,
 
     h = act(pw(params["lift0.w"], params["lift0.b"], x))
     theta = pw(params["lift1.w"], params["lift1.b"], h)
-    Fy, Fx, Gy, Gx = _dft_mats(H, W, shape.modes)
+    pad = getattr(shape, "padding", 0)
+    if pad:  # zero padding of the latent field, cropped after the last layer
+        theta = torch.nn.functional.pad(theta, (0, pad, 0, pad))
+    Hp, Wp = H + pad, W + pad
+    Fy, Fx, Gy, Gx = _dft_mats(Hp, Wp, shape.modes)
     for n in range(shape.layers):
         R = torch.cat([torch.complex(params[f"layer{n}.r1.re"], params[f"layer{n}.r1.im"]),
                        torch.complex(params[f"layer{n}.r2.re"], params[f"layer{n}.r2.im"])],
                       dim=2)
         X = Fy @ theta.to(torch.complex128) @ Fx
         Yh = torch.einsum("bikl,iokl->bokl", X, R)
-        s = torch.real(Gy @ Yh @ Gx) / (H * W)
+        s = torch.real(Gy @ Yh @ Gx) / (Hp * Wp)
         theta = act(pw(params[f"layer{n}.w"], params[f"layer{n}.b"], theta) + s)
-    h = theta
+    h = theta[:, :, :H, :W]
     for l in range(shape.dec_layers):
         h = act(pw(params[f"dec{l}.w"], params[f"dec{l}.b"], h))
     return pw(params["out.w"], params["out.b"], h)

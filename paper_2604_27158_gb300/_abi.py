@@ -47,7 +47,7 @@ class fno_config(ctypes.Structure):
     _fields_ = [("c_in", ctypes.c_int32), ("c_out", ctypes.c_int32), ("width", ctypes.c_int32),
                 ("layers", ctypes.c_int32), ("modes", ctypes.c_int32),
                 ("dec_layers", ctypes.c_int32), ("dec_size", ctypes.c_int32),
-                ("activation", ctypes.c_int32)]
+                ("activation", ctypes.c_int32), ("padding", ctypes.c_int32)]
 
 
 class fno_sizes(ctypes.Structure):
@@ -65,7 +65,8 @@ class hybrid_config(ctypes.Structure):
                 ("check_every", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("max_steps", ctypes.c_int64), ("k_lbm", ctypes.c_int32), ("m_fno", ctypes.c_int32),
                 ("rho_lo", ctypes.c_double), ("rho_hi", ctypes.c_double),
-                ("u_clamp", ctypes.c_double)]
+                ("u_clamp", ctypes.c_double),
+                ("in_channels", ctypes.c_int32), ("in_channels_u", ctypes.c_int32)]
 
 
 class hybrid_stats(ctypes.Structure):
@@ -89,6 +90,7 @@ _PROTOS = {
     "lbm_residual": ([VP, ctypes.POINTER(ctypes.c_double), I, VP], I),
     "lbm_reinit_from_macro": ([VP, VP, VP, VP, I, VP], I),
     "lbm_export_f": ([VP, VP, VP], I),
+    "lbm_vorticity": ([VP, VP, VP, VP, VP], I),
     "lbm_set_state": ([VP, VP, VP], I),
     "lbm_get_state": ([VP, VP, VP], I),
     "lbm_steps_done": ([VP, ctypes.POINTER(ctypes.c_longlong)], I),
@@ -112,8 +114,8 @@ _PROTOS = {
     "fno_train_forward": ([ctypes.POINTER(fno_config), VP, VP, VP, I, I, I, VP, VP, VP], I),
     "fno_train_backward": ([ctypes.POINTER(fno_config), VP, VP, VP, VP, VP, I, I, I, VP, VP], I),
     "hybrid_query_ws": ([ctypes.POINTER(lbm_grid), I, ctypes.POINTER(fno_config),
-                         ctypes.POINTER(ctypes.c_size_t)], I),
-    "hybrid_create": ([VP, VP, ctypes.POINTER(hybrid_config), VP, ctypes.c_size_t,
+                         ctypes.POINTER(fno_config), ctypes.POINTER(ctypes.c_size_t)], I),
+    "hybrid_create": ([VP, VP, VP, ctypes.POINTER(hybrid_config), VP, ctypes.c_size_t,
                        ctypes.POINTER(VP)], I),
     "hybrid_advance": ([VP, I, ctypes.POINTER(hybrid_stats), ctypes.POINTER(ctypes.c_int64),
                         ctypes.POINTER(ctypes.c_double), VP], I),

@@ -45,6 +45,7 @@ static int fno_offsets(const fno_config& c, FnoOffsets* o) {
               "fno: decoder shape out of range");
   LBM_REQUIRE(c.activation == FNO_ACT_GELU || c.activation == FNO_ACT_RELU,
               "fno: unknown activation");
+  LBM_REQUIRE(c.padding >= 0 && c.padding <= 64, "fno: padding must be in 0..64");
   const size_t C = c.width, h = C / 2, m = c.modes, cin2 = c.c_in + 2;
   size_t p = 0;
   auto take = [&](size_t n) {
@@ -84,9 +85,12 @@ static int fno_offsets(const fno_config& c, FnoOffsets* o) {
 struct FnoWs {
   size_t theta0, theta1, x1, xh, yh, z, twx, twy, total;
 };
-static FnoWs fno_ws_plan(const fno_config& c, int B, int H, int W) {
+// Workspace of the CUDA-core path for an input of B x H x W: the latent field and the
+// spectral buffers live on the padded grid (H + padding) x (W + padding).
+static FnoWs fno_ws_plan(const fno_config& c, int B, int H0, int W0) {
   FnoWs w{};
   const size_t C = c.width, m = c.modes;
+  const int H = H0 + c.padding, W = W0 + c.padding;
   size_t p = 0;
   auto take = [&](size_t bytes) {
     const size_t at = p;
@@ -151,16 +155,22 @@ __global__ void k_twiddle(float2* __restrict__ tw, int N) {
 }
 
 // Lifting network P with the two coordinate channels; one thread per pixel.
+// The latent field lives on the padded grid Hp x Wp (Hp = H + padding): pixels outside
+// the H x W input are zero (padding after lifting).
 __global__ void k_lift(const float* __restrict__ in, __nv_bfloat16* __restrict__ theta,
                        const float* __restrict__ w0, const float* __restrict__ b0,
                        const float* __restrict__ w1, const float* __restrict__ b1, int B, int H,
-                       int W, int cin, int C, int act) {
-  const size_t pix = (size_t)B * H * W;
+                       int W, int Hp, int Wp, int cin, int C, int act) {
+  const size_t pix = (size_t)B * Hp * Wp;
   const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (p >= pix) return;
-  const int x = (int)(p % W);
-  const int y = (int)((p / W) % H);
-  const int b = (int)(p / ((size_t)W * H));
+  const int x = (int)(p % Wp);
+  const int y = (int)((p / Wp) % Hp);
+  const int b = (int)(p / ((size_t)Wp * Hp));
+  if (x >= W || y >= H) {
+    for (int o = 0; o < C; ++o) theta[p * C + o] = __float2bfloat16_rn(0.0f);
+    return;
+  }
   float xin[18];
   for (int c = 0; c < cin; ++c) xin[c] = bf16r(in[(((size_t)b * cin + c) * H + y) * W + x]);
   xin[cin] = bf16r((float)x / (float)max(W - 1, 1));
@@ -323,14 +333,22 @@ __global__ void k_inv_x_w(const __nv_bfloat16* __restrict__ theta, const float2*
 }
 
 // Projection Q: hidden layers with the activation, then the linear output layer.
+// Reads the H x W corner of the padded latent field (the crop after the last layer).
 __global__ void k_decoder(const __nv_bfloat16* __restrict__ theta, float* __restrict__ out,
                           const float* __restrict__ params, const unsigned* __restrict__ offs,
-                          int nlayers, int B, int H, int W, int C, int S, int cout, int act) {
+                          int nlayers, int B, int H, int W, int Hp, int Wp, int C, int S, int cout,
+                          int act) {
   const size_t pix = (size_t)B * H * W;
   const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (p >= pix) return;
   float a[64], t[64];
-  for (int c = 0; c < C; ++c) a[c] = __bfloat162float(theta[p * C + c]);
+  {
+    const int x = (int)(p % W);
+    const int y = (int)((p / W) % H);
+    const int b = (int)(p / ((size_t)W * H));
+    const size_t q = ((size_t)b * Hp + y) * Wp + x;
+    for (int c = 0; c < C; ++c) a[c] = __bfloat162float(theta[q * C + c]);
+  }
   int fan = C;
   for (int l = 0; l < nlayers; ++l) {
     const float* w = params + offs[2 * l];
@@ -378,8 +396,9 @@ int fno_query(const fno_config* cfg_h, int B, int H, int W, fno_sizes* out_h) {
   FnoOffsets o;
   LBM_TRY(fno_offsets(*cfg_h, &o));
   LBM_REQUIRE(B >= 0 && H >= 1 && W >= 1, "fno_query: bad shape");
-  LBM_REQUIRE(2 * cfg_h->modes <= H && 2 * cfg_h->modes < W,
-              "fno_query: need 2m <= H and m < W/2 (m=%d, H=%d, W=%d)", cfg_h->modes, H, W);
+  LBM_REQUIRE(2 * cfg_h->modes <= H + cfg_h->padding && 2 * cfg_h->modes < W + cfg_h->padding,
+              "fno_query: need 2m <= H + padding and m < (W + padding)/2 (m=%d, H=%d, W=%d)",
+              cfg_h->modes, H, W);
   out_h->n_params = o.n_params;
   out_h->packed_bytes = align_up((o.total_floats + 64) * sizeof(float), 256);
   out_h->ws_bytes = std::max(fno_ws_plan(*cfg_h, std::max(B, 1), H, W).total,
@@ -446,8 +465,8 @@ int fno_forward(fno_handle* h, const float* in_d, float* out_d, int B, int H, in
                 size_t ws_bytes, void* stream) {
   LBM_REQUIRE(h && in_d && out_d && ws_d, "fno_forward: null argument");
   const fno_config& c = h->cfg;
-  LBM_REQUIRE(B >= 1 && 2 * c.modes <= H && 2 * c.modes < W,
-              "fno_forward: need B >= 1, 2m <= H, m < W/2");
+  LBM_REQUIRE(B >= 1 && 2 * c.modes <= H + c.padding && 2 * c.modes < W + c.padding,
+              "fno_forward: need B >= 1, 2m <= H + padding, m < (W + padding)/2");
   const FnoWs wp = fno_ws_plan(c, B, H, W);
   LBM_REQUIRE(ws_bytes >= wp.total, "fno_forward: workspace too small (%zu < %zu)", ws_bytes,
               wp.total);
@@ -483,12 +502,16 @@ int fno_forward(fno_handle* h, const float* in_d, float* out_d, int B, int H, in
   const int C = c.width, m = c.modes;
   const float* P = h->packed;
   const FnoOffsets& o = h->off;
+  const int H0 = H, W0 = W;  // input / output grid; the layers run on the padded grid
+  H = H0 + c.padding;
+  W = W0 + c.padding;
   k_twiddle<<<(W + 255) / 256, 256, 0, s>>>(twx, W);
   k_twiddle<<<(H + 255) / 256, 256, 0, s>>>(twy, H);
-  const size_t pix = (size_t)B * H * W;
-  k_lift<<<(unsigned)((pix + 127) / 128), 128, 0, s>>>(in_d, th[0], P + o.lift0_w, P + o.lift0_b,
-                                                       P + o.lift1_w, P + o.lift1_b, B, H, W,
-                                                       c.c_in, C, c.activation);
+  const size_t pix_p = (size_t)B * H * W;
+  k_lift<<<(unsigned)((pix_p + 127) / 128), 128, 0, s>>>(in_d, th[0], P + o.lift0_w,
+                                                         P + o.lift0_b, P + o.lift1_w,
+                                                         P + o.lift1_b, B, H0, W0, H, W, c.c_in,
+                                                         C, c.activation);
   LBM_CHECK_LAUNCH();
   const int rows = B * H;
   const size_t smem_fx = (size_t)W * C * sizeof(float) + (size_t)W * sizeof(float2);
@@ -509,9 +532,10 @@ int fno_forward(fno_handle* h, const float* in_d, float* out_d, int B, int H, in
     LBM_CHECK_LAUNCH();
     cur ^= 1;
   }
+  const size_t pix = (size_t)B * H0 * W0;
   k_decoder<<<(unsigned)((pix + 127) / 128), 128, 0, s>>>(th[cur], out_d, P, h->dec_offs,
-                                                          c.dec_layers, B, H, W, C, c.dec_size,
-                                                          c.c_out, c.activation);
+                                                          c.dec_layers, B, H0, W0, H, W, C,
+                                                          c.dec_size, c.c_out, c.activation);
   LBM_CHECK_LAUNCH();
   return LBM_OK;
 }

@@ -56,6 +56,7 @@ int tr_offsets(const fno_config& c, TrOff* o) {
               "fno_train: decoder shape out of range");
   LBM_REQUIRE(c.activation == FNO_ACT_GELU || c.activation == FNO_ACT_RELU,
               "fno_train: unknown activation");
+  LBM_REQUIRE(c.padding == 0, "fno_train: padding is not supported by the training path");
   const size_t C = c.width, h = C / 2, m = c.modes, cin2 = c.c_in + 2;
   size_t p = 0;
   auto take = [&](size_t n) {

@@ -27,9 +27,16 @@ struct Group {
 };
 
 struct HybWs {
-  size_t rho, ux, uy, fin, fout, fws, tables, total;
+  size_t rho, ux, uy, fin, fin_u, fout, fws, tables, total;
   size_t fws_bytes;
 };
+
+// Input planes selected by a channel mask (bit 0 rho - 1, 1 u_x, 2 u_y, 3 mask; 0 = all).
+static int channel_mask(int m) { return m == 0 ? 0xF : m; }
+static int channel_count(int m) {
+  m = channel_mask(m);
+  return (m & 1) + ((m >> 1) & 1) + ((m >> 2) & 1) + ((m >> 3) & 1);
+}
 
 static void make_groups(const lbm_grid* grids, int ngrids, std::vector<Group>* groups) {
   std::map<std::pair<int, int>, int> at;
@@ -49,8 +56,8 @@ static void make_groups(const lbm_grid* grids, int ngrids, std::vector<Group>* g
   }
 }
 
-static int plan_ws(const lbm_grid* grids, int ngrids, const fno_config* cfg, HybWs* w,
-                   std::vector<Group>* groups) {
+static int plan_ws(const lbm_grid* grids, int ngrids, const fno_config* cfg,
+                   const fno_config* cfg_u, HybWs* w, std::vector<Group>* groups) {
   LBM_REQUIRE(grids && ngrids > 0 && cfg, "hybrid: bad arguments");
   make_groups(grids, ngrids, groups);
   size_t cells = 0;
@@ -60,10 +67,15 @@ static int plan_ws(const lbm_grid* grids, int ngrids, const fno_config* cfg, Hyb
     fno_sizes fs;
     LBM_TRY(fno_query(cfg, (int)gr.grids.size(), gr.H, gr.W, &fs));
     max_ws = std::max(max_ws, fs.ws_bytes);
+    if (cfg_u) {
+      LBM_TRY(fno_query(cfg_u, (int)gr.grids.size(), gr.H, gr.W, &fs));
+      max_ws = std::max(max_ws, fs.ws_bytes);
+    }
     max_cells = std::max(max_cells, gr.grids.size() * (size_t)gr.H * gr.W);
   }
-  LBM_REQUIRE(cfg->c_in == 4 && cfg->c_out == 3,
-              "hybrid: the FNO must map (rho-1, ux, uy, mask) to (rho-1, ux, uy)");
+  LBM_REQUIRE(cfg->c_in <= 4 && cfg->c_out <= 3 && (!cfg_u || (cfg_u->c_in <= 4 && cfg_u->c_out <= 3)),
+              "hybrid: the networks read at most the 4 planes (rho-1, ux, uy, mask) and "
+              "write at most (rho-1, ux, uy)");
   size_t p = 0;
   auto take = [&](size_t bytes) {
     const size_t a = p;
@@ -74,6 +86,7 @@ static int plan_ws(const lbm_grid* grids, int ngrids, const fno_config* cfg, Hyb
   w->ux = take(cells * sizeof(float));
   w->uy = take(cells * sizeof(float));
   w->fin = take(max_cells * 4 * sizeof(float));
+  w->fin_u = take(cfg_u ? max_cells * 4 * sizeof(float) : 0);
   w->fout = take(max_cells * 3 * sizeof(float));
   w->fws = take(max_ws);
   w->fws_bytes = max_ws;
@@ -82,12 +95,14 @@ static int plan_ws(const lbm_grid* grids, int ngrids, const fno_config* cfg, Hyb
   return LBM_OK;
 }
 
-// FNO input of a size group: (rho - 1, u_x, u_y, mask) planes per grid.
+// FNO input of a size group: the planes of (rho - 1, u_x, u_y, mask) selected by
+// `chans` (bit mask, see channel_mask), in that order, per grid.
 __global__ void k_pack(const GridDev* __restrict__ gd, const int* __restrict__ gids, int B, int H,
                        int W, const uint32_t* __restrict__ mask, const float* __restrict__ rho,
-                       const float* __restrict__ ux, const float* __restrict__ uy,
+                       const float* __restrict__ ux, const float* __restrict__ uy, int chans,
                        float* __restrict__ in) {
   const size_t n = (size_t)B * H * W;
+  const int nch = (chans & 1) + ((chans >> 1) & 1) + ((chans >> 2) & 1) + ((chans >> 3) & 1);
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
        t += (size_t)gridDim.x * blockDim.x) {
     const int b = (int)(t / ((size_t)H * W));
@@ -95,22 +110,25 @@ __global__ void k_pack(const GridDev* __restrict__ gd, const int* __restrict__ g
     const int y = c / W, x = c % W;
     const GridDev& G = gd[gids[b]];
     const long long k = G.cell_off + c;
-    const float s = (float)mask_bit(mask + G.mask_off, G.wpr, x, y);
     const size_t plane = (size_t)H * W;
-    float* o = in + (size_t)b * 4 * plane + c;
-    o[0] = rho[k] - 1.0f;
-    o[plane] = ux[k];
-    o[2 * plane] = uy[k];
-    o[3 * plane] = s;
+    float* o = in + (size_t)b * nch * plane + c;
+    int q = 0;
+    if (chans & 1) o[(q++) * plane] = rho[k] - 1.0f;
+    if (chans & 2) o[(q++) * plane] = ux[k];
+    if (chans & 4) o[(q++) * plane] = uy[k];
+    if (chans & 8) o[(q++) * plane] = (float)mask_bit(mask + G.mask_off, G.wpr, x, y);
   }
 }
 
-// FNO output -> clamped dense fields: rho = clamp(1 + out0), |u| <= u_clamp.
+// FNO output -> clamped dense fields.  fields: 0 = (rho - 1, u_x, u_y) from 3 planes,
+// 1 = rho - 1 from 1 plane (density network), 2 = (u_x, u_y) from 2 planes (velocity
+// network).  rho = clamp(1 + out), |u| <= u_clamp.
 __global__ void k_unpack(const GridDev* __restrict__ gd, const int* __restrict__ gids, int B,
-                         int H, int W, const float* __restrict__ out, float rho_lo, float rho_hi,
-                         float u_clamp, float* __restrict__ rho, float* __restrict__ ux,
-                         float* __restrict__ uy) {
+                         int H, int W, const float* __restrict__ out, int fields, float rho_lo,
+                         float rho_hi, float u_clamp, float* __restrict__ rho,
+                         float* __restrict__ ux, float* __restrict__ uy) {
   const size_t n = (size_t)B * H * W;
+  const int nch = fields == 0 ? 3 : (fields == 1 ? 1 : 2);
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
        t += (size_t)gridDim.x * blockDim.x) {
     const int b = (int)(t / ((size_t)H * W));
@@ -118,18 +136,20 @@ __global__ void k_unpack(const GridDev* __restrict__ gd, const int* __restrict__
     const GridDev& G = gd[gids[b]];
     const long long k = G.cell_off + c;
     const size_t plane = (size_t)H * W;
-    const float* o = out + (size_t)b * 3 * plane + c;
-    const float r = fminf(fmaxf(1.0f + o[0], rho_lo), rho_hi);
-    float vx = o[plane], vy = o[2 * plane];
-    const float sp = sqrtf(vx * vx + vy * vy);
-    if (sp > u_clamp) {
-      const float sc = u_clamp / sp;
-      vx *= sc;
-      vy *= sc;
+    const float* o = out + (size_t)b * nch * plane + c;
+    if (fields != 2) rho[k] = fminf(fmaxf(1.0f + o[0], rho_lo), rho_hi);
+    if (fields != 1) {
+      const int q = fields == 0 ? 1 : 0;
+      float vx = o[q * plane], vy = o[(q + 1) * plane];
+      const float sp = sqrtf(vx * vx + vy * vy);
+      if (sp > u_clamp) {
+        const float sc = u_clamp / sp;
+        vx *= sc;
+        vy *= sc;
+      }
+      ux[k] = vx;
+      uy[k] = vy;
     }
-    rho[k] = r;
-    ux[k] = vx;
-    uy[k] = vy;
   }
 }
 
@@ -149,13 +169,15 @@ using namespace lbmfno;
 
 struct hybrid_handle {
   lbm_handle* lbm = nullptr;
-  fno_handle* fno = nullptr;
+  fno_handle* fno = nullptr;    // single network, or the density network
+  fno_handle* fno_u = nullptr;  // velocity network (may be null)
   hybrid_config cfg{};
-  fno_config fcfg{};
+  fno_config fcfg{}, fcfg_u{};
   std::vector<Group> groups;
   HybWs w{};
   char* ws = nullptr;
-  float *rho = nullptr, *ux = nullptr, *uy = nullptr, *fin = nullptr, *fout = nullptr;
+  float *rho = nullptr, *ux = nullptr, *uy = nullptr, *fin = nullptr, *fin_u = nullptr,
+        *fout = nullptr;
   void* fws = nullptr;
   cudaStream_t cap = nullptr;     // private stream used for graph capture and replay
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -165,20 +187,33 @@ struct hybrid_handle {
 static inline cudaStream_t HS(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 // FNO prediction for every size group from the dense fields, clamped into the same fields.
+// With two networks both inputs are packed before either output is written back, so
+// both read the fields of the same time level.
 static int hyb_predict(hybrid_handle* h, cudaStream_t s) {
   lbm_handle* L = h->lbm;
+  const float lo = (float)h->cfg.rho_lo, hi = (float)h->cfg.rho_hi, uc = (float)h->cfg.u_clamp;
   for (Group& gr : h->groups) {
     const int B = (int)gr.grids.size();
     const size_t n = (size_t)B * gr.H * gr.W;
     const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 65535);
     k_pack<<<blocks, 256, 0, s>>>(L->gd_d, gr.grids_d, B, gr.H, gr.W, L->mask, h->rho, h->ux,
-                                  h->uy, h->fin);
+                                  h->uy, channel_mask(h->cfg.in_channels), h->fin);
     LBM_CHECK_LAUNCH();
+    if (h->fno_u) {
+      k_pack<<<blocks, 256, 0, s>>>(L->gd_d, gr.grids_d, B, gr.H, gr.W, L->mask, h->rho, h->ux,
+                                    h->uy, channel_mask(h->cfg.in_channels_u), h->fin_u);
+      LBM_CHECK_LAUNCH();
+    }
     LBM_TRY(fno_forward(h->fno, h->fin, h->fout, B, gr.H, gr.W, h->fws, h->w.fws_bytes, s));
     k_unpack<<<blocks, 256, 0, s>>>(L->gd_d, gr.grids_d, B, gr.H, gr.W, h->fout,
-                                    (float)h->cfg.rho_lo, (float)h->cfg.rho_hi,
-                                    (float)h->cfg.u_clamp, h->rho, h->ux, h->uy);
+                                    h->fno_u ? 1 : 0, lo, hi, uc, h->rho, h->ux, h->uy);
     LBM_CHECK_LAUNCH();
+    if (h->fno_u) {
+      LBM_TRY(fno_forward(h->fno_u, h->fin_u, h->fout, B, gr.H, gr.W, h->fws, h->w.fws_bytes, s));
+      k_unpack<<<blocks, 256, 0, s>>>(L->gd_d, gr.grids_d, B, gr.H, gr.W, h->fout, 2, lo, hi, uc,
+                                      h->rho, h->ux, h->uy);
+      LBM_CHECK_LAUNCH();
+    }
   }
   return LBM_OK;
 }
@@ -193,17 +228,18 @@ static int hyb_cycle(hybrid_handle* h, cudaStream_t s) {
 
 extern "C" {
 
-int hybrid_query_ws(const lbm_grid* grids_h, int ngrids, const fno_config* cfg_h, size_t* ws_h) {
+int hybrid_query_ws(const lbm_grid* grids_h, int ngrids, const fno_config* cfg_h,
+                    const fno_config* cfg_u_h, size_t* ws_h) {
   LBM_REQUIRE(ws_h != nullptr, "hybrid_query_ws: null output");
   HybWs w;
   std::vector<Group> groups;
-  LBM_TRY(plan_ws(grids_h, ngrids, cfg_h, &w, &groups));
+  LBM_TRY(plan_ws(grids_h, ngrids, cfg_h, cfg_u_h, &w, &groups));
   *ws_h = w.total;
   return LBM_OK;
 }
 
-int hybrid_create(lbm_handle* lbm, fno_handle* fno, const hybrid_config* cfg_h, void* ws_d,
-                  size_t ws_bytes, hybrid_handle** out) {
+int hybrid_create(lbm_handle* lbm, fno_handle* fno, fno_handle* fno_u, const hybrid_config* cfg_h,
+                  void* ws_d, size_t ws_bytes, hybrid_handle** out) {
   LBM_REQUIRE(out != nullptr, "hybrid_create: null handle output");
   *out = nullptr;
   LBM_REQUIRE(lbm && cfg_h && ws_d, "hybrid_create: null argument");
@@ -220,22 +256,38 @@ int hybrid_create(lbm_handle* lbm, fno_handle* fno, const hybrid_config* cfg_h, 
   LBM_REQUIRE(!needs_fno || fno, "hybrid_create: this configuration needs an FNO handle");
   LBM_REQUIRE(c.rho_lo > 0.0 && c.rho_hi > c.rho_lo && c.u_clamp > 0.0,
               "hybrid_create: bad clamp bounds");
+  LBM_REQUIRE(c.in_channels >= 0 && c.in_channels <= 0xF && c.in_channels_u >= 0 &&
+                  c.in_channels_u <= 0xF,
+              "hybrid_create: in_channels must be a 4-bit plane mask");
+  LBM_REQUIRE(!fno_u || fno, "hybrid_create: a velocity network needs a density network");
+  fno_config fc{}, fcu{};
+  if (fno) {
+    LBM_TRY(fno_get_config(fno, &fc));
+    LBM_REQUIRE(fc.c_in == channel_count(c.in_channels),
+                "hybrid_create: the network reads %d planes, in_channels selects %d", fc.c_in,
+                channel_count(c.in_channels));
+    LBM_REQUIRE(fc.c_out == (fno_u ? 1 : 3),
+                "hybrid_create: the %s network must have %d output channels",
+                fno_u ? "density" : "single", fno_u ? 1 : 3);
+  } else {
+    fc = fno_config{4, 3, 2, 1, 1, 1, 1, FNO_ACT_GELU, 0};
+  }
+  if (fno_u) {
+    LBM_TRY(fno_get_config(fno_u, &fcu));
+    LBM_REQUIRE(fcu.c_in == channel_count(c.in_channels_u),
+                "hybrid_create: the velocity network reads %d planes, in_channels_u selects %d",
+                fcu.c_in, channel_count(c.in_channels_u));
+    LBM_REQUIRE(fcu.c_out == 2, "hybrid_create: the velocity network must have 2 outputs");
+  }
   hybrid_handle* h = new hybrid_handle();
   h->lbm = lbm;
   h->fno = fno;
+  h->fno_u = fno_u;
   h->cfg = c;
-  fno_config fc{};
-  if (fno) {
-    const int sc = fno_get_config(fno, &fc);
-    if (sc != LBM_OK) {
-      delete h;
-      return sc;
-    }
-  } else {
-    fc = fno_config{4, 3, 2, 1, 1, 1, 1, FNO_ACT_GELU};
-  }
   h->fcfg = fc;
-  int st = plan_ws(lbm->grids.data(), lbm->ngrids, &fc, &h->w, &h->groups);
+  h->fcfg_u = fcu;
+  int st = plan_ws(lbm->grids.data(), lbm->ngrids, &fc, fno_u ? &fcu : nullptr, &h->w,
+                   &h->groups);
   if (st == LBM_OK && ws_bytes < h->w.total) {
     set_error("hybrid_create: workspace too small (%zu < %zu)", ws_bytes, h->w.total);
     st = LBM_ERR_INVALID_ARG;
@@ -249,6 +301,7 @@ int hybrid_create(lbm_handle* lbm, fno_handle* fno, const hybrid_config* cfg_h, 
   h->ux = reinterpret_cast<float*>(h->ws + h->w.ux);
   h->uy = reinterpret_cast<float*>(h->ws + h->w.uy);
   h->fin = reinterpret_cast<float*>(h->ws + h->w.fin);
+  h->fin_u = reinterpret_cast<float*>(h->ws + h->w.fin_u);
   h->fout = reinterpret_cast<float*>(h->ws + h->w.fout);
   h->fws = h->ws + h->w.fws;
   // per-group index / offset tables
@@ -286,7 +339,7 @@ int hybrid_advance(hybrid_handle* h, int cycles, hybrid_stats* out_h, int64_t* g
     LBM_CHECK_LAUNCH();
     if (c.use_fno) {
       LBM_TRY(hyb_predict(h, s));
-      stats.fno_calls = (int)h->groups.size();
+      stats.fno_calls = (int)h->groups.size() * (h->fno_u ? 2 : 1);
     }
     LBM_TRY(lbm_reinit_from_macro(L, h->rho, h->ux, h->uy, c.use_fno ? c.neq_mode : 0, s));
     const int ng = L->ngrids;
@@ -340,7 +393,7 @@ int hybrid_advance(hybrid_handle* h, int cycles, hybrid_stats* out_h, int64_t* g
       if (c.k_lbm % 2) L->cur ^= 1;
       L->steps = 0;  // the cycle ends with a re-initialisation
       stats.steps += c.k_lbm;
-      stats.fno_calls += c.m_fno * (int)h->groups.size();
+      stats.fno_calls += c.m_fno * (int)h->groups.size() * (h->fno_u ? 2 : 1);
     }
     LBM_CHECK_CUDA(cudaEventRecord(h->ev_out, h->cap));
     LBM_CHECK_CUDA(cudaStreamWaitEvent(s, h->ev_out, 0));

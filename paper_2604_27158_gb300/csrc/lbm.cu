@@ -768,6 +768,26 @@ __global__ void __launch_bounds__(kBlock) k_reinit(const GridDev* __restrict__ g
   }
 }
 
+// Vorticity omega = d_x u_y - d_y u_x of dense velocity fields (the accuracy metric of
+// the unsteady results, Sec. 3.2.2), with the re-initialisation's difference stencils;
+// solid cells get 0.
+__global__ void __launch_bounds__(kBlock) k_vorticity(const GridDev* __restrict__ grids,
+                                                      int ngrids, const uint32_t* __restrict__ mask,
+                                                      const float* __restrict__ ux_i,
+                                                      const float* __restrict__ uy_i,
+                                                      float* __restrict__ omega) {
+  int gidx, x, y;
+  if (!cell_of_thread(grids, ngrids, gidx, x, y)) return;
+  const GridDev G = grids[gidx];
+  const uint32_t* m = mask + G.mask_off;
+  const long long c = G.cell_off + (long long)y * G.nx + x;
+  if (mask_bit(m, G.wpr, x, y)) {
+    omega[c] = 0.0f;
+    return;
+  }
+  omega[c] = dfield(G, m, uy_i + G.cell_off, x, y, 0) - dfield(G, m, ux_i + G.cell_off, x, y, 1);
+}
+
 // ------------------------------------------------------------ host side ---
 struct WsPlan {
   size_t grids_off, uprev_off, partial_off, stats_off, status_off, tiles_off, total;
@@ -1029,6 +1049,15 @@ int lbm_reinit_from_macro(lbm_handle* h, const float* rho_d, const float* ux_d,
                                                     h->uy_prev);
   LBM_CHECK_LAUNCH();
   h->steps = 0;
+  return LBM_OK;
+}
+
+int lbm_vorticity(lbm_handle* h, const float* ux_d, const float* uy_d, float* omega_d,
+                  void* stream) {
+  LBM_REQUIRE(h != nullptr && ux_d && uy_d && omega_d, "lbm_vorticity: bad arguments");
+  k_vorticity<<<h->nblk_total, kBlock, 0, S(stream)>>>(h->gd_d, h->ngrids, h->mask, ux_d, uy_d,
+                                                       omega_d);
+  LBM_CHECK_LAUNCH();
   return LBM_OK;
 }
 

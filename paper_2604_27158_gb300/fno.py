@@ -27,10 +27,11 @@ class FnoShape:
     dec_layers: int = 1
     dec_size: int = 32
     activation: int = _abi.FNO_ACT_GELU
+    padding: int = 0
 
     def c(self) -> fno_config:
         return fno_config(self.c_in, self.c_out, self.width, self.layers, self.modes,
-                          self.dec_layers, self.dec_size, self.activation)
+                          self.dec_layers, self.dec_size, self.activation, self.padding)
 
 
 def fno_query(shape: FnoShape, B: int, H: int, W: int) -> fno_sizes:
@@ -123,32 +124,40 @@ class HybridConfig:
     rho_lo: float = 0.9
     rho_hi: float = 1.1
     u_clamp: float = 0.2
+    in_channels: int = 0    # planes of (rho-1, ux, uy, mask) read by the (density) net, 0 = all
+    in_channels_u: int = 0  # planes read by the velocity net, 0 = all
 
     def c(self) -> hybrid_config:
         return hybrid_config(self.mode, self.use_fno, self.neq_mode, self.check_every, self.tol,
                              self.max_steps, self.k_lbm, self.m_fno, self.rho_lo, self.rho_hi,
-                             self.u_clamp)
+                             self.u_clamp, self.in_channels, self.in_channels_u)
 
 
 class Hybrid:
     """Hybrid FNO-LBM driver over a Lattice and an Fno (a thin owner of hybrid_handle)."""
 
     def __init__(self, lattice: Lattice, fno: Optional[Fno], cfg: HybridConfig,
-                 shape: Optional[FnoShape] = None):
+                 shape: Optional[FnoShape] = None, fno_u: Optional[Fno] = None):
+        """fno: the single network (3 outputs) or, with fno_u, the density network
+        (1 output); fno_u: the velocity network (2 outputs)."""
         self.lattice = lattice
         self.fno = fno
+        self.fno_u = fno_u
         self.cfg = cfg
         shape = fno.shape if fno is not None else (shape or FnoShape(width=2, layers=1, modes=1,
                                                                       dec_size=1))
         arr = (lbm_grid * len(lattice.grids))(*[g.c() for g in lattice.grids])
         n = ctypes.c_size_t()
         fc = shape.c()
-        call("hybrid_query_ws", arr, len(lattice.grids), ctypes.byref(fc), ctypes.byref(n))
+        fcu = fno_u.shape.c() if fno_u is not None else None
+        call("hybrid_query_ws", arr, len(lattice.grids), ctypes.byref(fc),
+             ctypes.byref(fcu) if fcu is not None else None, ctypes.byref(n))
         self.ws = torch.empty(max(n.value, 256), dtype=torch.uint8, device=lattice.device)
         self._h = ctypes.c_void_p()
         hc = cfg.c()
         call("hybrid_create", lattice.handle, fno.handle if fno is not None else None,
-             ctypes.byref(hc), self.ws.data_ptr(), self.ws.numel(), ctypes.byref(self._h))
+             fno_u.handle if fno_u is not None else None, ctypes.byref(hc), self.ws.data_ptr(),
+             self.ws.numel(), ctypes.byref(self._h))
 
     def advance(self, cycles: int = 0, stream=None):
         """Run the steady solve (cycles ignored) or `cycles` unsteady cycles.

@@ -115,6 +115,15 @@ class Lattice:
         call("lbm_reinit_from_macro", self._h, rho.data_ptr(), ux.data_ptr(), uy.data_ptr(),
              int(neq_mode), _stream_ptr(stream))
 
+    def vorticity(self, ux: torch.Tensor, uy: torch.Tensor, stream=None) -> torch.Tensor:
+        """omega = d_x u_y - d_y u_x of dense velocity fields (library stencils)."""
+        for t in (ux, uy):
+            assert t.dtype == torch.float32 and t.is_contiguous() and t.numel() == self.cells
+        out = torch.empty(self.cells, dtype=torch.float32, device=self.device)
+        call("lbm_vorticity", self._h, ux.data_ptr(), uy.data_ptr(), out.data_ptr(),
+             _stream_ptr(stream))
+        return out
+
     def export_f(self, stream=None) -> torch.Tensor:
         out = torch.empty(9 * self.cells, dtype=torch.float32, device=self.device)
         call("lbm_export_f", self._h, out.data_ptr(), _stream_ptr(stream))

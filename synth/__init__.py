@@ -38,6 +38,8 @@ __all__ = [
     "fno_random_params",
     "fno_flatten_params",
     "smooth_macro_fields",
+    "DoubleShear",
+    "double_shear",
     "unsteady_batch",
     "random_post_collision_state",
 ]
@@ -208,6 +210,59 @@ def unsteady_batch(n: int, seed: int = 0, sizes=UNSTEADY_SIZES, tau_range=(0.55,
     return out
 
 
+@dataclasses.dataclass(frozen=True)
+class DoubleShear:
+    """Lattice set-up of the double-shear-layer workload (Sec. 3.2.1): a periodic unit
+    square at n x n cells, U = 1 m/s, nu = 1e-3 m^2/s, and an FNO time step of
+    Delta T = 0.1 s = 223 LBM steps (30 Delta T = 3 s of simulated time)."""
+    n: int = 128
+    steps_per_dT: int = 223
+    dT_seconds: float = 0.1
+    U: float = 1.0
+    nu: float = 1e-3
+
+    @property
+    def dt(self) -> float:  # seconds per LBM step
+        return self.dT_seconds / self.steps_per_dT
+
+    @property
+    def u_lattice(self) -> float:  # lattice velocity of U
+        return self.U * self.dt * self.n
+
+    @property
+    def tau(self) -> float:  # 1/2 + 3 nu dt / dx^2
+        return 0.5 + 3.0 * self.nu * self.dt * self.n * self.n
+
+
+def double_shear(count: int, seed: int = 0, setup: DoubleShear = DoubleShear(),
+                 a_range=(20.0, 125.0), upper=(0.65, 0.85), lower=(0.15, 0.35)):
+    """Initial conditions of the double shear layer in lattice units.
+
+    u = U tanh(A1 (x2' - x2)) for x2 >= 0.5 and U tanh(A2 (x2 - x2'')) for x2 < 0.5,
+    v = 0.1 U sin(2 pi (x1 + 1/4)), on cell centres x = (i + 1/2)/n.  A1, A2 are drawn
+    from a_range (Re = U delta / nu with delta = 1/A spans 8 .. 50), the layer centres
+    x2' and x2'' from `upper` and `lower`.  Returns one dict per trajectory with rho, ux,
+    uy ([n, n] float32, rho = 1) and the drawn parameters.
+    """
+    rng = _rng(seed)
+    n = setup.n
+    c = (np.arange(n) + 0.5) / n
+    x1 = c[None, :]
+    x2 = c[:, None]
+    out = []
+    for _ in range(count):
+        a1, a2 = (float(v) for v in rng.uniform(*a_range, size=2))
+        y_up, y_lo = float(rng.uniform(*upper)), float(rng.uniform(*lower))
+        u = np.where(x2 >= 0.5, np.tanh(a1 * (y_up - x2)), np.tanh(a2 * (x2 - y_lo)))
+        u = np.broadcast_to(u, (n, n))
+        v = np.broadcast_to(0.1 * np.sin(2.0 * np.pi * (x1 + 0.25)), (n, n))
+        ul = setup.u_lattice
+        out.append({"rho": np.ones((n, n), np.float32), "ux": (ul * u).astype(np.float32),
+                    "uy": (ul * v).astype(np.float32), "A1": a1, "A2": a2, "x2_upper": y_up,
+                    "x2_lower": y_lo})
+    return out
+
+
 def pack_mask_bits(solid: np.ndarray) -> np.ndarray:
     """Bit-pack a [ny, nx] bool mask into uint32 words, one run of ceil(nx/32) words per row.
 
@@ -242,7 +297,8 @@ class FnoShape:
     c_in: physical input channels (2 coordinate channels are appended);
     width: latent channels C; layers: Fourier layers N; modes: m, kept modes per
     corner block; dec_layers / dec_size: hidden layers and width of the decoder Q;
-    c_out: output channels.
+    c_out: output channels; padding: zero padding of the latent field (architecture
+    option of the appendix tables; it adds no parameters).
     """
     c_in: int = 4
     c_out: int = 3
@@ -251,6 +307,7 @@ class FnoShape:
     modes: int = 12
     dec_layers: int = 1
     dec_size: int = 32
+    padding: int = 0
 
 
 def fno_param_shapes(s: FnoShape):

@@ -141,3 +141,28 @@ def test_tensor_core_and_cuda_core_paths_agree():
     e = rel_l2(y_tc, y_cc)
     print(f"tensor-core vs CUDA-core path: rel L2 {e:.3e}")
     assert e < REL_L2_FNO
+
+
+@pytest.mark.parametrize("name,cin,cout,width,layers,modes,dec_layers,dec,B,H,W", [
+    ("porous density model (114,273 params)", 1, 1, 16, 3, 6, 3, 32, 2, 64, 128),
+    ("porous velocity model (896,082 params)", 1, 2, 16, 6, 12, 3, 64, 1, 64, 128),
+    ("shear velocity model, 3 layers (2,409,771 params)", 2, 2, 14, 3, 32, 1, 32, 2, 64, 64),
+])
+def test_paper_models_with_padding_match_oracle(name, cin, cout, width, layers, modes, dec_layers,
+                                                dec, B, H, W):
+    """The appendix-table architectures with "Padding: 9" (latent field zero-padded after
+    lifting, cropped after the last Fourier layer), on the CUDA-core path."""
+    _requires_gpu()
+    s = synth.FnoShape(c_in=cin, c_out=cout, width=width, layers=layers, modes=modes,
+                       dec_layers=dec_layers, dec_size=dec, padding=9)
+    g = FnoShape(c_in=cin, c_out=cout, width=width, layers=layers, modes=modes,
+                 dec_layers=dec_layers, dec_size=dec, padding=9)
+    params = synth.fno_random_params(s, seed=21, out_scale=1.0)
+    net = Fno(g, synth.fno_flatten_params(s, params))
+    assert not net.uses_tensor_cores(H, W)
+    x = _inputs(B, cin, H, W, seed=23)
+    y = net(torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = fo.fno_forward(s, params, x)
+    e = rel_l2(y, ref)
+    print(f"{name} padded {B}x{H}x{W}: rel L2 {e:.3e} ({fo.param_count(s)} params)")
+    assert e < REL_L2_FNO

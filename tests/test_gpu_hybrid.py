@@ -135,3 +135,75 @@ def test_uneven_batch_super_time_stepping_matches_oracle():
         e = rel_l2(np.stack([ux[k].numpy()[fl], uy[k].numpy()[fl]]), np.stack([oux[fl], ouy[fl]]))
         print(f"uneven batch {g.nx}x{g.ny}: rel L2 u {e:.3e}")
         assert e < 2e-2
+
+
+def _pair_nets(cin_r, cin_u, width=8, modes=3, padding=0, seed=0, out_scale=1e-1):
+    sr = synth.FnoShape(c_in=cin_r, c_out=1, width=width, layers=1, modes=modes, dec_size=width,
+                        padding=padding)
+    su = synth.FnoShape(c_in=cin_u, c_out=2, width=width, layers=2, modes=modes, dec_size=width,
+                        padding=padding)
+    pr = synth.fno_random_params(sr, seed=seed, out_scale=out_scale)
+    pu = synth.fno_random_params(su, seed=seed + 1, out_scale=out_scale)
+    gr = Fno(FnoShape(c_in=cin_r, c_out=1, width=width, layers=1, modes=modes, dec_size=width,
+                      padding=padding), synth.fno_flatten_params(sr, pr))
+    gu = Fno(FnoShape(c_in=cin_u, c_out=2, width=width, layers=2, modes=modes, dec_size=width,
+                      padding=padding), synth.fno_flatten_params(su, pu))
+    return (sr, pr), (su, pu), gr, gu
+
+
+def test_density_and_velocity_networks_steady_from_the_mask():
+    """Porous-media model group: a density and a velocity network, each reading the mask
+    only (in channels: 1), padding 9, steady driver."""
+    _requires_gpu()
+    specs = _porous(2)
+    (sr, pr), (su, pu), gr, gu = _pair_nets(1, 1, padding=9, out_scale=1.0)
+    lat = Lattice([a for a, _ in specs], [b for _, b in specs])
+    hyb = Hybrid(lat, gr, HybridConfig(use_fno=1, neq_mode=1, check_every=100, tol=1e-30,
+                                       max_steps=200, in_channels=8, in_channels_u=8), fno_u=gu)
+    st, _, _ = hyb.advance()
+    assert st.steps == 200 and st.fno_calls == 2
+    parts = lat.split(lat.export_f().cpu(), per_cell=9)
+    nets = ((sr, pr, (3,)), (su, pu, (3,)))
+    for k, (g, solid) in enumerate(specs):
+        f, _ = oracle.hybrid_steady(to_oracle(g), solid, None, None, nsteps=200, check_every=100,
+                                    nets=nets)
+        fl = ~solid
+        e = rel_l2(parts[k].numpy()[:, fl], (f - W[:, None, None])[:, fl])
+        print(f"two-network steady grid {k}: rel L2 g {e:.3e}")
+        assert e < 2e-2
+
+
+def test_density_and_velocity_networks_unsteady_periodic():
+    """Shear-layer model group: density network on rho - 1, velocity network on (u_x, u_y),
+    padding 9, on fully periodic grids of two sizes, k = 20 LBM steps + 1 FNO step."""
+    _requires_gpu()
+    specs = []
+    for k, n in enumerate((32, 48)):
+        specs.append((GridSpec(n, n, 0.6), np.zeros((n, n), dtype=bool)))
+    (sr, pr), (su, pu), gr, gu = _pair_nets(1, 2, padding=9, seed=4)
+    lat = Lattice([a for a, _ in specs], [b for _, b in specs])
+    rho0, ux0, uy0 = [], [], []
+    for k, (g, _) in enumerate(specs):
+        r, u, v = synth.smooth_macro_fields(g.nx, g.ny, seed=60 + k, drho=1e-2, umax=0.05)
+        rho0.append(r.ravel()); ux0.append(u.ravel()); uy0.append(v.ravel())
+    fields = [torch.from_numpy(np.concatenate(a)).cuda() for a in (rho0, ux0, uy0)]
+    lat.reinit(*fields, neq_mode=1)
+    hyb = Hybrid(lat, gr, HybridConfig(mode=P._abi.HYBRID_UNSTEADY, k_lbm=20, m_fno=1, neq_mode=1,
+                                       in_channels=1, in_channels_u=6), fno_u=gu)
+    st, _, _ = hyb.advance(cycles=2)
+    torch.cuda.synchronize()
+    assert st.steps == 40 and st.fno_calls == 2 * 2 * 2
+    _, ux, uy = (lat.split(t.cpu()) for t in lat.macro())
+    nets = ((sr, pr, (0,)), (su, pu, (1, 2)))
+    off = lat.cell_offsets
+    for k, (g, solid) in enumerate(specs):
+        og = to_oracle(g)
+        f0 = oracle.reinit(og, solid, rho0[k].reshape(g.ny, g.nx).astype(np.float64),
+                           ux0[k].reshape(g.ny, g.nx).astype(np.float64),
+                           uy0[k].reshape(g.ny, g.nx).astype(np.float64), 1)
+        f = oracle.hybrid_unsteady(og, solid, None, None, f0, k_lbm=20, m_fno=1, cycles=2,
+                                   nets=nets)
+        _, oux, ouy = oracle.macro(og, solid, f)
+        e = rel_l2(np.stack([ux[k].numpy(), uy[k].numpy()]), np.stack([oux, ouy]))
+        print(f"two-network unsteady {g.nx}x{g.ny}: rel L2 u {e:.3e}")
+        assert e < 2e-2

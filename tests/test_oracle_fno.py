@@ -176,3 +176,85 @@ def test_fno_without_spectral_part_is_pointwise():
     out2 = fo.fno_forward(shape, params, phi2)
     diff = np.abs(out2 - out).sum(axis=(0, 1))
     assert diff[3, 5] > 0 and np.count_nonzero(diff > 1e-14) == 1
+
+
+def test_padding_with_zero_spectral_filters_is_invisible():
+    """With all spectral filters zero the network is pointwise, so padding the latent field
+    and cropping it back must not change the output (a crop of the wrong corner would:
+    the padded cells hold sigma(b), not the interior values)."""
+    base = synth.FnoShape(width=8, layers=2, modes=3, dec_size=8)
+    padded = synth.FnoShape(width=8, layers=2, modes=3, dec_size=8, padding=5)
+    params = synth.fno_random_params(base, seed=3, out_scale=1.0)
+    for n in range(2):
+        for k in ("r1.re", "r1.im", "r2.re", "r2.im"):
+            params[f"layer{n}.{k}"] = np.zeros_like(params[f"layer{n}.{k}"])
+    x = np.random.default_rng(1).standard_normal((2, 4, 9, 11))
+    np.testing.assert_allclose(fo.fno_forward(padded, params, x), fo.fno_forward(base, params, x),
+                               rtol=0, atol=1e-13)
+
+
+def test_padded_layer_matches_brute_force_sums():
+    """One padded Fourier layer written out with explicit loops: zero-extend the lifted field
+    to (H+p) x (W+p), truncated DFT / mixing / Hermitian inverse as double sums over the
+    padded grid, + W theta + b, GELU, crop to H x W, decoder."""
+    shape = synth.FnoShape(c_in=1, c_out=1, width=2, layers=1, modes=2, dec_size=2, padding=3)
+    params = synth.fno_random_params(shape, seed=5, out_scale=1.0)
+    p = {k: fo.bf16(v) for k, v in params.items()}
+    H, W, pad = 4, 5, 3
+    x = fo.bf16(np.random.default_rng(2).standard_normal((1, 1, H, W)))
+    Hp, Wp, m, C = H + pad, W + pad, 2, 2
+    coords = fo.coordinate_channels(H, W)
+    theta = np.zeros((C, Hp, Wp))
+    for y in range(H):
+        for xx in range(W):
+            v = np.array([x[0, 0, y, xx], coords[0, y, xx], coords[1, y, xx]])
+            h = fo.gelu(p["lift0.w"] @ v + p["lift0.b"])
+            theta[:, y, xx] = p["lift1.w"] @ h + p["lift1.b"]
+    kys = list(range(m)) + list(range(Hp - m, Hp))
+    R = np.concatenate([p["layer0.r1.re"] + 1j * p["layer0.r1.im"],
+                        p["layer0.r2.re"] + 1j * p["layer0.r2.im"]], axis=2)  # [i][o][a][kx]
+    Xh = np.zeros((C, 2 * m, m), complex)
+    for i in range(C):
+        for a, ky in enumerate(kys):
+            for kx in range(m):
+                Xh[i, a, kx] = sum(theta[i, y, xx] * np.exp(-2j * np.pi * (ky * y / Hp + kx * xx / Wp))
+                                   for y in range(Hp) for xx in range(Wp))
+    Yh = np.einsum("iak,ioak->oak", Xh, R)
+    out = np.zeros((C, Hp, Wp))
+    for o in range(C):
+        for y in range(Hp):
+            for xx in range(Wp):
+                s = 0.0
+                for a, ky in enumerate(kys):
+                    for kx in range(m):
+                        s += (1.0 if kx == 0 else 2.0) * np.real(
+                            Yh[o, a, kx] * np.exp(2j * np.pi * (ky * y / Hp + kx * xx / Wp)))
+                lin = p["layer0.w"][o] @ theta[:, y, xx] + p["layer0.b"][o]
+                out[o, y, xx] = fo.gelu(lin + s / (Hp * Wp))
+    ref = np.zeros((1, 1, H, W))
+    for y in range(H):
+        for xx in range(W):
+            h = fo.gelu(p["dec0.w"] @ out[:, y, xx] + p["dec0.b"])
+            ref[0, 0, y, xx] = (p["out.w"] @ h + p["out.b"])[0]
+    np.testing.assert_allclose(fo.fno_forward(shape, params, x), ref, rtol=0, atol=1e-12)
+
+
+def test_tensor_core_path_erf_constants_meet_the_published_bound():
+    """The tensor-core kernels evaluate GELU with the Abramowitz & Stegun 7.1.26 rational
+    approximation of erf.  The constants as written in the CUDA source, evaluated in FP64,
+    must stay within the formula's published bound |error| <= 1.5e-7 of the library erf
+    (a mistyped digit breaks the bound)."""
+    import os
+    import re
+    from scipy.special import erf
+    src = open(os.path.join(os.path.dirname(__file__), "..", "paper_2604_27158_gb300", "csrc",
+                            "fno_tc.cu")).read()
+    body = src[src.index("float erf_as("):src.index("// GELU in its erf form")]
+    nums = [float(v) for v in re.findall(r"-?\d+\.\d+(?=f)", body)]
+    # in source order: p, the 1 of 1 + p x, a5, a4, a3, a2, a1, the 1 of 1 - poly e^{-x^2}
+    assert len(nums) == 8 and nums[1] == 1.0 and nums[7] == 1.0
+    p, (a5, a4, a3, a2, a1) = nums[0], nums[2:7]
+    x = np.linspace(0.0, 6.0, 200001)
+    t = 1.0 / (1.0 + p * x)
+    approx = 1.0 - t * (a1 + t * (a2 + t * (a3 + t * (a4 + t * a5)))) * np.exp(-x * x)
+    assert np.max(np.abs(approx - erf(x))) <= 1.5e-7

@@ -335,3 +335,34 @@ def test_hybrid_steady_driver_runs_and_converges_toward_steady_state():
                                         use_fno=False)
     for hist in (hist_fno, hist_rest):
         assert hist[-1][1] < hist[1][1] < 1.0
+
+
+def test_vorticity_of_periodic_waves_is_the_closed_form_central_difference():
+    """On an empty periodic grid the central difference of sin(a n) is cos(a n) sin(a)
+    exactly, so omega = -sin(a) sin(a x) - sin(b) cos(b y) for u_y = cos(a x),
+    u_x = sin(b y)."""
+    nx, ny = 24, 16
+    g = _periodic(nx, ny, 0.8)
+    solid = np.zeros((ny, nx), bool)
+    a, b = 2 * np.pi * 3 / nx, 2 * np.pi * 2 / ny
+    X, Y = np.meshgrid(np.arange(nx), np.arange(ny))
+    w = oracle.vorticity(g, solid, np.sin(b * Y), np.cos(a * X))
+    ref = -np.sin(a) * np.sin(a * X) - np.sin(b) * np.cos(b * Y)
+    np.testing.assert_allclose(w, ref, rtol=0, atol=1e-14)
+
+
+def test_vorticity_stencils_near_solids_and_open_ends():
+    """u_y = 5 x, u_x = 0 on a grid with open ends and solid blocks: central and one-sided
+    differences of a linear field both give 5, except at fluid cells with no fluid
+    x-neighbour, where the stencil gives 0; solid cells report 0."""
+    nx, ny = 12, 8
+    g = oracle.Grid(nx=nx, ny=ny, tau=0.7, bc_west=oracle.BC_PRESSURE,
+                    bc_east=oracle.BC_PRESSURE, west_value=1.0, east_value=1.0)
+    solid = np.zeros((ny, nx), bool)
+    solid[2, 4] = solid[2, 6] = True     # cell (5, 2) has no fluid x-neighbour
+    solid[5:7, 8:10] = True
+    X, _ = np.meshgrid(np.arange(nx), np.arange(ny))
+    w = oracle.vorticity(g, solid, np.zeros((ny, nx)), 5.0 * X)
+    expect = np.where(solid, 0.0, 5.0)
+    expect[2, 5] = 0.0
+    np.testing.assert_array_equal(w, expect)
