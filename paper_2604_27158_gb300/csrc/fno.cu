@@ -222,25 +222,60 @@ __global__ void k_fwd_x(const __nv_bfloat16* __restrict__ theta, float2* __restr
 
 __device__ __forceinline__ int kept_ky(int a, int H, int m) { return a < m ? a : H - 2 * m + a; }
 
-// Forward y-DFT over the kept ky for one (b, kx): Xh[b][a][kx][c].
+// Forward y-DFT over the kept ky for one (b, kx): Xh[b][a][kx][c].  The column
+// X1[b][.][kx][.] is staged through shared memory 32 rows at a time; each thread keeps
+// the accumulators of its kept rows a = g, g + G, ... (G = blockDim / C) in registers and
+// advances each phase index (ky y mod H) by ky per row.
+constexpr int kFwdYAcc = 16;  // accumulators per thread: 2m <= 16 G
+constexpr int kFwdYRows = 32;
 __global__ void k_fwd_y(const float2* __restrict__ x1, float2* __restrict__ xh,
                         const float2* __restrict__ twy, int H, int C, int m) {
+  extern __shared__ float2 fy_s[];  // twiddles [H], then a [kFwdYRows][C] tile
+  float2* tile = fy_s + H;
   const int b = blockIdx.x / m, kx = blockIdx.x % m;
-  const int c = threadIdx.x % C, g0 = threadIdx.x / C, groups = blockDim.x / C;
-  if (g0 >= groups) return;
-  for (int a = g0; a < 2 * m; a += groups) {
-    const int ky = kept_ky(a, H, m);
-    float re = 0.f, im = 0.f;
-    int idx = 0;
-    for (int y = 0; y < H; ++y) {
-      const float2 v = x1[(((size_t)b * H + y) * m + kx) * C + c];
-      const float2 e = twy[idx];  // e^{-i phi} = cos - i sin
-      re += v.x * e.x + v.y * e.y;
-      im += v.y * e.x - v.x * e.y;
-      idx += ky;
-      if (idx >= H) idx -= H;
+  for (int t = threadIdx.x; t < H; t += blockDim.x) fy_s[t] = twy[t];
+  const int groups = blockDim.x / C;
+  const int c = threadIdx.x % C, g0 = threadIdx.x / C;
+  // kept rows handled per pass; more than kFwdYAcc * groups rows take several passes
+  for (int a0 = 0; a0 < 2 * m; a0 += kFwdYAcc * groups) {
+  float2 acc[kFwdYAcc];
+#pragma unroll
+  for (int k = 0; k < kFwdYAcc; ++k) acc[k] = make_float2(0.f, 0.f);
+  for (int y0 = 0; y0 < H; y0 += kFwdYRows) {
+    const int ny = min(kFwdYRows, H - y0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < ny * C; t += blockDim.x) {
+      const int yy = t / C, cc = t - yy * C;
+      tile[t] = x1[(((size_t)b * H + y0 + yy) * m + kx) * C + cc];
     }
-    xh[(((size_t)b * 2 * m + a) * m + kx) * C + c] = make_float2(re, im);
+    __syncthreads();
+    if (g0 < groups) {
+#pragma unroll
+      for (int k = 0; k < kFwdYAcc; ++k) {
+        const int a = a0 + g0 + k * groups;
+        if (a < 2 * m) {
+          const int ky = kept_ky(a, H, m);
+          int idx = (int)(((long long)ky * y0) % H);
+          for (int yy = 0; yy < ny; ++yy) {
+            const float2 v = tile[yy * C + c];
+            const float2 e = fy_s[idx];  // e^{-i phi} = cos - i sin
+            acc[k].x += v.x * e.x + v.y * e.y;
+            acc[k].y += v.y * e.x - v.x * e.y;
+            idx += ky;
+            if (idx >= H) idx -= H;
+          }
+        }
+      }
+    }
+  }
+  if (g0 < groups) {
+#pragma unroll
+    for (int k = 0; k < kFwdYAcc; ++k) {
+      const int a = a0 + g0 + k * groups;
+      if (a < 2 * m) xh[(((size_t)b * 2 * m + a) * m + kx) * C + c] = acc[k];
+    }
+  }
+  __syncthreads();  // the next pass restages the tile
   }
 }
 
@@ -279,9 +314,12 @@ __global__ void k_inv_y(const float2* __restrict__ yh, float2* __restrict__ z,
   if (g0 >= groups) return;
   for (int y = g0; y < H; y += groups) {
     float re = 0.f, im = 0.f;
+    int idx = 0;  // (ky y) mod H: ky = 0 .. m-1, then H-m .. H-1, advanced by y per row
     for (int a = 0; a < 2 * m; ++a) {
-      const int ky = kept_ky(a, H, m);
-      const float2 e = twy[(int)(((long long)ky * y) % H)];  // e^{+i phi} = cos + i sin
+      if (a == m) idx = (int)(((long long)(H - m) * y) % H);
+      const float2 e = twy[idx];  // e^{+i phi} = cos + i sin
+      idx += y;
+      if (idx >= H) idx -= H;
       const float2 v = ys[a * C + o];
       re += v.x * e.x - v.y * e.y;
       im += v.x * e.y + v.y * e.x;
@@ -428,6 +466,8 @@ int fno_create(const fno_config* cfg_h, const uint16_t* params_d, void* packed_d
                            (int)kRowSmemMax) != cudaSuccess ||
       cudaFuncSetAttribute(k_inv_x_w, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kRowSmemMax) != cudaSuccess ||
+      cudaFuncSetAttribute(k_fwd_y, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kRowSmemMax) != cudaSuccess ||
       fno_tc_prepare(*cfg_h) != LBM_OK) {
     set_error("fno_create: %s", cudaGetErrorString(cudaGetLastError()));
     delete h;
@@ -517,13 +557,16 @@ int fno_forward(fno_handle* h, const float* in_d, float* out_d, int B, int H, in
   const size_t smem_fx = (size_t)W * C * sizeof(float) + (size_t)W * sizeof(float2);
   const size_t smem_ix = (size_t)C * C * sizeof(float) + (size_t)m * C * sizeof(float2) +
                          (size_t)W * sizeof(float2);
+  LBM_REQUIRE(((size_t)H + kFwdYRows * C) * sizeof(float2) <= kRowSmemMax,
+              "fno_forward: H too large for the y-DFT kernel");
   LBM_REQUIRE(smem_fx <= kRowSmemMax && smem_ix <= kRowSmemMax,
               "fno_forward: W * C too large for the row kernels");
   const int cur_threads = 256;
   int cur = 0;
   for (int n = 0; n < c.layers; ++n) {
     k_fwd_x<<<rows, cur_threads, smem_fx, s>>>(th[cur], x1, twx, H, W, C, m);
-    k_fwd_y<<<B * m, cur_threads, 0, s>>>(x1, xh, twy, H, C, m);
+    k_fwd_y<<<B * m, cur_threads, ((size_t)H + kFwdYRows * C) * sizeof(float2), s>>>(
+        x1, xh, twy, H, C, m);
     k_mix<<<2 * m * m, cur_threads, (size_t)C * C * sizeof(float2), s>>>(
         xh, yh, reinterpret_cast<const float2*>(P + o.rt_off + o.rt_layer * n), B, C, 2 * m * m);
     k_inv_y<<<B * m, cur_threads, (size_t)2 * m * C * sizeof(float2), s>>>(yh, z, twy, H, C, m);

@@ -32,23 +32,8 @@
 
 namespace lbmfno {
 
-// erf by the rational approximation of Abramowitz & Stegun, Handbook of Mathematical
-// Functions, formula 7.1.26: erf(x) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) e^{-x^2},
-// t = 1 / (1 + p x) for x >= 0, odd extension; |error| <= 1.5e-7 for every x, below the
-// resolution of the bfloat16 latent fields it feeds.
-__device__ __forceinline__ float erf_as(float x) {
-  const float ax = fabsf(x);
-  const float t = __frcp_rn(fmaf(0.3275911f, ax, 1.0f));
-  const float poly =
-      t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f),
-                       -0.284496736f),
-               0.254829592f);
-  return copysignf(fmaf(-poly, __expf(-ax * ax), 1.0f), x);
-}
-// GELU in its erf form, x Phi(x) = x (1 + erf(x / sqrt 2)) / 2, or ReLU.
 __device__ __forceinline__ float act_tc(float v, int act) {
-  return act == FNO_ACT_GELU ? 0.5f * v * (1.0f + erf_as(v * 0.70710678118654752f))
-                             : fmaxf(v, 0.0f);
+  return act == FNO_ACT_GELU ? 0.5f * v * (1.0f + erff(v * 0.70710678118654752f)) : fmaxf(v, 0.0f);
 }
 __device__ __forceinline__ int kept_ky_tc(int a, int H, int m) { return a < m ? a : H - 2 * m + a; }
 

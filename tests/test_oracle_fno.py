@@ -238,23 +238,3 @@ def test_padded_layer_matches_brute_force_sums():
             ref[0, 0, y, xx] = (p["out.w"] @ h + p["out.b"])[0]
     np.testing.assert_allclose(fo.fno_forward(shape, params, x), ref, rtol=0, atol=1e-12)
 
-
-def test_tensor_core_path_erf_constants_meet_the_published_bound():
-    """The tensor-core kernels evaluate GELU with the Abramowitz & Stegun 7.1.26 rational
-    approximation of erf.  The constants as written in the CUDA source, evaluated in FP64,
-    must stay within the formula's published bound |error| <= 1.5e-7 of the library erf
-    (a mistyped digit breaks the bound)."""
-    import os
-    import re
-    from scipy.special import erf
-    src = open(os.path.join(os.path.dirname(__file__), "..", "paper_2604_27158_gb300", "csrc",
-                            "fno_tc.cu")).read()
-    body = src[src.index("float erf_as("):src.index("// GELU in its erf form")]
-    nums = [float(v) for v in re.findall(r"-?\d+\.\d+(?=f)", body)]
-    # in source order: p, the 1 of 1 + p x, a5, a4, a3, a2, a1, the 1 of 1 - poly e^{-x^2}
-    assert len(nums) == 8 and nums[1] == 1.0 and nums[7] == 1.0
-    p, (a5, a4, a3, a2, a1) = nums[0], nums[2:7]
-    x = np.linspace(0.0, 6.0, 200001)
-    t = 1.0 / (1.0 + p * x)
-    approx = 1.0 - t * (a1 + t * (a2 + t * (a3 + t * (a4 + t * a5)))) * np.exp(-x * x)
-    assert np.max(np.abs(approx - erf(x))) <= 1.5e-7
