@@ -190,8 +190,20 @@ __global__ void k_lift(const float* __restrict__ in, __nv_bfloat16* __restrict__
   }
 }
 
+// Twiddles by recurrence: e^{i k (n+1) phi} = e^{i k n phi} e^{i k phi}, a complex product
+// in registers instead of a shared-memory table load per term; the product is re-seeded
+// from the exact table every kReseed steps, which bounds the FP32 drift to ~kReseed ulps.
+constexpr int kReseed = 32;
+constexpr int kAccMaxV0 = 16;  // most accumulators per thread of the row / column DFTs
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
 // Forward x-DFT of one row (b, y): X1[kx][c] = sum_x theta[x][c] e^{-2 pi i kx x / W}.
-// Threads: c = tid % C, kx group = tid / C (kx = group, group + G, ...).
+// Threads: c = tid % C, kx group g = tid / C owns kx = g, g + G, ... (G = blockDim / C),
+// one pass of up to kAccX frequencies (a template: the launch picks the smallest power of
+// two covering ceil(m / G)); each staged value feeds all of them.
+template <int kAccX>
 __global__ void k_fwd_x(const __nv_bfloat16* __restrict__ theta, float2* __restrict__ x1,
                         const float2* __restrict__ twx, int H, int W, int C, int m) {
   extern __shared__ float smem_f[];
@@ -205,18 +217,39 @@ __global__ void k_fwd_x(const __nv_bfloat16* __restrict__ theta, float2* __restr
   const int groups = blockDim.x / C;
   const int c = threadIdx.x % C, g0 = threadIdx.x / C;
   if (g0 >= groups) return;
-  for (int kx = g0; kx < m; kx += groups) {
-    float re = 0.f, im = 0.f;
-    int idx = 0;
-    for (int x = 0; x < W; ++x) {
-      const float v = row[x * C + c];
-      const float2 e = tw[idx];
-      re = fmaf(v, e.x, re);
-      im = fmaf(-v, e.y, im);
-      idx += kx;
-      if (idx >= W) idx -= W;
+  for (int k0 = 0; k0 < m; k0 += kAccX * groups) {
+    float2 acc[kAccX], e[kAccX], step[kAccX];
+#pragma unroll
+    for (int k = 0; k < kAccX; ++k) {
+      const int kx = k0 + g0 + k * groups;
+      acc[k] = make_float2(0.f, 0.f);
+      step[k] = tw[kx < m ? kx : 0];
     }
-    x1[(r * m + kx) * C + c] = make_float2(re, im);
+    for (int x0 = 0; x0 < W; x0 += kReseed) {
+#pragma unroll
+      for (int k = 0; k < kAccX; ++k) {
+        const int kx = k0 + g0 + k * groups;
+        e[k] = tw[kx < m ? (int)(((long long)kx * x0) % W) : 0];
+      }
+      const int xe = min(W, x0 + kReseed);
+      for (int x = x0; x < xe; ++x) {
+        const float v = row[x * C + c];
+#pragma unroll
+        for (int k = 0; k < kAccX; ++k) {
+          const int kx = k0 + g0 + k * groups;
+          if (kx < m) {
+            acc[k].x = fmaf(v, e[k].x, acc[k].x);   // v e^{-i phi}: (v cos, -v sin)
+            acc[k].y = fmaf(-v, e[k].y, acc[k].y);
+            e[k] = cmul(e[k], step[k]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kAccX; ++k) {
+      const int kx = k0 + g0 + k * groups;
+      if (kx < m) x1[(r * m + kx) * C + c] = acc[k];
+    }
   }
 }
 
@@ -226,8 +259,8 @@ __device__ __forceinline__ int kept_ky(int a, int H, int m) { return a < m ? a :
 // X1[b][.][kx][.] is staged through shared memory 32 rows at a time; each thread keeps
 // the accumulators of its kept rows a = g, g + G, ... (G = blockDim / C) in registers and
 // advances each phase index (ky y mod H) by ky per row.
-constexpr int kFwdYAcc = 16;  // accumulators per thread: 2m <= 16 G
 constexpr int kFwdYRows = 32;
+template <int kFwdYAcc>
 __global__ void k_fwd_y(const float2* __restrict__ x1, float2* __restrict__ xh,
                         const float2* __restrict__ twy, int H, int C, int m) {
   extern __shared__ float2 fy_s[];  // twiddles [H], then a [kFwdYRows][C] tile
@@ -251,18 +284,24 @@ __global__ void k_fwd_y(const float2* __restrict__ x1, float2* __restrict__ xh,
     __syncthreads();
     if (g0 < groups) {
 #pragma unroll
+      float2 e[kFwdYAcc], step[kFwdYAcc];  // e^{+i ky y phi}, advanced by e^{+i ky phi}
+#pragma unroll
       for (int k = 0; k < kFwdYAcc; ++k) {
         const int a = a0 + g0 + k * groups;
-        if (a < 2 * m) {
-          const int ky = kept_ky(a, H, m);
-          int idx = (int)(((long long)ky * y0) % H);
-          for (int yy = 0; yy < ny; ++yy) {
-            const float2 v = tile[yy * C + c];
-            const float2 e = fy_s[idx];  // e^{-i phi} = cos - i sin
-            acc[k].x += v.x * e.x + v.y * e.y;
-            acc[k].y += v.y * e.x - v.x * e.y;
-            idx += ky;
-            if (idx >= H) idx -= H;
+        const int ky = a < 2 * m ? kept_ky(a, H, m) : 0;
+        e[k] = fy_s[(int)(((long long)ky * y0) % H)];
+        step[k] = fy_s[ky];
+      }
+      for (int yy = 0; yy < ny; ++yy) {
+        const float2 v = tile[yy * C + c];
+#pragma unroll
+        for (int k = 0; k < kFwdYAcc; ++k) {
+          const int a = a0 + g0 + k * groups;
+          if (a < 2 * m) {
+            // v e^{-i phi} = v conj(e)
+            acc[k].x += v.x * e[k].x + v.y * e[k].y;
+            acc[k].y += v.y * e[k].x - v.x * e[k].y;
+            e[k] = cmul(e[k], step[k]);
           }
         }
       }
@@ -314,15 +353,15 @@ __global__ void k_inv_y(const float2* __restrict__ yh, float2* __restrict__ z,
   if (g0 >= groups) return;
   for (int y = g0; y < H; y += groups) {
     float re = 0.f, im = 0.f;
-    int idx = 0;  // (ky y) mod H: ky = 0 .. m-1, then H-m .. H-1, advanced by y per row
+    const float2 step = twy[y];  // ky -> ky + 1 multiplies e^{+i ky y phi} by e^{+i y phi}
+    float2 e = make_float2(1.f, 0.f);
     for (int a = 0; a < 2 * m; ++a) {
-      if (a == m) idx = (int)(((long long)(H - m) * y) % H);
-      const float2 e = twy[idx];  // e^{+i phi} = cos + i sin
-      idx += y;
-      if (idx >= H) idx -= H;
+      if (a % kReseed == 0 || a == m)  // exact restart (and the jump to ky = H - m)
+        e = twy[(int)(((long long)kept_ky(a, H, m) * y) % H)];
       const float2 v = ys[a * C + o];
       re += v.x * e.x - v.y * e.y;
       im += v.x * e.y + v.y * e.x;
+      e = cmul(e, step);
     }
     z[(((size_t)b * H + y) * m + kx) * C + o] = make_float2(re, im);
   }
@@ -353,15 +392,16 @@ __global__ void k_inv_x_w(const __nv_bfloat16* __restrict__ theta, const float2*
   if (xg >= groups) return;
   const float bo = bias[o];
   for (int x = xg; x < W; x += groups) {
+    // sum_kx c_kx Re(Z[kx] e^{+i kx x phi}), e advanced by e^{+i x phi} per frequency
+    const float2 step = tw[x];
+    float2 e = make_float2(1.f, 0.f);
     float s = 0.f;
-    int idx = 0;
     for (int kx = 0; kx < m; ++kx) {
-      const float2 e = tw[idx];
+      if (kx % kReseed == 0 && kx > 0) e = tw[(int)(((long long)kx * x) % W)];
       const float2 v = zs[kx * C + o];
       const float t = v.x * e.x - v.y * e.y;
       s += (kx == 0 ? 1.0f : 2.0f) * t;
-      idx += x;
-      while (idx >= W) idx -= W;
+      e = cmul(e, step);
     }
     float a = fmaf(s, inv_hw, bo);
     const __nv_bfloat16* tv = src + (size_t)x * C;
@@ -417,6 +457,48 @@ using namespace lbmfno;
 
 static constexpr size_t kRowSmemMax = 200 * 1024;
 
+// Accumulators per thread for `count` outputs spread over `groups` thread groups: the
+// smallest power of two covering ceil(count / groups), at most kAccMaxV0 (more take passes).
+static int acc_per_thread(int count, int groups) {
+  const int need = (count + groups - 1) / groups;
+  int k = 1;
+  while (k < need && k < kAccMaxV0) k *= 2;
+  return k;
+}
+
+static int launch_fwd_x(int rows, int threads, size_t smem, cudaStream_t s,
+                        const __nv_bfloat16* th, float2* x1, const float2* twx, int H, int W,
+                        int C, int m) {
+  switch (acc_per_thread(m, threads / C)) {
+    case 1: k_fwd_x<1><<<rows, threads, smem, s>>>(th, x1, twx, H, W, C, m); break;
+    case 2: k_fwd_x<2><<<rows, threads, smem, s>>>(th, x1, twx, H, W, C, m); break;
+    case 4: k_fwd_x<4><<<rows, threads, smem, s>>>(th, x1, twx, H, W, C, m); break;
+    case 8: k_fwd_x<8><<<rows, threads, smem, s>>>(th, x1, twx, H, W, C, m); break;
+    default: k_fwd_x<16><<<rows, threads, smem, s>>>(th, x1, twx, H, W, C, m); break;
+  }
+  LBM_CHECK_LAUNCH();
+  return LBM_OK;
+}
+
+static int launch_fwd_y(int blocks, int threads, size_t smem, cudaStream_t s, const float2* x1,
+                        float2* xh, const float2* twy, int H, int C, int m) {
+  switch (acc_per_thread(2 * m, threads / C)) {
+    case 1: k_fwd_y<1><<<blocks, threads, smem, s>>>(x1, xh, twy, H, C, m); break;
+    case 2: k_fwd_y<2><<<blocks, threads, smem, s>>>(x1, xh, twy, H, C, m); break;
+    case 4: k_fwd_y<4><<<blocks, threads, smem, s>>>(x1, xh, twy, H, C, m); break;
+    case 8: k_fwd_y<8><<<blocks, threads, smem, s>>>(x1, xh, twy, H, C, m); break;
+    default: k_fwd_y<16><<<blocks, threads, smem, s>>>(x1, xh, twy, H, C, m); break;
+  }
+  LBM_CHECK_LAUNCH();
+  return LBM_OK;
+}
+
+template <typename K>
+static bool raise_smem(K kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kRowSmemMax) == cudaSuccess;
+}
+
 struct fno_handle {
   fno_config cfg;
   FnoOffsets off;
@@ -462,12 +544,10 @@ int fno_create(const fno_config* cfg_h, const uint16_t* params_d, void* packed_d
   h->packed = static_cast<float*>(packed_d);
   cudaStream_t s = SS(stream);
   // row kernels size their shared memory by W; opt in once (not allowed inside graph capture)
-  if (cudaFuncSetAttribute(k_fwd_x, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kRowSmemMax) != cudaSuccess ||
-      cudaFuncSetAttribute(k_inv_x_w, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kRowSmemMax) != cudaSuccess ||
-      cudaFuncSetAttribute(k_fwd_y, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kRowSmemMax) != cudaSuccess ||
+  if (!raise_smem(k_fwd_x<1>) || !raise_smem(k_fwd_x<2>) || !raise_smem(k_fwd_x<4>) ||
+      !raise_smem(k_fwd_x<8>) || !raise_smem(k_fwd_x<16>) || !raise_smem(k_fwd_y<1>) ||
+      !raise_smem(k_fwd_y<2>) || !raise_smem(k_fwd_y<4>) || !raise_smem(k_fwd_y<8>) ||
+      !raise_smem(k_fwd_y<16>) || !raise_smem(k_inv_x_w) ||
       fno_tc_prepare(*cfg_h) != LBM_OK) {
     set_error("fno_create: %s", cudaGetErrorString(cudaGetLastError()));
     delete h;
@@ -564,9 +644,9 @@ int fno_forward(fno_handle* h, const float* in_d, float* out_d, int B, int H, in
   const int cur_threads = 256;
   int cur = 0;
   for (int n = 0; n < c.layers; ++n) {
-    k_fwd_x<<<rows, cur_threads, smem_fx, s>>>(th[cur], x1, twx, H, W, C, m);
-    k_fwd_y<<<B * m, cur_threads, ((size_t)H + kFwdYRows * C) * sizeof(float2), s>>>(
-        x1, xh, twy, H, C, m);
+    LBM_TRY(launch_fwd_x(rows, cur_threads, smem_fx, s, th[cur], x1, twx, H, W, C, m));
+    LBM_TRY(launch_fwd_y(B * m, cur_threads, ((size_t)H + kFwdYRows * C) * sizeof(float2), s, x1,
+                         xh, twy, H, C, m));
     k_mix<<<2 * m * m, cur_threads, (size_t)C * C * sizeof(float2), s>>>(
         xh, yh, reinterpret_cast<const float2*>(P + o.rt_off + o.rt_layer * n), B, C, 2 * m * m);
     k_inv_y<<<B * m, cur_threads, (size_t)2 * m * C * sizeof(float2), s>>>(yh, z, twy, H, C, m);
