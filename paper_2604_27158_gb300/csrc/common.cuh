@@ -76,8 +76,8 @@ struct GridDev {
   int nx, ny;
   int pitch;        // floats between rows of a population plane (multiple of 32)
   int wpr;          // mask words per row = ceil(nx/32)
-  long long f_off;  // offset (floats) of population plane 0 in a state buffer
-  long long plane;  // floats per population plane = ny * pitch
+  long long f_off;  // offset (floats) of the grid's first row inside each population plane
+  long long plane;  // floats per population plane of the batch (every grid's rows)
   long long mask_off;
   long long cell_off;  // offset of the grid in dense fields
   int blk_start;       // first block of the grid in flat 256-cell block launches

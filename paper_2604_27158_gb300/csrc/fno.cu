@@ -283,7 +283,6 @@ __global__ void k_fwd_y(const float2* __restrict__ x1, float2* __restrict__ xh,
     }
     __syncthreads();
     if (g0 < groups) {
-#pragma unroll
       float2 e[kFwdYAcc], step[kFwdYAcc];  // e^{+i ky y phi}, advanced by e^{+i ky phi}
 #pragma unroll
       for (int k = 0; k < kFwdYAcc; ++k) {

@@ -8,10 +8,11 @@
 // State and data layout (all FP32, HBM resident, caller-owned):
 //   * Two state buffers A/B (ping-pong).  The current buffer holds the
 //     *post-collision* populations of the previous time level, shifted by the
-//     lattice weights (g*_i = f*_i - w_i), structure of arrays per grid:
-//     plane i of grid g at f_off + i * ny * pitch, rows `pitch` floats apart
-//     (pitch = nx rounded up to 32 so each warp's 32 lanes read one aligned
-//     128-byte line per population).
+//     lattice weights (g*_i = f*_i - w_i), structure of arrays over the whole
+//     batch: plane i holds population i of every grid, grid g's rows starting at
+//     f_off inside the plane, rows `pitch` floats apart (pitch = nx rounded up to
+//     32 so each warp's 32 lanes read one aligned 128-byte line per population).
+//     A batch of small grids is thus nine contiguous streams, like one tall grid.
 //   * One step is a *pull*: cell x gathers g*_i(x - c_i) (bounce-back
 //     g*_opp(i)(x) when x - c_i is solid), completes the Zou-He unknowns on the
 //     open end columns, takes moments, relaxes, and stores its own nine g*
@@ -20,6 +21,7 @@
 //   * Solid cells are never read by the step; it stores 0 into their slots.
 #include <math.h>
 #include <stdarg.h>
+#include <stddef.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -120,24 +122,13 @@ struct StepShape {
                 "stage row offsets");
 };
 
-// Grid of tile t: binary search over the shape's per-grid first-tile prefix.
-__device__ __forceinline__ int grid_of_tile(const int* __restrict__ tile_start, int ngrids,
-                                            int t) {
-  int lo = 0, hi = ngrids - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (__ldg(&tile_start[mid]) <= t)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  return lo;
-}
+// Tiles are described by an int4 per tile and shape, built at lbm_init: (grid, first
+// column x0, first row y0, rows covered -- the last tile row of a grid can be short).
 
 template <int TY, int ST, int MB>
 __global__ void __launch_bounds__((TY + 1) * 32, MB)
-    k_step_tma(const GridDev* __restrict__ grids, int ngrids, const int* __restrict__ tile_start,
-               int ntiles, const uint32_t* __restrict__ mask, const float* __restrict__ src,
+    k_step_tma(const GridDev* __restrict__ grids, const int4* __restrict__ tiles, int ntiles,
+               const uint32_t* __restrict__ mask, const float* __restrict__ src,
                float* __restrict__ dst, unsigned* __restrict__ status) {
   using SS = StepShape<TY, ST, MB>;
   using TileMeta = typename SS::Meta;
@@ -160,32 +151,44 @@ __global__ void __launch_bounds__((TY + 1) * 32, MB)
   if (warp == kTY) {
     // ------------------------------------------------------------ producer
     // Everything a tile needs from global memory besides the populations (its
-    // grid, the grid descriptor words, the mask words) is loaded into registers
-    // before waiting for the stage to drain, so those dependent loads overlap the
-    // consumers' work on the previous tiles.
+    // descriptor, the grid descriptor words, the mask words) is loaded into registers
+    // before waiting for the stage to drain, and the next tile's descriptor one
+    // iteration ahead, so these dependent loads stay off the consumers' path.  The
+    // grid's fields the producer itself needs come from the descriptor words by warp
+    // shuffles.
     constexpr int kMetaWords = (int)(sizeof(GridDev) / 4);
     constexpr int kMaskRegs = (kMaskWords + 31) / 32;
     static_assert(kMetaWords <= 32, "grid descriptor copied by one warp pass");
+    constexpr int kWNy = (int)(offsetof(GridDev, ny) / 4);
+    constexpr int kWPitch = (int)(offsetof(GridDev, pitch) / 4);
+    constexpr int kWWpr = (int)(offsetof(GridDev, wpr) / 4);
+    constexpr int kWFoff = (int)(offsetof(GridDev, f_off) / 4);
+    constexpr int kWPlane = (int)(offsetof(GridDev, plane) / 4);
+    constexpr int kWMask = (int)(offsetof(GridDev, mask_off) / 4);
+    auto word64 = [](uint32_t w, int at) {
+      const uint32_t lo = __shfl_sync(0xffffffffu, w, at);
+      const uint32_t hi = __shfl_sync(0xffffffffu, w, at + 1);
+      return (long long)(((unsigned long long)hi << 32) | lo);
+    };
     int k = 0;
     bool ok = true;
+    int4 next = blockIdx.x < (unsigned)ntiles ? __ldg(&tiles[blockIdx.x]) : make_int4(0, 0, 0, 0);
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
       const int s = k % kStages;
-      const int gi = grid_of_tile(tile_start, ngrids, t);
-      const GridDev* Gp = grids + gi;
-      const int lt = t - __ldg(&tile_start[gi]);
-      const int nseg = __ldg(&Gp->nseg), ny = __ldg(&Gp->ny), pitch = __ldg(&Gp->pitch);
-      const int yt = lt / nseg;
-      const int x0 = (lt - yt * nseg) * kSeg, y0 = yt * kTY;
-      const float* b = src + __ldg(&Gp->f_off);
-      const long long plane = __ldg(&Gp->plane);
+      const int4 d = next;
+      if (t + (int)gridDim.x < ntiles) next = __ldg(&tiles[t + gridDim.x]);
+      const int gi = d.x, x0 = d.y, y0 = d.z, rows = d.w;
+      const uint32_t* gw = reinterpret_cast<const uint32_t*>(grids + gi);
+      const uint32_t meta_w = lane < kMetaWords ? __ldg(gw + lane) : 0u;
+      const int ny = (int)__shfl_sync(0xffffffffu, meta_w, kWNy);
+      const int pitch = (int)__shfl_sync(0xffffffffu, meta_w, kWPitch);
+      const int wpr = (int)__shfl_sync(0xffffffffu, meta_w, kWWpr);
+      const float* b = src + word64(meta_w, kWFoff);
+      const long long plane = word64(meta_w, kWPlane);
+      const uint32_t* m = mask + word64(meta_w, kWMask);
       const int xs = max(x0 - 4, 0);
       const int xe = min(x0 + kSeg + 4, pitch);
       const unsigned seg_bytes = (unsigned)(xe - xs) * 4u;
-      const int rows = min(kTY, ny - y0);
-      const uint32_t* gw = reinterpret_cast<const uint32_t*>(Gp);
-      const uint32_t meta_w = lane < kMetaWords ? __ldg(gw + lane) : 0u;
-      const uint32_t* m = mask + __ldg(&Gp->mask_off);
-      const int wpr = __ldg(&Gp->wpr);
       uint32_t mask_w[kMaskRegs];
 #pragma unroll
       for (int q = 0; q < kMaskRegs; ++q) {
@@ -383,7 +386,7 @@ __global__ void __launch_bounds__((TY + 1) * 32, MB)
 // Tile shapes compiled into the library (rows per tile, stages, CTAs per SM).
 // Every shape performs the same arithmetic per cell in the same order, so the
 // choice changes speed only; lbm_autotune times them on the caller's batch.
-using StepKernel = void (*)(const GridDev*, int, const int*, int, const uint32_t*, const float*,
+using StepKernel = void (*)(const GridDev*, const int4*, int, const uint32_t*, const float*,
                            float*, unsigned*);
 struct StepVariant {
   int ty, stages, minb;
@@ -799,6 +802,18 @@ static int plan_layout(const lbm_grid* grids, int ngrids, lbm_layout* lay,
   size_t f = 0, words = 0, cells = 0;
   long long blk = 0, tiles = 0, rblk = 0;
   if (gd) gd->clear();
+  // Population-major batch layout: plane i holds population i of every grid, grid after
+  // grid (each grid ny rows of pitch floats), so a batch of small grids streams nine
+  // contiguous planes exactly like one tall grid.
+  size_t plane_all = 0;
+  for (int k = 0; k < ngrids; ++k) {
+    LBM_REQUIRE(grids[k].nx >= 2 && grids[k].ny >= 2 && grids[k].nx <= (1 << 20) &&
+                    grids[k].ny <= (1 << 20),
+                "lbm: grid %d has invalid size %d x %d", k, grids[k].nx, grids[k].ny);
+    plane_all += (size_t)grids[k].ny * align_up((size_t)grids[k].nx, 32);
+  }
+  LBM_REQUIRE((size_t)kQ * plane_all < (1ull << 31),
+              "lbm: batch too large (9 * padded cells >= 2^31)");
   for (int k = 0; k < ngrids; ++k) {
     const lbm_grid& g = grids[k];
     LBM_REQUIRE(g.nx >= 2 && g.ny >= 2 && g.nx <= (1 << 20) && g.ny <= (1 << 20),
@@ -822,11 +837,11 @@ static int plan_layout(const lbm_grid* grids, int ngrids, lbm_layout* lay,
     d.ny = g.ny;
     d.pitch = (int)align_up((size_t)g.nx, 32);
     d.wpr = (g.nx + 31) / 32;
-    d.f_off = (long long)f;
-    d.plane = (long long)g.ny * d.pitch;
+    d.f_off = (long long)f;  // offset of the grid's first row inside each plane
+    d.plane = (long long)plane_all;
     d.mask_off = (long long)words;
     d.cell_off = (long long)cells;
-    d.nblk = (int)((d.plane + kBlock - 1) / kBlock);
+    d.nblk = (int)(((long long)g.ny * d.pitch + kBlock - 1) / kBlock);
     d.blk_start = (int)blk;
     d.nseg = (g.nx + kSeg - 1) / kSeg;
     d.nrblk = (int)(((long long)d.nseg * g.ny + kBlock / 32 - 1) / (kBlock / 32));
@@ -843,9 +858,7 @@ static int plan_layout(const lbm_grid* grids, int ngrids, lbm_layout* lay,
     d.bc_east = g.bc_east;
     d.west_d = (float)(g.bc_west == LBM_BC_PRESSURE ? g.west_value - 1.0 : g.west_value);
     d.east_d = (float)(g.bc_east == LBM_BC_PRESSURE ? g.east_value - 1.0 : g.east_value);
-    LBM_REQUIRE((size_t)kQ * d.plane < (1ull << 31),
-                "lbm: grid %d too large for one batch entry (9*ny*pitch >= 2^31)", k);
-    f += (size_t)kQ * d.plane;
+    f += (size_t)g.ny * d.pitch;
     words += (size_t)d.wpr * g.ny;
     cells += (size_t)g.nx * g.ny;
     blk += d.nblk;
@@ -862,8 +875,13 @@ static int plan_layout(const lbm_grid* grids, int ngrids, lbm_layout* lay,
   w.stats_off = align_up(w.partial_off + (size_t)rblk * R_COUNT * sizeof(double), 256);
   w.status_off = align_up(w.stats_off + (size_t)ngrids * R_COUNT * sizeof(double), 256);
   w.tiles_off = align_up(w.status_off + sizeof(unsigned), 256);
-  w.total = align_up(w.tiles_off + (size_t)LBM_STEP_VARIANTS * (ngrids + 1) * sizeof(int), 256);
-  lay->f_elems = f;
+  size_t tiles_all = 0;  // descriptors of every tile shape
+  for (int v = 0; v < LBM_STEP_VARIANTS; ++v)
+    for (int k = 0; k < ngrids; ++k)
+      tiles_all += (size_t)((grids[k].nx + kSeg - 1) / kSeg) *
+                   ((grids[k].ny + kStepVariants[v].ty - 1) / kStepVariants[v].ty);
+  w.total = align_up(w.tiles_off + tiles_all * sizeof(int4), 256);
+  lay->f_elems = (size_t)kQ * plane_all;
   lay->mask_words = words;
   lay->cells = cells;
   lay->ws_bytes = w.total;
@@ -877,9 +895,8 @@ static inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s)
 static int launch_step(Handle* h, int v, const float* src, float* dst, cudaStream_t s) {
   const StepVariant& sv = kStepVariants[v];
   const int ctas = std::min(h->ntiles_v[v], h->nsm * std::max(1, h->blocks_per_sm_v[v]));
-  sv.kernel<<<ctas, (sv.ty + 1) * 32, sv.smem, s>>>(
-      h->gd_d, h->ngrids, h->tile_start_d + (size_t)v * (h->ngrids + 1), h->ntiles_v[v],
-      h->mask, src, dst, h->status_d);
+  sv.kernel<<<ctas, (sv.ty + 1) * 32, sv.smem, s>>>(h->gd_d, h->tiles_d[v], h->ntiles_v[v],
+                                                     h->mask, src, dst, h->status_d);
   LBM_CHECK_LAUNCH();
   return LBM_OK;
 }
@@ -928,17 +945,22 @@ int lbm_init(const lbm_grid* grids_h, int ngrids, const uint32_t* mask_d, float*
   h->partial = reinterpret_cast<double*>(ws + wp.partial_off);
   h->stats_d = reinterpret_cast<double*>(ws + wp.stats_off);
   h->status_d = reinterpret_cast<unsigned*>(ws + wp.status_off);
-  h->tile_start_d = reinterpret_cast<int*>(ws + wp.tiles_off);
-  std::vector<int> tile_prefix((size_t)LBM_STEP_VARIANTS * (ngrids + 1));
+  // tile descriptors of every shape: grid after grid, row of tiles after row of tiles
+  std::vector<int4> tiles;
+  std::vector<size_t> tiles_at(LBM_STEP_VARIANTS);
   for (int v = 0; v < LBM_STEP_VARIANTS; ++v) {
-    long long acc = 0;
+    tiles_at[v] = tiles.size();
+    const int ty = kStepVariants[v].ty;
     for (int k = 0; k < ngrids; ++k) {
-      tile_prefix[(size_t)v * (ngrids + 1) + k] = (int)acc;
-      acc += (long long)h->gd[k].nseg * ((h->gd[k].ny + kStepVariants[v].ty - 1) / kStepVariants[v].ty);
+      const GridDev& d = h->gd[k];
+      for (int y0 = 0; y0 < d.ny; y0 += ty)
+        for (int sg = 0; sg < d.nseg; ++sg)
+          tiles.push_back(make_int4(k, sg * kSeg, y0, std::min(ty, d.ny - y0)));
     }
-    tile_prefix[(size_t)v * (ngrids + 1) + ngrids] = (int)acc;
-    h->ntiles_v[v] = (int)acc;
+    h->ntiles_v[v] = (int)(tiles.size() - tiles_at[v]);
   }
+  for (int v = 0; v < LBM_STEP_VARIANTS; ++v)
+    h->tiles_d[v] = reinterpret_cast<int4*>(ws + wp.tiles_off) + tiles_at[v];
   h->stats_h.assign((size_t)ngrids * R_COUNT, 0.0);
   h->u_max2 = (float)(u_max * u_max);
   cudaStream_t s = S(stream);
@@ -970,7 +992,7 @@ int lbm_init(const lbm_grid* grids_h, int ngrids, const uint32_t* mask_d, float*
       cudaMemsetAsync(f_b_d, 0, h->layout.f_elems * sizeof(float), s) != cudaSuccess ||
       cudaMemsetAsync(h->ux_prev, 0, 2 * h->layout.cells * sizeof(float), s) != cudaSuccess ||
       cudaMemsetAsync(h->status_d, 0, sizeof(unsigned), s) != cudaSuccess ||
-      cudaMemcpyAsync(h->tile_start_d, tile_prefix.data(), tile_prefix.size() * sizeof(int),
+      cudaMemcpyAsync(h->tiles_d[0], tiles.data(), tiles.size() * sizeof(int4),
                       cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {
     set_error("lbm_init: %s", cudaGetErrorString(cudaGetLastError()));

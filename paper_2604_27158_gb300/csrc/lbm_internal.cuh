@@ -18,7 +18,7 @@ struct Handle {
   int variant = 0;                             // step-kernel tile shape in use
   int ntiles_v[LBM_STEP_VARIANTS] = {};        // tiles of the batch per shape
   int blocks_per_sm_v[LBM_STEP_VARIANTS] = {};  // resident CTAs per SM per shape
-  int* tile_start_d = nullptr;                 // per-shape first-tile prefixes (workspace)
+  int4* tiles_d[LBM_STEP_VARIANTS] = {};      // per-shape tile descriptors (workspace)
   unsigned* status_d = nullptr;
   unsigned status_h = 0;
   const uint32_t* mask = nullptr;
