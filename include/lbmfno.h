@@ -196,6 +196,17 @@ int lbm_steps_done(const lbm_handle* h, long long* out_h);
 
 int lbm_destroy(lbm_handle* h);
 
+/* Self-test of failure detection (the paper has no counterpart).  The step kernel and
+ * the tensor-core FNO kernels never wait without a limit: a device-side wait that does
+ * not complete in time sets a status bit, the kernel returns, and the next call that
+ * reads the status (lbm_residual, fno_check) reports LBM_ERR_TIMEOUT with the context
+ * still usable.  This call runs the same kind of bounded mbarrier wait in a one-warp
+ * kernel, on a barrier that nothing arrives on (arrive = 0) or on one that completes
+ * (arrive != 0), with a limit of limit_ms (0 < limit_ms <= 2000).  status_d: one
+ * caller-owned device word (overwritten).  Synchronises `stream`.  Returns
+ * LBM_ERR_TIMEOUT when the wait expired, LBM_OK when it completed. */
+int lbm_wait_selftest(unsigned* status_d, int arrive, double limit_ms, void* stream);
+
 /* ----------------------------------------------------------------------
  * Adjoint (reverse mode) of the LBM part of the hybrid pipeline, for training
  * the FNO on a loss taken after LBM steps that follow its prediction (Sec. 2.3).

@@ -99,6 +99,7 @@ _PROTOS = {
     "lbm_get_step_variant": ([VP, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                               ctypes.POINTER(I)], I),
     "lbm_destroy": ([VP], I),
+    "lbm_wait_selftest": ([VP, I, ctypes.c_double, VP], I),
     "lbm_adjoint_macro": ([VP, VP, VP, VP, VP, VP, VP], I),
     "lbm_adjoint_step": ([VP, VP, VP, VP, VP], I),
     "lbm_adjoint_reinit": ([VP, VP, VP, VP, VP, I, VP, VP, VP, VP, VP], I),

@@ -51,6 +51,14 @@ def _stream_ptr(stream: Optional[torch.cuda.Stream]) -> ctypes.c_void_p:
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def wait_selftest(arrive: bool, limit_ms: float, device: str = "cuda", stream=None) -> int:
+    """Run the library's bounded device-side wait on a barrier that completes (arrive) or
+    never does; returns the status code (LBM_OK or LBM_ERR_TIMEOUT) without raising."""
+    status = torch.zeros(1, dtype=torch.int32, device=device)
+    return int(_abi.lib().lbm_wait_selftest(ctypes.c_void_p(status.data_ptr()), int(arrive),
+                                            float(limit_ms), _stream_ptr(stream)))
+
+
 def query_layout(grids: Sequence[GridSpec]) -> lbm_layout:
     arr = (lbm_grid * len(grids))(*[g.c() for g in grids])
     lay = lbm_layout()
