@@ -147,6 +147,11 @@ __global__ void __launch_bounds__((TY + 1) * 32, MB)
     mbar_init_fence();
   }
   __syncthreads();
+  // Programmatic dependent launch: the next step may be scheduled as this grid drains;
+  // no thread touches the populations before the previous step has completed and its
+  // writes are visible (its source is this step's destination and vice versa).
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 
   if (warp == kTY) {
     // ------------------------------------------------------------ producer
@@ -895,9 +900,21 @@ static inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s)
 static int launch_step(Handle* h, int v, const float* src, float* dst, cudaStream_t s) {
   const StepVariant& sv = kStepVariants[v];
   const int ctas = std::min(h->ntiles_v[v], h->nsm * std::max(1, h->blocks_per_sm_v[v]));
-  sv.kernel<<<ctas, (sv.ty + 1) * 32, sv.smem, s>>>(h->gd_d, h->tiles_d[v], h->ntiles_v[v],
-                                                     h->mask, src, dst, h->status_d);
-  LBM_CHECK_LAUNCH();
+  // launched with programmatic stream serialisation: consecutive steps overlap the
+  // launch of the next grid with the tail of the previous one (see griddepcontrol above)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)ctas);
+  cfg.blockDim = dim3((unsigned)((sv.ty + 1) * 32));
+  cfg.dynamicSmemBytes = sv.smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  LBM_CHECK_CUDA(cudaLaunchKernelEx(&cfg, sv.kernel, (const GridDev*)h->gd_d,
+                                    (const int4*)h->tiles_d[v], h->ntiles_v[v],
+                                    (const uint32_t*)h->mask, src, dst, h->status_d));
   return LBM_OK;
 }
 
