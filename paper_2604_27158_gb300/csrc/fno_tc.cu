@@ -37,6 +37,25 @@ __device__ __forceinline__ float act_tc(float v, int act) {
 }
 __device__ __forceinline__ int kept_ky_tc(int a, int H, int m) { return a < m ? a : H - 2 * m + a; }
 
+// Copy n float2 from global to shared memory with kIlp loads in flight per thread before
+// the stores (a plain element loop waits for each load in turn).
+template <int kIlp, typename Src>
+__device__ __forceinline__ void stage_ilp(float2* __restrict__ dst, int n, Src src) {
+  for (int t0 = threadIdx.x; t0 < n; t0 += blockDim.x * kIlp) {
+    float2 v[kIlp];
+#pragma unroll
+    for (int u = 0; u < kIlp; ++u) {
+      const int t = t0 + u * (int)blockDim.x;
+      v[u] = t < n ? src(t) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < kIlp; ++u) {
+      const int t = t0 + u * (int)blockDim.x;
+      if (t < n) dst[t] = v[u];
+    }
+  }
+}
+
 // ------------------------------------------------------------------ tables
 // Fw[x/8][n][x%8]: n < m: cos(2 pi n x / W); m <= n < 2m: -sin(2 pi (n-m) x / W); else 0.
 __global__ void k_table_fwd(__nv_bfloat16* __restrict__ fw, int W, int m) {
@@ -367,10 +386,10 @@ __global__ void __launch_bounds__(256)
   float2* tw = col + (size_t)H * kC;  // H
   float2* xh = tw + H;                // 2m * kC
   const int b = blockIdx.x / m, kx = blockIdx.x % m;
-  for (int t = threadIdx.x; t < H * kC; t += blockDim.x) {
+  stage_ilp<8>(col, H * kC, [&](int t) {
     const int y = t / kC, c = t - y * kC;
-    col[t] = x1[(((size_t)b * H + y) * m + kx) * kC + c];
-  }
+    return x1[(((size_t)b * H + y) * m + kx) * kC + c];
+  });
   for (int t = threadIdx.x; t < H; t += blockDim.x) tw[t] = twy[t];
   __syncthreads();
   constexpr int kGroups = 256 / kC;
@@ -436,7 +455,7 @@ __global__ void __launch_bounds__(256)
   const int nblk = (H + kSpecRows - 1) / kSpecRows;
   const int b = blockIdx.x / nblk, y0 = (blockIdx.x - b * nblk) * kSpecRows;
   const int n = 2 * m * m * kC;
-  for (int t = threadIdx.x; t < n; t += blockDim.x) ys[t] = yh[(size_t)b * n + t];
+  stage_ilp<8>(ys, n, [&](int t) { return yh[(size_t)b * n + t]; });
   for (int t = threadIdx.x; t < kSpecRows * 2 * m; t += blockDim.x) {
     const int rr = t / (2 * m), a = t - rr * 2 * m;
     const int y = min(y0 + rr, H - 1);
