@@ -156,10 +156,9 @@ __global__ void __launch_bounds__(128)
   }
 }
 
-// Projection Q from the channel-blocked field; one thread per pixel, decoder
-// weights staged in shared memory.  kS > 0: one hidden layer of width kS and
-// kOut outputs, fully unrolled (registers); kS == 0: any decoder shape.
-template <int kC, int kS, int kOut>
+// Projection Q from the channel-blocked field, any decoder shape (the common shape
+// runs in k_decoder_tc); one thread per pixel, decoder weights staged in shared memory.
+template <int kC>
 __global__ void __launch_bounds__(128)
     k_decoder_blk(const __nv_bfloat16* __restrict__ theta, float* __restrict__ out,
                   const float* __restrict__ params, const unsigned* __restrict__ offs,
@@ -192,26 +191,7 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
     for (int q = 0; q < 8; ++q) a[g * 8 + q] = __bfloat162float(hv[q]);
   }
-  if constexpr (kS > 0) {
-    const float* w1 = dec_s;
-    const float* b1 = w1 + kS * kC;
-    const float* w2 = b1 + kS;
-    const float* b2 = w2 + kOut * kS;
-    float o[kOut];
-#pragma unroll
-    for (int q = 0; q < kOut; ++q) o[q] = b2[q];
-#pragma unroll 4
-    for (int j = 0; j < kS; ++j) {
-      float v = b1[j];
-#pragma unroll
-      for (int c = 0; c < kC; ++c) v = fmaf(w1[j * kC + c], a[c], v);
-      v = act_tc(v, act);
-#pragma unroll
-      for (int q = 0; q < kOut; ++q) o[q] = fmaf(w2[q * kS + j], v, o[q]);
-    }
-#pragma unroll
-    for (int q = 0; q < kOut; ++q) out[(((size_t)b * kOut + q) * H + y) * W + x] = o[q];
-  } else {
+  {
     float h[64], t[64];
 #pragma unroll
     for (int c = 0; c < kC; ++c) h[c] = a[c];
@@ -636,6 +616,152 @@ __global__ void __launch_bounds__(kInvThreads, 1)
   if (warp == 0) tmem_dealloc(tmem, 2 * kAccCols);
 }
 
+// ------------------------------------------ 5. projection Q (tcgen05 + CUDA cores)
+// One hidden layer of width S = C and kOut outputs:  out = Q2 act(Q1 theta + q1) + q2.
+// The C x S contraction runs on the tensor cores (M = 128 x positions of one image
+// row, N = S, K = C; theta and Q1 both K-major, no swizzle); the epilogue adds q1,
+// applies the activation and contracts with Q2 in FP32.  Several CTAs share an SM so
+// that enough epilogue warps hide the activation's latency.
+constexpr int kDecStages = 4;
+constexpr int kDecCtasPerSm = 3;
+
+template <int kC, int kOut>
+__global__ void __launch_bounds__(kTcThreads, kDecCtasPerSm)
+    k_decoder_tc(const __nv_bfloat16* __restrict__ theta, float* __restrict__ out,
+                 const float* __restrict__ params, const unsigned* __restrict__ offs, int B,
+                 int H, int W, int act, unsigned* __restrict__ status) {
+  constexpr int kS = kC;
+  constexpr int kG = kC / 8;
+  constexpr int kStageBytes = kG * 128 * 16;  // [channel group][x (128)][8]
+  constexpr int kAccCols = kS < 32 ? 32 : kS;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* q1_s = smem;                       // Q1 as [k group][s][8] bf16
+  unsigned char* stages = smem + kG * kS * 16;      // kDecStages * kStageBytes
+  __shared__ __align__(16) float4 ep_s[kS];         // {q1[j], Q2[0][j], Q2[1][j], Q2[2][j]}
+  __shared__ float q2_s[kOut];
+  __shared__ __align__(8) uint64_t full_bar[kDecStages], empty_bar[kDecStages];
+  __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
+  __shared__ uint32_t tmem_base;
+  static_assert(kOut <= 3, "epilogue packs Q2 rows into a float4 with the hidden bias");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int xt = W / 128;
+  const int ntiles = B * H * xt;
+  const float* w1 = params + offs[0];
+  const float* b1 = params + offs[1];
+  const float* w2 = params + offs[2];
+  const float* b2 = params + offs[3];
+
+  for (int e = threadIdx.x; e < kS * kC; e += blockDim.x) {
+    const int g = e / (kS * 8), sl = (e / 8) % kS, il = e % 8;
+    reinterpret_cast<__nv_bfloat16*>(q1_s)[e] = __float2bfloat16_rn(w1[sl * kC + g * 8 + il]);
+  }
+  for (int j = threadIdx.x; j < kS; j += blockDim.x)
+    ep_s[j] = make_float4(b1[j], kOut > 0 ? w2[j] : 0.f, kOut > 1 ? w2[kS + j] : 0.f,
+                          kOut > 2 ? w2[2 * kS + j] : 0.f);
+  for (int q = threadIdx.x; q < kOut; q += blockDim.x) q2_s[q] = b2[q];
+  fence_proxy_async_smem();
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kDecStages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], 4);
+    }
+    mbar_init_fence();
+  }
+  if (warp == 0) tmem_alloc(&tmem_base, 2 * kAccCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 4) {
+    // ------------------------------------------------------------ producer
+    int k = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+      const int s = k % kDecStages;
+      if (k >= kDecStages) ok = mbar_wait(&empty_bar[s], ((k / kDecStages) - 1) & 1, status);
+      if (!ok) break;
+      const int row = t / xt;  // b * H + y
+      const int x0 = (t - row * xt) * 128;
+      unsigned char* st = stages + (size_t)s * kStageBytes;
+      if (lane == 0) mbar_arrive_expect_tx(&full_bar[s], (unsigned)kStageBytes);
+      __syncwarp();
+      if (lane < kG)
+        bulk_g2s(st + lane * 2048, theta + (((size_t)row * kG + lane) * W + x0) * 8, 2048,
+                 &full_bar[s]);
+    }
+    for (int q = max(0, k - kDecStages); q < k; ++q)
+      mbar_wait(&full_bar[q % kDecStages], (q / kDecStages) & 1, status);
+  } else if (warp == 5) {
+    // ---------------------------------------------------------------- MMA
+    constexpr uint32_t idesc = idesc_bf16(128, kS, false, false);
+    int j = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+      const int acc = j & 1;
+      if (j >= 2) ok = mbar_wait(&acc_empty[acc], ((j >> 1) - 1) & 1, status);
+      if (ok) ok = mbar_wait(&full_bar[j % kDecStages], (j / kDecStages) & 1, status);
+      if (!ok) break;
+      tc_fence_after();
+      if (lane == 0) {
+        const unsigned char* st = stages + (size_t)(j % kDecStages) * kStageBytes;
+#pragma unroll
+        for (int kk = 0; kk < kG / 2; ++kk) {
+          const uint64_t ad = smem_desc(st + kk * 2 * 2048, 2048, 128);
+          const uint64_t bd = smem_desc(q1_s + kk * 2 * kS * 16, kS * 16, 128);
+          mma_bf16(tmem + acc * kAccCols, ad, bd, idesc, kk > 0);
+        }
+        mma_commit(&empty_bar[j % kDecStages]);
+        mma_commit(&acc_full[acc]);
+      }
+      __syncwarp();
+    }
+  } else {
+    // ----------------------------------------------------------- epilogue
+    // warp w holds TMEM lanes 32 w .. 32 w + 31: x positions x0 + 32 w + lane
+    int j = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+      const int acc = j & 1;
+      if (!mbar_wait(&acc_full[acc], (j >> 1) & 1, status)) break;
+      tc_fence_after();
+      float o[3] = {kOut > 0 ? q2_s[0] : 0.f, kOut > 1 ? q2_s[1] : 0.f, kOut > 2 ? q2_s[2] : 0.f};
+#pragma unroll
+      for (int cb = 0; cb < kAccCols / 32; ++cb) {
+        float v[32];
+        const uint32_t ta = tmem + acc * kAccCols + cb * 32 + ((uint32_t)(warp * 32) << 16);
+        if (kS >= 32) tmem_ld32(ta, v);
+        else tmem_ld16(ta, v);
+        if (cb == kAccCols / 32 - 1) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acc_empty[acc]);
+        }
+#pragma unroll
+        for (int i = 0; i < (kS < 32 ? kS : 32); ++i) {
+          const float4 e = ep_s[cb * 32 + i];
+          const float h = act_tc(v[i] + e.x, act);
+          o[0] = fmaf(e.y, h, o[0]);
+          o[1] = fmaf(e.z, h, o[1]);
+          o[2] = fmaf(e.w, h, o[2]);
+        }
+      }
+      const int row = t / xt;
+      const int b = row / H, y = row - b * H;
+      const int x = (t - row * xt) * 128 + warp * 32 + lane;
+#pragma unroll
+      for (int q = 0; q < kOut; ++q) out[(((size_t)b * kOut + q) * H + y) * W + x] = o[q];
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, 2 * kAccCols);
+}
+
 // ------------------------------------------------------------------- host
 bool fno_tc_supported(const fno_config& c, int H, int W) {
   const size_t C = c.width, m = c.modes;
@@ -725,14 +851,17 @@ static int fno_forward_tc_impl(const fno_config& c, const FnoTcParams& P, const 
   }
   const size_t dec_smem =
       ((size_t)c.dec_layers * (c.dec_size * 64 + c.dec_size) + c.c_out * 64 + c.c_out) * sizeof(float);
-  if (c.dec_layers == 1 && c.dec_size == kC && c.c_out == 3)
-    k_decoder_blk<kC, kC, 3><<<(unsigned)((pix + 127) / 128), 128, dec_smem, s>>>(
+  if (c.dec_layers == 1 && c.dec_size == kC && c.c_out == 3) {
+    const size_t smem_tc = (size_t)kC * kC * 2 + (size_t)kDecStages * (kC / 8) * 128 * 16;
+    const int ntiles = B * H * (W / 128);
+    const int ctas = std::min(ntiles, kDecCtasPerSm * nsm);
+    k_decoder_tc<kC, 3><<<ctas, kTcThreads, smem_tc, s>>>(th[cur], out, P.params, P.dec_offs, B,
+                                                          H, W, c.activation, status);
+  } else {
+    k_decoder_blk<kC><<<(unsigned)((pix + 127) / 128), 128, dec_smem, s>>>(
         th[cur], out, P.params, P.dec_offs, c.dec_layers, B, H, W, c.dec_size, c.c_out,
         c.activation);
-  else
-    k_decoder_blk<kC, 0, 1><<<(unsigned)((pix + 127) / 128), 128, dec_smem, s>>>(
-        th[cur], out, P.params, P.dec_offs, c.dec_layers, B, H, W, c.dec_size, c.c_out,
-        c.activation);
+  }
   LBM_CHECK_LAUNCH();
   return LBM_OK;
 }
@@ -744,6 +873,7 @@ static int tc_set_smem_attrs() {
   LBM_CHECK_CUDA(cudaFuncSetAttribute(k_inv_x_tc<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   LBM_CHECK_CUDA(cudaFuncSetAttribute(k_spec_fwd<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   LBM_CHECK_CUDA(cudaFuncSetAttribute(k_spec_inv<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_decoder_tc<kC, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   return LBM_OK;
 }
 
