@@ -8,10 +8,13 @@
 //  1. k_fwd_x_tc   X1[b][y][kx][c] = sum_x theta[x][c] e^{-2 pi i kx x / W}
 //                  tcgen05: D[(row, c)][kx re|im] = A[(row, c)][x] * Fw[x][kx re|im]
 //                  (M = 128 = 128/C rows x C channels, N = 32, K = W; A MN-major)
-//  2. k_spec_fwd   per (b, kx): y-DFT over the kept ky, then the per-mode complex
-//                  channel mixing -> Yh[b][a][kx][o]            (CUDA cores)
-//  3. k_spec_inv   per (b, row block): inverse y-DFT -> Zt[b][y][k'/8][o][k'%8]
-//                  (bfloat16, k' < m real parts, m <= k' < 2m imaginary parts)
+//  2. k_ydft_tc    Xh[a, kx][b][c] = sum_y X1[b][y][kx][c] e^{-2 pi i ky(a) y / H}
+//                  tcgen05: D[(kx, c)][(a, re|im)] = X1b[(kx, c)][(y, re|im)] * Fy
+//                  (M = 128, N = 4m rounded up to 16, K = 2H; X1 carried in bfloat16)
+//  3. k_mix        per mode: Y[b][o] = sum_c Xh[b][c] R[c][o]   (CUDA cores, FP32),
+//                  written as the bfloat16 operand Yb of the inverse y-DFT
+//     k_iydft_tc   Zt[b][y][k'/8][o][k'%8] = Ty[y][(a, re|im)] * Yb[(a, re|im)][(k', o)]
+//                  (k' < m real parts, m <= k' < 2m imaginary parts, M = 128 rows y)
 //  4. k_inv_x_tc   theta'[x][o] = act( sum_k' T[x][k'] Zt[k'][o] + sum_i theta[x][i] W[o][i] + b[o] )
 //                  tcgen05: D[x][o] = [T | theta][x][k] * [Zt ; W^T][k][o]
 //                  (M = 128 x positions, N = C, K = 32 + C; both operands K-major)
@@ -36,25 +39,6 @@ __device__ __forceinline__ float act_tc(float v, int act) {
   return act == FNO_ACT_GELU ? 0.5f * v * (1.0f + erff(v * 0.70710678118654752f)) : fmaxf(v, 0.0f);
 }
 __device__ __forceinline__ int kept_ky_tc(int a, int H, int m) { return a < m ? a : H - 2 * m + a; }
-
-// Copy n float2 from global to shared memory with kIlp loads in flight per thread before
-// the stores (a plain element loop waits for each load in turn).
-template <int kIlp, typename Src>
-__device__ __forceinline__ void stage_ilp(float2* __restrict__ dst, int n, Src src) {
-  for (int t0 = threadIdx.x; t0 < n; t0 += blockDim.x * kIlp) {
-    float2 v[kIlp];
-#pragma unroll
-    for (int u = 0; u < kIlp; ++u) {
-      const int t = t0 + u * (int)blockDim.x;
-      v[u] = t < n ? src(t) : make_float2(0.f, 0.f);
-    }
-#pragma unroll
-    for (int u = 0; u < kIlp; ++u) {
-      const int t = t0 + u * (int)blockDim.x;
-      if (t < n) dst[t] = v[u];
-    }
-  }
-}
 
 // ------------------------------------------------------------------ tables
 // Fw[x/8][n][x%8]: n < m: cos(2 pi n x / W); m <= n < 2m: -sin(2 pi (n-m) x / W); else 0.
@@ -89,14 +73,57 @@ __global__ void k_table_inv(__nv_bfloat16* __restrict__ ti, int H, int W, int m)
   }
   ti[t] = __float2bfloat16_rn(v);
 }
-// tw[t] = (cos, sin)(2 pi t / N)
-__global__ void k_twiddle_tc(float2* __restrict__ tw, int N) {
+// Sizes of the spectral stage.  The forward y-DFT's N (= the inverse y-DFT's K) runs
+// over (a, re|im) for the 2m kept ky, rounded up to a multiple of 16; the inverse's N
+// runs over (k', o) in chunks of knk consecutive k' (8, or 4 for C = 64 so that a
+// chunk is at most 256 accumulator columns).
+struct SpecDims {
+  int nf;      // 4m rounded up to 16
+  int kg;      // nf / 8: K groups of the inverse y-DFT
+  int knk;     // k' per inverse N chunk
+  int nc;      // inverse N chunks: ceil(2m / knk)
+  int nchunk;  // columns per inverse chunk: knk * C
+  int nn;      // nc * nchunk
+};
+__host__ __device__ inline SpecDims spec_dims(int C, int m) {
+  SpecDims d;
+  d.nf = (4 * m + 15) / 16 * 16;
+  d.kg = d.nf / 8;
+  d.knk = C <= 32 ? 8 : 4;
+  d.nc = (2 * m + d.knk - 1) / d.knk;
+  d.nchunk = d.knk * C;
+  d.nn = d.nc * d.nchunk;
+  return d;
+}
+// Fy[y/4][n][(y%4) * 2 + p], n = 2a + q: the real form of e^{-2 pi i ky(a) y / H} that
+// maps the pair (Re, Im) (p) of X1[y] to (Re, Im) (q) of the kept mode a; 0 for a >= 2m.
+__global__ void k_table_fy(__nv_bfloat16* __restrict__ fy, int H, int m, int nf) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < N) {
-    double s, c;
-    sincospi(2.0 * (double)t / (double)N, &s, &c);
-    tw[t] = make_float2((float)c, (float)s);
+  if (t >= (H / 4) * nf * 8) return;
+  const int j = t & 7, n = (t >> 3) % nf, yg = (t >> 3) / nf;
+  const int y = yg * 4 + (j >> 1), p = j & 1, a = n >> 1, q = n & 1;
+  float v = 0.0f;
+  if (a < 2 * m) {
+    double sn, cs;
+    sincospi(2.0 * (double)((long long)kept_ky_tc(a, H, m) * y % H) / (double)H, &sn, &cs);
+    v = (float)(p == 0 ? (q == 0 ? cs : -sn) : (q == 0 ? sn : cs));
   }
+  fy[t] = __float2bfloat16_rn(v);
+}
+// Ty[a/4][y][(a%4) * 2 + p]: cos (p = 0) and sin (p = 1) of 2 pi ky(a) y / H for the
+// inverse y-DFT; rows padded to hp (a multiple of 128) and a >= 2m are 0.
+__global__ void k_table_ty(__nv_bfloat16* __restrict__ ty, int H, int hp, int m, int kg) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= kg * hp * 8) return;
+  const int j = t & 7, y = (t >> 3) % hp, g = (t >> 3) / hp;
+  const int a = g * 4 + (j >> 1), p = j & 1;
+  float v = 0.0f;
+  if (a < 2 * m && y < H) {
+    double sn, cs;
+    sincospi(2.0 * (double)((long long)kept_ky_tc(a, H, m) * y % H) / (double)H, &sn, &cs);
+    v = (float)(p == 0 ? cs : sn);
+  }
+  ty[t] = __float2bfloat16_rn(v);
 }
 
 // ---------------------------------------------------- lifting / projection
@@ -228,7 +255,7 @@ constexpr int kFwdStageBytes = 128 * kFwdChunk * 2;  // 16 KB: 128 (row, channel
 template <int kC>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_fwd_x_tc(const __nv_bfloat16* __restrict__ theta, const __nv_bfloat16* __restrict__ fw,
-               float2* __restrict__ x1, int B, int H, int W, int m,
+               __nv_bfloat16* __restrict__ x1b, int B, int H, int W, int m,
                unsigned* __restrict__ status) {
   constexpr int kRows = 128 / kC;  // image rows per tile
   constexpr int kG = kC / 8;       // 8-channel groups
@@ -342,8 +369,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int r = mi / kC, c = mi - r * kC;
       const int y = y0 + r;
       if (y < H) {
-        float2* o = x1 + (((size_t)b * H + y) * m) * kC + c;
-        for (int kx = 0; kx < m; ++kx) o[(size_t)kx * kC] = make_float2(v[kx], v[m + kx]);
+        // X1b[b][y/4][kx][c][(y%4) * 2 + re|im]: the K-major operand of the y-DFT
+        uint32_t* o = reinterpret_cast<uint32_t*>(x1b) +
+                      ((((size_t)b * (H / 4) + (y >> 2)) * m) * kC + c) * 4 + (y & 3);
+        for (int kx = 0; kx < m; ++kx) {
+          const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[kx], v[m + kx]);
+          o[(size_t)kx * kC * 4] = *reinterpret_cast<const uint32_t*>(&h2);
+        }
       }
     }
   }
@@ -354,128 +386,325 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (warp == 0) tmem_dealloc(tmem, 64);
 }
 
-// ------------------------------------- 2. y-DFT + per-mode mixing (CUDA cores)
-// One block per (b, kx).  Xh[a][c] = sum_y X1[b][y][kx][c] e^{-2 pi i ky(a) y / H};
-// Yh[b][a][kx][o] = sum_c Xh[a][c] R[a * m + kx][c][o].
+// ------------------------------------------------------ 2. y-DFT (tcgen05)
+// Xh[a * m + kx][b][c] = sum_y X1[b][y][kx][c] e^{-2 pi i ky(a) y / H} for the 2m kept ky:
+// D[(kx, c)][(a, re|im)] = X1b[(kx, c)][(y, re|im)] * Fy[(y, re|im)][(a, re|im)]
+// (M = 128 (kx, c) rows of one batch item, N = nf, K = 2H; both operands K-major).
+// The Fy table stays in shared memory; X1b streams through a ring of kYChunk y groups.
+constexpr int kYStages = 4;
+constexpr int kYChunk = 8;                   // y groups of 4 rows per stage
+constexpr int kYStageBytes = kYChunk * 2048;  // [group][row (128)][8]
+
 template <int kC>
-__global__ void __launch_bounds__(256)
-    k_spec_fwd(const float2* __restrict__ x1, const float2* __restrict__ rt,
-               float2* __restrict__ yh, const float2* __restrict__ twy, int H, int m) {
-  extern __shared__ float2 sm2[];
-  float2* col = sm2;                  // H * kC
-  float2* tw = col + (size_t)H * kC;  // H
-  float2* xh = tw + H;                // 2m * kC
-  const int b = blockIdx.x / m, kx = blockIdx.x % m;
-  stage_ilp<8>(col, H * kC, [&](int t) {
-    const int y = t / kC, c = t - y * kC;
-    return x1[(((size_t)b * H + y) * m + kx) * kC + c];
-  });
-  for (int t = threadIdx.x; t < H; t += blockDim.x) tw[t] = twy[t];
-  __syncthreads();
-  constexpr int kGroups = 256 / kC;
-  constexpr int kMaxA = (32 + kGroups - 1) / kGroups;  // kept ky per thread (2m <= 32)
-  const int c = threadIdx.x % kC, g0 = threadIdx.x / kC;
-  float re[kMaxA], im[kMaxA];
-  int idx[kMaxA], step[kMaxA];
-#pragma unroll
-  for (int q = 0; q < kMaxA; ++q) {
-    re[q] = 0.f;
-    im[q] = 0.f;
-    idx[q] = 0;
-    const int a = g0 + q * kGroups;
-    step[q] = a < 2 * m ? kept_ky_tc(a, H, m) : 0;
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_ydft_tc(const __nv_bfloat16* __restrict__ x1b, const __nv_bfloat16* __restrict__ fy,
+              float2* __restrict__ xh, int B, int H, int m, unsigned* __restrict__ status) {
+  const SpecDims d = spec_dims(kC, m);
+  const int rows = m * kC;  // (kx, c) rows of one batch item
+  const int mt = (rows + 127) / 128;
+  const int ntiles = B * mt;
+  const int ngroups = H / 4;
+  const int nchunks = (ngroups + kYChunk - 1) / kYChunk;
+  const unsigned fy_bytes = (unsigned)ngroups * d.nf * 16;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* fy_s = smem;
+  unsigned char* stages = smem + ((fy_bytes + 1023) & ~1023u);
+  __shared__ __align__(8) uint64_t full_bar[kYStages], empty_bar[kYStages];
+  __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], fy_bar;
+  __shared__ uint32_t tmem_base;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kYStages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], 4);
+    }
+    mbar_init(&fy_bar, 1);
+    mbar_init_fence();
   }
-#pragma unroll 2
-  for (int y = 0; y < H; ++y) {
-    const float2 v = col[y * kC + c];
+  if (warp == 0) tmem_alloc(&tmem_base, 128);  // two accumulators of up to 64 columns
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 4) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      mbar_arrive_expect_tx(&fy_bar, fy_bytes);
+      bulk_g2s(fy_s, fy, fy_bytes, &fy_bar);
+    }
+    __syncwarp();
+    int k = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const int b = t / mt, m0 = (t - b * mt) * 128;
+      const int nv = min(128, rows - m0);
+      for (int ch = 0; ch < nchunks; ++ch, ++k) {
+        const int s = k % kYStages;
+        if (k >= kYStages) ok = mbar_wait(&empty_bar[s], ((k / kYStages) - 1) & 1, status);
+        if (!ok) break;
+        const int g0 = ch * kYChunk, gn = min(kYChunk, ngroups - g0);
+        unsigned char* st = stages + (size_t)s * kYStageBytes;
+        if (lane == 0) mbar_arrive_expect_tx(&full_bar[s], (unsigned)(gn * nv * 16));
+        __syncwarp();
+        for (int q = lane; q < gn; q += 32)
+          bulk_g2s(st + q * 2048, x1b + (((size_t)b * ngroups + g0 + q) * rows + m0) * 8,
+                   (unsigned)(nv * 16), &full_bar[s]);
+      }
+    }
+    mbar_wait(&fy_bar, 0, status);
+    for (int q = max(0, k - kYStages); q < k; ++q)
+      mbar_wait(&full_bar[q % kYStages], (q / kYStages) & 1, status);
+  } else if (warp == 5) {
+    // ---------------------------------------------------------------- MMA
+    const uint32_t idesc = idesc_bf16(128, d.nf, false, false);
+    bool ok = mbar_wait(&fy_bar, 0, status);
+    int k = 0, j = 0;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++j) {
+      const int acc = j & 1;
+      if (j >= 2) ok = mbar_wait(&acc_empty[acc], ((j >> 1) - 1) & 1, status);
+      if (!ok) break;
+      tc_fence_after();
+      for (int ch = 0; ch < nchunks; ++ch, ++k) {
+        const int s = k % kYStages;
+        ok = mbar_wait(&full_bar[s], (k / kYStages) & 1, status);
+        if (!ok) break;
+        tc_fence_after();
+        if (lane == 0) {
+          const unsigned char* st = stages + (size_t)s * kYStageBytes;
+          const int g0 = ch * kYChunk, gn = min(kYChunk, ngroups - g0);
+          for (int kk = 0; kk < gn / 2; ++kk) {
+            const uint64_t ad = smem_desc(st + kk * 4096, 2048, 128);
+            const uint64_t bd = smem_desc(fy_s + (size_t)(g0 + 2 * kk) * d.nf * 16, d.nf * 16, 128);
+            mma_bf16(tmem + acc * 64, ad, bd, idesc, ch > 0 || kk > 0);
+          }
+          mma_commit(&empty_bar[s]);
+        }
+        __syncwarp();
+      }
+      if (!ok) break;
+      if (lane == 0) mma_commit(&acc_full[acc]);
+      __syncwarp();
+    }
+  } else {
+    // ----------------------------------------------------------- epilogue
+    int j = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+      const int acc = j & 1;
+      if (!mbar_wait(&acc_full[acc], (j >> 1) & 1, status)) break;
+      tc_fence_after();
+      const int b = t / mt, row = (t - b * mt) * 128 + warp * 32 + lane;
+      const int kx = row / kC, c = row - kx * kC;
+      for (int cb = 0; cb < d.nf / 16; ++cb) {
+        float v[16];
+        tmem_ld16(tmem + acc * 64 + cb * 16 + ((uint32_t)(warp * 32) << 16), v);
+        if (row < rows) {
 #pragma unroll
-    for (int q = 0; q < kMaxA; ++q) {
-      const float2 e = tw[idx[q]];  // e^{-i phi} = cos - i sin
-      re[q] = fmaf(v.x, e.x, fmaf(v.y, e.y, re[q]));
-      im[q] = fmaf(v.y, e.x, fmaf(-v.x, e.y, im[q]));
-      idx[q] += step[q];
-      if (idx[q] >= H) idx[q] -= H;
+          for (int i = 0; i < 8; ++i) {
+            const int a = cb * 8 + i;
+            if (a < 2 * m) xh[(((size_t)a * m + kx) * B + b) * kC + c] = make_float2(v[2 * i], v[2 * i + 1]);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[acc]);
     }
   }
-#pragma unroll
-  for (int q = 0; q < kMaxA; ++q) {
-    const int a = g0 + q * kGroups;
-    if (a < 2 * m) xh[a * kC + c] = make_float2(re[q], im[q]);
-  }
+  tc_fence_before();
   __syncthreads();
-  const int o = threadIdx.x % kC;
-  for (int a = g0; a < 2 * m; a += kGroups) {
-    const float2* r = rt + ((size_t)(a * m + kx) * kC) * kC + o;
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, 128);
+}
+
+// ----------------------------------------- 3. per-mode channel mixing (CUDA cores)
+// Y[b][a][kx][o] = sum_c Xh[a * m + kx][b][c] R[a * m + kx][c][o]; one block per (mode,
+// batch chunk).  Y is written as the K-major B operand of the inverse y-DFT:
+// Yb[b][a/4][n][(a%4) * 2 + p] with n = n(k', o) and, for k' = kx (real part of the
+// inverse) (Re Y, -Im Y), for k' = m + kx (imaginary part) (Im Y, Re Y).
+constexpr int kMixB = 32;
+template <int kC>
+__global__ void __launch_bounds__(256)
+    k_mix(const float2* __restrict__ xh, const float2* __restrict__ rt,
+          __nv_bfloat16* __restrict__ yb, int B, int m) {
+  const SpecDims d = spec_dims(kC, m);
+  extern __shared__ float2 mix_s[];
+  float2* r_s = mix_s;             // [c][o]
+  float2* x_s = mix_s + kC * kC;   // [b][c]
+  const int md = blockIdx.x;
+  const int b0 = blockIdx.y * kMixB, nb = min(kMixB, B - b0);
+  for (int t = threadIdx.x; t < kC * kC; t += blockDim.x) r_s[t] = rt[(size_t)md * kC * kC + t];
+  for (int t = threadIdx.x; t < nb * kC; t += blockDim.x)
+    x_s[t] = xh[((size_t)md * B + b0) * kC + t];
+  __syncthreads();
+  const int a = md / m, kx = md - a * m;
+  auto ncol = [&](int kp, int o) { return (kp / d.knk) * d.nchunk + o * d.knk + kp % d.knk; };
+  for (int e = threadIdx.x; e < nb * kC; e += blockDim.x) {
+    const int bl = e / kC, o = e - bl * kC;
     float re = 0.f, im = 0.f;
 #pragma unroll 8
     for (int i = 0; i < kC; ++i) {
-      const float2 xv = xh[a * kC + i];
-      const float2 w = r[(size_t)i * kC];
+      const float2 xv = x_s[bl * kC + i];
+      const float2 w = r_s[i * kC + o];
       re = fmaf(xv.x, w.x, fmaf(-xv.y, w.y, re));
       im = fmaf(xv.x, w.y, fmaf(xv.y, w.x, im));
     }
-    yh[(((size_t)b * 2 * m + a) * m + kx) * kC + o] = make_float2(re, im);
+    uint32_t* base = reinterpret_cast<uint32_t*>(yb) +
+                     ((size_t)(b0 + bl) * d.kg + a / 4) * d.nn * 4 + (a % 4);
+    const __nv_bfloat162 lo = __floats2bfloat162_rn(re, -im);
+    const __nv_bfloat162 hi = __floats2bfloat162_rn(im, re);
+    base[(size_t)ncol(kx, o) * 4] = *reinterpret_cast<const uint32_t*>(&lo);
+    base[(size_t)ncol(m + kx, o) * 4] = *reinterpret_cast<const uint32_t*>(&hi);
   }
 }
 
-// ------------------------------------------------ 3. inverse y-DFT (CUDA cores)
-// One block per (b, block of kSpecRows rows).  Zt[b][y][k'/8][o][k'%8] (bf16):
-// k' < m: Re Z(kx = k'), m <= k' < 2m: Im Z(kx = k' - m), else 0, with
-// Z[kx][o] = sum_a Yh[b][a][kx][o] e^{+2 pi i ky(a) y / H}.  The block stages Yh[b]
-// and the e^{+i phi} factors of its rows in shared memory; each thread forms
-// complete complex sums and writes both halves.
-constexpr int kSpecRows = 16;
+// ---------------------------------------------- 3b. inverse y-DFT (tcgen05)
+// Zt[b][y][k'/8][o][k'%8] (bf16) = D[y][n(k', o)] = Ty[y][(a, re|im)] * Yb[(a, re|im)][n]:
+// k' < m gives Re Z(kx = k'), m <= k' < 2m gives Im Z(kx = k' - m) with
+// Z[kx][o] = sum_a Y[a][kx][o] e^{+2 pi i ky(a) y / H}; k' in [2m, 32) is written as 0.
+// One tile = (b, 128 rows, one chunk of knk k'); M = 128, N = knk * C, K = nf.
+constexpr int kIyStages = 4;
+constexpr int kIyMinSmem = 120 * 1024;  // one CTA per SM: the accumulators fill the TMEM
+
 template <int kC>
-__global__ void __launch_bounds__(256)
-    k_spec_inv(const float2* __restrict__ yh, __nv_bfloat16* __restrict__ zt,
-               const float2* __restrict__ twy, int H, int m) {
-  extern __shared__ float2 sm2[];
-  float2* ys = sm2;                              // 2m * m * kC
-  float2* ph = ys + (size_t)2 * m * m * kC;      // kSpecRows * 2m factors
-  const int nblk = (H + kSpecRows - 1) / kSpecRows;
-  const int b = blockIdx.x / nblk, y0 = (blockIdx.x - b * nblk) * kSpecRows;
-  const int n = 2 * m * m * kC;
-  stage_ilp<8>(ys, n, [&](int t) { return yh[(size_t)b * n + t]; });
-  for (int t = threadIdx.x; t < kSpecRows * 2 * m; t += blockDim.x) {
-    const int rr = t / (2 * m), a = t - rr * 2 * m;
-    const int y = min(y0 + rr, H - 1);
-    ph[t] = twy[(int)(((long long)kept_ky_tc(a, H, m) * y) % H)];
-  }
-  __syncthreads();
-  constexpr int kRow = 32 * kC;  // bf16 entries of one Zt row (k' padded to 32)
-  // zero the padding k' in [2m, 32) of this block's rows
-  for (int e = threadIdx.x; e < kSpecRows * kRow; e += blockDim.x) {
-    const int rr = e / kRow, q = e - rr * kRow;
-    const int kp = (q / (kC * 8)) * 8 + (q % 8);
-    if (y0 + rr < H && kp >= 2 * m) zt[((size_t)b * H + y0 + rr) * kRow + q] = __float2bfloat16_rn(0.0f);
-  }
-  for (int e = threadIdx.x; e < m * kC; e += blockDim.x) {
-    const int kx = e / kC, o = e - kx * kC;
-    float re[kSpecRows], im[kSpecRows];
-#pragma unroll
-    for (int rr = 0; rr < kSpecRows; ++rr) {
-      re[rr] = 0.f;
-      im[rr] = 0.f;
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_iydft_tc(const __nv_bfloat16* __restrict__ ty, const __nv_bfloat16* __restrict__ yb,
+               __nv_bfloat16* __restrict__ zt, int B, int H, int m,
+               unsigned* __restrict__ status) {
+  constexpr int kKnk = kC <= 32 ? 8 : 4;
+  constexpr int kN = kKnk * kC;  // accumulator columns per tile (128 or 256)
+  const SpecDims d = spec_dims(kC, m);
+  const int hp = (H + 127) / 128 * 128;
+  const int yt_n = hp / 128;
+  const int ntiles = B * yt_n * d.nc;
+  const int a_bytes = d.kg * 2048, b_bytes = d.kg * kN * 16;
+  const int stage_bytes = a_bytes + b_bytes;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full_bar[kIyStages], empty_bar[kIyStages];
+  __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
+  __shared__ uint32_t tmem_base;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kIyStages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
     }
-    for (int a = 0; a < 2 * m; ++a) {
-      const float2 w = ys[((size_t)a * m + kx) * kC + o];
-#pragma unroll
-      for (int rr = 0; rr < kSpecRows; ++rr) {
-        const float2 e2 = ph[rr * 2 * m + a];  // e^{+i phi}, broadcast
-        re[rr] = fmaf(w.x, e2.x, fmaf(-w.y, e2.y, re[rr]));
-        im[rr] = fmaf(w.x, e2.y, fmaf(w.y, e2.x, im[rr]));
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], 4);
+    }
+    mbar_init_fence();
+  }
+  if (warp == 0) tmem_alloc(&tmem_base, 2 * kN);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 4) {
+    // ------------------------------------------------------------ producer
+    int k = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+      const int s = k % kIyStages;
+      if (k >= kIyStages) ok = mbar_wait(&empty_bar[s], ((k / kIyStages) - 1) & 1, status);
+      if (!ok) break;
+      const int b = t / (yt_n * d.nc), rem = t - b * yt_n * d.nc;
+      const int yt = rem / d.nc, ci = rem - yt * d.nc;
+      unsigned char* st = smem + (size_t)s * stage_bytes;
+      if (lane == 0) mbar_arrive_expect_tx(&full_bar[s], (unsigned)stage_bytes);
+      __syncwarp();
+      for (int q = lane; q < 2 * d.kg; q += 32) {
+        if (q < d.kg)
+          bulk_g2s(st + q * 2048, ty + ((size_t)q * hp + yt * 128) * 8, 2048, &full_bar[s]);
+        else
+          bulk_g2s(st + a_bytes + (q - d.kg) * kN * 16,
+                   yb + (((size_t)b * d.kg + (q - d.kg)) * d.nn + (size_t)ci * kN) * 8,
+                   (unsigned)(kN * 16), &full_bar[s]);
       }
     }
-    const int kr = kx, ki = m + kx;
+    for (int q = max(0, k - kIyStages); q < k; ++q)
+      mbar_wait(&full_bar[q % kIyStages], (q / kIyStages) & 1, status);
+  } else if (warp == 5) {
+    // ---------------------------------------------------------------- MMA
+    constexpr uint32_t idesc = idesc_bf16(128, kN, false, false);
+    int j = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+      const int acc = j & 1;
+      if (j >= 2) ok = mbar_wait(&acc_empty[acc], ((j >> 1) - 1) & 1, status);
+      if (ok) ok = mbar_wait(&full_bar[j % kIyStages], (j / kIyStages) & 1, status);
+      if (!ok) break;
+      tc_fence_after();
+      if (lane == 0) {
+        const unsigned char* st = smem + (size_t)(j % kIyStages) * stage_bytes;
+        for (int kk = 0; kk < d.kg / 2; ++kk) {
+          const uint64_t ad = smem_desc(st + kk * 4096, 2048, 128);
+          const uint64_t bd = smem_desc(st + a_bytes + kk * 2 * kN * 16, kN * 16, 128);
+          mma_bf16(tmem + acc * kN, ad, bd, idesc, kk > 0);
+        }
+        mma_commit(&empty_bar[j % kIyStages]);
+        mma_commit(&acc_full[acc]);
+      }
+      __syncwarp();
+    }
+  } else {
+    // ----------------------------------------------------------- epilogue
+    // 32 accumulator columns = 32 / knk channels o, each with knk consecutive k'
+    constexpr int kOpl = 32 / kKnk;
+    int j = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+      const int acc = j & 1;
+      if (!mbar_wait(&acc_full[acc], (j >> 1) & 1, status)) break;
+      tc_fence_after();
+      const int b = t / (yt_n * d.nc), rem = t - b * yt_n * d.nc;
+      const int yt = rem / d.nc, ci = rem - yt * d.nc;
+      const int y = yt * 128 + warp * 32 + lane;
+      const int kp0 = ci * kKnk;
+      __nv_bfloat16* zrow = zt + ((size_t)b * H + y) * 32 * kC + (kp0 / 8) * kC * 8 + (kp0 % 8);
+#pragma unroll 1
+      for (int cb = 0; cb < kN / 32; ++cb) {
+        float v[32];
+        tmem_ld32(tmem + acc * kN + cb * 32 + ((uint32_t)(warp * 32) << 16), v);
+        if (y < H) {
 #pragma unroll
-    for (int rr = 0; rr < kSpecRows; ++rr) {
-      const int y = y0 + rr;
-      if (y >= H) break;
-      __nv_bfloat16* row = zt + ((size_t)b * H + y) * kRow;
-      row[((kr / 8) * kC + o) * 8 + (kr % 8)] = __float2bfloat16_rn(re[rr]);
-      row[((ki / 8) * kC + o) * 8 + (ki % 8)] = __float2bfloat16_rn(im[rr]);
+          for (int oo = 0; oo < kOpl; ++oo) {
+            const int o = cb * kOpl + oo;
+            __align__(16) __nv_bfloat16 h[kKnk];
+#pragma unroll
+            for (int q = 0; q < kKnk; ++q) h[q] = __float2bfloat16_rn(v[oo * kKnk + q]);
+            if constexpr (kKnk == 8)
+              *reinterpret_cast<uint4*>(zrow + o * 8) = *reinterpret_cast<const uint4*>(h);
+            else
+              *reinterpret_cast<uint2*>(zrow + o * 8) = *reinterpret_cast<const uint2*>(h);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[acc]);
+      if (ci == d.nc - 1 && y < H) {  // k' in [nc * knk, 32): zero
+        __nv_bfloat16* zr = zt + ((size_t)b * H + y) * 32 * kC;
+        for (int kp = d.nc * kKnk; kp < 32; kp += kKnk)
+          for (int o = 0; o < kC; ++o) {
+            if constexpr (kKnk == 8)
+              *reinterpret_cast<uint4*>(zr + ((kp / 8) * kC + o) * 8) = make_uint4(0, 0, 0, 0);
+            else
+              *reinterpret_cast<uint2*>(zr + ((kp / 8) * kC + o) * 8 + kp % 8) = make_uint2(0, 0);
+          }
+      }
     }
   }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, 2 * kN);
 }
 
 // ------------------------ 4. inverse x-DFT + W theta + bias + activation (tcgen05)
@@ -763,18 +992,29 @@ __global__ void __launch_bounds__(kTcThreads, kDecCtasPerSm)
 }
 
 // ------------------------------------------------------------------- host
+// Shared memory of the y-DFT kernel: the Fy table plus the operand ring.
+static size_t ydft_smem(int C, int H, int m) {
+  const SpecDims d = spec_dims(C, m);
+  return align_up((size_t)(H / 4) * d.nf * 16, 1024) + (size_t)kYStages * kYStageBytes;
+}
+static size_t iydft_smem(int C, int m) {
+  const SpecDims d = spec_dims(C, m);
+  const size_t st = (size_t)d.kg * 2048 + (size_t)d.kg * d.nchunk * 16;
+  return std::max((size_t)kIyStages * st, (size_t)kIyMinSmem);
+}
+
 bool fno_tc_supported(const fno_config& c, int H, int W) {
-  const size_t C = c.width, m = c.modes;
-  const size_t spec_fwd = ((size_t)H * C + H + 2 * m * C) * sizeof(float2);
-  const size_t spec_inv = ((size_t)2 * m * m * C + 16 * 2 * m) * sizeof(float2);
-  return c.padding == 0 && (C == 16 || C == 32 || C == 64) && m <= 16 && 2 * m <= (size_t)H &&
-         W % 128 == 0 &&
-         W <= 2048 && c.c_in <= 16 && spec_fwd <= 200 * 1024 && spec_inv <= 200 * 1024;
+  const int C = c.width, m = c.modes;
+  if (c.padding != 0 || !(C == 16 || C == 32 || C == 64) || m < 1 || m > 16 || 2 * m > H ||
+      H % 8 != 0 || W % 128 != 0 || W > 2048 || c.c_in > 16)
+    return false;
+  return ydft_smem(C, H, m) <= 200 * 1024 && iydft_smem(C, m) <= 200 * 1024;
 }
 
 FnoTcWs fno_tc_ws_plan(const fno_config& c, int B, int H, int W) {
   FnoTcWs w{};
   const size_t C = c.width, m = c.modes;
+  const SpecDims d = spec_dims((int)C, (int)m);
   size_t p = 0;
   auto take = [&](size_t bytes) {
     const size_t a = p;
@@ -782,14 +1022,17 @@ FnoTcWs fno_tc_ws_plan(const fno_config& c, int B, int H, int W) {
     return a;
   };
   const size_t pix = (size_t)B * H * W;
+  const size_t hp = ((size_t)H + 127) / 128 * 128;
   w.theta0 = take(pix * C * 2);
   w.theta1 = take(pix * C * 2);
-  w.x1 = take((size_t)B * H * m * C * sizeof(float2));
-  w.yh = take((size_t)B * 2 * m * m * C * sizeof(float2));
+  w.x1b = take((size_t)B * H * m * C * 4);
+  w.xh = take((size_t)2 * m * m * B * C * sizeof(float2));
+  w.yb = take((size_t)B * d.kg * d.nn * 16);
   w.zt = take((size_t)B * H * 32 * C * 2);
   w.fw = take((size_t)W * 64);
   w.ti = take((size_t)W * 64);
-  w.twy = take((size_t)H * sizeof(float2));
+  w.fy = take((size_t)(H / 4) * d.nf * 16);
+  w.ty = take((size_t)d.kg * hp * 16);
   w.status = take(sizeof(unsigned));
   w.total = p;
   return w;
@@ -801,21 +1044,28 @@ static int fno_forward_tc_impl(const fno_config& c, const FnoTcParams& P, const 
   const FnoTcWs wp = fno_tc_ws_plan(c, B, H, W);
   __nv_bfloat16* th[2] = {reinterpret_cast<__nv_bfloat16*>(ws + wp.theta0),
                           reinterpret_cast<__nv_bfloat16*>(ws + wp.theta1)};
-  float2* x1 = reinterpret_cast<float2*>(ws + wp.x1);
-  float2* yh = reinterpret_cast<float2*>(ws + wp.yh);
+  __nv_bfloat16* x1b = reinterpret_cast<__nv_bfloat16*>(ws + wp.x1b);
+  float2* xh = reinterpret_cast<float2*>(ws + wp.xh);
+  __nv_bfloat16* yb = reinterpret_cast<__nv_bfloat16*>(ws + wp.yb);
   __nv_bfloat16* zt = reinterpret_cast<__nv_bfloat16*>(ws + wp.zt);
   __nv_bfloat16* fw = reinterpret_cast<__nv_bfloat16*>(ws + wp.fw);
   __nv_bfloat16* ti = reinterpret_cast<__nv_bfloat16*>(ws + wp.ti);
-  float2* twy = reinterpret_cast<float2*>(ws + wp.twy);
+  __nv_bfloat16* fy = reinterpret_cast<__nv_bfloat16*>(ws + wp.fy);
+  __nv_bfloat16* ty = reinterpret_cast<__nv_bfloat16*>(ws + wp.ty);
   unsigned* status = reinterpret_cast<unsigned*>(ws + wp.status);
   const int m = c.modes;
+  const SpecDims d = spec_dims(kC, m);
+  const int hp = (H + 127) / 128 * 128;
   int dev = 0, nsm = 0;
   LBM_CHECK_CUDA(cudaGetDevice(&dev));
   LBM_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   LBM_CHECK_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), s));
+  // padding entries of Yb (k' >= 2m, a >= 2m) are never written by the mixing kernel
+  LBM_CHECK_CUDA(cudaMemsetAsync(yb, 0, (size_t)B * d.kg * d.nn * 16, s));
   k_table_fwd<<<(W * 32 + 255) / 256, 256, 0, s>>>(fw, W, m);
   k_table_inv<<<(W * 32 + 255) / 256, 256, 0, s>>>(ti, H, W, m);
-  k_twiddle_tc<<<(H + 255) / 256, 256, 0, s>>>(twy, H);
+  k_table_fy<<<((H / 4) * d.nf * 8 + 255) / 256, 256, 0, s>>>(fy, H, m, d.nf);
+  k_table_ty<<<(d.kg * hp * 8 + 255) / 256, 256, 0, s>>>(ty, H, hp, m, d.kg);
   const size_t pix = (size_t)B * H * W;
   if (c.c_in == 4)
     k_lift_blk<kC, 4><<<(unsigned)((pix + 127) / 128), 128, 0, s>>>(
@@ -825,23 +1075,27 @@ static int fno_forward_tc_impl(const fno_config& c, const FnoTcParams& P, const 
         in, th[0], P.lift0_w, P.lift0_b, P.lift1_w, P.lift1_b, B, H, W, c.c_in, c.activation);
   LBM_CHECK_LAUNCH();
   const size_t fwd_smem = (size_t)W * 64 + (size_t)kFwdStages * kFwdStageBytes;
-  const size_t spec_fwd_smem = ((size_t)H * kC + H + 2 * m * kC) * sizeof(float2);
-  const size_t spec_inv_smem = ((size_t)2 * m * m * kC + kSpecRows * 2 * m) * sizeof(float2);
   constexpr int kStageBytesInv = (4 + kC / 8) * 128 * 16 + (4 + kC / 8) * kC * 16;
   const size_t inv_smem = (size_t)kInvStages * kStageBytesInv;
-  LBM_REQUIRE(spec_fwd_smem <= 200 * 1024 && spec_inv_smem <= 200 * 1024,
+  const size_t y_smem = ydft_smem(kC, H, m), iy_smem = iydft_smem(kC, m);
+  const size_t mix_smem = (size_t)(kC * kC + kMixB * kC) * sizeof(float2);
+  LBM_REQUIRE(y_smem <= 200 * 1024 && iy_smem <= 200 * 1024,
               "fno_forward: spectral working set too large for shared memory");
   const int ytiles = (H + (128 / kC) - 1) / (128 / kC);
   const int fwd_ctas = std::min(B * ytiles, 2 * nsm);
   const int inv_ctas = std::min(B * H * (W / 128), 2 * nsm);
+  const int ydft_ctas = std::min(B * ((m * kC + 127) / 128), 2 * nsm);
+  const int iydft_ctas = std::min(B * (hp / 128) * d.nc, nsm);
+  const dim3 mix_grid((unsigned)(2 * m * m), (unsigned)((B + kMixB - 1) / kMixB));
   int cur = 0;
   for (int n = 0; n < c.layers; ++n) {
-    k_fwd_x_tc<kC><<<fwd_ctas, kTcThreads, fwd_smem, s>>>(th[cur], fw, x1, B, H, W, m, status);
+    k_fwd_x_tc<kC><<<fwd_ctas, kTcThreads, fwd_smem, s>>>(th[cur], fw, x1b, B, H, W, m, status);
     LBM_CHECK_LAUNCH();
-    k_spec_fwd<kC><<<B * m, 256, spec_fwd_smem, s>>>(x1, P.rt[n], yh, twy, H, m);
+    k_ydft_tc<kC><<<ydft_ctas, kTcThreads, y_smem, s>>>(x1b, fy, xh, B, H, m, status);
     LBM_CHECK_LAUNCH();
-    k_spec_inv<kC><<<B * ((H + kSpecRows - 1) / kSpecRows), 256, spec_inv_smem, s>>>(yh, zt, twy,
-                                                                                     H, m);
+    k_mix<kC><<<mix_grid, 256, mix_smem, s>>>(xh, P.rt[n], yb, B, m);
+    LBM_CHECK_LAUNCH();
+    k_iydft_tc<kC><<<iydft_ctas, kTcThreads, iy_smem, s>>>(ty, yb, zt, B, H, m, status);
     LBM_CHECK_LAUNCH();
     k_inv_x_tc<kC><<<inv_ctas, kInvThreads, inv_smem, s>>>(th[cur], ti, zt, P.w[n], P.b[n],
                                                           th[cur ^ 1], B, H, W, c.activation,
@@ -871,8 +1125,9 @@ static int tc_set_smem_attrs() {
   const int big = 200 * 1024;
   LBM_CHECK_CUDA(cudaFuncSetAttribute(k_fwd_x_tc<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   LBM_CHECK_CUDA(cudaFuncSetAttribute(k_inv_x_tc<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_spec_fwd<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_spec_inv<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_ydft_tc<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_iydft_tc<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_mix<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   LBM_CHECK_CUDA(cudaFuncSetAttribute(k_decoder_tc<kC, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   return LBM_OK;
 }

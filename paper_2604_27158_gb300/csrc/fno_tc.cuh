@@ -7,7 +7,7 @@ namespace lbmfno {
 
 // Workspace layout of the tensor-core path (byte offsets).
 struct FnoTcWs {
-  size_t theta0, theta1, x1, yh, zt, fw, ti, twy, status, total;
+  size_t theta0, theta1, x1b, xh, yb, zt, fw, ti, fy, ty, status, total;
 };
 
 // FP32 parameters of one FNO, already repacked on the device.
