@@ -321,7 +321,8 @@ int fno_forward(fno_handle* h, const float* in_d, float* out_d, int B, int H, in
 int fno_get_config(const fno_handle* h, fno_config* out_h);
 
 /* Kernel path.  FNO_PATH_AUTO (default): tcgen05 tensor-core kernels where the
- * shape allows (C in {16, 32, 64}, m <= 16, W a multiple of 128, W <= 2048, no padding),
+ * shape allows (C in {16, 32, 64}, m <= 16, H a multiple of 8, W a multiple of 128,
+ * W <= 2048, no padding),
  * CUDA-core kernels otherwise.  FNO_PATH_CUDA_CORES: always the CUDA-core
  * kernels (same results up to rounding). */
 enum fno_path { FNO_PATH_AUTO = 0, FNO_PATH_CUDA_CORES = 1 };
@@ -331,6 +332,12 @@ int fno_uses_tensor_cores(const fno_handle* h, int H, int W, int* out_h);
 /* Synchronise `stream` and report a device-side wait that expired during the
  * last fno_forward(B, H, W) on workspace ws_d (LBM_ERR_TIMEOUT), else LBM_OK. */
 int fno_check(const fno_handle* h, const void* ws_d, int B, int H, int W, void* stream);
+/* The activation between Fourier layers (Sec. 2.2; GELU or ReLU) exactly as the
+ * tensor-core kernels evaluate it, applied element-wise: y_d[i] = act(x_d[i]) for
+ * i < n, on `stream` (asynchronous).  x_d, y_d: caller-owned device FP32 arrays (may
+ * alias).  GELU is within 2e-7 (1 + |x|) of the exact x Phi(x).  For tests; returns
+ * LBM_ERR_INVALID_ARG for an unknown act or a null buffer with n > 0. */
+int fno_activation_eval(int act, const float* x_d, float* y_d, size_t n, void* stream);
 
 int fno_destroy(fno_handle* h);
 

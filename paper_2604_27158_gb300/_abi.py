@@ -110,6 +110,7 @@ _PROTOS = {
     "fno_set_path": ([VP, I], I),
     "fno_uses_tensor_cores": ([VP, I, I, ctypes.POINTER(I)], I),
     "fno_check": ([VP, VP, I, I, I, VP], I),
+    "fno_activation_eval": ([I, VP, VP, ctypes.c_size_t, VP], I),
     "fno_destroy": ([VP], I),
     "fno_train_query": ([ctypes.POINTER(fno_config), I, I, I, ctypes.POINTER(fno_train_sizes)], I),
     "fno_train_forward": ([ctypes.POINTER(fno_config), VP, VP, VP, I, I, I, VP, VP, VP], I),

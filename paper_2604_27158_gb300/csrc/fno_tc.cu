@@ -31,12 +31,30 @@
 
 #include "common.cuh"
 #include "fno_tc.cuh"
+#include "gelu_poly.cuh"
 #include "sm100.cuh"
 
 namespace lbmfno {
 
+// GELU(v) = v Phi(v) = max(v, 0) - a Q(a) with a = |v| and Q(a) = Phi(-a) =
+// exp(-a^2 / 2) S(a), S(a) = erfcx(a / sqrt 2) / 2 evaluated as a degree-10 polynomial in
+// u = a / 3 - 1 (gelu_poly.cuh, fitted by gelu_fit.py on a in [0, 6]); a is clamped to 6,
+// beyond which a Q(a) < 7e-9.  Absolute error within 2e-7 (1 + |v|) of the exact GELU,
+// NaN propagates, GELU(+inf) = +inf.  max(v, 0) is written 0.5 (v + |v|) so that a NaN
+// input is not turned into 0.
+__device__ __forceinline__ float gelu_tc(float v) {
+  constexpr float c[GELU_S_DEG + 1] = GELU_S_COEFFS;
+  const float a = fminf(fabsf(v), 6.0f);
+  const float u = fmaf(a, 1.0f / 3.0f, -1.0f);
+  float p = c[GELU_S_DEG];
+#pragma unroll
+  for (int k = GELU_S_DEG - 1; k >= 0; --k) p = fmaf(p, u, c[k]);
+  float e;  // exp(-a^2 / 2) = 2^(-a^2 log2(e) / 2)
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(a * a * -0.72134752044448170f));
+  return fmaf(-a, e * p, 0.5f * (v + fabsf(v)));
+}
 __device__ __forceinline__ float act_tc(float v, int act) {
-  return act == FNO_ACT_GELU ? 0.5f * v * (1.0f + erff(v * 0.70710678118654752f)) : fmaxf(v, 0.0f);
+  return act == FNO_ACT_GELU ? gelu_tc(v) : fmaxf(v, 0.0f);
 }
 __device__ __forceinline__ int kept_ky_tc(int a, int H, int m) { return a < m ? a : H - 2 * m + a; }
 
@@ -1153,4 +1171,23 @@ int fno_forward_tc(const fno_config& c, const FnoTcParams& P, const float* in, f
   }
 }
 
+// Element-wise activation of the tensor-core kernels, for tests.
+__global__ void k_act_eval(const float* __restrict__ x, float* __restrict__ y, size_t n, int act) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    y[i] = act_tc(x[i], act);
+}
+
 }  // namespace lbmfno
+
+using namespace lbmfno;
+
+extern "C" int fno_activation_eval(int act, const float* x_d, float* y_d, size_t n, void* stream) {
+  LBM_REQUIRE(act == FNO_ACT_GELU || act == FNO_ACT_RELU, "fno_activation_eval: unknown activation");
+  LBM_REQUIRE(n == 0 || (x_d != nullptr && y_d != nullptr), "fno_activation_eval: null buffer");
+  if (n == 0) return LBM_OK;
+  const unsigned grid = (unsigned)std::min<size_t>((n + 255) / 256, 4096);
+  k_act_eval<<<grid, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(x_d, y_d, n, act);
+  LBM_CHECK_LAUNCH();
+  return LBM_OK;
+}

@@ -110,6 +110,16 @@ class Fno:
             pass
 
 
+def activation(x: torch.Tensor, act: int = _abi.FNO_ACT_GELU) -> torch.Tensor:
+    """The activation exactly as the tensor-core FNO kernels evaluate it (element-wise,
+    FP32, on the device)."""
+    assert x.dtype == torch.float32 and x.is_cuda
+    x = x.contiguous()
+    y = torch.empty_like(x)
+    call("fno_activation_eval", int(act), x.data_ptr(), y.data_ptr(), x.numel(), _stream_ptr(None))
+    return y
+
+
 @dataclasses.dataclass
 class HybridConfig:
     """Fields of struct hybrid_config."""

@@ -111,6 +111,27 @@ def test_invalid_fno_shapes_rejected():
         net(torch.zeros((1, 4, 16, 8), device="cuda"))  # m >= W/2
 
 
+def test_tensor_core_activation_matches_exact_gelu():
+    """The tensor-core kernels' GELU (Gaussian-tail polynomial times exp) against the exact
+    v Phi(v) in FP64 (math.erf) on a dense grid, its tails, and special values."""
+    _requires_gpu()
+    import math
+    from paper_2604_27158_gb300.fno import activation
+    v = np.concatenate([np.linspace(-12.0, 12.0, 2_000_001), np.linspace(-1e-3, 1e-3, 20001),
+                        [-50.0, -7.0, -6.0, 6.0, 7.0, 50.0, 1e20, -1e20]]).astype(np.float32)
+    got = activation(torch.from_numpy(v).cuda()).cpu().numpy().astype(np.float64)
+    vd = v.astype(np.float64)
+    ref = np.array([0.5 * x * (1.0 + math.erf(x / math.sqrt(2.0))) for x in vd.tolist()])
+    err = np.abs(got - ref) / (1.0 + np.abs(vd))
+    print(f"GELU: max |err| / (1 + |v|) = {err.max():.2e}")
+    assert err.max() < 2e-7
+    special = torch.tensor([float("nan"), float("inf"), 0.0, -0.0], device="cuda")
+    out = activation(special).cpu().numpy()
+    assert np.isnan(out[0]) and out[1] == np.inf and out[2] == 0.0 and out[3] == 0.0
+    relu = activation(torch.from_numpy(v).cuda(), P._abi.FNO_ACT_RELU).cpu().numpy()
+    np.testing.assert_array_equal(relu, np.maximum(v, 0.0))
+
+
 @pytest.mark.parametrize("H,W,width", [(32, 128, 32), (64, 256, 32), (40, 128, 16), (32, 128, 64)])
 def test_tensor_core_path_matches_oracle(H, W, width):
     """tcgen05 path (channel-blocked latents, DFT and 1x1 layers as MMAs) vs the FP64 oracle."""
