@@ -56,6 +56,30 @@ __device__ __forceinline__ float gelu_tc(float v) {
 __device__ __forceinline__ float act_tc(float v, int act) {
   return act == FNO_ACT_GELU ? gelu_tc(v) : fmaxf(v, 0.0f);
 }
+template <int kAct>
+__device__ __forceinline__ float act_c(float v) {
+  return kAct == FNO_ACT_GELU ? gelu_tc(v) : fmaxf(v, 0.0f);
+}
+// Two activations at once with packed FP32 arithmetic: the same operations in the same
+// order as gelu_tc, so each lane's result is identical to gelu_tc's.
+__device__ __forceinline__ float2 gelu_tc2(float2 v) {
+  constexpr float c[GELU_S_DEG + 1] = GELU_S_COEFFS;
+  const float2 a = make_float2(fminf(fabsf(v.x), 6.0f), fminf(fabsf(v.y), 6.0f));
+  const float2 u = __ffma2_rn(a, make_float2(1.0f / 3.0f, 1.0f / 3.0f), make_float2(-1.0f, -1.0f));
+  float2 p = make_float2(c[GELU_S_DEG], c[GELU_S_DEG]);
+#pragma unroll
+  for (int k = GELU_S_DEG - 1; k >= 0; --k) p = __ffma2_rn(p, u, make_float2(c[k], c[k]));
+  const float2 t = __fmul2_rn(__fmul2_rn(a, a), make_float2(-0.72134752044448170f, -0.72134752044448170f));
+  float2 e;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.x) : "f"(t.x));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.y) : "f"(t.y));
+  const float2 h = __fmul2_rn(__fadd2_rn(v, make_float2(fabsf(v.x), fabsf(v.y))), make_float2(0.5f, 0.5f));
+  return __ffma2_rn(make_float2(-a.x, -a.y), __fmul2_rn(e, p), h);
+}
+template <int kAct>
+__device__ __forceinline__ float2 act_c2(float2 v) {
+  return kAct == FNO_ACT_GELU ? gelu_tc2(v) : make_float2(fmaxf(v.x, 0.0f), fmaxf(v.y, 0.0f));
+}
 __device__ __forceinline__ int kept_ky_tc(int a, int H, int m) { return a < m ? a : H - 2 * m + a; }
 
 // ------------------------------------------------------------------ tables
@@ -145,62 +169,91 @@ __global__ void k_table_ty(__nv_bfloat16* __restrict__ ty, int H, int hp, int m,
 }
 
 // ---------------------------------------------------- lifting / projection
-// Lifting network P (1x1, (c_in + 2) -> C/2 -> act -> C); one thread per pixel,
-// weights staged in shared memory (broadcast reads).
-template <int kC, int kCin>
+// Lifting network P (1x1, (c_in + 2) -> C/2 -> act -> C); each thread lifts two
+// neighbouring pixels (x, x + 1) so that every weight read from shared memory (a
+// broadcast) feeds two FMAs.  W is even.
+template <int kC, int kCin, int kAct>
 __global__ void __launch_bounds__(128)
     k_lift_blk(const float* __restrict__ in, __nv_bfloat16* __restrict__ theta,
                const float* __restrict__ w0, const float* __restrict__ b0,
                const float* __restrict__ w1, const float* __restrict__ b1, int B, int H, int W,
-               int cin_rt, int act) {
+               int cin_rt) {
   // kCin > 0: compile-time input channel count (registers); 0: runtime count
+  constexpr int kX = kCin > 0 ? kCin + 2 : 18;
+  constexpr int kHid = kC / 2;
   const int cin = kCin > 0 ? kCin : cin_rt;
-  __shared__ float s_w0[(kC / 2) * 18], s_b0[kC / 2], s_w1[kC * (kC / 2)], s_b1[kC];
+  __shared__ float s_w0[kHid * 18], s_b0[kHid], s_b1[kC];
+  __shared__ __align__(16) float s_w1[kC * kHid];
   const int cin2 = cin + 2;
-  for (int t = threadIdx.x; t < (kC / 2) * cin2; t += blockDim.x) s_w0[t] = w0[t];
-  for (int t = threadIdx.x; t < kC / 2; t += blockDim.x) s_b0[t] = b0[t];
-  for (int t = threadIdx.x; t < kC * (kC / 2); t += blockDim.x) s_w1[t] = w1[t];
+  for (int t = threadIdx.x; t < kHid * cin2; t += blockDim.x) s_w0[t] = w0[t];
+  for (int t = threadIdx.x; t < kHid; t += blockDim.x) s_b0[t] = b0[t];
+  for (int t = threadIdx.x; t < kC * kHid; t += blockDim.x) s_w1[t] = w1[t];
   for (int t = threadIdx.x; t < kC; t += blockDim.x) s_b1[t] = b1[t];
   __syncthreads();
-  const size_t pix = (size_t)B * H * W;
-  const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (p >= pix) return;
+  const size_t pairs = (size_t)B * H * W / 2;
+  const size_t pp = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (pp >= pairs) return;
+  const size_t p = 2 * pp;
   const int x = (int)(p % W);
   const size_t row = p / W;  // b * H + y
   const int y = (int)(row % H);
   const int b = (int)(row / H);
-  float xin[kCin > 0 ? kCin + 2 : 18];
+  float xin[2][kX];
 #pragma unroll
   for (int c = 0; c < (kCin > 0 ? kCin : 16); ++c)
-    if (c < cin)
-      xin[c] = __bfloat162float(__float2bfloat16_rn(in[(((size_t)b * cin + c) * H + y) * W + x]));
-  xin[cin] = __bfloat162float(__float2bfloat16_rn((float)x / (float)max(W - 1, 1)));
-  xin[cin + 1] = __bfloat162float(__float2bfloat16_rn((float)y / (float)max(H - 1, 1)));
-  float hid[kC / 2];
+    if (c < cin) {
+      const float* src = in + (((size_t)b * cin + c) * H + y) * W + x;  // 4-byte aligned only
+      xin[0][c] = __bfloat162float(__float2bfloat16_rn(src[0]));
+      xin[1][c] = __bfloat162float(__float2bfloat16_rn(src[1]));
+    }
+  const float gy = __bfloat162float(__float2bfloat16_rn((float)y / (float)max(H - 1, 1)));
 #pragma unroll
-  for (int j = 0; j < kC / 2; ++j) {
-    float a = s_b0[j];
+  for (int q = 0; q < 2; ++q) {
+    xin[q][cin] = __bfloat162float(__float2bfloat16_rn((float)(x + q) / (float)max(W - 1, 1)));
+    xin[q][cin + 1] = gy;
+  }
+  float hid[2][kHid];
 #pragma unroll
-    for (int c = 0; c < (kCin > 0 ? kCin + 2 : 18); ++c)
-      if (c < cin2) a = fmaf(s_w0[j * cin2 + c], xin[c], a);
-    hid[j] = act_tc(a, act);
+  for (int j = 0; j < kHid; ++j) {
+    float a0 = s_b0[j], a1 = a0;
+#pragma unroll
+    for (int c = 0; c < kX; ++c)
+      if (c < cin2) {
+        const float w = s_w0[j * cin2 + c];
+        a0 = fmaf(w, xin[0][c], a0);
+        a1 = fmaf(w, xin[1][c], a1);
+      }
+    const float2 h2 = act_c2<kAct>(make_float2(a0, a1));
+    hid[0][j] = h2.x;
+    hid[1][j] = h2.y;
   }
 #pragma unroll
   for (int g = 0; g < kC / 8; ++g) {
-    __align__(16) __nv_bfloat16 o8[8];
+    __align__(16) __nv_bfloat16 o8[2][8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int o = g * 8 + q;
-      float a = s_b1[o];
+      float a0 = s_b1[o], a1 = a0;
 #pragma unroll
-      for (int j = 0; j < kC / 2; ++j) a = fmaf(s_w1[o * (kC / 2) + j], hid[j], a);
-      o8[q] = __float2bfloat16_rn(a);
+      for (int j = 0; j < kHid; j += 4) {
+        const float4 w = *reinterpret_cast<const float4*>(&s_w1[o * kHid + j]);
+        a0 = fmaf(w.x, hid[0][j], a0);
+        a1 = fmaf(w.x, hid[1][j], a1);
+        a0 = fmaf(w.y, hid[0][j + 1], a0);
+        a1 = fmaf(w.y, hid[1][j + 1], a1);
+        a0 = fmaf(w.z, hid[0][j + 2], a0);
+        a1 = fmaf(w.z, hid[1][j + 2], a1);
+        a0 = fmaf(w.w, hid[0][j + 3], a0);
+        a1 = fmaf(w.w, hid[1][j + 3], a1);
+      }
+      o8[0][q] = __float2bfloat16_rn(a0);
+      o8[1][q] = __float2bfloat16_rn(a1);
     }
-    *reinterpret_cast<uint4*>(theta + ((row * (kC / 8) + g) * W + x) * 8) =
-        *reinterpret_cast<const uint4*>(o8);
+    uint4* dst = reinterpret_cast<uint4*>(theta + ((row * (kC / 8) + g) * W + x) * 8);
+    dst[0] = *reinterpret_cast<const uint4*>(o8[0]);
+    dst[1] = *reinterpret_cast<const uint4*>(o8[1]);
   }
 }
-
 // Projection Q from the channel-blocked field, any decoder shape (the common shape
 // runs in k_decoder_tc); one thread per pixel, decoder weights staged in shared memory.
 template <int kC>
@@ -320,7 +373,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int rows = min(kRows, H - y0);
       for (int ch = 0; ch < nchunks; ++ch, ++k) {
         const int s = k % kFwdStages;
-        if (k >= kFwdStages) ok = mbar_wait(&empty_bar[s], ((k / kFwdStages) - 1) & 1, status);
+        if (k >= kFwdStages) ok = mbar_wait_sleep(&empty_bar[s], ((k / kFwdStages) - 1) & 1, status);
         if (!ok) break;
         unsigned char* st = stages + (size_t)s * kFwdStageBytes;
         if (lane == 0) mbar_arrive_expect_tx(&full_bar[s], (unsigned)(rows * kG * kFwdChunk * 16));
@@ -334,22 +387,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
     }
     // no copy may still be in flight when the CTA exits
-    mbar_wait(&fw_bar, 0, status);
+    mbar_wait_sleep(&fw_bar, 0, status);
     for (int q = max(0, k - kFwdStages); q < k; ++q)
-      mbar_wait(&full_bar[q % kFwdStages], (q / kFwdStages) & 1, status);
+      mbar_wait_sleep(&full_bar[q % kFwdStages], (q / kFwdStages) & 1, status);
   } else if (warp == 5) {
     // ---------------------------------------------------------------- MMA
     constexpr uint32_t idesc = idesc_bf16(128, 32, /*a_mn=*/true, /*b_mn=*/false);
-    bool ok = mbar_wait(&fw_bar, 0, status);
+    bool ok = mbar_wait_sleep(&fw_bar, 0, status);
     int k = 0, j = 0;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++j) {
       const int acc = j & 1;
-      if (j >= 2) ok = mbar_wait(&acc_empty[acc], ((j >> 1) - 1) & 1, status);
+      if (j >= 2) ok = mbar_wait_sleep(&acc_empty[acc], ((j >> 1) - 1) & 1, status);
       if (!ok) break;
       tc_fence_after();
       for (int ch = 0; ch < nchunks; ++ch, ++k) {
         const int s = k % kFwdStages;
-        ok = mbar_wait(&full_bar[s], (k / kFwdStages) & 1, status);
+        ok = mbar_wait_sleep(&full_bar[s], (k / kFwdStages) & 1, status);
         if (!ok) break;
         tc_fence_after();
         if (lane == 0) {
@@ -375,7 +428,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     int j = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
       const int acc = j & 1;
-      if (!mbar_wait(&acc_full[acc], (j >> 1) & 1, status)) break;
+      if (!mbar_wait_sleep(&acc_full[acc], (j >> 1) & 1, status)) break;
       tc_fence_after();
       float v[32];
       tmem_ld32(tmem + acc * 32 + ((uint32_t)(warp * 32) << 16), v);
@@ -464,7 +517,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int nv = min(128, rows - m0);
       for (int ch = 0; ch < nchunks; ++ch, ++k) {
         const int s = k % kYStages;
-        if (k >= kYStages) ok = mbar_wait(&empty_bar[s], ((k / kYStages) - 1) & 1, status);
+        if (k >= kYStages) ok = mbar_wait_sleep(&empty_bar[s], ((k / kYStages) - 1) & 1, status);
         if (!ok) break;
         const int g0 = ch * kYChunk, gn = min(kYChunk, ngroups - g0);
         unsigned char* st = stages + (size_t)s * kYStageBytes;
@@ -475,22 +528,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                    (unsigned)(nv * 16), &full_bar[s]);
       }
     }
-    mbar_wait(&fy_bar, 0, status);
+    mbar_wait_sleep(&fy_bar, 0, status);
     for (int q = max(0, k - kYStages); q < k; ++q)
-      mbar_wait(&full_bar[q % kYStages], (q / kYStages) & 1, status);
+      mbar_wait_sleep(&full_bar[q % kYStages], (q / kYStages) & 1, status);
   } else if (warp == 5) {
     // ---------------------------------------------------------------- MMA
     const uint32_t idesc = idesc_bf16(128, d.nf, false, false);
-    bool ok = mbar_wait(&fy_bar, 0, status);
+    bool ok = mbar_wait_sleep(&fy_bar, 0, status);
     int k = 0, j = 0;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++j) {
       const int acc = j & 1;
-      if (j >= 2) ok = mbar_wait(&acc_empty[acc], ((j >> 1) - 1) & 1, status);
+      if (j >= 2) ok = mbar_wait_sleep(&acc_empty[acc], ((j >> 1) - 1) & 1, status);
       if (!ok) break;
       tc_fence_after();
       for (int ch = 0; ch < nchunks; ++ch, ++k) {
         const int s = k % kYStages;
-        ok = mbar_wait(&full_bar[s], (k / kYStages) & 1, status);
+        ok = mbar_wait_sleep(&full_bar[s], (k / kYStages) & 1, status);
         if (!ok) break;
         tc_fence_after();
         if (lane == 0) {
@@ -514,7 +567,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     int j = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
       const int acc = j & 1;
-      if (!mbar_wait(&acc_full[acc], (j >> 1) & 1, status)) break;
+      if (!mbar_wait_sleep(&acc_full[acc], (j >> 1) & 1, status)) break;
       tc_fence_after();
       const int b = t / mt, row = (t - b * mt) * 128 + warp * 32 + lane;
       const int kx = row / kC, c = row - kx * kC;
@@ -631,7 +684,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
       const int s = k % kIyStages;
-      if (k >= kIyStages) ok = mbar_wait(&empty_bar[s], ((k / kIyStages) - 1) & 1, status);
+      if (k >= kIyStages) ok = mbar_wait_sleep(&empty_bar[s], ((k / kIyStages) - 1) & 1, status);
       if (!ok) break;
       const int b = t / (yt_n * d.nc), rem = t - b * yt_n * d.nc;
       const int yt = rem / d.nc, ci = rem - yt * d.nc;
@@ -648,7 +701,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
     }
     for (int q = max(0, k - kIyStages); q < k; ++q)
-      mbar_wait(&full_bar[q % kIyStages], (q / kIyStages) & 1, status);
+      mbar_wait_sleep(&full_bar[q % kIyStages], (q / kIyStages) & 1, status);
   } else if (warp == 5) {
     // ---------------------------------------------------------------- MMA
     constexpr uint32_t idesc = idesc_bf16(128, kN, false, false);
@@ -656,8 +709,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
       const int acc = j & 1;
-      if (j >= 2) ok = mbar_wait(&acc_empty[acc], ((j >> 1) - 1) & 1, status);
-      if (ok) ok = mbar_wait(&full_bar[j % kIyStages], (j / kIyStages) & 1, status);
+      if (j >= 2) ok = mbar_wait_sleep(&acc_empty[acc], ((j >> 1) - 1) & 1, status);
+      if (ok) ok = mbar_wait_sleep(&full_bar[j % kIyStages], (j / kIyStages) & 1, status);
       if (!ok) break;
       tc_fence_after();
       if (lane == 0) {
@@ -679,7 +732,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     int j = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
       const int acc = j & 1;
-      if (!mbar_wait(&acc_full[acc], (j >> 1) & 1, status)) break;
+      if (!mbar_wait_sleep(&acc_full[acc], (j >> 1) & 1, status)) break;
       tc_fence_after();
       const int b = t / (yt_n * d.nc), rem = t - b * yt_n * d.nc;
       const int yt = rem / d.nc, ci = rem - yt * d.nc;
@@ -726,16 +779,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }
 
 // ------------------------ 4. inverse x-DFT + W theta + bias + activation (tcgen05)
-constexpr int kInvStages = 4;
+constexpr int kInvStages = 3;
+// CTAs per SM: three for C <= 32 (their epilogue warps hide the activation's latency),
+// two for C = 64 (shared memory)
+template <int kC>
+constexpr int inv_ctas_per_sm() { return kC <= 32 ? 3 : 2; }
 constexpr int kInvEpiWarps = 8;  // two warps per TMEM lane quadrant, each half of the columns
 constexpr int kInvThreads = (kInvEpiWarps + 2) * 32;
 
-template <int kC>
-__global__ void __launch_bounds__(kInvThreads, 1)
+template <int kC, int kAct>
+__global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
     k_inv_x_tc(const __nv_bfloat16* __restrict__ theta, const __nv_bfloat16* __restrict__ ti,
                const __nv_bfloat16* __restrict__ zt, const float* __restrict__ wmat,
                const float* __restrict__ bias, __nv_bfloat16* __restrict__ out, int B, int H,
-               int W, int act, unsigned* __restrict__ status) {
+               int W, unsigned* __restrict__ status) {
   constexpr int kG = kC / 8;
   constexpr int kKG = 4 + kG;                 // K groups of 8: 4 spectral (k' < 32) + C channels
   constexpr int kABytes = kKG * 128 * 16;     // A: [k group][x (128)][8]
@@ -783,7 +840,7 @@ __global__ void __launch_bounds__(kInvThreads, 1)
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
       const int s = k % kInvStages;
-      if (k >= kInvStages) ok = mbar_wait(&empty_bar[s], ((k / kInvStages) - 1) & 1, status);
+      if (k >= kInvStages) ok = mbar_wait_sleep(&empty_bar[s], ((k / kInvStages) - 1) & 1, status);
       if (!ok) break;
       const int row = t / xt;  // b * H + y
       const int x0 = (t - row * xt) * 128;
@@ -801,7 +858,7 @@ __global__ void __launch_bounds__(kInvThreads, 1)
       }
     }
     for (int q = max(0, k - kInvStages); q < k; ++q)
-      mbar_wait(&full_bar[q % kInvStages], (q / kInvStages) & 1, status);
+      mbar_wait_sleep(&full_bar[q % kInvStages], (q / kInvStages) & 1, status);
   } else if (warp == kInvEpiWarps + 1) {
     // ---------------------------------------------------------------- MMA
     constexpr uint32_t idesc = idesc_bf16(128, kC, false, false);
@@ -809,8 +866,8 @@ __global__ void __launch_bounds__(kInvThreads, 1)
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
       const int acc = j & 1;
-      if (j >= 2) ok = mbar_wait(&acc_empty[acc], ((j >> 1) - 1) & 1, status);
-      if (ok) ok = mbar_wait(&full_bar[j % kInvStages], (j / kInvStages) & 1, status);
+      if (j >= 2) ok = mbar_wait_sleep(&acc_empty[acc], ((j >> 1) - 1) & 1, status);
+      if (ok) ok = mbar_wait_sleep(&full_bar[j % kInvStages], (j / kInvStages) & 1, status);
       if (!ok) break;
       tc_fence_after();
       if (lane == 0) {
@@ -834,7 +891,7 @@ __global__ void __launch_bounds__(kInvThreads, 1)
     int j = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
       const int acc = j & 1;
-      if (!mbar_wait(&acc_full[acc], (j >> 1) & 1, status)) break;
+      if (!mbar_wait_sleep(&acc_full[acc], (j >> 1) & 1, status)) break;
       tc_fence_after();
       float v[32];
       const uint32_t ta = tmem + acc * kAccCols + half * kHalf + ((uint32_t)(quad * 32) << 16);
@@ -850,8 +907,12 @@ __global__ void __launch_bounds__(kInvThreads, 1)
         const int o0 = half * kHalf + g * 8;
         __align__(16) __nv_bfloat16 o8[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-          o8[q] = __float2bfloat16_rn(act_tc(v[g * 8 + q] + bias_s[o0 + q], act));
+        for (int q = 0; q < 8; q += 2) {
+          const float2 r = act_c2<kAct>(make_float2(v[g * 8 + q] + bias_s[o0 + q],
+                                                    v[g * 8 + q + 1] + bias_s[o0 + q + 1]));
+          o8[q] = __float2bfloat16_rn(r.x);
+          o8[q + 1] = __float2bfloat16_rn(r.y);
+        }
         *reinterpret_cast<uint4*>(out + (((size_t)row * kG + o0 / 8) * W + x) * 8) =
             *reinterpret_cast<const uint4*>(o8);
       }
@@ -870,13 +931,14 @@ __global__ void __launch_bounds__(kInvThreads, 1)
 // applies the activation and contracts with Q2 in FP32.  Several CTAs share an SM so
 // that enough epilogue warps hide the activation's latency.
 constexpr int kDecStages = 4;
-constexpr int kDecCtasPerSm = 3;
+template <int kC>
+constexpr int dec_ctas_per_sm() { return kC <= 32 ? 4 : 3; }
 
-template <int kC, int kOut>
-__global__ void __launch_bounds__(kTcThreads, kDecCtasPerSm)
+template <int kC, int kOut, int kAct>
+__global__ void __launch_bounds__(kTcThreads, dec_ctas_per_sm<kC>())
     k_decoder_tc(const __nv_bfloat16* __restrict__ theta, float* __restrict__ out,
                  const float* __restrict__ params, const unsigned* __restrict__ offs, int B,
-                 int H, int W, int act, unsigned* __restrict__ status) {
+                 int H, int W, unsigned* __restrict__ status) {
   constexpr int kS = kC;
   constexpr int kG = kC / 8;
   constexpr int kStageBytes = kG * 128 * 16;  // [channel group][x (128)][8]
@@ -930,7 +992,7 @@ __global__ void __launch_bounds__(kTcThreads, kDecCtasPerSm)
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
       const int s = k % kDecStages;
-      if (k >= kDecStages) ok = mbar_wait(&empty_bar[s], ((k / kDecStages) - 1) & 1, status);
+      if (k >= kDecStages) ok = mbar_wait_sleep(&empty_bar[s], ((k / kDecStages) - 1) & 1, status);
       if (!ok) break;
       const int row = t / xt;  // b * H + y
       const int x0 = (t - row * xt) * 128;
@@ -942,7 +1004,7 @@ __global__ void __launch_bounds__(kTcThreads, kDecCtasPerSm)
                  &full_bar[s]);
     }
     for (int q = max(0, k - kDecStages); q < k; ++q)
-      mbar_wait(&full_bar[q % kDecStages], (q / kDecStages) & 1, status);
+      mbar_wait_sleep(&full_bar[q % kDecStages], (q / kDecStages) & 1, status);
   } else if (warp == 5) {
     // ---------------------------------------------------------------- MMA
     constexpr uint32_t idesc = idesc_bf16(128, kS, false, false);
@@ -950,8 +1012,8 @@ __global__ void __launch_bounds__(kTcThreads, kDecCtasPerSm)
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
       const int acc = j & 1;
-      if (j >= 2) ok = mbar_wait(&acc_empty[acc], ((j >> 1) - 1) & 1, status);
-      if (ok) ok = mbar_wait(&full_bar[j % kDecStages], (j / kDecStages) & 1, status);
+      if (j >= 2) ok = mbar_wait_sleep(&acc_empty[acc], ((j >> 1) - 1) & 1, status);
+      if (ok) ok = mbar_wait_sleep(&full_bar[j % kDecStages], (j / kDecStages) & 1, status);
       if (!ok) break;
       tc_fence_after();
       if (lane == 0) {
@@ -973,7 +1035,7 @@ __global__ void __launch_bounds__(kTcThreads, kDecCtasPerSm)
     int j = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
       const int acc = j & 1;
-      if (!mbar_wait(&acc_full[acc], (j >> 1) & 1, status)) break;
+      if (!mbar_wait_sleep(&acc_full[acc], (j >> 1) & 1, status)) break;
       tc_fence_after();
       float o[3] = {kOut > 0 ? q2_s[0] : 0.f, kOut > 1 ? q2_s[1] : 0.f, kOut > 2 ? q2_s[2] : 0.f};
 #pragma unroll
@@ -988,12 +1050,15 @@ __global__ void __launch_bounds__(kTcThreads, kDecCtasPerSm)
           if (lane == 0) mbar_arrive(&acc_empty[acc]);
         }
 #pragma unroll
-        for (int i = 0; i < (kS < 32 ? kS : 32); ++i) {
-          const float4 e = ep_s[cb * 32 + i];
-          const float h = act_tc(v[i] + e.x, act);
-          o[0] = fmaf(e.y, h, o[0]);
-          o[1] = fmaf(e.z, h, o[1]);
-          o[2] = fmaf(e.w, h, o[2]);
+        for (int i = 0; i < (kS < 32 ? kS : 32); i += 2) {
+          const float4 e0 = ep_s[cb * 32 + i], e1 = ep_s[cb * 32 + i + 1];
+          const float2 h = act_c2<kAct>(make_float2(v[i] + e0.x, v[i + 1] + e1.x));
+          o[0] = fmaf(e0.y, h.x, o[0]);
+          o[1] = fmaf(e0.z, h.x, o[1]);
+          o[2] = fmaf(e0.w, h.x, o[2]);
+          o[0] = fmaf(e1.y, h.y, o[0]);
+          o[1] = fmaf(e1.z, h.y, o[1]);
+          o[2] = fmaf(e1.w, h.y, o[2]);
         }
       }
       const int row = t / xt;
@@ -1056,7 +1121,7 @@ FnoTcWs fno_tc_ws_plan(const fno_config& c, int B, int H, int W) {
   return w;
 }
 
-template <int kC>
+template <int kC, int kAct>
 static int fno_forward_tc_impl(const fno_config& c, const FnoTcParams& P, const float* in,
                                float* out, int B, int H, int W, char* ws, cudaStream_t s) {
   const FnoTcWs wp = fno_tc_ws_plan(c, B, H, W);
@@ -1085,12 +1150,13 @@ static int fno_forward_tc_impl(const fno_config& c, const FnoTcParams& P, const 
   k_table_fy<<<((H / 4) * d.nf * 8 + 255) / 256, 256, 0, s>>>(fy, H, m, d.nf);
   k_table_ty<<<(d.kg * hp * 8 + 255) / 256, 256, 0, s>>>(ty, H, hp, m, d.kg);
   const size_t pix = (size_t)B * H * W;
+  const unsigned lift_blocks = (unsigned)((pix / 2 + 127) / 128);
   if (c.c_in == 4)
-    k_lift_blk<kC, 4><<<(unsigned)((pix + 127) / 128), 128, 0, s>>>(
-        in, th[0], P.lift0_w, P.lift0_b, P.lift1_w, P.lift1_b, B, H, W, c.c_in, c.activation);
+    k_lift_blk<kC, 4, kAct><<<lift_blocks, 128, 0, s>>>(
+        in, th[0], P.lift0_w, P.lift0_b, P.lift1_w, P.lift1_b, B, H, W, c.c_in);
   else
-    k_lift_blk<kC, 0><<<(unsigned)((pix + 127) / 128), 128, 0, s>>>(
-        in, th[0], P.lift0_w, P.lift0_b, P.lift1_w, P.lift1_b, B, H, W, c.c_in, c.activation);
+    k_lift_blk<kC, 0, kAct><<<lift_blocks, 128, 0, s>>>(
+        in, th[0], P.lift0_w, P.lift0_b, P.lift1_w, P.lift1_b, B, H, W, c.c_in);
   LBM_CHECK_LAUNCH();
   const size_t fwd_smem = (size_t)W * 64 + (size_t)kFwdStages * kFwdStageBytes;
   constexpr int kStageBytesInv = (4 + kC / 8) * 128 * 16 + (4 + kC / 8) * kC * 16;
@@ -1101,7 +1167,7 @@ static int fno_forward_tc_impl(const fno_config& c, const FnoTcParams& P, const 
               "fno_forward: spectral working set too large for shared memory");
   const int ytiles = (H + (128 / kC) - 1) / (128 / kC);
   const int fwd_ctas = std::min(B * ytiles, 2 * nsm);
-  const int inv_ctas = std::min(B * H * (W / 128), 2 * nsm);
+  const int inv_ctas = std::min(B * H * (W / 128), inv_ctas_per_sm<kC>() * nsm);
   const int ydft_ctas = std::min(B * ((m * kC + 127) / 128), 2 * nsm);
   const int iydft_ctas = std::min(B * (hp / 128) * d.nc, nsm);
   const dim3 mix_grid((unsigned)(2 * m * m), (unsigned)((B + kMixB - 1) / kMixB));
@@ -1115,9 +1181,8 @@ static int fno_forward_tc_impl(const fno_config& c, const FnoTcParams& P, const 
     LBM_CHECK_LAUNCH();
     k_iydft_tc<kC><<<iydft_ctas, kTcThreads, iy_smem, s>>>(ty, yb, zt, B, H, m, status);
     LBM_CHECK_LAUNCH();
-    k_inv_x_tc<kC><<<inv_ctas, kInvThreads, inv_smem, s>>>(th[cur], ti, zt, P.w[n], P.b[n],
-                                                          th[cur ^ 1], B, H, W, c.activation,
-                                                          status);
+    k_inv_x_tc<kC, kAct><<<inv_ctas, kInvThreads, inv_smem, s>>>(
+        th[cur], ti, zt, P.w[n], P.b[n], th[cur ^ 1], B, H, W, status);
     LBM_CHECK_LAUNCH();
     cur ^= 1;
   }
@@ -1126,9 +1191,9 @@ static int fno_forward_tc_impl(const fno_config& c, const FnoTcParams& P, const 
   if (c.dec_layers == 1 && c.dec_size == kC && c.c_out == 3) {
     const size_t smem_tc = (size_t)kC * kC * 2 + (size_t)kDecStages * (kC / 8) * 128 * 16;
     const int ntiles = B * H * (W / 128);
-    const int ctas = std::min(ntiles, kDecCtasPerSm * nsm);
-    k_decoder_tc<kC, 3><<<ctas, kTcThreads, smem_tc, s>>>(th[cur], out, P.params, P.dec_offs, B,
-                                                          H, W, c.activation, status);
+    const int ctas = std::min(ntiles, dec_ctas_per_sm<kC>() * nsm);
+    k_decoder_tc<kC, 3, kAct><<<ctas, kTcThreads, smem_tc, s>>>(th[cur], out, P.params,
+                                                                P.dec_offs, B, H, W, status);
   } else {
     k_decoder_blk<kC><<<(unsigned)((pix + 127) / 128), 128, dec_smem, s>>>(
         th[cur], out, P.params, P.dec_offs, c.dec_layers, B, H, W, c.dec_size, c.c_out,
@@ -1138,16 +1203,22 @@ static int fno_forward_tc_impl(const fno_config& c, const FnoTcParams& P, const 
   return LBM_OK;
 }
 
+template <int kC, int kAct>
+static int tc_set_smem_attrs_act() {
+  const int big = 200 * 1024;
+  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_inv_x_tc<kC, kAct>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_decoder_tc<kC, 3, kAct>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  return LBM_OK;
+}
 template <int kC>
 static int tc_set_smem_attrs() {
   const int big = 200 * 1024;
   LBM_CHECK_CUDA(cudaFuncSetAttribute(k_fwd_x_tc<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_inv_x_tc<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   LBM_CHECK_CUDA(cudaFuncSetAttribute(k_ydft_tc<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   LBM_CHECK_CUDA(cudaFuncSetAttribute(k_iydft_tc<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   LBM_CHECK_CUDA(cudaFuncSetAttribute(k_mix<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_decoder_tc<kC, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  return LBM_OK;
+  const int rc = tc_set_smem_attrs_act<kC, FNO_ACT_GELU>();
+  return rc != LBM_OK ? rc : tc_set_smem_attrs_act<kC, FNO_ACT_RELU>();
 }
 
 int fno_tc_prepare(const fno_config& c) {
@@ -1161,21 +1232,34 @@ int fno_tc_prepare(const fno_config& c) {
 
 int fno_forward_tc(const fno_config& c, const FnoTcParams& P, const float* in, float* out, int B,
                    int H, int W, char* ws, cudaStream_t s) {
+  const bool gelu = c.activation == FNO_ACT_GELU;
   switch (c.width) {
-    case 16: return fno_forward_tc_impl<16>(c, P, in, out, B, H, W, ws, s);
-    case 32: return fno_forward_tc_impl<32>(c, P, in, out, B, H, W, ws, s);
-    case 64: return fno_forward_tc_impl<64>(c, P, in, out, B, H, W, ws, s);
+    case 16: return gelu ? fno_forward_tc_impl<16, FNO_ACT_GELU>(c, P, in, out, B, H, W, ws, s)
+                         : fno_forward_tc_impl<16, FNO_ACT_RELU>(c, P, in, out, B, H, W, ws, s);
+    case 32: return gelu ? fno_forward_tc_impl<32, FNO_ACT_GELU>(c, P, in, out, B, H, W, ws, s)
+                         : fno_forward_tc_impl<32, FNO_ACT_RELU>(c, P, in, out, B, H, W, ws, s);
+    case 64: return gelu ? fno_forward_tc_impl<64, FNO_ACT_GELU>(c, P, in, out, B, H, W, ws, s)
+                         : fno_forward_tc_impl<64, FNO_ACT_RELU>(c, P, in, out, B, H, W, ws, s);
     default:
       set_error("fno_forward: no tensor-core kernels for width %d", c.width);
       return LBM_ERR_UNSUPPORTED;
   }
 }
 
-// Element-wise activation of the tensor-core kernels, for tests.
-__global__ void k_act_eval(const float* __restrict__ x, float* __restrict__ y, size_t n, int act) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x)
-    y[i] = act_tc(x[i], act);
+// Element-wise activation of the tensor-core kernels, for tests: element pairs go
+// through the packed form the kernels use, an odd last element through the scalar one.
+template <int kAct>
+__global__ void k_act_eval(const float* __restrict__ x, float* __restrict__ y, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; 2 * i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    if (2 * i + 1 < n) {
+      const float2 r = act_c2<kAct>(make_float2(x[2 * i], x[2 * i + 1]));
+      y[2 * i] = r.x;
+      y[2 * i + 1] = r.y;
+    } else {
+      y[2 * i] = act_c<kAct>(x[2 * i]);
+    }
+  }
 }
 
 }  // namespace lbmfno
@@ -1186,8 +1270,11 @@ extern "C" int fno_activation_eval(int act, const float* x_d, float* y_d, size_t
   LBM_REQUIRE(act == FNO_ACT_GELU || act == FNO_ACT_RELU, "fno_activation_eval: unknown activation");
   LBM_REQUIRE(n == 0 || (x_d != nullptr && y_d != nullptr), "fno_activation_eval: null buffer");
   if (n == 0) return LBM_OK;
-  const unsigned grid = (unsigned)std::min<size_t>((n + 255) / 256, 4096);
-  k_act_eval<<<grid, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(x_d, y_d, n, act);
+  const unsigned grid = (unsigned)std::min<size_t>((n / 2 + 256) / 256, 4096);
+  if (act == FNO_ACT_GELU)
+    k_act_eval<FNO_ACT_GELU><<<grid, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(x_d, y_d, n);
+  else
+    k_act_eval<FNO_ACT_RELU><<<grid, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(x_d, y_d, n);
   LBM_CHECK_LAUNCH();
   return LBM_OK;
 }

@@ -63,6 +63,31 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsign
   }
   return true;
 }
+// The same bounded wait, but each try_wait lets the hardware suspend the thread for up
+// to kSleepHintNs (it resumes as soon as the phase completes), so that waiting warps
+// do not take issue slots from the warps that compute.
+constexpr unsigned kSleepHintNs = 200000u;
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kSleepHintNs)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, unsigned parity, unsigned* status) {
+  if (mbar_try_wait_sleep(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait_sleep(bar, parity)) {
+    if (clock64() - t0 > kWaitLimitClocks) {
+      atomicOr(status, kStatusTimeout);
+      return false;
+    }
+  }
+  return true;
+}
 // Bulk copy global -> shared (addresses 16-byte aligned, size a multiple of 16),
 // completion counted in bytes on `bar`.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
