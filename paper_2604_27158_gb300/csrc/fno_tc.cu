@@ -84,34 +84,30 @@ __device__ __forceinline__ int kept_ky_tc(int a, int H, int m) { return a < m ? 
 
 // ------------------------------------------------------------------ tables
 // Fw[x/8][n][x%8]: n < m: cos(2 pi n x / W); m <= n < 2m: -sin(2 pi (n-m) x / W); else 0.
-__global__ void k_table_fwd(__nv_bfloat16* __restrict__ fw, int W, int m) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= W * 32) return;
+__device__ void table_fw(int t, __nv_bfloat16* __restrict__ fw, int W, int m) {
   const int xl = t & 7, n = (t >> 3) & 31, xh = t >> 8;
   const int x = xh * 8 + xl;
   float v = 0.0f;
   if (n < 2 * m) {
     const int k = n < m ? n : n - m;
-    double s, c;
-    sincospi(2.0 * (double)((long long)k * x % W) / (double)W, &s, &c);
-    v = n < m ? (float)c : (float)(-s);
+    float s, c;
+    sincospif(2.0f * (float)((long long)k * x % W) / (float)W, &s, &c);
+    v = n < m ? c : -s;
   }
   fw[t] = __float2bfloat16_rn(v);
 }
 // Ti[k'/8][x][k'%8]: k' < m: c_k cos(2 pi k' x / W) / (H W); m <= k' < 2m:
 // -c_k sin(2 pi (k'-m) x / W) / (H W); else 0; c_0 = 1, c_k = 2 (k > 0).
-__global__ void k_table_inv(__nv_bfloat16* __restrict__ ti, int H, int W, int m) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= W * 32) return;
+__device__ void table_ti(int t, __nv_bfloat16* __restrict__ ti, int H, int W, int m) {
   const int kl = t & 7, x = (t >> 3) % W, kh = (t >> 3) / W;
   const int kp = kh * 8 + kl;
   float v = 0.0f;
   if (kp < 2 * m) {
     const int k = kp < m ? kp : kp - m;
-    double s, c;
-    sincospi(2.0 * (double)((long long)k * x % W) / (double)W, &s, &c);
-    const double w = (k == 0 ? 1.0 : 2.0) / ((double)H * (double)W);
-    v = kp < m ? (float)(w * c) : (float)(-w * s);
+    float s, c;
+    sincospif(2.0f * (float)((long long)k * x % W) / (float)W, &s, &c);
+    const float w = (k == 0 ? 1.0f : 2.0f) / ((float)H * (float)W);
+    v = kp < m ? w * c : -w * s;
   }
   ti[t] = __float2bfloat16_rn(v);
 }
@@ -139,33 +135,45 @@ __host__ __device__ inline SpecDims spec_dims(int C, int m) {
 }
 // Fy[y/4][n][(y%4) * 2 + p], n = 2a + q: the real form of e^{-2 pi i ky(a) y / H} that
 // maps the pair (Re, Im) (p) of X1[y] to (Re, Im) (q) of the kept mode a; 0 for a >= 2m.
-__global__ void k_table_fy(__nv_bfloat16* __restrict__ fy, int H, int m, int nf) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (H / 4) * nf * 8) return;
+__device__ void table_fy(int t, __nv_bfloat16* __restrict__ fy, int H, int m, int nf) {
   const int j = t & 7, n = (t >> 3) % nf, yg = (t >> 3) / nf;
   const int y = yg * 4 + (j >> 1), p = j & 1, a = n >> 1, q = n & 1;
   float v = 0.0f;
   if (a < 2 * m) {
-    double sn, cs;
-    sincospi(2.0 * (double)((long long)kept_ky_tc(a, H, m) * y % H) / (double)H, &sn, &cs);
-    v = (float)(p == 0 ? (q == 0 ? cs : -sn) : (q == 0 ? sn : cs));
+    float sn, cs;
+    sincospif(2.0f * (float)((long long)kept_ky_tc(a, H, m) * y % H) / (float)H, &sn, &cs);
+    v = p == 0 ? (q == 0 ? cs : -sn) : (q == 0 ? sn : cs);
   }
   fy[t] = __float2bfloat16_rn(v);
 }
 // Ty[a/4][y][(a%4) * 2 + p]: cos (p = 0) and sin (p = 1) of 2 pi ky(a) y / H for the
 // inverse y-DFT; rows padded to hp (a multiple of 128) and a >= 2m are 0.
-__global__ void k_table_ty(__nv_bfloat16* __restrict__ ty, int H, int hp, int m, int kg) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= kg * hp * 8) return;
+__device__ void table_ty(int t, __nv_bfloat16* __restrict__ ty, int H, int hp, int m, int kg) {
   const int j = t & 7, y = (t >> 3) % hp, g = (t >> 3) / hp;
   const int a = g * 4 + (j >> 1), p = j & 1;
   float v = 0.0f;
   if (a < 2 * m && y < H) {
-    double sn, cs;
-    sincospi(2.0 * (double)((long long)kept_ky_tc(a, H, m) * y % H) / (double)H, &sn, &cs);
-    v = (float)(p == 0 ? cs : sn);
+    float sn, cs;
+    sincospif(2.0f * (float)((long long)kept_ky_tc(a, H, m) * y % H) / (float)H, &sn, &cs);
+    v = p == 0 ? cs : sn;
   }
   ty[t] = __float2bfloat16_rn(v);
+}
+
+// All four DFT tables of one forward in one launch (FP32 sines and cosines of exactly
+// reduced integer phases; the tables are stored in bfloat16).
+__global__ void k_tables(__nv_bfloat16* __restrict__ fw, __nv_bfloat16* __restrict__ ti,
+                         __nv_bfloat16* __restrict__ fy, __nv_bfloat16* __restrict__ ty, int H,
+                         int W, int m, int hp, int nf, int kg) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n_fw = W * 32, n_fy = (H / 4) * nf * 8, n_ty = kg * hp * 8;
+  if (t < n_fw) return table_fw(t, fw, W, m);
+  t -= n_fw;
+  if (t < n_fw) return table_ti(t, ti, H, W, m);
+  t -= n_fw;
+  if (t < n_fy) return table_fy(t, fy, H, m, nf);
+  t -= n_fy;
+  if (t < n_ty) return table_ty(t, ty, H, hp, m, kg);
 }
 
 // ---------------------------------------------------- lifting / projection
@@ -609,28 +617,57 @@ __global__ void __launch_bounds__(256)
   float2* x_s = mix_s + kC * kC;   // [b][c]
   const int md = blockIdx.x;
   const int b0 = blockIdx.y * kMixB, nb = min(kMixB, B - b0);
-  for (int t = threadIdx.x; t < kC * kC; t += blockDim.x) r_s[t] = rt[(size_t)md * kC * kC + t];
-  for (int t = threadIdx.x; t < nb * kC; t += blockDim.x)
-    x_s[t] = xh[((size_t)md * B + b0) * kC + t];
+  {  // all of this thread's loads in flight before the first shared-memory store
+    constexpr int kR = (kC * kC + 255) / 256, kXn = (kMixB * kC + 255) / 256;
+    float2 rv[kR], xv[kXn];
+#pragma unroll
+    for (int u = 0; u < kR; ++u) {
+      const int t = threadIdx.x + u * 256;
+      rv[u] = t < kC * kC ? rt[(size_t)md * kC * kC + t] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < kXn; ++u) {
+      const int t = threadIdx.x + u * 256;
+      xv[u] = t < nb * kC ? xh[((size_t)md * B + b0) * kC + t] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < kR; ++u)
+      if (threadIdx.x + u * 256 < kC * kC) r_s[threadIdx.x + u * 256] = rv[u];
+#pragma unroll
+    for (int u = 0; u < kXn; ++u)
+      if (threadIdx.x + u * 256 < nb * kC) x_s[threadIdx.x + u * 256] = xv[u];
+  }
   __syncthreads();
   const int a = md / m, kx = md - a * m;
   auto ncol = [&](int kp, int o) { return (kp / d.knk) * d.nchunk + o * d.knk + kp % d.knk; };
-  for (int e = threadIdx.x; e < nb * kC; e += blockDim.x) {
-    const int bl = e / kC, o = e - bl * kC;
-    float re = 0.f, im = 0.f;
-#pragma unroll 8
+  // thread: channel o and four batch items bl, bl + kBl, bl + 2 kBl, bl + 3 kBl (one read
+  // of R[c][o] serves four outputs)
+  constexpr int kBl = 256 / kC;
+  const int o = threadIdx.x % kC;
+  for (int bl0 = threadIdx.x / kC; bl0 < nb; bl0 += 4 * kBl) {
+    float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
     for (int i = 0; i < kC; ++i) {
-      const float2 xv = x_s[bl * kC + i];
       const float2 w = r_s[i * kC + o];
-      re = fmaf(xv.x, w.x, fmaf(-xv.y, w.y, re));
-      im = fmaf(xv.x, w.y, fmaf(xv.y, w.x, im));
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int bl = min(bl0 + k * kBl, nb - 1);
+        const float2 xv = x_s[bl * kC + i];
+        re[k] = fmaf(xv.x, w.x, fmaf(-xv.y, w.y, re[k]));
+        im[k] = fmaf(xv.x, w.y, fmaf(xv.y, w.x, im[k]));
+      }
     }
-    uint32_t* base = reinterpret_cast<uint32_t*>(yb) +
-                     ((size_t)(b0 + bl) * d.kg + a / 4) * d.nn * 4 + (a % 4);
-    const __nv_bfloat162 lo = __floats2bfloat162_rn(re, -im);
-    const __nv_bfloat162 hi = __floats2bfloat162_rn(im, re);
-    base[(size_t)ncol(kx, o) * 4] = *reinterpret_cast<const uint32_t*>(&lo);
-    base[(size_t)ncol(m + kx, o) * 4] = *reinterpret_cast<const uint32_t*>(&hi);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int bl = bl0 + k * kBl;
+      if (bl >= nb) break;
+      uint32_t* base = reinterpret_cast<uint32_t*>(yb) +
+                       ((size_t)(b0 + bl) * d.kg + a / 4) * d.nn * 4 + (a % 4);
+      const __nv_bfloat162 lo = __floats2bfloat162_rn(re[k], -im[k]);
+      const __nv_bfloat162 hi = __floats2bfloat162_rn(im[k], re[k]);
+      base[(size_t)ncol(kx, o) * 4] = *reinterpret_cast<const uint32_t*>(&lo);
+      base[(size_t)ncol(m + kx, o) * 4] = *reinterpret_cast<const uint32_t*>(&hi);
+    }
   }
 }
 
@@ -803,7 +840,7 @@ __global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
   __shared__ __align__(8) uint64_t full_bar[kInvStages], empty_bar[kInvStages];
   __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_base;
-  __shared__ float bias_s[kC];
+  __shared__ __align__(16) float bias_s[kC];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int xt = W / 128;
   const int ntiles = B * H * xt;
@@ -908,8 +945,9 @@ __global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
         __align__(16) __nv_bfloat16 o8[8];
 #pragma unroll
         for (int q = 0; q < 8; q += 2) {
-          const float2 r = act_c2<kAct>(make_float2(v[g * 8 + q] + bias_s[o0 + q],
-                                                    v[g * 8 + q + 1] + bias_s[o0 + q + 1]));
+          const float2 r = act_c2<kAct>(
+              __fadd2_rn(make_float2(v[g * 8 + q], v[g * 8 + q + 1]),
+                         *reinterpret_cast<const float2*>(&bias_s[o0 + q])));
           o8[q] = __float2bfloat16_rn(r.x);
           o8[q + 1] = __float2bfloat16_rn(r.y);
         }
@@ -931,11 +969,10 @@ __global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
 // applies the activation and contracts with Q2 in FP32.  Several CTAs share an SM so
 // that enough epilogue warps hide the activation's latency.
 constexpr int kDecStages = 4;
-template <int kC>
-constexpr int dec_ctas_per_sm() { return kC <= 32 ? 4 : 3; }
+constexpr int kDecCtasPerSm = 3;
 
 template <int kC, int kOut, int kAct>
-__global__ void __launch_bounds__(kTcThreads, dec_ctas_per_sm<kC>())
+__global__ void __launch_bounds__(kTcThreads, kDecCtasPerSm)
     k_decoder_tc(const __nv_bfloat16* __restrict__ theta, float* __restrict__ out,
                  const float* __restrict__ params, const unsigned* __restrict__ offs, int B,
                  int H, int W, unsigned* __restrict__ status) {
@@ -946,7 +983,9 @@ __global__ void __launch_bounds__(kTcThreads, dec_ctas_per_sm<kC>())
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* q1_s = smem;                       // Q1 as [k group][s][8] bf16
   unsigned char* stages = smem + kG * kS * 16;      // kDecStages * kStageBytes
-  __shared__ __align__(16) float4 ep_s[kS];         // {q1[j], Q2[0][j], Q2[1][j], Q2[2][j]}
+  // per hidden pair (j, j + 1): {q1[j], q1[j+1], Q2[0][j], Q2[0][j+1]},
+  //                            {Q2[1][j], Q2[1][j+1], Q2[2][j], Q2[2][j+1]}
+  __shared__ __align__(16) float4 ep_s[kS];
   __shared__ float q2_s[kOut];
   __shared__ __align__(8) uint64_t full_bar[kDecStages], empty_bar[kDecStages];
   __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
@@ -964,9 +1003,12 @@ __global__ void __launch_bounds__(kTcThreads, dec_ctas_per_sm<kC>())
     const int g = e / (kS * 8), sl = (e / 8) % kS, il = e % 8;
     reinterpret_cast<__nv_bfloat16*>(q1_s)[e] = __float2bfloat16_rn(w1[sl * kC + g * 8 + il]);
   }
-  for (int j = threadIdx.x; j < kS; j += blockDim.x)
-    ep_s[j] = make_float4(b1[j], kOut > 0 ? w2[j] : 0.f, kOut > 1 ? w2[kS + j] : 0.f,
-                          kOut > 2 ? w2[2 * kS + j] : 0.f);
+  for (int jp = threadIdx.x; jp < kS / 2; jp += blockDim.x) {
+    const int j = 2 * jp;
+    auto q2w = [&](int q, int jj) { return q < kOut ? w2[q * kS + jj] : 0.f; };
+    ep_s[2 * jp] = make_float4(b1[j], b1[j + 1], q2w(0, j), q2w(0, j + 1));
+    ep_s[2 * jp + 1] = make_float4(q2w(1, j), q2w(1, j + 1), q2w(2, j), q2w(2, j + 1));
+  }
   for (int q = threadIdx.x; q < kOut; q += blockDim.x) q2_s[q] = b2[q];
   fence_proxy_async_smem();
   if (threadIdx.x == 0) {
@@ -1037,7 +1079,8 @@ __global__ void __launch_bounds__(kTcThreads, dec_ctas_per_sm<kC>())
       const int acc = j & 1;
       if (!mbar_wait_sleep(&acc_full[acc], (j >> 1) & 1, status)) break;
       tc_fence_after();
-      float o[3] = {kOut > 0 ? q2_s[0] : 0.f, kOut > 1 ? q2_s[1] : 0.f, kOut > 2 ? q2_s[2] : 0.f};
+      // Q2 contraction on packed pairs: oq[q] = (sum over even j, sum over odd j)
+      float2 oq[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
       for (int cb = 0; cb < kAccCols / 32; ++cb) {
         float v[32];
@@ -1052,15 +1095,16 @@ __global__ void __launch_bounds__(kTcThreads, dec_ctas_per_sm<kC>())
 #pragma unroll
         for (int i = 0; i < (kS < 32 ? kS : 32); i += 2) {
           const float4 e0 = ep_s[cb * 32 + i], e1 = ep_s[cb * 32 + i + 1];
-          const float2 h = act_c2<kAct>(make_float2(v[i] + e0.x, v[i + 1] + e1.x));
-          o[0] = fmaf(e0.y, h.x, o[0]);
-          o[1] = fmaf(e0.z, h.x, o[1]);
-          o[2] = fmaf(e0.w, h.x, o[2]);
-          o[0] = fmaf(e1.y, h.y, o[0]);
-          o[1] = fmaf(e1.z, h.y, o[1]);
-          o[2] = fmaf(e1.w, h.y, o[2]);
+          const float2 h =
+              act_c2<kAct>(__fadd2_rn(make_float2(v[i], v[i + 1]), make_float2(e0.x, e0.y)));
+          oq[0] = __ffma2_rn(make_float2(e0.z, e0.w), h, oq[0]);
+          oq[1] = __ffma2_rn(make_float2(e1.x, e1.y), h, oq[1]);
+          oq[2] = __ffma2_rn(make_float2(e1.z, e1.w), h, oq[2]);
         }
       }
+      float o[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) o[q] = (q < kOut ? q2_s[q] : 0.f) + (oq[q].x + oq[q].y);
       const int row = t / xt;
       const int b = row / H, y = row - b * H;
       const int x = (t - row * xt) * 128 + warp * 32 + lane;
@@ -1145,10 +1189,8 @@ static int fno_forward_tc_impl(const fno_config& c, const FnoTcParams& P, const 
   LBM_CHECK_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), s));
   // padding entries of Yb (k' >= 2m, a >= 2m) are never written by the mixing kernel
   LBM_CHECK_CUDA(cudaMemsetAsync(yb, 0, (size_t)B * d.kg * d.nn * 16, s));
-  k_table_fwd<<<(W * 32 + 255) / 256, 256, 0, s>>>(fw, W, m);
-  k_table_inv<<<(W * 32 + 255) / 256, 256, 0, s>>>(ti, H, W, m);
-  k_table_fy<<<((H / 4) * d.nf * 8 + 255) / 256, 256, 0, s>>>(fy, H, m, d.nf);
-  k_table_ty<<<(d.kg * hp * 8 + 255) / 256, 256, 0, s>>>(ty, H, hp, m, d.kg);
+  const int n_tables = 2 * W * 32 + (H / 4) * d.nf * 8 + d.kg * hp * 8;
+  k_tables<<<(n_tables + 255) / 256, 256, 0, s>>>(fw, ti, fy, ty, H, W, m, hp, d.nf, d.kg);
   const size_t pix = (size_t)B * H * W;
   const unsigned lift_blocks = (unsigned)((pix / 2 + 127) / 128);
   if (c.c_in == 4)
@@ -1191,7 +1233,7 @@ static int fno_forward_tc_impl(const fno_config& c, const FnoTcParams& P, const 
   if (c.dec_layers == 1 && c.dec_size == kC && c.c_out == 3) {
     const size_t smem_tc = (size_t)kC * kC * 2 + (size_t)kDecStages * (kC / 8) * 128 * 16;
     const int ntiles = B * H * (W / 128);
-    const int ctas = std::min(ntiles, dec_ctas_per_sm<kC>() * nsm);
+    const int ctas = std::min(ntiles, kDecCtasPerSm * nsm);
     k_decoder_tc<kC, 3, kAct><<<ctas, kTcThreads, smem_tc, s>>>(th[cur], out, P.params,
                                                                 P.dec_offs, B, H, W, status);
   } else {
