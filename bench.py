@@ -848,10 +848,10 @@ def main():
             "e2e": e2e,
             "cpu_baseline": cpu,
         }
-        # our kernels per step: FNO on the tensor-core path (3 table kernels + lift + 4 per
+        # our kernels per step: FNO on the tensor-core path (table kernel + lift + 5 per
         # layer + decoder, else 2 twiddle + lift + 5 per layer + decoder), reinit, fill,
         # pack/unpack, one step kernel per LBM step, two reduction kernels per check
-        fno_k = (3 + 1 + 4 * 4 + 1) if net.uses_tensor_cores(NY, NX) else (2 + 1 + 5 * 4 + 1)
+        fno_k = (1 + 1 + 5 * 4 + 1) if net.uses_tensor_cores(NY, NX) else (2 + 1 + 5 * 4 + 1)
         per_step = fno_k + 1 + 1 + 2 + steps_per_solve + 2 * math.ceil(steps_per_solve / CHECK_EVERY)
         line["gpu_launches"] = per_step * args.steps
         print(json.dumps(line), flush=True)
