@@ -262,6 +262,128 @@ __global__ void __launch_bounds__(128)
     dst[1] = *reinterpret_cast<const uint4*>(o8[1]);
   }
 }
+// Lifting network P on the tensor cores: layer 1 ((c_in + 2) -> C/2, activation) on
+// CUDA cores with one thread per pixel, its outputs rounded to bfloat16 into the K-major
+// A operand in shared memory; layer 2 (C/2 -> C) as one tcgen05 MMA per 128-pixel tile
+// (M = 128 x positions of one row, N = C, K = C/2 padded to 16) with the bias added in
+// the epilogue.  Several CTAs share an SM; each serialises fill -> MMA -> drain.
+constexpr int kLiftCtasPerSm = 6;
+template <int kC, int kCin, int kAct>
+__global__ void __launch_bounds__(128, kLiftCtasPerSm)
+    k_lift_tc(const float* __restrict__ in, __nv_bfloat16* __restrict__ theta,
+              const float* __restrict__ w0, const float* __restrict__ b0,
+              const float* __restrict__ w1, const float* __restrict__ b1, int B, int H, int W,
+              int cin_rt, unsigned* __restrict__ status) {
+  constexpr int kHid = kC / 2;
+  constexpr int kK = kHid < 16 ? 16 : kHid;  // MMA K (zero-padded hidden units)
+  constexpr int kKG = kK / 8;
+  constexpr int kX = kCin > 0 ? kCin + 2 : 18;
+  constexpr int kAccCols = kC < 32 ? 32 : kC;
+  const int cin = kCin > 0 ? kCin : cin_rt;
+  const int cin2 = cin + 2;
+  __shared__ __align__(1024) unsigned char a_s[kKG * 2048];   // [k group][x (128)][8]
+  __shared__ __align__(1024) unsigned char b_s[kKG * kC * 16];  // W1^T: [k group][o][8]
+  __shared__ float2 w0p_s[(kHid / 2) * 18];  // (w0[j][c], w0[j+1][c]) for hidden pairs
+  __shared__ __align__(16) float b0_s[kHid], b1_s[kC];
+  __shared__ __align__(8) uint64_t mma_bar;
+  __shared__ uint32_t tmem_base;
+  const int warp = threadIdx.x >> 5;
+  for (int e = threadIdx.x; e < kKG * kC * 8; e += blockDim.x) {
+    const int g = e / (kC * 8), o = (e / 8) % kC, il = e % 8, j = g * 8 + il;
+    reinterpret_cast<__nv_bfloat16*>(b_s)[e] = __float2bfloat16_rn(j < kHid ? w1[o * kHid + j] : 0.f);
+  }
+  for (int e = threadIdx.x; e < (kHid / 2) * cin2; e += blockDim.x) {
+    const int jp = e / cin2, c = e - jp * cin2;
+    w0p_s[e] = make_float2(w0[(2 * jp) * cin2 + c], w0[(2 * jp + 1) * cin2 + c]);
+  }
+  for (int j = threadIdx.x; j < kHid; j += blockDim.x) b0_s[j] = b0[j];
+  for (int o = threadIdx.x; o < kC; o += blockDim.x) b1_s[o] = b1[o];
+  if (kHid < kK)  // padded hidden units stay zero
+    for (int e = threadIdx.x; e < 128 * 8; e += blockDim.x)
+      reinterpret_cast<__nv_bfloat16*>(a_s + 2048)[e] = __float2bfloat16_rn(0.f);
+  fence_proxy_async_smem();
+  if (threadIdx.x == 0) {
+    mbar_init(&mma_bar, 1);
+    mbar_init_fence();
+  }
+  if (warp == 0) tmem_alloc(&tmem_base, kAccCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  const int xt = W / 128;
+  const int ntiles = B * H * xt;
+  constexpr uint32_t idesc = idesc_bf16(128, kC, false, false);
+  int j = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+    const int row = t / xt;  // b * H + y
+    const int y = row % H, b = row / H;
+    const int x = (t - row * xt) * 128 + threadIdx.x;
+    // layer 1 for this thread's pixel (inputs and coordinates rounded to bfloat16)
+    float xin[kX];
+#pragma unroll
+    for (int c = 0; c < (kCin > 0 ? kCin : 16); ++c)
+      if (c < cin)
+        xin[c] = __bfloat162float(__float2bfloat16_rn(in[(((size_t)b * cin + c) * H + y) * W + x]));
+    xin[cin] = __bfloat162float(__float2bfloat16_rn((float)x / (float)max(W - 1, 1)));
+    xin[cin + 1] = __bfloat162float(__float2bfloat16_rn((float)y / (float)max(H - 1, 1)));
+    __align__(16) __nv_bfloat16 h[kHid];
+#pragma unroll
+    for (int jp = 0; jp < kHid / 2; ++jp) {
+      float2 a = *reinterpret_cast<const float2*>(&b0_s[2 * jp]);
+#pragma unroll
+      for (int c = 0; c < kX; ++c)
+        if (c < cin2) a = __ffma2_rn(w0p_s[jp * cin2 + c], make_float2(xin[c], xin[c]), a);
+      const float2 r = act_c2<kAct>(a);
+      h[2 * jp] = __float2bfloat16_rn(r.x);
+      h[2 * jp + 1] = __float2bfloat16_rn(r.y);
+    }
+#pragma unroll
+    for (int g = 0; g < kHid / 8; ++g)
+      *reinterpret_cast<uint4*>(a_s + g * 2048 + threadIdx.x * 16) =
+          *reinterpret_cast<const uint4*>(&h[g * 8]);
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();  // A complete; every thread has drained the previous accumulator
+    tc_fence_after();
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int kk = 0; kk < kKG / 2; ++kk)
+        mma_bf16(tmem, smem_desc(a_s + kk * 4096, 2048, 128),
+                 smem_desc(b_s + kk * 2 * kC * 16, kC * 16, 128), idesc, kk > 0);
+      mma_commit(&mma_bar);
+    }
+    const bool ok = mbar_wait_sleep(&mma_bar, j & 1, status);
+    if (__syncthreads_or(!ok)) break;  // the whole CTA leaves together after a timeout
+    tc_fence_after();
+#pragma unroll
+    for (int cb = 0; cb < kAccCols / 32; ++cb) {
+      float v[32];
+      const uint32_t ta = tmem + cb * 32 + ((uint32_t)(warp * 32) << 16);
+      if (kC >= 32) tmem_ld32(ta, v);
+      else tmem_ld16(ta, v);
+#pragma unroll
+      for (int g = 0; g < (kC < 32 ? kC : 32) / 8; ++g) {
+        const int o0 = cb * 32 + g * 8;
+        __align__(16) __nv_bfloat16 o8[8];
+#pragma unroll
+        for (int q = 0; q < 8; q += 2) {
+          const float2 r = __fadd2_rn(make_float2(v[g * 8 + q], v[g * 8 + q + 1]),
+                                      *reinterpret_cast<const float2*>(&b1_s[o0 + q]));
+          o8[q] = __float2bfloat16_rn(r.x);
+          o8[q + 1] = __float2bfloat16_rn(r.y);
+        }
+        *reinterpret_cast<uint4*>(theta + (((size_t)row * (kC / 8) + o0 / 8) * W + x) * 8) =
+            *reinterpret_cast<const uint4*>(o8);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, kAccCols);
+}
+
 // Projection Q from the channel-blocked field, any decoder shape (the common shape
 // runs in k_decoder_tc); one thread per pixel, decoder weights staged in shared memory.
 template <int kC>
@@ -1192,13 +1314,13 @@ static int fno_forward_tc_impl(const fno_config& c, const FnoTcParams& P, const 
   const int n_tables = 2 * W * 32 + (H / 4) * d.nf * 8 + d.kg * hp * 8;
   k_tables<<<(n_tables + 255) / 256, 256, 0, s>>>(fw, ti, fy, ty, H, W, m, hp, d.nf, d.kg);
   const size_t pix = (size_t)B * H * W;
-  const unsigned lift_blocks = (unsigned)((pix / 2 + 127) / 128);
+  const int lift_ctas = (int)std::min<size_t>(pix / 128, (size_t)kLiftCtasPerSm * nsm);
   if (c.c_in == 4)
-    k_lift_blk<kC, 4, kAct><<<lift_blocks, 128, 0, s>>>(
-        in, th[0], P.lift0_w, P.lift0_b, P.lift1_w, P.lift1_b, B, H, W, c.c_in);
+    k_lift_tc<kC, 4, kAct><<<lift_ctas, 128, 0, s>>>(
+        in, th[0], P.lift0_w, P.lift0_b, P.lift1_w, P.lift1_b, B, H, W, c.c_in, status);
   else
-    k_lift_blk<kC, 0, kAct><<<lift_blocks, 128, 0, s>>>(
-        in, th[0], P.lift0_w, P.lift0_b, P.lift1_w, P.lift1_b, B, H, W, c.c_in);
+    k_lift_tc<kC, 0, kAct><<<lift_ctas, 128, 0, s>>>(
+        in, th[0], P.lift0_w, P.lift0_b, P.lift1_w, P.lift1_b, B, H, W, c.c_in, status);
   LBM_CHECK_LAUNCH();
   const size_t fwd_smem = (size_t)W * 64 + (size_t)kFwdStages * kFwdStageBytes;
   constexpr int kStageBytesInv = (4 + kC / 8) * 128 * 16 + (4 + kC / 8) * kC * 16;
