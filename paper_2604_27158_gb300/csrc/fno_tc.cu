@@ -177,91 +177,6 @@ __global__ void k_tables(__nv_bfloat16* __restrict__ fw, __nv_bfloat16* __restri
 }
 
 // ---------------------------------------------------- lifting / projection
-// Lifting network P (1x1, (c_in + 2) -> C/2 -> act -> C); each thread lifts two
-// neighbouring pixels (x, x + 1) so that every weight read from shared memory (a
-// broadcast) feeds two FMAs.  W is even.
-template <int kC, int kCin, int kAct>
-__global__ void __launch_bounds__(128)
-    k_lift_blk(const float* __restrict__ in, __nv_bfloat16* __restrict__ theta,
-               const float* __restrict__ w0, const float* __restrict__ b0,
-               const float* __restrict__ w1, const float* __restrict__ b1, int B, int H, int W,
-               int cin_rt) {
-  // kCin > 0: compile-time input channel count (registers); 0: runtime count
-  constexpr int kX = kCin > 0 ? kCin + 2 : 18;
-  constexpr int kHid = kC / 2;
-  const int cin = kCin > 0 ? kCin : cin_rt;
-  __shared__ float s_w0[kHid * 18], s_b0[kHid], s_b1[kC];
-  __shared__ __align__(16) float s_w1[kC * kHid];
-  const int cin2 = cin + 2;
-  for (int t = threadIdx.x; t < kHid * cin2; t += blockDim.x) s_w0[t] = w0[t];
-  for (int t = threadIdx.x; t < kHid; t += blockDim.x) s_b0[t] = b0[t];
-  for (int t = threadIdx.x; t < kC * kHid; t += blockDim.x) s_w1[t] = w1[t];
-  for (int t = threadIdx.x; t < kC; t += blockDim.x) s_b1[t] = b1[t];
-  __syncthreads();
-  const size_t pairs = (size_t)B * H * W / 2;
-  const size_t pp = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (pp >= pairs) return;
-  const size_t p = 2 * pp;
-  const int x = (int)(p % W);
-  const size_t row = p / W;  // b * H + y
-  const int y = (int)(row % H);
-  const int b = (int)(row / H);
-  float xin[2][kX];
-#pragma unroll
-  for (int c = 0; c < (kCin > 0 ? kCin : 16); ++c)
-    if (c < cin) {
-      const float* src = in + (((size_t)b * cin + c) * H + y) * W + x;  // 4-byte aligned only
-      xin[0][c] = __bfloat162float(__float2bfloat16_rn(src[0]));
-      xin[1][c] = __bfloat162float(__float2bfloat16_rn(src[1]));
-    }
-  const float gy = __bfloat162float(__float2bfloat16_rn((float)y / (float)max(H - 1, 1)));
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    xin[q][cin] = __bfloat162float(__float2bfloat16_rn((float)(x + q) / (float)max(W - 1, 1)));
-    xin[q][cin + 1] = gy;
-  }
-  float hid[2][kHid];
-#pragma unroll
-  for (int j = 0; j < kHid; ++j) {
-    float a0 = s_b0[j], a1 = a0;
-#pragma unroll
-    for (int c = 0; c < kX; ++c)
-      if (c < cin2) {
-        const float w = s_w0[j * cin2 + c];
-        a0 = fmaf(w, xin[0][c], a0);
-        a1 = fmaf(w, xin[1][c], a1);
-      }
-    const float2 h2 = act_c2<kAct>(make_float2(a0, a1));
-    hid[0][j] = h2.x;
-    hid[1][j] = h2.y;
-  }
-#pragma unroll
-  for (int g = 0; g < kC / 8; ++g) {
-    __align__(16) __nv_bfloat16 o8[2][8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int o = g * 8 + q;
-      float a0 = s_b1[o], a1 = a0;
-#pragma unroll
-      for (int j = 0; j < kHid; j += 4) {
-        const float4 w = *reinterpret_cast<const float4*>(&s_w1[o * kHid + j]);
-        a0 = fmaf(w.x, hid[0][j], a0);
-        a1 = fmaf(w.x, hid[1][j], a1);
-        a0 = fmaf(w.y, hid[0][j + 1], a0);
-        a1 = fmaf(w.y, hid[1][j + 1], a1);
-        a0 = fmaf(w.z, hid[0][j + 2], a0);
-        a1 = fmaf(w.z, hid[1][j + 2], a1);
-        a0 = fmaf(w.w, hid[0][j + 3], a0);
-        a1 = fmaf(w.w, hid[1][j + 3], a1);
-      }
-      o8[0][q] = __float2bfloat16_rn(a0);
-      o8[1][q] = __float2bfloat16_rn(a1);
-    }
-    uint4* dst = reinterpret_cast<uint4*>(theta + ((row * (kC / 8) + g) * W + x) * 8);
-    dst[0] = *reinterpret_cast<const uint4*>(o8[0]);
-    dst[1] = *reinterpret_cast<const uint4*>(o8[1]);
-  }
-}
 // Lifting network P on the tensor cores: layer 1 ((c_in + 2) -> C/2, activation) on
 // CUDA cores with one thread per pixel, its outputs rounded to bfloat16 into the K-major
 // A operand in shared memory; layer 2 (C/2 -> C) as one tcgen05 MMA per 128-pixel tile
@@ -943,7 +858,7 @@ constexpr int kInvStages = 3;
 // two for C = 64 (shared memory)
 template <int kC>
 constexpr int inv_ctas_per_sm() { return kC <= 32 ? 3 : 2; }
-constexpr int kInvEpiWarps = 8;  // two warps per TMEM lane quadrant, each half of the columns
+constexpr int kInvEpiWarps = 8;  // two groups of four: each drains alternate tiles
 constexpr int kInvThreads = (kInvEpiWarps + 2) * 32;
 
 template <int kC, int kAct>
@@ -983,7 +898,7 @@ __global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&acc_full[a], 1);
-      mbar_init(&acc_empty[a], kInvEpiWarps);
+      mbar_init(&acc_empty[a], kInvEpiWarps / 2);
     }
     mbar_init_fence();
   }
@@ -1044,37 +959,41 @@ __global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
     }
   } else {
     // ----------------------------------------------------------- epilogue
-    // warp w drains TMEM lanes 32 (w % 4) .. +31 (x positions) and the column half w / 4
-    constexpr int kHalf = kC / 2;  // output channels per epilogue warp (8, 16 or 32)
-    const int quad = warp & 3, half = warp >> 2;
-    int j = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
-      const int acc = j & 1;
-      if (!mbar_wait_sleep(&acc_full[acc], (j >> 1) & 1, status)) break;
+    // warp w drains TMEM lanes 32 (w % 4) .. +31 (x positions), all C columns, of the
+    // tiles whose accumulator is w / 4 (the two warp groups take alternate tiles)
+    const int quad = warp & 3, grp = warp >> 2;
+    for (int t = blockIdx.x + grp * gridDim.x, j = grp; t < ntiles; t += 2 * gridDim.x, j += 2) {
+      if (!mbar_wait_sleep(&acc_full[grp], (j >> 1) & 1, status)) break;
       tc_fence_after();
-      float v[32];
-      const uint32_t ta = tmem + acc * kAccCols + half * kHalf + ((uint32_t)(quad * 32) << 16);
-      if (kHalf >= 32) tmem_ld32(ta, v);
-      else tmem_ld16(ta, v);
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty[acc]);
       const int row = t / xt;
       const int x = (t - row * xt) * 128 + quad * 32 + lane;
 #pragma unroll
-      for (int g = 0; g < kHalf / 8; ++g) {
-        const int o0 = half * kHalf + g * 8;
-        __align__(16) __nv_bfloat16 o8[8];
-#pragma unroll
-        for (int q = 0; q < 8; q += 2) {
-          const float2 r = act_c2<kAct>(
-              __fadd2_rn(make_float2(v[g * 8 + q], v[g * 8 + q + 1]),
-                         *reinterpret_cast<const float2*>(&bias_s[o0 + q])));
-          o8[q] = __float2bfloat16_rn(r.x);
-          o8[q + 1] = __float2bfloat16_rn(r.y);
+      for (int cb = 0; cb < (kC + 31) / 32; ++cb) {
+        constexpr int kCols = kC < 32 ? kC : 32;
+        float v[32];
+        const uint32_t ta = tmem + grp * kAccCols + cb * 32 + ((uint32_t)(quad * 32) << 16);
+        if (kCols == 32) tmem_ld32(ta, v);
+        else tmem_ld16(ta, v);
+        if (cb == (kC + 31) / 32 - 1) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acc_empty[grp]);
         }
-        *reinterpret_cast<uint4*>(out + (((size_t)row * kG + o0 / 8) * W + x) * 8) =
-            *reinterpret_cast<const uint4*>(o8);
+#pragma unroll
+        for (int g = 0; g < kCols / 8; ++g) {
+          const int o0 = cb * 32 + g * 8;
+          __align__(16) __nv_bfloat16 o8[8];
+#pragma unroll
+          for (int q = 0; q < 8; q += 2) {
+            const float2 r = act_c2<kAct>(
+                __fadd2_rn(make_float2(v[g * 8 + q], v[g * 8 + q + 1]),
+                           *reinterpret_cast<const float2*>(&bias_s[o0 + q])));
+            o8[q] = __float2bfloat16_rn(r.x);
+            o8[q + 1] = __float2bfloat16_rn(r.y);
+          }
+          *reinterpret_cast<uint4*>(out + (((size_t)row * kG + o0 / 8) * W + x) * 8) =
+              *reinterpret_cast<const uint4*>(o8);
+        }
       }
     }
   }
