@@ -1010,10 +1010,12 @@ __global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
 // applies the activation and contracts with Q2 in FP32.  Several CTAs share an SM so
 // that enough epilogue warps hide the activation's latency.
 constexpr int kDecStages = 4;
-constexpr int kDecCtasPerSm = 3;
+constexpr int kDecCtasPerSm = 2;
+constexpr int kDecEpiWarps = 8;  // two groups of four: each drains alternate tiles
+constexpr int kDecThreads = (kDecEpiWarps + 2) * 32;
 
 template <int kC, int kOut, int kAct>
-__global__ void __launch_bounds__(kTcThreads, kDecCtasPerSm)
+__global__ void __launch_bounds__(kDecThreads, kDecCtasPerSm)
     k_decoder_tc(const __nv_bfloat16* __restrict__ theta, float* __restrict__ out,
                  const float* __restrict__ params, const unsigned* __restrict__ offs, int B,
                  int H, int W, unsigned* __restrict__ status) {
@@ -1069,7 +1071,7 @@ __global__ void __launch_bounds__(kTcThreads, kDecCtasPerSm)
   tc_fence_after();
   const uint32_t tmem = tmem_base;
 
-  if (warp == 4) {
+  if (warp == kDecEpiWarps) {
     // ------------------------------------------------------------ producer
     int k = 0;
     bool ok = true;
@@ -1088,7 +1090,7 @@ __global__ void __launch_bounds__(kTcThreads, kDecCtasPerSm)
     }
     for (int q = max(0, k - kDecStages); q < k; ++q)
       mbar_wait_sleep(&full_bar[q % kDecStages], (q / kDecStages) & 1, status);
-  } else if (warp == 5) {
+  } else if (warp == kDecEpiWarps + 1) {
     // ---------------------------------------------------------------- MMA
     constexpr uint32_t idesc = idesc_bf16(128, kS, false, false);
     int j = 0;
@@ -1114,10 +1116,10 @@ __global__ void __launch_bounds__(kTcThreads, kDecCtasPerSm)
     }
   } else {
     // ----------------------------------------------------------- epilogue
-    // warp w holds TMEM lanes 32 w .. 32 w + 31: x positions x0 + 32 w + lane
-    int j = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
-      const int acc = j & 1;
+    // warp w holds TMEM lanes 32 (w % 4) .. +31 (x positions x0 + 32 (w % 4) + lane) of
+    // the tiles whose accumulator is w / 4 (the two warp groups take alternate tiles)
+    const int quad = warp & 3, acc = warp >> 2;
+    for (int t = blockIdx.x + acc * gridDim.x, j = acc; t < ntiles; t += 2 * gridDim.x, j += 2) {
       if (!mbar_wait_sleep(&acc_full[acc], (j >> 1) & 1, status)) break;
       tc_fence_after();
       // Q2 contraction on packed pairs: oq[q] = (sum over even j, sum over odd j)
@@ -1125,7 +1127,7 @@ __global__ void __launch_bounds__(kTcThreads, kDecCtasPerSm)
 #pragma unroll
       for (int cb = 0; cb < kAccCols / 32; ++cb) {
         float v[32];
-        const uint32_t ta = tmem + acc * kAccCols + cb * 32 + ((uint32_t)(warp * 32) << 16);
+        const uint32_t ta = tmem + acc * kAccCols + cb * 32 + ((uint32_t)(quad * 32) << 16);
         if (kS >= 32) tmem_ld32(ta, v);
         else tmem_ld16(ta, v);
         if (cb == kAccCols / 32 - 1) {
@@ -1148,7 +1150,7 @@ __global__ void __launch_bounds__(kTcThreads, kDecCtasPerSm)
       for (int q = 0; q < 3; ++q) o[q] = (q < kOut ? q2_s[q] : 0.f) + (oq[q].x + oq[q].y);
       const int row = t / xt;
       const int b = row / H, y = row - b * H;
-      const int x = (t - row * xt) * 128 + warp * 32 + lane;
+      const int x = (t - row * xt) * 128 + quad * 32 + lane;
 #pragma unroll
       for (int q = 0; q < kOut; ++q) out[(((size_t)b * kOut + q) * H + y) * W + x] = o[q];
     }
@@ -1275,7 +1277,7 @@ static int fno_forward_tc_impl(const fno_config& c, const FnoTcParams& P, const 
     const size_t smem_tc = (size_t)kC * kC * 2 + (size_t)kDecStages * (kC / 8) * 128 * 16;
     const int ntiles = B * H * (W / 128);
     const int ctas = std::min(ntiles, kDecCtasPerSm * nsm);
-    k_decoder_tc<kC, 3, kAct><<<ctas, kTcThreads, smem_tc, s>>>(th[cur], out, P.params,
+    k_decoder_tc<kC, 3, kAct><<<ctas, kDecThreads, smem_tc, s>>>(th[cur], out, P.params,
                                                                 P.dec_offs, B, H, W, status);
   } else {
     k_decoder_blk<kC><<<(unsigned)((pix + 127) / 128), 128, dec_smem, s>>>(
