@@ -253,6 +253,58 @@ __global__ void k_fwd_x(const __nv_bfloat16* __restrict__ theta, float2* __restr
   }
 }
 
+// Forward x-DFT, one warp per row (b, y) and one lane per frequency kx (32 at a time):
+// each lane advances its own twiddle e^{-i kx x phi} once per x and applies it to all
+// C channels of the staged row, so the twiddle work is shared by the channels (the
+// kernel above shares a staged value among frequencies instead).  C <= kMaxC <= 32.
+constexpr int kFxRowsPerBlock = 4;
+constexpr int kFxChunk = 64;  // x positions staged per pass
+template <int kMaxC>
+__global__ void __launch_bounds__(32 * kFxRowsPerBlock)
+    k_fwd_x_row(const __nv_bfloat16* __restrict__ theta, float2* __restrict__ x1,
+                const float2* __restrict__ twx, int rows, int W, int C, int m) {
+  extern __shared__ float smem_f[];
+  float2* tw = reinterpret_cast<float2*>(smem_f);                              // W
+  float* rs = smem_f + 2 * (size_t)W + (size_t)(threadIdx.x >> 5) * kFxChunk * kMaxC;
+  for (int t = threadIdx.x; t < W; t += blockDim.x) tw[t] = twx[t];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const size_t r = (size_t)blockIdx.x * kFxRowsPerBlock + (threadIdx.x >> 5);
+  if (r >= (size_t)rows) return;
+  const __nv_bfloat16* src = theta + r * (size_t)W * C;
+  for (int kx0 = 0; kx0 < m; kx0 += 32) {
+    const int kx = min(kx0 + lane, m - 1);
+    const float2 step = tw[kx];
+    float2 e = make_float2(1.f, 0.f);
+    float2 acc[kMaxC];
+#pragma unroll
+    for (int c = 0; c < kMaxC; ++c) acc[c] = make_float2(0.f, 0.f);
+    for (int x0 = 0; x0 < W; x0 += kFxChunk) {
+      const int nx = min(kFxChunk, W - x0);
+      __syncwarp();
+      for (int t = lane; t < nx * C; t += 32) rs[t] = __bfloat162float(src[(size_t)x0 * C + t]);
+      __syncwarp();
+      for (int xl = 0; xl < nx; ++xl) {
+        const int x = x0 + xl;
+        if (x % kReseed == 0) e = tw[(int)(((long long)kx * x) % W)];
+        const float* v = rs + xl * C;
+#pragma unroll
+        for (int c = 0; c < kMaxC; ++c)
+          if (c < C) {
+            acc[c].x = fmaf(v[c], e.x, acc[c].x);   // v e^{-i phi}: (v cos, -v sin)
+            acc[c].y = fmaf(-v[c], e.y, acc[c].y);
+          }
+        e = cmul(e, step);
+      }
+    }
+    if (kx0 + lane < m) {
+#pragma unroll
+      for (int c = 0; c < kMaxC; ++c)
+        if (c < C) x1[(r * m + kx) * C + c] = acc[c];
+    }
+  }
+}
+
 __device__ __forceinline__ int kept_ky(int a, int H, int m) { return a < m ? a : H - 2 * m + a; }
 
 // Forward y-DFT over the kept ky for one (b, kx): Xh[b][a][kx][c].  The column
@@ -368,44 +420,60 @@ __global__ void k_inv_y(const float2* __restrict__ yh, float2* __restrict__ z,
 
 // Row kernel: theta'[x][o] = act( (1/HW) sum_kx c_kx Re(Z[kx][o] e^{+2 pi i kx x/W})
 //                                 + sum_i Wt[o][i] theta[x][i] + bias[o] ).
-__global__ void k_inv_x_w(const __nv_bfloat16* __restrict__ theta, const float2* __restrict__ z,
-                          const float* __restrict__ wmat, const float* __restrict__ bias,
-                          __nv_bfloat16* __restrict__ out, const float2* __restrict__ twx, int H,
-                          int W, int C, int m, int act) {
+// One thread per x position computes all C outputs: the twiddle e^{+i kx x phi} is
+// advanced once per frequency and applied to every channel; Z is staged pre-scaled by
+// c_kx / (H W).  C <= kMaxC, C even.
+template <int kMaxC>
+__global__ void k_inv_x_row(const __nv_bfloat16* __restrict__ theta, const float2* __restrict__ z,
+                            const float* __restrict__ wmat, const float* __restrict__ bias,
+                            __nv_bfloat16* __restrict__ out, const float2* __restrict__ twx,
+                            int H, int W, int C, int m, int act) {
   extern __shared__ float smem_f[];
   float* wt = smem_f;                                      // C * C, [i][o]
-  float2* zs = reinterpret_cast<float2*>(wt + C * C);      // m * C
+  float* bs = wt + C * C;                                  // C
+  float2* zs = reinterpret_cast<float2*>(bs + C + (C & 1));  // m * C, scaled
   float2* tw = zs + m * C;                                 // W
   const size_t r = blockIdx.x;
   for (int t = threadIdx.x; t < C * C; t += blockDim.x) {
     const int i = t / C, o = t % C;
     wt[t] = wmat[o * C + i];
   }
-  for (int t = threadIdx.x; t < m * C; t += blockDim.x) zs[t] = z[r * m * C + t];
+  for (int t = threadIdx.x; t < C; t += blockDim.x) bs[t] = bias[t];
+  const float inv_hw = 1.0f / ((float)H * (float)W);
+  for (int t = threadIdx.x; t < m * C; t += blockDim.x) {
+    const float2 v = z[r * m * C + t];
+    const float w = (t < C ? 1.0f : 2.0f) * inv_hw;  // kx = t / C; kx = 0 weight 1
+    zs[t] = make_float2(v.x * w, v.y * w);
+  }
   for (int t = threadIdx.x; t < W; t += blockDim.x) tw[t] = twx[t];
   __syncthreads();
-  const float inv_hw = 1.0f / ((float)H * (float)W);
   const __nv_bfloat16* src = theta + r * (size_t)W * C;
   __nv_bfloat16* dst = out + r * (size_t)W * C;
-  const int o = threadIdx.x % C, xg = threadIdx.x / C, groups = blockDim.x / C;
-  if (xg >= groups) return;
-  const float bo = bias[o];
-  for (int x = xg; x < W; x += groups) {
-    // sum_kx c_kx Re(Z[kx] e^{+i kx x phi}), e advanced by e^{+i x phi} per frequency
+  for (int x = threadIdx.x; x < W; x += blockDim.x) {
+    float acc[kMaxC];
+#pragma unroll
+    for (int o = 0; o < kMaxC; ++o) acc[o] = o < C ? bs[o] : 0.f;
     const float2 step = tw[x];
     float2 e = make_float2(1.f, 0.f);
-    float s = 0.f;
     for (int kx = 0; kx < m; ++kx) {
       if (kx % kReseed == 0 && kx > 0) e = tw[(int)(((long long)kx * x) % W)];
-      const float2 v = zs[kx * C + o];
-      const float t = v.x * e.x - v.y * e.y;
-      s += (kx == 0 ? 1.0f : 2.0f) * t;
+      const float2* zk = zs + kx * C;
+#pragma unroll
+      for (int o = 0; o < kMaxC; ++o)
+        if (o < C) acc[o] = fmaf(zk[o].x, e.x, fmaf(-zk[o].y, e.y, acc[o]));
       e = cmul(e, step);
     }
-    float a = fmaf(s, inv_hw, bo);
-    const __nv_bfloat16* tv = src + (size_t)x * C;
-    for (int i = 0; i < C; ++i) a = fmaf(wt[i * C + o], __bfloat162float(tv[i]), a);
-    dst[(size_t)x * C + o] = __float2bfloat16_rn(act_fn(a, act));
+    const __nv_bfloat162* tv = reinterpret_cast<const __nv_bfloat162*>(src + (size_t)x * C);
+    for (int i2 = 0; i2 < C / 2; ++i2) {
+      const float2 t = __bfloat1622float2(tv[i2]);
+#pragma unroll
+      for (int o = 0; o < kMaxC; ++o)
+        if (o < C) acc[o] = fmaf(wt[(2 * i2 + 1) * C + o], t.y, fmaf(wt[2 * i2 * C + o], t.x, acc[o]));
+    }
+    __nv_bfloat162* dv = reinterpret_cast<__nv_bfloat162*>(dst + (size_t)x * C);
+#pragma unroll
+    for (int o = 0; o < kMaxC; o += 2)
+      if (o < C) dv[o / 2] = __floats2bfloat162_rn(act_fn(acc[o], act), act_fn(acc[o + 1], act));
   }
 }
 
@@ -492,6 +560,39 @@ static int launch_fwd_y(int blocks, int threads, size_t smem, cudaStream_t s, co
   return LBM_OK;
 }
 
+static size_t fwd_x_row_smem(int W, int C) {
+  const int kmax = C <= 16 ? 16 : 32;
+  return (size_t)W * sizeof(float2) + (size_t)kFxRowsPerBlock * kFxChunk * kmax * sizeof(float);
+}
+static int launch_fwd_x_row(int rows, cudaStream_t s, const __nv_bfloat16* th, float2* x1,
+                            const float2* twx, int W, int C, int m) {
+  const unsigned blocks = (unsigned)((rows + kFxRowsPerBlock - 1) / kFxRowsPerBlock);
+  const size_t smem = fwd_x_row_smem(W, C);
+  if (C <= 16)
+    k_fwd_x_row<16><<<blocks, 32 * kFxRowsPerBlock, smem, s>>>(th, x1, twx, rows, W, C, m);
+  else
+    k_fwd_x_row<32><<<blocks, 32 * kFxRowsPerBlock, smem, s>>>(th, x1, twx, rows, W, C, m);
+  LBM_CHECK_LAUNCH();
+  return LBM_OK;
+}
+static size_t inv_x_row_smem(int W, int C, int m) {
+  return (size_t)(C * C + C + (C & 1)) * sizeof(float) + (size_t)(m * C + W) * sizeof(float2);
+}
+static int launch_inv_x_row(int rows, cudaStream_t s, const __nv_bfloat16* th, const float2* z,
+                            const float* w, const float* b, __nv_bfloat16* out,
+                            const float2* twx, int H, int W, int C, int m, int act) {
+  const int threads = std::min(256, (W + 31) / 32 * 32);
+  const size_t smem = inv_x_row_smem(W, C, m);
+  if (C <= 16)
+    k_inv_x_row<16><<<rows, threads, smem, s>>>(th, z, w, b, out, twx, H, W, C, m, act);
+  else if (C <= 32)
+    k_inv_x_row<32><<<rows, threads, smem, s>>>(th, z, w, b, out, twx, H, W, C, m, act);
+  else
+    k_inv_x_row<64><<<rows, threads, smem, s>>>(th, z, w, b, out, twx, H, W, C, m, act);
+  LBM_CHECK_LAUNCH();
+  return LBM_OK;
+}
+
 template <typename K>
 static bool raise_smem(K kernel) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -546,7 +647,9 @@ int fno_create(const fno_config* cfg_h, const uint16_t* params_d, void* packed_d
   if (!raise_smem(k_fwd_x<1>) || !raise_smem(k_fwd_x<2>) || !raise_smem(k_fwd_x<4>) ||
       !raise_smem(k_fwd_x<8>) || !raise_smem(k_fwd_x<16>) || !raise_smem(k_fwd_y<1>) ||
       !raise_smem(k_fwd_y<2>) || !raise_smem(k_fwd_y<4>) || !raise_smem(k_fwd_y<8>) ||
-      !raise_smem(k_fwd_y<16>) || !raise_smem(k_inv_x_w) ||
+      !raise_smem(k_fwd_y<16>) || !raise_smem(k_fwd_x_row<16>) || !raise_smem(k_fwd_x_row<32>) ||
+      !raise_smem(k_inv_x_row<16>) || !raise_smem(k_inv_x_row<32>) ||
+      !raise_smem(k_inv_x_row<64>) ||
       fno_tc_prepare(*cfg_h) != LBM_OK) {
     set_error("fno_create: %s", cudaGetErrorString(cudaGetLastError()));
     delete h;
@@ -634,24 +737,26 @@ int fno_forward(fno_handle* h, const float* in_d, float* out_d, int B, int H, in
   LBM_CHECK_LAUNCH();
   const int rows = B * H;
   const size_t smem_fx = (size_t)W * C * sizeof(float) + (size_t)W * sizeof(float2);
-  const size_t smem_ix = (size_t)C * C * sizeof(float) + (size_t)m * C * sizeof(float2) +
-                         (size_t)W * sizeof(float2);
+  const size_t smem_ix = inv_x_row_smem(W, C, m);
   LBM_REQUIRE(((size_t)H + kFwdYRows * C) * sizeof(float2) <= kRowSmemMax,
               "fno_forward: H too large for the y-DFT kernel");
-  LBM_REQUIRE(smem_fx <= kRowSmemMax && smem_ix <= kRowSmemMax,
+  LBM_REQUIRE(smem_fx <= kRowSmemMax && smem_ix <= kRowSmemMax &&
+                  fwd_x_row_smem(W, C) <= kRowSmemMax,
               "fno_forward: W * C too large for the row kernels");
   const int cur_threads = 256;
   int cur = 0;
   for (int n = 0; n < c.layers; ++n) {
-    LBM_TRY(launch_fwd_x(rows, cur_threads, smem_fx, s, th[cur], x1, twx, H, W, C, m));
+    if (C <= 32)
+      LBM_TRY(launch_fwd_x_row(rows, s, th[cur], x1, twx, W, C, m));
+    else
+      LBM_TRY(launch_fwd_x(rows, cur_threads, smem_fx, s, th[cur], x1, twx, H, W, C, m));
     LBM_TRY(launch_fwd_y(B * m, cur_threads, ((size_t)H + kFwdYRows * C) * sizeof(float2), s, x1,
                          xh, twy, H, C, m));
     k_mix<<<2 * m * m, cur_threads, (size_t)C * C * sizeof(float2), s>>>(
         xh, yh, reinterpret_cast<const float2*>(P + o.rt_off + o.rt_layer * n), B, C, 2 * m * m);
     k_inv_y<<<B * m, cur_threads, (size_t)2 * m * C * sizeof(float2), s>>>(yh, z, twy, H, C, m);
-    k_inv_x_w<<<rows, cur_threads, smem_ix, s>>>(th[cur], z, P + o.w[n], P + o.b[n],
-                                                 th[cur ^ 1], twx, H, W, C, m, c.activation);
-    LBM_CHECK_LAUNCH();
+    LBM_TRY(launch_inv_x_row(rows, s, th[cur], z, P + o.w[n], P + o.b[n], th[cur ^ 1], twx, H,
+                             W, C, m, c.activation));
     cur ^= 1;
   }
   const size_t pix = (size_t)B * H0 * W0;
