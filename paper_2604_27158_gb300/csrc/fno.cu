@@ -369,6 +369,84 @@ __global__ void k_fwd_y(const float2* __restrict__ x1, float2* __restrict__ xh,
   }
 }
 
+// Forward y-DFT with one thread per kept row a and all C channels in registers: each
+// thread advances its twiddle e^{+i ky y phi} once per row and applies it to every
+// channel of the staged tile (broadcast reads).  C <= kMaxC <= 32.
+template <int kMaxC>
+__global__ void k_fwd_y_row(const float2* __restrict__ x1, float2* __restrict__ xh,
+                            const float2* __restrict__ twy, int H, int C, int m) {
+  extern __shared__ float2 fy_s[];  // twiddles [H], then a [kFwdYRows][C] tile
+  float2* tile = fy_s + H;
+  const int b = blockIdx.x / m, kx = blockIdx.x % m;
+  for (int t = threadIdx.x; t < H; t += blockDim.x) fy_s[t] = twy[t];
+  const int a = min((int)threadIdx.x, 2 * m - 1);
+  const int ky = kept_ky(a, H, m);
+  float2 acc[kMaxC];
+#pragma unroll
+  for (int c = 0; c < kMaxC; ++c) acc[c] = make_float2(0.f, 0.f);
+  for (int y0 = 0; y0 < H; y0 += kFwdYRows) {
+    const int ny = min(kFwdYRows, H - y0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < ny * C; t += blockDim.x) {
+      const int yy = t / C, cc = t - yy * C;
+      tile[t] = x1[(((size_t)b * H + y0 + yy) * m + kx) * C + cc];
+    }
+    __syncthreads();
+    float2 e = fy_s[(int)(((long long)ky * y0) % H)];
+    const float2 step = fy_s[ky];
+    for (int yy = 0; yy < ny; ++yy) {
+      const float2* v = tile + yy * C;
+#pragma unroll
+      for (int c = 0; c < kMaxC; ++c)
+        if (c < C) {  // v e^{-i phi} = v conj(e)
+          acc[c].x += v[c].x * e.x + v[c].y * e.y;
+          acc[c].y += v[c].y * e.x - v[c].x * e.y;
+        }
+      e = cmul(e, step);
+    }
+  }
+  if ((int)threadIdx.x < 2 * m) {
+#pragma unroll
+    for (int c = 0; c < kMaxC; ++c)
+      if (c < C) xh[(((size_t)b * 2 * m + a) * m + kx) * C + c] = acc[c];
+  }
+}
+
+// Inverse y-DFT with one thread per row y and all C channels in registers (the twiddle
+// advanced once per kept row and applied to every channel).  C <= kMaxC <= 32.
+template <int kMaxC>
+__global__ void k_inv_y_row(const float2* __restrict__ yh, float2* __restrict__ z,
+                            const float2* __restrict__ twy, int H, int C, int m) {
+  extern __shared__ float2 ys[];  // 2m * C
+  const int b = blockIdx.x / m, kx = blockIdx.x % m;
+  for (int t = threadIdx.x; t < 2 * m * C; t += blockDim.x) {
+    const int a = t / C, o = t % C;
+    ys[t] = yh[(((size_t)b * 2 * m + a) * m + kx) * C + o];
+  }
+  __syncthreads();
+  for (int y = threadIdx.x; y < H; y += blockDim.x) {
+    float2 acc[kMaxC];
+#pragma unroll
+    for (int o = 0; o < kMaxC; ++o) acc[o] = make_float2(0.f, 0.f);
+    const float2 step = twy[y];
+    float2 e = make_float2(1.f, 0.f);
+    for (int a = 0; a < 2 * m; ++a) {
+      if (a % kReseed == 0 || a == m) e = twy[(int)(((long long)kept_ky(a, H, m) * y) % H)];
+      const float2* v = ys + a * C;
+#pragma unroll
+      for (int o = 0; o < kMaxC; ++o)
+        if (o < C) {
+          acc[o].x += v[o].x * e.x - v[o].y * e.y;
+          acc[o].y += v[o].x * e.y + v[o].y * e.x;
+        }
+      e = cmul(e, step);
+    }
+#pragma unroll
+    for (int o = 0; o < kMaxC; ++o)
+      if (o < C) z[(((size_t)b * H + y) * m + kx) * C + o] = acc[o];
+  }
+}
+
 // Per-mode complex channel mixing: Yh[b][mode][o] = sum_i Xh[b][mode][i] R[mode][i][o].
 __global__ void k_mix(const float2* __restrict__ xh, float2* __restrict__ yh,
                       const float2* __restrict__ rt, int B, int C, int modes) {
@@ -593,6 +671,26 @@ static int launch_inv_x_row(int rows, cudaStream_t s, const __nv_bfloat16* th, c
   return LBM_OK;
 }
 
+// The y-DFT pair for C <= 32: the forward one (x1 -> xh) when x1 is given, else the
+// inverse one (yh -> z).
+static int launch_y_rows(int B, cudaStream_t s, const float2* x1, float2* xh, const float2* yh,
+                         float2* z, const float2* twy, int H, int C, int m) {
+  const unsigned blocks = (unsigned)(B * m);
+  if (x1 != nullptr) {
+    const int threads = (2 * m + 31) / 32 * 32;
+    const size_t smem = ((size_t)H + kFwdYRows * C) * sizeof(float2);
+    if (C <= 16) k_fwd_y_row<16><<<blocks, threads, smem, s>>>(x1, xh, twy, H, C, m);
+    else k_fwd_y_row<32><<<blocks, threads, smem, s>>>(x1, xh, twy, H, C, m);
+  } else {
+    const int threads = std::min(256, (H + 31) / 32 * 32);
+    const size_t smem = (size_t)2 * m * C * sizeof(float2);
+    if (C <= 16) k_inv_y_row<16><<<blocks, threads, smem, s>>>(yh, z, twy, H, C, m);
+    else k_inv_y_row<32><<<blocks, threads, smem, s>>>(yh, z, twy, H, C, m);
+  }
+  LBM_CHECK_LAUNCH();
+  return LBM_OK;
+}
+
 template <typename K>
 static bool raise_smem(K kernel) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -649,7 +747,9 @@ int fno_create(const fno_config* cfg_h, const uint16_t* params_d, void* packed_d
       !raise_smem(k_fwd_y<2>) || !raise_smem(k_fwd_y<4>) || !raise_smem(k_fwd_y<8>) ||
       !raise_smem(k_fwd_y<16>) || !raise_smem(k_fwd_x_row<16>) || !raise_smem(k_fwd_x_row<32>) ||
       !raise_smem(k_inv_x_row<16>) || !raise_smem(k_inv_x_row<32>) ||
-      !raise_smem(k_inv_x_row<64>) ||
+      !raise_smem(k_inv_x_row<64>) || !raise_smem(k_fwd_y_row<16>) ||
+      !raise_smem(k_fwd_y_row<32>) || !raise_smem(k_inv_y_row<16>) ||
+      !raise_smem(k_inv_y_row<32>) ||
       fno_tc_prepare(*cfg_h) != LBM_OK) {
     set_error("fno_create: %s", cudaGetErrorString(cudaGetLastError()));
     delete h;
@@ -750,11 +850,17 @@ int fno_forward(fno_handle* h, const float* in_d, float* out_d, int B, int H, in
       LBM_TRY(launch_fwd_x_row(rows, s, th[cur], x1, twx, W, C, m));
     else
       LBM_TRY(launch_fwd_x(rows, cur_threads, smem_fx, s, th[cur], x1, twx, H, W, C, m));
-    LBM_TRY(launch_fwd_y(B * m, cur_threads, ((size_t)H + kFwdYRows * C) * sizeof(float2), s, x1,
-                         xh, twy, H, C, m));
+    if (C <= 32 && 2 * m >= 32)  // one thread per kept row: worth it from a full warp of rows
+      LBM_TRY(launch_y_rows(B, s, x1, xh, nullptr, nullptr, twy, H, C, m));
+    else
+      LBM_TRY(launch_fwd_y(B * m, cur_threads, ((size_t)H + kFwdYRows * C) * sizeof(float2), s,
+                           x1, xh, twy, H, C, m));
     k_mix<<<2 * m * m, cur_threads, (size_t)C * C * sizeof(float2), s>>>(
         xh, yh, reinterpret_cast<const float2*>(P + o.rt_off + o.rt_layer * n), B, C, 2 * m * m);
-    k_inv_y<<<B * m, cur_threads, (size_t)2 * m * C * sizeof(float2), s>>>(yh, z, twy, H, C, m);
+    if (C <= 32)
+      LBM_TRY(launch_y_rows(B, s, nullptr, nullptr, yh, z, twy, H, C, m));
+    else
+      k_inv_y<<<B * m, cur_threads, (size_t)2 * m * C * sizeof(float2), s>>>(yh, z, twy, H, C, m);
     LBM_TRY(launch_inv_x_row(rows, s, th[cur], z, P + o.w[n], P + o.b[n], th[cur ^ 1], twx, H,
                              W, C, m, c.activation));
     cur ^= 1;
