@@ -154,41 +154,6 @@ __global__ void k_twiddle(float2* __restrict__ tw, int N) {
   }
 }
 
-// Lifting network P with the two coordinate channels; one thread per pixel.
-// The latent field lives on the padded grid Hp x Wp (Hp = H + padding): pixels outside
-// the H x W input are zero (padding after lifting).
-__global__ void k_lift(const float* __restrict__ in, __nv_bfloat16* __restrict__ theta,
-                       const float* __restrict__ w0, const float* __restrict__ b0,
-                       const float* __restrict__ w1, const float* __restrict__ b1, int B, int H,
-                       int W, int Hp, int Wp, int cin, int C, int act) {
-  const size_t pix = (size_t)B * Hp * Wp;
-  const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (p >= pix) return;
-  const int x = (int)(p % Wp);
-  const int y = (int)((p / Wp) % Hp);
-  const int b = (int)(p / ((size_t)Wp * Hp));
-  if (x >= W || y >= H) {
-    for (int o = 0; o < C; ++o) theta[p * C + o] = __float2bfloat16_rn(0.0f);
-    return;
-  }
-  float xin[18];
-  for (int c = 0; c < cin; ++c) xin[c] = bf16r(in[(((size_t)b * cin + c) * H + y) * W + x]);
-  xin[cin] = bf16r((float)x / (float)max(W - 1, 1));
-  xin[cin + 1] = bf16r((float)y / (float)max(H - 1, 1));
-  const int h = C / 2, cin2 = cin + 2;
-  float hid[32];
-  for (int j = 0; j < h; ++j) {
-    float a = b0[j];
-    for (int c = 0; c < cin2; ++c) a = fmaf(w0[j * cin2 + c], xin[c], a);
-    hid[j] = act_fn(a, act);
-  }
-  __nv_bfloat16* out = theta + p * C;
-  for (int o = 0; o < C; ++o) {
-    float a = b1[o];
-    for (int j = 0; j < h; ++j) a = fmaf(w1[o * h + j], hid[j], a);
-    out[o] = __float2bfloat16_rn(a);
-  }
-}
 
 // Twiddles by recurrence: e^{i k (n+1) phi} = e^{i k n phi} e^{i k phi}, a complex product
 // in registers instead of a shared-memory table load per term; the product is re-seeded
@@ -555,6 +520,112 @@ __global__ void k_inv_x_row(const __nv_bfloat16* __restrict__ theta, const float
   }
 }
 
+// Lifting network with register-resident inputs and hidden units (C <= kMaxC): zero
+// for the padding pixels, else P = 1x1 (c_in + 2) -> C/2 -> act -> C.
+template <int kMaxC>
+__global__ void k_lift_reg(const float* __restrict__ in, __nv_bfloat16* __restrict__ theta,
+                           const float* __restrict__ w0, const float* __restrict__ b0,
+                           const float* __restrict__ w1, const float* __restrict__ b1, int B,
+                           int H, int W, int Hp, int Wp, int cin, int C, int act) {
+  const size_t pix = (size_t)B * Hp * Wp;
+  const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (p >= pix) return;
+  const int x = (int)(p % Wp);
+  const int y = (int)((p / Wp) % Hp);
+  const int b = (int)(p / ((size_t)Wp * Hp));
+  __nv_bfloat162* out = reinterpret_cast<__nv_bfloat162*>(theta + p * C);  // C even
+  if (x >= W || y >= H) {
+    for (int o = 0; o < C / 2; ++o) out[o] = __floats2bfloat162_rn(0.0f, 0.0f);
+    return;
+  }
+  float xin[18];
+#pragma unroll
+  for (int c = 0; c < 16; ++c)
+    if (c < cin) xin[c] = bf16r(in[(((size_t)b * cin + c) * H + y) * W + x]);
+  const float gx = bf16r((float)x / (float)max(W - 1, 1));
+  const float gy = bf16r((float)y / (float)max(H - 1, 1));
+  const int h = C / 2, cin2 = cin + 2;
+  float hid[kMaxC / 2];
+#pragma unroll
+  for (int j = 0; j < kMaxC / 2; ++j) {
+    float a = 0.f;
+    if (j < h) {
+      a = b0[j];
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        if (c < cin) a = fmaf(w0[j * cin2 + c], xin[c], a);
+      a = fmaf(w0[j * cin2 + cin], gx, a);
+      a = fmaf(w0[j * cin2 + cin + 1], gy, a);
+      a = act_fn(a, act);
+    }
+    hid[j] = a;
+  }
+#pragma unroll
+  for (int o = 0; o < kMaxC; o += 2)
+    if (o < C) {
+      float a0 = b1[o], a1 = b1[o + 1];
+#pragma unroll
+      for (int j = 0; j < kMaxC / 2; ++j)
+        if (j < h) {
+          a0 = fmaf(w1[o * h + j], hid[j], a0);
+          a1 = fmaf(w1[(o + 1) * h + j], hid[j], a1);
+        }
+      out[o / 2] = __floats2bfloat162_rn(a0, a1);
+    }
+}
+
+// Projection Q with one hidden layer, register-resident (C <= kMaxC, c_out <= 4): each
+// hidden unit is computed, activated and folded into the outputs at once; the weights
+// are staged in shared memory (broadcast reads).
+template <int kMaxC>
+__global__ void k_decoder1_reg(const __nv_bfloat16* __restrict__ theta, float* __restrict__ out,
+                               const float* __restrict__ params, const unsigned* __restrict__ offs,
+                               int B, int H, int W, int Hp, int Wp, int C, int S, int cout,
+                               int act) {
+  extern __shared__ float dec_s[];
+  float* w1 = dec_s;           // S * C
+  float* b1 = w1 + S * C;      // S
+  float* w2 = b1 + S;          // cout * S
+  float* b2 = w2 + cout * S;   // cout
+  for (int t = threadIdx.x; t < S * C; t += blockDim.x) w1[t] = params[offs[0] + t];
+  for (int t = threadIdx.x; t < S; t += blockDim.x) b1[t] = params[offs[1] + t];
+  for (int t = threadIdx.x; t < cout * S; t += blockDim.x) w2[t] = params[offs[2] + t];
+  for (int t = threadIdx.x; t < cout; t += blockDim.x) b2[t] = params[offs[3] + t];
+  __syncthreads();
+  const size_t pix = (size_t)B * H * W;
+  const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (p >= pix) return;
+  const int x = (int)(p % W);
+  const int y = (int)((p / W) % H);
+  const int b = (int)(p / ((size_t)W * H));
+  const __nv_bfloat162* src =
+      reinterpret_cast<const __nv_bfloat162*>(theta + (((size_t)b * Hp + y) * Wp + x) * C);
+  float a[kMaxC];
+#pragma unroll
+  for (int c = 0; c < kMaxC; c += 2) {
+    const float2 v = c < C ? __bfloat1622float2(src[c / 2]) : make_float2(0.f, 0.f);
+    a[c] = v.x;
+    a[c + 1] = v.y;
+  }
+  float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (q < cout) o[q] = b2[q];
+  for (int j = 0; j < S; ++j) {
+    float v = b1[j];
+#pragma unroll
+    for (int c = 0; c < kMaxC; ++c)
+      if (c < C) v = fmaf(w1[j * C + c], a[c], v);
+    v = act_fn(v, act);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (q < cout) o[q] = fmaf(w2[q * S + j], v, o[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (q < cout) out[(((size_t)b * cout + q) * H + y) * W + x] = o[q];
+}
+
 // Projection Q: hidden layers with the activation, then the linear output layer.
 // Reads the H x W corner of the padded latent field (the crop after the last layer).
 __global__ void k_decoder(const __nv_bfloat16* __restrict__ theta, float* __restrict__ out,
@@ -830,10 +901,21 @@ int fno_forward(fno_handle* h, const float* in_d, float* out_d, int B, int H, in
   k_twiddle<<<(W + 255) / 256, 256, 0, s>>>(twx, W);
   k_twiddle<<<(H + 255) / 256, 256, 0, s>>>(twy, H);
   const size_t pix_p = (size_t)B * H * W;
-  k_lift<<<(unsigned)((pix_p + 127) / 128), 128, 0, s>>>(in_d, th[0], P + o.lift0_w,
-                                                         P + o.lift0_b, P + o.lift1_w,
-                                                         P + o.lift1_b, B, H0, W0, H, W, c.c_in,
-                                                         C, c.activation);
+  {
+    const unsigned blocks = (unsigned)((pix_p + 127) / 128);
+    if (C <= 16)
+      k_lift_reg<16><<<blocks, 128, 0, s>>>(in_d, th[0], P + o.lift0_w, P + o.lift0_b,
+                                            P + o.lift1_w, P + o.lift1_b, B, H0, W0, H, W, c.c_in,
+                                            C, c.activation);
+    else if (C <= 32)
+      k_lift_reg<32><<<blocks, 128, 0, s>>>(in_d, th[0], P + o.lift0_w, P + o.lift0_b,
+                                            P + o.lift1_w, P + o.lift1_b, B, H0, W0, H, W, c.c_in,
+                                            C, c.activation);
+    else
+      k_lift_reg<64><<<blocks, 128, 0, s>>>(in_d, th[0], P + o.lift0_w, P + o.lift0_b,
+                                            P + o.lift1_w, P + o.lift1_b, B, H0, W0, H, W, c.c_in,
+                                            C, c.activation);
+  }
   LBM_CHECK_LAUNCH();
   const int rows = B * H;
   const size_t smem_fx = (size_t)W * C * sizeof(float) + (size_t)W * sizeof(float2);
@@ -866,9 +948,19 @@ int fno_forward(fno_handle* h, const float* in_d, float* out_d, int B, int H, in
     cur ^= 1;
   }
   const size_t pix = (size_t)B * H0 * W0;
-  k_decoder<<<(unsigned)((pix + 127) / 128), 128, 0, s>>>(th[cur], out_d, P, h->dec_offs,
-                                                          c.dec_layers, B, H0, W0, H, W, C,
-                                                          c.dec_size, c.c_out, c.activation);
+  const unsigned dblocks = (unsigned)((pix + 127) / 128);
+  const size_t dsmem = ((size_t)c.dec_size * C + c.dec_size + (size_t)c.c_out * c.dec_size + c.c_out) * sizeof(float);
+  if (c.dec_layers == 1 && c.c_out <= 4 && C <= 32) {
+    if (C <= 16)
+      k_decoder1_reg<16><<<dblocks, 128, dsmem, s>>>(th[cur], out_d, P, h->dec_offs, B, H0, W0, H,
+                                                     W, C, c.dec_size, c.c_out, c.activation);
+    else
+      k_decoder1_reg<32><<<dblocks, 128, dsmem, s>>>(th[cur], out_d, P, h->dec_offs, B, H0, W0, H,
+                                                     W, C, c.dec_size, c.c_out, c.activation);
+  } else {
+    k_decoder<<<dblocks, 128, 0, s>>>(th[cur], out_d, P, h->dec_offs, c.dec_layers, B, H0, W0, H,
+                                      W, C, c.dec_size, c.c_out, c.activation);
+  }
   LBM_CHECK_LAUNCH();
   return LBM_OK;
 }
