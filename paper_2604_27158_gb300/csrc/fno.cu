@@ -472,51 +472,62 @@ __global__ void k_inv_x_row(const __nv_bfloat16* __restrict__ theta, const float
                             __nv_bfloat16* __restrict__ out, const float2* __restrict__ twx,
                             int H, int W, int C, int m, int act) {
   extern __shared__ float smem_f[];
-  float* wt = smem_f;                                      // C * C, [i][o]
-  float* bs = wt + C * C;                                  // C
-  float2* zs = reinterpret_cast<float2*>(bs + C + (C & 1));  // m * C, scaled
-  float2* tw = zs + m * C;                                 // W
+  // channel pairs (o, o + 1) on packed FP32: wt2[i][o/2] = (W[o][i], W[o+1][i]),
+  // zs4[kx][o/2] = (Re Z[o], Re Z[o+1], -Im Z[o], -Im Z[o+1]) * c_kx / (H W)
+  const int C2 = C / 2;
+  float4* zs4 = reinterpret_cast<float4*>(smem_f);          // m * C2
+  float2* wt2 = reinterpret_cast<float2*>(zs4 + m * C2);   // C * C2
+  float2* bs2 = wt2 + C * C2;                               // C2
+  float2* tw = bs2 + C2;                                    // W
   const size_t r = blockIdx.x;
-  for (int t = threadIdx.x; t < C * C; t += blockDim.x) {
-    const int i = t / C, o = t % C;
-    wt[t] = wmat[o * C + i];
+  for (int t = threadIdx.x; t < C * C2; t += blockDim.x) {
+    const int i = t / C2, o = 2 * (t % C2);
+    wt2[t] = make_float2(wmat[o * C + i], wmat[(o + 1) * C + i]);
   }
-  for (int t = threadIdx.x; t < C; t += blockDim.x) bs[t] = bias[t];
+  for (int t = threadIdx.x; t < C2; t += blockDim.x) bs2[t] = make_float2(bias[2 * t], bias[2 * t + 1]);
   const float inv_hw = 1.0f / ((float)H * (float)W);
-  for (int t = threadIdx.x; t < m * C; t += blockDim.x) {
-    const float2 v = z[r * m * C + t];
-    const float w = (t < C ? 1.0f : 2.0f) * inv_hw;  // kx = t / C; kx = 0 weight 1
-    zs[t] = make_float2(v.x * w, v.y * w);
+  for (int t = threadIdx.x; t < m * C2; t += blockDim.x) {
+    const int kx = t / C2, o = 2 * (t % C2);
+    const float2 v0 = z[(r * m + kx) * C + o], v1 = z[(r * m + kx) * C + o + 1];
+    const float w = (kx == 0 ? 1.0f : 2.0f) * inv_hw;
+    zs4[t] = make_float4(v0.x * w, v1.x * w, -v0.y * w, -v1.y * w);
   }
   for (int t = threadIdx.x; t < W; t += blockDim.x) tw[t] = twx[t];
   __syncthreads();
   const __nv_bfloat16* src = theta + r * (size_t)W * C;
   __nv_bfloat16* dst = out + r * (size_t)W * C;
   for (int x = threadIdx.x; x < W; x += blockDim.x) {
-    float acc[kMaxC];
+    float2 acc[kMaxC / 2];
 #pragma unroll
-    for (int o = 0; o < kMaxC; ++o) acc[o] = o < C ? bs[o] : 0.f;
+    for (int q = 0; q < kMaxC / 2; ++q) acc[q] = q < C2 ? bs2[q] : make_float2(0.f, 0.f);
     const float2 step = tw[x];
     float2 e = make_float2(1.f, 0.f);
     for (int kx = 0; kx < m; ++kx) {
       if (kx % kReseed == 0 && kx > 0) e = tw[(int)(((long long)kx * x) % W)];
-      const float2* zk = zs + kx * C;
+      const float4* zk = zs4 + kx * C2;
+      const float2 ex = make_float2(e.x, e.x), ey = make_float2(e.y, e.y);
 #pragma unroll
-      for (int o = 0; o < kMaxC; ++o)
-        if (o < C) acc[o] = fmaf(zk[o].x, e.x, fmaf(-zk[o].y, e.y, acc[o]));
+      for (int q = 0; q < kMaxC / 2; ++q)
+        if (q < C2) {
+          const float4 v = zk[q];
+          acc[q] = __ffma2_rn(make_float2(v.z, v.w), ey, __ffma2_rn(make_float2(v.x, v.y), ex, acc[q]));
+        }
       e = cmul(e, step);
     }
     const __nv_bfloat162* tv = reinterpret_cast<const __nv_bfloat162*>(src + (size_t)x * C);
-    for (int i2 = 0; i2 < C / 2; ++i2) {
+    for (int i2 = 0; i2 < C2; ++i2) {
       const float2 t = __bfloat1622float2(tv[i2]);
+      const float2 tx = make_float2(t.x, t.x), ty = make_float2(t.y, t.y);
+      const float2* w0 = wt2 + (2 * i2) * C2;
+      const float2* w1 = w0 + C2;
 #pragma unroll
-      for (int o = 0; o < kMaxC; ++o)
-        if (o < C) acc[o] = fmaf(wt[(2 * i2 + 1) * C + o], t.y, fmaf(wt[2 * i2 * C + o], t.x, acc[o]));
+      for (int q = 0; q < kMaxC / 2; ++q)
+        if (q < C2) acc[q] = __ffma2_rn(w1[q], ty, __ffma2_rn(w0[q], tx, acc[q]));
     }
     __nv_bfloat162* dv = reinterpret_cast<__nv_bfloat162*>(dst + (size_t)x * C);
 #pragma unroll
-    for (int o = 0; o < kMaxC; o += 2)
-      if (o < C) dv[o / 2] = __floats2bfloat162_rn(act_fn(acc[o], act), act_fn(acc[o + 1], act));
+    for (int q = 0; q < kMaxC / 2; ++q)
+      if (q < C2) dv[q] = __floats2bfloat162_rn(act_fn(acc[q].x, act), act_fn(acc[q].y, act));
   }
 }
 
@@ -725,7 +736,7 @@ static int launch_fwd_x_row(int rows, cudaStream_t s, const __nv_bfloat16* th, f
   return LBM_OK;
 }
 static size_t inv_x_row_smem(int W, int C, int m) {
-  return (size_t)(C * C + C + (C & 1)) * sizeof(float) + (size_t)(m * C + W) * sizeof(float2);
+  return (size_t)m * (C / 2) * sizeof(float4) + (size_t)(C * (C / 2) + C / 2 + W) * sizeof(float2);
 }
 static int launch_inv_x_row(int rows, cudaStream_t s, const __nv_bfloat16* th, const float2* z,
                             const float* w, const float* b, __nv_bfloat16* out,
