@@ -341,7 +341,8 @@ template <int kMaxC>
 __global__ void k_fwd_y_row(const float2* __restrict__ x1, float2* __restrict__ xh,
                             const float2* __restrict__ twy, int H, int C, int m) {
   extern __shared__ float2 fy_s[];  // twiddles [H], then a [kFwdYRows][C] tile
-  float2* tile = fy_s + H;
+  // tile entries (Re v, Im v, Im v, -Re v): v conj(e) = (Re v, Im v) e.x + (Im v, -Re v) e.y
+  float4* tile = reinterpret_cast<float4*>(fy_s + H + (H & 1));
   const int b = blockIdx.x / m, kx = blockIdx.x % m;
   for (int t = threadIdx.x; t < H; t += blockDim.x) fy_s[t] = twy[t];
   const int a = min((int)threadIdx.x, 2 * m - 1);
@@ -354,18 +355,20 @@ __global__ void k_fwd_y_row(const float2* __restrict__ x1, float2* __restrict__ 
     __syncthreads();
     for (int t = threadIdx.x; t < ny * C; t += blockDim.x) {
       const int yy = t / C, cc = t - yy * C;
-      tile[t] = x1[(((size_t)b * H + y0 + yy) * m + kx) * C + cc];
+      const float2 v = x1[(((size_t)b * H + y0 + yy) * m + kx) * C + cc];
+      tile[t] = make_float4(v.x, v.y, v.y, -v.x);
     }
     __syncthreads();
     float2 e = fy_s[(int)(((long long)ky * y0) % H)];
     const float2 step = fy_s[ky];
     for (int yy = 0; yy < ny; ++yy) {
-      const float2* v = tile + yy * C;
+      const float4* v = tile + yy * C;
+      const float2 ex = make_float2(e.x, e.x), ey = make_float2(e.y, e.y);
 #pragma unroll
       for (int c = 0; c < kMaxC; ++c)
-        if (c < C) {  // v e^{-i phi} = v conj(e)
-          acc[c].x += v[c].x * e.x + v[c].y * e.y;
-          acc[c].y += v[c].y * e.x - v[c].x * e.y;
+        if (c < C) {
+          const float4 q = v[c];
+          acc[c] = __ffma2_rn(make_float2(q.z, q.w), ey, __ffma2_rn(make_float2(q.x, q.y), ex, acc[c]));
         }
       e = cmul(e, step);
     }
@@ -382,11 +385,13 @@ __global__ void k_fwd_y_row(const float2* __restrict__ x1, float2* __restrict__ 
 template <int kMaxC>
 __global__ void k_inv_y_row(const float2* __restrict__ yh, float2* __restrict__ z,
                             const float2* __restrict__ twy, int H, int C, int m) {
-  extern __shared__ float2 ys[];  // 2m * C
+  // entries (Re v, Re v, -Im v, Im v): v e = (Re v, Re v)(e.x, e.y) + (-Im v, Im v)(e.y, e.x)
+  extern __shared__ float4 ys4[];  // 2m * C
   const int b = blockIdx.x / m, kx = blockIdx.x % m;
   for (int t = threadIdx.x; t < 2 * m * C; t += blockDim.x) {
     const int a = t / C, o = t % C;
-    ys[t] = yh[(((size_t)b * 2 * m + a) * m + kx) * C + o];
+    const float2 v = yh[(((size_t)b * 2 * m + a) * m + kx) * C + o];
+    ys4[t] = make_float4(v.x, v.x, -v.y, v.y);
   }
   __syncthreads();
   for (int y = threadIdx.x; y < H; y += blockDim.x) {
@@ -397,12 +402,13 @@ __global__ void k_inv_y_row(const float2* __restrict__ yh, float2* __restrict__ 
     float2 e = make_float2(1.f, 0.f);
     for (int a = 0; a < 2 * m; ++a) {
       if (a % kReseed == 0 || a == m) e = twy[(int)(((long long)kept_ky(a, H, m) * y) % H)];
-      const float2* v = ys + a * C;
+      const float4* v = ys4 + a * C;
+      const float2 e1 = e, e2 = make_float2(e.y, e.x);
 #pragma unroll
       for (int o = 0; o < kMaxC; ++o)
         if (o < C) {
-          acc[o].x += v[o].x * e.x - v[o].y * e.y;
-          acc[o].y += v[o].x * e.y + v[o].y * e.x;
+          const float4 q = v[o];
+          acc[o] = __ffma2_rn(make_float2(q.z, q.w), e2, __ffma2_rn(make_float2(q.x, q.y), e1, acc[o]));
         }
       e = cmul(e, step);
     }
@@ -760,12 +766,12 @@ static int launch_y_rows(int B, cudaStream_t s, const float2* x1, float2* xh, co
   const unsigned blocks = (unsigned)(B * m);
   if (x1 != nullptr) {
     const int threads = (2 * m + 31) / 32 * 32;
-    const size_t smem = ((size_t)H + kFwdYRows * C) * sizeof(float2);
+    const size_t smem = ((size_t)H + 1) * sizeof(float2) + (size_t)kFwdYRows * C * sizeof(float4);
     if (C <= 16) k_fwd_y_row<16><<<blocks, threads, smem, s>>>(x1, xh, twy, H, C, m);
     else k_fwd_y_row<32><<<blocks, threads, smem, s>>>(x1, xh, twy, H, C, m);
   } else {
     const int threads = std::min(256, (H + 31) / 32 * 32);
-    const size_t smem = (size_t)2 * m * C * sizeof(float2);
+    const size_t smem = (size_t)2 * m * C * sizeof(float4);
     if (C <= 16) k_inv_y_row<16><<<blocks, threads, smem, s>>>(yh, z, twy, H, C, m);
     else k_inv_y_row<32><<<blocks, threads, smem, s>>>(yh, z, twy, H, C, m);
   }
