@@ -333,9 +333,9 @@ int fno_uses_tensor_cores(const fno_handle* h, int H, int W, int* out_h);
  * last fno_forward(B, H, W) on workspace ws_d (LBM_ERR_TIMEOUT), else LBM_OK. */
 int fno_check(const fno_handle* h, const void* ws_d, int B, int H, int W, void* stream);
 /* The activation between Fourier layers (Sec. 2.2; GELU or ReLU) exactly as the
- * tensor-core kernels evaluate it, applied element-wise: y_d[i] = act(x_d[i]) for
- * i < n, on `stream` (asynchronous).  x_d, y_d: caller-owned device FP32 arrays (may
- * alias).  GELU is within 2e-7 (1 + |x|) of the exact x Phi(x).  For tests; returns
+ * inference kernels (tensor-core and CUDA-core paths) evaluate it, applied
+ * element-wise: y_d[i] = act(x_d[i]) for i < n, on `stream` (asynchronous).  x_d, y_d:
+ * caller-owned device FP32 arrays (may alias).  GELU is within 2e-7 (1 + |x|) of the exact x Phi(x).  For tests; returns
  * LBM_ERR_INVALID_ARG for an unknown act or a null buffer with n > 0. */
 int fno_activation_eval(int act, const float* x_d, float* y_d, size_t n, void* stream);
 

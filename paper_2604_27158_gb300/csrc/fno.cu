@@ -20,6 +20,7 @@
 
 #include "common.cuh"
 #include "fno_tc.cuh"
+#include "gelu.cuh"
 #include "sm100.cuh"
 
 namespace lbmfno {
@@ -112,7 +113,7 @@ static FnoWs fno_ws_plan(const fno_config& c, int B, int H0, int W0) {
 
 // ---------------------------------------------------------------- kernels ---
 __device__ __forceinline__ float act_fn(float v, int act) {
-  return act == FNO_ACT_GELU ? 0.5f * v * (1.0f + erff(v * 0.70710678118654752f)) : fmaxf(v, 0.0f);
+  return act == FNO_ACT_GELU ? gelu_poly(v) : fmaxf(v, 0.0f);
 }
 __device__ __forceinline__ float bf16r(float v) {  // round to the nearest bfloat16 value
   return __bfloat162float(__float2bfloat16_rn(v));

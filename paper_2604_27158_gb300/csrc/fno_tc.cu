@@ -31,55 +31,21 @@
 
 #include "common.cuh"
 #include "fno_tc.cuh"
-#include "gelu_poly.cuh"
+#include "gelu.cuh"
 #include "sm100.cuh"
 
 namespace lbmfno {
 
-// GELU(v) = v Phi(v) = max(v, 0) - a Q(a) with a = |v| and Q(a) = Phi(-a) =
-// exp(-a^2 / 2) S(a), S(a) = erfcx(a / sqrt 2) / 2 evaluated as a degree-10 polynomial in
-// u = a / 3 - 1 (gelu_poly.cuh, fitted by gelu_fit.py on a in [0, 6]); a is clamped to 6:
-// beyond it the exact a Q(a) is below 7e-9 and the clamped value, 3e-8, stands in for it.
-// Absolute error within 2e-7 (1 + |v|) of the exact GELU,
-// NaN propagates, GELU(+inf) = +inf.  max(v, 0) is written 0.5 (v + |v|) so that a NaN
-// input is not turned into 0.
-__device__ __forceinline__ float gelu_tc(float v) {
-  constexpr float c[GELU_S_DEG + 1] = GELU_S_COEFFS;
-  const float a = fminf(fabsf(v), 6.0f);
-  const float u = fmaf(a, 1.0f / 3.0f, -1.0f);
-  float p = c[GELU_S_DEG];
-#pragma unroll
-  for (int k = GELU_S_DEG - 1; k >= 0; --k) p = fmaf(p, u, c[k]);
-  float e;  // exp(-a^2 / 2) = 2^(-a^2 log2(e) / 2)
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(a * a * -0.72134752044448170f));
-  return fmaf(-a, e * p, 0.5f * (v + fabsf(v)));
-}
 __device__ __forceinline__ float act_tc(float v, int act) {
-  return act == FNO_ACT_GELU ? gelu_tc(v) : fmaxf(v, 0.0f);
+  return act == FNO_ACT_GELU ? gelu_poly(v) : fmaxf(v, 0.0f);
 }
 template <int kAct>
 __device__ __forceinline__ float act_c(float v) {
-  return kAct == FNO_ACT_GELU ? gelu_tc(v) : fmaxf(v, 0.0f);
-}
-// Two activations at once with packed FP32 arithmetic: the same operations in the same
-// order as gelu_tc, so each lane's result is identical to gelu_tc's.
-__device__ __forceinline__ float2 gelu_tc2(float2 v) {
-  constexpr float c[GELU_S_DEG + 1] = GELU_S_COEFFS;
-  const float2 a = make_float2(fminf(fabsf(v.x), 6.0f), fminf(fabsf(v.y), 6.0f));
-  const float2 u = __ffma2_rn(a, make_float2(1.0f / 3.0f, 1.0f / 3.0f), make_float2(-1.0f, -1.0f));
-  float2 p = make_float2(c[GELU_S_DEG], c[GELU_S_DEG]);
-#pragma unroll
-  for (int k = GELU_S_DEG - 1; k >= 0; --k) p = __ffma2_rn(p, u, make_float2(c[k], c[k]));
-  const float2 t = __fmul2_rn(__fmul2_rn(a, a), make_float2(-0.72134752044448170f, -0.72134752044448170f));
-  float2 e;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.x) : "f"(t.x));
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.y) : "f"(t.y));
-  const float2 h = __fmul2_rn(__fadd2_rn(v, make_float2(fabsf(v.x), fabsf(v.y))), make_float2(0.5f, 0.5f));
-  return __ffma2_rn(make_float2(-a.x, -a.y), __fmul2_rn(e, p), h);
+  return kAct == FNO_ACT_GELU ? gelu_poly(v) : fmaxf(v, 0.0f);
 }
 template <int kAct>
 __device__ __forceinline__ float2 act_c2(float2 v) {
-  return kAct == FNO_ACT_GELU ? gelu_tc2(v) : make_float2(fmaxf(v.x, 0.0f), fmaxf(v.y, 0.0f));
+  return kAct == FNO_ACT_GELU ? gelu_poly2(v) : make_float2(fmaxf(v.x, 0.0f), fmaxf(v.y, 0.0f));
 }
 __device__ __forceinline__ int kept_ky_tc(int a, int H, int m) { return a < m ? a : H - 2 * m + a; }
 

@@ -1,4 +1,4 @@
-"""CPU pins of the tensor-core kernels' GELU (Sec. 2.2 activation, exact form v Phi(v)).
+"""CPU pins of the inference kernels' GELU (Sec. 2.2 activation, exact form v Phi(v)).
 
 The kernels evaluate GELU(v) = max(v, 0) - a Q(a), a = min(|v|, 6), with the Gaussian tail
 Q(a) = exp(-a^2/2) S(a) and S a degree-10 polynomial in u = a/3 - 1 whose coefficients
