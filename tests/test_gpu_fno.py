@@ -55,6 +55,26 @@ def test_small_fno_matches_oracle(B, H, W, act):
     assert e < REL_L2_FNO
 
 
+@pytest.mark.parametrize("width,modes,dec_layers,H,W", [
+    (48, 5, 1, 24, 40),    # C > 32: the frequency-parallel x/y kernels, k_inv_x_row<64>
+    (24, 16, 1, 40, 36),   # 2m >= 32: the row-parallel forward y-DFT, C <= 32 row kernels
+    (16, 4, 2, 18, 22),    # two hidden decoder layers: the general projection kernel
+])
+def test_cuda_core_kernel_variants_match_oracle(width, modes, dec_layers, H, W):
+    """Each CUDA-core kernel variant the dispatcher picks by channel count, mode count
+    and decoder depth, against the FP64 oracle (path forced to CUDA cores)."""
+    _requires_gpu()
+    s, g, params = _pair(width=width, layers=2, modes=modes, dec_layers=dec_layers,
+                         dec_size=20, seed=width + modes)
+    net = Fno(g, synth.fno_flatten_params(s, params))
+    net.set_path(P._abi.FNO_PATH_CUDA_CORES)
+    x = _inputs(2, 4, H, W, seed=width)
+    y = net(torch.from_numpy(x).cuda()).cpu().numpy()
+    e = rel_l2(y, fo.fno_forward(s, params, x))
+    print(f"FNO CUDA cores C={width} m={modes} dec={dec_layers} {H}x{W}: rel L2 {e:.3e}")
+    assert e < REL_L2_FNO
+
+
 @pytest.mark.parametrize("H,W", [(32, 48), (64, 64)])
 def test_hot_path_architecture_matches_oracle(H, W):
     """4 layers, 32 latent channels, 12x12 modes, decoder 32 -> 3 (2,365,331 parameters)."""
