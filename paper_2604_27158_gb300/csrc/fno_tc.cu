@@ -19,12 +19,15 @@
 //                  tcgen05: D[x][o] = [T | theta][x][k] * [Zt ; W^T][k][o]
 //                  (M = 128 x positions, N = C, K = 32 + C; both operands K-major)
 // T folds 1/(H W) and the real-input inverse weights (1 for kx = 0, 2 otherwise).
+// Around the layers: k_lift_tc (layer 1 of P on CUDA cores, layer 2 as one MMA per
+// 128-pixel tile) and k_decoder_tc (Q1 as an MMA, activation and Q2 in the epilogue).
 //
-// The tcgen05 kernels are persistent and warp-specialised: warps 0-3 drain the
-// TMEM accumulator (epilogue), warp 4 streams operand tiles with cp.async.bulk
-// into a ring of shared-memory stages, warp 5 issues the MMAs.  Two TMEM
-// accumulators let the epilogue of one tile overlap the MMAs of the next.  Every
-// wait is bounded and records a timeout in the status word.
+// The layer and projection kernels are persistent and warp-specialised: epilogue warps
+// (four, or two groups of four that take alternate tiles) drain the TMEM accumulators,
+// one producer warp streams operand tiles with cp.async.bulk into a ring of
+// shared-memory stages, one warp issues the MMAs.  Two TMEM accumulators let the
+// epilogue of one tile overlap the MMAs of the next.  Every wait is bounded (the
+// waiting warp suspends in try_wait) and records a timeout in the status word.
 #include <math.h>
 
 #include <algorithm>
