@@ -152,20 +152,22 @@ def test_tensor_core_activation_matches_exact_gelu():
     np.testing.assert_array_equal(relu, np.maximum(v, 0.0))
 
 
-@pytest.mark.parametrize("H,W,width", [(32, 128, 32), (64, 256, 32), (40, 128, 16), (32, 128, 64)])
-def test_tensor_core_path_matches_oracle(H, W, width):
-    """tcgen05 path (channel-blocked latents, DFT and 1x1 layers as MMAs) vs the FP64 oracle."""
+@pytest.mark.parametrize("H,W,width,act", [(32, 128, 32, 0), (64, 256, 32, 0), (40, 128, 16, 0),
+                                            (32, 128, 64, 0), (24, 128, 32, 1), (24, 256, 64, 1)])
+def test_tensor_core_path_matches_oracle(H, W, width, act):
+    """tcgen05 path (channel-blocked latents, DFT and 1x1 layers as MMAs) vs the FP64 oracle,
+    with GELU and with ReLU (the activation is a compile-time parameter of the kernels)."""
     _requires_gpu()
     s, g, params = _pair(width=width, layers=3, modes=12 if width != 16 else 6,
-                         dec_size=width, seed=11)
+                         dec_size=width, seed=11, act=act)
     net = Fno(g, synth.fno_flatten_params(s, params))
     assert net.uses_tensor_cores(H, W)
     x = _inputs(2, 4, H, W, seed=13)
     y = net(torch.from_numpy(x).cuda()).cpu().numpy()
     net.check(2, H, W)
-    ref = fo.fno_forward(s, params, x)
+    ref = fo.fno_forward(s, params, x, activation="gelu" if act == 0 else "relu")
     e = rel_l2(y, ref)
-    print(f"FNO tensor cores C={width} {H}x{W}: rel L2 {e:.3e}")
+    print(f"FNO tensor cores C={width} {H}x{W} act={act}: rel L2 {e:.3e}")
     assert e < REL_L2_FNO
 
 
