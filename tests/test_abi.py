@@ -58,3 +58,34 @@ def test_mask_packing_layout():
     w = P.pack_mask(solid)
     assert w.shape == (6,)
     assert w[1 * 2 + 1] == (1 << 1) and w[2 * 2] == 1 and w.sum() == 3
+
+
+def test_fno_query_counts_the_papers_parameters():
+    """The library's parameter layout (fno_query, host only) has exactly the totals the
+    paper prints for its six model shapes."""
+    import json
+    import os
+    from paper_2604_27158_gb300.fno import FnoShape, fno_query
+    with open(os.path.join(os.path.dirname(__file__), "golden", "fno_param_counts.json")) as fh:
+        models = json.load(fh)["models"]
+    for mdl in models:
+        shape = FnoShape(c_in=mdl["c_in"], c_out=mdl["c_out"], width=mdl["width"],
+                         layers=mdl["layers"], modes=mdl["modes"], dec_layers=mdl["dec_layers"],
+                         dec_size=mdl["dec_size"])
+        sz = fno_query(shape, 1, 2 * mdl["modes"], 2 * mdl["modes"] + 1)
+        assert sz.n_params == mdl["params"], mdl["name"]
+        assert sz.packed_bytes % 256 == 0 and sz.ws_bytes > 0
+
+
+@pytest.mark.parametrize("kw,B,H,W", [
+    (dict(modes=8), 1, 15, 64),      # 2m > H
+    (dict(modes=8), 1, 32, 16),      # m >= W / 2
+    (dict(width=15), 1, 32, 32),     # odd width
+    (dict(width=66), 1, 32, 32),     # width above 64
+    (dict(activation=5), 1, 32, 32),
+])
+def test_fno_query_rejects_invalid_shapes(kw, B, H, W):
+    from paper_2604_27158_gb300.fno import FnoShape, fno_query
+    with pytest.raises(P.LbmError) as e:
+        fno_query(FnoShape(**kw), B, H, W)
+    assert e.value.code == _abi.LBM_ERR_INVALID_ARG
