@@ -289,6 +289,10 @@ def hybrid_steady(grid: Grid, solid: np.ndarray, shape, params, nsteps: int,
     (delta rho, u_x, u_y) is clamped and turned into populations.  `nets` overrides the
     single (shape, params) network (see fno_predict).  Returns (f, residual history
     [(step, r)]).
+
+    The residual at a check compares u with the velocity of the previous check; before
+    the first check that is the velocity the start prescribed (zero from rest, the
+    clamped prediction from the FNO), so the first residual from rest is 1.
     """
     one = np.ones((grid.ny, grid.nx))
     zero = np.zeros_like(one)
@@ -296,10 +300,12 @@ def hybrid_steady(grid: Grid, solid: np.ndarray, shape, params, nsteps: int,
         nets = nets or ((shape, params, ALL_CHANNELS),)
         rho, ux, uy = fno_predict(solid, one, zero, zero, nets, activation, clamp)
         f = reinit(grid, solid, rho, ux, uy, neq_mode)
+        fl = ~np.asarray(solid, dtype=bool)
+        ux_p, uy_p = np.where(fl, ux, 0.0), np.where(fl, uy, 0.0)
     else:
         f = rest_state(grid, solid)
+        ux_p, uy_p = zero, zero
     hist = []
-    _, ux_p, uy_p = macro(grid, solid, f)
     done = 0
     while done < nsteps:
         k = min(check_every, nsteps - done)
