@@ -122,21 +122,32 @@ int lbm_macro(lbm_handle* h, float* rho_d, float* ux_d, float* uy_d, void* strea
 int lbm_residual(lbm_handle* h, double* out_h, int update_prev, void* stream);
 
 /*
+ * lbm_residual of the current time level followed by one lbm_step, in one launch of
+ * the step kernel (the statistics are taken from the populations the step pulls, so a
+ * convergence check costs about one step instead of a step and a separate pass; the
+ * steady driver of the hybrid framework, Sec. 2.3, checks this way).  out_h and
+ * update_prev as for lbm_residual: the statistics are those of the level BEFORE the
+ * step.  The step is taken (and counted) also when LBM_ERR_UNSTABLE is returned; not
+ * on LBM_ERR_CUDA or LBM_ERR_TIMEOUT.  Synchronises `stream`.
+ */
+int lbm_step_residual(lbm_handle* h, double* out_h, int update_prev, void* stream);
+
+/*
  * lbm_residual without caller-provided scratch memory (the paper has no
  * counterpart: this is a library convenience).  Same statistics, same output
- * layout and same update_prev behaviour as lbm_residual; the FP64 block partials
- * and per-grid sums live in a 1 MiB array compiled into the library instead of
- * the lbm_init workspace, for callers that cannot allocate device memory when
- * they need the statistics (their device memory is owned by another allocator,
- * or their runtime forbids allocation after start-up).  Allocates nothing: no
- * cudaMalloc, no cudaFree, no allocating library routine.
- *  - Limit: batches whose reduction needs more than 1 MiB of scratch (about 11,900
- *    blocks of 8 row segments of 128 cells, i.e. roughly 12 million lattice cells
- *    counting row padding) are rejected with LBM_ERR_INVALID_ARG; use lbm_residual
- *    for them.
- *  - The first call on a device looks up the array's device address with that
- *    device current (cudaGetSymbolAddress) and caches it; make that first call
- *    before any stream capture.
+ * layout and same update_prev behaviour as lbm_residual; the FP32 row-segment
+ * partials, FP64 block sums and per-grid sums live in a 4 MiB array compiled into
+ * the library instead of the lbm_init workspace, for callers that cannot allocate
+ * device memory when they need the statistics (their device memory is owned by
+ * another allocator, or their runtime forbids allocation after start-up).
+ * Allocates nothing: no cudaMalloc, no cudaFree, no allocating library routine.
+ *  - Limit: batches whose statistics need more than 4 MiB of scratch (about 87,000
+ *    row segments of 128 cells, roughly 11 million lattice cells; each grid rounds
+ *    its segment count up to a multiple of 256) are rejected with
+ *    LBM_ERR_INVALID_ARG; use lbm_residual for them.
+ *  - Every call looks up the array's device address for the current device
+ *    (cudaGetSymbolAddress, which allocates nothing), so the address stays right
+ *    after the device's context has been destroyed and created again.
  *  - Every GPU that loads the library holds the array until the process exits.
  *    All calls share it and it keeps the last call's contents (every slot a call
  *    reads is rewritten by that call first, so nothing needs clearing).  Calls
@@ -174,6 +185,16 @@ int lbm_export_f(lbm_handle* h, float* g_d, void* stream);
  * (lbm_export_f) gives the current time level. */
 int lbm_set_state(lbm_handle* h, const float* gstar_d, void* stream);
 int lbm_get_state(lbm_handle* h, float* gstar_d, void* stream);
+
+/* Streaming alone, through the step kernel's own gather (Sec. 2.1 streaming with
+ * halfway bounce-back on solid cells, then the Zou-He completion of open end
+ * columns): one launch of tile shape `variant` (0 .. LBM_STEP_VARIANTS-1) with the
+ * BGK collision replaced by the identity, so the stored state becomes its streamed
+ * populations (solid cells 0).  Not a time step of the method: it exists so that the
+ * index map of the kernel that advances the lattice can be compared bit for bit with
+ * a reference streaming (values are moved, never combined, except the Zou-He
+ * unknowns).  The step counter is unchanged.  Asynchronous on `stream`. */
+int lbm_stream_probe(lbm_handle* h, int variant, void* stream);
 
 /*
  * Step-kernel tile shapes.  The fused step runs as a persistent kernel whose

@@ -88,6 +88,8 @@ _PROTOS = {
     "lbm_step": ([VP, I, VP], I),
     "lbm_macro": ([VP, VP, VP, VP, VP], I),
     "lbm_residual": ([VP, ctypes.POINTER(ctypes.c_double), I, VP], I),
+    "lbm_step_residual": ([VP, ctypes.POINTER(ctypes.c_double), I, VP], I),
+    "lbm_stream_probe": ([VP, I, VP], I),
     "lbm_reinit_from_macro": ([VP, VP, VP, VP, I, VP], I),
     "lbm_export_f": ([VP, VP, VP], I),
     "lbm_vorticity": ([VP, VP, VP, VP, VP], I),

@@ -83,8 +83,9 @@ struct GridDev {
   int blk_start;       // first block of the grid in flat 256-cell block launches
   int nblk;            // blocks of the grid
   int nseg;            // 128-cell row segments per row (step kernel)
-  int rblk_start;      // first block of the grid in the residual kernel
-  int nrblk;           // residual-kernel blocks of the grid
+  int rblk_start;      // first block of the grid in the statistics reduction (each
+                       // block sums kSegsPerRblk row-segment partials)
+  int nrblk;           // statistics-reduction blocks of the grid
   float omega;         // 1 / tau
   float tau;
   float guo;           // 1 - 1/(2 tau)
@@ -96,6 +97,9 @@ struct GridDev {
 };
 
 constexpr int kBlock = 256;  // threads per block of the flat cell launches
+// Row segments (128 cells) whose statistics partials one reduction block sums; a
+// grid's segment (y, s) has partial slot rblk_start * kSegsPerRblk + y * nseg + s.
+constexpr int kSegsPerRblk = kBlock;
 
 // Grid of a block index: binary search over a per-grid prefix of first blocks.
 template <int GridDev::*START>

@@ -347,11 +347,16 @@ int hybrid_advance(hybrid_handle* h, int cycles, hybrid_stats* out_h, int64_t* g
     std::vector<double> st((size_t)ng * LBM_NSTAT);
     long long steps = 0;
     bool all = false;
+    // A check takes the statistics of level `steps` inside the step kernel that writes
+    // level steps + 1 into the other buffer; that step is kept (it is the first step of
+    // the next interval) unless the loop ends at this check.
+    int carried = 0;
     while (steps < c.max_steps) {
       const int k = (int)std::min<long long>(c.check_every, c.max_steps - steps);
-      LBM_TRY(lbm_step(L, k, s));
+      LBM_TRY(lbm_step(L, k - carried, s));
       steps += k;
-      LBM_TRY(lbm_residual(L, st.data(), 1, s));
+      LBM_TRY(residual_step(L, st.data(), 1, s));
+      carried = 0;
       all = true;
       double mx = 0.0;
       for (int g = 0; g < ng; ++g) {
@@ -361,7 +366,9 @@ int hybrid_advance(hybrid_handle* h, int cycles, hybrid_stats* out_h, int64_t* g
         mx = std::max(mx, r);
       }
       stats.max_residual = mx;
-      if (all) break;
+      if (all || steps >= c.max_steps) break;
+      accept_step(L);
+      carried = 1;
     }
     stats.steps = steps;
     stats.converged = all ? 1 : 0;

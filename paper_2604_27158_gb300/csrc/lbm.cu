@@ -62,6 +62,15 @@ enum {
 };
 
 // --------------------------------------------------------------- kernels ---
+__device__ __forceinline__ float f4get(const float4& v, int j) {
+  return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // ------------------------------------------------------ the fused step ---
 // One time step of every grid of the batch in one launch: pull streaming with
 // halfway bounce-back, Zou-He completion, moments, BGK collision (Sec. 2.1).
@@ -125,11 +134,46 @@ struct StepShape {
 // Tiles are described by an int4 per tile and shape, built at lbm_init: (grid, first
 // column x0, first row y0, rows covered -- the last tile row of a grid can be short).
 
-template <int TY, int ST, int MB>
-__global__ void __launch_bounds__((TY + 1) * 32, MB)
+// What one launch of the step kernel does with the pulled populations of a cell (the
+// gather -- streaming, halfway bounce-back, Zou-He completion -- is the same code in
+// every mode):
+//  * kModeStep:   BGK collision, store: one time step (Sec. 2.1).
+//  * kModeStream: store the pulled populations unchanged (collision replaced by the
+//                 identity): the state becomes its streamed populations, so the gather's
+//                 index map can be compared bit for bit with the oracle's streaming.
+//  * kModeStats:  no collision, no population store: the FP32 statistics of the pulled
+//                 time level (velocity residual, |u|^2, end-column densities, mass,
+//                 momentum, unstable cells) per 128-cell row segment, and optionally the
+//                 velocity stored for the next residual.
+//  * kModeStepStats: both kModeStep and kModeStats in one pass.
+enum StepMode { kModeStep = 0, kModeStream = 1, kModeStats = 2, kModeStepStats = 3 };
+// floats per row-segment statistics slot (R_COUNT values, padded)
+constexpr int kSegStride = 12;
+static_assert(R_COUNT <= kSegStride, "segment statistics slot");
+
+// Extra arguments of the statistics modes (unused by the others).
+struct StatsArgs {
+  float* ux_prev;      // dense velocity of the previous residual (read; written if update)
+  float* uy_prev;
+  float* seg_partial;  // kSegStride floats per row segment (slot of GridDev)
+  float u_max2;
+  int update_prev;
+};
+
+// The statistics modes hold eleven more lane partials and four velocities; they are
+// compiled for one CTA per SM fewer than the shape's time step (no spills).
+__host__ __device__ constexpr int step_min_blocks(int mb, int mode) {
+  return (mode == kModeStats || mode == kModeStepStats) && mb > 1 ? mb - 1 : mb;
+}
+
+template <int TY, int ST, int MB, int MODE>
+__global__ void __launch_bounds__((TY + 1) * 32, step_min_blocks(MB, MODE))
     k_step_tma(const GridDev* __restrict__ grids, const int4* __restrict__ tiles, int ntiles,
                const uint32_t* __restrict__ mask, const float* __restrict__ src,
-               float* __restrict__ dst, unsigned* __restrict__ status) {
+               float* __restrict__ dst, unsigned* __restrict__ status, StatsArgs sa) {
+  constexpr bool kCollide = MODE == kModeStep || MODE == kModeStepStats;
+  constexpr bool kStore = MODE != kModeStats;
+  constexpr bool kStats = MODE == kModeStats || MODE == kModeStepStats;
   using SS = StepShape<TY, ST, MB>;
   using TileMeta = typename SS::Meta;
   constexpr int kTY = TY, kStages = ST, kStageFloats = SS::kStageFloats,
@@ -339,9 +383,24 @@ __global__ void __launch_bounds__((TY + 1) * 32, MB)
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty_bar[s]);  // this warp no longer reads the stage
-    if (!active) continue;
+    if constexpr (!kStats) {
+      if (!active) continue;
+    }
+    // statistics of this lane's four cells (kStats): FP32 lane partials; the velocity
+    // difference to the previous residual is taken after the loop
+    float acc[kStats ? R_COUNT : 1];
+    float ux4[kVec], uy4[kVec];
+    if constexpr (kStats) {
+#pragma unroll
+      for (int k = 0; k < R_COUNT; ++k) acc[k] = 0.0f;
+    }
 #pragma unroll
     for (int j = 0; j < kVec; ++j) {
+      ux4[j] = 0.0f;
+      uy4[j] = 0.0f;
+      if constexpr (kStats) {
+        if (!active) continue;
+      }
       float c[kQ];
 #pragma unroll
       for (int i = 0; i < kQ; ++i) c[i] = g[i][j];
@@ -367,23 +426,95 @@ __global__ void __launch_bounds__((TY + 1) * 32, MB)
           c[6] = c[8] - tt - (1.0f / 6.0f) * ru;
         }
       }
-      collide(G, c);
       const bool keep = !((own_solid >> j) & 1u);  // solid cells store 0
-#pragma unroll
-      for (int i = 0; i < kQ; ++i) g[i][j] = keep ? c[i] : 0.0f;
-    }
-    float* o = dst + G.f_off + (size_t)y * G.pitch + x;
-    if (x + kVec <= nx) {
-#pragma unroll
-      for (int i = 0; i < kQ; ++i)
-        *reinterpret_cast<float4*>(o + i * P) = make_float4(g[i][0], g[i][1], g[i][2], g[i][3]);
-    } else {
-#pragma unroll
-      for (int j = 0; j < kVec; ++j)
-        if (x + j < nx) {
-#pragma unroll
-          for (int i = 0; i < kQ; ++i) o[i * P + j] = g[i][j];
+      if constexpr (kStats) {
+        if (keep && x + j < nx) {
+          float drho, rho, ux, uy;
+          moments(G, c, drho, rho, ux, uy);
+          const float u2 = ux * ux + uy * uy;
+          acc[R_U2] += u2;
+          if (!periodic && x + j == 0) {
+            acc[R_RHO_W] += drho;
+            acc[R_N_W] += 1.0f;
+          }
+          if (!periodic && x + j == nx - 1) {
+            acc[R_RHO_E] += drho;
+            acc[R_N_E] += 1.0f;
+          }
+          acc[R_DRHO] += drho;
+          acc[R_MOMX] += rho * ux;
+          acc[R_MOMY] += rho * uy;
+          acc[R_BAD] += (!isfinite(drho) || !isfinite(u2) || u2 > sa.u_max2) ? 1.0f : 0.0f;
+          acc[R_FLUID] += 1.0f;
+          ux4[j] = ux;
+          uy4[j] = uy;
         }
+      }
+      if constexpr (kCollide) collide(G, c);
+      if constexpr (kStore) {
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) g[i][j] = keep ? c[i] : 0.0f;
+      }
+    }
+    if constexpr (kStats) {
+      const long long c0 = G.cell_off + (long long)y * nx + x;
+      // vector access only where both fields are 16-byte aligned at this cell
+      const bool vec = active && (x + kVec <= nx) &&
+                       ((reinterpret_cast<uintptr_t>(sa.ux_prev + c0) & 15) == 0) &&
+                       ((reinterpret_cast<uintptr_t>(sa.uy_prev + c0) & 15) == 0);
+      if (active) {
+        float4 pu = make_float4(0.f, 0.f, 0.f, 0.f), pv = pu;
+        if (vec) {
+          pu = *reinterpret_cast<const float4*>(sa.ux_prev + c0);
+          pv = *reinterpret_cast<const float4*>(sa.uy_prev + c0);
+        }
+#pragma unroll
+        for (int j = 0; j < kVec; ++j) {
+          if (((own_solid >> j) & 1u) || x + j >= nx) continue;
+          const float dux = ux4[j] - (vec ? f4get(pu, j) : sa.ux_prev[c0 + j]);
+          const float duy = uy4[j] - (vec ? f4get(pv, j) : sa.uy_prev[c0 + j]);
+          acc[R_DU2] += dux * dux + duy * duy;
+        }
+      }
+      if (active && sa.update_prev) {
+        if (vec) {
+          // solid cells keep u_prev = 0, as set by the re-initialisation
+          *reinterpret_cast<float4*>(sa.ux_prev + c0) = make_float4(ux4[0], ux4[1], ux4[2], ux4[3]);
+          *reinterpret_cast<float4*>(sa.uy_prev + c0) = make_float4(uy4[0], uy4[1], uy4[2], uy4[3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < kVec; ++j)
+            if (x + j < nx) {
+              sa.ux_prev[c0 + j] = ux4[j];
+              sa.uy_prev[c0 + j] = uy4[j];
+            }
+        }
+      }
+      // warp tree in FP32 over the segment's 128 cells (fixed lane map: deterministic)
+      float mine = 0.0f;
+#pragma unroll
+      for (int k = 0; k < R_COUNT; ++k) {
+        const float w = warp_sum(acc[k]);
+        if (lane == k) mine = w;
+      }
+      const long long slot = (long long)G.rblk_start * kSegsPerRblk + (long long)y * G.nseg + x0 / kSeg;
+      if (lane < R_COUNT) sa.seg_partial[slot * kSegStride + lane] = mine;
+      if (!active) continue;
+    }
+    if constexpr (kStore) {
+      float* o = dst + G.f_off + (size_t)y * G.pitch + x;
+      if (x + kVec <= nx) {
+#pragma unroll
+        for (int i = 0; i < kQ; ++i)
+          *reinterpret_cast<float4*>(o + i * P) = make_float4(g[i][0], g[i][1], g[i][2], g[i][3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < kVec; ++j)
+          if (x + j < nx) {
+#pragma unroll
+            for (int i = 0; i < kQ; ++i) o[i * P + j] = g[i][j];
+          }
+      }
     }
   }
 }
@@ -392,14 +523,20 @@ __global__ void __launch_bounds__((TY + 1) * 32, MB)
 // Every shape performs the same arithmetic per cell in the same order, so the
 // choice changes speed only; lbm_autotune times them on the caller's batch.
 using StepKernel = void (*)(const GridDev*, const int4*, int, const uint32_t*, const float*,
-                           float*, unsigned*);
+                           float*, unsigned*, StatsArgs);
+constexpr int kStepModes = 4;
 struct StepVariant {
   int ty, stages, minb;
-  StepKernel kernel;
+  StepKernel kernel[kStepModes];  // by StepMode
   size_t smem;
 };
-#define LBM_STEP_VARIANT(TY, ST, MB) \
-  StepVariant { TY, ST, MB, k_step_tma<TY, ST, MB>, StepShape<TY, ST, MB>::kSmem }
+#define LBM_STEP_VARIANT(TY, ST, MB)                                                       \
+  StepVariant {                                                                            \
+    TY, ST, MB,                                                                            \
+        {k_step_tma<TY, ST, MB, kModeStep>, k_step_tma<TY, ST, MB, kModeStream>,           \
+         k_step_tma<TY, ST, MB, kModeStats>, k_step_tma<TY, ST, MB, kModeStepStats>},      \
+        StepShape<TY, ST, MB>::kSmem                                                       \
+  }
 static const StepVariant kStepVariants[LBM_STEP_VARIANTS] = {
     LBM_STEP_VARIANT(3, 2, 5), LBM_STEP_VARIANT(4, 2, 4), LBM_STEP_VARIANT(2, 2, 7),
     LBM_STEP_VARIANT(5, 2, 4), LBM_STEP_VARIANT(3, 3, 4), LBM_STEP_VARIANT(6, 2, 3)};
@@ -479,222 +616,28 @@ __device__ __forceinline__ void block_reduce_store(double v[R_COUNT], double* ou
   }
 }
 
-// Macroscopic fields + steady-state statistics of the current time level.  One
-// warp owns a 128-cell row segment, each lane four cells: the nine pulled values
-// are aligned 16-byte loads at the source rows (the +-1 x-shift from the
-// neighbouring lane by shuffle), the solid bits come from the segment's mask words
-// (loaded once per warp), and Zou-He completes open columns - the same pull as the
-// step.  Each lane sums its four cells in FP32, the warp reduces in FP32 (a tree
-// over 128 cells, relative error ~ 1e-6 at worst), and the eight warps of a block
-// are combined in FP64; blocks are combined in FP64 by k_residual_final.  Fixed
-// cell-to-lane map and fixed trees: deterministic.
-__device__ __forceinline__ float f4get(const float4& v, int j) {
-  return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
-}
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-__global__ void __launch_bounds__(kBlock) k_residual(const GridDev* __restrict__ grids,
-                                                     int ngrids,
-                                                     const uint32_t* __restrict__ mask,
-                                                     const float* __restrict__ src,
-                                                     float* __restrict__ ux_prev,
-                                                     float* __restrict__ uy_prev,
-                                                     int update_prev, float u_max2,
-                                                     double* __restrict__ partial) {
-  constexpr int kWarps = kBlock / 32;
-  __shared__ double red[kWarps][R_COUNT];
+// Steady-state statistics of the current time level, stage 1: the step kernel in a
+// statistics mode leaves FP32 sums (a warp tree over the 128 cells of one row segment)
+// per row segment; block b of grid g sums the segments b * kSegsPerRblk .. +kSegsPerRblk
+// of the grid in FP64, one segment per thread, then in a fixed FP64 tree.  Stage 2
+// (k_residual_final) adds a grid's blocks.  Fixed maps and trees: deterministic.
+__global__ void __launch_bounds__(kBlock) k_stats_reduce(const GridDev* __restrict__ grids,
+                                                         int ngrids,
+                                                         const float* __restrict__ seg_partial,
+                                                         double* __restrict__ partial) {
+  static_assert(kSegsPerRblk == kBlock, "one segment per thread");
   const int gidx = grid_of<&GridDev::rblk_start>(grids, ngrids, blockIdx.x);
-  const GridDev G = grids[gidx];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int task = (blockIdx.x - G.rblk_start) * kWarps + warp;
-  float acc[R_COUNT];
+  const GridDev& G = grids[gidx];
+  const long long task = (long long)(blockIdx.x - G.rblk_start) * kSegsPerRblk + threadIdx.x;
+  double v[R_COUNT];
 #pragma unroll
-  for (int k = 0; k < R_COUNT; ++k) acc[k] = 0.0f;
-  const int nx = G.nx, ny = G.ny;
-  const int y = task / G.nseg;
-  if (y < ny) {  // warp-uniform
-    const int x0 = (task - y * G.nseg) * kSeg;
-    const int x = x0 + kVec * lane;
-    const bool active = x < nx;
-    const bool periodic = G.periodic_x != 0;
-    const int ym = (y == 0) ? ny - 1 : y - 1;
-    const int yp = (y == ny - 1) ? 0 : y + 1;
-    const float* b = src + G.f_off;
-    const unsigned P = (unsigned)G.plane;
-    const int pitch = G.pitch;
-    const uint32_t* m = mask + G.mask_off;
-    // solid bits around the segment: lanes 0..17 fetch the 6 words of rows y-1, y, y+1
-    uint32_t word = 0;
-    if (lane < 18) {
-      const int r = lane / 6;
-      const int wi = (x0 >> 5) - 1 + (lane - r * 6);
-      const int yy = r == 0 ? ym : (r == 1 ? y : yp);
-      if (wi >= 0 && wi < G.wpr) word = __ldg(&m[yy * G.wpr + wi]);
-    }
-    const int bitpos = 31 + kVec * lane;
-    const int k0 = bitpos >> 5, sh = bitpos & 31;
-    uint32_t win[3];
+  for (int k = 0; k < R_COUNT; ++k) v[k] = 0.0;
+  if (task < (long long)G.nseg * G.ny) {
+    const float* sp = seg_partial + ((long long)G.rblk_start * kSegsPerRblk + task) * kSegStride;
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      const uint32_t lo = __shfl_sync(0xffffffffu, word, r * 6 + k0);
-      const uint32_t hi = __shfl_sync(0xffffffffu, word, r * 6 + k0 + 1);
-      win[r] = __funnelshift_r(lo, hi, sh) & 0x3Fu;
-    }
-    const int jw = nx - 1 - x;
-    if (active) {
-      if (x == 0) {
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          win[r] &= ~1u;
-          if (periodic) win[r] |= (uint32_t)mask_bit(m, G.wpr, nx - 1, r == 0 ? ym : (r == 1 ? y : yp));
-        }
-      }
-      if (jw >= 0 && jw < kVec) {
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          win[r] &= ~(1u << (jw + 2));
-          if (periodic)
-            win[r] |= (uint32_t)mask_bit(m, G.wpr, 0, r == 0 ? ym : (r == 1 ? y : yp)) << (jw + 2);
-        }
-      }
-    }
-    const uint32_t own_solid = (win[1] >> 1) & 0xFu;
-    float g[kQ][kVec];
-#pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-      const unsigned row = (unsigned)((cy_of(i) == 0 ? y : (cy_of(i) > 0 ? ym : yp)) * pitch);
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (active) v = __ldg(reinterpret_cast<const float4*>(b + i * P + row + x));
-      if (cx_of(i) == 0) {
-        g[i][0] = v.x; g[i][1] = v.y; g[i][2] = v.z; g[i][3] = v.w;
-      } else if (cx_of(i) > 0) {  // source x - 1
-        float pw = __shfl_up_sync(0xffffffffu, v.w, 1);
-        if (lane == 0)
-          pw = x0 > 0 ? __ldg(b + i * P + row + x0 - 1)
-                      : (periodic ? __ldg(b + i * P + row + nx - 1) : 0.0f);
-        g[i][0] = pw; g[i][1] = v.x; g[i][2] = v.y; g[i][3] = v.z;
-      } else {  // source x + 1
-        float nv = __shfl_down_sync(0xffffffffu, v.x, 1);
-        if (lane == 31) nv = (x0 + kSeg < nx) ? __ldg(b + i * P + row + x0 + kSeg) : 0.0f;
-        g[i][0] = v.y; g[i][1] = v.z; g[i][2] = v.w; g[i][3] = nv;
-        if (active && jw >= 0 && jw < kVec) {
-          const float wrap = periodic ? __ldg(b + i * P + row) : 0.0f;
-#pragma unroll
-          for (int j = 0; j < kVec; ++j)
-            if (j == jw) g[i][j] = wrap;
-        }
-      }
-    }
-    if (active) {
-#pragma unroll
-      for (int i = 1; i < kQ; ++i) {  // halfway bounce-back
-        const int r = cy_of(i) > 0 ? 0 : (cy_of(i) == 0 ? 1 : 2);
-        const uint32_t bb = ((win[r] >> (1 - cx_of(i))) & 0xFu) & ~own_solid;
-        if (bb) {
-          const float4 o = __ldg(reinterpret_cast<const float4*>(b + opp_of(i) * P + y * pitch + x));
-          if (bb & 1u) g[i][0] = o.x;
-          if (bb & 2u) g[i][1] = o.y;
-          if (bb & 4u) g[i][2] = o.z;
-          if (bb & 8u) g[i][3] = o.w;
-        }
-      }
-      float ux4[kVec], uy4[kVec];
-      const long long c0 = G.cell_off + (long long)y * nx + x;
-      float4 pu = make_float4(0.f, 0.f, 0.f, 0.f), pv = pu;
-      // vector access only where both fields are 16-byte aligned at this cell
-      const bool vec = (x + kVec <= nx) && ((reinterpret_cast<uintptr_t>(ux_prev + c0) & 15) == 0) &&
-                       ((reinterpret_cast<uintptr_t>(uy_prev + c0) & 15) == 0);
-      if (vec) {
-        pu = *reinterpret_cast<const float4*>(ux_prev + c0);
-        pv = *reinterpret_cast<const float4*>(uy_prev + c0);
-      }
-#pragma unroll
-      for (int j = 0; j < kVec; ++j) {
-        ux4[j] = 0.0f;
-        uy4[j] = 0.0f;
-        if (x + j >= nx || ((own_solid >> j) & 1u)) continue;
-        float c[kQ];
-#pragma unroll
-        for (int i = 0; i < kQ; ++i) c[i] = g[i][j];
-        if (!periodic) {
-          if (x + j == 0) {
-            const float G0 = c[0] + c[2] + c[4] + 2.0f * (c[3] + c[6] + c[7]);
-            const float ru = (G.bc_west == LBM_BC_PRESSURE)
-                                 ? G.west_d - G0
-                                 : (1.0f + G0) / (1.0f - G.west_d) * G.west_d;
-            const float t = 0.5f * (c[2] - c[4]);
-            c[1] = c[3] + (2.0f / 3.0f) * ru;
-            c[5] = c[7] - t + (1.0f / 6.0f) * ru;
-            c[8] = c[6] + t + (1.0f / 6.0f) * ru;
-          }
-          if (x + j == nx - 1) {
-            const float G0 = c[0] + c[2] + c[4] + 2.0f * (c[1] + c[5] + c[8]);
-            const float ru = (G.bc_east == LBM_BC_PRESSURE)
-                                 ? G0 - G.east_d
-                                 : (1.0f + G0) / (1.0f + G.east_d) * G.east_d;
-            const float t = 0.5f * (c[2] - c[4]);
-            c[3] = c[1] - (2.0f / 3.0f) * ru;
-            c[7] = c[5] + t - (1.0f / 6.0f) * ru;
-            c[6] = c[8] - t - (1.0f / 6.0f) * ru;
-          }
-        }
-        float drho, rho, ux, uy;
-        moments(G, c, drho, rho, ux, uy);
-        const float pux = vec ? f4get(pu, j) : ux_prev[c0 + j];
-        const float puy = vec ? f4get(pv, j) : uy_prev[c0 + j];
-        const float dux = ux - pux, duy = uy - puy;
-        const float u2 = ux * ux + uy * uy;
-        acc[R_DU2] += dux * dux + duy * duy;
-        acc[R_U2] += u2;
-        if (!periodic && x + j == 0) {
-          acc[R_RHO_W] += drho;
-          acc[R_N_W] += 1.0f;
-        }
-        if (!periodic && x + j == nx - 1) {
-          acc[R_RHO_E] += drho;
-          acc[R_N_E] += 1.0f;
-        }
-        acc[R_DRHO] += drho;
-        acc[R_MOMX] += rho * ux;
-        acc[R_MOMY] += rho * uy;
-        acc[R_BAD] += (!isfinite(drho) || !isfinite(u2) || u2 > u_max2) ? 1.0f : 0.0f;
-        acc[R_FLUID] += 1.0f;
-        ux4[j] = ux;
-        uy4[j] = uy;
-      }
-      if (update_prev) {
-        if (vec) {
-          // solid cells keep u_prev = 0, as set by the re-initialisation
-          *reinterpret_cast<float4*>(ux_prev + c0) = make_float4(ux4[0], ux4[1], ux4[2], ux4[3]);
-          *reinterpret_cast<float4*>(uy_prev + c0) = make_float4(uy4[0], uy4[1], uy4[2], uy4[3]);
-        } else {
-#pragma unroll
-          for (int j = 0; j < kVec; ++j)
-            if (x + j < nx) {
-              ux_prev[c0 + j] = ux4[j];
-              uy_prev[c0 + j] = uy4[j];
-            }
-        }
-      }
-    }
+    for (int k = 0; k < R_COUNT; ++k) v[k] = (double)sp[k];
   }
-  // warp tree in FP32, then the block's warps in FP64
-#pragma unroll
-  for (int k = 0; k < R_COUNT; ++k) {
-    const float w = warp_sum(acc[k]);
-    if (lane == 0) red[warp][k] = (double)w;
-  }
-  __syncthreads();
-  if (threadIdx.x < R_COUNT) {
-    double a = 0.0;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) a += red[w][threadIdx.x];
-    partial[(size_t)blockIdx.x * R_COUNT + threadIdx.x] = a;
-  }
+  block_reduce_store(v, partial + (size_t)blockIdx.x * R_COUNT);
 }
 
 __global__ void __launch_bounds__(kBlock) k_residual_final(const GridDev* __restrict__ grids,
@@ -798,8 +741,22 @@ __global__ void __launch_bounds__(kBlock) k_vorticity(const GridDev* __restrict_
 
 // ------------------------------------------------------------ host side ---
 struct WsPlan {
-  size_t grids_off, uprev_off, partial_off, stats_off, status_off, tiles_off, total;
+  size_t grids_off, uprev_off, seg_off, partial_off, stats_off, status_off, tiles_off, total;
 };
+
+// Scratch of one statistics evaluation: FP32 row-segment partials, FP64 block sums,
+// FP64 per-grid sums, laid out one after the other at 256-byte boundaries.
+struct StatsScratch {
+  size_t seg_off, partial_off, stats_off, total;
+};
+static StatsScratch stats_scratch(long long nrblk_total, int ngrids) {
+  StatsScratch r{};
+  r.seg_off = 0;
+  r.partial_off = align_up((size_t)nrblk_total * kSegsPerRblk * kSegStride * sizeof(float), 256);
+  r.stats_off = align_up(r.partial_off + (size_t)nrblk_total * R_COUNT * sizeof(double), 256);
+  r.total = align_up(r.stats_off + (size_t)ngrids * R_COUNT * sizeof(double), 256);
+  return r;
+}
 
 static int plan_layout(const lbm_grid* grids, int ngrids, lbm_layout* lay,
                        std::vector<GridDev>* gd, WsPlan* wp) {
@@ -849,7 +806,7 @@ static int plan_layout(const lbm_grid* grids, int ngrids, lbm_layout* lay,
     d.nblk = (int)(((long long)g.ny * d.pitch + kBlock - 1) / kBlock);
     d.blk_start = (int)blk;
     d.nseg = (g.nx + kSeg - 1) / kSeg;
-    d.nrblk = (int)(((long long)d.nseg * g.ny + kBlock / 32 - 1) / (kBlock / 32));
+    d.nrblk = (int)(((long long)d.nseg * g.ny + kSegsPerRblk - 1) / kSegsPerRblk);
     d.rblk_start = (int)rblk;
 
 
@@ -876,9 +833,11 @@ static int plan_layout(const lbm_grid* grids, int ngrids, lbm_layout* lay,
   WsPlan w{};
   w.grids_off = 0;
   w.uprev_off = align_up(sizeof(GridDev) * ngrids, 256);
-  w.partial_off = align_up(w.uprev_off + 2 * cells * sizeof(float), 256);
-  w.stats_off = align_up(w.partial_off + (size_t)rblk * R_COUNT * sizeof(double), 256);
-  w.status_off = align_up(w.stats_off + (size_t)ngrids * R_COUNT * sizeof(double), 256);
+  const StatsScratch sc = stats_scratch(rblk, ngrids);
+  w.seg_off = align_up(w.uprev_off + 2 * cells * sizeof(float), 256);
+  w.partial_off = w.seg_off + sc.partial_off;
+  w.stats_off = w.seg_off + sc.stats_off;
+  w.status_off = w.seg_off + sc.total;
   w.tiles_off = align_up(w.status_off + sizeof(unsigned), 256);
   size_t tiles_all = 0;  // descriptors of every tile shape
   for (int v = 0; v < LBM_STEP_VARIANTS; ++v)
@@ -896,10 +855,12 @@ static int plan_layout(const lbm_grid* grids, int ngrids, lbm_layout* lay,
 
 static inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
-// One step of every grid with tile shape `v`: reads `src`, writes `dst`.
-static int launch_step(Handle* h, int v, const float* src, float* dst, cudaStream_t s) {
+// One launch of the step kernel in `mode` over every grid with tile shape `v`: reads
+// `src`, writes `dst` (modes that store populations).
+static int launch_step(Handle* h, int v, int mode, const float* src, float* dst, cudaStream_t s,
+                       const StatsArgs& sa = StatsArgs{}) {
   const StepVariant& sv = kStepVariants[v];
-  const int ctas = std::min(h->ntiles_v[v], h->nsm * std::max(1, h->blocks_per_sm_v[v]));
+  const int ctas = std::min(h->ntiles_v[v], h->nsm * std::max(1, h->blocks_per_sm_vm[v][mode]));
   // launched with programmatic stream serialisation: consecutive steps overlap the
   // launch of the next grid with the tail of the previous one (see griddepcontrol above)
   cudaLaunchConfig_t cfg = {};
@@ -912,10 +873,69 @@ static int launch_step(Handle* h, int v, const float* src, float* dst, cudaStrea
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  LBM_CHECK_CUDA(cudaLaunchKernelEx(&cfg, sv.kernel, (const GridDev*)h->gd_d,
+  LBM_CHECK_CUDA(cudaLaunchKernelEx(&cfg, sv.kernel[mode], (const GridDev*)h->gd_d,
                                     (const int4*)h->tiles_d[v], h->ntiles_v[v],
-                                    (const uint32_t*)h->mask, src, dst, h->status_d));
+                                    (const uint32_t*)h->mask, src, dst, h->status_d, sa));
   return LBM_OK;
+}
+
+// Per-grid statistics (enum lbm_stat_index) from the FP64 sums of R_COUNT raw values;
+// returns LBM_ERR_UNSTABLE if a grid has non-finite values or |u| > u_max.
+static int finish_stats(const Handle* h, double* out_h, const char* name) {
+  bool bad = false;
+  for (int g = 0; g < h->ngrids; ++g) {
+    const double* r = &h->stats_h[(size_t)g * R_COUNT];
+    double* o = out_h + (size_t)g * LBM_NSTAT;
+    o[LBM_STAT_RESIDUAL] = r[R_U2] > 0 ? sqrt(r[R_DU2] / r[R_U2]) : INFINITY;
+    o[LBM_STAT_UNORM] = sqrt(r[R_U2]);
+    const double rw = r[R_N_W] > 0 ? r[R_RHO_W] / r[R_N_W] : 0.0;
+    const double re = r[R_N_E] > 0 ? r[R_RHO_E] / r[R_N_E] : 0.0;
+    o[LBM_STAT_DP] = (rw - re) / 3.0;
+    o[LBM_STAT_MASS] = r[R_FLUID] + r[R_DRHO];
+    o[LBM_STAT_MOMX] = r[R_MOMX];
+    o[LBM_STAT_MOMY] = r[R_MOMY];
+    o[LBM_STAT_BAD] = r[R_BAD];
+    o[LBM_STAT_FLUID] = r[R_FLUID];
+    if (r[R_BAD] > 0 || !std::isfinite(r[R_DU2]) || !std::isfinite(r[R_U2])) bad = true;
+  }
+  if (bad) {
+    set_error("%s: non-finite values or |u| > u_max detected", name);
+    return LBM_ERR_UNSTABLE;
+  }
+  return LBM_OK;
+}
+
+// Statistics of the current time level into out_h, with the scratch at `scratch`
+// (layout of stats_scratch): the step kernel in kModeStats (nothing else written) or
+// kModeStepStats (the next time level written to the other buffer, which the caller
+// may accept), the two reduction stages, one copy back.  Synchronises `s`.
+static int residual_run(Handle* h, int mode, char* scratch, double* out_h, int update_prev,
+                        cudaStream_t s, const char* name) {
+  const StatsScratch sc = stats_scratch(h->nrblk_total, h->ngrids);
+  float* seg = reinterpret_cast<float*>(scratch + sc.seg_off);
+  double* partial = reinterpret_cast<double*>(scratch + sc.partial_off);
+  double* stats = reinterpret_cast<double*>(scratch + sc.stats_off);
+  StatsArgs sa{h->ux_prev, h->uy_prev, seg, h->u_max2, update_prev ? 1 : 0};
+  LBM_TRY(launch_step(h, h->variant, mode, h->f[h->cur], h->f[h->cur ^ 1], s, sa));
+  k_stats_reduce<<<h->nrblk_total, kBlock, 0, s>>>(h->gd_d, h->ngrids, seg, partial);
+  LBM_CHECK_LAUNCH();
+  k_residual_final<<<h->ngrids, kBlock, 0, s>>>(h->gd_d, partial, stats);
+  LBM_CHECK_LAUNCH();
+  LBM_CHECK_CUDA(cudaMemcpyAsync(h->stats_h.data(), stats, sizeof(double) * R_COUNT * h->ngrids,
+                                 cudaMemcpyDeviceToHost, s));
+  LBM_CHECK_CUDA(cudaMemcpyAsync(&h->status_h, h->status_d, sizeof(unsigned),
+                                 cudaMemcpyDeviceToHost, s));
+  LBM_CHECK_CUDA(cudaStreamSynchronize(s));
+  if (h->status_h & kStatusTimeout) {
+    set_error("lbm: a device-side wait expired (status 0x%x)", h->status_h);
+    return LBM_ERR_TIMEOUT;
+  }
+  return finish_stats(h, out_h, name);
+}
+
+int residual_step(Handle* h, double* out_h, int update_prev, cudaStream_t s) {
+  return residual_run(h, kModeStepStats, h->scratch, out_h, update_prev, s,
+                      "lbm_step_residual");
 }
 
 }  // namespace lbmfno
@@ -959,8 +979,7 @@ int lbm_init(const lbm_grid* grids_h, int ngrids, const uint32_t* mask_d, float*
   h->gd_d = reinterpret_cast<GridDev*>(ws + wp.grids_off);
   h->ux_prev = reinterpret_cast<float*>(ws + wp.uprev_off);
   h->uy_prev = h->ux_prev + h->layout.cells;
-  h->partial = reinterpret_cast<double*>(ws + wp.partial_off);
-  h->stats_d = reinterpret_cast<double*>(ws + wp.stats_off);
+  h->scratch = ws + wp.seg_off;
   h->status_d = reinterpret_cast<unsigned*>(ws + wp.status_off);
   // tile descriptors of every shape: grid after grid, row of tiles after row of tiles
   std::vector<int4> tiles;
@@ -987,10 +1006,15 @@ int lbm_init(const lbm_grid* grids_h, int ngrids, const uint32_t* mask_d, float*
               cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess;
     for (int v = 0; ok && v < LBM_STEP_VARIANTS; ++v) {
       const StepVariant& sv = kStepVariants[v];
-      ok = cudaFuncSetAttribute(sv.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sv.smem) == cudaSuccess &&
-           cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->blocks_per_sm_v[v], sv.kernel,
-                                                         (sv.ty + 1) * 32, sv.smem) == cudaSuccess;
+      for (int m = 0; ok && m < kStepModes; ++m)
+        ok = cudaFuncSetAttribute(sv.kernel[m], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sv.smem) == cudaSuccess;
+      // each mode's persistent grid holds the CTAs that fit at once
+      for (int m = 0; ok && m < kStepModes; ++m)
+        ok = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->blocks_per_sm_vm[v][m],
+                                                           sv.kernel[m], (sv.ty + 1) * 32,
+                                                           sv.smem) == cudaSuccess;
+      h->blocks_per_sm_v[v] = h->blocks_per_sm_vm[v][kModeStep];
     }
     if (!ok) {
       set_error("lbm_init: %s", cudaGetErrorString(cudaGetLastError()));
@@ -1023,7 +1047,7 @@ int lbm_step(lbm_handle* h, int nsteps, void* stream) {
   LBM_REQUIRE(h != nullptr && nsteps >= 0, "lbm_step: bad arguments");
   cudaStream_t s = S(stream);
   for (int k = 0; k < nsteps; ++k) {
-    LBM_TRY(launch_step(h, h->variant, h->f[h->cur], h->f[h->cur ^ 1], s));
+    LBM_TRY(launch_step(h, h->variant, kModeStep, h->f[h->cur], h->f[h->cur ^ 1], s));
     h->cur ^= 1;
   }
   h->steps += nsteps;
@@ -1040,43 +1064,23 @@ int lbm_macro(lbm_handle* h, float* rho_d, float* ux_d, float* uy_d, void* strea
 
 int lbm_residual(lbm_handle* h, double* out_h, int update_prev, void* stream) {
   LBM_REQUIRE(h != nullptr && out_h != nullptr, "lbm_residual: bad arguments");
-  cudaStream_t s = S(stream);
-  k_residual<<<h->nrblk_total, kBlock, 0, s>>>(h->gd_d, h->ngrids, h->mask, h->f[h->cur],
-                                              h->ux_prev, h->uy_prev, update_prev, h->u_max2,
-                                              h->partial);
-  LBM_CHECK_LAUNCH();
-  k_residual_final<<<h->ngrids, kBlock, 0, s>>>(h->gd_d, h->partial, h->stats_d);
-  LBM_CHECK_LAUNCH();
-  LBM_CHECK_CUDA(cudaMemcpyAsync(h->stats_h.data(), h->stats_d,
-                                 sizeof(double) * R_COUNT * h->ngrids, cudaMemcpyDeviceToHost,
-                                 s));
-  LBM_CHECK_CUDA(cudaMemcpyAsync(&h->status_h, h->status_d, sizeof(unsigned),
-                                 cudaMemcpyDeviceToHost, s));
-  LBM_CHECK_CUDA(cudaStreamSynchronize(s));
-  if (h->status_h & kStatusTimeout) {
-    set_error("lbm: a device-side wait expired (status 0x%x)", h->status_h);
-    return LBM_ERR_TIMEOUT;
-  }
-  bool bad = false;
-  for (int g = 0; g < h->ngrids; ++g) {
-    const double* r = &h->stats_h[(size_t)g * R_COUNT];
-    double* o = out_h + (size_t)g * LBM_NSTAT;
-    o[LBM_STAT_RESIDUAL] = r[R_U2] > 0 ? sqrt(r[R_DU2] / r[R_U2]) : INFINITY;
-    o[LBM_STAT_UNORM] = sqrt(r[R_U2]);
-    const double rw = r[R_N_W] > 0 ? r[R_RHO_W] / r[R_N_W] : 0.0;
-    const double re = r[R_N_E] > 0 ? r[R_RHO_E] / r[R_N_E] : 0.0;
-    o[LBM_STAT_DP] = (rw - re) / 3.0;
-    o[LBM_STAT_MASS] = r[R_FLUID] + r[R_DRHO];
-    o[LBM_STAT_MOMX] = r[R_MOMX];
-    o[LBM_STAT_MOMY] = r[R_MOMY];
-    o[LBM_STAT_BAD] = r[R_BAD];
-    o[LBM_STAT_FLUID] = r[R_FLUID];
-    if (r[R_BAD] > 0 || !std::isfinite(r[R_DU2]) || !std::isfinite(r[R_U2])) bad = true;
-  }
-  if (bad) {
-    set_error("lbm_residual: non-finite values or |u| > u_max detected");
-    return LBM_ERR_UNSTABLE;
-  }
+  return residual_run(h, kModeStats, h->scratch, out_h, update_prev, S(stream), "lbm_residual");
+}
+
+int lbm_step_residual(lbm_handle* h, double* out_h, int update_prev, void* stream) {
+  LBM_REQUIRE(h != nullptr && out_h != nullptr, "lbm_step_residual: bad arguments");
+  const int rc = residual_step(h, out_h, update_prev, S(stream));
+  if (rc == LBM_OK || rc == LBM_ERR_UNSTABLE) accept_step(h);
+  return rc;
+}
+
+int lbm_stream_probe(lbm_handle* h, int variant, void* stream) {
+  LBM_REQUIRE(h != nullptr && variant >= 0 && variant < LBM_STEP_VARIANTS,
+              "lbm_stream_probe: bad arguments");
+  LBM_REQUIRE(h->blocks_per_sm_v[variant] > 0, "lbm_stream_probe: shape %d does not fit",
+              variant);
+  LBM_TRY(launch_step(h, variant, kModeStream, h->f[h->cur], h->f[h->cur ^ 1], S(stream)));
+  h->cur ^= 1;
   return LBM_OK;
 }
 
@@ -1144,9 +1148,9 @@ int lbm_autotune(lbm_handle* h, int reps, float* ms_h, int* chosen_h, void* stre
   for (int v = 0; v < LBM_STEP_VARIANTS && rc == LBM_OK; ++v) {
     float ms = INFINITY;
     if (h->blocks_per_sm_v[v] > 0) {
-      for (int w = 0; w < 2 && rc == LBM_OK; ++w) rc = launch_step(h, v, src, scratch, s);
+      for (int w = 0; w < 2 && rc == LBM_OK; ++w) rc = launch_step(h, v, kModeStep, src, scratch, s);
       if (rc == LBM_OK && cudaEventRecord(e0, s) != cudaSuccess) rc = LBM_ERR_CUDA;
-      for (int k = 0; k < reps && rc == LBM_OK; ++k) rc = launch_step(h, v, src, scratch, s);
+      for (int k = 0; k < reps && rc == LBM_OK; ++k) rc = launch_step(h, v, kModeStep, src, scratch, s);
       if (rc == LBM_OK && (cudaEventRecord(e1, s) != cudaSuccess ||
                            cudaEventSynchronize(e1) != cudaSuccess ||
                            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
@@ -1206,93 +1210,42 @@ int lbm_destroy(lbm_handle* h) {
 // ---------------------------------------------------------------------------
 // Residual statistics without caller-provided scratch memory.
 //
-// lbm_residual keeps its FP64 block partials and per-grid sums in the workspace
-// the caller allocated for lbm_init.  Some callers cannot allocate device memory
-// when they want these statistics: for example a host program whose device
-// memory is entirely handed out by another allocator (a framework's caching
-// allocator that already owns the budget), or a runtime that forbids device
-// allocation once it has started.  lbm_residual_static gives them the same
-// numbers with the scratch held in a fixed array compiled into this library.
+// lbm_residual keeps its FP32 row-segment partials, FP64 block sums and per-grid
+// sums in the workspace the caller allocated for lbm_init.  Some callers cannot
+// allocate device memory when they want these statistics: for example a host program
+// whose device memory is entirely handed out by another allocator (a framework's
+// caching allocator that already owns the budget), or a runtime that forbids device
+// allocation once it has started.  lbm_residual_static gives them the same numbers
+// with the scratch held in a fixed array compiled into this library.
 //
 // The array is file-scope device memory of kResidualStaticBytes; every GPU that
 // loads the library holds it until the process exits.  Host code may not use the
-// array's name as a device address, so the first call on each device looks the
-// address up with cudaGetSymbolAddress (with that device current) and caches it.
-// Every call shares the array and it keeps the previous call's contents: each
-// block overwrites its own partial slot and the final pass overwrites every
-// per-grid slot, so nothing has to start at zero.  Calls whose kernels overlap
-// on the GPU (two streams, two threads) race on the array.
+// array's name as a device address, so every call looks the address up with
+// cudaGetSymbolAddress for the device that is current (a lookup allocates nothing;
+// looking it up every call also stays correct after the context has been destroyed
+// and created again, when the module, and with it the array, is loaded anew).
+// Every call shares the array and it keeps the previous call's contents: every slot
+// a call reads is written by that call first (each row segment's partial by the
+// step kernel, each block sum by the first reduction stage, each grid sum by the
+// second), so nothing has to start at zero.  Calls whose kernels overlap on the
+// GPU (two streams, two threads) race on the array.
 // ---------------------------------------------------------------------------
-#include <mutex>
-
 namespace lbmfno {
-constexpr size_t kResidualStaticBytes = 1u << 20;  // 1 MiB
+constexpr size_t kResidualStaticBytes = 4u << 20;  // 4 MiB
 static __device__ __align__(256) unsigned char g_residual_static[kResidualStaticBytes];
-constexpr int kMaxStaticDevices = 64;
-static void* g_residual_static_addr[kMaxStaticDevices] = {};
-static std::mutex g_residual_static_mutex;
 }  // namespace lbmfno
 
 extern "C" int lbm_residual_static(lbm_handle* h, double* out_h, int update_prev, void* stream) {
   LBM_REQUIRE(h != nullptr && out_h != nullptr, "lbm_residual_static: bad arguments");
-  const size_t partial_bytes = (size_t)h->nrblk_total * R_COUNT * sizeof(double);
-  const size_t stats_off = align_up(partial_bytes, 256);
-  const size_t need = stats_off + (size_t)h->ngrids * R_COUNT * sizeof(double);
+  const size_t need = stats_scratch(h->nrblk_total, h->ngrids).total;
   LBM_REQUIRE(need <= kResidualStaticBytes,
               "lbm_residual_static: batch needs %zu bytes of scratch, the static array holds "
-              "%zu (at most about %zu reduction blocks of 8 x 128 cells); use lbm_residual",
-              need, kResidualStaticBytes, kResidualStaticBytes / (R_COUNT * sizeof(double)));
-  int dev = 0;
-  LBM_CHECK_CUDA(cudaGetDevice(&dev));
-  LBM_REQUIRE(dev >= 0 && dev < kMaxStaticDevices, "lbm_residual_static: device %d out of range",
-              dev);
+              "%zu (at most about %zu row segments of 128 cells); use lbm_residual",
+              need, kResidualStaticBytes,
+              kResidualStaticBytes / (kSegStride * sizeof(float) + R_COUNT * sizeof(double) /
+                                                                       kSegsPerRblk));
   void* base = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_residual_static_mutex);
-    if (g_residual_static_addr[dev] == nullptr) {
-      void* p = nullptr;
-      LBM_CHECK_CUDA(cudaGetSymbolAddress(&p, g_residual_static));
-      g_residual_static_addr[dev] = p;
-    }
-    base = g_residual_static_addr[dev];
-  }
-  double* partial = static_cast<double*>(base);
-  double* stats = reinterpret_cast<double*>(static_cast<char*>(base) + stats_off);
-  cudaStream_t s = S(stream);
-  k_residual<<<h->nrblk_total, kBlock, 0, s>>>(h->gd_d, h->ngrids, h->mask, h->f[h->cur],
-                                              h->ux_prev, h->uy_prev, update_prev, h->u_max2,
-                                              partial);
-  LBM_CHECK_LAUNCH();
-  k_residual_final<<<h->ngrids, kBlock, 0, s>>>(h->gd_d, partial, stats);
-  LBM_CHECK_LAUNCH();
-  LBM_CHECK_CUDA(cudaMemcpyAsync(h->stats_h.data(), stats, sizeof(double) * R_COUNT * h->ngrids,
-                                 cudaMemcpyDeviceToHost, s));
-  LBM_CHECK_CUDA(cudaMemcpyAsync(&h->status_h, h->status_d, sizeof(unsigned),
-                                 cudaMemcpyDeviceToHost, s));
-  LBM_CHECK_CUDA(cudaStreamSynchronize(s));
-  if (h->status_h & kStatusTimeout) {
-    set_error("lbm: a device-side wait expired (status 0x%x)", h->status_h);
-    return LBM_ERR_TIMEOUT;
-  }
-  bool bad = false;
-  for (int g = 0; g < h->ngrids; ++g) {
-    const double* r = &h->stats_h[(size_t)g * R_COUNT];
-    double* o = out_h + (size_t)g * LBM_NSTAT;
-    o[LBM_STAT_RESIDUAL] = r[R_U2] > 0 ? sqrt(r[R_DU2] / r[R_U2]) : INFINITY;
-    o[LBM_STAT_UNORM] = sqrt(r[R_U2]);
-    const double rw = r[R_N_W] > 0 ? r[R_RHO_W] / r[R_N_W] : 0.0;
-    const double re = r[R_N_E] > 0 ? r[R_RHO_E] / r[R_N_E] : 0.0;
-    o[LBM_STAT_DP] = (rw - re) / 3.0;
-    o[LBM_STAT_MASS] = r[R_FLUID] + r[R_DRHO];
-    o[LBM_STAT_MOMX] = r[R_MOMX];
-    o[LBM_STAT_MOMY] = r[R_MOMY];
-    o[LBM_STAT_BAD] = r[R_BAD];
-    o[LBM_STAT_FLUID] = r[R_FLUID];
-    if (r[R_BAD] > 0 || !std::isfinite(r[R_DU2]) || !std::isfinite(r[R_U2])) bad = true;
-  }
-  if (bad) {
-    set_error("lbm_residual_static: non-finite values or |u| > u_max detected");
-    return LBM_ERR_UNSTABLE;
-  }
-  return LBM_OK;
+  LBM_CHECK_CUDA(cudaGetSymbolAddress(&base, g_residual_static));
+  return residual_run(h, kModeStats, static_cast<char*>(base), out_h, update_prev, S(stream),
+                      "lbm_residual_static");
 }

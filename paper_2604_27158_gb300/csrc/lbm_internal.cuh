@@ -13,11 +13,12 @@ struct Handle {
   GridDev* gd_d = nullptr;  // in the caller's workspace
   int ngrids = 0;
   int nblk_total = 0;
-  int nrblk_total = 0;  // blocks of the residual kernel
+  int nrblk_total = 0;  // blocks of the statistics reduction
   int nsm = 0;
   int variant = 0;                             // step-kernel tile shape in use
   int ntiles_v[LBM_STEP_VARIANTS] = {};        // tiles of the batch per shape
   int blocks_per_sm_v[LBM_STEP_VARIANTS] = {};  // resident CTAs per SM per shape
+  int blocks_per_sm_vm[LBM_STEP_VARIANTS][4] = {};  // ... per shape and kernel mode
   int4* tiles_d[LBM_STEP_VARIANTS] = {};      // per-shape tile descriptors (workspace)
   unsigned* status_d = nullptr;
   unsigned status_h = 0;
@@ -26,13 +27,23 @@ struct Handle {
   int cur = 0;  // buffer holding the current state
   float* ux_prev = nullptr;
   float* uy_prev = nullptr;
-  double* partial = nullptr;
-  double* stats_d = nullptr;
+  char* scratch = nullptr;  // statistics scratch in the workspace: FP32 row-segment
+                            // partials, FP64 block sums, FP64 per-grid sums
   std::vector<double> stats_h;
   lbm_layout layout{};
   float u_max2 = 0.04f;
   long long steps = 0;
 };
+
+// Statistics of the current time level (what lbm_residual returns) computed by the
+// step kernel while it writes the next time level into the other buffer.  The handle's
+// current buffer is NOT switched: the caller either keeps the state (nothing to do) or
+// accepts the step with accept_step().  Synchronises `s`.
+int residual_step(Handle* h, double* out_h, int update_prev, cudaStream_t s);
+inline void accept_step(Handle* h) {
+  h->cur ^= 1;
+  h->steps += 1;
+}
 
 }  // namespace lbmfno
 

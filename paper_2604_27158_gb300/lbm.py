@@ -116,6 +116,22 @@ class Lattice:
         _abi.check("lbm_residual", code)
         return out
 
+    def step_residual(self, update_prev: bool = True, stream=None,
+                      raise_unstable: bool = True) -> np.ndarray:
+        """Statistics of the current level (as residual()) and one step, in one launch."""
+        out = np.zeros((len(self.grids), _abi.LBM_NSTAT), dtype=np.float64)
+        code = _abi.lib().lbm_step_residual(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                            int(update_prev), _stream_ptr(stream))
+        if code == _abi.LBM_ERR_UNSTABLE and not raise_unstable:
+            return out
+        _abi.check("lbm_step_residual", code)
+        return out
+
+    def stream_probe(self, variant: int, stream=None) -> None:
+        """Replace the state by its streamed populations, through the step kernel's
+        gather with tile shape `variant` (collision replaced by the identity)."""
+        call("lbm_stream_probe", self._h, int(variant), _stream_ptr(stream))
+
     def reinit(self, rho: torch.Tensor, ux: torch.Tensor, uy: torch.Tensor, neq_mode: int = 1,
                stream=None) -> None:
         for t in (rho, ux, uy):

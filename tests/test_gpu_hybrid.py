@@ -67,6 +67,21 @@ def test_steady_driver_matches_oracle(use_fno):
         assert abs(res[k] - hist[-1][1]) / hist[-1][1] < (1e-3 if not use_fno else 5e-2)
 
 
+def test_steady_driver_first_check_from_rest():
+    """From rest the stored velocity is 0, so the first check's residual is exactly 1;
+    the driver's fused check (statistics taken inside a step) keeps level 100."""
+    _requires_gpu()
+    specs = _porous(2, nx=48, ny=24)
+    lat = Lattice([a for a, _ in specs], [b for _, b in specs])
+    hyb = Hybrid(lat, None, HybridConfig(use_fno=0, check_every=100, tol=1e-30, max_steps=100))
+    st, first, res = hyb.advance()
+    assert st.steps == 100 and lat.steps_done() == 100
+    np.testing.assert_array_equal(res, 1.0)
+    ref = Lattice([a for a, _ in specs], [b for _, b in specs])
+    ref.step(100)
+    assert torch.equal(lat.get_state().cpu(), ref.get_state().cpu())
+
+
 def test_steady_driver_reports_convergence():
     _requires_gpu()
     specs = _porous(2, nx=48, ny=24)

@@ -278,3 +278,133 @@ def test_autotune_keeps_state_and_picks_a_shape():
     ref = Lattice([g], [solid])
     ref.step(16)
     assert torch.equal(lat.get_state().cpu(), ref.get_state().cpu())
+
+
+# ---------------------------------------------------------------------------
+# The index map of the kernel that advances the lattice.  lbm_stream_probe runs the
+# step kernel (the same cp.async.bulk row staging, +-1 shifts across 16-byte chunks,
+# funnel-shifted mask windows, wrap columns and short last tiles) with the collision
+# replaced by the identity, so the stored state becomes the streamed populations.
+# With the index-valued probe state every value is an exact integer in FP32: the
+# moved values must equal the oracle's streaming (Sec. 2.1) bit for bit.
+
+def _probe_specs():
+    specs = [GEOMS[k]() for k in sorted(GEOMS)]
+    solid, _, _ = synth.porous_media(512, 256, 4, 12, seed=7)       # 4 x-tiles, Zou-He ends
+    specs.append((GridSpec(512, 256, 0.7, bc_west=P.BC_PRESSURE, bc_east=P.BC_PRESSURE,
+                           west_value=1.001, east_value=1.0), solid))
+    # periodic, 3 x-tiles with a ragged last one (301 = 2 * 128 + 45), ny prime
+    solid = synth.rasterise_disks(301, 23, [synth.Disk(0, 5, 4), synth.Disk(300, 17, 3),
+                                            synth.Disk(128, 11, 5), synth.Disk(255, 0, 3)],
+                                  True, True)
+    specs.append((GridSpec(301, 23, 0.8), solid))
+    return specs
+
+
+def _check_streamed(specs, got_parts, base0=0):
+    base = base0
+    for k, (g, solid) in enumerate(specs):
+        fs = probe_state(g.ny, g.nx, base)
+        want = oracle.stream(to_oracle(g), solid, fs)
+        got = got_parts[k].numpy().astype(np.float64).reshape(9, g.ny, g.nx)
+        sel = ~zou_he_unknown(g, solid) & np.broadcast_to(~solid, want.shape)
+        np.testing.assert_array_equal(got[sel], want[sel], err_msg=f"grid {k} {g.nx}x{g.ny}")
+        assert np.all(got[:, solid] == 0.0), f"grid {k}: solid cells must store 0"
+        base += g.nx * g.ny
+
+
+@pytest.mark.parametrize("variant", range(6))
+def test_step_kernel_streaming_bit_exact_every_tile_shape(variant):
+    _requires_gpu()
+    assert P._abi.LBM_STEP_VARIANTS == 6
+    specs = _probe_specs()
+    # each grid alone (one launch covers one geometry) ...
+    for g, solid in specs:
+        lat = Lattice([g], [solid])
+        lat.set_state(torch.from_numpy(probe_state(g.ny, g.nx).astype(np.float32).ravel()).cuda())
+        lat.stream_probe(variant)
+        _check_streamed([(g, solid)], [lat.get_state().cpu()])
+        lat.close()
+    # ... and all of them as one batch of uneven grids
+    lat = Lattice([s[0] for s in specs], [s[1] for s in specs])
+    parts, base = [], 0
+    for g, _ in specs:
+        parts.append(probe_state(g.ny, g.nx, base).ravel())
+        base += g.nx * g.ny
+    assert 9 * base < 2 ** 24  # every probe value is exact in FP32
+    lat.set_state(torch.from_numpy(np.concatenate(parts).astype(np.float32)).cuda())
+    lat.stream_probe(variant)
+    _check_streamed(specs, lat.split(lat.get_state().cpu(), per_cell=9))
+    lat.close()
+
+
+def test_stream_probe_equals_export_on_moved_values():
+    """The step kernel's gather and the per-cell gather of lbm_export_f agree."""
+    _requires_gpu()
+    specs = _probe_specs()
+    lat = Lattice([s[0] for s in specs], [s[1] for s in specs])
+    rng = np.random.default_rng(3)
+    state = torch.from_numpy(rng.standard_normal(9 * lat.cells).astype(np.float32)).cuda()
+    lat.set_state(state)
+    exported = lat.export_f().cpu()
+    lat.stream_probe(3)
+    streamed = lat.get_state().cpu()
+    for k, (g, solid) in enumerate(specs):
+        a = lat.split(exported, per_cell=9)[k].numpy().reshape(9, g.ny, g.nx)
+        b = lat.split(streamed, per_cell=9)[k].numpy().reshape(9, g.ny, g.nx)
+        known = ~zou_he_unknown(g, solid)
+        np.testing.assert_array_equal(a[known], b[known])
+        # the Zou-He unknowns: the same FP32 formula, up to rounding order
+        np.testing.assert_allclose(a[~known], b[~known], rtol=1e-5, atol=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# Statistics taken by the step kernel (stats-only mode for lbm_residual, step + stats
+# for lbm_step_residual and the steady driver).
+
+def _stats_lattice():
+    specs = _probe_specs()
+    specs.append((GridSpec(128, 64, 0.8, fx=1e-6), synth.channel_with_disks(128, 64, 6, 4, 8, seed=0)[0]))
+    return specs
+
+
+def test_residual_identical_for_every_tile_shape():
+    _requires_gpu()
+    specs = _stats_lattice()
+    ref = None
+    for v in range(P._abi.LBM_STEP_VARIANTS):
+        lat = Lattice([s[0] for s in specs], [s[1] for s in specs])
+        lat.set_step_variant(v)
+        lat.step(60)
+        lat.residual(update_prev=True)
+        lat.step(40)
+        st = lat.residual(update_prev=False)
+        if ref is None:
+            ref = st
+        else:  # same per-segment FP32 trees and the same FP64 order in every shape
+            np.testing.assert_array_equal(st, ref, err_msg=f"tile shape {v}")
+        lat.close()
+    assert np.all(ref[:, P._abi.LBM_STAT_RESIDUAL] > 0)
+
+
+@pytest.mark.parametrize("variant", [0, 3])
+def test_step_residual_equals_residual_then_step(variant):
+    _requires_gpu()
+    specs = _stats_lattice()
+    a = Lattice([s[0] for s in specs], [s[1] for s in specs])
+    b = Lattice([s[0] for s in specs], [s[1] for s in specs])
+    for lat in (a, b):
+        lat.set_step_variant(variant)
+        lat.step(50)
+        lat.residual(update_prev=True)
+        lat.step(25)
+    for _ in range(3):
+        sa = a.step_residual(update_prev=True)
+        sb = b.residual(update_prev=True)
+        b.step(1)
+        np.testing.assert_array_equal(sa, sb)
+        assert torch.equal(a.get_state().cpu(), b.get_state().cpu())
+        a.step(9)
+        b.step(9)
+    assert a.steps_done() == b.steps_done()
+    np.testing.assert_array_equal(a.residual(update_prev=False), b.residual(update_prev=False))

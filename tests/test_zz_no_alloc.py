@@ -75,7 +75,8 @@ def test_static_scratch_residual_matches_workspace_residual():
 
 def test_static_scratch_rejects_batches_beyond_its_size():
     _requires_gpu()
-    # 5000 x 5000 cells need ~25,000 reduction blocks of 8 x 128 cells: more than 1 MiB of partials
+    # 5000 x 5000 cells are 200,000 row segments of 128 cells: ~9.6 MB of partials, more than
+    # the 4 MiB array holds
     lat = Lattice([GridSpec(5000, 5000, 0.8)], [np.zeros((5000, 5000), bool)])
     code, _ = _static_call(lat, update_prev=0)
     assert code == _abi.LBM_ERR_INVALID_ARG
