@@ -282,7 +282,26 @@ def cpu_baseline(masks, budget_s=8.0):
             "sample": f"FP64 C oracle, OpenMP rows on {cores} host threads: {nm} LBM steps of one "
                       f"512x256 porous trajectory (seed 0) in {dtm:.1f} s",
             "single_thread": {"value": v1, "unit": "GLUPS", "cores": 1,
-                              "sample": f"{n1} steps in {dt1:.1f} s"}}
+                              "sample": f"{n1} steps in {dt1:.1f} s"},
+            "fno_oracle": fno_oracle_baseline()}
+
+
+def fno_oracle_baseline(reps=2):
+    """The FP64 numpy FNO oracle (naive truncated DFTs as BLAS matrix products) on the
+    FNO throughput workload's shape, timed at B = 1 and scaled x32."""
+    import oracle
+    import synth
+    shape, _ = fno_params()
+    params = synth.fno_random_params(shape, seed=0)
+    x = np.random.default_rng(0).standard_normal((1, 4, 256, 256)) * 1e-2
+    oracle.fno_forward(shape, params, x)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.fno_forward(shape, params, x)
+    ms1 = 1e3 * (time.perf_counter() - t0) / reps
+    return {"ms_per_forward_b32": 32 * ms1, "ms_per_forward_b1": ms1,
+            "sample": f"B=1 x 256 x 256 forward (4 layers, 32 channels, 12x12 modes), {reps} "
+                      f"runs, scaled x32; numpy BLAS threads on the host"}
 
 
 def bench_config(T, phis, solve_steps, world):
@@ -553,6 +572,61 @@ def main():
             lat_s.close()
             del solid
 
+    # small, L2-resident lattices where launch cost may dominate: the 128 x 64 channel
+    # (tau 0.8, g_x 1e-6, six disks r 4-8, 2000 steps) alone and as a batch of its ten
+    # seeds in one launch per step, and one 512 x 256 porous trajectory; each timed with
+    # one stream launch per step (programmatic dependent launch) and as CUDA graphs of
+    # 100 steps
+    launch_bound = None
+    if rank == 0:
+        import synth
+        launch_bound = {}
+        cases = []
+        ch = [synth.channel_with_disks(128, 64, 6, 4, 8, seed=k)[0] for k in range(10)]
+        gch = GridSpec(128, 64, 0.8, fx=1e-6)
+        cases.append(("channel_128x64", [gch], ch[:1]))
+        cases.append(("channel_128x64_x10_batch", [gch] * 10, ch))
+        gpo = GridSpec(NX, NY, TAU, bc_west=P.BC_PRESSURE, bc_east=P.BC_PRESSURE,
+                       west_value=RHO_IN, east_value=RHO_OUT)
+        cases.append(("porous_512x256_one_trajectory", [gpo], masks[:1]))
+        for name, gl, ml in cases:
+            lat_b = Lattice(gl, ml)
+            lat_b.autotune(reps=20)
+            nsteps = 2000
+            lat_b.step(200)
+            b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            b0.record(stream)
+            lat_b.step(nsteps)
+            b1.record(stream)
+            torch.cuda.synchronize()
+            ms_stream = b0.elapsed_time(b1)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                lat_b.step(100)
+            for _ in range(2):
+                graph.replay()
+            b0.record(stream)
+            for _ in range(nsteps // 100):
+                graph.replay()
+            b1.record(stream)
+            torch.cuda.synchronize()
+            ms_graph = b0.elapsed_time(b1)
+            cl = lat_b.cells
+            sv = lat_b.step_variant()
+            launch_bound[name] = {
+                "cells": cl, "steps": nsteps,
+                "us_per_step_stream": 1e3 * ms_stream / nsteps,
+                "us_per_step_graph": 1e3 * ms_graph / nsteps,
+                "glups_stream": cl * nsteps / (ms_stream * 1e-3) / 1e9,
+                "glups_graph": cl * nsteps / (ms_graph * 1e-3) / 1e9,
+                "f_bytes": 2 * 36 * cl,
+                "tile_shape": {"rows_per_tile": sv[1], "stages": sv[2], "ctas_per_sm": sv[3]}}
+            del graph
+            lat_b.close()
+        launch_bound["note"] = ("L2-resident working sets (no HBM roofline); one launch per "
+                                "step overlapped by programmatic dependent launch vs replay of "
+                                "captured 100-step graphs")
+
     # FNO throughput alone (B=32, 256x256, 4 channels -> 32 latent, 4 layers, 12x12 modes)
     fno_tp = None
     if rank == 0:
@@ -610,6 +684,20 @@ def main():
         k_lbm, m_fno, dT = 50, 5, 223
         hyb_u = Hybrid(lat_h, net, HybridConfig(mode=1, k_lbm=k_lbm, m_fno=m_fno, neq_mode=1))
         fluid = torch.from_numpy(~np.concatenate([m.ravel() for m in um])).cuda()
+        # sampled trajectories (the two smallest grids) run through the FP64 oracle hybrid
+        # with the same bfloat16 weights, cycle by cycle, for the per-cycle relative L2
+        import oracle
+        offs = np.cumsum([0] + [t["nx"] * t["ny"] for t in ub])
+        sample = sorted(range(len(ub)), key=lambda i: (ub[i]["nx"] * ub[i]["ny"], i))[:2]
+        o_params = synth.fno_random_params(sshape, seed=0)
+        o_state = {}
+        for i in sample:
+            t = ub[i]
+            og = oracle.Grid(nx=t["nx"], ny=t["ny"], tau=t["tau"], bc_west=oracle.BC_VELOCITY,
+                             bc_east=oracle.BC_PRESSURE, west_value=t["u_in"], east_value=1.0)
+            o_state[i] = (og, oracle.rest_state(og, t["solid"]))
+        o_errs = {i: [] for i in sample}
+        o_secs = 0.0
         cyc_ms, ref_ms, errs = [], [], []
         for c in range(args.unsteady_cycles):
             c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -628,6 +716,19 @@ def main():
             num = ((uxh - uxr)[fluid] ** 2 + (uyh - uyr)[fluid] ** 2).sum()
             den = (uxr[fluid] ** 2 + uyr[fluid] ** 2).sum()
             errs.append(float(torch.sqrt(num / den)))
+            o0 = time.perf_counter()
+            for i in sample:
+                og, of = o_state[i]
+                of = oracle.hybrid_unsteady(og, ub[i]["solid"], sshape, o_params, of, k_lbm,
+                                            m_fno, cycles=1)
+                o_state[i] = (og, of)
+                _, oux, ouy = oracle.macro(og, ub[i]["solid"], of)
+                fl_i = ~ub[i]["solid"]
+                gx = uxh[offs[i]:offs[i + 1]].view(og.ny, og.nx).cpu().numpy()
+                gy = uyh[offs[i]:offs[i + 1]].view(og.ny, og.nx).cpu().numpy()
+                dn = np.sqrt(((gx - oux)[fl_i] ** 2 + (gy - ouy)[fl_i] ** 2).sum())
+                o_errs[i].append(float(dn / np.sqrt((oux[fl_i] ** 2 + ouy[fl_i] ** 2).sum())))
+            o_secs += time.perf_counter() - o0
         ucells = lat_h.cells
         steady_ms = float(np.mean(cyc_ms[1:])) if len(cyc_ms) > 1 else cyc_ms[0]
         unsteady = {
@@ -638,13 +739,17 @@ def main():
             "cycles": args.unsteady_cycles, "cycle_ms": cyc_ms, "first_cycle_includes_capture": True,
             "cycle_ms_steady": steady_ms,
             "lbm_glups": k_lbm * ucells / (steady_ms * 1e-3) / 1e9,
+            "rel_l2_u_vs_fp64_oracle_hybrid_per_cycle": {
+                f"traj{i}_{ub[i]['nx']}x{ub[i]['ny']}": o_errs[i] for i in sample},
+            "oracle_hybrid_seconds": o_secs,
             "pure_lbm_ms_per_cycle": float(np.mean(ref_ms)),
-            "eps_T": 1.0 - steady_ms / float(np.mean(ref_ms)),
+            "cost_ratio_vs_pure_lbm_same_time": steady_ms / float(np.mean(ref_ms)),
             "eps_N": 1.0 - k_lbm / (k_lbm + m_fno * dT),
             "rel_l2_u_vs_pure_lbm_per_cycle": errs,
-            "reference": "pure GPU LBM over the same physical time (FP32; matches the FP64 "
-                         "oracle to < 1e-5 rel. L2 in the parity tests)",
-            "fno": "seeded random weights: the error is not a claim about accuracy"}
+            "reference": "parity: the FP64 oracle hybrid (same bfloat16 weights) on the two "
+                         "smallest trajectories; cost: pure GPU LBM over the same physical time",
+            "fno": "seeded random weights: the hybrid is ~100% off pure LBM in u, so the cost "
+                   "ratio is launch-pattern arithmetic, not a speed-up at equal accuracy"}
         hyb_u.close()
         lat_h.close()
         lat_r.close()
@@ -834,11 +939,19 @@ def main():
                                         "ctas_per_sm": shape[3], "autotune_ms": tune_ms},
                          "launch_ms": kms, "traffic": step_kernel_traffic(cells, shape),
                          "traffic_unit": "bytes per launch (ncu dram read + write)"},
+            "time_to_steady_summary": None if tts is None else {
+                "tol": tts["tol"], "trajectories": tts["trajectories"],
+                "fno_init_s": tts["fno_init"]["seconds"],
+                "fno_init_converged": tts["fno_init"]["converged"],
+                "plain_init_s": tts["plain_init"]["seconds"],
+                "plain_init_converged": tts["plain_init"]["converged"],
+                "step_cap": tts["step_cap"]},
             "solve": {"lbm_steps": steps_per_solve, "converged": bool(st.converged),
                       "max_residual": float(st.max_residual)},
             "time_to_steady": tts,
             "tolerance_ladder": ladder,
             "lbm_sweep": sweep,
+            "launch_bound": launch_bound,
             "hybrid_training": training,
             "double_shear": shear,
             "fno_throughput": fno_tp,
@@ -850,9 +963,12 @@ def main():
         }
         # our kernels per step: FNO on the tensor-core path (table kernel + lift + 5 per
         # layer + decoder, else 2 twiddle + lift + 5 per layer + decoder), reinit, fill,
-        # pack/unpack, one step kernel per LBM step, two reduction kernels per check
+        # pack/unpack, one step kernel per LBM step (a check runs the step kernel with
+        # statistics: the last check's step is computed and not kept), two reduction
+        # kernels per check
         fno_k = (1 + 1 + 5 * 4 + 1) if net.uses_tensor_cores(NY, NX) else (2 + 1 + 5 * 4 + 1)
-        per_step = fno_k + 1 + 1 + 2 + steps_per_solve + 2 * math.ceil(steps_per_solve / CHECK_EVERY)
+        per_step = (fno_k + 1 + 1 + 2 + steps_per_solve + 1
+                    + 2 * math.ceil(steps_per_solve / CHECK_EVERY))
         line["gpu_launches"] = per_step * args.steps
         print(json.dumps(line), flush=True)
     hyb.close()
