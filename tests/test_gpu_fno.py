@@ -121,6 +121,66 @@ def test_fno_throughput_workload_sampled_against_oracle():
     np.testing.assert_array_equal(y1[0], y[5])
 
 
+def test_fno_throughput_workload_every_item_against_oracle():
+    """Batch 32 at 256x256 (the FNO throughput workload): every item element by element."""
+    _requires_gpu()
+    s, g, params = _pair(width=32, layers=4, modes=12, dec_size=32, seed=0, out_scale=1e-2)
+    net = Fno(g, synth.fno_flatten_params(s, params))
+    assert net.uses_tensor_cores(256, 256)
+    x = _flow_inputs(32, 256, 256)
+    y = net(torch.from_numpy(x).cuda()).cpu().numpy()
+    net.check(32, 256, 256)
+    ref = fo.fno_forward(s, params, x)
+    errs = [rel_l2(y[b], ref[b]) for b in range(32)]
+    print(f"FNO 32x256x256 all items: rel L2 max {max(errs):.3e} mean {np.mean(errs):.3e}")
+    assert max(errs) < REL_L2_FNO and rel_l2(y, ref) < REL_L2_FNO
+
+
+def test_bench_batch_shape_on_tensor_cores():
+    """The bench's steady-framework FNO (C=32, m=12, 4 layers) on its 256 x 512 porous grids,
+    B = 8, input (rho-1 = 0, u = 0, mask) as the steady driver feeds it."""
+    _requires_gpu()
+    s, g, params = _pair(width=32, layers=4, modes=12, dec_size=32, seed=0, out_scale=1.0)
+    net = Fno(g, synth.fno_flatten_params(s, params))
+    assert net.uses_tensor_cores(256, 512)
+    x = np.zeros((8, 4, 256, 512), np.float32)
+    for b in range(8):
+        x[b, 3] = synth.porous_media(512, 256, 4, 12, seed=b)[0]
+    y = net(torch.from_numpy(x).cuda()).cpu().numpy()
+    net.check(8, 256, 512)
+    ref = fo.fno_forward(s, params, x)
+    errs = [rel_l2(y[b], ref[b]) for b in range(8)]
+    print(f"FNO 8x256x512 porous: rel L2 max {max(errs):.3e}")
+    assert max(errs) < REL_L2_FNO
+
+
+def test_spectral_chain_alone_at_full_size():
+    """Fourier layers with W = 0 and b = 0 and a decoder without biases: the output is then
+    carried entirely by the x-DFT, y-DFT, mixing and inverse chain of every layer, so the
+    relative L2 measures that chain (B = 8 of the 256x256 throughput workload)."""
+    _requires_gpu()
+    s, g, params = _pair(width=32, layers=4, modes=12, dec_size=32, seed=2, out_scale=1.0)
+    for n in range(4):
+        params[f"layer{n}.w"] = np.zeros_like(params[f"layer{n}.w"])
+        params[f"layer{n}.b"] = np.zeros_like(params[f"layer{n}.b"])
+        for blk in ("r1.re", "r1.im", "r2.re", "r2.im"):  # gain O(1) per layer
+            k = f"layer{n}.{blk}"
+            params[k] = synth.round_to_bf16((params[k] * 128).astype(np.float32))
+    params["dec0.b"] = np.zeros_like(params["dec0.b"])
+    params["out.b"] = np.zeros_like(params["out.b"])
+    net = Fno(g, synth.fno_flatten_params(s, params))
+    assert net.uses_tensor_cores(256, 256)
+    x = _flow_inputs(8, 256, 256, seed0=40)
+    y = net(torch.from_numpy(x).cuda()).cpu().numpy()
+    net.check(8, 256, 256)
+    ref = fo.fno_forward(s, params, x)
+    # the chain is not trivial: outputs vary in space (not a constant field)
+    assert np.std(ref[0, 0]) > 1e-3 * np.abs(ref[0, 0]).max() > 0
+    errs = [rel_l2(y[b], ref[b]) for b in range(8)]
+    print(f"FNO spectral chain alone 8x256x256: rel L2 max {max(errs):.3e}")
+    assert max(errs) < REL_L2_FNO
+
+
 def test_invalid_fno_shapes_rejected():
     _requires_gpu()
     s, g, params = _pair(modes=4)
