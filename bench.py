@@ -836,7 +836,11 @@ def main():
                              f"tau {setup.tau:.4f}, U {setup.u_lattice:.4f} (lattice), A1, A2 "
                              f"U(20, 125), Delta T = {dT} steps, 30 Delta T horizon",
                  "model_group": {"density_params": nparams[0], "velocity_params": nparams[1],
-                                 "padding": 9, "path": "CUDA cores (14 channels, padded grid)"},
+                                 "padding": 9,
+                                 "path": ("tensor cores (14 channels zero-padded to 16, 137 x 137 "
+                                          "padded grid in 144 x 256 storage)"
+                                          if dnet.uses_tensor_cores(ns, ns) and
+                                          vnet.uses_tensor_cores(ns, ns) else "CUDA cores")},
                  "arms": arms,
                  "fno": "seeded random weights: errors are not an accuracy claim"}
         dnet.close()

@@ -33,6 +33,13 @@ struct FnoOffsets {
   size_t n_params;
   size_t rt_off;     // float offset of the transposed spectral filters
   size_t rt_layer;   // floats per layer of transposed filters
+  // Copies for the tensor-core kernels with the channel dimensions zero-padded to
+  // tcw = fno_tc_width(C), present when tcw != C (tc_pad): lift, per layer the
+  // transposed filters [mode][tcw][tcw], W [tcw][tcw] and b [tcw], decoder layer 0 [S][tcw].
+  bool tc_pad = false;
+  int tcw = 0;
+  size_t tp_lift0_w = 0, tp_lift0_b = 0, tp_lift1_w = 0, tp_lift1_b = 0, tp_q1 = 0;
+  std::vector<size_t> tp_rt, tp_w, tp_b;
   size_t total_floats;
 };
 
@@ -80,6 +87,28 @@ static int fno_offsets(const fno_config& c, FnoOffsets* o) {
   o->rt_off = align_up(p, 64);
   o->rt_layer = 2 * m * m * C * C * 2;  // float2 per (mode, i, o)
   o->total_floats = o->rt_off + o->rt_layer * c.layers;
+  o->tcw = fno_tc_width(c.width);
+  o->tc_pad = (size_t)o->tcw != C;
+  o->tp_rt.clear(); o->tp_w.clear(); o->tp_b.clear();
+  if (o->tc_pad) {
+    const size_t T = o->tcw, th = T / 2;
+    p = align_up(o->total_floats, 64);
+    auto take2 = [&](size_t n) {  // 2-float aligned for float2 arrays
+      p = align_up(p, 2);
+      return take(n);
+    };
+    o->tp_lift0_w = take(th * cin2);
+    o->tp_lift0_b = take(th);
+    o->tp_lift1_w = take(T * th);
+    o->tp_lift1_b = take(T);
+    for (int n = 0; n < c.layers; ++n) {
+      o->tp_rt.push_back(take2(2 * m * m * T * T * 2));
+      o->tp_w.push_back(take(T * T));
+      o->tp_b.push_back(take(T));
+    }
+    o->tp_q1 = take((size_t)c.dec_size * T);
+    o->total_floats = p;
+  }
   return LBM_OK;
 }
 
@@ -142,6 +171,28 @@ __global__ void k_transpose_r(const float* __restrict__ r1re, const float* __res
     const int ky = lo ? a : a - m;
     const size_t src = (((size_t)i * C + o) * m + ky) * m + kx;
     rt[t] = lo ? make_float2(r1re[src], r1im[src]) : make_float2(r2re[src], r2im[src]);
+  }
+}
+
+// dst [drows][dcols] = src [srows][scols] zero-padded (drows >= srows, dcols >= scols)
+__global__ void k_pad2d(const float* __restrict__ src, int srows, int scols,
+                        float* __restrict__ dst, int drows, int dcols) {
+  const size_t n = (size_t)drows * dcols;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / dcols), c = (int)(t % dcols);
+    dst[t] = (r < srows && c < scols) ? src[(size_t)r * scols + c] : 0.0f;
+  }
+}
+// dst[(mode * T + i) * T + o] = src[(mode * C + i) * C + o] for i, o < C, else 0
+__global__ void k_pad_rt(const float2* __restrict__ src, int C, float2* __restrict__ dst, int T,
+                         int modes) {
+  const size_t n = (size_t)modes * T * T;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int o = (int)(t % T), i = (int)((t / T) % T);
+    const size_t mode = t / ((size_t)T * T);
+    dst[t] = (i < C && o < C) ? src[(mode * C + i) * C + o] : make_float2(0.0f, 0.0f);
   }
 }
 
@@ -786,11 +837,14 @@ static bool raise_smem(K kernel) {
                               (int)kRowSmemMax) == cudaSuccess;
 }
 
+constexpr size_t kDecOffsSlots = 32;  // decoder offsets per table (2 per layer, <= 9 layers)
+
 struct fno_handle {
   fno_config cfg;
   FnoOffsets off;
   float* packed = nullptr;  // caller-owned
   unsigned* dec_offs = nullptr;  // inside packed: decoder offsets table (as floats' bits)
+  unsigned* tc_dec_offs = nullptr;  // the same for the tensor-core kernels (padded layer 0)
   bool force_cuda_cores = false;  // use the CUDA-core kernels even where tensor cores apply
 };
 
@@ -807,7 +861,7 @@ int fno_query(const fno_config* cfg_h, int B, int H, int W, fno_sizes* out_h) {
               "fno_query: need 2m <= H + padding and m < (W + padding)/2 (m=%d, H=%d, W=%d)",
               cfg_h->modes, H, W);
   out_h->n_params = o.n_params;
-  out_h->packed_bytes = align_up((o.total_floats + 64) * sizeof(float), 256);
+  out_h->packed_bytes = align_up((o.total_floats + 2 * kDecOffsSlots) * sizeof(float), 256);
   out_h->ws_bytes = std::max(fno_ws_plan(*cfg_h, std::max(B, 1), H, W).total,
                              fno_tc_supported(*cfg_h, H, W)
                                  ? fno_tc_ws_plan(*cfg_h, std::max(B, 1), H, W).total
@@ -852,7 +906,24 @@ int fno_create(const fno_config* cfg_h, const uint16_t* params_d, void* packed_d
                                       reinterpret_cast<float2*>(h->packed + o.rt_off + o.rt_layer * n),
                                       cfg_h->width, cfg_h->modes);
   }
-  // decoder offset table after the transposed filters
+  if (o.tc_pad) {  // zero-padded copies for the tensor-core kernels
+    const int C = cfg_h->width, T = o.tcw, cin2 = cfg_h->c_in + 2;
+    float* P = h->packed;
+    k_pad2d<<<64, 256, 0, s>>>(P + o.lift0_w, C / 2, cin2, P + o.tp_lift0_w, T / 2, cin2);
+    k_pad2d<<<64, 256, 0, s>>>(P + o.lift0_b, 1, C / 2, P + o.tp_lift0_b, 1, T / 2);
+    k_pad2d<<<64, 256, 0, s>>>(P + o.lift1_w, C, C / 2, P + o.tp_lift1_w, T, T / 2);
+    k_pad2d<<<64, 256, 0, s>>>(P + o.lift1_b, 1, C, P + o.tp_lift1_b, 1, T);
+    for (int n = 0; n < cfg_h->layers; ++n) {
+      k_pad_rt<<<512, 256, 0, s>>>(reinterpret_cast<const float2*>(P + o.rt_off + o.rt_layer * n),
+                                   C, reinterpret_cast<float2*>(P + o.tp_rt[n]), T,
+                                   2 * cfg_h->modes * cfg_h->modes);
+      k_pad2d<<<64, 256, 0, s>>>(P + o.w[n], C, C, P + o.tp_w[n], T, T);
+      k_pad2d<<<64, 256, 0, s>>>(P + o.b[n], 1, C, P + o.tp_b[n], 1, T);
+    }
+    k_pad2d<<<64, 256, 0, s>>>(P + o.dec_w[0], cfg_h->dec_size, C, P + o.tp_q1, cfg_h->dec_size, T);
+  }
+  // decoder offset tables after the transposed filters: the CUDA-core kernels', then the
+  // tensor-core kernels' (layer 0's weights zero-padded to the tensor-core width)
   std::vector<unsigned> offs;
   for (int l = 0; l < cfg_h->dec_layers; ++l) {
     offs.push_back((unsigned)o.dec_w[l]);
@@ -860,7 +931,12 @@ int fno_create(const fno_config* cfg_h, const uint16_t* params_d, void* packed_d
   }
   offs.push_back((unsigned)o.out_w);
   offs.push_back((unsigned)o.out_b);
+  offs.resize(kDecOffsSlots, 0u);
+  const std::vector<unsigned> first(offs);
+  offs.insert(offs.end(), first.begin(), first.end());
+  if (o.tc_pad) offs[kDecOffsSlots] = (unsigned)o.tp_q1;
   h->dec_offs = reinterpret_cast<unsigned*>(h->packed + o.total_floats);
+  h->tc_dec_offs = h->dec_offs + kDecOffsSlots;
   if (cudaMemcpyAsync(h->dec_offs, offs.data(), offs.size() * sizeof(unsigned),
                       cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
@@ -887,17 +963,18 @@ int fno_forward(fno_handle* h, const float* in_d, float* out_d, int B, int H, in
     FnoTcParams tp{};
     const float* P0 = h->packed;
     const FnoOffsets& o0 = h->off;
-    tp.lift0_w = P0 + o0.lift0_w;
-    tp.lift0_b = P0 + o0.lift0_b;
-    tp.lift1_w = P0 + o0.lift1_w;
-    tp.lift1_b = P0 + o0.lift1_b;
+    const bool pd = o0.tc_pad;
+    tp.lift0_w = P0 + (pd ? o0.tp_lift0_w : o0.lift0_w);
+    tp.lift0_b = P0 + (pd ? o0.tp_lift0_b : o0.lift0_b);
+    tp.lift1_w = P0 + (pd ? o0.tp_lift1_w : o0.lift1_w);
+    tp.lift1_b = P0 + (pd ? o0.tp_lift1_b : o0.lift1_b);
     for (int n = 0; n < c.layers; ++n) {
-      tp.rt[n] = reinterpret_cast<const float2*>(P0 + o0.rt_off + o0.rt_layer * n);
-      tp.w[n] = P0 + o0.w[n];
-      tp.b[n] = P0 + o0.b[n];
+      tp.rt[n] = reinterpret_cast<const float2*>(P0 + (pd ? o0.tp_rt[n] : o0.rt_off + o0.rt_layer * n));
+      tp.w[n] = P0 + (pd ? o0.tp_w[n] : o0.w[n]);
+      tp.b[n] = P0 + (pd ? o0.tp_b[n] : o0.b[n]);
     }
     tp.params = P0;
-    tp.dec_offs = h->dec_offs;
+    tp.dec_offs = h->tc_dec_offs;
     return fno_forward_tc(c, tp, in_d, out_d, B, H, W, static_cast<char*>(ws_d), SS(stream));
   }
   char* ws = static_cast<char*>(ws_d);

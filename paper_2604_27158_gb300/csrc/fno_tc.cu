@@ -53,30 +53,46 @@ __device__ __forceinline__ float2 act_c2(float2 v) {
 __device__ __forceinline__ int kept_ky_tc(int a, int H, int m) { return a < m ? a : H - 2 * m + a; }
 
 // ------------------------------------------------------------------ tables
-// Fw[x/8][n][x%8]: n < m: cos(2 pi n x / W); m <= n < 2m: -sin(2 pi (n-m) x / W); else 0.
-__device__ void table_fw(int t, __nv_bfloat16* __restrict__ fw, int W, int m) {
-  const int xl = t & 7, n = (t >> 3) & 31, xh = t >> 8;
+// Grid sizes of the tensor-core path.  The Fourier layers run on the (padded) grid
+// Hv x Wv (the input grid plus the padding); the latent field is stored on Hs x Ws
+// (Hs = Hv rounded up to 8 rows, Ws = Wv rounded up to 128 columns).  Every DFT table
+// uses the true periods Hv and Wv and is zero on the storage padding, and the storage
+// padding of the latent field is kept at zero, so the contractions over the padded
+// extents equal the DFTs of the Hv x Wv grid.  K2: the kept x-frequencies as MMA
+// columns, 2m rounded up to 32 or 64.
+struct TcGrid {
+  int H0, W0;  // input / output grid
+  int Hv, Wv;  // grid of the Fourier layers (H0 + padding, W0 + padding)
+  int Hs, Ws;  // storage of the latent field
+};
+__host__ __device__ inline int tc_k2(int m) { return 2 * m <= 32 ? 32 : 64; }
+
+// Fw[x/8][n][x%8] (n < K2): n < K2/2: cos(2 pi n x / Wv) for n < m; K2/2 <= n: -sin(2 pi
+// (n - K2/2) x / Wv) for n - K2/2 < m; 0 elsewhere and for x >= Wv.
+__device__ void table_fw(int t, __nv_bfloat16* __restrict__ fw, int Wv, int m, int k2) {
+  const int xl = t & 7, n = (t >> 3) % k2, xh = (t >> 3) / k2;
   const int x = xh * 8 + xl;
+  const int k = n < k2 / 2 ? n : n - k2 / 2;
   float v = 0.0f;
-  if (n < 2 * m) {
-    const int k = n < m ? n : n - m;
+  if (k < m && x < Wv) {
     float s, c;
-    sincospif(2.0f * (float)((long long)k * x % W) / (float)W, &s, &c);
-    v = n < m ? c : -s;
+    sincospif(2.0f * (float)((long long)k * x % Wv) / (float)Wv, &s, &c);
+    v = n < k2 / 2 ? c : -s;
   }
   fw[t] = __float2bfloat16_rn(v);
 }
-// Ti[k'/8][x][k'%8]: k' < m: c_k cos(2 pi k' x / W) / (H W); m <= k' < 2m:
-// -c_k sin(2 pi (k'-m) x / W) / (H W); else 0; c_0 = 1, c_k = 2 (k > 0).
-__device__ void table_ti(int t, __nv_bfloat16* __restrict__ ti, int H, int W, int m) {
-  const int kl = t & 7, x = (t >> 3) % W, kh = (t >> 3) / W;
+// Ti[k'/8][x][k'%8] (k' < K2, x < Ws): k' < m: c_k cos(2 pi k' x / Wv) / (Hv Wv);
+// m <= k' < 2m: -c_k sin(2 pi (k'-m) x / Wv) / (Hv Wv); else 0, and 0 for x >= Wv;
+// c_0 = 1, c_k = 2 (k > 0).
+__device__ void table_ti(int t, __nv_bfloat16* __restrict__ ti, int Hv, int Wv, int Ws, int m) {
+  const int kl = t & 7, x = (t >> 3) % Ws, kh = (t >> 3) / Ws;
   const int kp = kh * 8 + kl;
   float v = 0.0f;
-  if (kp < 2 * m) {
+  if (kp < 2 * m && x < Wv) {
     const int k = kp < m ? kp : kp - m;
     float s, c;
-    sincospif(2.0f * (float)((long long)k * x % W) / (float)W, &s, &c);
-    const float w = (k == 0 ? 1.0f : 2.0f) / ((float)H * (float)W);
+    sincospif(2.0f * (float)((long long)k * x % Wv) / (float)Wv, &s, &c);
+    const float w = (k == 0 ? 1.0f : 2.0f) / ((float)Hv * (float)Wv);
     v = kp < m ? w * c : -w * s;
   }
   ti[t] = __float2bfloat16_rn(v);
@@ -103,28 +119,29 @@ __host__ __device__ inline SpecDims spec_dims(int C, int m) {
   d.nn = d.nc * d.nchunk;
   return d;
 }
-// Fy[y/4][n][(y%4) * 2 + p], n = 2a + q: the real form of e^{-2 pi i ky(a) y / H} that
-// maps the pair (Re, Im) (p) of X1[y] to (Re, Im) (q) of the kept mode a; 0 for a >= 2m.
-__device__ void table_fy(int t, __nv_bfloat16* __restrict__ fy, int H, int m, int nf) {
+// Fy[y/4][n][(y%4) * 2 + p], n = 2a + q: the real form of e^{-2 pi i ky(a) y / Hv} that
+// maps the pair (Re, Im) (p) of X1[y] to (Re, Im) (q) of the kept mode a; 0 for a >= 2m
+// and for y >= Hv.
+__device__ void table_fy(int t, __nv_bfloat16* __restrict__ fy, int Hv, int m, int nf) {
   const int j = t & 7, n = (t >> 3) % nf, yg = (t >> 3) / nf;
   const int y = yg * 4 + (j >> 1), p = j & 1, a = n >> 1, q = n & 1;
   float v = 0.0f;
-  if (a < 2 * m) {
+  if (a < 2 * m && y < Hv) {
     float sn, cs;
-    sincospif(2.0f * (float)((long long)kept_ky_tc(a, H, m) * y % H) / (float)H, &sn, &cs);
+    sincospif(2.0f * (float)((long long)kept_ky_tc(a, Hv, m) * y % Hv) / (float)Hv, &sn, &cs);
     v = p == 0 ? (q == 0 ? cs : -sn) : (q == 0 ? sn : cs);
   }
   fy[t] = __float2bfloat16_rn(v);
 }
-// Ty[a/4][y][(a%4) * 2 + p]: cos (p = 0) and sin (p = 1) of 2 pi ky(a) y / H for the
+// Ty[a/4][y][(a%4) * 2 + p]: cos (p = 0) and sin (p = 1) of 2 pi ky(a) y / Hv for the
 // inverse y-DFT; rows padded to hp (a multiple of 128) and a >= 2m are 0.
-__device__ void table_ty(int t, __nv_bfloat16* __restrict__ ty, int H, int hp, int m, int kg) {
+__device__ void table_ty(int t, __nv_bfloat16* __restrict__ ty, int Hv, int hp, int m, int kg) {
   const int j = t & 7, y = (t >> 3) % hp, g = (t >> 3) / hp;
   const int a = g * 4 + (j >> 1), p = j & 1;
   float v = 0.0f;
-  if (a < 2 * m && y < H) {
+  if (a < 2 * m && y < Hv) {
     float sn, cs;
-    sincospif(2.0f * (float)((long long)kept_ky_tc(a, H, m) * y % H) / (float)H, &sn, &cs);
+    sincospif(2.0f * (float)((long long)kept_ky_tc(a, Hv, m) * y % Hv) / (float)Hv, &sn, &cs);
     v = p == 0 ? cs : sn;
   }
   ty[t] = __float2bfloat16_rn(v);
@@ -133,17 +150,18 @@ __device__ void table_ty(int t, __nv_bfloat16* __restrict__ ty, int H, int hp, i
 // All four DFT tables of one forward in one launch (FP32 sines and cosines of exactly
 // reduced integer phases; the tables are stored in bfloat16).
 __global__ void k_tables(__nv_bfloat16* __restrict__ fw, __nv_bfloat16* __restrict__ ti,
-                         __nv_bfloat16* __restrict__ fy, __nv_bfloat16* __restrict__ ty, int H,
-                         int W, int m, int hp, int nf, int kg) {
+                         __nv_bfloat16* __restrict__ fy, __nv_bfloat16* __restrict__ ty,
+                         TcGrid g, int m, int hp, int nf, int kg) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int n_fw = W * 32, n_fy = (H / 4) * nf * 8, n_ty = kg * hp * 8;
-  if (t < n_fw) return table_fw(t, fw, W, m);
+  const int k2 = tc_k2(m);
+  const int n_fw = g.Ws * k2, n_fy = (g.Hs / 4) * nf * 8, n_ty = kg * hp * 8;
+  if (t < n_fw) return table_fw(t, fw, g.Wv, m, k2);
   t -= n_fw;
-  if (t < n_fw) return table_ti(t, ti, H, W, m);
+  if (t < n_fw) return table_ti(t, ti, g.Hv, g.Wv, g.Ws, m);
   t -= n_fw;
-  if (t < n_fy) return table_fy(t, fy, H, m, nf);
+  if (t < n_fy) return table_fy(t, fy, g.Hv, m, nf);
   t -= n_fy;
-  if (t < n_ty) return table_ty(t, ty, H, hp, m, kg);
+  if (t < n_ty) return table_ty(t, ty, g.Hv, hp, m, kg);
 }
 
 // ---------------------------------------------------- lifting / projection
@@ -153,12 +171,17 @@ __global__ void k_tables(__nv_bfloat16* __restrict__ fw, __nv_bfloat16* __restri
 // (M = 128 x positions of one row, N = C, K = C/2 padded to 16) with the bias added in
 // the epilogue.  Several CTAs share an SM; each serialises fill -> MMA -> drain.
 constexpr int kLiftCtasPerSm = 6;
+// The tiles cover the storage grid Hs x Ws: pixels outside the input grid H0 x W0 (the
+// zero padding of the lifted field and the storage padding) are written as 0 without an
+// MMA, and rows y >= Hv of the second latent buffer `theta_alt` are zeroed too (no layer
+// writes them).
 template <int kC, int kCin, int kAct>
 __global__ void __launch_bounds__(128, kLiftCtasPerSm)
     k_lift_tc(const float* __restrict__ in, __nv_bfloat16* __restrict__ theta,
-              const float* __restrict__ w0, const float* __restrict__ b0,
-              const float* __restrict__ w1, const float* __restrict__ b1, int B, int H, int W,
-              int cin_rt, unsigned* __restrict__ status) {
+              __nv_bfloat16* __restrict__ theta_alt, const float* __restrict__ w0,
+              const float* __restrict__ b0, const float* __restrict__ w1,
+              const float* __restrict__ b1, int B, TcGrid gd, int cin_rt,
+              unsigned* __restrict__ status) {
   constexpr int kHid = kC / 2;
   constexpr int kK = kHid < 16 ? 16 : kHid;  // MMA K (zero-padded hidden units)
   constexpr int kKG = kK / 8;
@@ -196,20 +219,33 @@ __global__ void __launch_bounds__(128, kLiftCtasPerSm)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base;
-  const int xt = W / 128;
-  const int ntiles = B * H * xt;
+  const int H = gd.H0, W = gd.W0, Hs = gd.Hs, Ws = gd.Ws;
+  const int xt = Ws / 128;
+  const int ntiles = B * Hs * xt;
   constexpr uint32_t idesc = idesc_bf16(128, kC, false, false);
-  int j = 0;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
-    const int row = t / xt;  // b * H + y
-    const int y = row % H, b = row / H;
-    const int x = (t - row * xt) * 128 + threadIdx.x;
+  int j = 0;  // MMA tiles of this CTA
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int row = t / xt;  // b * Hs + y
+    const int y = row % Hs, b = row / Hs;
+    const int x0 = (t - row * xt) * 128, x = x0 + threadIdx.x;
+    if (y >= H || x0 >= W) {  // CTA-uniform: the tile is padding
+#pragma unroll
+      for (int g = 0; g < kC / 8; ++g) {
+        const size_t at = (((size_t)row * (kC / 8) + g) * Ws + x) * 8;
+        *reinterpret_cast<uint4*>(theta + at) = make_uint4(0, 0, 0, 0);
+        if (y >= gd.Hv) *reinterpret_cast<uint4*>(theta_alt + at) = make_uint4(0, 0, 0, 0);
+      }
+      continue;
+    }
+    const bool valid = x < W;
     // layer 1 for this thread's pixel (inputs and coordinates rounded to bfloat16)
     float xin[kX];
 #pragma unroll
     for (int c = 0; c < (kCin > 0 ? kCin : 16); ++c)
       if (c < cin)
-        xin[c] = __bfloat162float(__float2bfloat16_rn(in[(((size_t)b * cin + c) * H + y) * W + x]));
+        xin[c] = valid ? __bfloat162float(__float2bfloat16_rn(
+                             in[(((size_t)b * cin + c) * H + y) * W + x]))
+                       : 0.0f;
     xin[cin] = __bfloat162float(__float2bfloat16_rn((float)x / (float)max(W - 1, 1)));
     xin[cin + 1] = __bfloat162float(__float2bfloat16_rn((float)y / (float)max(H - 1, 1)));
     __align__(16) __nv_bfloat16 h[kHid];
@@ -239,6 +275,7 @@ __global__ void __launch_bounds__(128, kLiftCtasPerSm)
       mma_commit(&mma_bar);
     }
     const bool ok = mbar_wait_sleep(&mma_bar, j & 1, status);
+    ++j;
     if (__syncthreads_or(!ok)) break;  // the whole CTA leaves together after a timeout
     tc_fence_after();
 #pragma unroll
@@ -255,10 +292,10 @@ __global__ void __launch_bounds__(128, kLiftCtasPerSm)
         for (int q = 0; q < 8; q += 2) {
           const float2 r = __fadd2_rn(make_float2(v[g * 8 + q], v[g * 8 + q + 1]),
                                       *reinterpret_cast<const float2*>(&b1_s[o0 + q]));
-          o8[q] = __float2bfloat16_rn(r.x);
-          o8[q + 1] = __float2bfloat16_rn(r.y);
+          o8[q] = __float2bfloat16_rn(valid ? r.x : 0.0f);
+          o8[q + 1] = __float2bfloat16_rn(valid ? r.y : 0.0f);
         }
-        *reinterpret_cast<uint4*>(theta + (((size_t)row * (kC / 8) + o0 / 8) * W + x) * 8) =
+        *reinterpret_cast<uint4*>(theta + (((size_t)row * (kC / 8) + o0 / 8) * Ws + x) * 8) =
             *reinterpret_cast<const uint4*>(o8);
       }
     }
@@ -270,12 +307,14 @@ __global__ void __launch_bounds__(128, kLiftCtasPerSm)
 }
 
 // Projection Q from the channel-blocked field, any decoder shape (the common shape
-// runs in k_decoder_tc); one thread per pixel, decoder weights staged in shared memory.
+// runs in k_decoder_tc); one thread per pixel of the output grid H0 x W0 (the padded
+// grid is cropped), decoder weights staged in shared memory.
 template <int kC>
 __global__ void __launch_bounds__(128)
     k_decoder_blk(const __nv_bfloat16* __restrict__ theta, float* __restrict__ out,
                   const float* __restrict__ params, const unsigned* __restrict__ offs,
-                  int nlayers, int B, int H, int W, int S, int cout, int act) {
+                  int nlayers, int B, TcGrid gd, int S, int cout, int act) {
+  const int H = gd.H0, W = gd.W0;
   extern __shared__ float dec_s[];
   // layout: for each layer l: w [S][fan] then b [S]; then out.w [cout][fan], out.b [cout]
   int at = 0, fan = kC;
@@ -293,13 +332,13 @@ __global__ void __launch_bounds__(128)
   const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (p >= pix) return;
   const int x = (int)(p % W);
-  const size_t row = p / W;
-  const int y = (int)(row % H);
-  const int b = (int)(row / H);
+  const int y = (int)((p / W) % H);
+  const int b = (int)(p / ((size_t)W * H));
+  const size_t row = (size_t)b * gd.Hs + y;  // storage row
   float a[kC];
 #pragma unroll
   for (int g = 0; g < kC / 8; ++g) {
-    const uint4 v = *reinterpret_cast<const uint4*>(theta + ((row * (kC / 8) + g) * W + x) * 8);
+    const uint4 v = *reinterpret_cast<const uint4*>(theta + ((row * (kC / 8) + g) * gd.Ws + x) * 8);
     const __nv_bfloat16* hv = reinterpret_cast<const __nv_bfloat16*>(&v);
 #pragma unroll
     for (int q = 0; q < 8; ++q) a[g * 8 + q] = __bfloat162float(hv[q]);
@@ -338,16 +377,17 @@ constexpr int kFwdChunk = 64;    // x positions per stage
 constexpr int kFwdStages = 3;
 constexpr int kFwdStageBytes = 128 * kFwdChunk * 2;  // 16 KB: 128 (row, channel) x 64 x
 
-template <int kC>
+template <int kC, int kK2>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_fwd_x_tc(const __nv_bfloat16* __restrict__ theta, const __nv_bfloat16* __restrict__ fw,
                __nv_bfloat16* __restrict__ x1b, int B, int H, int W, int m,
                unsigned* __restrict__ status) {
+  // H, W: the storage grid Hs x Ws (the table is zero beyond the layers' grid)
   constexpr int kRows = 128 / kC;  // image rows per tile
   constexpr int kG = kC / 8;       // 8-channel groups
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* fw_s = smem;                                // W * 64 bytes
-  unsigned char* stages = smem + (size_t)W * 64;             // kFwdStages * 16 KB
+  unsigned char* fw_s = smem;                                // W * kK2 * 2 bytes
+  unsigned char* stages = smem + (size_t)W * kK2 * 2;        // kFwdStages * 16 KB
   __shared__ __align__(8) uint64_t full_bar[kFwdStages], empty_bar[kFwdStages];
   __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], fw_bar;
   __shared__ uint32_t tmem_base;
@@ -368,7 +408,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     mbar_init(&fw_bar, 1);
     mbar_init_fence();
   }
-  if (warp == 0) tmem_alloc(&tmem_base, 64);
+  if (warp == 0) tmem_alloc(&tmem_base, 2 * kK2);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -377,8 +417,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (warp == 4) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
-      mbar_arrive_expect_tx(&fw_bar, (unsigned)(W * 64));
-      bulk_g2s(fw_s, fw, (unsigned)(W * 64), &fw_bar);
+      mbar_arrive_expect_tx(&fw_bar, (unsigned)(W * kK2 * 2));
+      bulk_g2s(fw_s, fw, (unsigned)(W * kK2 * 2), &fw_bar);
     }
     __syncwarp();
     int k = 0;
@@ -407,7 +447,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_wait_sleep(&full_bar[q % kFwdStages], (q / kFwdStages) & 1, status);
   } else if (warp == 5) {
     // ---------------------------------------------------------------- MMA
-    constexpr uint32_t idesc = idesc_bf16(128, 32, /*a_mn=*/true, /*b_mn=*/false);
+    constexpr uint32_t idesc = idesc_bf16(128, kK2, /*a_mn=*/true, /*b_mn=*/false);
     bool ok = mbar_wait_sleep(&fw_bar, 0, status);
     int k = 0, j = 0;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++j) {
@@ -426,9 +466,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           for (int kk = 0; kk < kFwdChunk / 16; ++kk) {
             // A: MN-major, K-adjacent core matrices 128 B apart, MN-adjacent 1024 B
             const uint64_t ad = smem_desc(st + kk * 256, 128, kFwdChunk * 16);
-            // B: K-major, K-adjacent core matrices 512 B apart, N-adjacent 128 B
-            const uint64_t bd = smem_desc(fw_s + (size_t)((ch * kFwdChunk + kk * 16) / 8) * 512, 512, 128);
-            mma_bf16(tmem + acc * 32, ad, bd, idesc, ch > 0 || kk > 0);
+            // B: K-major, K-adjacent core matrices kK2 * 16 B apart, N-adjacent 128 B
+            const uint64_t bd = smem_desc(
+                fw_s + (size_t)((ch * kFwdChunk + kk * 16) / 8) * (kK2 * 16), kK2 * 16, 128);
+            mma_bf16(tmem + acc * kK2, ad, bd, idesc, ch > 0 || kk > 0);
           }
           mma_commit(&empty_bar[s]);  // stage reusable once these MMAs have read it
         }
@@ -445,8 +486,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int acc = j & 1;
       if (!mbar_wait_sleep(&acc_full[acc], (j >> 1) & 1, status)) break;
       tc_fence_after();
-      float v[32];
-      tmem_ld32(tmem + acc * 32 + ((uint32_t)(warp * 32) << 16), v);
+      float v[kK2];
+#pragma unroll
+      for (int q = 0; q < kK2 / 32; ++q)
+        tmem_ld32(tmem + acc * kK2 + q * 32 + ((uint32_t)(warp * 32) << 16), v + q * 32);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[acc]);
@@ -455,12 +498,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int r = mi / kC, c = mi - r * kC;
       const int y = y0 + r;
       if (y < H) {
-        // X1b[b][y/4][kx][c][(y%4) * 2 + re|im]: the K-major operand of the y-DFT
+        // X1b[b][y/4][kx][c][(y%4) * 2 + re|im]: the K-major operand of the y-DFT; column
+        // kx holds the cosine sum, column kK2/2 + kx the negated sine sum
         uint32_t* o = reinterpret_cast<uint32_t*>(x1b) +
                       ((((size_t)b * (H / 4) + (y >> 2)) * m) * kC + c) * 4 + (y & 3);
-        for (int kx = 0; kx < m; ++kx) {
-          const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[kx], v[m + kx]);
-          o[(size_t)kx * kC * 4] = *reinterpret_cast<const uint32_t*>(&h2);
+#pragma unroll
+        for (int kx = 0; kx < kK2 / 2; ++kx) {
+          if (kx < m) {
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[kx], v[kK2 / 2 + kx]);
+            o[(size_t)kx * kC * 4] = *reinterpret_cast<const uint32_t*>(&h2);
+          }
         }
       }
     }
@@ -469,7 +516,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, 64);
+  if (warp == 0) tmem_dealloc(tmem, 2 * kK2);
 }
 
 // ------------------------------------------------------ 2. y-DFT (tcgen05)
@@ -512,7 +559,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     mbar_init(&fy_bar, 1);
     mbar_init_fence();
   }
-  if (warp == 0) tmem_alloc(&tmem_base, 128);  // two accumulators of up to 64 columns
+  const int acc_cols = d.nf <= 64 ? 64 : 128;  // two accumulators of nf <= 128 columns
+  if (warp == 0) tmem_alloc(&tmem_base, 2 * acc_cols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -567,7 +615,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           for (int kk = 0; kk < gn / 2; ++kk) {
             const uint64_t ad = smem_desc(st + kk * 4096, 2048, 128);
             const uint64_t bd = smem_desc(fy_s + (size_t)(g0 + 2 * kk) * d.nf * 16, d.nf * 16, 128);
-            mma_bf16(tmem + acc * 64, ad, bd, idesc, ch > 0 || kk > 0);
+            mma_bf16(tmem + acc * acc_cols, ad, bd, idesc, ch > 0 || kk > 0);
           }
           mma_commit(&empty_bar[s]);
         }
@@ -588,7 +636,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int kx = row / kC, c = row - kx * kC;
       for (int cb = 0; cb < d.nf / 16; ++cb) {
         float v[16];
-        tmem_ld16(tmem + acc * 64 + cb * 16 + ((uint32_t)(warp * 32) << 16), v);
+        tmem_ld16(tmem + acc * acc_cols + cb * 16 + ((uint32_t)(warp * 32) << 16), v);
         if (row < rows) {
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
@@ -605,7 +653,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, 128);
+  if (warp == 0) tmem_dealloc(tmem, 2 * acc_cols);
 }
 
 // ----------------------------------------- 3. per-mode channel mixing (CUDA cores)
@@ -679,14 +727,24 @@ __global__ void __launch_bounds__(256)
 }
 
 // ---------------------------------------------- 3b. inverse y-DFT (tcgen05)
-// Zt[b][y][k'/8][o][k'%8] (bf16) = D[y][n(k', o)] = Ty[y][(a, re|im)] * Yb[(a, re|im)][n]:
-// k' < m gives Re Z(kx = k'), m <= k' < 2m gives Im Z(kx = k' - m) with
-// Z[kx][o] = sum_a Y[a][kx][o] e^{+2 pi i ky(a) y / H}; k' in [2m, 32) is written as 0.
-// One tile = (b, 128 rows, one chunk of knk k'); M = 128, N = knk * C, K = nf.
-constexpr int kIyStages = 4;
+// Zt[b][y][k'/8][o][k'%8] (bf16, kK2 slots k') = D[y][n(k', o)] = Ty[y][(a, re|im)] *
+// Yb[(a, re|im)][n]: k' < m gives Re Z(kx = k'), m <= k' < 2m gives Im Z(kx = k' - m)
+// with Z[kx][o] = sum_a Y[a][kx][o] e^{+2 pi i ky(a) y / H}; k' in [2m, kK2) is written
+// as 0.  One tile = (b, 128 rows, one chunk of knk k'); M = 128, N = knk * C, K = nf.
+// H: the layers' grid rows Hv (rows y >= Hv are not written).
+constexpr int kIyStagesMax = 4;
 constexpr int kIyMinSmem = 120 * 1024;  // one CTA per SM: the accumulators fill the TMEM
+constexpr int kTcSmemMax = 200 * 1024;
+__host__ __device__ inline int iy_stage_bytes(int C, int m) {
+  const SpecDims d = spec_dims(C, m);
+  return d.kg * 2048 + d.kg * d.nchunk * 16;
+}
+__host__ __device__ inline int iy_stages(int C, int m) {
+  const int n = kTcSmemMax / iy_stage_bytes(C, m);
+  return n < kIyStagesMax ? n : kIyStagesMax;
+}
 
-template <int kC>
+template <int kC, int kK2>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_iydft_tc(const __nv_bfloat16* __restrict__ ty, const __nv_bfloat16* __restrict__ yb,
                __nv_bfloat16* __restrict__ zt, int B, int H, int m,
@@ -699,8 +757,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int ntiles = B * yt_n * d.nc;
   const int a_bytes = d.kg * 2048, b_bytes = d.kg * kN * 16;
   const int stage_bytes = a_bytes + b_bytes;
+  const int kIyStages = iy_stages(kC, m);
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t full_bar[kIyStages], empty_bar[kIyStages];
+  __shared__ __align__(8) uint64_t full_bar[kIyStagesMax], empty_bar[kIyStagesMax];
   __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_base;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -782,7 +841,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int yt = rem / d.nc, ci = rem - yt * d.nc;
       const int y = yt * 128 + warp * 32 + lane;
       const int kp0 = ci * kKnk;
-      __nv_bfloat16* zrow = zt + ((size_t)b * H + y) * 32 * kC + (kp0 / 8) * kC * 8 + (kp0 % 8);
+      __nv_bfloat16* zrow = zt + ((size_t)b * H + y) * kK2 * kC + (kp0 / 8) * kC * 8 + (kp0 % 8);
 #pragma unroll 1
       for (int cb = 0; cb < kN / 32; ++cb) {
         float v[32];
@@ -804,9 +863,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[acc]);
-      if (ci == d.nc - 1 && y < H) {  // k' in [nc * knk, 32): zero
-        __nv_bfloat16* zr = zt + ((size_t)b * H + y) * 32 * kC;
-        for (int kp = d.nc * kKnk; kp < 32; kp += kKnk)
+      if (ci == d.nc - 1 && y < H) {  // k' in [nc * knk, kK2): zero
+        __nv_bfloat16* zr = zt + ((size_t)b * H + y) * kK2 * kC;
+        for (int kp = d.nc * kKnk; kp < kK2; kp += kKnk)
           for (int o = 0; o < kC; ++o) {
             if constexpr (kKnk == 8)
               *reinterpret_cast<uint4*>(zr + ((kp / 8) * kC + o) * 8) = make_uint4(0, 0, 0, 0);
@@ -831,14 +890,18 @@ constexpr int inv_ctas_per_sm() { return kC <= 32 ? 3 : 2; }
 constexpr int kInvEpiWarps = 8;  // two groups of four: each drains alternate tiles
 constexpr int kInvThreads = (kInvEpiWarps + 2) * 32;
 
-template <int kC, int kAct>
+// Tiles: the layers' grid rows y < Hv, 128 storage columns each; columns x >= Wv (the
+// storage padding) are written as 0.  Zt rows are indexed on the Hv grid, latent rows on
+// the Hs storage.
+template <int kC, int kAct, int kK2>
 __global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
     k_inv_x_tc(const __nv_bfloat16* __restrict__ theta, const __nv_bfloat16* __restrict__ ti,
                const __nv_bfloat16* __restrict__ zt, const float* __restrict__ wmat,
-               const float* __restrict__ bias, __nv_bfloat16* __restrict__ out, int B, int H,
-               int W, unsigned* __restrict__ status) {
+               const float* __restrict__ bias, __nv_bfloat16* __restrict__ out, int B, TcGrid gd,
+               unsigned* __restrict__ status) {
   constexpr int kG = kC / 8;
-  constexpr int kKG = 4 + kG;                 // K groups of 8: 4 spectral (k' < 32) + C channels
+  constexpr int kSG = kK2 / 8;                // spectral K groups (k' < kK2)
+  constexpr int kKG = kSG + kG;               // K groups of 8: spectral + C channels
   constexpr int kABytes = kKG * 128 * 16;     // A: [k group][x (128)][8]
   constexpr int kBBytes = kKG * kC * 16;      // B: [k group][o (C)][8]
   constexpr int kStageBytes = kABytes + kBBytes;
@@ -849,6 +912,7 @@ __global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
   __shared__ uint32_t tmem_base;
   __shared__ __align__(16) float bias_s[kC];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int H = gd.Hv, W = gd.Ws;
   const int xt = W / 128;
   const int ntiles = B * H * xt;
 
@@ -857,7 +921,7 @@ __global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
     const int s = e / (kG * kC * 8), q = e - s * (kG * kC * 8);
     const int g = q / (kC * 8), o = (q / 8) % kC, il = q % 8;
     __nv_bfloat16* bq = reinterpret_cast<__nv_bfloat16*>(smem + (size_t)s * kStageBytes + kABytes);
-    bq[(4 + g) * kC * 8 + o * 8 + il] = __float2bfloat16_rn(wmat[o * kC + g * 8 + il]);
+    bq[(kSG + g) * kC * 8 + o * 8 + il] = __float2bfloat16_rn(wmat[o * kC + g * 8 + il]);
   }
   for (int o = threadIdx.x; o < kC; o += blockDim.x) bias_s[o] = bias[o];
   fence_proxy_async_smem();
@@ -886,19 +950,21 @@ __global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
       const int s = k % kInvStages;
       if (k >= kInvStages) ok = mbar_wait_sleep(&empty_bar[s], ((k / kInvStages) - 1) & 1, status);
       if (!ok) break;
-      const int row = t / xt;  // b * H + y
+      const int row = t / xt;  // b * Hv + y
       const int x0 = (t - row * xt) * 128;
+      const int b = row / H, y = row - b * H;
+      const size_t srow = (size_t)b * gd.Hs + y;  // latent storage row
       unsigned char* st = smem + (size_t)s * kStageBytes;
-      if (lane == 0) mbar_arrive_expect_tx(&full_bar[s], (unsigned)(kKG * 128 * 16 + 4 * kC * 16));
+      if (lane == 0)
+        mbar_arrive_expect_tx(&full_bar[s], (unsigned)(kKG * 128 * 16 + kSG * kC * 16));
       __syncwarp();
-      if (lane < 4) {  // inverse-DFT table, k group = lane
+      if (lane < kSG) {  // inverse-DFT table, k group = lane
         bulk_g2s(st + lane * 2048, ti + ((size_t)lane * W + x0) * 8, 2048, &full_bar[s]);
-      } else if (lane < 4 + kG) {  // latent channels, group lane - 4
-        const int g = lane - 4;
-        bulk_g2s(st + lane * 2048, theta + (((size_t)row * kG + g) * W + x0) * 8, 2048,
-                 &full_bar[s]);
-      } else if (lane == 4 + kG) {  // spectral half of B: Zt row
-        bulk_g2s(st + kABytes, zt + (size_t)row * 32 * kC, 4 * kC * 16, &full_bar[s]);
+      } else if (lane < kSG + kG) {  // latent channels, group lane - kSG
+        const int g = lane - kSG;
+        bulk_g2s(st + lane * 2048, theta + ((srow * kG + g) * W + x0) * 8, 2048, &full_bar[s]);
+      } else if (lane == kSG + kG) {  // spectral half of B: Zt row
+        bulk_g2s(st + kABytes, zt + (size_t)row * kK2 * kC, kSG * kC * 16, &full_bar[s]);
       }
     }
     for (int q = max(0, k - kInvStages); q < k; ++q)
@@ -937,6 +1003,9 @@ __global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
       tc_fence_after();
       const int row = t / xt;
       const int x = (t - row * xt) * 128 + quad * 32 + lane;
+      const int b = row / H;
+      const size_t srow = (size_t)b * gd.Hs + (row - b * H);
+      const bool valid = x < gd.Wv;
 #pragma unroll
       for (int cb = 0; cb < (kC + 31) / 32; ++cb) {
         constexpr int kCols = kC < 32 ? kC : 32;
@@ -958,10 +1027,10 @@ __global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
             const float2 r = act_c2<kAct>(
                 __fadd2_rn(make_float2(v[g * 8 + q], v[g * 8 + q + 1]),
                            *reinterpret_cast<const float2*>(&bias_s[o0 + q])));
-            o8[q] = __float2bfloat16_rn(r.x);
-            o8[q + 1] = __float2bfloat16_rn(r.y);
+            o8[q] = __float2bfloat16_rn(valid ? r.x : 0.0f);
+            o8[q + 1] = __float2bfloat16_rn(valid ? r.y : 0.0f);
           }
-          *reinterpret_cast<uint4*>(out + (((size_t)row * kG + o0 / 8) * W + x) * 8) =
+          *reinterpret_cast<uint4*>(out + ((srow * kG + o0 / 8) * W + x) * 8) =
               *reinterpret_cast<const uint4*>(o8);
         }
       }
@@ -984,11 +1053,14 @@ constexpr int kDecCtasPerSm = 2;
 constexpr int kDecEpiWarps = 8;  // two groups of four: each drains alternate tiles
 constexpr int kDecThreads = (kDecEpiWarps + 2) * 32;
 
+// Tiles: 128 columns of a row of the output grid H0 x W0 (W0 a multiple of 128), read
+// from the latent storage (the padded grid is cropped).
 template <int kC, int kOut, int kAct>
 __global__ void __launch_bounds__(kDecThreads, kDecCtasPerSm)
     k_decoder_tc(const __nv_bfloat16* __restrict__ theta, float* __restrict__ out,
                  const float* __restrict__ params, const unsigned* __restrict__ offs, int B,
-                 int H, int W, unsigned* __restrict__ status) {
+                 TcGrid gd, unsigned* __restrict__ status) {
+  const int H = gd.H0, W = gd.W0;
   constexpr int kS = kC;
   constexpr int kG = kC / 8;
   constexpr int kStageBytes = kG * 128 * 16;  // [channel group][x (128)][8]
@@ -1049,13 +1121,15 @@ __global__ void __launch_bounds__(kDecThreads, kDecCtasPerSm)
       const int s = k % kDecStages;
       if (k >= kDecStages) ok = mbar_wait_sleep(&empty_bar[s], ((k / kDecStages) - 1) & 1, status);
       if (!ok) break;
-      const int row = t / xt;  // b * H + y
+      const int row = t / xt;  // b * H0 + y
       const int x0 = (t - row * xt) * 128;
+      const int b = row / H;
+      const size_t srow = (size_t)b * gd.Hs + (row - b * H);  // latent storage row
       unsigned char* st = stages + (size_t)s * kStageBytes;
       if (lane == 0) mbar_arrive_expect_tx(&full_bar[s], (unsigned)kStageBytes);
       __syncwarp();
       if (lane < kG)
-        bulk_g2s(st + lane * 2048, theta + (((size_t)row * kG + lane) * W + x0) * 8, 2048,
+        bulk_g2s(st + lane * 2048, theta + ((srow * kG + lane) * gd.Ws + x0) * 8, 2048,
                  &full_bar[s]);
     }
     for (int q = max(0, k - kDecStages); q < k; ++q)
@@ -1132,56 +1206,76 @@ __global__ void __launch_bounds__(kDecThreads, kDecCtasPerSm)
 }
 
 // ------------------------------------------------------------------- host
-// Shared memory of the y-DFT kernel: the Fy table plus the operand ring.
-static size_t ydft_smem(int C, int H, int m) {
+int fno_tc_width(int C) { return C <= 16 ? 16 : (C <= 32 ? 32 : 64); }
+
+static TcGrid tc_grid(const fno_config& c, int H, int W) {
+  TcGrid g;
+  g.H0 = H;
+  g.W0 = W;
+  g.Hv = H + c.padding;
+  g.Wv = W + c.padding;
+  g.Hs = (g.Hv + 7) / 8 * 8;
+  g.Ws = (g.Wv + 127) / 128 * 128;
+  return g;
+}
+// Shared memory of the kernels whose footprint depends on the shape.
+static size_t fwd_smem(int Ws, int k2) { return (size_t)Ws * k2 * 2 + (size_t)kFwdStages * kFwdStageBytes; }
+static size_t ydft_smem(int C, int Hs, int m) {
   const SpecDims d = spec_dims(C, m);
-  return align_up((size_t)(H / 4) * d.nf * 16, 1024) + (size_t)kYStages * kYStageBytes;
+  return align_up((size_t)(Hs / 4) * d.nf * 16, 1024) + (size_t)kYStages * kYStageBytes;
 }
 static size_t iydft_smem(int C, int m) {
-  const SpecDims d = spec_dims(C, m);
-  const size_t st = (size_t)d.kg * 2048 + (size_t)d.kg * d.nchunk * 16;
-  return std::max((size_t)kIyStages * st, (size_t)kIyMinSmem);
+  return std::max((size_t)iy_stages(C, m) * iy_stage_bytes(C, m), (size_t)kIyMinSmem);
+}
+static size_t inv_smem(int C, int k2) {
+  const int kkg = k2 / 8 + C / 8;
+  return (size_t)kInvStages * ((size_t)kkg * 128 * 16 + (size_t)kkg * C * 16);
 }
 
 bool fno_tc_supported(const fno_config& c, int H, int W) {
-  const int C = c.width, m = c.modes;
-  if (c.padding != 0 || !(C == 16 || C == 32 || C == 64) || m < 1 || m > 16 || 2 * m > H ||
-      H % 8 != 0 || W % 128 != 0 || W > 2048 || c.c_in > 16)
+  const int C = fno_tc_width(c.width), m = c.modes;
+  const TcGrid g = tc_grid(c, H, W);
+  if (m < 1 || m > 32 || 2 * m > g.Hv || 2 * m >= g.Wv || g.Ws > 2048 || c.c_in > 16 || H < 1 ||
+      W < 1)
     return false;
-  return ydft_smem(C, H, m) <= 200 * 1024 && iydft_smem(C, m) <= 200 * 1024;
+  const int k2 = tc_k2(m);
+  return fwd_smem(g.Ws, k2) <= (size_t)kTcSmemMax && ydft_smem(C, g.Hs, m) <= (size_t)kTcSmemMax &&
+         iy_stages(C, m) >= 2 && inv_smem(C, k2) <= (size_t)kTcSmemMax;
 }
 
 FnoTcWs fno_tc_ws_plan(const fno_config& c, int B, int H, int W) {
   FnoTcWs w{};
-  const size_t C = c.width, m = c.modes;
+  const size_t C = fno_tc_width(c.width), m = c.modes, k2 = tc_k2(c.modes);
   const SpecDims d = spec_dims((int)C, (int)m);
+  const TcGrid g = tc_grid(c, H, W);
   size_t p = 0;
   auto take = [&](size_t bytes) {
     const size_t a = p;
     p = align_up(p + bytes, 256);
     return a;
   };
-  const size_t pix = (size_t)B * H * W;
-  const size_t hp = ((size_t)H + 127) / 128 * 128;
-  w.theta0 = take(pix * C * 2);
-  w.theta1 = take(pix * C * 2);
-  w.x1b = take((size_t)B * H * m * C * 4);
+  const size_t spix = (size_t)B * g.Hs * g.Ws;
+  const size_t hp = ((size_t)g.Hv + 127) / 128 * 128;
+  w.theta0 = take(spix * C * 2);
+  w.theta1 = take(spix * C * 2);
+  w.x1b = take((size_t)B * g.Hs * m * C * 4);
   w.xh = take((size_t)2 * m * m * B * C * sizeof(float2));
   w.yb = take((size_t)B * d.kg * d.nn * 16);
-  w.zt = take((size_t)B * H * 32 * C * 2);
-  w.fw = take((size_t)W * 64);
-  w.ti = take((size_t)W * 64);
-  w.fy = take((size_t)(H / 4) * d.nf * 16);
+  w.zt = take((size_t)B * g.Hv * k2 * C * 2);
+  w.fw = take((size_t)g.Ws * k2 * 2);
+  w.ti = take((size_t)g.Ws * k2 * 2);
+  w.fy = take((size_t)(g.Hs / 4) * d.nf * 16);
   w.ty = take((size_t)d.kg * hp * 16);
   w.status = take(sizeof(unsigned));
   w.total = p;
   return w;
 }
 
-template <int kC, int kAct>
+template <int kC, int kAct, int kK2>
 static int fno_forward_tc_impl(const fno_config& c, const FnoTcParams& P, const float* in,
                                float* out, int B, int H, int W, char* ws, cudaStream_t s) {
   const FnoTcWs wp = fno_tc_ws_plan(c, B, H, W);
+  const TcGrid gd = tc_grid(c, H, W);
   __nv_bfloat16* th[2] = {reinterpret_cast<__nv_bfloat16*>(ws + wp.theta0),
                           reinterpret_cast<__nv_bfloat16*>(ws + wp.theta1)};
   __nv_bfloat16* x1b = reinterpret_cast<__nv_bfloat16*>(ws + wp.x1b);
@@ -1195,109 +1289,126 @@ static int fno_forward_tc_impl(const fno_config& c, const FnoTcParams& P, const 
   unsigned* status = reinterpret_cast<unsigned*>(ws + wp.status);
   const int m = c.modes;
   const SpecDims d = spec_dims(kC, m);
-  const int hp = (H + 127) / 128 * 128;
+  const int hp = (gd.Hv + 127) / 128 * 128;
   int dev = 0, nsm = 0;
   LBM_CHECK_CUDA(cudaGetDevice(&dev));
   LBM_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   LBM_CHECK_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), s));
   // padding entries of Yb (k' >= 2m, a >= 2m) are never written by the mixing kernel
   LBM_CHECK_CUDA(cudaMemsetAsync(yb, 0, (size_t)B * d.kg * d.nn * 16, s));
-  const int n_tables = 2 * W * 32 + (H / 4) * d.nf * 8 + d.kg * hp * 8;
-  k_tables<<<(n_tables + 255) / 256, 256, 0, s>>>(fw, ti, fy, ty, H, W, m, hp, d.nf, d.kg);
-  const size_t pix = (size_t)B * H * W;
-  const int lift_ctas = (int)std::min<size_t>(pix / 128, (size_t)kLiftCtasPerSm * nsm);
+  const int n_tables = 2 * gd.Ws * kK2 + (gd.Hs / 4) * d.nf * 8 + d.kg * hp * 8;
+  k_tables<<<(n_tables + 255) / 256, 256, 0, s>>>(fw, ti, fy, ty, gd, m, hp, d.nf, d.kg);
+  const size_t spix = (size_t)B * gd.Hs * gd.Ws;
+  const int lift_ctas = (int)std::min<size_t>(spix / 128, (size_t)kLiftCtasPerSm * nsm);
   if (c.c_in == 4)
-    k_lift_tc<kC, 4, kAct><<<lift_ctas, 128, 0, s>>>(
-        in, th[0], P.lift0_w, P.lift0_b, P.lift1_w, P.lift1_b, B, H, W, c.c_in, status);
+    k_lift_tc<kC, 4, kAct><<<lift_ctas, 128, 0, s>>>(in, th[0], th[1], P.lift0_w, P.lift0_b,
+                                                     P.lift1_w, P.lift1_b, B, gd, c.c_in, status);
   else
-    k_lift_tc<kC, 0, kAct><<<lift_ctas, 128, 0, s>>>(
-        in, th[0], P.lift0_w, P.lift0_b, P.lift1_w, P.lift1_b, B, H, W, c.c_in, status);
+    k_lift_tc<kC, 0, kAct><<<lift_ctas, 128, 0, s>>>(in, th[0], th[1], P.lift0_w, P.lift0_b,
+                                                     P.lift1_w, P.lift1_b, B, gd, c.c_in, status);
   LBM_CHECK_LAUNCH();
-  const size_t fwd_smem = (size_t)W * 64 + (size_t)kFwdStages * kFwdStageBytes;
-  constexpr int kStageBytesInv = (4 + kC / 8) * 128 * 16 + (4 + kC / 8) * kC * 16;
-  const size_t inv_smem = (size_t)kInvStages * kStageBytesInv;
-  const size_t y_smem = ydft_smem(kC, H, m), iy_smem = iydft_smem(kC, m);
+  const size_t f_smem = fwd_smem(gd.Ws, kK2), i_smem = inv_smem(kC, kK2);
+  const size_t y_smem = ydft_smem(kC, gd.Hs, m), iy_smem = iydft_smem(kC, m);
   const size_t mix_smem = (size_t)(kC * kC + kMixB * kC) * sizeof(float2);
-  LBM_REQUIRE(y_smem <= 200 * 1024 && iy_smem <= 200 * 1024,
+  LBM_REQUIRE(y_smem <= (size_t)kTcSmemMax && iy_smem <= (size_t)kTcSmemMax &&
+                  f_smem <= (size_t)kTcSmemMax && i_smem <= (size_t)kTcSmemMax,
               "fno_forward: spectral working set too large for shared memory");
-  const int ytiles = (H + (128 / kC) - 1) / (128 / kC);
-  const int fwd_ctas = std::min(B * ytiles, 2 * nsm);
-  const int inv_ctas = std::min(B * H * (W / 128), inv_ctas_per_sm<kC>() * nsm);
+  const int fwd_ctas = std::min(B * (gd.Hs / (128 / kC)), 2 * nsm);
+  const int inv_ctas = std::min(B * gd.Hv * (gd.Ws / 128), inv_ctas_per_sm<kC>() * nsm);
   const int ydft_ctas = std::min(B * ((m * kC + 127) / 128), 2 * nsm);
   const int iydft_ctas = std::min(B * (hp / 128) * d.nc, nsm);
   const dim3 mix_grid((unsigned)(2 * m * m), (unsigned)((B + kMixB - 1) / kMixB));
   int cur = 0;
   for (int n = 0; n < c.layers; ++n) {
-    k_fwd_x_tc<kC><<<fwd_ctas, kTcThreads, fwd_smem, s>>>(th[cur], fw, x1b, B, H, W, m, status);
+    k_fwd_x_tc<kC, kK2><<<fwd_ctas, kTcThreads, f_smem, s>>>(th[cur], fw, x1b, B, gd.Hs, gd.Ws,
+                                                             m, status);
     LBM_CHECK_LAUNCH();
-    k_ydft_tc<kC><<<ydft_ctas, kTcThreads, y_smem, s>>>(x1b, fy, xh, B, H, m, status);
+    k_ydft_tc<kC><<<ydft_ctas, kTcThreads, y_smem, s>>>(x1b, fy, xh, B, gd.Hs, m, status);
     LBM_CHECK_LAUNCH();
     k_mix<kC><<<mix_grid, 256, mix_smem, s>>>(xh, P.rt[n], yb, B, m);
     LBM_CHECK_LAUNCH();
-    k_iydft_tc<kC><<<iydft_ctas, kTcThreads, iy_smem, s>>>(ty, yb, zt, B, H, m, status);
+    k_iydft_tc<kC, kK2><<<iydft_ctas, kTcThreads, iy_smem, s>>>(ty, yb, zt, B, gd.Hv, m, status);
     LBM_CHECK_LAUNCH();
-    k_inv_x_tc<kC, kAct><<<inv_ctas, kInvThreads, inv_smem, s>>>(
-        th[cur], ti, zt, P.w[n], P.b[n], th[cur ^ 1], B, H, W, status);
+    k_inv_x_tc<kC, kAct, kK2><<<inv_ctas, kInvThreads, i_smem, s>>>(
+        th[cur], ti, zt, P.w[n], P.b[n], th[cur ^ 1], B, gd, status);
     LBM_CHECK_LAUNCH();
     cur ^= 1;
   }
-  const size_t dec_smem =
-      ((size_t)c.dec_layers * (c.dec_size * 64 + c.dec_size) + c.c_out * 64 + c.c_out) * sizeof(float);
-  if (c.dec_layers == 1 && c.dec_size == kC && c.c_out == 3) {
+  const size_t pix = (size_t)B * H * W;
+  if (c.dec_layers == 1 && c.dec_size == kC && c.c_out == 3 && W % 128 == 0) {
     const size_t smem_tc = (size_t)kC * kC * 2 + (size_t)kDecStages * (kC / 8) * 128 * 16;
     const int ntiles = B * H * (W / 128);
     const int ctas = std::min(ntiles, kDecCtasPerSm * nsm);
     k_decoder_tc<kC, 3, kAct><<<ctas, kDecThreads, smem_tc, s>>>(th[cur], out, P.params,
-                                                                P.dec_offs, B, H, W, status);
+                                                                P.dec_offs, B, gd, status);
   } else {
+    const size_t dec_smem =
+        ((size_t)c.dec_layers * (c.dec_size * 64 + c.dec_size) + c.c_out * 64 + c.c_out) *
+        sizeof(float);
     k_decoder_blk<kC><<<(unsigned)((pix + 127) / 128), 128, dec_smem, s>>>(
-        th[cur], out, P.params, P.dec_offs, c.dec_layers, B, H, W, c.dec_size, c.c_out,
+        th[cur], out, P.params, P.dec_offs, c.dec_layers, B, gd, c.dec_size, c.c_out,
         c.activation);
   }
   LBM_CHECK_LAUNCH();
   return LBM_OK;
 }
 
+template <int kC, int kAct, int kK2>
+static int tc_set_smem_attrs_k2() {
+  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_inv_x_tc<kC, kAct, kK2>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemMax));
+  if (kAct == FNO_ACT_GELU) {
+    LBM_CHECK_CUDA(cudaFuncSetAttribute(k_fwd_x_tc<kC, kK2>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemMax));
+    LBM_CHECK_CUDA(cudaFuncSetAttribute(k_iydft_tc<kC, kK2>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemMax));
+  }
+  return LBM_OK;
+}
 template <int kC, int kAct>
 static int tc_set_smem_attrs_act() {
-  const int big = 200 * 1024;
-  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_inv_x_tc<kC, kAct>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_decoder_tc<kC, 3, kAct>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  return LBM_OK;
+  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_decoder_tc<kC, 3, kAct>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemMax));
+  LBM_TRY((tc_set_smem_attrs_k2<kC, kAct, 32>()));
+  return tc_set_smem_attrs_k2<kC, kAct, 64>();
 }
 template <int kC>
 static int tc_set_smem_attrs() {
-  const int big = 200 * 1024;
-  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_fwd_x_tc<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_ydft_tc<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_iydft_tc<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_mix<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  const int rc = tc_set_smem_attrs_act<kC, FNO_ACT_GELU>();
-  return rc != LBM_OK ? rc : tc_set_smem_attrs_act<kC, FNO_ACT_RELU>();
+  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_ydft_tc<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemMax));
+  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_mix<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemMax));
+  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_decoder_blk<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemMax));
+  LBM_TRY((tc_set_smem_attrs_act<kC, FNO_ACT_GELU>()));
+  return tc_set_smem_attrs_act<kC, FNO_ACT_RELU>();
 }
 
 int fno_tc_prepare(const fno_config& c) {
-  switch (c.width) {
+  switch (fno_tc_width(c.width)) {
     case 16: return tc_set_smem_attrs<16>();
     case 32: return tc_set_smem_attrs<32>();
-    case 64: return tc_set_smem_attrs<64>();
-    default: return LBM_OK;
+    default: return tc_set_smem_attrs<64>();
   }
+}
+
+template <int kC, int kAct>
+static int fno_forward_tc_k2(const fno_config& c, const FnoTcParams& P, const float* in, float* out,
+                             int B, int H, int W, char* ws, cudaStream_t s) {
+  return tc_k2(c.modes) == 32 ? fno_forward_tc_impl<kC, kAct, 32>(c, P, in, out, B, H, W, ws, s)
+                              : fno_forward_tc_impl<kC, kAct, 64>(c, P, in, out, B, H, W, ws, s);
+}
+template <int kC>
+static int fno_forward_tc_act(const fno_config& c, const FnoTcParams& P, const float* in, float* out,
+                              int B, int H, int W, char* ws, cudaStream_t s) {
+  return c.activation == FNO_ACT_GELU
+             ? fno_forward_tc_k2<kC, FNO_ACT_GELU>(c, P, in, out, B, H, W, ws, s)
+             : fno_forward_tc_k2<kC, FNO_ACT_RELU>(c, P, in, out, B, H, W, ws, s);
 }
 
 int fno_forward_tc(const fno_config& c, const FnoTcParams& P, const float* in, float* out, int B,
                    int H, int W, char* ws, cudaStream_t s) {
-  const bool gelu = c.activation == FNO_ACT_GELU;
-  switch (c.width) {
-    case 16: return gelu ? fno_forward_tc_impl<16, FNO_ACT_GELU>(c, P, in, out, B, H, W, ws, s)
-                         : fno_forward_tc_impl<16, FNO_ACT_RELU>(c, P, in, out, B, H, W, ws, s);
-    case 32: return gelu ? fno_forward_tc_impl<32, FNO_ACT_GELU>(c, P, in, out, B, H, W, ws, s)
-                         : fno_forward_tc_impl<32, FNO_ACT_RELU>(c, P, in, out, B, H, W, ws, s);
-    case 64: return gelu ? fno_forward_tc_impl<64, FNO_ACT_GELU>(c, P, in, out, B, H, W, ws, s)
-                         : fno_forward_tc_impl<64, FNO_ACT_RELU>(c, P, in, out, B, H, W, ws, s);
-    default:
-      set_error("fno_forward: no tensor-core kernels for width %d", c.width);
-      return LBM_ERR_UNSUPPORTED;
+  switch (fno_tc_width(c.width)) {
+    case 16: return fno_forward_tc_act<16>(c, P, in, out, B, H, W, ws, s);
+    case 32: return fno_forward_tc_act<32>(c, P, in, out, B, H, W, ws, s);
+    default: return fno_forward_tc_act<64>(c, P, in, out, B, H, W, ws, s);
   }
 }
 

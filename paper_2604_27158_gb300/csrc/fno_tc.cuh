@@ -10,7 +10,8 @@ struct FnoTcWs {
   size_t theta0, theta1, x1b, xh, yb, zt, fw, ti, fy, ty, status, total;
 };
 
-// FP32 parameters of one FNO, already repacked on the device.
+// FP32 parameters of one FNO, already repacked on the device (channel dimensions padded
+// to fno_tc_width with zeros when the width is not 16, 32 or 64).
 struct FnoTcParams {
   const float *lift0_w, *lift0_b, *lift1_w, *lift1_b;
   const float2* rt[16];  // per layer: spectral filters [mode][C_in][C_out]
@@ -20,6 +21,9 @@ struct FnoTcParams {
   const unsigned* dec_offs;
 };
 
+// Latent width of the tensor-core kernels for c.width channels (16, 32 or 64): the extra
+// channels carry zero weights and stay exactly 0.
+int fno_tc_width(int C);
 bool fno_tc_supported(const fno_config& c, int H, int W);
 FnoTcWs fno_tc_ws_plan(const fno_config& c, int B, int H, int W);
 int fno_tc_prepare(const fno_config& c);

@@ -254,7 +254,9 @@ def test_tensor_core_and_cuda_core_paths_agree():
 def test_paper_models_with_padding_match_oracle(name, cin, cout, width, layers, modes, dec_layers,
                                                 dec, B, H, W):
     """The appendix-table architectures with "Padding: 9" (latent field zero-padded after
-    lifting, cropped after the last Fourier layer), on the CUDA-core path."""
+    lifting, cropped after the last Fourier layer), on the tensor-core path (channels
+    padded to 16 with zero weights, grids padded to the tile sizes, 2m up to 64 kept
+    x-frequencies) and with the path forced to CUDA cores."""
     _requires_gpu()
     s = synth.FnoShape(c_in=cin, c_out=cout, width=width, layers=layers, modes=modes,
                        dec_layers=dec_layers, dec_size=dec, padding=9)
@@ -262,10 +264,42 @@ def test_paper_models_with_padding_match_oracle(name, cin, cout, width, layers, 
                  dec_layers=dec_layers, dec_size=dec, padding=9)
     params = synth.fno_random_params(s, seed=21, out_scale=1.0)
     net = Fno(g, synth.fno_flatten_params(s, params))
-    assert not net.uses_tensor_cores(H, W)
+    assert net.uses_tensor_cores(H, W)
     x = _inputs(B, cin, H, W, seed=23)
-    y = net(torch.from_numpy(x).cuda()).cpu().numpy()
     ref = fo.fno_forward(s, params, x)
+    y = net(torch.from_numpy(x).cuda()).cpu().numpy()
+    net.check(B, H, W)
     e = rel_l2(y, ref)
-    print(f"{name} padded {B}x{H}x{W}: rel L2 {e:.3e} ({fo.param_count(s)} params)")
-    assert e < REL_L2_FNO
+    net.set_path(P._abi.FNO_PATH_CUDA_CORES)
+    y_cc = net(torch.from_numpy(x).cuda()).cpu().numpy()
+    e_cc = rel_l2(y_cc, ref)
+    print(f"{name} padded {B}x{H}x{W}: rel L2 tensor cores {e:.3e}, CUDA cores {e_cc:.3e} "
+          f"({fo.param_count(s)} params)")
+    assert e < REL_L2_FNO and e_cc < REL_L2_FNO
+
+
+@pytest.mark.parametrize("which", ["density", "velocity"])
+def test_double_shear_model_pair_on_tensor_cores(which):
+    """The 2.6 M double-shear model group (Sec. 3.2.1; 14 channels, 3 layers, decoder 32,
+    padding 9) at its workload size, B = 4 periodic 128 x 128 fields -> 137 x 137 padded
+    grid: density net (rho - 1 -> rho - 1, 8 modes) and velocity net ((u, v) -> (u, v),
+    32 modes: 64 kept x-frequencies)."""
+    _requires_gpu()
+    cin, modes = (1, 8) if which == "density" else (2, 32)
+    s = synth.FnoShape(c_in=cin, c_out=cin, width=14, layers=3, modes=modes, dec_size=32,
+                       padding=9)
+    g = FnoShape(c_in=cin, c_out=cin, width=14, layers=3, modes=modes, dec_size=32, padding=9)
+    params = synth.fno_random_params(s, seed=31 if which == "density" else 32, out_scale=1.0)
+    assert fo.param_count(s) == (151811 if which == "density" else 2409771)
+    net = Fno(g, synth.fno_flatten_params(s, params))
+    assert net.uses_tensor_cores(128, 128)
+    ics = synth.double_shear(4, seed=2000)
+    planes = [("rho",)] if which == "density" else [("ux",), ("uy",)]
+    x = np.stack([np.stack([(ic["rho"] - 1.0) if k[0] == "rho" else ic[k[0]] for k in planes])
+                  for ic in ics]).astype(np.float32)
+    y = net(torch.from_numpy(x).cuda()).cpu().numpy()
+    net.check(4, 128, 128)
+    ref = fo.fno_forward(s, params, x)
+    errs = [rel_l2(y[b], ref[b]) for b in range(4)]
+    print(f"double-shear {which} net on tensor cores: rel L2 max {max(errs):.3e}")
+    assert max(errs) < REL_L2_FNO
