@@ -107,6 +107,31 @@ int lbm_init(const lbm_grid* grids_h, int ngrids, const uint32_t* mask_d, float*
  * One kernel launch per step. */
 int lbm_step(lbm_handle* h, int nsteps, void* stream);
 
+/*
+ * Persistent multi-step execution (the super-time-stepping loop of Sec. 2.3 advances
+ * many trajectories of uneven size for k steps between FNO calls).  With on != 0,
+ * lbm_step(h, nsteps > 1) runs all nsteps time steps of the batch in ONE cooperative
+ * launch of the step kernel: its CTAs stay resident and meet at a grid-wide barrier
+ * between steps instead of ending the grid; results are bitwise identical to one launch
+ * per step.  Every barrier wait is bounded (2 s): an expired wait records
+ * LBM_ERR_TIMEOUT (reported by the next lbm_residual) and every CTA returns.
+ * Default off.  Host only.
+ */
+int lbm_set_persistent(lbm_handle* h, int on);
+
+/*
+ * Self-test of the multi-step launch's bounded grid barrier (the paper has no
+ * counterpart).  Runs two persistent steps whose barrier waits for every CTA
+ * (arrive_all != 0: completes, the state advances by two steps) or for one CTA more than
+ * the launch has (arrive_all == 0: the wait expires after limit_ms, 0 < limit_ms <= 2000,
+ * every CTA returns after the first step's stores, which go to the other buffer, so the
+ * state is unchanged).  status_d: one caller-owned device word (overwritten).
+ * Synchronises `stream`.  Returns LBM_ERR_TIMEOUT when the wait expired, LBM_OK when it
+ * completed; the context stays usable either way.
+ */
+int lbm_barrier_selftest(lbm_handle* h, unsigned* status_d, int arrive_all, double limit_ms,
+                         void* stream);
+
 /* Macroscopic fields (Sec. 2.1 moments) of the current state, dense layout.
  * Solid cells report rho = 1, u = 0.  Any output pointer may be NULL. */
 int lbm_macro(lbm_handle* h, float* rho_d, float* ux_d, float* uy_d, void* stream);

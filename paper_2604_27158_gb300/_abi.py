@@ -90,6 +90,8 @@ _PROTOS = {
     "lbm_residual": ([VP, ctypes.POINTER(ctypes.c_double), I, VP], I),
     "lbm_step_residual": ([VP, ctypes.POINTER(ctypes.c_double), I, VP], I),
     "lbm_stream_probe": ([VP, I, VP], I),
+    "lbm_set_persistent": ([VP, I], I),
+    "lbm_barrier_selftest": ([VP, VP, I, ctypes.c_double, VP], I),
     "lbm_reinit_from_macro": ([VP, VP, VP, VP, I, VP], I),
     "lbm_export_f": ([VP, VP, VP], I),
     "lbm_vorticity": ([VP, VP, VP, VP, VP], I),

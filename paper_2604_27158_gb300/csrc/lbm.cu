@@ -146,7 +146,10 @@ struct StepShape {
 //                 momentum, unstable cells) per 128-cell row segment, and optionally the
 //                 velocity stored for the next residual.
 //  * kModeStepStats: both kModeStep and kModeStats in one pass.
-enum StepMode { kModeStep = 0, kModeStream = 1, kModeStats = 2, kModeStepStats = 3 };
+//  * kModeMulti:  kModeStep for ma.nsteps time steps in one persistent launch: the CTAs
+//                 stay resident (cooperative launch) and meet at a grid-wide barrier
+//                 between steps; the source and destination buffers swap every step.
+enum StepMode { kModeStep = 0, kModeStream = 1, kModeStats = 2, kModeStepStats = 3, kModeMulti = 4 };
 // floats per row-segment statistics slot (R_COUNT values, padded)
 constexpr int kSegStride = 12;
 static_assert(R_COUNT <= kSegStride, "segment statistics slot");
@@ -160,6 +163,67 @@ struct StatsArgs {
   int update_prev;
 };
 
+// Extra arguments of the persistent multi-step mode (unused by the others).
+struct MultiArgs {
+  int nsteps;                   // time steps of this launch
+  unsigned* bar_count;          // grid-barrier arrivals, 0 at launch
+  unsigned expected_ctas;       // CTAs arriving at every barrier (gridDim.x)
+  unsigned long long limit_ns;  // bound of one barrier wait
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// All threads of the CTA, whatever code path they are on (named barrier 1).
+__device__ __forceinline__ void cta_sync() {
+  asm volatile("bar.sync 1, %0;" ::"r"(blockDim.x) : "memory");
+}
+// Grid-wide barrier between two steps of the multi-step mode, called by every thread.
+// Stores of the step are made visible to the bulk copies (async proxy) and device-wide
+// before the CTA's arrival; thread 0 spins (bounded by limit_ns) until every CTA has
+// arrived.  An expired wait, here or earlier in any CTA, sets kStatusTimeout and the
+// function returns false in every thread of the CTA.
+__device__ __forceinline__ bool grid_barrier(const MultiArgs& ma, int sstep, unsigned* status,
+                                             int* abort_s) {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  cta_sync();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(ma.bar_count, 1u);
+    const unsigned target = (unsigned)(sstep + 1) * ma.expected_ctas;
+    const unsigned long long t0 = global_ns();
+    int abort = 0;
+    while (true) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ma.bar_count) : "memory");
+      if (v >= target) break;
+      if (global_ns() - t0 > ma.limit_ns) {
+        atomicOr(status, kStatusTimeout);
+        abort = 1;
+        break;
+      }
+      __nanosleep(64);
+    }
+    unsigned st;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(st) : "l"(status) : "memory");
+    *abort_s = abort || (st & kStatusTimeout) != 0;
+    __threadfence();
+  }
+  cta_sync();
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  return *abort_s == 0;
+}
+
+// Population loads outside the staged rows: read-only path for a single step; for the
+// multi-step mode, which reads buffers that other CTAs wrote earlier in the same launch,
+// the L2 (coherent) path.
+template <bool kCoherent>
+__device__ __forceinline__ float ldpop(const float* p) {
+  return kCoherent ? __ldcg(p) : __ldg(p);
+}
+
 // The statistics modes hold eleven more lane partials and four velocities; they are
 // compiled for one CTA per SM fewer than the shape's time step (no spills).
 __host__ __device__ constexpr int step_min_blocks(int mb, int mode) {
@@ -169,11 +233,15 @@ __host__ __device__ constexpr int step_min_blocks(int mb, int mode) {
 template <int TY, int ST, int MB, int MODE>
 __global__ void __launch_bounds__((TY + 1) * 32, step_min_blocks(MB, MODE))
     k_step_tma(const GridDev* __restrict__ grids, const int4* __restrict__ tiles, int ntiles,
-               const uint32_t* __restrict__ mask, const float* __restrict__ src,
-               float* __restrict__ dst, unsigned* __restrict__ status, StatsArgs sa) {
-  constexpr bool kCollide = MODE == kModeStep || MODE == kModeStepStats;
+               const uint32_t* __restrict__ mask, const float* __restrict__ src0,
+               float* __restrict__ dst0, unsigned* __restrict__ status, StatsArgs sa,
+               MultiArgs ma) {
+  constexpr bool kMulti = MODE == kModeMulti;
+  constexpr bool kCollide = MODE == kModeStep || MODE == kModeStepStats || kMulti;
   constexpr bool kStore = MODE != kModeStats;
   constexpr bool kStats = MODE == kModeStats || MODE == kModeStepStats;
+  const int nst = kMulti ? ma.nsteps : 1;
+  __shared__ int abort_s;
   using SS = StepShape<TY, ST, MB>;
   using TileMeta = typename SS::Meta;
   constexpr int kTY = TY, kStages = ST, kStageFloats = SS::kStageFloats,
@@ -221,8 +289,10 @@ __global__ void __launch_bounds__((TY + 1) * 32, step_min_blocks(MB, MODE))
     };
     int k = 0;
     bool ok = true;
+    for (int sstep = 0; sstep < nst; ++sstep) {
+    const float* src = (kMulti && (sstep & 1)) ? dst0 : src0;
     int4 next = blockIdx.x < (unsigned)ntiles ? __ldg(&tiles[blockIdx.x]) : make_int4(0, 0, 0, 0);
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++k) {
       const int s = k % kStages;
       const int4 d = next;
       if (t + (int)gridDim.x < ntiles) next = __ldg(&tiles[t + gridDim.x]);
@@ -281,6 +351,10 @@ __global__ void __launch_bounds__((TY + 1) * 32, step_min_blocks(MB, MODE))
       __syncwarp();
       if (lane == 0) mbar_arrive(&full_bar[s]);
     }
+    if constexpr (kMulti) {
+      if (!grid_barrier(ma, sstep, status, &abort_s)) break;
+    }
+    }  // steps
     // never leave with bulk copies in flight: wait (bounded) for the issued stages
     const int issued = k;
     for (int q = max(0, issued - kStages); q < issued; ++q)
@@ -290,9 +364,16 @@ __global__ void __launch_bounds__((TY + 1) * 32, step_min_blocks(MB, MODE))
 
   // -------------------------------------------------------------- consumers
   int k = 0;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+  bool alive = true;
+  for (int sstep = 0; sstep < nst; ++sstep) {
+  const float* src = (kMulti && (sstep & 1)) ? dst0 : src0;
+  float* dst = (kMulti && (sstep & 1)) ? const_cast<float*>(src0) : dst0;
+  for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x, ++k) {
     const int s = k % kStages;
-    if (!mbar_wait(&full_bar[s], (k / kStages) & 1, status)) return;
+    if (!mbar_wait(&full_bar[s], (k / kStages) & 1, status)) {
+      alive = false;
+      break;
+    }
     const TileMeta* tm = metas + s;
     const GridDev G = tm->g;
     const int x0 = tm->x0, y0 = tm->y0;
@@ -353,12 +434,12 @@ __global__ void __launch_bounds__((TY + 1) * 32, step_min_blocks(MB, MODE))
         } else if (cx_of(i) > 0) {  // source x - 1
           const float4 cm = *reinterpret_cast<const float4*>(rowp - 4);
           g[i][0] = cm.w; g[i][1] = c0.x; g[i][2] = c0.y; g[i][3] = c0.z;
-          if (x == 0) g[i][0] = periodic ? __ldg(b + i * P + ys * G.pitch + nx - 1) : 0.0f;
+          if (x == 0) g[i][0] = periodic ? ldpop<kMulti>(b + i * P + ys * G.pitch + nx - 1) : 0.0f;
         } else {  // source x + 1
           const float4 cp = *reinterpret_cast<const float4*>(rowp + 4);
           g[i][0] = c0.y; g[i][1] = c0.z; g[i][2] = c0.w; g[i][3] = cp.x;
           if (jw >= 0 && jw < kVec) {
-            const float wrap = periodic ? __ldg(b + i * P + ys * G.pitch) : 0.0f;
+            const float wrap = periodic ? ldpop<kMulti>(b + i * P + ys * G.pitch) : 0.0f;
 #pragma unroll
             for (int j = 0; j < kVec; ++j)
               if (j == jw) g[i][j] = wrap;
@@ -517,14 +598,18 @@ __global__ void __launch_bounds__((TY + 1) * 32, step_min_blocks(MB, MODE))
       }
     }
   }
+  if constexpr (kMulti) {
+    if (!grid_barrier(ma, sstep, status, &abort_s)) break;
+  }
+  }  // steps
 }
 
 // Tile shapes compiled into the library (rows per tile, stages, CTAs per SM).
 // Every shape performs the same arithmetic per cell in the same order, so the
 // choice changes speed only; lbm_autotune times them on the caller's batch.
 using StepKernel = void (*)(const GridDev*, const int4*, int, const uint32_t*, const float*,
-                           float*, unsigned*, StatsArgs);
-constexpr int kStepModes = 4;
+                           float*, unsigned*, StatsArgs, MultiArgs);
+constexpr int kStepModes = 5;
 struct StepVariant {
   int ty, stages, minb;
   StepKernel kernel[kStepModes];  // by StepMode
@@ -534,7 +619,8 @@ struct StepVariant {
   StepVariant {                                                                            \
     TY, ST, MB,                                                                            \
         {k_step_tma<TY, ST, MB, kModeStep>, k_step_tma<TY, ST, MB, kModeStream>,           \
-         k_step_tma<TY, ST, MB, kModeStats>, k_step_tma<TY, ST, MB, kModeStepStats>},      \
+         k_step_tma<TY, ST, MB, kModeStats>, k_step_tma<TY, ST, MB, kModeStepStats>,       \
+         k_step_tma<TY, ST, MB, kModeMulti>},                                              \
         StepShape<TY, ST, MB>::kSmem                                                       \
   }
 static const StepVariant kStepVariants[LBM_STEP_VARIANTS] = {
@@ -741,7 +827,8 @@ __global__ void __launch_bounds__(kBlock) k_vorticity(const GridDev* __restrict_
 
 // ------------------------------------------------------------ host side ---
 struct WsPlan {
-  size_t grids_off, uprev_off, seg_off, partial_off, stats_off, status_off, tiles_off, total;
+  size_t grids_off, uprev_off, seg_off, partial_off, stats_off, status_off, bar_off, tiles_off,
+      total;
 };
 
 // Scratch of one statistics evaluation: FP32 row-segment partials, FP64 block sums,
@@ -838,7 +925,8 @@ static int plan_layout(const lbm_grid* grids, int ngrids, lbm_layout* lay,
   w.partial_off = w.seg_off + sc.partial_off;
   w.stats_off = w.seg_off + sc.stats_off;
   w.status_off = w.seg_off + sc.total;
-  w.tiles_off = align_up(w.status_off + sizeof(unsigned), 256);
+  w.bar_off = align_up(w.status_off + sizeof(unsigned), 256);
+  w.tiles_off = align_up(w.bar_off + sizeof(unsigned), 256);
   size_t tiles_all = 0;  // descriptors of every tile shape
   for (int v = 0; v < LBM_STEP_VARIANTS; ++v)
     for (int k = 0; k < ngrids; ++k)
@@ -854,6 +942,7 @@ static int plan_layout(const lbm_grid* grids, int ngrids, lbm_layout* lay,
 }
 
 static inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+constexpr double kBarrierLimitMs = 2000.0;  // bound of one grid-barrier wait
 
 // One launch of the step kernel in `mode` over every grid with tile shape `v`: reads
 // `src`, writes `dst` (modes that store populations).
@@ -875,7 +964,36 @@ static int launch_step(Handle* h, int v, int mode, const float* src, float* dst,
   cfg.numAttrs = 1;
   LBM_CHECK_CUDA(cudaLaunchKernelEx(&cfg, sv.kernel[mode], (const GridDev*)h->gd_d,
                                     (const int4*)h->tiles_d[v], h->ntiles_v[v],
-                                    (const uint32_t*)h->mask, src, dst, h->status_d, sa));
+                                    (const uint32_t*)h->mask, src, dst, h->status_d, sa,
+                                    MultiArgs{}));
+  return LBM_OK;
+}
+
+// nsteps time steps in one cooperative launch of the multi-step mode (every CTA resident;
+// grid-wide barrier between steps).  expected_extra > 0 makes every barrier wait for CTAs
+// that do not exist (the self-test of the bounded wait); status: the word the kernel
+// reports an expired wait in.
+static int launch_multi(Handle* h, int v, int nsteps, const float* src, float* dst,
+                        unsigned* status, unsigned expected_extra, double limit_ms,
+                        cudaStream_t s) {
+  const StepVariant& sv = kStepVariants[v];
+  const int ctas = std::min(h->ntiles_v[v], h->nsm * std::max(1, h->blocks_per_sm_vm[v][kModeMulti]));
+  LBM_CHECK_CUDA(cudaMemsetAsync(h->bar_count, 0, sizeof(unsigned), s));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)ctas);
+  cfg.blockDim = dim3((unsigned)((sv.ty + 1) * 32));
+  cfg.dynamicSmemBytes = sv.smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  MultiArgs ma{nsteps, h->bar_count, (unsigned)ctas + expected_extra,
+               (unsigned long long)(limit_ms * 1.0e6)};
+  LBM_CHECK_CUDA(cudaLaunchKernelEx(&cfg, sv.kernel[kModeMulti], (const GridDev*)h->gd_d,
+                                    (const int4*)h->tiles_d[v], h->ntiles_v[v],
+                                    (const uint32_t*)h->mask, src, dst, status, StatsArgs{}, ma));
   return LBM_OK;
 }
 
@@ -981,6 +1099,7 @@ int lbm_init(const lbm_grid* grids_h, int ngrids, const uint32_t* mask_d, float*
   h->uy_prev = h->ux_prev + h->layout.cells;
   h->scratch = ws + wp.seg_off;
   h->status_d = reinterpret_cast<unsigned*>(ws + wp.status_off);
+  h->bar_count = reinterpret_cast<unsigned*>(ws + wp.bar_off);
   // tile descriptors of every shape: grid after grid, row of tiles after row of tiles
   std::vector<int4> tiles;
   std::vector<size_t> tiles_at(LBM_STEP_VARIANTS);
@@ -1046,6 +1165,13 @@ int lbm_init(const lbm_grid* grids_h, int ngrids, const uint32_t* mask_d, float*
 int lbm_step(lbm_handle* h, int nsteps, void* stream) {
   LBM_REQUIRE(h != nullptr && nsteps >= 0, "lbm_step: bad arguments");
   cudaStream_t s = S(stream);
+  if (h->persistent && nsteps > 1) {
+    LBM_TRY(launch_multi(h, h->variant, nsteps, h->f[h->cur], h->f[h->cur ^ 1], h->status_d, 0u,
+                         kBarrierLimitMs, s));
+    if (nsteps & 1) h->cur ^= 1;
+    h->steps += nsteps;
+    return LBM_OK;
+  }
   for (int k = 0; k < nsteps; ++k) {
     LBM_TRY(launch_step(h, h->variant, kModeStep, h->f[h->cur], h->f[h->cur ^ 1], s));
     h->cur ^= 1;
@@ -1072,6 +1198,35 @@ int lbm_step_residual(lbm_handle* h, double* out_h, int update_prev, void* strea
   const int rc = residual_step(h, out_h, update_prev, S(stream));
   if (rc == LBM_OK || rc == LBM_ERR_UNSTABLE) accept_step(h);
   return rc;
+}
+
+int lbm_set_persistent(lbm_handle* h, int on) {
+  LBM_REQUIRE(h != nullptr, "lbm_set_persistent: null handle");
+  h->persistent = on != 0;
+  return LBM_OK;
+}
+
+int lbm_barrier_selftest(lbm_handle* h, unsigned* status_d, int arrive_all, double limit_ms,
+                         void* stream) {
+  LBM_REQUIRE(h != nullptr && status_d != nullptr, "lbm_barrier_selftest: bad arguments");
+  LBM_REQUIRE(limit_ms > 0.0 && limit_ms <= 2000.0,
+              "lbm_barrier_selftest: limit_ms must be in (0, 2000]");
+  cudaStream_t s = S(stream);
+  LBM_CHECK_CUDA(cudaMemsetAsync(status_d, 0, sizeof(unsigned), s));
+  // two steps from the current state into the other buffer and back: the second step
+  // only runs after the barrier, so with arrive_all == 0 the state is left unchanged
+  LBM_TRY(launch_multi(h, h->variant, 2, h->f[h->cur], h->f[h->cur ^ 1], status_d,
+                       arrive_all ? 0u : 1u, limit_ms, s));
+  unsigned st = 0;
+  LBM_CHECK_CUDA(cudaMemcpyAsync(&st, status_d, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  LBM_CHECK_CUDA(cudaStreamSynchronize(s));
+  if (st & kStatusTimeout) {
+    set_error("lbm_barrier_selftest: the grid barrier wait expired after %.3f ms (status 0x%x)",
+              limit_ms, st);
+    return LBM_ERR_TIMEOUT;
+  }
+  h->steps += 2;  // two steps taken: the state is back in the current buffer
+  return LBM_OK;
 }
 
 int lbm_stream_probe(lbm_handle* h, int variant, void* stream) {

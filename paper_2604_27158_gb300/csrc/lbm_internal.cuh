@@ -18,7 +18,9 @@ struct Handle {
   int variant = 0;                             // step-kernel tile shape in use
   int ntiles_v[LBM_STEP_VARIANTS] = {};        // tiles of the batch per shape
   int blocks_per_sm_v[LBM_STEP_VARIANTS] = {};  // resident CTAs per SM per shape
-  int blocks_per_sm_vm[LBM_STEP_VARIANTS][4] = {};  // ... per shape and kernel mode
+  int blocks_per_sm_vm[LBM_STEP_VARIANTS][5] = {};  // ... per shape and kernel mode
+  bool persistent = false;     // lbm_step runs nsteps > 1 in one multi-step launch
+  unsigned* bar_count = nullptr;  // grid-barrier counter of the multi-step launch
   int4* tiles_d[LBM_STEP_VARIANTS] = {};      // per-shape tile descriptors (workspace)
   unsigned* status_d = nullptr;
   unsigned status_h = 0;

@@ -127,6 +127,17 @@ class Lattice:
         _abi.check("lbm_step_residual", code)
         return out
 
+    def set_persistent(self, on: bool = True) -> None:
+        """step(n > 1) runs all n steps in one persistent launch (grid barrier between steps)."""
+        call("lbm_set_persistent", self._h, int(bool(on)))
+
+    def barrier_selftest(self, arrive_all: bool, limit_ms: float, stream=None) -> int:
+        """Bounded grid-barrier self-test; returns the status code without raising."""
+        status = torch.zeros(1, dtype=torch.int32, device=self.device)
+        return int(_abi.lib().lbm_barrier_selftest(self._h, ctypes.c_void_p(status.data_ptr()),
+                                                   int(bool(arrive_all)), float(limit_ms),
+                                                   _stream_ptr(stream)))
+
     def stream_probe(self, variant: int, stream=None) -> None:
         """Replace the state by its streamed populations, through the step kernel's
         gather with tile shape `variant` (collision replaced by the identity)."""

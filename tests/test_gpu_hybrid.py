@@ -222,3 +222,25 @@ def test_density_and_velocity_networks_unsteady_periodic():
         e = rel_l2(np.stack([ux[k].numpy(), uy[k].numpy()]), np.stack([oux, ouy]))
         print(f"two-network unsteady {g.nx}x{g.ny}: rel L2 u {e:.3e}")
         assert e < 2e-2
+
+
+def test_unsteady_cycles_with_persistent_lbm_steps_are_identical():
+    """The cycle's k LBM steps as one persistent launch (captured into the cycle's CUDA
+    graph) give bitwise the same state as one launch per step."""
+    _requires_gpu()
+    specs = []
+    for k, (nx, ny) in enumerate([(48, 24), (64, 32), (48, 24)]):
+        solid, _ = synth.flow_past_disks(nx, ny, seed=k, rmax=4)
+        specs.append((GridSpec(nx, ny, 0.6 + 0.05 * k, bc_west=P.BC_VELOCITY, bc_east=P.BC_PRESSURE,
+                               west_value=0.03, east_value=1.0), solid))
+    s, params, net = _net(out_scale=1e-1)
+    states = []
+    for persistent in (False, True):
+        lat = Lattice([a for a, _ in specs], [b for _, b in specs])
+        lat.set_persistent(persistent)
+        hyb = Hybrid(lat, net, HybridConfig(mode=P._abi.HYBRID_UNSTEADY, k_lbm=7, m_fno=2,
+                                            neq_mode=1))
+        hyb.advance(cycles=3)
+        torch.cuda.synchronize()
+        states.append(lat.get_state().cpu())
+    assert torch.equal(states[0], states[1])

@@ -408,3 +408,48 @@ def test_step_residual_equals_residual_then_step(variant):
         b.step(9)
     assert a.steps_done() == b.steps_done()
     np.testing.assert_array_equal(a.residual(update_prev=False), b.residual(update_prev=False))
+
+
+# ---------------------------------------------------------------------------
+# Persistent multi-step launch: nsteps in one cooperative launch with a grid-wide
+# barrier between steps.
+
+@pytest.mark.parametrize("variant", range(6))
+def test_persistent_steps_bitwise_equal_one_launch_per_step(variant):
+    _requires_gpu()
+    specs = _stats_lattice()
+    a = Lattice([s[0] for s in specs], [s[1] for s in specs])
+    b = Lattice([s[0] for s in specs], [s[1] for s in specs])
+    for lat in (a, b):
+        lat.set_step_variant(variant)
+    a.set_persistent(True)
+    for n in (37, 100, 1, 2):   # odd and even counts; a single step takes one launch
+        a.step(n)
+        b.step(n)
+        assert torch.equal(a.get_state().cpu(), b.get_state().cpu()), f"after {n} steps"
+    assert a.steps_done() == b.steps_done() == 140
+    np.testing.assert_array_equal(a.residual(update_prev=False), b.residual(update_prev=False))
+
+
+def test_persistent_barrier_selftest_expires_and_context_stays_usable():
+    """The grid barrier's bounded wait: a barrier that waits for one CTA more than the
+    launch has expires after the limit with LBM_ERR_TIMEOUT and leaves the state as it
+    was; the same launch with every CTA arriving completes; normal work follows."""
+    _requires_gpu()
+    g, solid = GEOMS["porous_zou_he_70x33"]()
+    lat = Lattice([g], [solid])
+    lat.step(10)
+    before = lat.get_state().cpu()
+    assert lat.barrier_selftest(arrive_all=False, limit_ms=5.0) == P._abi.LBM_ERR_TIMEOUT
+    assert "grid barrier" in P._abi.last_error()
+    assert torch.equal(lat.get_state().cpu(), before)
+    assert lat.barrier_selftest(arrive_all=True, limit_ms=500.0) == P._abi.LBM_OK
+    ref = Lattice([g], [solid])
+    ref.step(12)
+    assert torch.equal(lat.get_state().cpu(), ref.get_state().cpu())
+    lat.set_persistent(True)
+    lat.step(20)
+    ref.step(20)
+    assert torch.equal(lat.get_state().cpu(), ref.get_state().cpu())
+    st = lat.residual()   # the step kernel's own status word is clean
+    assert st[0, P._abi.LBM_STAT_BAD] == 0
