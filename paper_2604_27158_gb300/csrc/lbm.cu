@@ -182,34 +182,33 @@ __device__ __forceinline__ void cta_sync() {
 }
 // Grid-wide barrier between two steps of the multi-step mode, called by every thread.
 // Stores of the step are made visible to the bulk copies (async proxy) and device-wide
-// before the CTA's arrival; thread 0 spins (bounded by limit_ns) until every CTA has
-// arrived.  An expired wait, here or earlier in any CTA, sets kStatusTimeout and the
+// before the CTA's arrival (a release add); thread 0 spins on an acquire load (checking
+// the limit every 64 polls) until every CTA has arrived.  An expired wait, here or earlier in any CTA, sets kStatusTimeout and the
 // function returns false in every thread of the CTA.
 __device__ __forceinline__ bool grid_barrier(const MultiArgs& ma, int sstep, unsigned* status,
                                              int* abort_s) {
   asm volatile("fence.proxy.async.global;" ::: "memory");
   cta_sync();
   if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(ma.bar_count, 1u);
+    // release: the CTA's stores (ordered before this thread by the CTA barrier) become
+    // visible device-wide no later than the arrival; acquire on the polling load
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ma.bar_count) : "memory");
     const unsigned target = (unsigned)(sstep + 1) * ma.expected_ctas;
     const unsigned long long t0 = global_ns();
     int abort = 0;
-    while (true) {
+    for (unsigned it = 0;; ++it) {
       unsigned v;
       asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ma.bar_count) : "memory");
       if (v >= target) break;
-      if (global_ns() - t0 > ma.limit_ns) {
+      if ((it & 63u) == 63u && global_ns() - t0 > ma.limit_ns) {
         atomicOr(status, kStatusTimeout);
         abort = 1;
         break;
       }
-      __nanosleep(64);
     }
     unsigned st;
     asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(st) : "l"(status) : "memory");
     *abort_s = abort || (st & kStatusTimeout) != 0;
-    __threadfence();
   }
   cta_sync();
   asm volatile("fence.proxy.async.global;" ::: "memory");

@@ -109,14 +109,15 @@ __device__ __forceinline__ void collide_pair(float& gi, float& go, float w, floa
   go = go + om * (even - odd - go) + (s_even - s_odd);
 }
 
-// Unforced pair update (no source term).
+// Unforced pair update (no source term).  Every multiply-add that is fused is written as
+// fmaf: the LBM kernels are compiled without automatic contraction, so each variant of
+// the step kernel rounds identically.
 __device__ __forceinline__ void relax_pair(float& gi, float& go, float wr3, float wcu, float cu,
                                            float base, float rho, float om) {
   // even part w (drho + rho (4.5 cu^2 - 1.5 u^2)) = w drho - w rho usq + 4.5 w rho cu^2
   const float even = fmaf(4.5f * wcu * cu, cu, base);
-  const float odd = wr3 * cu;
-  gi = fmaf(om, (even + odd) - gi, gi);
-  go = fmaf(om, (even - odd) - go, go);
+  gi = fmaf(om, fmaf(wr3, cu, even) - gi, gi);    // even + odd, odd = wr3 cu
+  go = fmaf(om, fmaf(-wr3, cu, even) - go, go);   // even - odd
 }
 
 // One BGK collision of a cell's nine shifted populations (Sec. 2.1), with the Guo
@@ -145,7 +146,7 @@ __device__ __forceinline__ void collide(const GridDev& G, float g[kQ]) {
   const float rusq = rho * 1.5f * fmaf(ux, ux, uy * uy);   // rho * 1.5 u^2
   const float e1 = kW1 * (drho - rusq), e2 = kW2 * (drho - rusq);
   const float r1 = kW1 * rho, r2 = kW2 * rho;
-  g[0] = fmaf(om, kW0 * (drho - rusq) - g[0], g[0]);
+  g[0] = fmaf(om, fmaf(kW0, drho - rusq, -g[0]), g[0]);
   relax_pair(g[1], g[3], 3.0f * r1, r1, ux, e1, rho, om);
   relax_pair(g[2], g[4], 3.0f * r1, r1, uy, e1, rho, om);
   relax_pair(g[5], g[7], 3.0f * r2, r2, ux + uy, e2, rho, om);
