@@ -381,7 +381,7 @@ int fno_check(const fno_handle* h, const void* ws_d, int B, int H, int W, void* 
 /* The activation between Fourier layers (Sec. 2.2; GELU or ReLU) exactly as the
  * inference kernels (tensor-core and CUDA-core paths) evaluate it, applied
  * element-wise: y_d[i] = act(x_d[i]) for i < n, on `stream` (asynchronous).  x_d, y_d:
- * caller-owned device FP32 arrays (may alias).  GELU is within 2e-7 (1 + |x|) of the exact x Phi(x).  For tests; returns
+ * caller-owned device FP32 arrays (may alias).  GELU is within 5e-6 (1 + |x|) of the exact x Phi(x).  For tests; returns
  * LBM_ERR_INVALID_ARG for an unknown act or a null buffer with n > 0. */
 int fno_activation_eval(int act, const float* x_d, float* y_d, size_t n, void* stream);
 

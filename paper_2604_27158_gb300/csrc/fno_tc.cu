@@ -39,6 +39,17 @@
 
 namespace lbmfno {
 
+// Programmatic dependent launch across the kernels of one forward (and from one forward
+// to the next): every kernel lets its successor be scheduled as soon as it has started
+// (pdl_trigger) and waits for its predecessor to complete, with its memory visible, before
+// it reads or writes any buffer a predecessor uses (pdl_wait).  What runs in between is
+// set-up that touches only this kernel's shared memory, TMEM and the read-only
+// parameters, and it overlaps the predecessor's tail.
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ float act_tc(float v, int act) {
   return act == FNO_ACT_GELU ? gelu_poly(v) : fmaxf(v, 0.0f);
 }
@@ -152,6 +163,8 @@ __device__ void table_ty(int t, __nv_bfloat16* __restrict__ ty, int Hv, int hp, 
 __global__ void k_tables(__nv_bfloat16* __restrict__ fw, __nv_bfloat16* __restrict__ ti,
                          __nv_bfloat16* __restrict__ fy, __nv_bfloat16* __restrict__ ty,
                          TcGrid g, int m, int hp, int nf, int kg) {
+  pdl_trigger();
+  pdl_wait();
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int k2 = tc_k2(m);
   const int n_fw = g.Ws * k2, n_fy = (g.Hs / 4) * nf * 8, n_ty = kg * hp * 8;
@@ -169,19 +182,25 @@ __global__ void k_tables(__nv_bfloat16* __restrict__ fw, __nv_bfloat16* __restri
 // CUDA cores with one thread per pixel, its outputs rounded to bfloat16 into the K-major
 // A operand in shared memory; layer 2 (C/2 -> C) as one tcgen05 MMA per 128-pixel tile
 // (M = 128 x positions of one row, N = C, K = C/2 padded to 16) with the bias added in
-// the epilogue.  Several CTAs share an SM; each serialises fill -> MMA -> drain.
+// the epilogue.  Two A buffers and two TMEM accumulators: the MMA of tile j runs while
+// the threads drain tile j - 1 and compute layer 1 of tile j + 1.  Several CTAs share
+// an SM (as many as their accumulators fit in TMEM, at most six).
 constexpr int kLiftCtasPerSm = 6;
+__host__ __device__ constexpr int lift_ctas_per_sm(int C) {
+  return C <= 32 ? kLiftCtasPerSm : 4;  // 2 x 64 TMEM columns per CTA at C = 64
+}
 // The tiles cover the storage grid Hs x Ws: pixels outside the input grid H0 x W0 (the
 // zero padding of the lifted field and the storage padding) are written as 0 without an
 // MMA, and rows y >= Hv of the second latent buffer `theta_alt` are zeroed too (no layer
 // writes them).
 template <int kC, int kCin, int kAct>
-__global__ void __launch_bounds__(128, kLiftCtasPerSm)
+__global__ void __launch_bounds__(128, lift_ctas_per_sm(kC))
     k_lift_tc(const float* __restrict__ in, __nv_bfloat16* __restrict__ theta,
               __nv_bfloat16* __restrict__ theta_alt, const float* __restrict__ w0,
               const float* __restrict__ b0, const float* __restrict__ w1,
               const float* __restrict__ b1, int B, TcGrid gd, int cin_rt,
               unsigned* __restrict__ status) {
+  pdl_trigger();
   constexpr int kHid = kC / 2;
   constexpr int kK = kHid < 16 ? 16 : kHid;  // MMA K (zero-padded hidden units)
   constexpr int kKG = kK / 8;
@@ -189,11 +208,11 @@ __global__ void __launch_bounds__(128, kLiftCtasPerSm)
   constexpr int kAccCols = kC < 32 ? 32 : kC;
   const int cin = kCin > 0 ? kCin : cin_rt;
   const int cin2 = cin + 2;
-  __shared__ __align__(1024) unsigned char a_s[kKG * 2048];   // [k group][x (128)][8]
+  __shared__ __align__(1024) unsigned char a_s[2][kKG * 2048];  // [buffer][k group][x (128)][8]
   __shared__ __align__(1024) unsigned char b_s[kKG * kC * 16];  // W1^T: [k group][o][8]
   __shared__ float2 w0p_s[(kHid / 2) * 18];  // (w0[j][c], w0[j+1][c]) for hidden pairs
   __shared__ __align__(16) float b0_s[kHid], b1_s[kC];
-  __shared__ __align__(8) uint64_t mma_bar;
+  __shared__ __align__(8) uint64_t mma_bar[2];
   __shared__ uint32_t tmem_base;
   const int warp = threadIdx.x >> 5;
   for (int e = threadIdx.x; e < kKG * kC * 8; e += blockDim.x) {
@@ -207,23 +226,52 @@ __global__ void __launch_bounds__(128, kLiftCtasPerSm)
   for (int j = threadIdx.x; j < kHid; j += blockDim.x) b0_s[j] = b0[j];
   for (int o = threadIdx.x; o < kC; o += blockDim.x) b1_s[o] = b1[o];
   if (kHid < kK)  // padded hidden units stay zero
-    for (int e = threadIdx.x; e < 128 * 8; e += blockDim.x)
-      reinterpret_cast<__nv_bfloat16*>(a_s + 2048)[e] = __float2bfloat16_rn(0.f);
+    for (int e = threadIdx.x; e < 2 * 128 * 8; e += blockDim.x)
+      reinterpret_cast<__nv_bfloat16*>(a_s[e / 1024] + 2048)[e % 1024] = __float2bfloat16_rn(0.f);
   fence_proxy_async_smem();
   if (threadIdx.x == 0) {
-    mbar_init(&mma_bar, 1);
+    mbar_init(&mma_bar[0], 1);
+    mbar_init(&mma_bar[1], 1);
     mbar_init_fence();
   }
-  if (warp == 0) tmem_alloc(&tmem_base, kAccCols);
+  if (warp == 0) tmem_alloc(&tmem_base, 2 * kAccCols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  pdl_wait();  // everything below may touch buffers of the previous kernels
   const uint32_t tmem = tmem_base;
   const int H = gd.H0, W = gd.W0, Hs = gd.Hs, Ws = gd.Ws;
   const int xt = Ws / 128;
   const int ntiles = B * Hs * xt;
   constexpr uint32_t idesc = idesc_bf16(128, kC, false, false);
+  // drain accumulator `acc` (the MMA tile whose pixel of this thread is (prow, px)):
+  // bias, bfloat16, channel-blocked store
+  auto drain = [&](int acc, int prow, int px, bool pvalid) {
+#pragma unroll
+    for (int cb = 0; cb < kAccCols / 32; ++cb) {
+      float v[32];
+      const uint32_t ta = tmem + acc * kAccCols + cb * 32 + ((uint32_t)(warp * 32) << 16);
+      if (kC >= 32) tmem_ld32(ta, v);
+      else tmem_ld16(ta, v);
+#pragma unroll
+      for (int g = 0; g < (kC < 32 ? kC : 32) / 8; ++g) {
+        const int o0 = cb * 32 + g * 8;
+        __align__(16) __nv_bfloat16 o8[8];
+#pragma unroll
+        for (int q = 0; q < 8; q += 2) {
+          const float2 r = __fadd2_rn(make_float2(v[g * 8 + q], v[g * 8 + q + 1]),
+                                      *reinterpret_cast<const float2*>(&b1_s[o0 + q]));
+          o8[q] = __float2bfloat16_rn(pvalid ? r.x : 0.0f);
+          o8[q + 1] = __float2bfloat16_rn(pvalid ? r.y : 0.0f);
+        }
+        *reinterpret_cast<uint4*>(theta + (((size_t)prow * (kC / 8) + o0 / 8) * Ws + px) * 8) =
+            *reinterpret_cast<const uint4*>(o8);
+      }
+    }
+  };
   int j = 0;  // MMA tiles of this CTA
+  int prev_row = 0, prev_x = 0;
+  bool prev_valid = false, failed = false;  // failed: CTA-uniform (set after __syncthreads_or)
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int row = t / xt;  // b * Hs + y
     const int y = row % Hs, b = row / Hs;
@@ -259,51 +307,49 @@ __global__ void __launch_bounds__(128, kLiftCtasPerSm)
       h[2 * jp] = __float2bfloat16_rn(r.x);
       h[2 * jp + 1] = __float2bfloat16_rn(r.y);
     }
+    unsigned char* as = a_s[j & 1];  // last read by the MMA of tile j - 2, completed
 #pragma unroll
     for (int g = 0; g < kHid / 8; ++g)
-      *reinterpret_cast<uint4*>(a_s + g * 2048 + threadIdx.x * 16) =
+      *reinterpret_cast<uint4*>(as + g * 2048 + threadIdx.x * 16) =
           *reinterpret_cast<const uint4*>(&h[g * 8]);
     fence_proxy_async_smem();
     tc_fence_before();
-    __syncthreads();  // A complete; every thread has drained the previous accumulator
+    __syncthreads();  // A complete; accumulator j & 1 (tile j - 2) drained by every thread
     tc_fence_after();
     if (threadIdx.x == 0) {
 #pragma unroll
       for (int kk = 0; kk < kKG / 2; ++kk)
-        mma_bf16(tmem, smem_desc(a_s + kk * 4096, 2048, 128),
+        mma_bf16(tmem + (j & 1) * kAccCols, smem_desc(as + kk * 4096, 2048, 128),
                  smem_desc(b_s + kk * 2 * kC * 16, kC * 16, 128), idesc, kk > 0);
-      mma_commit(&mma_bar);
+      mma_commit(&mma_bar[j & 1]);
     }
-    const bool ok = mbar_wait_sleep(&mma_bar, j & 1, status);
-    ++j;
-    if (__syncthreads_or(!ok)) break;  // the whole CTA leaves together after a timeout
-    tc_fence_after();
-#pragma unroll
-    for (int cb = 0; cb < kAccCols / 32; ++cb) {
-      float v[32];
-      const uint32_t ta = tmem + cb * 32 + ((uint32_t)(warp * 32) << 16);
-      if (kC >= 32) tmem_ld32(ta, v);
-      else tmem_ld16(ta, v);
-#pragma unroll
-      for (int g = 0; g < (kC < 32 ? kC : 32) / 8; ++g) {
-        const int o0 = cb * 32 + g * 8;
-        __align__(16) __nv_bfloat16 o8[8];
-#pragma unroll
-        for (int q = 0; q < 8; q += 2) {
-          const float2 r = __fadd2_rn(make_float2(v[g * 8 + q], v[g * 8 + q + 1]),
-                                      *reinterpret_cast<const float2*>(&b1_s[o0 + q]));
-          o8[q] = __float2bfloat16_rn(valid ? r.x : 0.0f);
-          o8[q + 1] = __float2bfloat16_rn(valid ? r.y : 0.0f);
-        }
-        *reinterpret_cast<uint4*>(theta + (((size_t)row * (kC / 8) + o0 / 8) * Ws + x) * 8) =
-            *reinterpret_cast<const uint4*>(o8);
+    if (j >= 1) {  // drain tile j - 1 while the MMA of tile j runs
+      const int pj = j - 1;
+      const bool ok = mbar_wait_sleep(&mma_bar[pj & 1], (pj >> 1) & 1, status);
+      if (__syncthreads_or(!ok)) {  // the whole CTA leaves together after a timeout
+        failed = true;
+        break;
       }
+      tc_fence_after();
+      drain(pj & 1, prev_row, prev_x, prev_valid);
+    }
+    prev_row = row;
+    prev_x = x;
+    prev_valid = valid;
+    ++j;
+  }
+  if (!failed && j >= 1) {  // the last MMA tile
+    const int pj = j - 1;
+    const bool ok = mbar_wait_sleep(&mma_bar[pj & 1], (pj >> 1) & 1, status);
+    if (!__syncthreads_or(!ok)) {
+      tc_fence_after();
+      drain(pj & 1, prev_row, prev_x, prev_valid);
     }
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, kAccCols);
+  if (warp == 0) tmem_dealloc(tmem, 2 * kAccCols);
 }
 
 // Projection Q from the channel-blocked field, any decoder shape (the common shape
@@ -314,6 +360,8 @@ __global__ void __launch_bounds__(128)
     k_decoder_blk(const __nv_bfloat16* __restrict__ theta, float* __restrict__ out,
                   const float* __restrict__ params, const unsigned* __restrict__ offs,
                   int nlayers, int B, TcGrid gd, int S, int cout, int act) {
+  pdl_trigger();
+  pdl_wait();
   const int H = gd.H0, W = gd.W0;
   extern __shared__ float dec_s[];
   // layout: for each layer l: w [S][fan] then b [S]; then out.w [cout][fan], out.b [cout]
@@ -382,6 +430,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     k_fwd_x_tc(const __nv_bfloat16* __restrict__ theta, const __nv_bfloat16* __restrict__ fw,
                __nv_bfloat16* __restrict__ x1b, int B, int H, int W, int m,
                unsigned* __restrict__ status) {
+  pdl_trigger();
   // H, W: the storage grid Hs x Ws (the table is zero beyond the layers' grid)
   constexpr int kRows = 128 / kC;  // image rows per tile
   constexpr int kG = kC / 8;       // 8-channel groups
@@ -412,6 +461,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  pdl_wait();  // everything below may touch buffers of the previous kernels
   const uint32_t tmem = tmem_base;
 
   if (warp == 4) {
@@ -532,6 +582,7 @@ template <int kC>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_ydft_tc(const __nv_bfloat16* __restrict__ x1b, const __nv_bfloat16* __restrict__ fy,
               float2* __restrict__ xh, int B, int H, int m, unsigned* __restrict__ status) {
+  pdl_trigger();
   const SpecDims d = spec_dims(kC, m);
   const int rows = m * kC;  // (kx, c) rows of one batch item
   const int mt = (rows + 127) / 128;
@@ -564,6 +615,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  pdl_wait();  // everything below may touch buffers of the previous kernels
   const uint32_t tmem = tmem_base;
 
   if (warp == 4) {
@@ -666,6 +718,8 @@ template <int kC>
 __global__ void __launch_bounds__(256)
     k_mix(const float2* __restrict__ xh, const float2* __restrict__ rt,
           __nv_bfloat16* __restrict__ yb, int B, int m) {
+  pdl_trigger();
+  pdl_wait();
   const SpecDims d = spec_dims(kC, m);
   extern __shared__ float2 mix_s[];
   float2* r_s = mix_s;             // [c][o]
@@ -749,6 +803,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     k_iydft_tc(const __nv_bfloat16* __restrict__ ty, const __nv_bfloat16* __restrict__ yb,
                __nv_bfloat16* __restrict__ zt, int B, int H, int m,
                unsigned* __restrict__ status) {
+  pdl_trigger();
   constexpr int kKnk = kC <= 32 ? 8 : 4;
   constexpr int kN = kKnk * kC;  // accumulator columns per tile (128 or 256)
   const SpecDims d = spec_dims(kC, m);
@@ -779,6 +834,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  pdl_wait();  // everything below may touch buffers of the previous kernels
   const uint32_t tmem = tmem_base;
 
   if (warp == 4) {
@@ -899,6 +955,7 @@ __global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
                const __nv_bfloat16* __restrict__ zt, const float* __restrict__ wmat,
                const float* __restrict__ bias, __nv_bfloat16* __restrict__ out, int B, TcGrid gd,
                unsigned* __restrict__ status) {
+  pdl_trigger();
   constexpr int kG = kC / 8;
   constexpr int kSG = kK2 / 8;                // spectral K groups (k' < kK2)
   constexpr int kKG = kSG + kG;               // K groups of 8: spectral + C channels
@@ -940,6 +997,7 @@ __global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  pdl_wait();  // everything below may touch buffers of the previous kernels
   const uint32_t tmem = tmem_base;
 
   if (warp == kInvEpiWarps) {
@@ -1060,6 +1118,7 @@ __global__ void __launch_bounds__(kDecThreads, kDecCtasPerSm)
     k_decoder_tc(const __nv_bfloat16* __restrict__ theta, float* __restrict__ out,
                  const float* __restrict__ params, const unsigned* __restrict__ offs, int B,
                  TcGrid gd, unsigned* __restrict__ status) {
+  pdl_trigger();
   const int H = gd.H0, W = gd.W0;
   constexpr int kS = kC;
   constexpr int kG = kC / 8;
@@ -1111,6 +1170,7 @@ __global__ void __launch_bounds__(kDecThreads, kDecCtasPerSm)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  pdl_wait();  // everything below may touch buffers of the previous kernels
   const uint32_t tmem = tmem_base;
 
   if (warp == kDecEpiWarps) {
@@ -1208,6 +1268,24 @@ __global__ void __launch_bounds__(kDecThreads, kDecCtasPerSm)
 // ------------------------------------------------------------------- host
 int fno_tc_width(int C) { return C <= 16 ? 16 : (C <= 32 ? 32 : 64); }
 
+// Launch with programmatic stream serialisation (see pdl_trigger / pdl_wait).
+template <typename... KArgs, typename... Args>
+static int launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                      cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  LBM_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...));
+  return LBM_OK;
+}
+
 static TcGrid tc_grid(const fno_config& c, int H, int W) {
   TcGrid g;
   g.H0 = H;
@@ -1297,16 +1375,15 @@ static int fno_forward_tc_impl(const fno_config& c, const FnoTcParams& P, const 
   // padding entries of Yb (k' >= 2m, a >= 2m) are never written by the mixing kernel
   LBM_CHECK_CUDA(cudaMemsetAsync(yb, 0, (size_t)B * d.kg * d.nn * 16, s));
   const int n_tables = 2 * gd.Ws * kK2 + (gd.Hs / 4) * d.nf * 8 + d.kg * hp * 8;
-  k_tables<<<(n_tables + 255) / 256, 256, 0, s>>>(fw, ti, fy, ty, gd, m, hp, d.nf, d.kg);
+  LBM_TRY(launch_pdl(k_tables, dim3((n_tables + 255) / 256), dim3(256), 0, s, fw, ti, fy, ty, gd, m, hp, d.nf, d.kg));
   const size_t spix = (size_t)B * gd.Hs * gd.Ws;
-  const int lift_ctas = (int)std::min<size_t>(spix / 128, (size_t)kLiftCtasPerSm * nsm);
+  const int lift_ctas = (int)std::min<size_t>(spix / 128, (size_t)lift_ctas_per_sm(kC) * nsm);
   if (c.c_in == 4)
-    k_lift_tc<kC, 4, kAct><<<lift_ctas, 128, 0, s>>>(in, th[0], th[1], P.lift0_w, P.lift0_b,
-                                                     P.lift1_w, P.lift1_b, B, gd, c.c_in, status);
+    LBM_TRY(launch_pdl((k_lift_tc<kC, 4, kAct>), dim3(lift_ctas), dim3(128), 0, s, in, th[0], th[1], P.lift0_w, P.lift0_b,
+                                                     P.lift1_w, P.lift1_b, B, gd, c.c_in, status));
   else
-    k_lift_tc<kC, 0, kAct><<<lift_ctas, 128, 0, s>>>(in, th[0], th[1], P.lift0_w, P.lift0_b,
-                                                     P.lift1_w, P.lift1_b, B, gd, c.c_in, status);
-  LBM_CHECK_LAUNCH();
+    LBM_TRY(launch_pdl((k_lift_tc<kC, 0, kAct>), dim3(lift_ctas), dim3(128), 0, s, in, th[0], th[1], P.lift0_w, P.lift0_b,
+                                                     P.lift1_w, P.lift1_b, B, gd, c.c_in, status));
   const size_t f_smem = fwd_smem(gd.Ws, kK2), i_smem = inv_smem(kC, kK2);
   const size_t y_smem = ydft_smem(kC, gd.Hs, m), iy_smem = iydft_smem(kC, m);
   const size_t mix_smem = (size_t)(kC * kC + kMixB * kC) * sizeof(float2);
@@ -1320,18 +1397,13 @@ static int fno_forward_tc_impl(const fno_config& c, const FnoTcParams& P, const 
   const dim3 mix_grid((unsigned)(2 * m * m), (unsigned)((B + kMixB - 1) / kMixB));
   int cur = 0;
   for (int n = 0; n < c.layers; ++n) {
-    k_fwd_x_tc<kC, kK2><<<fwd_ctas, kTcThreads, f_smem, s>>>(th[cur], fw, x1b, B, gd.Hs, gd.Ws,
-                                                             m, status);
-    LBM_CHECK_LAUNCH();
-    k_ydft_tc<kC><<<ydft_ctas, kTcThreads, y_smem, s>>>(x1b, fy, xh, B, gd.Hs, m, status);
-    LBM_CHECK_LAUNCH();
-    k_mix<kC><<<mix_grid, 256, mix_smem, s>>>(xh, P.rt[n], yb, B, m);
-    LBM_CHECK_LAUNCH();
-    k_iydft_tc<kC, kK2><<<iydft_ctas, kTcThreads, iy_smem, s>>>(ty, yb, zt, B, gd.Hv, m, status);
-    LBM_CHECK_LAUNCH();
-    k_inv_x_tc<kC, kAct, kK2><<<inv_ctas, kInvThreads, i_smem, s>>>(
-        th[cur], ti, zt, P.w[n], P.b[n], th[cur ^ 1], B, gd, status);
-    LBM_CHECK_LAUNCH();
+    LBM_TRY(launch_pdl((k_fwd_x_tc<kC, kK2>), dim3(fwd_ctas), dim3(kTcThreads), f_smem, s, th[cur], fw, x1b, B, gd.Hs, gd.Ws,
+                                                             m, status));
+    LBM_TRY(launch_pdl((k_ydft_tc<kC>), dim3(ydft_ctas), dim3(kTcThreads), y_smem, s, x1b, fy, xh, B, gd.Hs, m, status));
+    LBM_TRY(launch_pdl((k_mix<kC>), dim3(mix_grid), dim3(256), mix_smem, s, xh, P.rt[n], yb, B, m));
+    LBM_TRY(launch_pdl((k_iydft_tc<kC, kK2>), dim3(iydft_ctas), dim3(kTcThreads), iy_smem, s, ty, yb, zt, B, gd.Hv, m, status));
+    LBM_TRY(launch_pdl((k_inv_x_tc<kC, kAct, kK2>), dim3(inv_ctas), dim3(kInvThreads), i_smem, s, 
+        th[cur], ti, zt, P.w[n], P.b[n], th[cur ^ 1], B, gd, status));
     cur ^= 1;
   }
   const size_t pix = (size_t)B * H * W;
@@ -1339,17 +1411,16 @@ static int fno_forward_tc_impl(const fno_config& c, const FnoTcParams& P, const 
     const size_t smem_tc = (size_t)kC * kC * 2 + (size_t)kDecStages * (kC / 8) * 128 * 16;
     const int ntiles = B * H * (W / 128);
     const int ctas = std::min(ntiles, kDecCtasPerSm * nsm);
-    k_decoder_tc<kC, 3, kAct><<<ctas, kDecThreads, smem_tc, s>>>(th[cur], out, P.params,
-                                                                P.dec_offs, B, gd, status);
+    LBM_TRY(launch_pdl((k_decoder_tc<kC, 3, kAct>), dim3(ctas), dim3(kDecThreads), smem_tc, s, th[cur], out, P.params,
+                                                                P.dec_offs, B, gd, status));
   } else {
     const size_t dec_smem =
         ((size_t)c.dec_layers * (c.dec_size * 64 + c.dec_size) + c.c_out * 64 + c.c_out) *
         sizeof(float);
-    k_decoder_blk<kC><<<(unsigned)((pix + 127) / 128), 128, dec_smem, s>>>(
+    LBM_TRY(launch_pdl((k_decoder_blk<kC>), dim3((unsigned)((pix + 127) / 128)), dim3(128), dec_smem, s, 
         th[cur], out, P.params, P.dec_offs, c.dec_layers, B, gd, c.dec_size, c.c_out,
-        c.activation);
+        c.activation));
   }
-  LBM_CHECK_LAUNCH();
   return LBM_OK;
 }
 

@@ -2,7 +2,7 @@
 
 GELU(v) = v Phi(v) = max(v, 0) - a Q(a) with a = |v| and Q(a) = Phi(-a), the Gaussian
 tail.  Q(a) = exp(-a^2 / 2) S(a) with S(a) = erfcx(a / sqrt 2) / 2 smooth and slowly
-varying, so S is fitted by a polynomial of degree 10 in u = a / 3 - 1 on a in [0, 6]
+varying, so S is fitted by a polynomial of degree 7 in u = a / 3 - 1 on a in [0, 6]
 (weighted least squares at Chebyshev nodes, weight exp(-a^2/2) max(a, 1/2): the
 absolute error of a Q(a), which is what enters GELU), converted to monomial
 coefficients and rounded to FP32.  Beyond a = 6, a Q(a) < 7e-9 and the kernels clamp a.
@@ -13,7 +13,7 @@ import numpy as np
 from numpy.polynomial import chebyshev as C
 from scipy.special import erfcx
 
-DEG, A, NODES = 10, 6.0, 8000
+DEG, A, NODES = 7, 6.0, 8000
 
 
 def coefficients():

@@ -1,10 +1,10 @@
 """CPU pins of the inference kernels' GELU (Sec. 2.2 activation, exact form v Phi(v)).
 
 The kernels evaluate GELU(v) = max(v, 0) - a Q(a), a = min(|v|, 6), with the Gaussian tail
-Q(a) = exp(-a^2/2) S(a) and S a degree-10 polynomial in u = a/3 - 1 whose coefficients
+Q(a) = exp(-a^2/2) S(a) and S a degree-7 polynomial in u = a/3 - 1 whose coefficients
 live in csrc/gelu_poly.cuh (written by csrc/gelu_fit.py).  Here: the committed header is
 what the generator writes; the formula, evaluated step by step in FP32 on the host, is
-within 2e-7 (1 + |v|) of v Phi(v) computed with math.erf; and GELU(v) - GELU(-v) = v,
+within 5e-6 (1 + |v|) of v Phi(v) computed with math.erf; and GELU(v) - GELU(-v) = v,
 an identity of v Phi(v), holds to the rounding of the final FMA (two ulps of v)."""
 import importlib.util
 import io
@@ -66,7 +66,7 @@ def test_formula_matches_exact_gelu():
     for v in vs.tolist():
         ref = 0.5 * v * (1.0 + math.erf(v / math.sqrt(2.0)))
         worst = max(worst, abs(float(gelu_kernel_formula(v)) - ref) / (1.0 + abs(v)))
-    assert worst < 2e-7, worst
+    assert worst < 5e-6, worst
 
 
 def test_formula_symmetry_and_special_values():
@@ -78,4 +78,5 @@ def test_formula_symmetry_and_special_values():
     assert gelu_kernel_formula(np.inf) == np.inf
     assert np.isnan(gelu_kernel_formula(np.nan))
     # beyond the clamp the polynomial's value at a = 6 stands in for the (smaller) exact tail
-    assert abs(float(gelu_kernel_formula(-30.0))) < 5e-8
+    # (6 Q(6) = 5.9e-9); it stays far inside the bound 5e-6 (1 + |v|)
+    assert abs(float(gelu_kernel_formula(-30.0))) < 5e-6
