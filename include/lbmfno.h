@@ -168,7 +168,7 @@ int lbm_step_residual(lbm_handle* h, double* out_h, int update_prev, void* strea
  * Allocates nothing: no cudaMalloc, no cudaFree, no allocating library routine.
  *  - Limit: batches whose statistics need more than 4 MiB of scratch (about 87,000
  *    row segments of 128 cells, roughly 11 million lattice cells; each grid rounds
- *    its segment count up to a multiple of 256) are rejected with
+ *    its segment count up to a multiple of 1024) are rejected with
  *    LBM_ERR_INVALID_ARG; use lbm_residual for them.
  *  - Every call looks up the array's device address for the current device
  *    (cudaGetSymbolAddress, which allocates nothing), so the address stays right

@@ -99,7 +99,7 @@ struct GridDev {
 constexpr int kBlock = 256;  // threads per block of the flat cell launches
 // Row segments (128 cells) whose statistics partials one reduction block sums; a
 // grid's segment (y, s) has partial slot rblk_start * kSegsPerRblk + y * nseg + s.
-constexpr int kSegsPerRblk = kBlock;
+constexpr int kSegsPerRblk = 4 * kBlock;
 
 // Grid of a block index: binary search over a per-grid prefix of first blocks.
 template <int GridDev::*START>

@@ -70,6 +70,25 @@ __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+// Sums of 16 per-lane values over the warp in one butterfly: at the level with lane bit
+// b (16, 8, 4, 2) every lane keeps one half of its remaining slots (the upper half if its
+// bit b is set) and adds the partner's copy of that half, so each level moves half as
+// many values as the one before (8 + 4 + 2 + 1 shuffles, then one more for the last lane
+// bit).  On return lanes 2s and 2s + 1 hold the total of slot s in v[0].  Fixed lane and
+// slot order: deterministic.
+__device__ __forceinline__ float warp_sum16(float v[16], int lane) {
+#pragma unroll
+  for (int half = 8, bit = 16; half >= 1; half >>= 1, bit >>= 1) {
+    const bool up = (lane & bit) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const float send = up ? v[i] : v[i + half];
+      const float keep = up ? v[i + half] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
 
 // ------------------------------------------------------ the fused step ---
 // One time step of every grid of the batch in one launch: pull streaming with
@@ -118,6 +137,9 @@ template <int TY, int ST, int MB>
 struct StepShape {
   static constexpr int kStageRows = stage_row0<TY>(kQ);  // 9 TY + 6
   static constexpr int kStageFloats = kStageRows * kRowF;
+  // statistics modes: the stage also holds the tile's rows of the previous residual's
+  // velocity (u_x rows, then u_y rows, 128 floats each)
+  static constexpr int kStageFloatsStats = kStageFloats + 2 * TY * kSeg;
   static constexpr int kMaskWords = (TY + 2) * kWords;  // rows y0-1 .. y0+TY
   struct __align__(16) Meta {
     GridDev g;
@@ -126,6 +148,8 @@ struct StepShape {
   };
   static constexpr size_t kSmem =
       (size_t)ST * kStageFloats * sizeof(float) + (size_t)ST * sizeof(Meta);
+  static constexpr size_t kSmemStats =
+      (size_t)ST * kStageFloatsStats * sizeof(float) + (size_t)ST * sizeof(Meta);
   static_assert(stage_row0<TY>(3) == 3 * TY + 1 && stage_row0<TY>(kQ) == 9 * TY + 6 &&
                     stage_row0<TY>(8) + stage_rows<TY>(8) == stage_row0<TY>(kQ),
                 "stage row offsets");
@@ -156,8 +180,8 @@ static_assert(R_COUNT <= kSegStride, "segment statistics slot");
 
 // Extra arguments of the statistics modes (unused by the others).
 struct StatsArgs {
-  float* ux_prev;      // dense velocity of the previous residual (read; written if update)
-  float* uy_prev;
+  float* ux_prev;      // velocity of the previous residual, pitched like a population plane
+  float* uy_prev;      // (read; written if update_prev)
   float* seg_partial;  // kSegStride floats per row segment (slot of GridDev)
   float u_max2;
   int update_prev;
@@ -243,7 +267,9 @@ __global__ void __launch_bounds__((TY + 1) * 32, step_min_blocks(MB, MODE))
   __shared__ int abort_s;
   using SS = StepShape<TY, ST, MB>;
   using TileMeta = typename SS::Meta;
-  constexpr int kTY = TY, kStages = ST, kStageFloats = SS::kStageFloats,
+  constexpr int kTY = TY, kStages = ST,
+                kStageFloats = kStats ? SS::kStageFloatsStats : SS::kStageFloats,
+                kUOff = SS::kStageFloats,  // statistics modes: u rows after the populations
                 kMaskWords = SS::kMaskWords;
   extern __shared__ __align__(128) float stage_mem[];
   TileMeta* metas = reinterpret_cast<TileMeta*>(stage_mem + (size_t)kStages * kStageFloats);
@@ -323,7 +349,10 @@ __global__ void __launch_bounds__((TY + 1) * 32, step_min_blocks(MB, MODE))
       if (k >= kStages) ok = mbar_wait(&empty_bar[s], ((k / kStages) - 1) & 1, status);
       if (!ok) break;
       float* st = stage_mem + (size_t)s * kStageFloats;
-      if (lane == 0) mbar_expect_tx(&full_bar[s], seg_bytes * (unsigned)(kQ * rows + 6));
+      if (lane == 0)
+        mbar_expect_tx(&full_bar[s], seg_bytes * (unsigned)(kQ * rows + 6) +
+                                         (kStats ? 2u * (unsigned)rows * (unsigned)min(kSeg, pitch - x0) * 4u
+                                                 : 0u));
       static_assert(kStageFloats > 0 && kMaskWords > 0, "shape");
       __syncwarp();
 #pragma unroll
@@ -334,6 +363,18 @@ __global__ void __launch_bounds__((TY + 1) * 32, step_min_blocks(MB, MODE))
           ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
           bulk_g2s(st + (stage_row0<TY>(i) + r) * kRowF + (xs - (x0 - 4)),
                    b + (size_t)i * plane + (size_t)ys * pitch + xs, seg_bytes, &full_bar[s]);
+        }
+      }
+      if constexpr (kStats) {
+        // the tile's rows of the previous residual's velocity (pitched planes, so every
+        // row segment is 16-byte aligned): u_x rows, then u_y rows
+        const unsigned u_bytes = (unsigned)min(kSeg, pitch - x0) * 4u;
+        const long long foff = word64(meta_w, kWFoff);
+        for (int q = lane; q < 2 * rows; q += 32) {
+          const int f = q / rows, r = q - f * rows;
+          bulk_g2s(st + kUOff + (f * kTY + r) * kSeg,
+                   (f ? sa.uy_prev : sa.ux_prev) + foff + (size_t)(y0 + r) * pitch + x0, u_bytes,
+                   &full_bar[s]);
         }
       }
       // tile metadata and mask words (generic-proxy stores, released by the arrive)
@@ -461,13 +502,18 @@ __global__ void __launch_bounds__((TY + 1) * 32, step_min_blocks(MB, MODE))
         }
       }
     }
+    float4 pu = make_float4(0.f, 0.f, 0.f, 0.f), pv = pu;
+    if constexpr (kStats) {  // the previous residual's velocity of this lane's four cells
+      pu = *reinterpret_cast<const float4*>(st + kUOff + warp * kSeg + kVec * lane);
+      pv = *reinterpret_cast<const float4*>(st + kUOff + (kTY + warp) * kSeg + kVec * lane);
+    }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty_bar[s]);  // this warp no longer reads the stage
     if constexpr (!kStats) {
       if (!active) continue;
     }
-    // statistics of this lane's four cells (kStats): FP32 lane partials; the velocity
-    // difference to the previous residual is taken after the loop
+    // statistics of this lane's four cells (kStats): FP32 lane partials; the difference
+    // to the previous residual's velocity is taken after the loop
     float acc[kStats ? R_COUNT : 1];
     float ux4[kVec], uy4[kVec];
     if constexpr (kStats) {
@@ -530,56 +576,57 @@ __global__ void __launch_bounds__((TY + 1) * 32, step_min_blocks(MB, MODE))
           uy4[j] = uy;
         }
       }
-      if constexpr (kCollide) collide(G, c);
-      if constexpr (kStore) {
+      if constexpr (!kStats) {
+        if constexpr (kCollide) collide(G, c);
+        if constexpr (kStore) {
 #pragma unroll
-        for (int i = 0; i < kQ; ++i) g[i][j] = keep ? c[i] : 0.0f;
+          for (int i = 0; i < kQ; ++i) g[i][j] = keep ? c[i] : 0.0f;
+        }
+      } else if constexpr (kStore) {
+        // statistics modes: keep the completed populations; the collision runs after the
+        // statistics are reduced, so the lane partials are dead by then
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) g[i][j] = c[i];
       }
     }
     if constexpr (kStats) {
-      const long long c0 = G.cell_off + (long long)y * nx + x;
-      // vector access only where both fields are 16-byte aligned at this cell
-      const bool vec = active && (x + kVec <= nx) &&
-                       ((reinterpret_cast<uintptr_t>(sa.ux_prev + c0) & 15) == 0) &&
-                       ((reinterpret_cast<uintptr_t>(sa.uy_prev + c0) & 15) == 0);
       if (active) {
-        float4 pu = make_float4(0.f, 0.f, 0.f, 0.f), pv = pu;
-        if (vec) {
-          pu = *reinterpret_cast<const float4*>(sa.ux_prev + c0);
-          pv = *reinterpret_cast<const float4*>(sa.uy_prev + c0);
-        }
 #pragma unroll
         for (int j = 0; j < kVec; ++j) {
           if (((own_solid >> j) & 1u) || x + j >= nx) continue;
-          const float dux = ux4[j] - (vec ? f4get(pu, j) : sa.ux_prev[c0 + j]);
-          const float duy = uy4[j] - (vec ? f4get(pv, j) : sa.uy_prev[c0 + j]);
+          const float dux = ux4[j] - f4get(pu, j);
+          const float duy = uy4[j] - f4get(pv, j);
           acc[R_DU2] += dux * dux + duy * duy;
         }
       }
       if (active && sa.update_prev) {
-        if (vec) {
-          // solid cells keep u_prev = 0, as set by the re-initialisation
-          *reinterpret_cast<float4*>(sa.ux_prev + c0) = make_float4(ux4[0], ux4[1], ux4[2], ux4[3]);
-          *reinterpret_cast<float4*>(sa.uy_prev + c0) = make_float4(uy4[0], uy4[1], uy4[2], uy4[3]);
-        } else {
+        // pitched rows: the four cells (and any row padding past nx, which stays 0) are
+        // one aligned float4; solid cells keep 0, as set by the re-initialisation
+        const size_t pc = (size_t)G.f_off + (size_t)y * G.pitch + x;
+        *reinterpret_cast<float4*>(sa.ux_prev + pc) = make_float4(ux4[0], ux4[1], ux4[2], ux4[3]);
+        *reinterpret_cast<float4*>(sa.uy_prev + pc) = make_float4(uy4[0], uy4[1], uy4[2], uy4[3]);
+      }
+      // FP32 sums over the segment's 128 cells, all statistics in one warp butterfly
+      float v16[16];
 #pragma unroll
-          for (int j = 0; j < kVec; ++j)
-            if (x + j < nx) {
-              sa.ux_prev[c0 + j] = ux4[j];
-              sa.uy_prev[c0 + j] = uy4[j];
-            }
+      for (int k = 0; k < 16; ++k) v16[k] = k < R_COUNT ? acc[k] : 0.0f;
+      const float tot = warp_sum16(v16, lane);
+      const long long slot = (long long)G.rblk_start * kSegsPerRblk + (long long)y * G.nseg + x0 / kSeg;
+      if ((lane & 1) == 0 && (lane >> 1) < R_COUNT)
+        sa.seg_partial[slot * kSegStride + (lane >> 1)] = tot;
+      if (!active) continue;
+      if constexpr (kStore) {
+#pragma unroll
+        for (int j = 0; j < kVec; ++j) {
+          float c[kQ];
+#pragma unroll
+          for (int i = 0; i < kQ; ++i) c[i] = g[i][j];
+          if constexpr (kCollide) collide(G, c);
+          const bool keep = !((own_solid >> j) & 1u);  // solid cells store 0
+#pragma unroll
+          for (int i = 0; i < kQ; ++i) g[i][j] = keep ? c[i] : 0.0f;
         }
       }
-      // warp tree in FP32 over the segment's 128 cells (fixed lane map: deterministic)
-      float mine = 0.0f;
-#pragma unroll
-      for (int k = 0; k < R_COUNT; ++k) {
-        const float w = warp_sum(acc[k]);
-        if (lane == k) mine = w;
-      }
-      const long long slot = (long long)G.rblk_start * kSegsPerRblk + (long long)y * G.nseg + x0 / kSeg;
-      if (lane < R_COUNT) sa.seg_partial[slot * kSegStride + lane] = mine;
-      if (!active) continue;
     }
     if constexpr (kStore) {
       float* o = dst + G.f_off + (size_t)y * G.pitch + x;
@@ -612,7 +659,11 @@ constexpr int kStepModes = 5;
 struct StepVariant {
   int ty, stages, minb;
   StepKernel kernel[kStepModes];  // by StepMode
-  size_t smem;
+  size_t smem;        // dynamic shared memory of the modes without statistics
+  size_t smem_stats;  // ... of kModeStats and kModeStepStats
+  size_t smem_of(int mode) const {
+    return mode == kModeStats || mode == kModeStepStats ? smem_stats : smem;
+  }
 };
 #define LBM_STEP_VARIANT(TY, ST, MB)                                                       \
   StepVariant {                                                                            \
@@ -620,7 +671,7 @@ struct StepVariant {
         {k_step_tma<TY, ST, MB, kModeStep>, k_step_tma<TY, ST, MB, kModeStream>,           \
          k_step_tma<TY, ST, MB, kModeStats>, k_step_tma<TY, ST, MB, kModeStepStats>,       \
          k_step_tma<TY, ST, MB, kModeMulti>},                                              \
-        StepShape<TY, ST, MB>::kSmem                                                       \
+        StepShape<TY, ST, MB>::kSmem, StepShape<TY, ST, MB>::kSmemStats                    \
   }
 static const StepVariant kStepVariants[LBM_STEP_VARIANTS] = {
     LBM_STEP_VARIANT(3, 2, 5), LBM_STEP_VARIANT(4, 2, 4), LBM_STEP_VARIANT(2, 2, 7),
@@ -704,23 +755,29 @@ __device__ __forceinline__ void block_reduce_store(double v[R_COUNT], double* ou
 // Steady-state statistics of the current time level, stage 1: the step kernel in a
 // statistics mode leaves FP32 sums (a warp tree over the 128 cells of one row segment)
 // per row segment; block b of grid g sums the segments b * kSegsPerRblk .. +kSegsPerRblk
-// of the grid in FP64, one segment per thread, then in a fixed FP64 tree.  Stage 2
+// of the grid in FP64, four consecutive segments per thread, then in a fixed FP64 tree.  Stage 2
 // (k_residual_final) adds a grid's blocks.  Fixed maps and trees: deterministic.
 __global__ void __launch_bounds__(kBlock) k_stats_reduce(const GridDev* __restrict__ grids,
                                                          int ngrids,
                                                          const float* __restrict__ seg_partial,
                                                          double* __restrict__ partial) {
-  static_assert(kSegsPerRblk == kBlock, "one segment per thread");
+  constexpr int kPerThread = kSegsPerRblk / kBlock;
+  static_assert(kPerThread * kBlock == kSegsPerRblk, "whole segments per thread");
   const int gidx = grid_of<&GridDev::rblk_start>(grids, ngrids, blockIdx.x);
   const GridDev& G = grids[gidx];
-  const long long task = (long long)(blockIdx.x - G.rblk_start) * kSegsPerRblk + threadIdx.x;
+  const long long nsegs = (long long)G.nseg * G.ny;
+  const long long task0 =
+      (long long)(blockIdx.x - G.rblk_start) * kSegsPerRblk + (long long)threadIdx.x * kPerThread;
   double v[R_COUNT];
 #pragma unroll
   for (int k = 0; k < R_COUNT; ++k) v[k] = 0.0;
-  if (task < (long long)G.nseg * G.ny) {
-    const float* sp = seg_partial + ((long long)G.rblk_start * kSegsPerRblk + task) * kSegStride;
+  for (int q = 0; q < kPerThread; ++q) {  // consecutive segments, in order
+    const long long task = task0 + q;
+    if (task < nsegs) {
+      const float* sp = seg_partial + ((long long)G.rblk_start * kSegsPerRblk + task) * kSegStride;
 #pragma unroll
-    for (int k = 0; k < R_COUNT; ++k) v[k] = (double)sp[k];
+      for (int k = 0; k < R_COUNT; ++k) v[k] += (double)sp[k];
+    }
   }
   block_reduce_store(v, partial + (size_t)blockIdx.x * R_COUNT);
 }
@@ -759,8 +816,8 @@ __global__ void __launch_bounds__(kBlock) k_reinit(const GridDev* __restrict__ g
   const float* UX = ux_i + G.cell_off;
   const float* UY = uy_i + G.cell_off;
   const bool solid = mask_bit(m, G.wpr, x, y);
-  ux_prev[G.cell_off + c] = solid ? 0.0f : UX[c];
-  uy_prev[G.cell_off + c] = solid ? 0.0f : UY[c];
+  ux_prev[G.f_off + (long long)y * G.pitch + x] = solid ? 0.0f : UX[c];
+  uy_prev[G.f_off + (long long)y * G.pitch + x] = solid ? 0.0f : UY[c];
   if (solid) return;
   const float rho = R[c], ux = UX[c], uy = UY[c];
   const float drho = rho - 1.0f;
@@ -920,7 +977,7 @@ static int plan_layout(const lbm_grid* grids, int ngrids, lbm_layout* lay,
   w.grids_off = 0;
   w.uprev_off = align_up(sizeof(GridDev) * ngrids, 256);
   const StatsScratch sc = stats_scratch(rblk, ngrids);
-  w.seg_off = align_up(w.uprev_off + 2 * cells * sizeof(float), 256);
+  w.seg_off = align_up(w.uprev_off + 2 * plane_all * sizeof(float), 256);
   w.partial_off = w.seg_off + sc.partial_off;
   w.stats_off = w.seg_off + sc.stats_off;
   w.status_off = w.seg_off + sc.total;
@@ -954,7 +1011,7 @@ static int launch_step(Handle* h, int v, int mode, const float* src, float* dst,
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)ctas);
   cfg.blockDim = dim3((unsigned)((sv.ty + 1) * 32));
-  cfg.dynamicSmemBytes = sv.smem;
+  cfg.dynamicSmemBytes = sv.smem_of(mode);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -1034,10 +1091,16 @@ static int residual_run(Handle* h, int mode, char* scratch, double* out_h, int u
   double* stats = reinterpret_cast<double*>(scratch + sc.stats_off);
   StatsArgs sa{h->ux_prev, h->uy_prev, seg, h->u_max2, update_prev ? 1 : 0};
   LBM_TRY(launch_step(h, h->variant, mode, h->f[h->cur], h->f[h->cur ^ 1], s, sa));
-  k_stats_reduce<<<h->nrblk_total, kBlock, 0, s>>>(h->gd_d, h->ngrids, seg, partial);
-  LBM_CHECK_LAUNCH();
-  k_residual_final<<<h->ngrids, kBlock, 0, s>>>(h->gd_d, partial, stats);
-  LBM_CHECK_LAUNCH();
+  if (h->nrblk_total == h->ngrids) {
+    // every grid's segments fit one first-stage block: its sum is the grid's total
+    k_stats_reduce<<<h->nrblk_total, kBlock, 0, s>>>(h->gd_d, h->ngrids, seg, stats);
+    LBM_CHECK_LAUNCH();
+  } else {
+    k_stats_reduce<<<h->nrblk_total, kBlock, 0, s>>>(h->gd_d, h->ngrids, seg, partial);
+    LBM_CHECK_LAUNCH();
+    k_residual_final<<<h->ngrids, kBlock, 0, s>>>(h->gd_d, partial, stats);
+    LBM_CHECK_LAUNCH();
+  }
   LBM_CHECK_CUDA(cudaMemcpyAsync(h->stats_h.data(), stats, sizeof(double) * R_COUNT * h->ngrids,
                                  cudaMemcpyDeviceToHost, s));
   LBM_CHECK_CUDA(cudaMemcpyAsync(&h->status_h, h->status_d, sizeof(unsigned),
@@ -1095,7 +1158,7 @@ int lbm_init(const lbm_grid* grids_h, int ngrids, const uint32_t* mask_d, float*
   char* ws = static_cast<char*>(ws_d);
   h->gd_d = reinterpret_cast<GridDev*>(ws + wp.grids_off);
   h->ux_prev = reinterpret_cast<float*>(ws + wp.uprev_off);
-  h->uy_prev = h->ux_prev + h->layout.cells;
+  h->uy_prev = h->ux_prev + h->layout.f_elems / kQ;  // one pitched plane per field
   h->scratch = ws + wp.seg_off;
   h->status_d = reinterpret_cast<unsigned*>(ws + wp.status_off);
   h->bar_count = reinterpret_cast<unsigned*>(ws + wp.bar_off);
@@ -1126,12 +1189,12 @@ int lbm_init(const lbm_grid* grids_h, int ngrids, const uint32_t* mask_d, float*
       const StepVariant& sv = kStepVariants[v];
       for (int m = 0; ok && m < kStepModes; ++m)
         ok = cudaFuncSetAttribute(sv.kernel[m], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)sv.smem) == cudaSuccess;
+                                  (int)sv.smem_of(m)) == cudaSuccess;
       // each mode's persistent grid holds the CTAs that fit at once
       for (int m = 0; ok && m < kStepModes; ++m)
         ok = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->blocks_per_sm_vm[v][m],
                                                            sv.kernel[m], (sv.ty + 1) * 32,
-                                                           sv.smem) == cudaSuccess;
+                                                           sv.smem_of(m)) == cudaSuccess;
       h->blocks_per_sm_v[v] = h->blocks_per_sm_vm[v][kModeStep];
     }
     if (!ok) {
@@ -1149,7 +1212,7 @@ int lbm_init(const lbm_grid* grids_h, int ngrids, const uint32_t* mask_d, float*
                       s) != cudaSuccess ||
       cudaMemsetAsync(f_a_d, 0, h->layout.f_elems * sizeof(float), s) != cudaSuccess ||
       cudaMemsetAsync(f_b_d, 0, h->layout.f_elems * sizeof(float), s) != cudaSuccess ||
-      cudaMemsetAsync(h->ux_prev, 0, 2 * h->layout.cells * sizeof(float), s) != cudaSuccess ||
+      cudaMemsetAsync(h->ux_prev, 0, 2 * (h->layout.f_elems / kQ) * sizeof(float), s) != cudaSuccess ||
       cudaMemsetAsync(h->status_d, 0, sizeof(unsigned), s) != cudaSuccess ||
       cudaMemcpyAsync(h->tiles_d[0], tiles.data(), tiles.size() * sizeof(int4),
                       cudaMemcpyHostToDevice, s) != cudaSuccess ||
