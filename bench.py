@@ -76,7 +76,50 @@ def parse():
                     help="timed steps of the differentiable hybrid training workload (0: skip)")
     ap.add_argument("--step-variant", type=int, default=-1,
                     help="step-kernel tile shape index; -1 (default) times all shapes and keeps the fastest")
+    ap.add_argument("--case", default=None, choices=["lbm", "check", "fno"],
+                    help="run one small case to be profiled and exit (no JSON line): 'lbm' 60 "
+                         "steps of the bench batch (tile shape 3), 'check' 5 steps + 5 "
+                         "statistics-only residuals + 5 step+statistics checks of it, 'fno' "
+                         "8 forwards of the FNO throughput shape")
     return ap.parse_args()
+
+
+def run_case(args):
+    """Small cases for ncu captures (one kernel, few launches before the captured ones)."""
+    import torch
+    import synth
+    import paper_2604_27158_gb300 as P
+    from paper_2604_27158_gb300.fno import Fno, FnoShape
+    from paper_2604_27158_gb300.lbm import GridSpec, Lattice
+    if args.case in ("lbm", "check"):
+        T = args.trajectories
+        masks, _ = workload(T, 0)
+        lat = Lattice([GridSpec(NX, NY, TAU, bc_west=P.BC_PRESSURE, bc_east=P.BC_PRESSURE,
+                                west_value=RHO_IN, east_value=RHO_OUT)] * T, masks)
+        lat.set_step_variant(3 if args.step_variant < 0 else args.step_variant)
+        if args.case == "lbm":
+            lat.step(60)
+        else:
+            lat.step(20)
+            for _ in range(5):
+                lat.step(1)
+            for _ in range(5):
+                lat.residual(update_prev=True)
+            for _ in range(5):
+                lat.step_residual(update_prev=True)
+        lat.close()
+    else:
+        B = 32
+        sshape, flat = fno_params()
+        net = Fno(FnoShape(), flat)
+        x = torch.randn(B, 4, 256, 256, device="cuda") * 1e-2
+        y = torch.empty(B, 3, 256, 256, device="cuda")
+        for _ in range(8):
+            net(x, y)
+        net.check(B, 256, 256)
+        net.close()
+    torch.cuda.synchronize()
+    return 0
 
 
 def dist_env():
@@ -347,6 +390,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.case is not None:
+        return run_case(args)
     rank, world, local = dist_env()
     import torch
     import torch.distributed as dist

@@ -272,10 +272,26 @@ __global__ void __launch_bounds__(128, lift_ctas_per_sm(kC))
   int j = 0;  // MMA tiles of this CTA
   int prev_row = 0, prev_x = 0;
   bool prev_valid = false, failed = false;  // failed: CTA-uniform (set after __syncthreads_or)
+  // this thread's raw inputs of tile t (loaded one tile ahead, so the loads of the next
+  // tile are in flight while this one is computed)
+  constexpr int kCinR = kCin > 0 ? kCin : 16;
+  auto load_in = [&](int tt, float (&dst)[kCinR]) {
+    const int rw = tt / xt, yy = rw % Hs, bb = rw / Hs, xx = (tt - rw * xt) * 128 + threadIdx.x;
+    const bool ok = tt < ntiles && yy < H && xx < W;
+#pragma unroll
+    for (int c = 0; c < kCinR; ++c)
+      dst[c] = (ok && c < cin) ? in[(((size_t)bb * cin + c) * H + yy) * W + xx] : 0.0f;
+  };
+  float raw[kCinR];
+  load_in(blockIdx.x, raw);
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int row = t / xt;  // b * Hs + y
     const int y = row % Hs, b = row / Hs;
     const int x0 = (t - row * xt) * 128, x = x0 + threadIdx.x;
+    float cur[kCinR];
+#pragma unroll
+    for (int c = 0; c < kCinR; ++c) cur[c] = raw[c];
+    load_in(t + gridDim.x, raw);
     if (y >= H || x0 >= W) {  // CTA-uniform: the tile is padding
 #pragma unroll
       for (int g = 0; g < kC / 8; ++g) {
@@ -289,11 +305,8 @@ __global__ void __launch_bounds__(128, lift_ctas_per_sm(kC))
     // layer 1 for this thread's pixel (inputs and coordinates rounded to bfloat16)
     float xin[kX];
 #pragma unroll
-    for (int c = 0; c < (kCin > 0 ? kCin : 16); ++c)
-      if (c < cin)
-        xin[c] = valid ? __bfloat162float(__float2bfloat16_rn(
-                             in[(((size_t)b * cin + c) * H + y) * W + x]))
-                       : 0.0f;
+    for (int c = 0; c < kCinR; ++c)
+      if (c < cin) xin[c] = __bfloat162float(__float2bfloat16_rn(cur[c]));  // 0 if !valid
     xin[cin] = __bfloat162float(__float2bfloat16_rn((float)x / (float)max(W - 1, 1)));
     xin[cin + 1] = __bfloat162float(__float2bfloat16_rn((float)y / (float)max(H - 1, 1)));
     __align__(16) __nv_bfloat16 h[kHid];
