@@ -76,11 +76,12 @@ def parse():
                     help="timed steps of the differentiable hybrid training workload (0: skip)")
     ap.add_argument("--step-variant", type=int, default=-1,
                     help="step-kernel tile shape index; -1 (default) times all shapes and keeps the fastest")
-    ap.add_argument("--case", default=None, choices=["lbm", "check", "fno"],
+    ap.add_argument("--case", default=None, choices=["lbm", "check", "fno", "shear_fno"],
                     help="run one small case to be profiled and exit (no JSON line): 'lbm' 60 "
                          "steps of the bench batch (tile shape 3), 'check' 5 steps + 5 "
                          "statistics-only residuals + 5 step+statistics checks of it, 'fno' "
-                         "8 forwards of the FNO throughput shape")
+                         "8 forwards of the FNO throughput shape, 'shear_fno' 8 forwards of "
+                         "the double-shear density and velocity networks on 100 fields")
     return ap.parse_args()
 
 
@@ -108,6 +109,25 @@ def run_case(args):
             for _ in range(5):
                 lat.step_residual(update_prev=True)
         lat.close()
+    elif args.case == "shear_fno":
+        ics = synth.double_shear(100, seed=2000)
+        n = ics[0]["rho"].shape[0]
+        xr = torch.from_numpy(np.stack([ic["rho"] - 1.0 for ic in ics])[:, None].astype(np.float32)).cuda()
+        xu = torch.from_numpy(np.stack([np.stack([ic["ux"], ic["uy"]]) for ic in ics]).astype(np.float32)).cuda()
+        nets = []
+        for cin, modes, seed, x in ((1, 8, 31, xr), (2, 32, 32, xu)):
+            sh = synth.FnoShape(c_in=cin, c_out=cin, width=14, layers=3, modes=modes,
+                                dec_size=32, padding=9)
+            nets.append((Fno(FnoShape(c_in=cin, c_out=cin, width=14, layers=3, modes=modes,
+                                      dec_size=32, padding=9),
+                             synth.fno_flatten_params(sh, synth.fno_random_params(sh, seed=seed))),
+                         x, torch.empty_like(x)))
+        for _ in range(8):
+            for net, x, y in nets:
+                net(x, y)
+        for net, _, _ in nets:
+            net.check(100, n, n)
+            net.close()
     else:
         B = 32
         sshape, flat = fno_params()
@@ -893,8 +913,10 @@ def main():
                              f"U(20, 125), Delta T = {dT} steps, 30 Delta T horizon",
                  "model_group": {"density_params": nparams[0], "velocity_params": nparams[1],
                                  "padding": 9,
-                                 "path": ("tensor cores (14 channels zero-padded to 16, 137 x 137 "
-                                          "padded grid in 144 x 256 storage)"
+                                 "path": ("tensor cores (14 channels zero-padded to 16, "
+                                          f"{ns + 9} x {ns + 9} padded grid in "
+                                          f"{(ns + 9 + 7) // 8 * 8} x {(ns + 9 + 63) // 64 * 64} "
+                                          "storage)"
                                           if dnet.uses_tensor_cores(ns, ns) and
                                           vnet.uses_tensor_cores(ns, ns) else "CUDA cores")},
                  "arms": arms,

@@ -66,7 +66,10 @@ __device__ __forceinline__ int kept_ky_tc(int a, int H, int m) { return a < m ? 
 // ------------------------------------------------------------------ tables
 // Grid sizes of the tensor-core path.  The Fourier layers run on the (padded) grid
 // Hv x Wv (the input grid plus the padding); the latent field is stored on Hs x Ws
-// (Hs = Hv rounded up to 8 rows, Ws = Wv rounded up to 128 columns).  Every DFT table
+// (Hs = Hv rounded up to 8 rows, Ws = Wv rounded up to 64 columns; the lift and the
+// inverse x-DFT work in tiles of 128 columns, the last of which may cover storage columns
+// Ws .. +63 that do not exist: their loads read the workspace that follows, their results
+// are not stored).  Every DFT table
 // uses the true periods Hv and Wv and is zero on the storage padding, and the storage
 // padding of the latent field is kept at zero, so the contractions over the padded
 // extents equal the DFTs of the Hv x Wv grid.  K2: the kept x-frequencies as MMA
@@ -182,19 +185,52 @@ __global__ void k_tables(__nv_bfloat16* __restrict__ fw, __nv_bfloat16* __restri
 // CUDA cores with one thread per pixel, its outputs rounded to bfloat16 into the K-major
 // A operand in shared memory; layer 2 (C/2 -> C) as one tcgen05 MMA per 128-pixel tile
 // (M = 128 x positions of one row, N = C, K = C/2 padded to 16) with the bias added in
-// the epilogue.  Two A buffers and two TMEM accumulators: the MMA of tile j runs while
-// the threads drain tile j - 1 and compute layer 1 of tile j + 1.  Several CTAs share
-// an SM (as many as their accumulators fit in TMEM, at most six).
-constexpr int kLiftCtasPerSm = 6;
-__host__ __device__ constexpr int lift_ctas_per_sm(int C) {
-  return C <= 32 ? kLiftCtasPerSm : 4;  // 2 x 64 TMEM columns per CTA at C = 64
-}
+// the epilogue.  Warp-specialised: four producer warps compute layer 1 of successive
+// tiles into a ring of A stages, one warp issues the MMAs into two TMEM accumulators,
+// four epilogue warps drain them — no CTA-wide barrier in the loop.
 // The tiles cover the storage grid Hs x Ws: pixels outside the input grid H0 x W0 (the
 // zero padding of the lifted field and the storage padding) are written as 0 without an
 // MMA, and rows y >= Hv of the second latent buffer `theta_alt` are zeroed too (no layer
 // writes them).
+// The tiles t = t0, t0 + G, t0 + 2G, ... (G = gridDim.x) of a (b, y, x tile) raster with
+// xt tiles a row and Hs rows an image, stepped without a division per tile.
+struct TileWalk {
+  int xt, Hs, dq, dr, dy0, dy1, db0, db1;  // a step moves dq (+1 on a carry) rows
+  int t, row, b, y, xi;
+  __device__ TileWalk(int t0, int xt_, int Hs_) : xt(xt_), Hs(Hs_), t(t0) {
+    dq = gridDim.x / xt;
+    dr = gridDim.x - dq * xt;
+    dy0 = dq % Hs;
+    db0 = dq / Hs;
+    dy1 = (dq + 1) % Hs;
+    db1 = (dq + 1) / Hs;
+    row = t0 / xt;
+    xi = t0 - row * xt;
+    b = row / Hs;
+    y = row - b * Hs;
+  }
+  __device__ void next() {
+    t += gridDim.x;
+    xi += dr;
+    const bool c = xi >= xt;
+    if (c) xi -= xt;
+    row += dq + (c ? 1 : 0);
+    y += c ? dy1 : dy0;
+    b += c ? db1 : db0;
+    if (y >= Hs) {
+      y -= Hs;
+      ++b;
+    }
+  }
+};
+constexpr int kLiftStages = 4;
+constexpr int kLiftInStages = 6;  // input ring (dynamic shared memory, cin x 512 B a stage)
+constexpr int kLiftThreads = 9 * 32;  // warps 0-3 producer, 4 MMA, 5-8 epilogue
+// three CTAs per SM; two for width 64 with a runtime input width (the producers then hold
+// 16 input channels and their prefetch, which would spill at three)
+constexpr int lift_ctas_per_sm(int cin, int C) { return cin > 0 || C < 64 ? 3 : 2; }
 template <int kC, int kCin, int kAct>
-__global__ void __launch_bounds__(128, lift_ctas_per_sm(kC))
+__global__ void __launch_bounds__(kLiftThreads, lift_ctas_per_sm(kCin, kC))
     k_lift_tc(const float* __restrict__ in, __nv_bfloat16* __restrict__ theta,
               __nv_bfloat16* __restrict__ theta_alt, const float* __restrict__ w0,
               const float* __restrict__ b0, const float* __restrict__ w1,
@@ -204,17 +240,19 @@ __global__ void __launch_bounds__(128, lift_ctas_per_sm(kC))
   constexpr int kHid = kC / 2;
   constexpr int kK = kHid < 16 ? 16 : kHid;  // MMA K (zero-padded hidden units)
   constexpr int kKG = kK / 8;
-  constexpr int kX = kCin > 0 ? kCin + 2 : 18;
+  constexpr int kX = kCin > 0 ? kCin + 2 : 18;  // inputs and the two coordinates
   constexpr int kAccCols = kC < 32 ? 32 : kC;
   const int cin = kCin > 0 ? kCin : cin_rt;
   const int cin2 = cin + 2;
-  __shared__ __align__(1024) unsigned char a_s[2][kKG * 2048];  // [buffer][k group][x (128)][8]
+  __shared__ __align__(1024) unsigned char a_s[kLiftStages][kKG * 2048];  // [k group][x][8]
   __shared__ __align__(1024) unsigned char b_s[kKG * kC * 16];  // W1^T: [k group][o][8]
   __shared__ float2 w0p_s[(kHid / 2) * 18];  // (w0[j][c], w0[j+1][c]) for hidden pairs
   __shared__ __align__(16) float b0_s[kHid], b1_s[kC];
-  __shared__ __align__(8) uint64_t mma_bar[2];
+  __shared__ __align__(8) uint64_t a_full[kLiftStages], a_empty[kLiftStages];
+  __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_base;
-  const int warp = threadIdx.x >> 5;
+  extern __shared__ __align__(16) float in_s[];  // [kLiftInStages][cin][128 pixels]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int e = threadIdx.x; e < kKG * kC * 8; e += blockDim.x) {
     const int g = e / (kC * 8), o = (e / 8) % kC, il = e % 8, j = g * 8 + il;
     reinterpret_cast<__nv_bfloat16*>(b_s)[e] = __float2bfloat16_rn(j < kHid ? w1[o * kHid + j] : 0.f);
@@ -226,12 +264,18 @@ __global__ void __launch_bounds__(128, lift_ctas_per_sm(kC))
   for (int j = threadIdx.x; j < kHid; j += blockDim.x) b0_s[j] = b0[j];
   for (int o = threadIdx.x; o < kC; o += blockDim.x) b1_s[o] = b1[o];
   if (kHid < kK)  // padded hidden units stay zero
-    for (int e = threadIdx.x; e < 2 * 128 * 8; e += blockDim.x)
+    for (int e = threadIdx.x; e < kLiftStages * 128 * 8; e += blockDim.x)
       reinterpret_cast<__nv_bfloat16*>(a_s[e / 1024] + 2048)[e % 1024] = __float2bfloat16_rn(0.f);
   fence_proxy_async_smem();
   if (threadIdx.x == 0) {
-    mbar_init(&mma_bar[0], 1);
-    mbar_init(&mma_bar[1], 1);
+    for (int s = 0; s < kLiftStages; ++s) {
+      mbar_init(&a_full[s], 4);
+      mbar_init(&a_empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], 4);
+    }
     mbar_init_fence();
   }
   if (warp == 0) tmem_alloc(&tmem_base, 2 * kAccCols);
@@ -241,124 +285,145 @@ __global__ void __launch_bounds__(128, lift_ctas_per_sm(kC))
   pdl_wait();  // everything below may touch buffers of the previous kernels
   const uint32_t tmem = tmem_base;
   const int H = gd.H0, W = gd.W0, Hs = gd.Hs, Ws = gd.Ws;
-  const int xt = Ws / 128;
+  const int xt = (Ws + 127) / 128;
   const int ntiles = B * Hs * xt;
-  constexpr uint32_t idesc = idesc_bf16(128, kC, false, false);
-  // drain accumulator `acc` (the MMA tile whose pixel of this thread is (prow, px)):
-  // bias, bfloat16, channel-blocked store
-  auto drain = [&](int acc, int prow, int px, bool pvalid) {
+  // CTA-uniform: the whole tile is padding (no MMA)
+  auto is_pad = [&](const TileWalk& w) { return w.y >= H || w.xi * 128 >= W; };
+
+  if (warp < 4) {
+    // ---------------------------------------------------------- producers
+    // inputs of the next kLiftInStages - 1 tiles in flight: each thread copies and later
+    // reads only its own pixel's channels, so the per-thread commit groups order them
+    constexpr int kCinR = kCin > 0 ? kCin : 16;
+    TileWalk ahead(blockIdx.x, xt, Hs);
+    auto issue = [&](int i) {  // the CTA's i-th tile, at `ahead`
+      const int xx = ahead.xi * 128 + threadIdx.x;
+      const bool ok = ahead.t < ntiles && ahead.y < H && xx < W;
+      const float* src = ok ? in + (((size_t)ahead.b * cin) * H + ahead.y) * W + xx : in;
+      float* dst = in_s + (size_t)(i % kLiftInStages) * (cin * 128) + threadIdx.x;
 #pragma unroll
-    for (int cb = 0; cb < kAccCols / 32; ++cb) {
-      float v[32];
-      const uint32_t ta = tmem + acc * kAccCols + cb * 32 + ((uint32_t)(warp * 32) << 16);
-      if (kC >= 32) tmem_ld32(ta, v);
-      else tmem_ld16(ta, v);
+      for (int c = 0; c < kCinR; ++c)
+        if (c < cin) cp_async4(dst + c * 128, ok ? src + (size_t)c * H * W : in, ok ? 4u : 0u);
+      cp_async_commit();
+      ahead.next();
+    };
+#pragma unroll 1
+    for (int i = 0; i < kLiftInStages - 1; ++i) issue(i);
+    int k = 0, i = 0;
+    for (TileWalk w(blockIdx.x, xt, Hs); w.t < ntiles; w.next(), ++i) {
+      const int y = w.y, x = w.xi * 128 + threadIdx.x;
+      issue(i + kLiftInStages - 1);  // its stage was last read in iteration i - 1
+      cp_async_wait<kLiftInStages - 1>();
+      const float* cur = in_s + (size_t)(i % kLiftInStages) * cin * 128 + threadIdx.x;
+      if (is_pad(w)) {
+        if (x < Ws) {
 #pragma unroll
-      for (int g = 0; g < (kC < 32 ? kC : 32) / 8; ++g) {
-        const int o0 = cb * 32 + g * 8;
-        __align__(16) __nv_bfloat16 o8[8];
-#pragma unroll
-        for (int q = 0; q < 8; q += 2) {
-          const float2 r = __fadd2_rn(make_float2(v[g * 8 + q], v[g * 8 + q + 1]),
-                                      *reinterpret_cast<const float2*>(&b1_s[o0 + q]));
-          o8[q] = __float2bfloat16_rn(pvalid ? r.x : 0.0f);
-          o8[q + 1] = __float2bfloat16_rn(pvalid ? r.y : 0.0f);
+          for (int g = 0; g < kC / 8; ++g) {
+            const size_t at = (((size_t)w.row * (kC / 8) + g) * Ws + x) * 8;
+            *reinterpret_cast<uint4*>(theta + at) = make_uint4(0, 0, 0, 0);
+            if (y >= gd.Hv) *reinterpret_cast<uint4*>(theta_alt + at) = make_uint4(0, 0, 0, 0);
+          }
         }
-        *reinterpret_cast<uint4*>(theta + (((size_t)prow * (kC / 8) + o0 / 8) * Ws + px) * 8) =
-            *reinterpret_cast<const uint4*>(o8);
+        continue;
       }
-    }
-  };
-  int j = 0;  // MMA tiles of this CTA
-  int prev_row = 0, prev_x = 0;
-  bool prev_valid = false, failed = false;  // failed: CTA-uniform (set after __syncthreads_or)
-  // this thread's raw inputs of tile t (loaded one tile ahead, so the loads of the next
-  // tile are in flight while this one is computed)
-  constexpr int kCinR = kCin > 0 ? kCin : 16;
-  auto load_in = [&](int tt, float (&dst)[kCinR]) {
-    const int rw = tt / xt, yy = rw % Hs, bb = rw / Hs, xx = (tt - rw * xt) * 128 + threadIdx.x;
-    const bool ok = tt < ntiles && yy < H && xx < W;
+      // layer 1 for this thread's pixel (inputs and coordinates rounded to bfloat16)
+      const float xc = (float)x / (float)max(W - 1, 1), yc = (float)y / (float)max(H - 1, 1);
+      float xin[kX];  // inputs then the two coordinates, all indices compile-time
 #pragma unroll
-    for (int c = 0; c < kCinR; ++c)
-      dst[c] = (ok && c < cin) ? in[(((size_t)bb * cin + c) * H + yy) * W + xx] : 0.0f;
-  };
-  float raw[kCinR];
-  load_in(blockIdx.x, raw);
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int row = t / xt;  // b * Hs + y
-    const int y = row % Hs, b = row / Hs;
-    const int x0 = (t - row * xt) * 128, x = x0 + threadIdx.x;
-    float cur[kCinR];
-#pragma unroll
-    for (int c = 0; c < kCinR; ++c) cur[c] = raw[c];
-    load_in(t + gridDim.x, raw);
-    if (y >= H || x0 >= W) {  // CTA-uniform: the tile is padding
-#pragma unroll
-      for (int g = 0; g < kC / 8; ++g) {
-        const size_t at = (((size_t)row * (kC / 8) + g) * Ws + x) * 8;
-        *reinterpret_cast<uint4*>(theta + at) = make_uint4(0, 0, 0, 0);
-        if (y >= gd.Hv) *reinterpret_cast<uint4*>(theta_alt + at) = make_uint4(0, 0, 0, 0);
+      for (int c = 0; c < kX; ++c) {
+        const float v = c < kCinR && c < cin ? cur[(c < kCinR ? c : 0) * 128]  // 0 off the grid
+                        : c == cin           ? xc
+                        : c == cin + 1       ? yc
+                                             : 0.0f;
+        xin[c] = __bfloat162float(__float2bfloat16_rn(v));
       }
-      continue;
-    }
-    const bool valid = x < W;
-    // layer 1 for this thread's pixel (inputs and coordinates rounded to bfloat16)
-    float xin[kX];
-#pragma unroll
-    for (int c = 0; c < kCinR; ++c)
-      if (c < cin) xin[c] = __bfloat162float(__float2bfloat16_rn(cur[c]));  // 0 if !valid
-    xin[cin] = __bfloat162float(__float2bfloat16_rn((float)x / (float)max(W - 1, 1)));
-    xin[cin + 1] = __bfloat162float(__float2bfloat16_rn((float)y / (float)max(H - 1, 1)));
-    __align__(16) __nv_bfloat16 h[kHid];
-#pragma unroll
-    for (int jp = 0; jp < kHid / 2; ++jp) {
-      float2 a = *reinterpret_cast<const float2*>(&b0_s[2 * jp]);
-#pragma unroll
-      for (int c = 0; c < kX; ++c)
-        if (c < cin2) a = __ffma2_rn(w0p_s[jp * cin2 + c], make_float2(xin[c], xin[c]), a);
-      const float2 r = act_c2<kAct>(a);
-      h[2 * jp] = __float2bfloat16_rn(r.x);
-      h[2 * jp + 1] = __float2bfloat16_rn(r.y);
-    }
-    unsigned char* as = a_s[j & 1];  // last read by the MMA of tile j - 2, completed
-#pragma unroll
-    for (int g = 0; g < kHid / 8; ++g)
-      *reinterpret_cast<uint4*>(as + g * 2048 + threadIdx.x * 16) =
-          *reinterpret_cast<const uint4*>(&h[g * 8]);
-    fence_proxy_async_smem();
-    tc_fence_before();
-    __syncthreads();  // A complete; accumulator j & 1 (tile j - 2) drained by every thread
-    tc_fence_after();
-    if (threadIdx.x == 0) {
-#pragma unroll
-      for (int kk = 0; kk < kKG / 2; ++kk)
-        mma_bf16(tmem + (j & 1) * kAccCols, smem_desc(as + kk * 4096, 2048, 128),
-                 smem_desc(b_s + kk * 2 * kC * 16, kC * 16, 128), idesc, kk > 0);
-      mma_commit(&mma_bar[j & 1]);
-    }
-    if (j >= 1) {  // drain tile j - 1 while the MMA of tile j runs
-      const int pj = j - 1;
-      const bool ok = mbar_wait_sleep(&mma_bar[pj & 1], (pj >> 1) & 1, status);
-      if (__syncthreads_or(!ok)) {  // the whole CTA leaves together after a timeout
-        failed = true;
+      const int s = k % kLiftStages;
+      if (k >= kLiftStages && !mbar_wait_sleep(&a_empty[s], ((k / kLiftStages) - 1) & 1, status))
         break;
+#pragma unroll
+      for (int g = 0; g < kHid / 8; ++g) {  // eight hidden units at a time into the A stage
+        __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+        for (int jq = 0; jq < 4; ++jq) {
+          const int jp = g * 4 + jq;
+          float2 a = *reinterpret_cast<const float2*>(&b0_s[2 * jp]);
+#pragma unroll
+          for (int c = 0; c < kX; ++c)
+            if (c < cin2) a = __ffma2_rn(w0p_s[jp * cin2 + c], make_float2(xin[c], xin[c]), a);
+          const float2 r = act_c2<kAct>(a);
+          h[2 * jq] = __float2bfloat16_rn(r.x);
+          h[2 * jq + 1] = __float2bfloat16_rn(r.y);
+        }
+        *reinterpret_cast<uint4*>(a_s[s] + g * 2048 + threadIdx.x * 16) =
+            *reinterpret_cast<const uint4*>(h);
       }
-      tc_fence_after();
-      drain(pj & 1, prev_row, prev_x, prev_valid);
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&a_full[s]);
+      ++k;
     }
-    prev_row = row;
-    prev_x = x;
-    prev_valid = valid;
-    ++j;
-  }
-  if (!failed && j >= 1) {  // the last MMA tile
-    const int pj = j - 1;
-    const bool ok = mbar_wait_sleep(&mma_bar[pj & 1], (pj >> 1) & 1, status);
-    if (!__syncthreads_or(!ok)) {
+    cp_async_wait<0>();  // the zero-filled copies issued past the last tile
+  } else if (warp == 4) {
+    // --------------------------------------------------------------- MMA
+    constexpr uint32_t idesc = idesc_bf16(128, kC, false, false);
+    int j = 0;
+    for (TileWalk w(blockIdx.x, xt, Hs); w.t < ntiles; w.next()) {
+      if (is_pad(w)) continue;
+      const int s = j % kLiftStages, acc = j & 1;
+      bool ok = mbar_wait_sleep(&a_full[s], (j / kLiftStages) & 1, status);
+      if (ok && j >= 2) ok = mbar_wait_sleep(&acc_empty[acc], ((j >> 1) - 1) & 1, status);
+      if (!ok) break;
       tc_fence_after();
-      drain(pj & 1, prev_row, prev_x, prev_valid);
+      if (lane == 0) {
+#pragma unroll
+        for (int kk = 0; kk < kKG / 2; ++kk)
+          mma_bf16(tmem + acc * kAccCols, smem_desc(a_s[s] + kk * 4096, 2048, 128),
+                   smem_desc(b_s + kk * 2 * kC * 16, kC * 16, 128), idesc, kk > 0);
+        mma_commit(&a_empty[s]);
+        mma_commit(&acc_full[acc]);
+      }
+      __syncwarp();
+      ++j;
+    }
+  } else {
+    // ----------------------------------------------------------- epilogue
+    const int quad = warp & 3;  // a warp reads TMEM lanes 32 (warp % 4) .. +31: pixels x0 + 32 quad + lane
+    int j = 0;
+    for (TileWalk w(blockIdx.x, xt, Hs); w.t < ntiles; w.next()) {
+      if (is_pad(w)) continue;
+      const int acc = j & 1;
+      if (!mbar_wait_sleep(&acc_full[acc], (j >> 1) & 1, status)) break;
+      tc_fence_after();
+      const int row = w.row;
+      const int x = w.xi * 128 + quad * 32 + lane;
+      const bool valid = x < W, in_storage = x < Ws;
+#pragma unroll
+      for (int cb = 0; cb < kC / 16; ++cb) {
+        float v[16];
+        tmem_ld16(tmem + acc * kAccCols + cb * 16 + ((uint32_t)(quad * 32) << 16), v);
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+          const int o0 = cb * 16 + g * 8;
+          __align__(16) __nv_bfloat16 o8[8];
+#pragma unroll
+          for (int q = 0; q < 8; q += 2) {
+            const float2 r = __fadd2_rn(make_float2(v[g * 8 + q], v[g * 8 + q + 1]),
+                                        *reinterpret_cast<const float2*>(&b1_s[o0 + q]));
+            o8[q] = __float2bfloat16_rn(valid ? r.x : 0.0f);
+            o8[q + 1] = __float2bfloat16_rn(valid ? r.y : 0.0f);
+          }
+          if (in_storage)
+            *reinterpret_cast<uint4*>(theta + (((size_t)row * (kC / 8) + o0 / 8) * Ws + x) * 8) =
+                *reinterpret_cast<const uint4*>(o8);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[acc]);
+      ++j;
     }
   }
+  // all MMAs of this CTA have completed once the epilogue has drained (or timed out)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -587,9 +652,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // D[(kx, c)][(a, re|im)] = X1b[(kx, c)][(y, re|im)] * Fy[(y, re|im)][(a, re|im)]
 // (M = 128 (kx, c) rows of one batch item, N = nf, K = 2H; both operands K-major).
 // The Fy table stays in shared memory; X1b streams through a ring of kYChunk y groups.
-constexpr int kYStages = 4;
+constexpr int kYStagesMax = 8;
 constexpr int kYChunk = 8;                   // y groups of 4 rows per stage
 constexpr int kYStageBytes = kYChunk * 2048;  // [group][row (128)][8]
+constexpr int kYSmemMax = 200 * 1024;
+// As many stages as fit next to the Fy table (a tile's whole K extent is in flight for
+// the workloads' heights, so a CTA's single tile is not paced by stage round trips).
+__host__ __device__ inline int ydft_stages(int Hs, int nf) {
+  const int fy = ((Hs / 4) * nf * 16 + 1023) / 1024 * 1024;
+  const int n = (kYSmemMax - fy) / kYStageBytes;
+  return n < 2 ? 2 : (n > kYStagesMax ? kYStagesMax : n);
+}
 
 template <int kC>
 __global__ void __launch_bounds__(kTcThreads, 1)
@@ -606,7 +679,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* fy_s = smem;
   unsigned char* stages = smem + ((fy_bytes + 1023) & ~1023u);
-  __shared__ __align__(8) uint64_t full_bar[kYStages], empty_bar[kYStages];
+  const int kYStages = ydft_stages(H, d.nf);
+  __shared__ __align__(8) uint64_t full_bar[kYStagesMax], empty_bar[kYStagesMax];
   __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], fy_bar;
   __shared__ uint32_t tmem_base;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -811,8 +885,11 @@ __host__ __device__ inline int iy_stages(int C, int m) {
   return n < kIyStagesMax ? n : kIyStagesMax;
 }
 
+constexpr int kIyEpiWarps = 8;  // two per TMEM lane quadrant, each draining half the columns
+constexpr int kIyThreads = (kIyEpiWarps + 2) * 32;
+
 template <int kC, int kK2>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kIyThreads, 1)
     k_iydft_tc(const __nv_bfloat16* __restrict__ ty, const __nv_bfloat16* __restrict__ yb,
                __nv_bfloat16* __restrict__ zt, int B, int H, int m,
                unsigned* __restrict__ status) {
@@ -839,7 +916,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&acc_full[a], 1);
-      mbar_init(&acc_empty[a], 4);
+      mbar_init(&acc_empty[a], kIyEpiWarps);
     }
     mbar_init_fence();
   }
@@ -850,7 +927,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   pdl_wait();  // everything below may touch buffers of the previous kernels
   const uint32_t tmem = tmem_base;
 
-  if (warp == 4) {
+  if (warp == kIyEpiWarps) {
     // ------------------------------------------------------------ producer
     int k = 0;
     bool ok = true;
@@ -874,7 +951,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     for (int q = max(0, k - kIyStages); q < k; ++q)
       mbar_wait_sleep(&full_bar[q % kIyStages], (q / kIyStages) & 1, status);
-  } else if (warp == 5) {
+  } else if (warp == kIyEpiWarps + 1) {
     // ---------------------------------------------------------------- MMA
     constexpr uint32_t idesc = idesc_bf16(128, kN, false, false);
     int j = 0;
@@ -901,6 +978,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // ----------------------------------------------------------- epilogue
     // 32 accumulator columns = 32 / knk channels o, each with knk consecutive k'
     constexpr int kOpl = 32 / kKnk;
+    const int quad = warp & 3, half = warp >> 2;  // TMEM lanes 32 quad.., column half
     int j = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
       const int acc = j & 1;
@@ -908,13 +986,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       tc_fence_after();
       const int b = t / (yt_n * d.nc), rem = t - b * yt_n * d.nc;
       const int yt = rem / d.nc, ci = rem - yt * d.nc;
-      const int y = yt * 128 + warp * 32 + lane;
+      const int y = yt * 128 + quad * 32 + lane;
       const int kp0 = ci * kKnk;
       __nv_bfloat16* zrow = zt + ((size_t)b * H + y) * kK2 * kC + (kp0 / 8) * kC * 8 + (kp0 % 8);
 #pragma unroll 1
-      for (int cb = 0; cb < kN / 32; ++cb) {
+      for (int cb = half * (kN / 64); cb < (half + 1) * (kN / 64); ++cb) {
         float v[32];
-        tmem_ld32(tmem + acc * kN + cb * 32 + ((uint32_t)(warp * 32) << 16), v);
+        tmem_ld32(tmem + acc * kN + cb * 32 + ((uint32_t)(quad * 32) << 16), v);
         if (y < H) {
 #pragma unroll
           for (int oo = 0; oo < kOpl; ++oo) {
@@ -932,7 +1010,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[acc]);
-      if (ci == d.nc - 1 && y < H) {  // k' in [nc * knk, kK2): zero
+      if (half == 0 && ci == d.nc - 1 && y < H) {  // k' in [nc * knk, kK2): zero
         __nv_bfloat16* zr = zt + ((size_t)b * H + y) * kK2 * kC;
         for (int kp = d.nc * kKnk; kp < kK2; kp += kKnk)
           for (int o = 0; o < kC; ++o) {
@@ -983,7 +1061,7 @@ __global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
   __shared__ __align__(16) float bias_s[kC];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int H = gd.Hv, W = gd.Ws;
-  const int xt = W / 128;
+  const int xt = (W + 127) / 128;
   const int ntiles = B * H * xt;
 
   // the W^T half of every stage's B operand is constant: fill it once
@@ -1073,10 +1151,22 @@ __global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
       if (!mbar_wait_sleep(&acc_full[grp], (j >> 1) & 1, status)) break;
       tc_fence_after();
       const int row = t / xt;
-      const int x = (t - row * xt) * 128 + quad * 32 + lane;
+      const int xw = (t - row * xt) * 128 + quad * 32;  // this warp's first column
+      const int x = xw + lane;
       const int b = row / H;
       const size_t srow = (size_t)b * gd.Hs + (row - b * H);
       const bool valid = x < gd.Wv;
+      if (xw >= gd.Wv) {  // warp-uniform: every column of this warp is storage padding
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[grp]);
+        if (x < W) {
+#pragma unroll
+          for (int g = 0; g < kG; ++g)
+            *reinterpret_cast<uint4*>(out + ((srow * kG + g) * W + x) * 8) = make_uint4(0, 0, 0, 0);
+        }
+        continue;
+      }
 #pragma unroll
       for (int cb = 0; cb < (kC + 31) / 32; ++cb) {
         constexpr int kCols = kC < 32 ? kC : 32;
@@ -1101,8 +1191,9 @@ __global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
             o8[q] = __float2bfloat16_rn(valid ? r.x : 0.0f);
             o8[q + 1] = __float2bfloat16_rn(valid ? r.y : 0.0f);
           }
-          *reinterpret_cast<uint4*>(out + ((srow * kG + o0 / 8) * W + x) * 8) =
-              *reinterpret_cast<const uint4*>(o8);
+          if (x < W)
+            *reinterpret_cast<uint4*>(out + ((srow * kG + o0 / 8) * W + x) * 8) =
+                *reinterpret_cast<const uint4*>(o8);
         }
       }
     }
@@ -1114,10 +1205,10 @@ __global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
 }
 
 // ------------------------------------------ 5. projection Q (tcgen05 + CUDA cores)
-// One hidden layer of width S = C and kOut outputs:  out = Q2 act(Q1 theta + q1) + q2.
-// The C x S contraction runs on the tensor cores (M = 128 x positions of one image
-// row, N = S, K = C; theta and Q1 both K-major, no swizzle); the epilogue adds q1,
-// applies the activation and contracts with Q2 in FP32.  Several CTAs share an SM so
+// One hidden layer of width S (32 or 64) and cout <= 3 outputs:
+// out = Q2 act(Q1 theta + q1) + q2.  The C x S contraction runs on the tensor cores
+// (M = 128 x positions of one image row, N = S, K = C; theta and Q1 both K-major, no
+// swizzle); the epilogue adds q1, applies the activation and contracts with Q2 in FP32.  Several CTAs share an SM so
 // that enough epilogue warps hide the activation's latency.
 constexpr int kDecStages = 4;
 constexpr int kDecCtasPerSm = 2;
@@ -1126,14 +1217,13 @@ constexpr int kDecThreads = (kDecEpiWarps + 2) * 32;
 
 // Tiles: 128 columns of a row of the output grid H0 x W0 (W0 a multiple of 128), read
 // from the latent storage (the padded grid is cropped).
-template <int kC, int kOut, int kAct>
+template <int kC, int kS, int kAct>
 __global__ void __launch_bounds__(kDecThreads, kDecCtasPerSm)
     k_decoder_tc(const __nv_bfloat16* __restrict__ theta, float* __restrict__ out,
                  const float* __restrict__ params, const unsigned* __restrict__ offs, int B,
-                 TcGrid gd, unsigned* __restrict__ status) {
+                 TcGrid gd, int cout, unsigned* __restrict__ status) {
   pdl_trigger();
   const int H = gd.H0, W = gd.W0;
-  constexpr int kS = kC;
   constexpr int kG = kC / 8;
   constexpr int kStageBytes = kG * 128 * 16;  // [channel group][x (128)][8]
   constexpr int kAccCols = kS < 32 ? 32 : kS;
@@ -1143,11 +1233,11 @@ __global__ void __launch_bounds__(kDecThreads, kDecCtasPerSm)
   // per hidden pair (j, j + 1): {q1[j], q1[j+1], Q2[0][j], Q2[0][j+1]},
   //                            {Q2[1][j], Q2[1][j+1], Q2[2][j], Q2[2][j+1]}
   __shared__ __align__(16) float4 ep_s[kS];
-  __shared__ float q2_s[kOut];
+  __shared__ float q2_s[3];
   __shared__ __align__(8) uint64_t full_bar[kDecStages], empty_bar[kDecStages];
   __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_base;
-  static_assert(kOut <= 3, "epilogue packs Q2 rows into a float4 with the hidden bias");
+  // cout <= 3: the epilogue packs Q2 rows into a float4 with the hidden bias
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int xt = W / 128;
   const int ntiles = B * H * xt;
@@ -1162,11 +1252,11 @@ __global__ void __launch_bounds__(kDecThreads, kDecCtasPerSm)
   }
   for (int jp = threadIdx.x; jp < kS / 2; jp += blockDim.x) {
     const int j = 2 * jp;
-    auto q2w = [&](int q, int jj) { return q < kOut ? w2[q * kS + jj] : 0.f; };
+    auto q2w = [&](int q, int jj) { return q < cout ? w2[q * kS + jj] : 0.f; };
     ep_s[2 * jp] = make_float4(b1[j], b1[j + 1], q2w(0, j), q2w(0, j + 1));
     ep_s[2 * jp + 1] = make_float4(q2w(1, j), q2w(1, j + 1), q2w(2, j), q2w(2, j + 1));
   }
-  for (int q = threadIdx.x; q < kOut; q += blockDim.x) q2_s[q] = b2[q];
+  for (int q = threadIdx.x; q < 3; q += blockDim.x) q2_s[q] = q < cout ? b2[q] : 0.f;
   fence_proxy_async_smem();
   if (threadIdx.x == 0) {
     for (int s = 0; s < kDecStages; ++s) {
@@ -1264,12 +1354,13 @@ __global__ void __launch_bounds__(kDecThreads, kDecCtasPerSm)
       }
       float o[3];
 #pragma unroll
-      for (int q = 0; q < 3; ++q) o[q] = (q < kOut ? q2_s[q] : 0.f) + (oq[q].x + oq[q].y);
+      for (int q = 0; q < 3; ++q) o[q] = q2_s[q] + (oq[q].x + oq[q].y);
       const int row = t / xt;
       const int b = row / H, y = row - b * H;
       const int x = (t - row * xt) * 128 + quad * 32 + lane;
 #pragma unroll
-      for (int q = 0; q < kOut; ++q) out[(((size_t)b * kOut + q) * H + y) * W + x] = o[q];
+      for (int q = 0; q < 3; ++q)
+        if (q < cout) out[(((size_t)b * cout + q) * H + y) * W + x] = o[q];
     }
   }
   tc_fence_before();
@@ -1306,14 +1397,15 @@ static TcGrid tc_grid(const fno_config& c, int H, int W) {
   g.Hv = H + c.padding;
   g.Wv = W + c.padding;
   g.Hs = (g.Hv + 7) / 8 * 8;
-  g.Ws = (g.Wv + 127) / 128 * 128;
+  g.Ws = (g.Wv + 63) / 64 * 64;
   return g;
 }
 // Shared memory of the kernels whose footprint depends on the shape.
 static size_t fwd_smem(int Ws, int k2) { return (size_t)Ws * k2 * 2 + (size_t)kFwdStages * kFwdStageBytes; }
 static size_t ydft_smem(int C, int Hs, int m) {
   const SpecDims d = spec_dims(C, m);
-  return align_up((size_t)(Hs / 4) * d.nf * 16, 1024) + (size_t)kYStages * kYStageBytes;
+  return align_up((size_t)(Hs / 4) * d.nf * 16, 1024) +
+         (size_t)ydft_stages(Hs, d.nf) * kYStageBytes;
 }
 static size_t iydft_smem(int C, int m) {
   return std::max((size_t)iy_stages(C, m) * iy_stage_bytes(C, m), (size_t)kIyMinSmem);
@@ -1347,14 +1439,15 @@ FnoTcWs fno_tc_ws_plan(const fno_config& c, int B, int H, int W) {
   };
   const size_t spix = (size_t)B * g.Hs * g.Ws;
   const size_t hp = ((size_t)g.Hv + 127) / 128 * 128;
-  w.theta0 = take(spix * C * 2);
-  w.theta1 = take(spix * C * 2);
+  const size_t tail = 128 * 16;  // a last 128-column tile reads up to 64 columns past the end
+  w.theta0 = take(spix * C * 2 + tail);
+  w.theta1 = take(spix * C * 2 + tail);
   w.x1b = take((size_t)B * g.Hs * m * C * 4);
   w.xh = take((size_t)2 * m * m * B * C * sizeof(float2));
   w.yb = take((size_t)B * d.kg * d.nn * 16);
   w.zt = take((size_t)B * g.Hv * k2 * C * 2);
   w.fw = take((size_t)g.Ws * k2 * 2);
-  w.ti = take((size_t)g.Ws * k2 * 2);
+  w.ti = take((size_t)g.Ws * k2 * 2 + tail);
   w.fy = take((size_t)(g.Hs / 4) * d.nf * 16);
   w.ty = take((size_t)d.kg * hp * 16);
   w.status = take(sizeof(unsigned));
@@ -1389,14 +1482,19 @@ static int fno_forward_tc_impl(const fno_config& c, const FnoTcParams& P, const 
   LBM_CHECK_CUDA(cudaMemsetAsync(yb, 0, (size_t)B * d.kg * d.nn * 16, s));
   const int n_tables = 2 * gd.Ws * kK2 + (gd.Hs / 4) * d.nf * 8 + d.kg * hp * 8;
   LBM_TRY(launch_pdl(k_tables, dim3((n_tables + 255) / 256), dim3(256), 0, s, fw, ti, fy, ty, gd, m, hp, d.nf, d.kg));
-  const size_t spix = (size_t)B * gd.Hs * gd.Ws;
-  const int lift_ctas = (int)std::min<size_t>(spix / 128, (size_t)lift_ctas_per_sm(kC) * nsm);
-  if (c.c_in == 4)
-    LBM_TRY(launch_pdl((k_lift_tc<kC, 4, kAct>), dim3(lift_ctas), dim3(128), 0, s, in, th[0], th[1], P.lift0_w, P.lift0_b,
-                                                     P.lift1_w, P.lift1_b, B, gd, c.c_in, status));
-  else
-    LBM_TRY(launch_pdl((k_lift_tc<kC, 0, kAct>), dim3(lift_ctas), dim3(128), 0, s, in, th[0], th[1], P.lift0_w, P.lift0_b,
-                                                     P.lift1_w, P.lift1_b, B, gd, c.c_in, status));
+  const size_t lift_smem = (size_t)kLiftInStages * c.c_in * 128 * 4;
+  const size_t lift_tiles = (size_t)B * gd.Hs * ((gd.Ws + 127) / 128);
+  auto lift = [&](auto kern, int cin_c) {
+    const int ctas = (int)std::min<size_t>(lift_tiles, (size_t)lift_ctas_per_sm(cin_c, kC) * nsm);
+    return launch_pdl(kern, dim3(ctas), dim3(kLiftThreads), lift_smem, s, in, th[0], th[1],
+                      P.lift0_w, P.lift0_b, P.lift1_w, P.lift1_b, B, gd, c.c_in, status);
+  };
+  switch (c.c_in) {  // the input widths of the paper's models get their own instances
+    case 1: LBM_TRY(lift(k_lift_tc<kC, 1, kAct>, 1)); break;
+    case 2: LBM_TRY(lift(k_lift_tc<kC, 2, kAct>, 2)); break;
+    case 4: LBM_TRY(lift(k_lift_tc<kC, 4, kAct>, 4)); break;
+    default: LBM_TRY(lift(k_lift_tc<kC, 0, kAct>, 0)); break;
+  }
   const size_t f_smem = fwd_smem(gd.Ws, kK2), i_smem = inv_smem(kC, kK2);
   const size_t y_smem = ydft_smem(kC, gd.Hs, m), iy_smem = iydft_smem(kC, m);
   const size_t mix_smem = (size_t)(kC * kC + kMixB * kC) * sizeof(float2);
@@ -1404,7 +1502,7 @@ static int fno_forward_tc_impl(const fno_config& c, const FnoTcParams& P, const 
                   f_smem <= (size_t)kTcSmemMax && i_smem <= (size_t)kTcSmemMax,
               "fno_forward: spectral working set too large for shared memory");
   const int fwd_ctas = std::min(B * (gd.Hs / (128 / kC)), 2 * nsm);
-  const int inv_ctas = std::min(B * gd.Hv * (gd.Ws / 128), inv_ctas_per_sm<kC>() * nsm);
+  const int inv_ctas = std::min(B * gd.Hv * ((gd.Ws + 127) / 128), inv_ctas_per_sm<kC>() * nsm);
   const int ydft_ctas = std::min(B * ((m * kC + 127) / 128), 2 * nsm);
   const int iydft_ctas = std::min(B * (hp / 128) * d.nc, nsm);
   const dim3 mix_grid((unsigned)(2 * m * m), (unsigned)((B + kMixB - 1) / kMixB));
@@ -1414,18 +1512,24 @@ static int fno_forward_tc_impl(const fno_config& c, const FnoTcParams& P, const 
                                                              m, status));
     LBM_TRY(launch_pdl((k_ydft_tc<kC>), dim3(ydft_ctas), dim3(kTcThreads), y_smem, s, x1b, fy, xh, B, gd.Hs, m, status));
     LBM_TRY(launch_pdl((k_mix<kC>), dim3(mix_grid), dim3(256), mix_smem, s, xh, P.rt[n], yb, B, m));
-    LBM_TRY(launch_pdl((k_iydft_tc<kC, kK2>), dim3(iydft_ctas), dim3(kTcThreads), iy_smem, s, ty, yb, zt, B, gd.Hv, m, status));
+    LBM_TRY(launch_pdl((k_iydft_tc<kC, kK2>), dim3(iydft_ctas), dim3(kIyThreads), iy_smem, s, ty, yb, zt, B, gd.Hv, m, status));
     LBM_TRY(launch_pdl((k_inv_x_tc<kC, kAct, kK2>), dim3(inv_ctas), dim3(kInvThreads), i_smem, s, 
         th[cur], ti, zt, P.w[n], P.b[n], th[cur ^ 1], B, gd, status));
     cur ^= 1;
   }
   const size_t pix = (size_t)B * H * W;
-  if (c.dec_layers == 1 && c.dec_size == kC && c.c_out == 3 && W % 128 == 0) {
-    const size_t smem_tc = (size_t)kC * kC * 2 + (size_t)kDecStages * (kC / 8) * 128 * 16;
+  if (c.dec_layers == 1 && (c.dec_size == 32 || c.dec_size == 64) && c.c_out <= 3 &&
+      W % 128 == 0) {
+    const size_t smem_tc =
+        (size_t)kC * c.dec_size * 2 + (size_t)kDecStages * (kC / 8) * 128 * 16;
     const int ntiles = B * H * (W / 128);
     const int ctas = std::min(ntiles, kDecCtasPerSm * nsm);
-    LBM_TRY(launch_pdl((k_decoder_tc<kC, 3, kAct>), dim3(ctas), dim3(kDecThreads), smem_tc, s, th[cur], out, P.params,
-                                                                P.dec_offs, B, gd, status));
+    if (c.dec_size == 32)
+      LBM_TRY(launch_pdl((k_decoder_tc<kC, 32, kAct>), dim3(ctas), dim3(kDecThreads), smem_tc, s,
+                         th[cur], out, P.params, P.dec_offs, B, gd, c.c_out, status));
+    else
+      LBM_TRY(launch_pdl((k_decoder_tc<kC, 64, kAct>), dim3(ctas), dim3(kDecThreads), smem_tc, s,
+                         th[cur], out, P.params, P.dec_offs, B, gd, c.c_out, status));
   } else {
     const size_t dec_smem =
         ((size_t)c.dec_layers * (c.dec_size * 64 + c.dec_size) + c.c_out * 64 + c.c_out) *
@@ -1451,7 +1555,18 @@ static int tc_set_smem_attrs_k2() {
 }
 template <int kC, int kAct>
 static int tc_set_smem_attrs_act() {
-  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_decoder_tc<kC, 3, kAct>,
+  constexpr int lift_in_max = kLiftInStages * 16 * 128 * 4;  // c_in <= 16
+  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_lift_tc<kC, 1, kAct>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, lift_in_max));
+  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_lift_tc<kC, 2, kAct>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, lift_in_max));
+  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_lift_tc<kC, 4, kAct>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, lift_in_max));
+  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_lift_tc<kC, 0, kAct>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, lift_in_max));
+  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_decoder_tc<kC, 32, kAct>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemMax));
+  LBM_CHECK_CUDA(cudaFuncSetAttribute(k_decoder_tc<kC, 64, kAct>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemMax));
   LBM_TRY((tc_set_smem_attrs_k2<kC, kAct, 32>()));
   return tc_set_smem_attrs_k2<kC, kAct, 64>();

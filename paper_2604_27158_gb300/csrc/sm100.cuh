@@ -97,6 +97,21 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+// Asynchronous 4-byte copy global -> shared (cp.async, completion tracked per thread by
+// commit groups); src_bytes = 0 writes a zero without reading `src`.
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, unsigned src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+// Wait until at most N of this thread's committed groups are still pending.
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 // Make generic-proxy shared-memory writes visible to the async proxy (bulk copies,
 // tensor-core operand reads).
 __device__ __forceinline__ void fence_proxy_async_smem() {

@@ -278,6 +278,28 @@ def test_paper_models_with_padding_match_oracle(name, cin, cout, width, layers, 
     assert e < REL_L2_FNO and e_cc < REL_L2_FNO
 
 
+@pytest.mark.parametrize("cin,width,act", [(1, 16, 0), (2, 32, 1), (3, 16, 0), (4, 64, 0),
+                                            (7, 64, 1), (16, 32, 0)])
+def test_lift_input_widths_on_tensor_cores(cin, width, act):
+    """The tensor-core lift has instances for 1, 2 and 4 input channels and one with a
+    runtime input width (up to 16) for the rest: each against the oracle, on grids with a
+    ragged last x tile (W = 150: tiles of 128 and 22 pixels in 192-pixel storage rows)
+    and more tiles than CTAs, with both activations."""
+    _requires_gpu()
+    s, g, params = _pair(c_in=cin, c_out=2, width=width, layers=1, modes=4, dec_size=32,
+                         act=act, seed=cin + width)
+    net = Fno(g, synth.fno_flatten_params(s, params))
+    B, H, W = 6, 200, 150
+    assert net.uses_tensor_cores(H, W)
+    x = _inputs(B, cin, H, W, seed=cin)
+    y = net(torch.from_numpy(x).cuda()).cpu().numpy()
+    net.check(B, H, W)
+    ref = fo.fno_forward(s, params, x, activation="gelu" if act == 0 else "relu")
+    e = rel_l2(y, ref)
+    print(f"lift c_in={cin} C={width} act={act} {B}x{H}x{W}: rel L2 {e:.3e}")
+    assert e < REL_L2_FNO
+
+
 @pytest.mark.parametrize("which", ["density", "velocity"])
 def test_double_shear_model_pair_on_tensor_cores(which):
     """The 2.6 M double-shear model group (Sec. 3.2.1; 14 channels, 3 layers, decoder 32,
