@@ -45,6 +45,7 @@ NX, NY = 512, 256
 TAU, RHO_IN, RHO_OUT = 0.7, 1.001, 1.0
 TOL, CHECK_EVERY = 1e-7, 100
 BYTES_PER_CELL = 72.125  # 9 x 4 B read + 9 x 4 B written + 1 mask bit per cell update
+REINIT_BYTES_PER_CELL = 56  # (rho, u_x, u_y) read; 9 populations + stored (u_x, u_y) written
 
 
 def parse():
@@ -76,10 +77,12 @@ def parse():
                     help="timed steps of the differentiable hybrid training workload (0: skip)")
     ap.add_argument("--step-variant", type=int, default=-1,
                     help="step-kernel tile shape index; -1 (default) times all shapes and keeps the fastest")
-    ap.add_argument("--case", default=None, choices=["lbm", "check", "fno", "shear_fno"],
+    ap.add_argument("--case", default=None,
+                    choices=["lbm", "check", "reinit", "fno", "shear_fno"],
                     help="run one small case to be profiled and exit (no JSON line): 'lbm' 60 "
                          "steps of the bench batch (tile shape 3), 'check' 5 steps + 5 "
-                         "statistics-only residuals + 5 step+statistics checks of it, 'fno' "
+                         "statistics-only residuals + 5 step+statistics checks of it, "
+                         "'reinit' 5 re-initialisations of it from its fields after 20 steps, 'fno' "
                          "8 forwards of the FNO throughput shape, 'shear_fno' 8 forwards of "
                          "the double-shear density and velocity networks on 100 fields")
     return ap.parse_args()
@@ -108,6 +111,16 @@ def run_case(args):
                 lat.residual(update_prev=True)
             for _ in range(5):
                 lat.step_residual(update_prev=True)
+        lat.close()
+    elif args.case == "reinit":
+        T = args.trajectories
+        masks, _ = workload(T, 0)
+        lat = Lattice([GridSpec(NX, NY, TAU, bc_west=P.BC_PRESSURE, bc_east=P.BC_PRESSURE,
+                                west_value=RHO_IN, east_value=RHO_OUT)] * T, masks)
+        lat.step(20)
+        rho, ux, uy = lat.macro()
+        for _ in range(5):
+            lat.reinit(rho, ux, uy, neq_mode=1)
         lat.close()
     elif args.case == "shear_fno":
         ics = synth.double_shear(100, seed=2000)
@@ -475,6 +488,25 @@ def main():
     kms = k0.elapsed_time(k1) / nk
     peak, peak_kind = read_peaks()
     achieved = BYTES_PER_CELL * cells / (kms * 1e-3) / 1e9
+
+    # the re-initialisation kernel (a4) on the same batch, from its macroscopic fields: reads
+    # (rho, u_x, u_y), writes the nine populations and the stored velocity (56 B a cell;
+    # 470 MB a launch at this size, well above the L2)
+    rho_m, ux_m, uy_m = lat.macro()
+    for _ in range(3):
+        lat.reinit(rho_m, ux_m, uy_m, neq_mode=1)
+    nr = 20
+    k0.record(stream)
+    for _ in range(nr):
+        lat.reinit(rho_m, ux_m, uy_m, neq_mode=1)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    rms = k0.elapsed_time(k1) / nr
+    reinit_gbs = REINIT_BYTES_PER_CELL * cells / (rms * 1e-3) / 1e9
+    reinit_kernel = {"kernel": "k_reinit", "neq_mode": 1, "launch_ms": rms,
+                     "bytes_per_launch": REINIT_BYTES_PER_CELL * cells, "achieved_gbs": reinit_gbs,
+                     "frac_of_measured_hbm": reinit_gbs / peak}
+    del rho_m, ux_m, uy_m
 
     tts = None
 
@@ -1021,6 +1053,7 @@ def main():
                                         "ctas_per_sm": shape[3], "autotune_ms": tune_ms},
                          "launch_ms": kms, "traffic": step_kernel_traffic(cells, shape),
                          "traffic_unit": "bytes per launch (ncu dram read + write)"},
+            "reinit_kernel": reinit_kernel,
             "time_to_steady_summary": None if tts is None else {
                 "tol": tts["tol"], "trajectories": tts["trajectories"],
                 "fno_init_s": tts["fno_init"]["seconds"],
