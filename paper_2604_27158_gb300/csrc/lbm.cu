@@ -797,197 +797,6 @@ __global__ void __launch_bounds__(kBlock) k_residual_final(const GridDev* __rest
   block_reduce_store(v, stats + (size_t)blockIdx.x * R_COUNT);
 }
 
-// Re-initialisation: f = f^eq(rho, u) (+ f^neq), laid out *inverse-streamed* in the
-// post-collision buffer so that the next pull reproduces it: the pull of population j at
-// a fluid cell n reads plane j at n - c_j when that cell is fluid, else (halfway bounce-
-// back) plane opp(j) at n itself.  So plane j at a fluid location p holds g_j(p + c_j)
-// when p + c_j is a fluid cell, g_opp(j)(p) when it is a solid cell, and 0 when it lies
-// outside a non-periodic grid (an open-boundary unknown, completed by the next pull);
-// solid locations hold 0.  None of the zeros is ever read by a pull.
-//
-// One CTA per tile of kReinitRows rows x 128 columns.  (0) rho, u and the cell kinds of
-// the tile and a two-cell halo are staged in shared memory, every load of a thread issued
-// before the first is used; (1) the populations of the tile and a one-cell halo are
-// computed from them (derivatives central where both neighbours along an axis are fluid
-// cells of the grid, one-sided where one is, zero otherwise; y periodic, x periodic for
-// periodic grids), and a fluid cell of the tile whose neighbour p + c_j is solid or
-// outside a non-periodic grid puts g_opp(j)(p) or 0 into that neighbour's slot of plane j
-// (read by no one else); (2) every plane of the tile is written as whole rows, a value a
-// thread and column: slot p + c_j of plane j for fluid p, 0 for solid p.
-constexpr int kReinitRows = 6;
-constexpr int kReinitHW = 132;  // one-cell halo row: columns x0 - 1 .. x0 + 128, padded
-constexpr int kReinitSW = 132;  // two-cell halo row: columns x0 - 2 .. x0 + 129
-constexpr int kReinitSY = kReinitRows + 4;
-enum : unsigned char { kRiFluid = 0, kRiSolid = 1, kRiOutside = 2 };
-struct ReinitSmem {
-  float gs[kQ][kReinitRows + 2][kReinitHW];  // populations of the tile and its halo
-  float fs[3][kReinitSY][kReinitSW];         // rho, u_x, u_y of the tile and two halo cells
-  unsigned char ks[kReinitSY][kReinitSW];    // cell kinds of the same cells
-};
-
-// One-axis difference of a staged field: central, one-sided or zero as dfield, without
-// branches (the values of cells that are not selected may be anything).
-__device__ __forceinline__ float dsel(bool okp, bool okm, float vp, float vc, float vm) {
-  const float central = 0.5f * (vp - vm), fwd = vp - vc, bwd = vc - vm;
-  return okp ? (okm ? central : fwd) : (okm ? bwd : 0.0f);
-}
-
-// f^eq + f^neq of staged cell (hy, hx) into gs[.][hy][hx]; for a cell of the tile (kOwn)
-// also the bounce-back / open-boundary values into the slots of its solid or outside
-// neighbours.  Opposite directions share the even part (c_a c_b is even in c); lattice
-// constants are folded into per-pair expressions.  Branch-free: every cell is evaluated,
-// and a store that must not happen (a non-fluid cell's own slots, a fluid neighbour's
-// slot) goes to the unread padding column kReinitHW - 1 of its row instead.  The kinds of
-// the eight neighbours and the neighbours' velocities are loaded once.
-template <bool kOwn>
-__device__ __forceinline__ void reinit_cell(ReinitSmem& S, int hy, int hx, int neq_mode,
-                                            float kneq_tau) {
-  constexpr int kPad = kReinitHW - 1;
-  const int sy = hy + 1, sx = hx + 1;
-  unsigned char kn[kQ];  // kind of the neighbour p + c_i (kn[0]: the cell itself)
-#pragma unroll
-  for (int i = 0; i < kQ; ++i) kn[i] = S.ks[sy + cy_of(i)][sx + cx_of(i)];
-  const bool fluid = kn[0] == kRiFluid;
-  const int hxw = fluid ? hx : kPad;
-  const float rho = S.fs[0][sy][sx], ux = S.fs[1][sy][sx], uy = S.fs[2][sy][sx];
-  const float drho = rho - 1.0f;
-  float dxux = 0.f, dxuy = 0.f, dyux = 0.f, dyuy = 0.f;
-  if (neq_mode) {
-    const bool xp = kn[1] == kRiFluid, xm = kn[3] == kRiFluid;
-    const bool yp = kn[2] == kRiFluid, ym = kn[4] == kRiFluid;
-    dxux = dsel(xp, xm, S.fs[1][sy][sx + 1], ux, S.fs[1][sy][sx - 1]);
-    dxuy = dsel(xp, xm, S.fs[2][sy][sx + 1], uy, S.fs[2][sy][sx - 1]);
-    dyux = dsel(yp, ym, S.fs[1][sy + 1][sx], ux, S.fs[1][sy - 1][sx]);
-    dyuy = dsel(yp, ym, S.fs[2][sy + 1][sx], uy, S.fs[2][sy - 1][sx]);
-  }
-  const float usq = 1.5f * fmaf(ux, ux, uy * uy);
-  const float div3 = (1.0f / 3.0f) * (dxux + dyuy);
-  const float kneq = kneq_tau * rho;  // -(tau rho / c_s^2)
-  const float shear = dxuy + dyux;
-  // Q_iab d_a u_b = c_ia c_ib d_a u_b - c_s^2 div u, per direction pair
-  S.gs[0][hy][hxw] = kW0 * fmaf(kneq, -div3, fmaf(-rho, usq, drho));
-  auto pair = [&](int i, float w, float cu, float qd) {
-    const float even = w * fmaf(kneq, qd, fmaf(rho, fmaf(4.5f * cu, cu, -usq), drho));
-    const float odd = (3.0f * w) * (rho * cu);
-    const float gi = even + odd, go = even - odd;
-    const int io = opp_of(i);
-    S.gs[i][hy][hxw] = gi;
-    S.gs[io][hy][hxw] = go;
-    if (kOwn) {  // plane i at the neighbour p + c_i, plane opp(i) at p - c_i
-      const int cx = cx_of(i), cy = cy_of(i);
-      const bool bp = fluid && kn[i] != kRiFluid, bm = fluid && kn[io] != kRiFluid;
-      S.gs[i][bp ? hy + cy : hy][bp ? hx + cx : kPad] = kn[i] == kRiSolid ? go : 0.0f;
-      S.gs[io][bm ? hy - cy : hy][bm ? hx - cx : kPad] = kn[io] == kRiSolid ? gi : 0.0f;
-    }
-  };
-  pair(1, kW1, ux, dxux - div3);                        // c = (1, 0)
-  pair(2, kW1, uy, dyuy - div3);                        // c = (0, 1)
-  pair(5, kW2, ux + uy, (dxux + dyuy) + shear - div3);  // c = (1, 1)
-  pair(6, kW2, uy - ux, (dxux + dyuy) - shear - div3);  // c = (-1, 1)
-}
-
-__global__ void __launch_bounds__(kBlock) k_reinit(const GridDev* __restrict__ grids,
-                                                   const int4* __restrict__ tiles,
-                                                   const uint32_t* __restrict__ mask,
-                                                   const float* __restrict__ rho_i,
-                                                   const float* __restrict__ ux_i,
-                                                   const float* __restrict__ uy_i, int neq_mode,
-                                                   float* __restrict__ state,
-                                                   float* __restrict__ ux_prev,
-                                                   float* __restrict__ uy_prev) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  ReinitSmem& S = *reinterpret_cast<ReinitSmem*>(smem_raw);
-  const int4 tile = __ldg(&tiles[blockIdx.x]);  // (grid, x0, y0, rows)
-  const GridDev G = grids[tile.x];              // registers: stores below cannot alias it
-  const int x0 = tile.y, y0 = tile.z, rows = tile.w;
-  const uint32_t* m = mask + G.mask_off;
-  const float* F[3] = {rho_i + G.cell_off, ux_i + G.cell_off, uy_i + G.cell_off};
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // 0. stage rows y0 - 2 .. y0 + rows + 1 (wrapped in y) and columns x0 - 2 .. x0 + 129
-  //    (wrapped in x for periodic grids, outside otherwise): a warp a row
-  constexpr int kSlotsY = (kReinitSY + kBlock / 32 - 1) / (kBlock / 32);
-  constexpr int kSlotsX = (kReinitSW + 31) / 32;
-  float fv[kSlotsY][kSlotsX][3];
-  uint32_t mw[kSlotsY][kSlotsX];
-  int gxs[kSlotsX];
-#pragma unroll
-  for (int q = 0; q < kSlotsX; ++q) {  // column of slot q, -1 when outside the grid
-    int gx = x0 - 2 + lane + 32 * q;
-    if (G.periodic_x && (gx < 0 || gx >= G.nx)) gx = (gx % G.nx + G.nx) % G.nx;
-    gxs[q] = (gx >= 0 && gx < G.nx && lane + 32 * q < kReinitSW) ? gx : -1;
-  }
-#pragma unroll
-  for (int r = 0; r < kSlotsY; ++r) {
-    const int sy = warp + r * (kBlock / 32);
-    int gy = y0 - 2 + sy;
-    if (gy < 0 || gy >= G.ny) gy = (gy % G.ny + G.ny) % G.ny;
-    const uint32_t* mrow = m + (long long)gy * G.wpr;
-    const long long crow = (long long)gy * G.nx;
-#pragma unroll
-    for (int q = 0; q < kSlotsX; ++q) {
-      if (sy < rows + 4 && gxs[q] >= 0) {
-        mw[r][q] = __ldg(&mrow[gxs[q] >> 5]);
-#pragma unroll
-        for (int f = 0; f < 3; ++f) fv[r][q][f] = __ldg(&F[f][crow + gxs[q]]);
-      }
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < kSlotsY; ++r) {
-    const int sy = warp + r * (kBlock / 32);
-#pragma unroll
-    for (int q = 0; q < kSlotsX; ++q) {
-      const int sx = lane + 32 * q;
-      if (sy < rows + 4 && sx < kReinitSW) {
-        unsigned char k = kRiOutside;
-        if (gxs[q] >= 0) {
-          k = (mw[r][q] >> (gxs[q] & 31)) & 1u ? kRiSolid : kRiFluid;
-#pragma unroll
-          for (int f = 0; f < 3; ++f) S.fs[f][sy][sx] = fv[r][q][f];
-        }
-        S.ks[sy][sx] = k;
-      }
-    }
-  }
-  __syncthreads();
-  // 1. populations of the columns x0 .. x0 + 127 of rows y0 - 1 .. y0 + rows (cell e:
-  //    row e / 128, so whether a warp's cells belong to the tile is warp-uniform) and of
-  //    the halo columns x0 - 1, x0 + 128; the tile's cells also put their neighbours'
-  //    bounce-back slots (slots of non-fluid cells, which compute nothing: no two writers
-  //    share a slot) and store the current velocity (0 at solid cells) for the next check
-  const float kneq_tau = -3.0f * G.tau;
-  for (int e = threadIdx.x; e < (rows + 2) * 128; e += kBlock) {
-    const int hy = e >> 7, hx = 1 + (e & 127);
-    if (hy >= 1 && hy <= rows) {
-      const int gx = x0 + hx - 1;
-      if (gx < G.nx) {
-        const bool fluid = S.ks[hy + 1][hx + 1] == kRiFluid;
-        const long long at = G.f_off + (long long)(y0 + hy - 1) * G.pitch + gx;
-        ux_prev[at] = fluid ? S.fs[1][hy + 1][hx + 1] : 0.0f;
-        uy_prev[at] = fluid ? S.fs[2][hy + 1][hx + 1] : 0.0f;
-      }
-      reinit_cell<true>(S, hy, hx, neq_mode, kneq_tau);
-    } else {
-      reinit_cell<false>(S, hy, hx, neq_mode, kneq_tau);
-    }
-  }
-  if (warp == kBlock / 32 - 1 && lane < 2 * (rows + 2))  // halo columns x0 - 1, x0 + 128
-    reinit_cell<false>(S, lane >> 1, (lane & 1) ? 129 : 0, neq_mode, kneq_tau);
-  __syncthreads();
-  // 2. the tile's planes: a warp a (row, 32 columns), a lane a column, all nine planes:
-  //    slot p + c_j of plane j for fluid p, 0 for solid p
-  const int ncols = min(128, G.nx - x0);
-  for (int u = warp; u < rows * 4; u += kBlock / 32) {
-    const int r = u >> 2, c = (u & 3) * 32 + lane;
-    if (c >= ncols) continue;
-    const bool fluid = S.ks[r + 2][c + 2] == kRiFluid;
-    float* dst = state + G.f_off + (long long)(y0 + r) * G.pitch + x0 + c;
-#pragma unroll
-    for (int j = 0; j < kQ; ++j)
-      dst[(long long)j * G.plane] = fluid ? S.gs[j][r + 1 + cy_of(j)][c + 1 + cx_of(j)] : 0.0f;
-  }
-}
-
 // Vorticity omega = d_x u_y - d_y u_x of dense velocity fields (the accuracy metric of
 // the unsteady results, Sec. 3.2.2), with the re-initialisation's difference stencils;
 // solid cells get 0.
@@ -1324,9 +1133,7 @@ int lbm_init(const lbm_grid* grids_h, int ngrids, const uint32_t* mask_d, float*
                                                            sv.smem_of(m)) == cudaSuccess;
       h->blocks_per_sm_v[v] = h->blocks_per_sm_vm[v][kModeStep];
     }
-    if (ok)
-      ok = cudaFuncSetAttribute(k_reinit, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sizeof(ReinitSmem)) == cudaSuccess;
+    if (ok) ok = reinit_init(h) == LBM_OK;
     if (!ok) {
       set_error("lbm_init: %s", cudaGetErrorString(cudaGetLastError()));
       delete h;
@@ -1439,12 +1246,7 @@ int lbm_reinit_from_macro(lbm_handle* h, const float* rho_d, const float* ux_d,
   LBM_REQUIRE(v < LBM_STEP_VARIANTS, "lbm_reinit_from_macro: no tile table of %d rows",
               kReinitRows);
   h->steps = 0;
-  if (h->ntiles_v[v] == 0) return LBM_OK;
-  k_reinit<<<h->ntiles_v[v], kBlock, sizeof(ReinitSmem), S(stream)>>>(
-      h->gd_d, h->tiles_d[v], h->mask, rho_d, ux_d, uy_d, neq_mode, h->f[h->cur], h->ux_prev,
-      h->uy_prev);
-  LBM_CHECK_LAUNCH();
-  return LBM_OK;
+  return reinit_launch(h, h->tiles_d[v], h->ntiles_v[v], rho_d, ux_d, uy_d, neq_mode, S(stream));
 }
 
 int lbm_vorticity(lbm_handle* h, const float* ux_d, const float* uy_d, float* omega_d,

@@ -42,6 +42,13 @@ struct Handle {
 // current buffer is NOT switched: the caller either keeps the state (nothing to do) or
 // accepts the step with accept_step().  Synchronises `s`.
 int residual_step(Handle* h, double* out_h, int update_prev, cudaStream_t s);
+
+// f = f^eq(rho, u) (+ f^neq) of every grid into the current buffer (reinit.cu), one CTA
+// a tile of the step-kernel tile table with kReinitRows rows a tile.
+constexpr int kReinitRows = 6;
+int reinit_init(Handle* h);  // sets the kernel's shared-memory limit (once per handle)
+int reinit_launch(Handle* h, const int4* tiles, int ntiles, const float* rho_d,
+                  const float* ux_d, const float* uy_d, int neq_mode, cudaStream_t s);
 inline void accept_step(Handle* h) {
   h->cur ^= 1;
   h->steps += 1;
