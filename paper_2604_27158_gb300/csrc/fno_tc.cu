@@ -867,6 +867,80 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// The same mixing for C <= 32, one block per (group of four modes a = 4 g .. 4 g + 3 with
+// the same kx, batch chunk): the four modes share one 16-byte entry of Yb
+// ([b][a/4][n][(a%4) * 2 + p]), so a thread writes whole entries (one store where the
+// per-mode kernel makes four 4-byte ones).  Modes a >= 2m of the last group get 0.  The
+// batch chunk bc (<= kMixB) is chosen so that the grid covers the multiprocessors.
+template <int kC>
+__global__ void __launch_bounds__(256)
+    k_mix4(const float2* __restrict__ xh, const float2* __restrict__ rt,
+           __nv_bfloat16* __restrict__ yb, int B, int m, int bc) {
+  static_assert(kC <= 32, "shared memory");
+  pdl_trigger();
+  pdl_wait();
+  const SpecDims d = spec_dims(kC, m);
+  extern __shared__ float2 mix_s[];
+  float2* r_s = mix_s;                  // [q][c][o]
+  float2* x_s = mix_s + 4 * kC * kC;    // [q][b][c]
+  const int ag = blockIdx.x / m, kx = blockIdx.x - ag * m;  // modes a = 4 ag + q
+  const int b0 = blockIdx.y * bc, nb = min(bc, B - b0);  // batch chunk bc <= kMixB
+  {  // all of this thread's loads in flight before the first shared-memory store
+    constexpr int kR = (4 * kC * kC + 255) / 256, kXn = (4 * kMixB * kC + 255) / 256;
+    float2 rv[kR], xv[kXn];
+#pragma unroll
+    for (int u = 0; u < kR; ++u) {
+      const int t = threadIdx.x + u * 256;
+      const int q = t / (kC * kC), e = t - q * (kC * kC), a = 4 * ag + q;
+      rv[u] = (t < 4 * kC * kC && a < 2 * m) ? rt[((size_t)a * m + kx) * kC * kC + e]
+                                             : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < kXn; ++u) {
+      const int t = threadIdx.x + u * 256;
+      const int q = t / (kMixB * kC), e = t - q * (kMixB * kC), a = 4 * ag + q;
+      xv[u] = (t < 4 * kMixB * kC && e < nb * kC && a < 2 * m)
+                  ? xh[(((size_t)a * m + kx) * B + b0) * kC + e]
+                  : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < kR; ++u)
+      if (threadIdx.x + u * 256 < 4 * kC * kC) r_s[threadIdx.x + u * 256] = rv[u];
+#pragma unroll
+    for (int u = 0; u < kXn; ++u)
+      if (threadIdx.x + u * 256 < 4 * kMixB * kC) x_s[threadIdx.x + u * 256] = xv[u];
+  }
+  __syncthreads();
+  const int n_re = (kx / d.knk) * d.nchunk + kx % d.knk;            // ncol(kx, 0)
+  const int n_im = ((m + kx) / d.knk) * d.nchunk + (m + kx) % d.knk;  // ncol(m + kx, 0)
+  // thread: channel o of batch items bl = tid / C, + 256 / C, ...; four modes each
+  for (int e = threadIdx.x; e < nb * kC; e += 256) {
+    const int bl = e / kC, o = e - bl * kC;
+    float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+    for (int i = 0; i < kC; ++i) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 w = r_s[(q * kC + i) * kC + o];
+        const float2 xv = x_s[(q * kMixB + bl) * kC + i];
+        re[q] = fmaf(xv.x, w.x, fmaf(-xv.y, w.y, re[q]));
+        im[q] = fmaf(xv.x, w.y, fmaf(xv.y, w.x, im[q]));
+      }
+    }
+    // entry (b, ag, n): (a%4) * 2 + p; real part of the inverse (Re Y, -Im Y) at
+    // n = ncol(kx, o), imaginary part (Im Y, Re Y) at n = ncol(m + kx, o)
+    __align__(16) __nv_bfloat162 lo[4], hi[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      lo[q] = __floats2bfloat162_rn(re[q], -im[q]);
+      hi[q] = __floats2bfloat162_rn(im[q], re[q]);
+    }
+    uint4* base = reinterpret_cast<uint4*>(yb) + ((size_t)(b0 + bl) * d.kg + ag) * d.nn;
+    base[n_re + o * d.knk] = *reinterpret_cast<const uint4*>(lo);
+    base[n_im + o * d.knk] = *reinterpret_cast<const uint4*>(hi);
+  }
+}
+
 // ---------------------------------------------- 3b. inverse y-DFT (tcgen05)
 // Zt[b][y][k'/8][o][k'%8] (bf16, kK2 slots k') = D[y][n(k', o)] = Ty[y][(a, re|im)] *
 // Yb[(a, re|im)][n]: k' < m gives Re Z(kx = k'), m <= k' < 2m gives Im Z(kx = k' - m)
@@ -876,6 +950,7 @@ __global__ void __launch_bounds__(256)
 constexpr int kIyStagesMax = 4;
 constexpr int kIyMinSmem = 120 * 1024;  // one CTA per SM: the accumulators fill the TMEM
 constexpr int kTcSmemMax = 200 * 1024;
+constexpr int kTcSmemSm = 228 * 1024;  // shared memory of one multiprocessor
 __host__ __device__ inline int iy_stage_bytes(int C, int m) {
   const SpecDims d = spec_dims(C, m);
   return d.kg * 2048 + d.kg * d.nchunk * 16;
@@ -1029,62 +1104,74 @@ __global__ void __launch_bounds__(kIyThreads, 1)
 }
 
 // ------------------------ 4. inverse x-DFT + W theta + bias + activation (tcgen05)
-constexpr int kInvStages = 3;
+constexpr int kInvMaxStages = 8;
 // CTAs per SM: three for C <= 32 (their epilogue warps hide the activation's latency),
 // two for C = 64 (shared memory)
 template <int kC>
 constexpr int inv_ctas_per_sm() { return kC <= 32 ? 3 : 2; }
 constexpr int kInvEpiWarps = 8;  // two groups of four: each drains alternate tiles
+constexpr int kInvAccs = 2;      // TMEM accumulators, one a warp group
 constexpr int kInvThreads = (kInvEpiWarps + 2) * 32;
+// Shared memory: a resident part (the CTA's 128-column slice of the inverse-DFT table
+// and W^T) and `stages` stages of (latent tile, Zt row), each 1024-byte aligned.
+__host__ __device__ constexpr size_t inv_res_bytes(int C, int k2) {
+  return (size_t)(k2 / 8) * 2048 + ((size_t)(C / 8) * C * 16 + 1023) / 1024 * 1024;
+}
+__host__ __device__ constexpr size_t inv_stage_bytes(int C, int k2) {
+  return (size_t)(C / 8) * 2048 + (size_t)(k2 / 8) * C * 16;
+}
 
 // Tiles: the layers' grid rows y < Hv, 128 storage columns each; columns x >= Wv (the
 // storage padding) are written as 0.  Zt rows are indexed on the Hv grid, latent rows on
-// the Hs storage.
+// the Hs storage.  The grid is a multiple of the tiles a row, so that a CTA's tiles all
+// have the same 128 columns and their table slice stays in shared memory.
 template <int kC, int kAct, int kK2>
 __global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
     k_inv_x_tc(const __nv_bfloat16* __restrict__ theta, const __nv_bfloat16* __restrict__ ti,
                const __nv_bfloat16* __restrict__ zt, const float* __restrict__ wmat,
                const float* __restrict__ bias, __nv_bfloat16* __restrict__ out, int B, TcGrid gd,
-               unsigned* __restrict__ status) {
+               int stages, unsigned* __restrict__ status) {
   pdl_trigger();
   constexpr int kG = kC / 8;
-  constexpr int kSG = kK2 / 8;                // spectral K groups (k' < kK2)
-  constexpr int kKG = kSG + kG;               // K groups of 8: spectral + C channels
-  constexpr int kABytes = kKG * 128 * 16;     // A: [k group][x (128)][8]
-  constexpr int kBBytes = kKG * kC * 16;      // B: [k group][o (C)][8]
-  constexpr int kStageBytes = kABytes + kBBytes;
+  constexpr int kSG = kK2 / 8;  // spectral K groups (k' < kK2)
+  constexpr int kThetaBytes = kG * 128 * 16;  // A, channel part: [group][x (128)][8]
+  constexpr size_t kResBytes = inv_res_bytes(kC, kK2);
+  constexpr size_t kStageBytes = inv_stage_bytes(kC, kK2);
+  static_assert(kStageBytes % 1024 == 0, "stage alignment");
   constexpr int kAccCols = kC < 32 ? 32 : kC;
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t full_bar[kInvStages], empty_bar[kInvStages];
-  __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
+  unsigned char* ti_s = smem;                      // A, spectral part: [group][x][8]
+  unsigned char* w_s = smem + kSG * 2048;          // B, channel part: W^T as [group][o][8]
+  unsigned char* stage0 = smem + kResBytes;        // stage s: latent tile, then Zt row
+  __shared__ __align__(8) uint64_t full_bar[kInvMaxStages], empty_bar[kInvMaxStages];
+  __shared__ __align__(8) uint64_t acc_full[kInvAccs], acc_empty[kInvAccs], res_bar;
   __shared__ uint32_t tmem_base;
   __shared__ __align__(16) float bias_s[kC];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int H = gd.Hv, W = gd.Ws;
   const int xt = (W + 127) / 128;
   const int ntiles = B * H * xt;
+  const int x0 = (blockIdx.x % xt) * 128;  // this CTA's columns (gridDim.x % xt == 0)
 
-  // the W^T half of every stage's B operand is constant: fill it once
-  for (int e = threadIdx.x; e < kInvStages * kG * kC * 8; e += blockDim.x) {
-    const int s = e / (kG * kC * 8), q = e - s * (kG * kC * 8);
-    const int g = q / (kC * 8), o = (q / 8) % kC, il = q % 8;
-    __nv_bfloat16* bq = reinterpret_cast<__nv_bfloat16*>(smem + (size_t)s * kStageBytes + kABytes);
-    bq[(kSG + g) * kC * 8 + o * 8 + il] = __float2bfloat16_rn(wmat[o * kC + g * 8 + il]);
+  for (int e = threadIdx.x; e < kG * kC * 8; e += blockDim.x) {  // W^T, once
+    const int g = e / (kC * 8), o = (e / 8) % kC, il = e % 8;
+    reinterpret_cast<__nv_bfloat16*>(w_s)[e] = __float2bfloat16_rn(wmat[o * kC + g * 8 + il]);
   }
   for (int o = threadIdx.x; o < kC; o += blockDim.x) bias_s[o] = bias[o];
   fence_proxy_async_smem();
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kInvStages; ++s) {
+    for (int s = 0; s < stages; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
-    for (int a = 0; a < 2; ++a) {
+    for (int a = 0; a < kInvAccs; ++a) {
       mbar_init(&acc_full[a], 1);
       mbar_init(&acc_empty[a], kInvEpiWarps / 2);
     }
+    mbar_init(&res_bar, 1);
     mbar_init_fence();
   }
-  if (warp == 0) tmem_alloc(&tmem_base, 2 * kAccCols);
+  if (warp == 0) tmem_alloc(&tmem_base, kInvAccs * kAccCols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -1093,51 +1180,58 @@ __global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
 
   if (warp == kInvEpiWarps) {
     // ------------------------------------------------------------ producer
+    if (lane == 0) mbar_arrive_expect_tx(&res_bar, (unsigned)(kSG * 2048));
+    __syncwarp();
+    if (lane < kSG)  // the table slice of this CTA's columns, group = lane
+      bulk_g2s(ti_s + lane * 2048, ti + ((size_t)lane * W + x0) * 8, 2048, &res_bar);
     int k = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
-      const int s = k % kInvStages;
-      if (k >= kInvStages) ok = mbar_wait_sleep(&empty_bar[s], ((k / kInvStages) - 1) & 1, status);
+      const int s = k % stages;
+      if (k >= stages) ok = mbar_wait_sleep(&empty_bar[s], ((k / stages) - 1) & 1, status);
       if (!ok) break;
       const int row = t / xt;  // b * Hv + y
-      const int x0 = (t - row * xt) * 128;
       const int b = row / H, y = row - b * H;
       const size_t srow = (size_t)b * gd.Hs + y;  // latent storage row
-      unsigned char* st = smem + (size_t)s * kStageBytes;
-      if (lane == 0)
-        mbar_arrive_expect_tx(&full_bar[s], (unsigned)(kKG * 128 * 16 + kSG * kC * 16));
+      unsigned char* st = stage0 + (size_t)s * kStageBytes;
+      if (lane == 0) mbar_arrive_expect_tx(&full_bar[s], (unsigned)kStageBytes);
       __syncwarp();
-      if (lane < kSG) {  // inverse-DFT table, k group = lane
-        bulk_g2s(st + lane * 2048, ti + ((size_t)lane * W + x0) * 8, 2048, &full_bar[s]);
-      } else if (lane < kSG + kG) {  // latent channels, group lane - kSG
-        const int g = lane - kSG;
-        bulk_g2s(st + lane * 2048, theta + ((srow * kG + g) * W + x0) * 8, 2048, &full_bar[s]);
-      } else if (lane == kSG + kG) {  // spectral half of B: Zt row
-        bulk_g2s(st + kABytes, zt + (size_t)row * kK2 * kC, kSG * kC * 16, &full_bar[s]);
+      if (lane < kG) {  // latent channels, group = lane
+        bulk_g2s(st + lane * 2048, theta + ((srow * kG + lane) * W + x0) * 8, 2048, &full_bar[s]);
+      } else if (lane == kG) {  // spectral half of B: Zt row
+        bulk_g2s(st + kThetaBytes, zt + (size_t)row * kK2 * kC, kSG * kC * 16, &full_bar[s]);
       }
     }
-    for (int q = max(0, k - kInvStages); q < k; ++q)
-      mbar_wait_sleep(&full_bar[q % kInvStages], (q / kInvStages) & 1, status);
+    for (int q = max(0, k - stages); q < k; ++q)
+      mbar_wait_sleep(&full_bar[q % stages], (q / stages) & 1, status);
+    mbar_wait_sleep(&res_bar, 0, status);
   } else if (warp == kInvEpiWarps + 1) {
     // ---------------------------------------------------------------- MMA
     constexpr uint32_t idesc = idesc_bf16(128, kC, false, false);
     int j = 0;
-    bool ok = true;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
-      const int acc = j & 1;
-      if (j >= 2) ok = mbar_wait_sleep(&acc_empty[acc], ((j >> 1) - 1) & 1, status);
-      if (ok) ok = mbar_wait_sleep(&full_bar[j % kInvStages], (j / kInvStages) & 1, status);
+    bool ok = mbar_wait_sleep(&res_bar, 0, status);  // the table slice
+    for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++j) {
+      const int acc = j % kInvAccs;
+      if (j >= kInvAccs) ok = mbar_wait_sleep(&acc_empty[acc], ((j / kInvAccs) - 1) & 1, status);
+      if (ok) ok = mbar_wait_sleep(&full_bar[j % stages], (j / stages) & 1, status);
       if (!ok) break;
       tc_fence_after();
       if (lane == 0) {
-        const unsigned char* st = smem + (size_t)(j % kInvStages) * kStageBytes;
+        const unsigned char* st = stage0 + (size_t)(j % stages) * kStageBytes;
+        // K = [spectral k' (table slice x Zt row) | channels (latent tile x W^T)]
 #pragma unroll
-        for (int kk = 0; kk < kKG / 2; ++kk) {
-          const uint64_t ad = smem_desc(st + kk * 2 * 2048, 2048, 128);
-          const uint64_t bd = smem_desc(st + kABytes + kk * 2 * kC * 16, kC * 16, 128);
+        for (int kk = 0; kk < kSG / 2; ++kk) {
+          const uint64_t ad = smem_desc(ti_s + kk * 2 * 2048, 2048, 128);
+          const uint64_t bd = smem_desc(st + kThetaBytes + kk * 2 * kC * 16, kC * 16, 128);
           mma_bf16(tmem + acc * kAccCols, ad, bd, idesc, kk > 0);
         }
-        mma_commit(&empty_bar[j % kInvStages]);
+#pragma unroll
+        for (int kk = 0; kk < kG / 2; ++kk) {
+          const uint64_t ad = smem_desc(st + kk * 2 * 2048, 2048, 128);
+          const uint64_t bd = smem_desc(w_s + kk * 2 * kC * 16, kC * 16, 128);
+          mma_bf16(tmem + acc * kAccCols, ad, bd, idesc, true);
+        }
+        mma_commit(&empty_bar[j % stages]);
         mma_commit(&acc_full[acc]);
       }
       __syncwarp();
@@ -1148,7 +1242,8 @@ __global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
     // tiles whose accumulator is w / 4 (the two warp groups take alternate tiles)
     const int quad = warp & 3, grp = warp >> 2;
     for (int t = blockIdx.x + grp * gridDim.x, j = grp; t < ntiles; t += 2 * gridDim.x, j += 2) {
-      if (!mbar_wait_sleep(&acc_full[grp], (j >> 1) & 1, status)) break;
+      const int acc = j % kInvAccs;
+      if (!mbar_wait_sleep(&acc_full[acc], (j / kInvAccs) & 1, status)) break;
       tc_fence_after();
       const int row = t / xt;
       const int xw = (t - row * xt) * 128 + quad * 32;  // this warp's first column
@@ -1159,7 +1254,7 @@ __global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
       if (xw >= gd.Wv) {  // warp-uniform: every column of this warp is storage padding
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&acc_empty[grp]);
+        if (lane == 0) mbar_arrive(&acc_empty[acc]);
         if (x < W) {
 #pragma unroll
           for (int g = 0; g < kG; ++g)
@@ -1171,13 +1266,13 @@ __global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
       for (int cb = 0; cb < (kC + 31) / 32; ++cb) {
         constexpr int kCols = kC < 32 ? kC : 32;
         float v[32];
-        const uint32_t ta = tmem + grp * kAccCols + cb * 32 + ((uint32_t)(quad * 32) << 16);
+        const uint32_t ta = tmem + acc * kAccCols + cb * 32 + ((uint32_t)(quad * 32) << 16);
         if (kCols == 32) tmem_ld32(ta, v);
         else tmem_ld16(ta, v);
         if (cb == (kC + 31) / 32 - 1) {
           tc_fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive(&acc_empty[grp]);
+          if (lane == 0) mbar_arrive(&acc_empty[acc]);
         }
 #pragma unroll
         for (int g = 0; g < kCols / 8; ++g) {
@@ -1201,7 +1296,7 @@ __global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, 2 * kAccCols);
+  if (warp == 0) tmem_dealloc(tmem, kInvAccs * kAccCols);
 }
 
 // ------------------------------------------ 5. projection Q (tcgen05 + CUDA cores)
@@ -1410,9 +1505,16 @@ static size_t ydft_smem(int C, int Hs, int m) {
 static size_t iydft_smem(int C, int m) {
   return std::max((size_t)iy_stages(C, m) * iy_stage_bytes(C, m), (size_t)kIyMinSmem);
 }
+// Stages of the inverse x-DFT kernel: as many as fit the CTAs a multiprocessor holds
+// (inv_ctas_per_sm), at most kInvMaxStages.
+static int inv_stages(int C, int k2) {
+  const size_t per_cta = (size_t)kTcSmemSm / (C <= 32 ? 3 : 2) - 2048;  // static + reserved
+  const size_t res = inv_res_bytes(C, k2), st = inv_stage_bytes(C, k2);
+  if (per_cta <= res) return 0;
+  return (int)std::min<size_t>(kInvMaxStages, (per_cta - res) / st);
+}
 static size_t inv_smem(int C, int k2) {
-  const int kkg = k2 / 8 + C / 8;
-  return (size_t)kInvStages * ((size_t)kkg * 128 * 16 + (size_t)kkg * C * 16);
+  return inv_res_bytes(C, k2) + (size_t)std::max(inv_stages(C, k2), 2) * inv_stage_bytes(C, k2);
 }
 
 bool fno_tc_supported(const fno_config& c, int H, int W) {
@@ -1423,7 +1525,7 @@ bool fno_tc_supported(const fno_config& c, int H, int W) {
     return false;
   const int k2 = tc_k2(m);
   return fwd_smem(g.Ws, k2) <= (size_t)kTcSmemMax && ydft_smem(C, g.Hs, m) <= (size_t)kTcSmemMax &&
-         iy_stages(C, m) >= 2 && inv_smem(C, k2) <= (size_t)kTcSmemMax;
+         iy_stages(C, m) >= 2 && inv_stages(C, k2) >= 2 && inv_smem(C, k2) <= (size_t)kTcSmemMax;
 }
 
 FnoTcWs fno_tc_ws_plan(const fno_config& c, int B, int H, int W) {
@@ -1502,19 +1604,32 @@ static int fno_forward_tc_impl(const fno_config& c, const FnoTcParams& P, const 
                   f_smem <= (size_t)kTcSmemMax && i_smem <= (size_t)kTcSmemMax,
               "fno_forward: spectral working set too large for shared memory");
   const int fwd_ctas = std::min(B * (gd.Hs / (128 / kC)), 2 * nsm);
-  const int inv_ctas = std::min(B * gd.Hv * ((gd.Ws + 127) / 128), inv_ctas_per_sm<kC>() * nsm);
+  const int inv_xt = (gd.Ws + 127) / 128;  // a CTA keeps one column slice: grid % inv_xt == 0
+  const int inv_ctas = std::max(
+      inv_xt, std::min(B * gd.Hv * inv_xt, inv_ctas_per_sm<kC>() * nsm) / inv_xt * inv_xt);
+  const int inv_st = inv_stages(kC, kK2);
   const int ydft_ctas = std::min(B * ((m * kC + 127) / 128), 2 * nsm);
   const int iydft_ctas = std::min(B * (hp / 128) * d.nc, nsm);
   const dim3 mix_grid((unsigned)(2 * m * m), (unsigned)((B + kMixB - 1) / kMixB));
+  int mix4_bc = kMixB;  // batch chunk: halved while the grid would not cover the SMs twice
+  while (mix4_bc > 4 && (2 * m + 3) / 4 * m * ((B + mix4_bc - 1) / mix4_bc) < 2 * nsm)
+    mix4_bc /= 2;
+  const dim3 mix4_grid((unsigned)((2 * m + 3) / 4 * m), (unsigned)((B + mix4_bc - 1) / mix4_bc));
+  const size_t mix4_smem = (size_t)4 * (kC * kC + kMixB * kC) * sizeof(float2);
   int cur = 0;
   for (int n = 0; n < c.layers; ++n) {
     LBM_TRY(launch_pdl((k_fwd_x_tc<kC, kK2>), dim3(fwd_ctas), dim3(kTcThreads), f_smem, s, th[cur], fw, x1b, B, gd.Hs, gd.Ws,
                                                              m, status));
     LBM_TRY(launch_pdl((k_ydft_tc<kC>), dim3(ydft_ctas), dim3(kTcThreads), y_smem, s, x1b, fy, xh, B, gd.Hs, m, status));
-    LBM_TRY(launch_pdl((k_mix<kC>), dim3(mix_grid), dim3(256), mix_smem, s, xh, P.rt[n], yb, B, m));
+    if constexpr (kC <= 32)  // a block per group of four modes
+      LBM_TRY(launch_pdl((k_mix4<kC>), dim3(mix4_grid), dim3(256), mix4_smem, s, xh, P.rt[n], yb,
+                         B, m, mix4_bc));
+    else
+      LBM_TRY(launch_pdl((k_mix<kC>), dim3(mix_grid), dim3(256), mix_smem, s, xh, P.rt[n], yb, B,
+                         m));
     LBM_TRY(launch_pdl((k_iydft_tc<kC, kK2>), dim3(iydft_ctas), dim3(kIyThreads), iy_smem, s, ty, yb, zt, B, gd.Hv, m, status));
     LBM_TRY(launch_pdl((k_inv_x_tc<kC, kAct, kK2>), dim3(inv_ctas), dim3(kInvThreads), i_smem, s, 
-        th[cur], ti, zt, P.w[n], P.b[n], th[cur ^ 1], B, gd, status));
+        th[cur], ti, zt, P.w[n], P.b[n], th[cur ^ 1], B, gd, inv_st, status));
     cur ^= 1;
   }
   const size_t pix = (size_t)B * H * W;
@@ -1575,6 +1690,9 @@ template <int kC>
 static int tc_set_smem_attrs() {
   LBM_CHECK_CUDA(cudaFuncSetAttribute(k_ydft_tc<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemMax));
   LBM_CHECK_CUDA(cudaFuncSetAttribute(k_mix<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemMax));
+  if constexpr (kC <= 32)
+    LBM_CHECK_CUDA(cudaFuncSetAttribute(k_mix4<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        kTcSmemMax));
   LBM_CHECK_CUDA(cudaFuncSetAttribute(k_decoder_blk<kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemMax));
   LBM_TRY((tc_set_smem_attrs_act<kC, FNO_ACT_GELU>()));
   return tc_set_smem_attrs_act<kC, FNO_ACT_RELU>();
