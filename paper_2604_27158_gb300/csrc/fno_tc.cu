@@ -229,6 +229,9 @@ constexpr int kLiftThreads = 9 * 32;  // warps 0-3 producer, 4 MMA, 5-8 epilogue
 // three CTAs per SM; two for width 64 with a runtime input width (the producers then hold
 // 16 input channels and their prefetch, which would spill at three)
 constexpr int lift_ctas_per_sm(int cin, int C) { return cin > 0 || C < 64 ? 3 : 2; }
+// Grid rows a tile: two for C = 16 (the second row fills the other 16 columns of the
+// 32-column accumulator, halving the tiles' fixed costs), else one.
+__host__ __device__ constexpr int lift_rows(int C) { return C == 16 ? 2 : 1; }
 template <int kC, int kCin, int kAct>
 __global__ void __launch_bounds__(kLiftThreads, lift_ctas_per_sm(kCin, kC))
     k_lift_tc(const float* __restrict__ in, __nv_bfloat16* __restrict__ theta,
@@ -242,16 +245,18 @@ __global__ void __launch_bounds__(kLiftThreads, lift_ctas_per_sm(kCin, kC))
   constexpr int kKG = kK / 8;
   constexpr int kX = kCin > 0 ? kCin + 2 : 18;  // inputs and the two coordinates
   constexpr int kAccCols = kC < 32 ? 32 : kC;
+  constexpr int kR = lift_rows(kC);  // grid rows a tile
+  static_assert(kR * kC <= kAccCols, "rows fit the accumulator");
   const int cin = kCin > 0 ? kCin : cin_rt;
   const int cin2 = cin + 2;
-  __shared__ __align__(1024) unsigned char a_s[kLiftStages][kKG * 2048];  // [k group][x][8]
+  __shared__ __align__(1024) unsigned char a_s[kLiftStages][kR][kKG * 2048];  // [k group][x][8]
   __shared__ __align__(1024) unsigned char b_s[kKG * kC * 16];  // W1^T: [k group][o][8]
   __shared__ float2 w0p_s[(kHid / 2) * 18];  // (w0[j][c], w0[j+1][c]) for hidden pairs
   __shared__ __align__(16) float b0_s[kHid], b1_s[kC];
   __shared__ __align__(8) uint64_t a_full[kLiftStages], a_empty[kLiftStages];
   __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_base;
-  extern __shared__ __align__(16) float in_s[];  // [kLiftInStages][cin][128 pixels]
+  extern __shared__ __align__(16) float in_s[];  // [kLiftInStages][kR rows][cin][128 pixels]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int e = threadIdx.x; e < kKG * kC * 8; e += blockDim.x) {
     const int g = e / (kC * 8), o = (e / 8) % kC, il = e % 8, j = g * 8 + il;
@@ -264,8 +269,9 @@ __global__ void __launch_bounds__(kLiftThreads, lift_ctas_per_sm(kCin, kC))
   for (int j = threadIdx.x; j < kHid; j += blockDim.x) b0_s[j] = b0[j];
   for (int o = threadIdx.x; o < kC; o += blockDim.x) b1_s[o] = b1[o];
   if (kHid < kK)  // padded hidden units stay zero
-    for (int e = threadIdx.x; e < kLiftStages * 128 * 8; e += blockDim.x)
-      reinterpret_cast<__nv_bfloat16*>(a_s[e / 1024] + 2048)[e % 1024] = __float2bfloat16_rn(0.f);
+    for (int e = threadIdx.x; e < kLiftStages * kR * 128 * 8; e += blockDim.x)
+      reinterpret_cast<__nv_bfloat16*>(&a_s[0][0][0] + (size_t)(e / 1024) * kKG * 2048 +
+                                       2048)[e % 1024] = __float2bfloat16_rn(0.f);
   fence_proxy_async_smem();
   if (threadIdx.x == 0) {
     for (int s = 0; s < kLiftStages; ++s) {
@@ -286,46 +292,61 @@ __global__ void __launch_bounds__(kLiftThreads, lift_ctas_per_sm(kCin, kC))
   const uint32_t tmem = tmem_base;
   const int H = gd.H0, W = gd.W0, Hs = gd.Hs, Ws = gd.Ws;
   const int xt = (Ws + 127) / 128;
-  const int ntiles = B * Hs * xt;
-  // CTA-uniform: the whole tile is padding (no MMA)
-  auto is_pad = [&](const TileWalk& w) { return w.y >= H || w.xi * 128 >= W; };
+  const int Hp = Hs / kR;  // row groups an image (Hs is a multiple of 8)
+  const int ntiles = B * Hp * xt;
+  // CTA-uniform: the whole tile is padding (no MMA); TileWalk rows are row groups
+  auto is_pad = [&](const TileWalk& w) { return w.y * kR >= H || w.xi * 128 >= W; };
 
   if (warp < 4) {
     // ---------------------------------------------------------- producers
     // inputs of the next kLiftInStages - 1 tiles in flight: each thread copies and later
     // reads only its own pixel's channels, so the per-thread commit groups order them
     constexpr int kCinR = kCin > 0 ? kCin : 16;
-    TileWalk ahead(blockIdx.x, xt, Hs);
+    TileWalk ahead(blockIdx.x, xt, Hp);
     auto issue = [&](int i) {  // the CTA's i-th tile, at `ahead`
       const int xx = ahead.xi * 128 + threadIdx.x;
-      const bool ok = ahead.t < ntiles && ahead.y < H && xx < W;
-      const float* src = ok ? in + (((size_t)ahead.b * cin) * H + ahead.y) * W + xx : in;
-      float* dst = in_s + (size_t)(i % kLiftInStages) * (cin * 128) + threadIdx.x;
 #pragma unroll
-      for (int c = 0; c < kCinR; ++c)
-        if (c < cin) cp_async4(dst + c * 128, ok ? src + (size_t)c * H * W : in, ok ? 4u : 0u);
+      for (int r = 0; r < kR; ++r) {
+        const int yy = ahead.y * kR + r;
+        const bool ok = ahead.t < ntiles && yy < H && xx < W;
+        const float* src = ok ? in + (((size_t)ahead.b * cin) * H + yy) * W + xx : in;
+        float* dst = in_s + ((size_t)(i % kLiftInStages) * kR + r) * (cin * 128) + threadIdx.x;
+#pragma unroll
+        for (int c = 0; c < kCinR; ++c)
+          if (c < cin) cp_async4(dst + c * 128, ok ? src + (size_t)c * H * W : in, ok ? 4u : 0u);
+      }
       cp_async_commit();
       ahead.next();
     };
 #pragma unroll 1
     for (int i = 0; i < kLiftInStages - 1; ++i) issue(i);
     int k = 0, i = 0;
-    for (TileWalk w(blockIdx.x, xt, Hs); w.t < ntiles; w.next(), ++i) {
-      const int y = w.y, x = w.xi * 128 + threadIdx.x;
+    for (TileWalk w(blockIdx.x, xt, Hp); w.t < ntiles; w.next(), ++i) {
+      const int y0 = w.y * kR, x = w.xi * 128 + threadIdx.x;
       issue(i + kLiftInStages - 1);  // its stage was last read in iteration i - 1
       cp_async_wait<kLiftInStages - 1>();
-      const float* cur = in_s + (size_t)(i % kLiftInStages) * cin * 128 + threadIdx.x;
       if (is_pad(w)) {
         if (x < Ws) {
 #pragma unroll
-          for (int g = 0; g < kC / 8; ++g) {
-            const size_t at = (((size_t)w.row * (kC / 8) + g) * Ws + x) * 8;
-            *reinterpret_cast<uint4*>(theta + at) = make_uint4(0, 0, 0, 0);
-            if (y >= gd.Hv) *reinterpret_cast<uint4*>(theta_alt + at) = make_uint4(0, 0, 0, 0);
-          }
+          for (int r = 0; r < kR; ++r)
+#pragma unroll
+            for (int g = 0; g < kC / 8; ++g) {
+              const size_t at = (((size_t)(w.row * kR + r) * (kC / 8) + g) * Ws + x) * 8;
+              *reinterpret_cast<uint4*>(theta + at) = make_uint4(0, 0, 0, 0);
+              if (y0 + r >= gd.Hv)
+                *reinterpret_cast<uint4*>(theta_alt + at) = make_uint4(0, 0, 0, 0);
+            }
         }
         continue;
       }
+      const int s = k % kLiftStages;
+      if (k >= kLiftStages && !mbar_wait_sleep(&a_empty[s], ((k / kLiftStages) - 1) & 1, status))
+        break;
+#pragma unroll 1
+      for (int r = 0; r < kR; ++r) {
+      const int y = y0 + r;
+      const float* cur =
+          in_s + ((size_t)(i % kLiftInStages) * kR + r) * cin * 128 + threadIdx.x;
       // layer 1 for this thread's pixel (inputs and coordinates rounded to bfloat16)
       const float xc = (float)x / (float)max(W - 1, 1), yc = (float)y / (float)max(H - 1, 1);
       float xin[kX];  // inputs then the two coordinates, all indices compile-time
@@ -337,9 +358,6 @@ __global__ void __launch_bounds__(kLiftThreads, lift_ctas_per_sm(kCin, kC))
                                              : 0.0f;
         xin[c] = __bfloat162float(__float2bfloat16_rn(v));
       }
-      const int s = k % kLiftStages;
-      if (k >= kLiftStages && !mbar_wait_sleep(&a_empty[s], ((k / kLiftStages) - 1) & 1, status))
-        break;
 #pragma unroll
       for (int g = 0; g < kHid / 8; ++g) {  // eight hidden units at a time into the A stage
         __align__(16) __nv_bfloat16 h[8];
@@ -354,9 +372,10 @@ __global__ void __launch_bounds__(kLiftThreads, lift_ctas_per_sm(kCin, kC))
           h[2 * jq] = __float2bfloat16_rn(r.x);
           h[2 * jq + 1] = __float2bfloat16_rn(r.y);
         }
-        *reinterpret_cast<uint4*>(a_s[s] + g * 2048 + threadIdx.x * 16) =
+        *reinterpret_cast<uint4*>(a_s[s][r] + g * 2048 + threadIdx.x * 16) =
             *reinterpret_cast<const uint4*>(h);
       }
+      }  // rows of the tile
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(&a_full[s]);
@@ -367,7 +386,7 @@ __global__ void __launch_bounds__(kLiftThreads, lift_ctas_per_sm(kCin, kC))
     // --------------------------------------------------------------- MMA
     constexpr uint32_t idesc = idesc_bf16(128, kC, false, false);
     int j = 0;
-    for (TileWalk w(blockIdx.x, xt, Hs); w.t < ntiles; w.next()) {
+    for (TileWalk w(blockIdx.x, xt, Hp); w.t < ntiles; w.next()) {
       if (is_pad(w)) continue;
       const int s = j % kLiftStages, acc = j & 1;
       bool ok = mbar_wait_sleep(&a_full[s], (j / kLiftStages) & 1, status);
@@ -376,9 +395,11 @@ __global__ void __launch_bounds__(kLiftThreads, lift_ctas_per_sm(kCin, kC))
       tc_fence_after();
       if (lane == 0) {
 #pragma unroll
-        for (int kk = 0; kk < kKG / 2; ++kk)
-          mma_bf16(tmem + acc * kAccCols, smem_desc(a_s[s] + kk * 4096, 2048, 128),
-                   smem_desc(b_s + kk * 2 * kC * 16, kC * 16, 128), idesc, kk > 0);
+        for (int r = 0; r < kR; ++r)  // row r into accumulator columns r C ..
+#pragma unroll
+          for (int kk = 0; kk < kKG / 2; ++kk)
+            mma_bf16(tmem + acc * kAccCols + r * kC, smem_desc(a_s[s][r] + kk * 4096, 2048, 128),
+                     smem_desc(b_s + kk * 2 * kC * 16, kC * 16, 128), idesc, kk > 0);
         mma_commit(&a_empty[s]);
         mma_commit(&acc_full[acc]);
       }
@@ -389,18 +410,26 @@ __global__ void __launch_bounds__(kLiftThreads, lift_ctas_per_sm(kCin, kC))
     // ----------------------------------------------------------- epilogue
     const int quad = warp & 3;  // a warp reads TMEM lanes 32 (warp % 4) .. +31: pixels x0 + 32 quad + lane
     int j = 0;
-    for (TileWalk w(blockIdx.x, xt, Hs); w.t < ntiles; w.next()) {
+    for (TileWalk w(blockIdx.x, xt, Hp); w.t < ntiles; w.next()) {
       if (is_pad(w)) continue;
       const int acc = j & 1;
       if (!mbar_wait_sleep(&acc_full[acc], (j >> 1) & 1, status)) break;
       tc_fence_after();
-      const int row = w.row;
       const int x = w.xi * 128 + quad * 32 + lane;
-      const bool valid = x < W, in_storage = x < Ws;
+#pragma unroll
+      for (int r = 0; r < kR; ++r) {
+      // a row past the input grid (the second row of a tile) is zero padding
+      const int row = w.row * kR + r, y = w.y * kR + r;
+      const bool valid = x < W && y < H, in_storage = x < Ws;
+      if (y >= gd.Hv && in_storage)
+#pragma unroll
+        for (int g = 0; g < kC / 8; ++g)
+          *reinterpret_cast<uint4*>(theta_alt + (((size_t)row * (kC / 8) + g) * Ws + x) * 8) =
+              make_uint4(0, 0, 0, 0);
 #pragma unroll
       for (int cb = 0; cb < kC / 16; ++cb) {
         float v[16];
-        tmem_ld16(tmem + acc * kAccCols + cb * 16 + ((uint32_t)(quad * 32) << 16), v);
+        tmem_ld16(tmem + acc * kAccCols + r * kC + cb * 16 + ((uint32_t)(quad * 32) << 16), v);
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
           const int o0 = cb * 16 + g * 8;
@@ -417,6 +446,7 @@ __global__ void __launch_bounds__(kLiftThreads, lift_ctas_per_sm(kCin, kC))
                 *reinterpret_cast<const uint4*>(o8);
         }
       }
+      }  // rows of the tile
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[acc]);
@@ -1117,12 +1147,15 @@ constexpr int kInvThreads = (kInvEpiWarps + 2) * 32;
 __host__ __device__ constexpr size_t inv_res_bytes(int C, int k2) {
   return (size_t)(k2 / 8) * 2048 + ((size_t)(C / 8) * C * 16 + 1023) / 1024 * 1024;
 }
+// Grid rows a tile: four for C = 16 (each row's MMA fills 16 columns of a 64-column
+// accumulator, spreading the tiles' fixed costs), else one.
+__host__ __device__ constexpr int inv_rows(int C) { return C == 16 ? 4 : 1; }
 __host__ __device__ constexpr size_t inv_stage_bytes(int C, int k2) {
-  return (size_t)(C / 8) * 2048 + (size_t)(k2 / 8) * C * 16;
+  return (size_t)inv_rows(C) * ((size_t)(C / 8) * 2048 + (size_t)(k2 / 8) * C * 16);
 }
 
-// Tiles: the layers' grid rows y < Hv, 128 storage columns each; columns x >= Wv (the
-// storage padding) are written as 0.  Zt rows are indexed on the Hv grid, latent rows on
+// Tiles: inv_rows(C) consecutive rows (b, y < Hv) of the layers' grid, 128 storage columns
+// each; columns x >= Wv (the storage padding) are written as 0.  Zt rows are indexed on the Hv grid, latent rows on
 // the Hs storage.  The grid is a multiple of the tiles a row, so that a CTA's tiles all
 // have the same 128 columns and their table slice stays in shared memory.
 template <int kC, int kAct, int kK2>
@@ -1137,12 +1170,14 @@ __global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
   constexpr int kThetaBytes = kG * 128 * 16;  // A, channel part: [group][x (128)][8]
   constexpr size_t kResBytes = inv_res_bytes(kC, kK2);
   constexpr size_t kStageBytes = inv_stage_bytes(kC, kK2);
+  constexpr int kR = inv_rows(kC);                              // grid rows a tile
+  constexpr int kPartBytes = kThetaBytes + kSG * kC * 16;      // one row's part of a stage
   static_assert(kStageBytes % 1024 == 0, "stage alignment");
-  constexpr int kAccCols = kC < 32 ? 32 : kC;
+  constexpr int kAccCols = kR * kC < 32 ? 32 : kR * kC;  // the rows' columns side by side
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* ti_s = smem;                      // A, spectral part: [group][x][8]
   unsigned char* w_s = smem + kSG * 2048;          // B, channel part: W^T as [group][o][8]
-  unsigned char* stage0 = smem + kResBytes;        // stage s: latent tile, then Zt row
+  unsigned char* stage0 = smem + kResBytes;        // stage s, part r: latent tile, Zt row
   __shared__ __align__(8) uint64_t full_bar[kInvMaxStages], empty_bar[kInvMaxStages];
   __shared__ __align__(8) uint64_t acc_full[kInvAccs], acc_empty[kInvAccs], res_bar;
   __shared__ uint32_t tmem_base;
@@ -1150,7 +1185,8 @@ __global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int H = gd.Hv, W = gd.Ws;
   const int xt = (W + 127) / 128;
-  const int ntiles = B * H * xt;
+  const int nrows = B * H;
+  const int ntiles = (nrows + kR - 1) / kR * xt;
   const int x0 = (blockIdx.x % xt) * 128;  // this CTA's columns (gridDim.x % xt == 0)
 
   for (int e = threadIdx.x; e < kG * kC * 8; e += blockDim.x) {  // W^T, once
@@ -1190,16 +1226,20 @@ __global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
       const int s = k % stages;
       if (k >= stages) ok = mbar_wait_sleep(&empty_bar[s], ((k / stages) - 1) & 1, status);
       if (!ok) break;
-      const int row = t / xt;  // b * Hv + y
-      const int b = row / H, y = row - b * H;
-      const size_t srow = (size_t)b * gd.Hs + y;  // latent storage row
+      const int row0 = t / xt * kR;  // first row b * Hv + y of the tile
+      const int nr = min(kR, nrows - row0);
       unsigned char* st = stage0 + (size_t)s * kStageBytes;
-      if (lane == 0) mbar_arrive_expect_tx(&full_bar[s], (unsigned)kStageBytes);
+      if (lane == 0) mbar_arrive_expect_tx(&full_bar[s], (unsigned)(nr * kPartBytes));
       __syncwarp();
-      if (lane < kG) {  // latent channels, group = lane
-        bulk_g2s(st + lane * 2048, theta + ((srow * kG + lane) * W + x0) * 8, 2048, &full_bar[s]);
-      } else if (lane == kG) {  // spectral half of B: Zt row
-        bulk_g2s(st + kThetaBytes, zt + (size_t)row * kK2 * kC, kSG * kC * 16, &full_bar[s]);
+      if (lane < nr * (kG + 1)) {  // row r = lane / (kG + 1): kG latent groups, Zt row
+        const int r = lane / (kG + 1), q = lane - r * (kG + 1), row = row0 + r;
+        const int b = row / H, y = row - b * H;
+        const size_t srow = (size_t)b * gd.Hs + y;  // latent storage row
+        unsigned char* part = st + r * kPartBytes;
+        if (q < kG)
+          bulk_g2s(part + q * 2048, theta + ((srow * kG + q) * W + x0) * 8, 2048, &full_bar[s]);
+        else
+          bulk_g2s(part + kThetaBytes, zt + (size_t)row * kK2 * kC, kSG * kC * 16, &full_bar[s]);
       }
     }
     for (int q = max(0, k - stages); q < k; ++q)
@@ -1217,19 +1257,24 @@ __global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
       if (!ok) break;
       tc_fence_after();
       if (lane == 0) {
-        const unsigned char* st = stage0 + (size_t)(j % stages) * kStageBytes;
-        // K = [spectral k' (table slice x Zt row) | channels (latent tile x W^T)]
+        const int nr = min(kR, nrows - t / xt * kR);
+        // per row r, into accumulator columns r C ..: K = [spectral k' (table slice x Zt
+        // row) | channels (latent tile x W^T)]
+        for (int r = 0; r < nr; ++r) {
+          const unsigned char* part = stage0 + (size_t)(j % stages) * kStageBytes + r * kPartBytes;
+          const uint32_t d = tmem + acc * kAccCols + r * kC;
 #pragma unroll
-        for (int kk = 0; kk < kSG / 2; ++kk) {
-          const uint64_t ad = smem_desc(ti_s + kk * 2 * 2048, 2048, 128);
-          const uint64_t bd = smem_desc(st + kThetaBytes + kk * 2 * kC * 16, kC * 16, 128);
-          mma_bf16(tmem + acc * kAccCols, ad, bd, idesc, kk > 0);
-        }
+          for (int kk = 0; kk < kSG / 2; ++kk) {
+            const uint64_t ad = smem_desc(ti_s + kk * 2 * 2048, 2048, 128);
+            const uint64_t bd = smem_desc(part + kThetaBytes + kk * 2 * kC * 16, kC * 16, 128);
+            mma_bf16(d, ad, bd, idesc, kk > 0);
+          }
 #pragma unroll
-        for (int kk = 0; kk < kG / 2; ++kk) {
-          const uint64_t ad = smem_desc(st + kk * 2 * 2048, 2048, 128);
-          const uint64_t bd = smem_desc(w_s + kk * 2 * kC * 16, kC * 16, 128);
-          mma_bf16(tmem + acc * kAccCols, ad, bd, idesc, true);
+          for (int kk = 0; kk < kG / 2; ++kk) {
+            const uint64_t ad = smem_desc(part + kk * 2 * 2048, 2048, 128);
+            const uint64_t bd = smem_desc(w_s + kk * 2 * kC * 16, kC * 16, 128);
+            mma_bf16(d, ad, bd, idesc, true);
+          }
         }
         mma_commit(&empty_bar[j % stages]);
         mma_commit(&acc_full[acc]);
@@ -1245,50 +1290,60 @@ __global__ void __launch_bounds__(kInvThreads, inv_ctas_per_sm<kC>())
       const int acc = j % kInvAccs;
       if (!mbar_wait_sleep(&acc_full[acc], (j / kInvAccs) & 1, status)) break;
       tc_fence_after();
-      const int row = t / xt;
-      const int xw = (t - row * xt) * 128 + quad * 32;  // this warp's first column
+      const int rp = t / xt, row0 = rp * kR, nr = min(kR, nrows - row0);
+      const int xw = (t - rp * xt) * 128 + quad * 32;  // this warp's first column
       const int x = xw + lane;
-      const int b = row / H;
-      const size_t srow = (size_t)b * gd.Hs + (row - b * H);
       const bool valid = x < gd.Wv;
+      auto srow_of = [&](int r) {  // latent storage row of the tile's row r
+        const int row = row0 + r, b = row / H;
+        return (size_t)b * gd.Hs + (row - b * H);
+      };
       if (xw >= gd.Wv) {  // warp-uniform: every column of this warp is storage padding
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&acc_empty[acc]);
         if (x < W) {
+          for (int r = 0; r < nr; ++r) {
+            const size_t srow = srow_of(r);
 #pragma unroll
-          for (int g = 0; g < kG; ++g)
-            *reinterpret_cast<uint4*>(out + ((srow * kG + g) * W + x) * 8) = make_uint4(0, 0, 0, 0);
+            for (int g = 0; g < kG; ++g)
+              *reinterpret_cast<uint4*>(out + ((srow * kG + g) * W + x) * 8) =
+                  make_uint4(0, 0, 0, 0);
+          }
         }
         continue;
       }
+      for (int r = 0; r < nr; ++r) {
+        const size_t srow = srow_of(r);
 #pragma unroll
-      for (int cb = 0; cb < (kC + 31) / 32; ++cb) {
-        constexpr int kCols = kC < 32 ? kC : 32;
-        float v[32];
-        const uint32_t ta = tmem + acc * kAccCols + cb * 32 + ((uint32_t)(quad * 32) << 16);
-        if (kCols == 32) tmem_ld32(ta, v);
-        else tmem_ld16(ta, v);
-        if (cb == (kC + 31) / 32 - 1) {
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&acc_empty[acc]);
-        }
-#pragma unroll
-        for (int g = 0; g < kCols / 8; ++g) {
-          const int o0 = cb * 32 + g * 8;
-          __align__(16) __nv_bfloat16 o8[8];
-#pragma unroll
-          for (int q = 0; q < 8; q += 2) {
-            const float2 r = act_c2<kAct>(
-                __fadd2_rn(make_float2(v[g * 8 + q], v[g * 8 + q + 1]),
-                           *reinterpret_cast<const float2*>(&bias_s[o0 + q])));
-            o8[q] = __float2bfloat16_rn(valid ? r.x : 0.0f);
-            o8[q + 1] = __float2bfloat16_rn(valid ? r.y : 0.0f);
+        for (int cb = 0; cb < (kC + 31) / 32; ++cb) {
+          constexpr int kCols = kC < 32 ? kC : 32;
+          float v[32];
+          const uint32_t ta =
+              tmem + acc * kAccCols + r * kC + cb * 32 + ((uint32_t)(quad * 32) << 16);
+          if (kCols == 32) tmem_ld32(ta, v);
+          else tmem_ld16(ta, v);
+          if (r == nr - 1 && cb == (kC + 31) / 32 - 1) {  // the accumulator is free
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[acc]);
           }
-          if (x < W)
-            *reinterpret_cast<uint4*>(out + ((srow * kG + o0 / 8) * W + x) * 8) =
-                *reinterpret_cast<const uint4*>(o8);
+#pragma unroll
+          for (int g = 0; g < kCols / 8; ++g) {
+            const int o0 = cb * 32 + g * 8;
+            __align__(16) __nv_bfloat16 o8[8];
+#pragma unroll
+            for (int q = 0; q < 8; q += 2) {
+              const float2 rr = act_c2<kAct>(
+                  __fadd2_rn(make_float2(v[g * 8 + q], v[g * 8 + q + 1]),
+                             *reinterpret_cast<const float2*>(&bias_s[o0 + q])));
+              o8[q] = __float2bfloat16_rn(valid ? rr.x : 0.0f);
+              o8[q + 1] = __float2bfloat16_rn(valid ? rr.y : 0.0f);
+            }
+            if (x < W)
+              *reinterpret_cast<uint4*>(out + ((srow * kG + o0 / 8) * W + x) * 8) =
+                  *reinterpret_cast<const uint4*>(o8);
+          }
         }
       }
     }
@@ -1584,8 +1639,8 @@ static int fno_forward_tc_impl(const fno_config& c, const FnoTcParams& P, const 
   LBM_CHECK_CUDA(cudaMemsetAsync(yb, 0, (size_t)B * d.kg * d.nn * 16, s));
   const int n_tables = 2 * gd.Ws * kK2 + (gd.Hs / 4) * d.nf * 8 + d.kg * hp * 8;
   LBM_TRY(launch_pdl(k_tables, dim3((n_tables + 255) / 256), dim3(256), 0, s, fw, ti, fy, ty, gd, m, hp, d.nf, d.kg));
-  const size_t lift_smem = (size_t)kLiftInStages * c.c_in * 128 * 4;
-  const size_t lift_tiles = (size_t)B * gd.Hs * ((gd.Ws + 127) / 128);
+  const size_t lift_smem = (size_t)kLiftInStages * lift_rows(kC) * c.c_in * 128 * 4;
+  const size_t lift_tiles = (size_t)B * (gd.Hs / lift_rows(kC)) * ((gd.Ws + 127) / 128);
   auto lift = [&](auto kern, int cin_c) {
     const int ctas = (int)std::min<size_t>(lift_tiles, (size_t)lift_ctas_per_sm(cin_c, kC) * nsm);
     return launch_pdl(kern, dim3(ctas), dim3(kLiftThreads), lift_smem, s, in, th[0], th[1],
@@ -1670,7 +1725,7 @@ static int tc_set_smem_attrs_k2() {
 }
 template <int kC, int kAct>
 static int tc_set_smem_attrs_act() {
-  constexpr int lift_in_max = kLiftInStages * 16 * 128 * 4;  // c_in <= 16
+  constexpr int lift_in_max = kLiftInStages * lift_rows(kC) * 16 * 128 * 4;  // c_in <= 16
   LBM_CHECK_CUDA(cudaFuncSetAttribute(k_lift_tc<kC, 1, kAct>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, lift_in_max));
   LBM_CHECK_CUDA(cudaFuncSetAttribute(k_lift_tc<kC, 2, kAct>,
