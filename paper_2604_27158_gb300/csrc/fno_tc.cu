@@ -1364,6 +1364,9 @@ constexpr int kDecStages = 4;
 constexpr int kDecCtasPerSm = 2;
 constexpr int kDecEpiWarps = 8;  // two groups of four: each drains alternate tiles
 constexpr int kDecThreads = (kDecEpiWarps + 2) * 32;
+// Output rows a tile: two for C = 16 (their hidden layers side by side in one
+// accumulator, spreading the tiles' fixed costs), else one.
+__host__ __device__ constexpr int dec_rows(int C) { return C == 16 ? 2 : 1; }
 
 // Tiles: 128 columns of a row of the output grid H0 x W0 (W0 a multiple of 128), read
 // from the latent storage (the padded grid is cropped).
@@ -1375,8 +1378,11 @@ __global__ void __launch_bounds__(kDecThreads, kDecCtasPerSm)
   pdl_trigger();
   const int H = gd.H0, W = gd.W0;
   constexpr int kG = kC / 8;
-  constexpr int kStageBytes = kG * 128 * 16;  // [channel group][x (128)][8]
-  constexpr int kAccCols = kS < 32 ? 32 : kS;
+  constexpr int kR = dec_rows(kC);                 // output rows a tile
+  constexpr int kPartBytes = kG * 128 * 16;        // one row: [channel group][x (128)][8]
+  constexpr int kStageBytes = kR * kPartBytes;
+  constexpr int kAccCols = kR * kS;                // the rows' hidden layers side by side
+  static_assert(kS == 32 || kS == 64, "hidden width");
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* q1_s = smem;                       // Q1 as [k group][s][8] bf16
   unsigned char* stages = smem + kG * kS * 16;      // kDecStages * kStageBytes
@@ -1390,7 +1396,8 @@ __global__ void __launch_bounds__(kDecThreads, kDecCtasPerSm)
   // cout <= 3: the epilogue packs Q2 rows into a float4 with the hidden bias
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int xt = W / 128;
-  const int ntiles = B * H * xt;
+  const int nrows = B * H;
+  const int ntiles = (nrows + kR - 1) / kR * xt;
   const float* w1 = params + offs[0];
   const float* b1 = params + offs[1];
   const float* w2 = params + offs[2];
@@ -1434,16 +1441,18 @@ __global__ void __launch_bounds__(kDecThreads, kDecCtasPerSm)
       const int s = k % kDecStages;
       if (k >= kDecStages) ok = mbar_wait_sleep(&empty_bar[s], ((k / kDecStages) - 1) & 1, status);
       if (!ok) break;
-      const int row = t / xt;  // b * H0 + y
-      const int x0 = (t - row * xt) * 128;
-      const int b = row / H;
-      const size_t srow = (size_t)b * gd.Hs + (row - b * H);  // latent storage row
+      const int rp = t / xt, row0 = rp * kR;  // first row b * H0 + y of the tile
+      const int nr = min(kR, nrows - row0);
+      const int x0 = (t - rp * xt) * 128;
       unsigned char* st = stages + (size_t)s * kStageBytes;
-      if (lane == 0) mbar_arrive_expect_tx(&full_bar[s], (unsigned)kStageBytes);
+      if (lane == 0) mbar_arrive_expect_tx(&full_bar[s], (unsigned)(nr * kPartBytes));
       __syncwarp();
-      if (lane < kG)
-        bulk_g2s(st + lane * 2048, theta + ((srow * kG + lane) * gd.Ws + x0) * 8, 2048,
-                 &full_bar[s]);
+      if (lane < nr * kG) {  // row r = lane / kG, channel group lane % kG
+        const int r = lane / kG, g = lane - r * kG, row = row0 + r, b = row / H;
+        const size_t srow = (size_t)b * gd.Hs + (row - b * H);  // latent storage row
+        bulk_g2s(st + r * kPartBytes + g * 2048, theta + ((srow * kG + g) * gd.Ws + x0) * 8,
+                 2048, &full_bar[s]);
+      }
     }
     for (int q = max(0, k - kDecStages); q < k; ++q)
       mbar_wait_sleep(&full_bar[q % kDecStages], (q / kDecStages) & 1, status);
@@ -1460,12 +1469,14 @@ __global__ void __launch_bounds__(kDecThreads, kDecCtasPerSm)
       tc_fence_after();
       if (lane == 0) {
         const unsigned char* st = stages + (size_t)(j % kDecStages) * kStageBytes;
+        const int nr = min(kR, nrows - t / xt * kR);
+        for (int r = 0; r < nr; ++r)  // row r into accumulator columns r S ..
 #pragma unroll
-        for (int kk = 0; kk < kG / 2; ++kk) {
-          const uint64_t ad = smem_desc(st + kk * 2 * 2048, 2048, 128);
-          const uint64_t bd = smem_desc(q1_s + kk * 2 * kS * 16, kS * 16, 128);
-          mma_bf16(tmem + acc * kAccCols, ad, bd, idesc, kk > 0);
-        }
+          for (int kk = 0; kk < kG / 2; ++kk) {
+            const uint64_t ad = smem_desc(st + r * kPartBytes + kk * 2 * 2048, 2048, 128);
+            const uint64_t bd = smem_desc(q1_s + kk * 2 * kS * 16, kS * 16, 128);
+            mma_bf16(tmem + acc * kAccCols + r * kS, ad, bd, idesc, kk > 0);
+          }
         mma_commit(&empty_bar[j % kDecStages]);
         mma_commit(&acc_full[acc]);
       }
@@ -1479,38 +1490,38 @@ __global__ void __launch_bounds__(kDecThreads, kDecCtasPerSm)
     for (int t = blockIdx.x + acc * gridDim.x, j = acc; t < ntiles; t += 2 * gridDim.x, j += 2) {
       if (!mbar_wait_sleep(&acc_full[acc], (j >> 1) & 1, status)) break;
       tc_fence_after();
-      // Q2 contraction on packed pairs: oq[q] = (sum over even j, sum over odd j)
-      float2 oq[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+      const int rp = t / xt, row0 = rp * kR, nr = min(kR, nrows - row0);
+      const int x = (t - rp * xt) * 128 + quad * 32 + lane;
+      for (int r = 0; r < nr; ++r) {
+        // Q2 contraction on packed pairs: oq[q] = (sum over even j, sum over odd j)
+        float2 oq[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
-      for (int cb = 0; cb < kAccCols / 32; ++cb) {
-        float v[32];
-        const uint32_t ta = tmem + acc * kAccCols + cb * 32 + ((uint32_t)(quad * 32) << 16);
-        if (kS >= 32) tmem_ld32(ta, v);
-        else tmem_ld16(ta, v);
-        if (cb == kAccCols / 32 - 1) {
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&acc_empty[acc]);
-        }
+        for (int cb = 0; cb < kS / 32; ++cb) {
+          float v[32];
+          tmem_ld32(tmem + acc * kAccCols + r * kS + cb * 32 + ((uint32_t)(quad * 32) << 16), v);
+          if (r == nr - 1 && cb == kS / 32 - 1) {  // the accumulator is free
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[acc]);
+          }
 #pragma unroll
-        for (int i = 0; i < (kS < 32 ? kS : 32); i += 2) {
-          const float4 e0 = ep_s[cb * 32 + i], e1 = ep_s[cb * 32 + i + 1];
-          const float2 h =
-              act_c2<kAct>(__fadd2_rn(make_float2(v[i], v[i + 1]), make_float2(e0.x, e0.y)));
-          oq[0] = __ffma2_rn(make_float2(e0.z, e0.w), h, oq[0]);
-          oq[1] = __ffma2_rn(make_float2(e1.x, e1.y), h, oq[1]);
-          oq[2] = __ffma2_rn(make_float2(e1.z, e1.w), h, oq[2]);
+          for (int i = 0; i < 32; i += 2) {
+            const float4 e0 = ep_s[cb * 32 + i], e1 = ep_s[cb * 32 + i + 1];
+            const float2 h =
+                act_c2<kAct>(__fadd2_rn(make_float2(v[i], v[i + 1]), make_float2(e0.x, e0.y)));
+            oq[0] = __ffma2_rn(make_float2(e0.z, e0.w), h, oq[0]);
+            oq[1] = __ffma2_rn(make_float2(e1.x, e1.y), h, oq[1]);
+            oq[2] = __ffma2_rn(make_float2(e1.z, e1.w), h, oq[2]);
+          }
         }
+        float o[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) o[q] = q2_s[q] + (oq[q].x + oq[q].y);
+        const int row = row0 + r, b = row / H, y = row - b * H;
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          if (q < cout) out[(((size_t)b * cout + q) * H + y) * W + x] = o[q];
       }
-      float o[3];
-#pragma unroll
-      for (int q = 0; q < 3; ++q) o[q] = q2_s[q] + (oq[q].x + oq[q].y);
-      const int row = t / xt;
-      const int b = row / H, y = row - b * H;
-      const int x = (t - row * xt) * 128 + quad * 32 + lane;
-#pragma unroll
-      for (int q = 0; q < 3; ++q)
-        if (q < cout) out[(((size_t)b * cout + q) * H + y) * W + x] = o[q];
     }
   }
   tc_fence_before();
@@ -1690,9 +1701,9 @@ static int fno_forward_tc_impl(const fno_config& c, const FnoTcParams& P, const 
   const size_t pix = (size_t)B * H * W;
   if (c.dec_layers == 1 && (c.dec_size == 32 || c.dec_size == 64) && c.c_out <= 3 &&
       W % 128 == 0) {
-    const size_t smem_tc =
-        (size_t)kC * c.dec_size * 2 + (size_t)kDecStages * (kC / 8) * 128 * 16;
-    const int ntiles = B * H * (W / 128);
+    const size_t smem_tc = (size_t)kC * c.dec_size * 2 +
+                           (size_t)kDecStages * dec_rows(kC) * (kC / 8) * 128 * 16;
+    const int ntiles = (B * H + dec_rows(kC) - 1) / dec_rows(kC) * (W / 128);
     const int ctas = std::min(ntiles, kDecCtasPerSm * nsm);
     if (c.dec_size == 32)
       LBM_TRY(launch_pdl((k_decoder_tc<kC, 32, kAct>), dim3(ctas), dim3(kDecThreads), smem_tc, s,

@@ -27,8 +27,8 @@ struct Group {
 };
 
 struct HybWs {
-  size_t rho, ux, uy, fin, fin_u, fout, fws, tables, total;
-  size_t fws_bytes;
+  size_t rho, ux, uy, fin, fin_u, fout, fout_u, fws, fws_u, tables, total;
+  size_t fws_bytes, fws_u_bytes;  // FNO workspaces of the density and velocity networks
 };
 
 // Input planes selected by a channel mask (bit 0 rho - 1, 1 u_x, 2 u_y, 3 mask; 0 = all).
@@ -62,14 +62,14 @@ static int plan_ws(const lbm_grid* grids, int ngrids, const fno_config* cfg,
   make_groups(grids, ngrids, groups);
   size_t cells = 0;
   for (int g = 0; g < ngrids; ++g) cells += (size_t)grids[g].nx * grids[g].ny;
-  size_t max_cells = 0, max_ws = 0;
+  size_t max_cells = 0, max_ws = 0, max_ws_u = 0;
   for (const Group& gr : *groups) {
     fno_sizes fs;
     LBM_TRY(fno_query(cfg, (int)gr.grids.size(), gr.H, gr.W, &fs));
     max_ws = std::max(max_ws, fs.ws_bytes);
     if (cfg_u) {
       LBM_TRY(fno_query(cfg_u, (int)gr.grids.size(), gr.H, gr.W, &fs));
-      max_ws = std::max(max_ws, fs.ws_bytes);
+      max_ws_u = std::max(max_ws_u, fs.ws_bytes);
     }
     max_cells = std::max(max_cells, gr.grids.size() * (size_t)gr.H * gr.W);
   }
@@ -88,8 +88,11 @@ static int plan_ws(const lbm_grid* grids, int ngrids, const fno_config* cfg,
   w->fin = take(max_cells * 4 * sizeof(float));
   w->fin_u = take(cfg_u ? max_cells * 4 * sizeof(float) : 0);
   w->fout = take(max_cells * 3 * sizeof(float));
+  w->fout_u = take(cfg_u ? max_cells * 2 * sizeof(float) : 0);
   w->fws = take(max_ws);
   w->fws_bytes = max_ws;
+  w->fws_u = take(max_ws_u);  // the two networks run side by side
+  w->fws_u_bytes = max_ws_u;
   w->tables = take((size_t)ngrids * (sizeof(int) + sizeof(long long)) + 256);
   w->total = p;
   return LBM_OK;
@@ -177,10 +180,11 @@ struct hybrid_handle {
   HybWs w{};
   char* ws = nullptr;
   float *rho = nullptr, *ux = nullptr, *uy = nullptr, *fin = nullptr, *fin_u = nullptr,
-        *fout = nullptr;
-  void* fws = nullptr;
+        *fout = nullptr, *fout_u = nullptr;
+  void *fws = nullptr, *fws_u = nullptr;
   cudaStream_t cap = nullptr;     // private stream used for graph capture and replay
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaStream_t side = nullptr;    // the velocity network's branch of an FNO step
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t cycle[2] = {nullptr, nullptr};  // by starting buffer parity
 };
 
@@ -188,7 +192,9 @@ static inline cudaStream_t HS(void* s) { return reinterpret_cast<cudaStream_t>(s
 
 // FNO prediction for every size group from the dense fields, clamped into the same fields.
 // With two networks both inputs are packed before either output is written back, so
-// both read the fields of the same time level.
+// both read the fields of the same time level; the velocity network then runs on a side
+// stream (a parallel branch of a captured cycle) while the density network and its
+// write-back (rho only) run on `s`, and `s` waits for it before writing u back.
 static int hyb_predict(hybrid_handle* h, cudaStream_t s) {
   lbm_handle* L = h->lbm;
   const float lo = (float)h->cfg.rho_lo, hi = (float)h->cfg.rho_hi, uc = (float)h->cfg.u_clamp;
@@ -204,14 +210,21 @@ static int hyb_predict(hybrid_handle* h, cudaStream_t s) {
                                     h->uy, channel_mask(h->cfg.in_channels_u), h->fin_u);
       LBM_CHECK_LAUNCH();
     }
+    if (h->fno_u) {  // fork: the velocity network on the side stream
+      LBM_CHECK_CUDA(cudaEventRecord(h->ev_fork, s));
+      LBM_CHECK_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+      LBM_TRY(fno_forward(h->fno_u, h->fin_u, h->fout_u, B, gr.H, gr.W, h->fws_u,
+                          h->w.fws_u_bytes, h->side));
+      LBM_CHECK_CUDA(cudaEventRecord(h->ev_join, h->side));
+    }
     LBM_TRY(fno_forward(h->fno, h->fin, h->fout, B, gr.H, gr.W, h->fws, h->w.fws_bytes, s));
     k_unpack<<<blocks, 256, 0, s>>>(L->gd_d, gr.grids_d, B, gr.H, gr.W, h->fout,
                                     h->fno_u ? 1 : 0, lo, hi, uc, h->rho, h->ux, h->uy);
     LBM_CHECK_LAUNCH();
-    if (h->fno_u) {
-      LBM_TRY(fno_forward(h->fno_u, h->fin_u, h->fout, B, gr.H, gr.W, h->fws, h->w.fws_bytes, s));
-      k_unpack<<<blocks, 256, 0, s>>>(L->gd_d, gr.grids_d, B, gr.H, gr.W, h->fout, 2, lo, hi, uc,
-                                      h->rho, h->ux, h->uy);
+    if (h->fno_u) {  // join
+      LBM_CHECK_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
+      k_unpack<<<blocks, 256, 0, s>>>(L->gd_d, gr.grids_d, B, gr.H, gr.W, h->fout_u, 2, lo, hi,
+                                      uc, h->rho, h->ux, h->uy);
       LBM_CHECK_LAUNCH();
     }
   }
@@ -303,7 +316,9 @@ int hybrid_create(lbm_handle* lbm, fno_handle* fno, fno_handle* fno_u, const hyb
   h->fin = reinterpret_cast<float*>(h->ws + h->w.fin);
   h->fin_u = reinterpret_cast<float*>(h->ws + h->w.fin_u);
   h->fout = reinterpret_cast<float*>(h->ws + h->w.fout);
+  h->fout_u = reinterpret_cast<float*>(h->ws + h->w.fout_u);
   h->fws = h->ws + h->w.fws;
+  h->fws_u = h->ws + h->w.fws_u;
   // per-group index / offset tables
   std::vector<int> ids;
   int* ids_d = reinterpret_cast<int*>(h->ws + h->w.tables);
@@ -315,10 +330,12 @@ int hybrid_create(lbm_handle* lbm, fno_handle* fno, fno_handle* fno_u, const hyb
           cudaSuccess ||
       cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
     set_error("hybrid_create: %s", cudaGetErrorString(cudaGetLastError()));
-    if (h->cap) cudaStreamDestroy(h->cap);
-    delete h;
+    hybrid_destroy(h);
     return LBM_ERR_CUDA;
   }
   *out = h;
@@ -415,6 +432,9 @@ int hybrid_destroy(hybrid_handle* h) {
     if (h->cycle[p]) cudaGraphExecDestroy(h->cycle[p]);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->side) cudaStreamDestroy(h->side);
   if (h->cap) cudaStreamDestroy(h->cap);
   delete h;
   return LBM_OK;
