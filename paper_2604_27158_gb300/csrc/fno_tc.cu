@@ -230,7 +230,8 @@ constexpr int kLiftThreads = 9 * 32;  // warps 0-3 producer, 4 MMA, 5-8 epilogue
 // 16 input channels and their prefetch, which would spill at three)
 constexpr int lift_ctas_per_sm(int cin, int C) { return cin > 0 || C < 64 ? 3 : 2; }
 // Grid rows a tile: two for C = 16 (the second row fills the other 16 columns of the
-// 32-column accumulator, halving the tiles' fixed costs), else one.
+// 32-column accumulator, halving the tiles' fixed costs), else one (two rows of a wider
+// latent spill the producers at this occupancy).
 __host__ __device__ constexpr int lift_rows(int C) { return C == 16 ? 2 : 1; }
 template <int kC, int kCin, int kAct>
 __global__ void __launch_bounds__(kLiftThreads, lift_ctas_per_sm(kCin, kC))
@@ -244,9 +245,8 @@ __global__ void __launch_bounds__(kLiftThreads, lift_ctas_per_sm(kCin, kC))
   constexpr int kK = kHid < 16 ? 16 : kHid;  // MMA K (zero-padded hidden units)
   constexpr int kKG = kK / 8;
   constexpr int kX = kCin > 0 ? kCin + 2 : 18;  // inputs and the two coordinates
-  constexpr int kAccCols = kC < 32 ? 32 : kC;
   constexpr int kR = lift_rows(kC);  // grid rows a tile
-  static_assert(kR * kC <= kAccCols, "rows fit the accumulator");
+  constexpr int kAccCols = kR * kC < 32 ? 32 : kR * kC;  // the rows side by side
   const int cin = kCin > 0 ? kCin : cin_rt;
   const int cin2 = cin + 2;
   __shared__ __align__(1024) unsigned char a_s[kLiftStages][kR][kKG * 2048];  // [k group][x][8]
@@ -1147,9 +1147,9 @@ constexpr int kInvThreads = (kInvEpiWarps + 2) * 32;
 __host__ __device__ constexpr size_t inv_res_bytes(int C, int k2) {
   return (size_t)(k2 / 8) * 2048 + ((size_t)(C / 8) * C * 16 + 1023) / 1024 * 1024;
 }
-// Grid rows a tile: four for C = 16 (each row's MMA fills 16 columns of a 64-column
-// accumulator, spreading the tiles' fixed costs), else one.
-__host__ __device__ constexpr int inv_rows(int C) { return C == 16 ? 4 : 1; }
+// Grid rows a tile: four for C = 16 and two for C = 32 (each row's MMA fills C columns of
+// a 64-column accumulator, spreading the tiles' fixed costs), one for C = 64.
+__host__ __device__ constexpr int inv_rows(int C) { return C == 16 ? 4 : (C == 32 ? 2 : 1); }
 __host__ __device__ constexpr size_t inv_stage_bytes(int C, int k2) {
   return (size_t)inv_rows(C) * ((size_t)(C / 8) * 2048 + (size_t)(k2 / 8) * C * 16);
 }
@@ -1364,9 +1364,9 @@ constexpr int kDecStages = 4;
 constexpr int kDecCtasPerSm = 2;
 constexpr int kDecEpiWarps = 8;  // two groups of four: each drains alternate tiles
 constexpr int kDecThreads = (kDecEpiWarps + 2) * 32;
-// Output rows a tile: two for C = 16 (their hidden layers side by side in one
+// Output rows a tile: two for C <= 32 (their hidden layers side by side in one
 // accumulator, spreading the tiles' fixed costs), else one.
-__host__ __device__ constexpr int dec_rows(int C) { return C == 16 ? 2 : 1; }
+__host__ __device__ constexpr int dec_rows(int C) { return C <= 32 ? 2 : 1; }
 
 // Tiles: 128 columns of a row of the output grid H0 x W0 (W0 a multiple of 128), read
 // from the latent storage (the padded grid is cropped).
