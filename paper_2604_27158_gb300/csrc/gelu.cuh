@@ -14,8 +14,9 @@ namespace lbmfno {
 // beyond it the exact a Q(a) is below 6e-9 and the clamped value, 1.1e-7, stands in for it.
 // Absolute error within 5e-6 (1 + |v|) of the exact GELU (the activation is rounded to
 // bfloat16 right after, a relative step of 2^-8),
-// NaN propagates, GELU(+inf) = +inf.  max(v, 0) is written 0.5 (v + |v|) so that a NaN
-// input is not turned into 0.
+// NaN propagates, GELU(+inf) = +inf.  max(v, 0) is the NaN-propagating max.NaN (an ALU
+// instruction, which leaves the FP32 pipes to the polynomial), so that a NaN input is
+// not turned into 0.
 __device__ __forceinline__ float gelu_poly(float v) {
   constexpr float c[GELU_S_DEG + 1] = GELU_S_COEFFS;
   const float a = fminf(fabsf(v), 6.0f);
@@ -25,7 +26,9 @@ __device__ __forceinline__ float gelu_poly(float v) {
   for (int k = GELU_S_DEG - 1; k >= 0; --k) p = fmaf(p, u, c[k]);
   float e;  // exp(-a^2 / 2) = 2^(-a^2 log2(e) / 2)
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(a * a * -0.72134752044448170f));
-  return fmaf(-a, e * p, 0.5f * (v + fabsf(v)));
+  float h;
+  asm("max.NaN.f32 %0, %1, 0f00000000;" : "=f"(h) : "f"(v));
+  return fmaf(-a, e * p, h);
 }
 
 // Two activations at once with packed FP32 arithmetic: the same operations in the same
@@ -41,7 +44,9 @@ __device__ __forceinline__ float2 gelu_poly2(float2 v) {
   float2 e;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.x) : "f"(t.x));
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.y) : "f"(t.y));
-  const float2 h = __fmul2_rn(__fadd2_rn(v, make_float2(fabsf(v.x), fabsf(v.y))), make_float2(0.5f, 0.5f));
+  float2 h;
+  asm("max.NaN.f32 %0, %1, 0f00000000;" : "=f"(h.x) : "f"(v.x));
+  asm("max.NaN.f32 %0, %1, 0f00000000;" : "=f"(h.y) : "f"(v.y));
   return __ffma2_rn(make_float2(-a.x, -a.y), __fmul2_rn(e, p), h);
 }
 

@@ -44,7 +44,7 @@ def gelu_kernel_formula(v):
         p = _fma(p, u, c[k])
     t = F32(F32(a * a) * F32(-0.72134752044448170))
     e = F32(2.0 ** np.float64(t))  # the kernels use ex2.approx (relative error < 2^-22)
-    h = F32(F32(0.5) * F32(v + abs(v)))
+    h = v if np.isnan(v) else max(v, F32(0.0))  # the kernels' NaN-propagating max.NaN
     return _fma(-a, F32(e * p), h)
 
 
