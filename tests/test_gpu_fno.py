@@ -300,6 +300,28 @@ def test_lift_input_widths_on_tensor_cores(cin, width, act):
     assert e < REL_L2_FNO
 
 
+@pytest.mark.parametrize("width,B,H,pad", [(16, 1, 37, 0), (32, 1, 37, 0), (16, 3, 29, 0),
+                                           (32, 1, 28, 9)])
+def test_multi_row_tiles_with_short_last_tile(width, B, H, pad):
+    """The tensor-core inverse x-DFT (four rows a tile at C = 16, two at C = 32), decoder
+    (two rows) and lift (two rows at C = 16) on row counts that leave a short last tile
+    (B H0 or B Hv odd, or not a multiple of four), W = 128 so the decoder takes the
+    tensor cores; against the oracle."""
+    _requires_gpu()
+    s = synth.FnoShape(c_in=4, c_out=3, width=width, layers=2, modes=5, dec_size=32,
+                       padding=pad)
+    g = FnoShape(c_in=4, c_out=3, width=width, layers=2, modes=5, dec_size=32, padding=pad)
+    params = synth.fno_random_params(s, seed=width + H, out_scale=1.0)
+    net = Fno(g, synth.fno_flatten_params(s, params))
+    assert net.uses_tensor_cores(H, 128)
+    x = _inputs(B, 4, H, 128, seed=H)
+    y = net(torch.from_numpy(x).cuda()).cpu().numpy()
+    net.check(B, H, 128)
+    e = rel_l2(y, fo.fno_forward(s, params, x))
+    print(f"multi-row tiles C={width} {B}x{H}x128 pad {pad}: rel L2 {e:.3e}")
+    assert e < REL_L2_FNO
+
+
 @pytest.mark.parametrize("which", ["density", "velocity"])
 def test_double_shear_model_pair_on_tensor_cores(which):
     """The 2.6 M double-shear model group (Sec. 3.2.1; 14 channels, 3 layers, decoder 32,
