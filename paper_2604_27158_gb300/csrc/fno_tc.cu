@@ -11,16 +11,19 @@
 //  2. k_ydft_tc    Xh[a, kx][b][c] = sum_y X1[b][y][kx][c] e^{-2 pi i ky(a) y / H}
 //                  tcgen05: D[(kx, c)][(a, re|im)] = X1b[(kx, c)][(y, re|im)] * Fy
 //                  (M = 128, N = 4m rounded up to 16, K = 2H; X1 carried in bfloat16)
-//  3. k_mix        per mode: Y[b][o] = sum_c Xh[b][c] R[c][o]   (CUDA cores, FP32),
-//                  written as the bfloat16 operand Yb of the inverse y-DFT
+//  3. k_mix4 / k_mix  per mode: Y[b][o] = sum_c Xh[b][c] R[c][o] (CUDA cores, FP32),
+//                  written as the bfloat16 operand Yb of the inverse y-DFT (k_mix4: a
+//                  block per group of four modes sharing Yb's 16-byte entries, C <= 32)
 //     k_iydft_tc   Zt[b][y][k'/8][o][k'%8] = Ty[y][(a, re|im)] * Yb[(a, re|im)][(k', o)]
 //                  (k' < m real parts, m <= k' < 2m imaginary parts, M = 128 rows y)
 //  4. k_inv_x_tc   theta'[x][o] = act( sum_k' T[x][k'] Zt[k'][o] + sum_i theta[x][i] W[o][i] + b[o] )
 //                  tcgen05: D[x][o] = [T | theta][x][k] * [Zt ; W^T][k][o]
-//                  (M = 128 x positions, N = C, K = 32 + C; both operands K-major)
+//                  (M = 128 x positions, N = C, K = K2 + C; both operands K-major;
+//                  the CTA's slice of T and W^T stay in shared memory; for C <= 32
+//                  a tile covers several grid rows, side by side in the accumulator)
 // T folds 1/(H W) and the real-input inverse weights (1 for kx = 0, 2 otherwise).
-// Around the layers: k_lift_tc (layer 1 of P on CUDA cores, layer 2 as one MMA per
-// 128-pixel tile) and k_decoder_tc (Q1 as an MMA, activation and Q2 in the epilogue).
+// Around the layers: k_lift_tc (layer 1 of P on CUDA cores in producer warps, layer 2 as
+// MMAs) and k_decoder_tc (Q1 as an MMA, activation and Q2 in the epilogue).
 //
 // The layer and projection kernels are persistent and warp-specialised: epilogue warps
 // (four, or two groups of four that take alternate tiles) drain the TMEM accumulators,
@@ -1368,8 +1371,8 @@ constexpr int kDecThreads = (kDecEpiWarps + 2) * 32;
 // accumulator, spreading the tiles' fixed costs), else one.
 __host__ __device__ constexpr int dec_rows(int C) { return C <= 32 ? 2 : 1; }
 
-// Tiles: 128 columns of a row of the output grid H0 x W0 (W0 a multiple of 128), read
-// from the latent storage (the padded grid is cropped).
+// Tiles: dec_rows(C) consecutive rows (b, y) of the output grid H0 x W0, 128 columns each
+// (W0 a multiple of 128), read from the latent storage (the padded grid is cropped).
 template <int kC, int kS, int kAct>
 __global__ void __launch_bounds__(kDecThreads, kDecCtasPerSm)
     k_decoder_tc(const __nv_bfloat16* __restrict__ theta, float* __restrict__ out,
