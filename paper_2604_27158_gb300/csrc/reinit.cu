@@ -34,6 +34,7 @@ namespace {
 
 enum : unsigned char { kRiFluid = 0, kRiSolid = 1, kRiOutside = 2 };
 constexpr int kTR = kReinitRows;
+constexpr int kRiThreads = 256;  // threads a CTA (a tile's rows, columns and planes are shared out)
 constexpr int kSW = 132;      // staged row: columns x0 - 2 .. x0 + 129 (sx = 0 .. 131)
 constexpr int kOW = 136;      // slot row: hx = 0 .. 129 at hx + 3, so that hx = 1 (the
                               // tile's first column) is 16-byte aligned; 133 .. 135 unread
@@ -118,7 +119,7 @@ __device__ __forceinline__ void eval_cell(Smem& S, int hy, int hx, int rows, int
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_reinit(const GridDev* __restrict__ grids,
+__global__ void __launch_bounds__(kRiThreads, 1024 / kRiThreads) k_reinit(const GridDev* __restrict__ grids,
                                                    const int4* __restrict__ tiles,
                                                    const uint32_t* __restrict__ mask,
                                                    const float* __restrict__ rho_i,
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(kBlock) k_reinit(const GridDev* __restrict__ g
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // 0. stage rows y0 - 2 .. y0 + rows + 1 (wrapped in y) and columns x0 - 2 .. x0 + 129
   //    (wrapped in x for periodic grids, outside otherwise): a warp a row
-  constexpr int kSlotsY = (kTR + 4 + kBlock / 32 - 1) / (kBlock / 32);
+  constexpr int kSlotsY = (kTR + 4 + kRiThreads / 32 - 1) / (kRiThreads / 32);
   constexpr int kSlotsX = (kSW + 31) / 32;
   float fv[kSlotsY][kSlotsX][3];
   uint32_t mw[kSlotsY][kSlotsX];
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(kBlock) k_reinit(const GridDev* __restrict__ g
   }
 #pragma unroll
   for (int r = 0; r < kSlotsY; ++r) {
-    const int sy = warp + r * (kBlock / 32);
+    const int sy = warp + r * (kRiThreads / 32);
     int gy = y0 - 2 + sy;
     if (gy < 0 || gy >= G.ny) gy = (gy % G.ny + G.ny) % G.ny;
     const uint32_t* mrow = m + (long long)gy * G.wpr;
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(kBlock) k_reinit(const GridDev* __restrict__ g
   }
 #pragma unroll
   for (int r = 0; r < kSlotsY; ++r) {
-    const int sy = warp + r * (kBlock / 32);
+    const int sy = warp + r * (kRiThreads / 32);
 #pragma unroll
     for (int q = 0; q < kSlotsX; ++q) {
       const int sx = lane + 32 * q;
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(kBlock) k_reinit(const GridDev* __restrict__ g
   //    x0 + 128; the tile's cells also store the current velocity (0 at solid cells) for
   //    the next steady-state check
   const float kneq_tau = -3.0f * G.tau;
-  for (int e = threadIdx.x; e < (rows + 2) * 128; e += kBlock) {
+  for (int e = threadIdx.x; e < (rows + 2) * 128; e += kRiThreads) {
     const int hy = e >> 7, hx = 1 + (e & 127);
     if (hy >= 1 && hy <= rows) {
       const int gx = x0 + hx - 1;
@@ -202,13 +203,13 @@ __global__ void __launch_bounds__(kBlock) k_reinit(const GridDev* __restrict__ g
       eval_cell<false>(S, hy, hx, rows, neq_mode, kneq_tau);
     }
   }
-  if (warp == kBlock / 32 - 1 && lane < 2 * (rows + 2))  // halo columns x0 - 1, x0 + 128
+  if (warp == kRiThreads / 32 - 1 && lane < 2 * (rows + 2))  // halo columns x0 - 1, x0 + 128
     eval_cell<false>(S, lane >> 1, (lane & 1) ? 129 : 0, rows, neq_mode, kneq_tau);
   __syncthreads();
   // 2. a thread a (row, 4 columns), all nine planes: aligned 16-byte chunks, 0 at solid
   //    cells (four cell kinds in one 4-byte load)
   const int ncols = min(128, G.nx - x0);
-  for (int u = threadIdx.x; u < rows * 32; u += kBlock) {
+  for (int u = threadIdx.x; u < rows * 32; u += kRiThreads) {
     const int r = u >> 5, c0 = (u & 31) * 4;
     if (c0 >= ncols) continue;
     const uint32_t k4 = *reinterpret_cast<const uint32_t*>(&S.ks[r + 2][c0 + 2 + kKOff]);
@@ -244,7 +245,7 @@ int reinit_init(Handle*) {
 int reinit_launch(Handle* h, const int4* tiles, int ntiles, const float* rho_d,
                   const float* ux_d, const float* uy_d, int neq_mode, cudaStream_t s) {
   if (ntiles == 0) return LBM_OK;
-  k_reinit<<<ntiles, kBlock, sizeof(Smem), s>>>(h->gd_d, tiles, h->mask, rho_d, ux_d, uy_d,
+  k_reinit<<<ntiles, kRiThreads, sizeof(Smem), s>>>(h->gd_d, tiles, h->mask, rho_d, ux_d, uy_d,
                                                 neq_mode, h->f[h->cur], h->ux_prev,
                                                 h->uy_prev);
   LBM_CHECK_LAUNCH();
