@@ -465,7 +465,10 @@ typedef struct hybrid_stats {
 typedef struct hybrid_handle hybrid_handle;
 
 /* Device workspace bytes of a hybrid over the LBM batch `grids_h` with the network
- * `cfg_h` and, if cfg_u_h is not NULL, the velocity network cfg_u_h. */
+ * `cfg_h` and, if cfg_u_h is not NULL, the velocity network cfg_u_h.  The grids are
+ * predicted in size groups (one FNO call per network and group); every group and network
+ * has its own FNO buffers, because an FNO step runs them as parallel branches on streams
+ * the hybrid handle owns (forked from and joined back into the caller's stream). */
 int hybrid_query_ws(const lbm_grid* grids_h, int ngrids, const fno_config* cfg_h,
                     const fno_config* cfg_u_h, size_t* ws_h);
 

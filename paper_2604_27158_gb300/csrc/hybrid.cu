@@ -20,15 +20,23 @@
 
 namespace lbmfno {
 
+// A size group: the grids of one (ny, nx), predicted by one FNO call per network.  Each
+// group has its own FNO buffers and streams, so that the groups of an FNO step (and the
+// two networks of a group) run as parallel branches.
 struct Group {
   int H, W;                 // ny, nx of its grids
   std::vector<int> grids;   // grid indices
   int* grids_d = nullptr;   // device copy (workspace)
+  // workspace offsets: inputs of the density (or single) and velocity networks, outputs,
+  // FNO workspaces (bytes)
+  size_t fin = 0, fin_u = 0, fout = 0, fout_u = 0, fws = 0, fws_u = 0;
+  size_t fws_bytes = 0, fws_u_bytes = 0;
+  cudaStream_t st = nullptr, st_u = nullptr;  // the group's chain; its velocity network
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_done = nullptr;
 };
 
 struct HybWs {
-  size_t rho, ux, uy, fin, fin_u, fout, fout_u, fws, fws_u, tables, total;
-  size_t fws_bytes, fws_u_bytes;  // FNO workspaces of the density and velocity networks
+  size_t rho, ux, uy, tables, total;
 };
 
 // Input planes selected by a channel mask (bit 0 rho - 1, 1 u_x, 2 u_y, 3 mask; 0 = all).
@@ -62,17 +70,6 @@ static int plan_ws(const lbm_grid* grids, int ngrids, const fno_config* cfg,
   make_groups(grids, ngrids, groups);
   size_t cells = 0;
   for (int g = 0; g < ngrids; ++g) cells += (size_t)grids[g].nx * grids[g].ny;
-  size_t max_cells = 0, max_ws = 0, max_ws_u = 0;
-  for (const Group& gr : *groups) {
-    fno_sizes fs;
-    LBM_TRY(fno_query(cfg, (int)gr.grids.size(), gr.H, gr.W, &fs));
-    max_ws = std::max(max_ws, fs.ws_bytes);
-    if (cfg_u) {
-      LBM_TRY(fno_query(cfg_u, (int)gr.grids.size(), gr.H, gr.W, &fs));
-      max_ws_u = std::max(max_ws_u, fs.ws_bytes);
-    }
-    max_cells = std::max(max_cells, gr.grids.size() * (size_t)gr.H * gr.W);
-  }
   LBM_REQUIRE(cfg->c_in <= 4 && cfg->c_out <= 3 && (!cfg_u || (cfg_u->c_in <= 4 && cfg_u->c_out <= 3)),
               "hybrid: the networks read at most the 4 planes (rho-1, ux, uy, mask) and "
               "write at most (rho-1, ux, uy)");
@@ -85,14 +82,22 @@ static int plan_ws(const lbm_grid* grids, int ngrids, const fno_config* cfg,
   w->rho = take(cells * sizeof(float));
   w->ux = take(cells * sizeof(float));
   w->uy = take(cells * sizeof(float));
-  w->fin = take(max_cells * 4 * sizeof(float));
-  w->fin_u = take(cfg_u ? max_cells * 4 * sizeof(float) : 0);
-  w->fout = take(max_cells * 3 * sizeof(float));
-  w->fout_u = take(cfg_u ? max_cells * 2 * sizeof(float) : 0);
-  w->fws = take(max_ws);
-  w->fws_bytes = max_ws;
-  w->fws_u = take(max_ws_u);  // the two networks run side by side
-  w->fws_u_bytes = max_ws_u;
+  for (Group& gr : *groups) {  // every group's own buffers: the groups run side by side
+    const size_t gc = gr.grids.size() * (size_t)gr.H * gr.W;
+    fno_sizes fs;
+    LBM_TRY(fno_query(cfg, (int)gr.grids.size(), gr.H, gr.W, &fs));
+    gr.fws_bytes = fs.ws_bytes;
+    gr.fin = take(gc * 4 * sizeof(float));
+    gr.fout = take(gc * 3 * sizeof(float));
+    gr.fws = take(gr.fws_bytes);
+    if (cfg_u) {
+      LBM_TRY(fno_query(cfg_u, (int)gr.grids.size(), gr.H, gr.W, &fs));
+      gr.fws_u_bytes = fs.ws_bytes;
+      gr.fin_u = take(gc * 4 * sizeof(float));
+      gr.fout_u = take(gc * 2 * sizeof(float));
+      gr.fws_u = take(gr.fws_u_bytes);
+    }
+  }
   w->tables = take((size_t)ngrids * (sizeof(int) + sizeof(long long)) + 256);
   w->total = p;
   return LBM_OK;
@@ -179,54 +184,62 @@ struct hybrid_handle {
   std::vector<Group> groups;
   HybWs w{};
   char* ws = nullptr;
-  float *rho = nullptr, *ux = nullptr, *uy = nullptr, *fin = nullptr, *fin_u = nullptr,
-        *fout = nullptr, *fout_u = nullptr;
-  void *fws = nullptr, *fws_u = nullptr;
+  float *rho = nullptr, *ux = nullptr, *uy = nullptr;
   cudaStream_t cap = nullptr;     // private stream used for graph capture and replay
-  cudaStream_t side = nullptr;    // the velocity network's branch of an FNO step
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaEvent_t ev_fno = nullptr;   // start of an FNO step (the groups' branches wait on it)
   cudaGraphExec_t cycle[2] = {nullptr, nullptr};  // by starting buffer parity
 };
 
 static inline cudaStream_t HS(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 // FNO prediction for every size group from the dense fields, clamped into the same fields.
-// With two networks both inputs are packed before either output is written back, so
-// both read the fields of the same time level; the velocity network then runs on a side
-// stream (a parallel branch of a captured cycle) while the density network and its
-// write-back (rho only) run on `s`, and `s` waits for it before writing u back.
+// A group's chain (pack, FNO, write-back) reads and writes only its own grids' cells, so
+// the groups run as parallel branches (their own streams, forked from and joined back into
+// `s` by events, which a stream capture turns into graph edges).  With two networks both
+// inputs of a group are packed before either output is written back, so both read the
+// fields of the same time level; the velocity network runs on a further branch while the
+// density network and its write-back (rho only) run on the group's chain, which waits for
+// it before writing u back.
 static int hyb_predict(hybrid_handle* h, cudaStream_t s) {
   lbm_handle* L = h->lbm;
   const float lo = (float)h->cfg.rho_lo, hi = (float)h->cfg.rho_hi, uc = (float)h->cfg.u_clamp;
+  LBM_CHECK_CUDA(cudaEventRecord(h->ev_fno, s));
   for (Group& gr : h->groups) {
     const int B = (int)gr.grids.size();
     const size_t n = (size_t)B * gr.H * gr.W;
     const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 65535);
-    k_pack<<<blocks, 256, 0, s>>>(L->gd_d, gr.grids_d, B, gr.H, gr.W, L->mask, h->rho, h->ux,
-                                  h->uy, channel_mask(h->cfg.in_channels), h->fin);
+    float* fin = reinterpret_cast<float*>(h->ws + gr.fin);
+    float* fout = reinterpret_cast<float*>(h->ws + gr.fout);
+    float* fin_u = reinterpret_cast<float*>(h->ws + gr.fin_u);
+    float* fout_u = reinterpret_cast<float*>(h->ws + gr.fout_u);
+    cudaStream_t cs = gr.st;
+    LBM_CHECK_CUDA(cudaStreamWaitEvent(cs, h->ev_fno, 0));
+    k_pack<<<blocks, 256, 0, cs>>>(L->gd_d, gr.grids_d, B, gr.H, gr.W, L->mask, h->rho, h->ux,
+                                   h->uy, channel_mask(h->cfg.in_channels), fin);
     LBM_CHECK_LAUNCH();
     if (h->fno_u) {
-      k_pack<<<blocks, 256, 0, s>>>(L->gd_d, gr.grids_d, B, gr.H, gr.W, L->mask, h->rho, h->ux,
-                                    h->uy, channel_mask(h->cfg.in_channels_u), h->fin_u);
+      k_pack<<<blocks, 256, 0, cs>>>(L->gd_d, gr.grids_d, B, gr.H, gr.W, L->mask, h->rho, h->ux,
+                                     h->uy, channel_mask(h->cfg.in_channels_u), fin_u);
       LBM_CHECK_LAUNCH();
+      LBM_CHECK_CUDA(cudaEventRecord(gr.ev_fork, cs));  // fork: the velocity network
+      LBM_CHECK_CUDA(cudaStreamWaitEvent(gr.st_u, gr.ev_fork, 0));
+      LBM_TRY(fno_forward(h->fno_u, fin_u, fout_u, B, gr.H, gr.W, h->ws + gr.fws_u,
+                          gr.fws_u_bytes, gr.st_u));
+      LBM_CHECK_CUDA(cudaEventRecord(gr.ev_join, gr.st_u));
     }
-    if (h->fno_u) {  // fork: the velocity network on the side stream
-      LBM_CHECK_CUDA(cudaEventRecord(h->ev_fork, s));
-      LBM_CHECK_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
-      LBM_TRY(fno_forward(h->fno_u, h->fin_u, h->fout_u, B, gr.H, gr.W, h->fws_u,
-                          h->w.fws_u_bytes, h->side));
-      LBM_CHECK_CUDA(cudaEventRecord(h->ev_join, h->side));
-    }
-    LBM_TRY(fno_forward(h->fno, h->fin, h->fout, B, gr.H, gr.W, h->fws, h->w.fws_bytes, s));
-    k_unpack<<<blocks, 256, 0, s>>>(L->gd_d, gr.grids_d, B, gr.H, gr.W, h->fout,
-                                    h->fno_u ? 1 : 0, lo, hi, uc, h->rho, h->ux, h->uy);
+    LBM_TRY(fno_forward(h->fno, fin, fout, B, gr.H, gr.W, h->ws + gr.fws, gr.fws_bytes, cs));
+    k_unpack<<<blocks, 256, 0, cs>>>(L->gd_d, gr.grids_d, B, gr.H, gr.W, fout,
+                                     h->fno_u ? 1 : 0, lo, hi, uc, h->rho, h->ux, h->uy);
     LBM_CHECK_LAUNCH();
     if (h->fno_u) {  // join
-      LBM_CHECK_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
-      k_unpack<<<blocks, 256, 0, s>>>(L->gd_d, gr.grids_d, B, gr.H, gr.W, h->fout_u, 2, lo, hi,
-                                      uc, h->rho, h->ux, h->uy);
+      LBM_CHECK_CUDA(cudaStreamWaitEvent(cs, gr.ev_join, 0));
+      k_unpack<<<blocks, 256, 0, cs>>>(L->gd_d, gr.grids_d, B, gr.H, gr.W, fout_u, 2, lo, hi, uc,
+                                       h->rho, h->ux, h->uy);
       LBM_CHECK_LAUNCH();
     }
+    LBM_CHECK_CUDA(cudaEventRecord(gr.ev_done, cs));
+    LBM_CHECK_CUDA(cudaStreamWaitEvent(s, gr.ev_done, 0));
   }
   return LBM_OK;
 }
@@ -313,12 +326,6 @@ int hybrid_create(lbm_handle* lbm, fno_handle* fno, fno_handle* fno_u, const hyb
   h->rho = reinterpret_cast<float*>(h->ws + h->w.rho);
   h->ux = reinterpret_cast<float*>(h->ws + h->w.ux);
   h->uy = reinterpret_cast<float*>(h->ws + h->w.uy);
-  h->fin = reinterpret_cast<float*>(h->ws + h->w.fin);
-  h->fin_u = reinterpret_cast<float*>(h->ws + h->w.fin_u);
-  h->fout = reinterpret_cast<float*>(h->ws + h->w.fout);
-  h->fout_u = reinterpret_cast<float*>(h->ws + h->w.fout_u);
-  h->fws = h->ws + h->w.fws;
-  h->fws_u = h->ws + h->w.fws_u;
   // per-group index / offset tables
   std::vector<int> ids;
   int* ids_d = reinterpret_cast<int*>(h->ws + h->w.tables);
@@ -331,9 +338,14 @@ int hybrid_create(lbm_handle* lbm, fno_handle* fno, fno_handle* fno_u, const hyb
       cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&h->ev_fno, cudaEventDisableTiming) != cudaSuccess ||
+      !std::all_of(h->groups.begin(), h->groups.end(), [](Group& gr) {
+        return cudaStreamCreateWithFlags(&gr.st, cudaStreamNonBlocking) == cudaSuccess &&
+               cudaStreamCreateWithFlags(&gr.st_u, cudaStreamNonBlocking) == cudaSuccess &&
+               cudaEventCreateWithFlags(&gr.ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+               cudaEventCreateWithFlags(&gr.ev_join, cudaEventDisableTiming) == cudaSuccess &&
+               cudaEventCreateWithFlags(&gr.ev_done, cudaEventDisableTiming) == cudaSuccess;
+      })) {
     set_error("hybrid_create: %s", cudaGetErrorString(cudaGetLastError()));
     hybrid_destroy(h);
     return LBM_ERR_CUDA;
@@ -432,9 +444,13 @@ int hybrid_destroy(hybrid_handle* h) {
     if (h->cycle[p]) cudaGraphExecDestroy(h->cycle[p]);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
-  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
-  if (h->ev_join) cudaEventDestroy(h->ev_join);
-  if (h->side) cudaStreamDestroy(h->side);
+  if (h->ev_fno) cudaEventDestroy(h->ev_fno);
+  for (Group& gr : h->groups) {
+    for (cudaEvent_t e : {gr.ev_fork, gr.ev_join, gr.ev_done})
+      if (e) cudaEventDestroy(e);
+    if (gr.st) cudaStreamDestroy(gr.st);
+    if (gr.st_u) cudaStreamDestroy(gr.st_u);
+  }
   if (h->cap) cudaStreamDestroy(h->cap);
   delete h;
   return LBM_OK;
