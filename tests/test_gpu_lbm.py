@@ -190,6 +190,9 @@ def test_reinit_matches_oracle():
         fl = ~solid
         e = rel_l2(gg[:, fl], (f - W[:, None, None])[:, fl])
         assert e < 1e-6, (neq, e)
+        # the stored slots of solid cells hold g = 0 (no pull reads them)
+        raw = lat.get_state().cpu().numpy().reshape(9, g.ny, g.nx)
+        assert np.all(raw[:, solid] == 0.0)
 
 
 def test_residual_statistics_match_oracle():
