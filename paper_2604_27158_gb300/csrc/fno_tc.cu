@@ -533,22 +533,22 @@ __global__ void __launch_bounds__(128)
 // --------------------------------------------------- 1. forward x-DFT (tcgen05)
 constexpr int kTcThreads = 192;  // warps 0-3 epilogue, 4 producer, 5 MMA
 constexpr int kFwdChunk = 64;    // x positions per stage
-constexpr int kFwdStages = 3;
+constexpr int kFwdMaxStages = 6;  // stages: as many as two CTAs a multiprocessor hold
 constexpr int kFwdStageBytes = 128 * kFwdChunk * 2;  // 16 KB: 128 (row, channel) x 64 x
 
 template <int kC, int kK2>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_fwd_x_tc(const __nv_bfloat16* __restrict__ theta, const __nv_bfloat16* __restrict__ fw,
-               __nv_bfloat16* __restrict__ x1b, int B, int H, int W, int m,
+               __nv_bfloat16* __restrict__ x1b, int B, int H, int W, int m, int nst,
                unsigned* __restrict__ status) {
   pdl_trigger();
-  // H, W: the storage grid Hs x Ws (the table is zero beyond the layers' grid)
+  // H, W: the storage grid Hs x Ws (the table is zero beyond the layers' grid); nst stages
   constexpr int kRows = 128 / kC;  // image rows per tile
   constexpr int kG = kC / 8;       // 8-channel groups
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* fw_s = smem;                                // W * kK2 * 2 bytes
-  unsigned char* stages = smem + (size_t)W * kK2 * 2;        // kFwdStages * 16 KB
-  __shared__ __align__(8) uint64_t full_bar[kFwdStages], empty_bar[kFwdStages];
+  unsigned char* stages = smem + (size_t)W * kK2 * 2;        // nst * 16 KB
+  __shared__ __align__(8) uint64_t full_bar[kFwdMaxStages], empty_bar[kFwdMaxStages];
   __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], fw_bar;
   __shared__ uint32_t tmem_base;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -557,7 +557,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int nchunks = W / kFwdChunk;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kFwdStages; ++s) {
+    for (int s = 0; s < nst; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
@@ -588,8 +588,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int b = t / ytiles, y0 = (t - b * ytiles) * kRows;
       const int rows = min(kRows, H - y0);
       for (int ch = 0; ch < nchunks; ++ch, ++k) {
-        const int s = k % kFwdStages;
-        if (k >= kFwdStages) ok = mbar_wait_sleep(&empty_bar[s], ((k / kFwdStages) - 1) & 1, status);
+        const int s = k % nst;
+        if (k >= nst) ok = mbar_wait_sleep(&empty_bar[s], ((k / nst) - 1) & 1, status);
         if (!ok) break;
         unsigned char* st = stages + (size_t)s * kFwdStageBytes;
         if (lane == 0) mbar_arrive_expect_tx(&full_bar[s], (unsigned)(rows * kG * kFwdChunk * 16));
@@ -604,8 +604,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     // no copy may still be in flight when the CTA exits
     mbar_wait_sleep(&fw_bar, 0, status);
-    for (int q = max(0, k - kFwdStages); q < k; ++q)
-      mbar_wait_sleep(&full_bar[q % kFwdStages], (q / kFwdStages) & 1, status);
+    for (int q = max(0, k - nst); q < k; ++q)
+      mbar_wait_sleep(&full_bar[q % nst], (q / nst) & 1, status);
   } else if (warp == 5) {
     // ---------------------------------------------------------------- MMA
     constexpr uint32_t idesc = idesc_bf16(128, kK2, /*a_mn=*/true, /*b_mn=*/false);
@@ -617,8 +617,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (!ok) break;
       tc_fence_after();
       for (int ch = 0; ch < nchunks; ++ch, ++k) {
-        const int s = k % kFwdStages;
-        ok = mbar_wait_sleep(&full_bar[s], (k / kFwdStages) & 1, status);
+        const int s = k % nst;
+        ok = mbar_wait_sleep(&full_bar[s], (k / nst) & 1, status);
         if (!ok) break;
         tc_fence_after();
         if (lane == 0) {
@@ -1565,7 +1565,26 @@ static TcGrid tc_grid(const fno_config& c, int H, int W) {
   return g;
 }
 // Shared memory of the kernels whose footprint depends on the shape.
-static size_t fwd_smem(int Ws, int k2) { return (size_t)Ws * k2 * 2 + (size_t)kFwdStages * kFwdStageBytes; }
+// Stages and CTAs a multiprocessor of the forward x-DFT: two CTAs with as many stages as
+// fit half a multiprocessor's shared memory beside the table (at most kFwdMaxStages),
+// else (wide storage grids) one CTA; 0 stages when fewer than two fit.
+struct FwdPlan {
+  int stages, ctas_per_sm;
+};
+static FwdPlan fwd_plan(int Ws, int k2) {
+  const long long table = (long long)Ws * k2 * 2;
+  for (int ctas = 2; ctas >= 1; --ctas) {
+    const long long room =
+        std::min<long long>(kTcSmemMax, (long long)kTcSmemSm / ctas - 2048) - table;
+    const int n = room > 0 ? (int)std::min<long long>(kFwdMaxStages, room / kFwdStageBytes) : 0;
+    if (n >= 2) return {n, ctas};
+  }
+  return {0, 1};
+}
+static int fwd_stages(int Ws, int k2) { return fwd_plan(Ws, k2).stages; }
+static size_t fwd_smem(int Ws, int k2) {
+  return (size_t)Ws * k2 * 2 + (size_t)std::max(fwd_stages(Ws, k2), 2) * kFwdStageBytes;
+}
 static size_t ydft_smem(int C, int Hs, int m) {
   const SpecDims d = spec_dims(C, m);
   return align_up((size_t)(Hs / 4) * d.nf * 16, 1024) +
@@ -1593,7 +1612,7 @@ bool fno_tc_supported(const fno_config& c, int H, int W) {
       W < 1)
     return false;
   const int k2 = tc_k2(m);
-  return fwd_smem(g.Ws, k2) <= (size_t)kTcSmemMax && ydft_smem(C, g.Hs, m) <= (size_t)kTcSmemMax &&
+  return fwd_stages(g.Ws, k2) >= 2 && ydft_smem(C, g.Hs, m) <= (size_t)kTcSmemMax &&
          iy_stages(C, m) >= 2 && inv_stages(C, k2) >= 2 && inv_smem(C, k2) <= (size_t)kTcSmemMax;
 }
 
@@ -1672,7 +1691,7 @@ static int fno_forward_tc_impl(const fno_config& c, const FnoTcParams& P, const 
   LBM_REQUIRE(y_smem <= (size_t)kTcSmemMax && iy_smem <= (size_t)kTcSmemMax &&
                   f_smem <= (size_t)kTcSmemMax && i_smem <= (size_t)kTcSmemMax,
               "fno_forward: spectral working set too large for shared memory");
-  const int fwd_ctas = std::min(B * (gd.Hs / (128 / kC)), 2 * nsm);
+  const int fwd_ctas = std::min(B * (gd.Hs / (128 / kC)), fwd_plan(gd.Ws, kK2).ctas_per_sm * nsm);
   const int inv_xt = (gd.Ws + 127) / 128;  // a CTA keeps one column slice: grid % inv_xt == 0
   const int inv_ctas = std::max(
       inv_xt, std::min(B * gd.Hv * inv_xt, inv_ctas_per_sm<kC>() * nsm) / inv_xt * inv_xt);
@@ -1687,8 +1706,8 @@ static int fno_forward_tc_impl(const fno_config& c, const FnoTcParams& P, const 
   const size_t mix4_smem = (size_t)4 * (kC * kC + kMixB * kC) * sizeof(float2);
   int cur = 0;
   for (int n = 0; n < c.layers; ++n) {
-    LBM_TRY(launch_pdl((k_fwd_x_tc<kC, kK2>), dim3(fwd_ctas), dim3(kTcThreads), f_smem, s, th[cur], fw, x1b, B, gd.Hs, gd.Ws,
-                                                             m, status));
+    LBM_TRY(launch_pdl((k_fwd_x_tc<kC, kK2>), dim3(fwd_ctas), dim3(kTcThreads), f_smem, s, th[cur],
+                       fw, x1b, B, gd.Hs, gd.Ws, m, fwd_stages(gd.Ws, kK2), status));
     LBM_TRY(launch_pdl((k_ydft_tc<kC>), dim3(ydft_ctas), dim3(kTcThreads), y_smem, s, x1b, fy, xh, B, gd.Hs, m, status));
     if constexpr (kC <= 32)  // a block per group of four modes
       LBM_TRY(launch_pdl((k_mix4<kC>), dim3(mix4_grid), dim3(256), mix4_smem, s, xh, P.rt[n], yb,
