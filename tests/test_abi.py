@@ -89,3 +89,30 @@ def test_fno_query_rejects_invalid_shapes(kw, B, H, W):
     with pytest.raises(P.LbmError) as e:
         fno_query(FnoShape(**kw), B, H, W)
     assert e.value.code == _abi.LBM_ERR_INVALID_ARG
+
+
+def test_hybrid_workspace_holds_every_group_and_network():
+    """An FNO step runs its size groups, and the two networks of a group, as parallel
+    branches, so no two of them may share FNO buffers: the hybrid workspace (a host-only
+    query) grows by at least the FNO workspaces of both networks when a size group is
+    added, and holds those of every (group, network) pair."""
+    from paper_2604_27158_gb300._abi import call, lbm_grid
+    from paper_2604_27158_gb300.fno import FnoShape, fno_query
+    sr = FnoShape(c_in=1, c_out=1, width=16, layers=2, modes=4, dec_size=32)
+    su = FnoShape(c_in=2, c_out=2, width=16, layers=2, modes=8, dec_size=32)
+
+    def ws(grids):
+        arr = (lbm_grid * len(grids))(*[g.c() for g in grids])
+        n = ctypes.c_size_t()
+        fc, fcu = sr.c(), su.c()
+        call("hybrid_query_ws", arr, len(grids), ctypes.byref(fc), ctypes.byref(fcu),
+             ctypes.byref(n))
+        return n.value
+
+    one = [GridSpec(128, 64, 0.8)] * 3
+    two = one + [GridSpec(96, 48, 0.7)] * 2
+    fno_ws = {(B, H, W): fno_query(sr, B, H, W).ws_bytes + fno_query(su, B, H, W).ws_bytes
+              for B, H, W in ((3, 64, 128), (2, 48, 96))}
+    assert ws(one) >= fno_ws[(3, 64, 128)]
+    assert ws(two) - ws(one) >= fno_ws[(2, 48, 96)]
+    assert ws(two) >= sum(fno_ws.values())
